@@ -1,0 +1,170 @@
+"""Seeded synthetic inputs for the ETDM energy+gradient path.
+
+This module is the single source of inputs for both the CUDA path and the
+oracle.  It draws random numbers and lays out geometry; it holds none of the
+method's arithmetic (no basis values, overlaps, exponentials or energies).
+
+Every system is a plain dict of numpy arrays in atomic units:
+
+    pos        (n_atoms, 3) float64   atom positions, bohr, wrapped into [0, L)
+    Z          (n_atoms,)   float64   ion charge of each site
+    bf_atom    (M,)         int32     atom carrying each basis function
+    bf_exp     (M,)         float64   Gaussian exponent alpha, bohr^-2
+    bf_rcut    (M,)         float64   hard truncation radius, bohr
+    box        (3,)         float64   orthorhombic cell edges, bohr
+    grid       (3,)         int32     real-space grid points per axis
+    ion_sigma  float                  width of the Gaussian ion charge, bohr
+    n_electrons int                   even; N = n_electrons / 2 doubly occupied
+    a0         (N, M-N)     float64   starting occupied-virtual block A_ov
+
+The recipes (positions, exponents, grid, truncation, A_ov distribution) follow
+the workloads the paper studies (small molecules, liquid-water boxes), shrunk
+to a model Hamiltonian of s-type Gaussians; the water-like boxes stand in for
+the paper's liquid-water snapshots, which are not reproduced here.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+ANGSTROM = 1.8897261246  # bohr per angstrom (CODATA 2018)
+
+HEAVY_EXPS = [0.3 * 10.0 ** (k / 3.0) for k in range(4)]  # 0.3 .. 3.0 bohr^-2
+LIGHT_EXPS = [0.5, 1.5]
+
+
+def _min_image_dist(d, box):
+    d = d - box * np.round(d / box)
+    return np.sqrt((d * d).sum(-1))
+
+
+def _uniform_positions(rng, n, box, min_sep):
+    pos = []
+    while len(pos) < n:
+        p = rng.uniform(0.0, 1.0, 3) * box
+        if all(_min_image_dist(p - q, box) >= min_sep for q in pos):
+            pos.append(p)
+    return np.array(pos)
+
+
+def _random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def _finish(pos, Z, exps_per_atom, box, grid, rcut, sigma, a_sigma, a_seed):
+    bf_atom, bf_exp = [], []
+    for ia, exps in enumerate(exps_per_atom):
+        for e in exps:
+            bf_atom.append(ia)
+            bf_exp.append(e)
+    bf_exp = np.array(bf_exp, dtype=np.float64)
+    if rcut is None:
+        # no radius given: cut where the Gaussian has fallen to 1e-16
+        bf_rcut = np.sqrt(math.log(1e16) / bf_exp)
+    else:
+        bf_rcut = np.full(len(bf_exp), float(rcut))
+    Zarr = np.asarray(Z, dtype=np.float64)
+    n_e = int(round(Zarr.sum()))
+    assert n_e % 2 == 0, "closed-shell systems only"
+    M = len(bf_exp)
+    N = n_e // 2
+    box = np.asarray(box, dtype=np.float64)
+    pos = np.mod(np.asarray(pos, dtype=np.float64), box)
+    a0 = np.random.default_rng(a_seed).normal(0.0, a_sigma, size=(N, M - N))
+    return dict(
+        pos=pos,
+        Z=Zarr,
+        bf_atom=np.array(bf_atom, dtype=np.int32),
+        bf_exp=bf_exp,
+        bf_rcut=bf_rcut,
+        box=box,
+        grid=np.asarray(grid, dtype=np.int32),
+        ion_sigma=float(sigma),
+        n_electrons=n_e,
+        a0=a0,
+    )
+
+
+def random_atoms(n_atoms=8, box_ang=6.4, grid=(32, 32, 32), min_sep_ang=1.0,
+                 exps=(0.5, 1.5), Z=1.0, rcut_ang=None, sigma=0.5,
+                 a_sigma=0.05, seed=0):
+    """Atoms at seeded uniform positions in a cubic box (min-image separation)."""
+    box = np.full(3, box_ang * ANGSTROM)
+    rng = np.random.default_rng(seed + 1000)
+    pos = _uniform_positions(rng, n_atoms, box, min_sep_ang * ANGSTROM)
+    rcut = None if rcut_ang is None else rcut_ang * ANGSTROM
+    return _finish(pos, [Z] * n_atoms, [list(exps)] * n_atoms, box, grid,
+                   rcut, sigma, a_sigma, seed)
+
+
+def water_box(lattice=(4, 4, 2), box_ang=9.9, grid=(96, 96, 96), rcut_ang=4.0,
+              sigma=0.5, a_sigma=0.02, seed=1, jitter_ang=0.2):
+    """Triatomic water-like units: heavy site Z=6 (4 Gaussians 0.3..3.0) and
+    two light sites Z=1 (exponents 0.5, 1.5) at 0.96 A, 104.5 deg, heavy sites
+    on a jittered lattice, each unit randomly oriented."""
+    box = np.full(3, box_ang * ANGSTROM)
+    rng = np.random.default_rng(seed + 1000)
+    nx, ny, nz = lattice
+    half = math.radians(104.5) / 2.0
+    bond = 0.96 * ANGSTROM
+    local = np.array([[0.0, 0.0, 0.0],
+                      [bond * math.sin(half), 0.0, bond * math.cos(half)],
+                      [-bond * math.sin(half), 0.0, bond * math.cos(half)]])
+    pos, Z, exps = [], [], []
+    for i in range(nx):
+        for j in range(ny):
+            for k in range(nz):
+                c = (np.array([i, j, k]) + 0.5) / np.array(lattice) * box
+                c = c + rng.uniform(-jitter_ang, jitter_ang, 3) * ANGSTROM
+                R = _random_rotation(rng)
+                for s in range(3):
+                    pos.append(c + R @ local[s])
+                    Z.append(6.0 if s == 0 else 1.0)
+                    exps.append(HEAVY_EXPS if s == 0 else LIGHT_EXPS)
+    return _finish(np.array(pos), Z, exps, box, grid, rcut_ang * ANGSTROM,
+                   sigma, a_sigma, seed)
+
+
+# --- named workloads -------------------------------------------------------
+
+def config_small_molecule():
+    """8 atoms, M=16, N=4, 32^3 grid, A_ov ~ N(0, 0.05) (seed 0)."""
+    return random_atoms()
+
+
+def config_water32():
+    """32 water-like units (96 atoms), M=256, N=128, 96^3 grid, r_c = 4 A,
+    A_ov ~ N(0, 0.02) (seed 1)."""
+    return water_box()
+
+
+def config_water576():
+    """576 water-like units (1728 atoms), M=4608, N=2304, 192^3 grid,
+    r_c = 3.5 A, 25 A box, A_ov ~ N(0, 0.01) (seed 2)."""
+    return water_box(lattice=(9, 8, 8), box_ang=25.0, grid=(192, 192, 192),
+                     rcut_ang=3.5, a_sigma=0.01, seed=2)
+
+
+def tiny(grid=(16, 16, 16), seed=7):
+    """2 atoms with 2 functions each in a 4 A box: brute-force sized."""
+    return random_atoms(n_atoms=2, box_ang=4.0, grid=grid, a_sigma=0.1,
+                        seed=seed)
+
+
+def ragged_water(grid=(36, 28, 44), seed=11):
+    """2 water-like units on a grid whose sizes are not tile multiples."""
+    return water_box(lattice=(2, 1, 1), box_ang=6.0, grid=grid, rcut_ang=3.0,
+                     a_sigma=0.05, seed=seed)
+
+
+def direction(shape, seed, scale=1.0):
+    """A seeded random array (search directions, FD probes, test vectors)."""
+    return np.random.default_rng(seed).normal(0.0, scale, size=shape)

@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, textbook special cases, finite differences, invariances, brute force,
+or a second route through a different formula of the paper.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import etdm_synth as synth
+from oracle.etdm_oracle import (LBFGS, Oracle, cubic_min, line_search,
+                                minimize, wolfe_ok)
+import oracle.etdm_oracle as orc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def small():
+    d = synth.config_small_molecule()
+    return d, Oracle(d)
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    d = synth.ragged_water()
+    return d, Oracle(d)
+
+
+# ---- matrix exponential (Eq. 35, Eq. 37) ------------------------------------
+
+@pytest.mark.parametrize("N,V,scale", [(1, 1, 0.7), (4, 12, 0.05), (7, 5, 0.4),
+                                       (12, 20, 1.3)])
+def test_expm_three_routes_agree_and_unitary(N, V, scale):
+    d = synth.tiny()
+    o = Oracle(d)
+    o.N, o.M, o.V = N, N + V, V
+    Aov = synth.direction((N, V), seed=N * 31 + V, scale=scale)
+    A = o.full_A(Aov)
+    U35 = o.expm_eig(A)
+    U37 = o.expm_occvirt(Aov)
+    Ut = np.asarray(o.expm_taylor(A), dtype=np.float64)
+    assert np.abs(U35.imag).max() < 1e-13
+    assert np.abs(U35.real - Ut).max() < 1e-13
+    assert np.abs(U37 - Ut).max() < 1e-13
+    assert np.abs(U37.T @ U37 - np.eye(N + V)).max() < 1e-12
+
+
+def test_expm_rotation_special_case():
+    # one occupied, one virtual: exp(A) is the plane rotation by theta
+    o = Oracle(synth.tiny())
+    o.N, o.M, o.V = 1, 2, 1
+    th = 0.83
+    U = o.expm_occvirt(np.array([[th]]))
+    R = np.array([[math.cos(th), math.sin(th)], [-math.sin(th), math.cos(th)]])
+    assert np.abs(U - R).max() < 1e-15
+    assert np.abs(o.expm_eig(o.full_A(np.array([[th]]))).real - R).max() < 1e-15
+
+
+def test_expm_small_A_matches_short_taylor():
+    o = Oracle(synth.tiny())
+    o.N, o.M, o.V = 3, 8, 5
+    Aov = synth.direction((3, 5), seed=3, scale=1e-3)
+    A = o.full_A(Aov)
+    ref, term = np.eye(8), np.eye(8)
+    for k in range(1, 6):
+        term = term @ A / k
+        ref = ref + term
+    assert np.abs(o.expm_occvirt(Aov) - ref).max() < 1e-15
+    assert np.abs(o.expm_eig(A).real - ref).max() < 1e-15
+
+
+# ---- basis, overlap, kinetic (Eq. 4, Eq. 11) -----------------------------------
+
+def test_overlap_matches_grid_quadrature(small):
+    d, o = small
+    X = o.X()
+    S_quad = o.dV * X.T @ X
+    S, _ = o.overlap_kinetic()
+    assert np.abs(S - S_quad).max() < 1e-8
+
+
+def test_isolated_kinetic_diagonal_is_three_halves_alpha():
+    d = synth.random_atoms(n_atoms=1, box_ang=12.0, exps=(0.4, 1.1, 2.5),
+                           Z=2.0, rcut_ang=4.0, seed=5)
+    o = Oracle(d)
+    S, T = o.overlap_kinetic()
+    assert np.allclose(np.diag(S), 1.0, atol=1e-14)
+    assert np.allclose(np.diag(T), 1.5 * np.array([0.4, 1.1, 2.5]), atol=1e-14)
+
+
+def test_kinetic_matches_spectral_laplacian(small):
+    d, o = small
+    X = o.X()
+    _, G2 = o.gvectors()
+    F = np.fft.fftn(X.reshape(*tuple(o.n), o.M), axes=(0, 1, 2)).reshape(-1, o.M)
+    # Parseval: dV sum_r grad f . grad g = (dV / Ng) sum_G G^2 conj(F) G
+    T_quad = 0.5 * o.dV / o.G * (F.conj().T @ (G2.reshape(-1, 1) * F)).real
+    _, T = o.overlap_kinetic()
+    assert np.abs(T - T_quad).max() < 1e-6
+
+
+# ---- density (Eq. 2, Eq. 12) ------------------------------------------------------
+
+def test_density_trace_and_integral(small):
+    d, o = small
+    ref = o.reference()
+    O = o.orbitals(d["a0"])
+    D = o.density_matrix(O)
+    assert abs(float(np.sum(D * ref["S"])) - d["n_electrons"]) < 1e-12
+    rho = o.density(D)
+    assert abs(o.dV * rho.sum() - d["n_electrons"]) < 1e-8 * d["n_electrons"]
+    assert rho.min() > -1e-15
+
+
+def test_density_via_orbitals(ragged):
+    d, o = ragged
+    O = o.orbitals(d["a0"])
+    rho_D = o.density(o.density_matrix(O)).ravel()
+    phi = o.X() @ O[:, : o.N]
+    rho_orb = 2.0 * (phi * phi).sum(1)
+    assert np.abs(rho_D - rho_orb).max() < 1e-12 * max(1.0, rho_orb.max())
+
+
+def test_reference_orthonormal_and_sorted(small):
+    d, o = small
+    ref = o.reference()
+    C0 = ref["C0"]
+    assert np.abs(C0.T @ ref["S"] @ C0 - np.eye(o.M)).max() < 1e-12
+    diag = np.einsum("mj,mn,nj->j", C0, ref["hcore"], C0)
+    assert np.all(np.diff(diag) >= 0)
+
+
+# ---- potentials (Eq. 1) ------------------------------------------------------------
+
+def test_poisson_plane_wave():
+    d = synth.random_atoms(n_atoms=1, box_ang=5.0, grid=(20, 24, 16), Z=2.0,
+                           seed=3)
+    o = Oracle(d)
+    x = o.coords(0)[:, None, None]
+    y = o.coords(1)[None, :, None]
+    z = o.coords(2)[None, None, :]
+    k = 2 * math.pi * np.array([2, -3, 1]) / o.L
+    rho = np.cos(k[0] * x + k[1] * y + k[2] * z) + 0.0 * y + 0.0 * z
+    vh = o.hartree_potential(rho)
+    assert np.abs(vh - 4 * math.pi / (k @ k) * rho).max() < 1e-12
+
+
+def test_vext_single_ion_near_field():
+    # one ion at a grid point of a cubic cell: v(r) - v(0) follows the
+    # Gaussian-charge potential plus the r^2 term of the neutralizing uniform
+    # background (phi_bg = 2 pi Z r^2 / (3 Omega), v = -phi for an electron);
+    # the images add no isotropic r^2 term in a cubic cell
+    L_ang = 8.0
+    d = synth.random_atoms(n_atoms=1, box_ang=L_ang, grid=(64, 64, 64), Z=4.0,
+                           seed=1)
+    o = Oracle(d)
+    o.pos = np.array([[32 * o.h[0], 32 * o.h[1], 32 * o.h[2]]])
+    v = o.vext()
+    sig, Z = o.sigma, 4.0
+    r = np.arange(1, 8) * o.h[0]
+    num = v[32 + np.arange(1, 8), 32, 32] - v[32, 32, 32]
+    exact = -Z * (erf(r / (math.sqrt(2) * sig)) / r - math.sqrt(2 / math.pi) / sig) \
+        - 2 * math.pi * Z / (3 * o.omega) * r * r
+    assert np.abs(num - exact).max() < 2e-4
+
+
+def test_slater_exchange_pair():
+    o = Oracle(synth.tiny())
+    rho = np.array([1.0, 0.37, 2.2, 0.0])
+    e, v = o.lda_x(rho)
+    assert abs(e[0] + 0.75 * (3 / math.pi) ** (1 / 3)) < 1e-15
+    h = 1e-6
+    ep, _ = o.lda_x(rho + h)
+    em, _ = o.lda_x(rho - h)
+    assert np.abs((ep - em)[:3] / (2 * h) - v[:3]).max() < 1e-8
+    assert e[3] == 0.0 and v[3] == 0.0
+
+
+# ---- energy and gradient (Eq. 1, Eq. 14, Eq. 39-42) --------------------------------
+
+def test_energy_invariant_under_occupied_rotation(small):
+    d, o = small
+    ref = o.reference()
+    R, _ = np.linalg.qr(synth.direction((o.N, o.N), seed=9))
+    C0r = ref["C0"].copy()
+    C0r[:, : o.N] = C0r[:, : o.N] @ R
+    a = d["a0"]
+    E, g = o.energy_grad(a)
+    Er, gr = o.energy_grad(R.T @ a, C0=C0r)
+    assert abs(E - Er) < 1e-12
+    assert np.abs(gr - R.T @ g).max() < 1e-11
+
+
+@pytest.mark.parametrize("which", ["small", "ragged"])
+def test_gradient_central_differences(which, small, ragged):
+    d, o = small if which == "small" else ragged
+    a = d["a0"]
+    E, g = o.energy_grad(a)
+    rng = np.random.default_rng(4)
+    idx = [tuple(rng.integers(0, s) for s in a.shape) for _ in range(8)]
+    h = 1e-5
+    for (i, j) in idx:
+        ap = a.copy(); ap[i, j] += h
+        am = a.copy(); am[i, j] -= h
+        fd = (o.energy(ap) - o.energy(am)) / (2 * h)
+        assert abs(fd - g[i, j]) <= max(1e-6, 1e-5 * abs(g[i, j])), (i, j, fd, g[i, j])
+
+
+def test_gradient_at_zero_is_eq42(small):
+    d, o = small
+    a = np.zeros_like(d["a0"])
+    E, g, ex = o.energy_grad(a, want=True)
+    Hmo = ex["Hmo"]
+    N = o.N
+    # dE/dRe a_ij = 2 (f_j - f_i) H_ji with f_i = 2, f_j = 0
+    assert np.abs(g - (-4.0) * Hmo[N:, :N].T).max() < 1e-12
+
+
+def test_gradient_series_eq19(small):
+    d, o = small
+    a = 1e-2 * synth.direction(d["a0"].shape, seed=12)
+    _, _, ex = o.energy_grad(a, want=True)
+    A, L = o.full_A(a), ex["L"]
+    ser, term = L.copy(), L.copy()
+    for n in range(2, 12):
+        term = (A @ term - term @ A) / n
+        ser = ser + term
+    G = ex["dEda"] / np.where(np.eye(o.M, dtype=bool), 0.5, 1.0)
+    assert np.abs(G.T - ser).max() < 1e-13 * max(1.0, np.abs(ser).max())
+
+
+def test_imaginary_diagonal_direction_has_zero_gradient(small):
+    # a purely imaginary diagonal of A only changes orbital phases
+    d, o = small
+    _, _, ex = o.energy_grad(d["a0"], want=True)
+    assert np.abs(np.diag(ex["dEda"]).real).max() < 1e-12
+
+
+# ---- preconditioner (Eq. 31-34) ---------------------------------------------------
+
+def test_diagonal_hessian_eq31_fixed_potential():
+    d = synth.config_small_molecule()
+    o = Oracle(d, hartree=False, exchange=False)
+    ref = o.reference()
+    from scipy.linalg import eigh
+    eps, C = eigh(ref["hcore"], ref["S"])
+    h = 1e-4
+    for (i, j) in [(0, 0), (1, 5), (3, 11), (2, 7)]:
+        e = np.zeros((o.N, o.V)); e[i, j] = h
+        Ep, E0, Em = o.energy(e, C0=C), o.energy(0 * e, C0=C), o.energy(-e, C0=C)
+        fd2 = (Ep - 2 * E0 + Em) / h**2
+        want = -2 * (eps[i] - eps[o.N + j]) * (2.0 - 0.0)
+        assert abs(fd2 - want) < 1e-5 * max(1.0, abs(want)), (fd2, want)
+
+
+def test_preconditioner_formula():
+    o = Oracle(synth.config_small_molecule())
+    eps = np.linspace(-1.0, 2.0, o.M)
+    P = o.precond(eps, beta=3.0)
+    i, j = 2, 5
+    want = 1.0 / (-2 * 0.75 * (eps[i] - eps[o.N + j]) * 2.0 + 0.25 * 3.0)
+    assert abs(P[i, j] - want) < 1e-15
+    assert P.shape == (o.N, o.V) and np.all(P > 0)
+
+
+def test_paper_parameters_golden():
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
+        g = json.load(f)
+    assert (orc.C1, orc.C2, orc.DELTA, orc.SIGMA, orc.EPS_E) == tuple(g["eq29"][k] for k in ("c1", "c2", "delta", "sigma", "epsilon"))
+    assert orc.GAMMA == g["eq33_gamma"]
+    assert orc.LBFGS_M == g["lbfgs_m"]
+
+
+# ---- L-BFGS and line search (Sec. 3.1-3.2) --------------------------------------------
+
+def test_lbfgs_two_loop_equals_dense_bfgs():
+    rng = np.random.default_rng(0)
+    n = 9
+    Q = rng.normal(size=(n, n)); Amat = Q @ Q.T + n * np.eye(n)
+    b = rng.normal(size=n)
+    diagP = lambda beta: 1.0 / (np.linspace(1, 3, n) + 0.25 * beta)
+    lb = LBFGS(diagP, m=3)
+    x = rng.normal(size=n)
+    pairs = []
+    for k in range(6):
+        gr = Amat @ x - b
+        p = lb.step(x, gr)
+        # dense BFGS inverse update from H0 over the same (<= m) stored pairs
+        H = np.diag(diagP(lb.beta))
+        for s, y in zip(lb.s, lb.y):
+            r = 1.0 / (y @ s)
+            I = np.eye(n)
+            H = (I - r * np.outer(s, y)) @ H @ (I - r * np.outer(y, s)) + r * np.outer(s, s)
+        assert np.abs(p - (-H @ gr)).max() < 1e-12 * max(1, np.abs(p).max())
+        x = x + 0.5 * p
+
+
+def test_cubic_min_exact_on_cubic():
+    f = lambda t: (t - 0.3) ** 2 * (t + 2.0)
+    df = lambda t: 2 * (t - 0.3) * (t + 2.0) + (t - 0.3) ** 2
+    t = cubic_min(0.0, f(0.0), df(0.0), 1.0, f(1.0), df(1.0))
+    assert abs(t - 0.3) < 1e-12
+
+
+def test_line_search_returns_wolfe_point():
+    f = lambda t: (t - 3.7) ** 2 - 1.0 + 0.1 * (t - 3.7) ** 3 / 10
+    df = lambda t: 2 * (t - 3.7) + 0.03 * (t - 3.7) ** 2
+    phi = lambda t: (f(t), df(t), t)
+    alpha, E, d, _, trials = line_search(phi, f(0.0), df(0.0))
+    assert wolfe_ok(alpha, E, d, f(0.0), df(0.0))
+    assert trials <= 20
+
+
+def test_minimization_decreases_energy(small):
+    d, o = small
+    hist, a = minimize(o, d["a0"], n_steps=8)
+    Es = [h[0] for h in hist]
+    assert all(Es[k + 1] <= Es[k] + 1e-12 for k in range(len(Es) - 1))
+    _, g = o.energy_grad(a)
+    _, g0 = o.energy_grad(d["a0"])
+    assert np.abs(g).max() < 0.2 * np.abs(g0).max()
+
+
+# ---- truncation lists (index work) --------------------------------------------------
+
+@pytest.mark.parametrize("tile", [(4, 4, 4), (8, 4, 4)])
+def test_tile_lists_cover_nonzero_basis_values(ragged, tile):
+    d, o = ragged
+    X = o.X().reshape(*tuple(o.n), o.M)
+    nt = o.n_tiles(tile)
+    nby = -(-int(o.n[1]) // tile[1])
+    nbz = -(-int(o.n[2]) // tile[2])
+    for t in range(0, nt, max(1, nt // 9)):
+        keys = o.tile_list(tile, t)
+        assert np.all(np.diff(keys) > 0)
+        bx, rem = divmod(t, nby * nbz)
+        by, bz = divmod(rem, nbz)
+        sub = X[bx * tile[0]:(bx + 1) * tile[0], by * tile[1]:(by + 1) * tile[1],
+                bz * tile[2]:(bz + 1) * tile[2]]
+        nonzero = set(np.nonzero(np.abs(sub).reshape(-1, o.M).max(0) > 0)[0])
+        assert set((keys // 512).tolist()) == nonzero
+
+
+def test_oracle_matches_stored_small_molecule_values(small):
+    # stored values come from tests/golden/make_golden.py (oracle only); this
+    # guards the oracle against unreviewed arithmetic changes
+    d, o = small
+    with open(os.path.join(GOLDEN, "small_molecule_oracle.json")) as f:
+        gold = json.load(f)
+    E, g = o.energy_grad(d["a0"])
+    assert abs(E - gold["E_a0"]) < 1e-11
+    assert np.abs(g - np.array(gold["g_a0"])).max() < 1e-10
+    assert o.reference()["order"].tolist() == gold["order"]
