@@ -1,0 +1,198 @@
+/*
+ * etdm.h -- C ABI of the ETDM energy + gradient library (sm_103a).
+ *
+ * Exponential-transformation direct minimization (ETDM) of a Kohn-Sham
+ * energy in a localized Gaussian basis, after Ivanov, Jonsson, Vegge and
+ * Jonsson, arXiv:2101.12597.  The orbitals are O = C0 exp(A) (Eq. 7) with the
+ * occupied-virtual parametrization A = [[0, A_ov], [-A_ov^T, 0]] (Eq. 36);
+ * the library evaluates E(A_ov) (Eq. 1) and dE/dA_ov (Eq. 14, 20), applies
+ * the diagonal preconditioner (Eq. 33-34) and the L-BFGS two-loop update
+ * (Sec. 3.1), and runs the line search of Eq. 25-29 on the host.
+ *
+ * The model Hamiltonian is: normalized s-type Gaussians truncated at a hard
+ * radius, Gaussian ion charges, a spectral (FFT) Poisson solve and Slater
+ * exchange, all on a periodic real-space grid at the Gamma point.
+ *
+ * Conventions (every entry point):
+ *  - Return value: ETDM_OK (0) or a negative ETDM_ERR_* status; nothing
+ *    throws across the ABI.  etdm_last_error() gives a one-line message.
+ *  - Pointers named *_dev are device pointers on the handle's device; *_host
+ *    are host pointers.  All are caller-owned and borrowed only for the
+ *    duration of the call (device work is ordered on the given stream; the
+ *    caller keeps buffers alive until that stream reaches the call's end).
+ *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
+ *    stream).  One handle must not be used from two streams at once.
+ *  - Matrices are row-major FP64.  A_ov, g and p are N x V row-major
+ *    (N occupied, V = M - N virtual orbitals), so g[i*V + j] = dE/dA_ov[i][j].
+ *  - Units: bohr, hartree.
+ */
+#ifndef ETDM_H
+#define ETDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct etdm_handle etdm_handle; /* opaque; owns all device memory */
+
+enum {
+  ETDM_OK = 0,
+  ETDM_ERR_INVALID_ARG = -1, /* bad size, pointer or option */
+  ETDM_ERR_CUDA = -2,        /* a CUDA call failed (message has the name) */
+  ETDM_ERR_OOM = -3,         /* device allocation failed */
+  ETDM_ERR_NOT_CONVERGED = -4, /* iterative init step did not converge */
+  ETDM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  ETDM_ERR_STATE = -6,       /* call order (e.g. precondition before init) */
+  ETDM_ERR_NUMERIC = -7      /* NaN/Inf, S not positive definite, |P| too large */
+};
+
+enum {
+  ETDM_PREC_FP64 = 0,  /* every step in FP64 */
+  ETDM_PREC_MIXED = 1  /* grid contractions on tensor cores with split
+                          operands and FP32 accumulation; exp(A), energy
+                          sums and L-BFGS in FP64 */
+};
+
+/* One periodic system (Eq. 3-5 at the Gamma point).  All host pointers,
+ * read during etdm_init_basis only. */
+typedef struct {
+  int32_t n_atoms;
+  const double *pos;      /* [n_atoms*3] positions, bohr, inside [0, box) */
+  const double *Z;        /* [n_atoms] ion charges */
+  int32_t n_basis;        /* M */
+  const int32_t *bf_atom; /* [M] atom carrying each s-Gaussian */
+  const double *bf_exp;   /* [M] exponents alpha, bohr^-2 */
+  const double *bf_rcut;  /* [M] truncation radii, bohr (0 < r_c < 2 min box) */
+  double box[3];          /* orthorhombic cell edges, bohr */
+  int32_t grid[3];        /* grid points per axis; prime factors <= 13 */
+  double ion_sigma;       /* Gaussian ion-charge width, bohr */
+  int32_t n_electrons;    /* even, 2 <= n_electrons <= 2M; N = n_electrons/2 */
+} etdm_system;
+
+typedef struct {
+  int32_t precision; /* ETDM_PREC_FP64 or ETDM_PREC_MIXED */
+  int32_t lbfgs_m;   /* L-BFGS memory (Sec. 3.1: 3), 1..16 */
+  double gamma;      /* Eq. 33 mixing (0.25) */
+  double beta0;      /* beta before any step exists (1.0) */
+  int32_t device;    /* CUDA device ordinal */
+} etdm_options;
+
+/* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1). */
+void etdm_default_options(etdm_options *opt);
+
+/* Build everything that does not depend on A (Sec. 2, Eq. 4-6): grid basis
+ * tables, truncation lists per grid tile, analytic S and T, v_ext, the
+ * reference C0 = S^(-1/2) (columns ordered by ascending diagonal of
+ * C0^T (T + V_ext) C0, the first N occupied) and the orbital energies of
+ * Eq. 33 (diagonal of C0^T H C0 at A = 0).  On success *out owns device
+ * memory until etdm_free().  Errors: INVALID_ARG (sizes, radii, grid
+ * factors, list lengths over the tile limit), OOM, CUDA, NUMERIC (S not
+ * positive definite), NOT_CONVERGED (S^(-1/2) iteration). */
+int etdm_init_basis(const etdm_system *sys, const etdm_options *opt,
+                    etdm_handle **out);
+
+/* One energy + gradient evaluation (Eq. 1, 7, 12, 11, 14 / 39-41):
+ * a_dev [N*V] (A_ov) -> E_dev [1] and g_dev [N*V] = dE/dA_ov (Eq. 20).
+ * g_dev may be NULL (energy only).  Asynchronous on `stream`; numerical
+ * failures (NaN/Inf, |P| beyond the exp range) are reported by the next
+ * synchronizing call (etdm_check or a *_host call) as ETDM_ERR_NUMERIC. */
+int etdm_energy_grad(etdm_handle *h, const double *a_dev, double *E_dev,
+                     double *g_dev, void *stream);
+
+/* Same with host buffers: copies a in, evaluates, copies E and g out and
+ * synchronizes.  g_host may be NULL. */
+int etdm_energy_grad_host(etdm_handle *h, const double *a_host,
+                          double *E_host, double *g_host);
+
+/* pg = P^(k) o g (Eq. 33) with the current beta^(k) (Eq. 34). */
+int etdm_precondition(etdm_handle *h, const double *g_dev, double *pg_dev,
+                      void *stream);
+
+/* L-BFGS direction (Sec. 3.1): if a previous point exists, push
+ * (s, y) = (a - a_prev, g - g_prev) when s.y > 1e-30 and set beta = y.y/s.y
+ * (Eq. 34); then the two-loop recursion with H0 = P^(k) gives p = -H g.
+ * a and g become the previous point. */
+int etdm_lbfgs_step(etdm_handle *h, const double *a_dev, const double *g_dev,
+                    double *p_dev, void *stream);
+
+/* Erase the L-BFGS memory (Sec. 3.4: after a reference update): no stored
+ * pairs, no previous point, beta back to beta0. */
+int etdm_lbfgs_reset(etdm_handle *h);
+
+/* Run n_steps ETDM iterations from a_dev (updated in place): L-BFGS
+ * direction, then the line search (alpha = 1 first; strong Wolfe Eq. 25-26,
+ * or approximate Wolfe Eq. 27 with Eq. 28; cubic interpolation; at most 20
+ * trials).  Per step i (0 = the start point) the host arrays, each of
+ * n_steps+1 entries and each optional, receive E, the accepted alpha and the
+ * number of evaluations.  Synchronizes `stream` once per trial. */
+int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps,
+                  double *E_hist, double *alpha_hist, int32_t *trials_hist,
+                  void *stream);
+
+/* Wait for `stream` and report any deferred device-side error. */
+int etdm_check(etdm_handle *h, void *stream);
+
+/* Sizes: dims[0..ETDM_NDIMS-1] = M, N, V, G (grid points), n_tiles,
+ * list entries (sum over tiles), max list length, tile edge x, y, z,
+ * sum over points of n_pt^2 (pairs of functions within r_c of a point),
+ * precision. */
+#define ETDM_NDIMS 12
+int etdm_layout(const etdm_handle *h, int64_t *dims);
+
+/* Copy an internal array to host memory (for inspection and tests).
+ * `which` is one of ETDM_ARR_*; n_bytes must equal the array's size
+ * (etdm_array_bytes).  Synchronizes the handle's work. */
+enum {
+  ETDM_ARR_S = 0,        /* [M*M] f64 overlap */
+  ETDM_ARR_T = 1,        /* [M*M] f64 kinetic */
+  ETDM_ARR_C0 = 2,       /* [M*M] f64 reference orbitals (columns) */
+  ETDM_ARR_ORDER = 3,    /* [M] i32 Loewdin column of each C0 column */
+  ETDM_ARR_VEXT = 4,     /* [G] f64 external potential on the grid */
+  ETDM_ARR_RHO = 5,      /* [G] f64 density of the last evaluation */
+  ETDM_ARR_VTOT = 6,     /* [G] f64 v_ext + v_H + v_x of the last evaluation */
+  ETDM_ARR_H = 7,        /* [M*M] f64 Hamiltonian matrix, last evaluation */
+  ETDM_ARR_D = 8,        /* [M*M] f64 density matrix, last evaluation */
+  ETDM_ARR_UOCC = 9,     /* [M*N] f64 occupied columns of exp(A) */
+  ETDM_ARR_TILE_PTR = 10,/* [n_tiles+1] i32 list offsets */
+  ETDM_ARR_TILE_KEYS = 11,/* [entries] i32 keys mu*512 + (nx+4)*64 + (ny+4)*8 + (nz+4) */
+  ETDM_ARR_EPS = 12,     /* [M] f64 orbital energies of Eq. 33 */
+  ETDM_ARR_ETERMS = 13,  /* [4] f64 kinetic, external, Hartree, exchange */
+  ETDM_ARR_BETA = 14,    /* [1] f64 current beta^(k) */
+  ETDM_NARR = 15
+};
+int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);
+int etdm_get_array(etdm_handle *h, int32_t which, void *host_dst,
+                   int64_t n_bytes);
+
+/* Per-stage timing with CUDA events recorded on the calling stream around
+ * each stage (off by default).  etdm_stage_times synchronizes, adds the
+ * elapsed milliseconds since the last call into ms[ETDM_NSTAGES] and the
+ * number of timed launches of each stage into counts[ETDM_NSTAGES]; the last
+ * entry of counts is the number of kernel launches issued since the last
+ * call. */
+enum {
+  ETDM_STAGE_DENSE_FWD = 0, /* exp(A), O = C0 U, D (cooperative kernel) */
+  ETDM_STAGE_RHO = 1,       /* basis -> grid density */
+  ETDM_STAGE_POTENTIAL = 2, /* FFT Poisson, exchange, energy partials */
+  ETDM_STAGE_VMAT = 3,      /* grid -> basis Hamiltonian */
+  ETDM_STAGE_DENSE_REV = 4, /* energy sum and analytic gradient */
+  ETDM_STAGE_LBFGS = 5,     /* two-loop update */
+  ETDM_NSTAGES = 8
+};
+int etdm_set_profiling(etdm_handle *h, int on);
+int etdm_stage_times(etdm_handle *h, double *ms, int64_t *counts);
+
+/* Message of the last failed call on h (or of the last failed init when h
+ * is NULL).  Valid until the next call on the same handle. */
+const char *etdm_last_error(const etdm_handle *h);
+
+/* Release all device memory of h (NULL is a no-op). */
+void etdm_free(etdm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ETDM_H */

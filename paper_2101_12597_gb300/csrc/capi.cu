@@ -1,0 +1,820 @@
+// C ABI of libetdm (include/etdm.h): handle set-up, the evaluation sequence,
+// the L-BFGS / preconditioner entry points and the host line search.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace etdm;
+
+namespace {
+
+std::string g_init_err;
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+#define CUDA_TRY(expr)                                                            \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess)                                                        \
+      throw Fail{ETDM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
+  } while (0)
+
+template <typename T>
+T *dalloc(etdm_handle *h, size_t count) {
+  void *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{ETDM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+                                 " bytes failed: " + cudaGetErrorString(e)};
+  }
+  h->allocs.push_back(p);
+  CUDA_TRY(cudaMemset(p, 0, count * sizeof(T)));
+  return (T *)p;
+}
+
+void release(etdm_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  for (auto &pe : h->prof_events) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  h->prof_events.clear();
+  for (void *p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  h->h_pinned = nullptr;
+}
+
+int set_err(etdm_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg; else g_init_err = msg;
+  return code;
+}
+
+// deferred device-side status
+int check_flags(etdm_handle *h, cudaStream_t s) {
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int f[FLAG_NFLAGS];
+  CUDA_TRY(cudaMemcpy(f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f[FLAG_ERR] != 0) {
+    int code = f[FLAG_ERR];
+    int zero = 0;
+    CUDA_TRY(cudaMemcpy(h->d_flags + FLAG_ERR, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    if (code == ETDM_ERR_TIMEOUT) {
+      CUDA_TRY(cudaMemset(h->d_bar, 0, 4 * sizeof(unsigned)));
+      throw Fail{code, "a bounded device-side grid barrier gave up (blocks not co-resident?)"};
+    }
+    throw Fail{code, "numerical failure on the device (NaN/Inf, or |A_ov A_ov^T|_F > 4^8)"};
+  }
+  return ETDM_OK;
+}
+
+// Optional stage timing: events around a stage on the calling stream.
+struct StageTimer {
+  etdm_handle *h;
+  cudaStream_t s;
+  int stage;
+  cudaEvent_t e0 = nullptr;
+  StageTimer(etdm_handle *hh, cudaStream_t ss, int st) : h(hh), s(ss), stage(st) {
+    if (h->profiling) {
+      CUDA_TRY(cudaEventCreate(&e0));
+      CUDA_TRY(cudaEventRecord(e0, s));
+    }
+  }
+  void done() {
+    if (!h->profiling) return;
+    cudaEvent_t e1;
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e1, s));
+    h->prof_events.push_back({stage, {e0, e1}});
+  }
+};
+
+// One energy (+ gradient) evaluation, all on `s`.
+void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s) {
+  {
+    StageTimer t(h, s, ETDM_STAGE_DENSE_FWD);
+    CUDA_TRY(launch_dense_forward(h, a, s));
+    t.done();
+  }
+  {
+    StageTimer t(h, s, ETDM_STAGE_RHO);
+    CUDA_TRY(launch_rho_fp64(h, h->d_D, h->d_rho, s));
+    t.done();
+  }
+  {
+    StageTimer t(h, s, ETDM_STAGE_POTENTIAL);
+    CUDA_TRY(launch_pack_real(h, h->d_rho, h->d_fft, s));
+    CUDA_TRY(fft3d(h, h->d_fft, -1, s));
+    CUDA_TRY(launch_poisson_scale(h, h->d_fft, s));
+    CUDA_TRY(fft3d(h, h->d_fft, +1, s));
+    CUDA_TRY(launch_potential(h, s));
+    t.done();
+  }
+  h->launches += 11;
+  if (g) {
+    StageTimer t(h, s, ETDM_STAGE_VMAT);
+    CUDA_TRY(launch_vmat_fp64(h, h->d_vtot, h->d_H, s));
+    t.done();
+    h->launches += 1;
+  }
+  {
+    StageTimer t(h, s, ETDM_STAGE_DENSE_REV);
+    CUDA_TRY(launch_dense_reverse(h, a, g, E, s));
+    t.done();
+  }
+}
+
+void lbfgs(etdm_handle *h, const double *a, const double *g, double *p, cudaStream_t s) {
+  StageTimer t(h, s, ETDM_STAGE_LBFGS);
+  CUDA_TRY(launch_lbfgs(h, a, g, p, s));
+  t.done();
+  h->launches += 1;
+}
+
+int factor_ok(int n) {
+  int m = n;
+  const int pr[] = {2, 3, 5, 7, 11, 13};
+  for (int p : pr)
+    while (m % p == 0) m /= p;
+  return m == 1;
+}
+
+void validate(const etdm_system *sys, const etdm_options *opt) {
+  auto bad = [](const std::string &m) { throw Fail{ETDM_ERR_INVALID_ARG, m}; };
+  if (!sys) bad("sys is NULL");
+  if (sys->n_atoms < 1 || !sys->pos || !sys->Z) bad("need n_atoms >= 1 with pos and Z");
+  if (sys->n_basis < 2 || !sys->bf_atom || !sys->bf_exp || !sys->bf_rcut)
+    bad("need n_basis >= 2 with bf_atom, bf_exp, bf_rcut");
+  if (sys->n_electrons < 2 || sys->n_electrons % 2 || sys->n_electrons / 2 > sys->n_basis)
+    bad("n_electrons must be even with 2 <= n_electrons <= 2 n_basis");
+  if (sys->n_basis > (1 << 22)) bad("n_basis too large");
+  double Lmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    if (!(sys->box[a] > 0.0)) bad("box edges must be positive");
+    Lmin = std::min(Lmin, sys->box[a]);
+    if (sys->grid[a] < 2 || sys->grid[a] > kMaxFFT || !factor_ok(sys->grid[a]))
+      bad("grid sizes must be in [2, 256] with prime factors <= 13");
+  }
+  for (int i = 0; i < sys->n_atoms; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double x = sys->pos[3 * i + a];
+      if (!(x >= 0.0 && x < sys->box[a])) bad("positions must lie in [0, box)");
+    }
+  for (int m = 0; m < sys->n_basis; ++m) {
+    if (sys->bf_atom[m] < 0 || sys->bf_atom[m] >= sys->n_atoms) bad("bf_atom out of range");
+    if (!(sys->bf_exp[m] > 0.0)) bad("bf_exp must be positive");
+    if (!(sys->bf_rcut[m] > 0.0 && sys->bf_rcut[m] < 2.0 * Lmin))
+      bad("bf_rcut must be in (0, 2 * min(box))");
+  }
+  if (!(sys->ion_sigma > 0.0)) bad("ion_sigma must be positive");
+  if (opt) {
+    if (opt->precision != ETDM_PREC_FP64 && opt->precision != ETDM_PREC_MIXED)
+      bad("unknown precision");
+    if (opt->lbfgs_m < 1 || opt->lbfgs_m > 16) bad("lbfgs_m must be in [1, 16]");
+    if (!(opt->gamma >= 0.0 && opt->gamma <= 1.0)) bad("gamma must be in [0, 1]");
+    if (!(opt->beta0 > 0.0)) bad("beta0 must be positive");
+  }
+}
+
+// S^(-1/2) by the coupled Newton-Schulz iteration on S / c (c >= lambda_max).
+void inverse_sqrt(etdm_handle *h, cudaStream_t s) {
+  const int M = h->M;
+  const long MM = (long)M * M;
+  double *Y = dalloc<double>(h, MM), *Zm = dalloc<double>(h, MM), *Tm = dalloc<double>(h, MM),
+         *Y2 = dalloc<double>(h, MM), *Z2 = dalloc<double>(h, MM), *sc = dalloc<double>(h, 2);
+  CUDA_TRY(launch_max_rowsum(h->d_S, sc, M, s));
+  double c = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(&c, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (!(c > 0.0) || !std::isfinite(c)) throw Fail{ETDM_ERR_NUMERIC, "overlap matrix is not finite"};
+  CUDA_TRY(launch_ns_prep(h->d_S, Y, Zm, c, M, s));
+  bool done = false;
+  int extra = 0;
+  for (int it = 0; it < 200; ++it) {
+    Phase ph{};
+    ph.m = M; ph.n = M; ph.k = M; ph.np = 1;
+    ph.p[0] = Prod{Zm, Y, M, M, 0, 0, -0.5};
+    ph.diag = 1.5; ph.out = Tm; ph.ldo = M;
+    CUDA_TRY(launch_gemm(ph, s));
+    CUDA_TRY(launch_resid(Tm, sc + 1, M, s));
+    Phase py{};
+    py.m = M; py.n = M; py.k = M; py.np = 1;
+    py.p[0] = Prod{Y, Tm, M, M, 0, 0, 1.0};
+    py.out = Y2; py.ldo = M;
+    CUDA_TRY(launch_gemm(py, s));
+    Phase pz = py;
+    pz.p[0] = Prod{Tm, Zm, M, M, 0, 0, 1.0};
+    pz.out = Z2;
+    CUDA_TRY(launch_gemm(pz, s));
+    std::swap(Y, Y2);
+    std::swap(Zm, Z2);
+    double r = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&r, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (!std::isfinite(r)) throw Fail{ETDM_ERR_NUMERIC, "S^(-1/2) iteration diverged"};
+    if (done && ++extra >= 2) break;
+    if (2.0 * r < 1e-13) done = true;
+  }
+  if (!done)
+    throw Fail{ETDM_ERR_NOT_CONVERGED,
+               "S^(-1/2) Newton-Schulz iteration did not converge (S ill-conditioned?)"};
+  // S^(-1/2) = Z / sqrt(c), into d_S scratch? keep S: write into Tm then permute later
+  CUDA_TRY(launch_scale_copy(Zm, h->d_C0, 1.0 / sqrt(c), MM, s));
+}
+
+__global__ void extract_ptr_kernel(const long long *off, long long total, int M, int n_tiles,
+                                   int *ptr) {
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t <= n_tiles;
+       t += (long)gridDim.x * blockDim.x)
+    ptr[t] = (t == n_tiles) ? (int)total : (int)off[t * (long)M];
+}
+
+__global__ void symmetrize_upper_kernel(double *H, int M) {
+  long MM = (long)M * M;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
+       e += (long)gridDim.x * blockDim.x) {
+    int i = (int)(e / M), c = (int)(e % M);
+    if (i > c) H[e] = H[(long)c * M + i];
+  }
+}
+
+void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) {
+  validate(sys, opt);
+  etdm_options o;
+  etdm_default_options(&o);
+  if (opt) o = *opt;
+  h->device = o.device;
+  h->precision = o.precision;
+  h->lbfgs_m = o.lbfgs_m;
+  h->gamma = o.gamma;
+  h->beta0 = o.beta0;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (o.device < 0 || o.device >= ndev) throw Fail{ETDM_ERR_INVALID_ARG, "no such CUDA device"};
+  CUDA_TRY(cudaSetDevice(o.device));
+  CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, o.device));
+  int coop = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, o.device));
+  if (!coop) throw Fail{ETDM_ERR_CUDA, "device does not support cooperative launch"};
+
+  const int M = sys->n_basis;
+  h->M = M;
+  h->N = sys->n_electrons / 2;
+  h->V = M - h->N;
+  h->n_atoms = sys->n_atoms;
+  for (int a = 0; a < 3; ++a) {
+    h->n[a] = sys->grid[a];
+    h->L[a] = sys->box[a];
+    h->h[a] = sys->box[a] / sys->grid[a];
+  }
+  h->G = (long)h->n[0] * h->n[1] * h->n[2];
+  h->dV = h->h[0] * h->h[1] * h->h[2];
+  h->omega = h->L[0] * h->L[1] * h->L[2];
+  h->sigma = sys->ion_sigma;
+  cudaStream_t s = 0;
+
+  // system arrays
+  std::vector<double> center(3 * M), alpha(M), norm(M), rcut(M), rc2(M);
+  for (int m = 0; m < M; ++m) {
+    int at = sys->bf_atom[m];
+    for (int a = 0; a < 3; ++a) center[3 * m + a] = sys->pos[3 * at + a];
+    alpha[m] = sys->bf_exp[m];
+    norm[m] = pow(2.0 * alpha[m] / M_PI, 0.75);
+    rcut[m] = sys->bf_rcut[m];
+    rc2[m] = rcut[m] * rcut[m];
+  }
+  h->d_center = dalloc<double>(h, 3 * M);
+  h->d_alpha = dalloc<double>(h, M);
+  h->d_norm = dalloc<double>(h, M);
+  h->d_rcut = dalloc<double>(h, M);
+  h->d_rc2 = dalloc<double>(h, M);
+  h->d_pos = dalloc<double>(h, 3 * sys->n_atoms);
+  h->d_Z = dalloc<double>(h, sys->n_atoms);
+  CUDA_TRY(cudaMemcpy(h->d_center, center.data(), 3 * M * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_alpha, alpha.data(), M * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_norm, norm.data(), M * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_rcut, rcut.data(), M * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_rc2, rc2.data(), M * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_pos, sys->pos, 3 * sys->n_atoms * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_Z, sys->Z, sys->n_atoms * 8, cudaMemcpyHostToDevice));
+
+  // basis tables
+  long tab = 0;
+  for (int a = 0; a < 3; ++a) {
+    h->tab_off[a] = tab;
+    tab += (long)M * kImgN * h->n[a];
+  }
+  h->d_sq = dalloc<double>(h, tab);
+  h->d_ex = dalloc<double>(h, tab);
+  CUDA_TRY(launch_tables(h, s));
+
+  // tiles and truncation lists
+  GridGeom &g = h->geom;
+  g.nx = h->n[0]; g.ny = h->n[1]; g.nz = h->n[2];
+  g.tx = g.ty = g.tz = 4;
+  g.nbx = (g.nx + g.tx - 1) / g.tx;
+  g.nby = (g.ny + g.ty - 1) / g.ty;
+  g.nbz = (g.nz + g.tz - 1) / g.tz;
+  g.M = M;
+  g.dV = h->dV;
+  h->n_tiles = g.nbx * g.nby * g.nbz;
+  const long ncnt = (long)h->n_tiles * M;
+  int *d_count = dalloc<int>(h, ncnt);
+  long long *d_off = dalloc<long long>(h, ncnt);
+  long long *d_tmp = dalloc<long long>(h, ncnt / 1024 + 4);
+  CUDA_TRY(launch_list_count(h, d_count, s));
+  CUDA_TRY(launch_scan(d_count, d_off, ncnt, d_tmp, s));
+  long nb = (ncnt + 1023) / 1024;
+  if (nb < 1) nb = 1;
+  long long total = 0;
+  CUDA_TRY(cudaMemcpy(&total, d_tmp + nb, sizeof(long long), cudaMemcpyDeviceToHost));
+  if (total > 2000000000LL) throw Fail{ETDM_ERR_INVALID_ARG, "truncation lists too long"};
+  h->n_entries = (long)total;
+  h->d_keys = dalloc<int>(h, total);
+  h->d_tile_ptr = dalloc<int>(h, h->n_tiles + 1);
+  CUDA_TRY(launch_list_fill(h, d_off, s));
+  extract_ptr_kernel<<<(h->n_tiles + 256) / 256, 256, 0, s>>>(d_off, total, M, h->n_tiles,
+                                                               h->d_tile_ptr);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<int> ptr(h->n_tiles + 1);
+  CUDA_TRY(cudaMemcpy(ptr.data(), h->d_tile_ptr, (h->n_tiles + 1) * sizeof(int),
+                      cudaMemcpyDeviceToHost));
+  h->max_list = 0;
+  for (int t = 0; t < h->n_tiles; ++t) h->max_list = std::max(h->max_list, ptr[t + 1] - ptr[t]);
+  if (h->max_list > kMaxList)
+    throw Fail{ETDM_ERR_INVALID_ARG,
+               "a grid tile touches " + std::to_string(h->max_list) +
+                   " function images (limit " + std::to_string(kMaxList) +
+                   "): use a finer grid or shorter truncation radii"};
+  {
+    unsigned long long *d_sum = dalloc<unsigned long long>(h, 1);
+    CUDA_TRY(launch_npt2(h, d_sum, s));
+    unsigned long long v = 0;
+    CUDA_TRY(cudaMemcpy(&v, d_sum, 8, cudaMemcpyDeviceToHost));
+    h->sum_npt2 = (long long)v;
+  }
+
+  // analytic S, T
+  const long MM = (long)M * M;
+  h->d_S = dalloc<double>(h, MM);
+  h->d_T = dalloc<double>(h, MM);
+  h->d_C0 = dalloc<double>(h, MM);
+  CUDA_TRY(launch_overlap_kinetic(h, s));
+
+  // grid buffers and v_ext
+  h->d_vext = dalloc<double>(h, h->G);
+  h->d_rho = dalloc<double>(h, h->G);
+  h->d_vtot = dalloc<double>(h, h->G);
+  h->d_fft = dalloc<double2>(h, h->G);
+  h->d_tw = dalloc<double2>(h, h->n[0] + h->n[1] + h->n[2]);
+  h->n_gridpart = kPotBlocks;
+  h->d_gridpart = dalloc<double>(h, 3 * kPotBlocks);
+  CUDA_TRY(launch_twiddles(h, s));
+  CUDA_TRY(launch_vext_recip(h, s));
+  CUDA_TRY(fft3d(h, h->d_fft, +1, s));
+  CUDA_TRY(launch_real_part(h, h->d_fft, h->d_vext, s));
+
+  // dense workspaces
+  const int N = h->N, V = h->V;
+  const long NN = (long)N * N;
+  h->d_D = dalloc<double>(h, MM);
+  h->d_H = dalloc<double>(h, MM);
+  h->d_Uocc = dalloc<double>(h, (long)M * N);
+  h->d_O = dalloc<double>(h, (long)M * N);
+  h->d_P = dalloc<double>(h, NN);
+  h->d_Qk = dalloc<double>(h, NN * kTaylor);
+  h->d_Kt = dalloc<double>(h, NN * (kJmax + 1));
+  h->d_St = dalloc<double>(h, NN * (kJmax + 1));
+  h->d_Gbar = dalloc<double>(h, (long)M * N);
+  h->d_Ubar = dalloc<double>(h, (long)M * N);
+  for (int i = 0; i < 6; ++i) h->d_bar2[i] = dalloc<double>(h, NN);
+  h->d_Qbar = dalloc<double>(h, NN);
+  h->d_Abar = dalloc<double>(h, (long)N * V);
+  h->d_Psym = dalloc<double>(h, NN);
+  h->d_E = dalloc<double>(h, 2);
+  h->d_eterms = dalloc<double>(h, 4);
+  h->d_scal = dalloc<double>(h, 4);
+  h->d_flags = dalloc<int>(h, FLAG_NFLAGS);
+  h->d_bar = dalloc<unsigned>(h, 4);
+  h->d_eps = dalloc<double>(h, M);
+  int bps = 0;
+  if (occupancy_dense(&bps) != 0 || bps < 1)
+    throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative dense kernels"};
+  h->coop_blocks = h->num_sms;
+  int bpl = 0;
+  if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
+    throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};
+  const long nvar = (long)N * V;
+  h->lb_blocks = (int)std::min<long>((long)h->num_sms * std::min(bpl, 2),
+                                     std::max<long>(1, (nvar + 1023) / 1024));
+  h->d_red = dalloc<double>(h, 2 * std::max(h->coop_blocks, h->lb_blocks) + 8);
+
+  // L-BFGS memory and line-search buffers
+  h->d_s = dalloc<double>(h, (long)h->lbfgs_m * nvar);
+  h->d_y = dalloc<double>(h, (long)h->lbfgs_m * nvar);
+  h->d_aprev = dalloc<double>(h, nvar);
+  h->d_gprev = dalloc<double>(h, nvar);
+  h->d_q = dalloc<double>(h, nvar);
+  h->d_lbstate = dalloc<double>(h, 4 + 2 * 16);
+  h->d_a = dalloc<double>(h, nvar);
+  h->d_g = dalloc<double>(h, nvar);
+  h->d_at = dalloc<double>(h, nvar);
+  h->d_gt = dalloc<double>(h, nvar);
+  h->d_p = dalloc<double>(h, nvar);
+  h->d_dot = dalloc<double>(h, 4);
+  CUDA_TRY(cudaMallocHost(&h->h_pinned, 8 * sizeof(double)));
+
+  // reference orbitals: Loewdin S^(-1/2), columns by ascending diag of C0^T h_core C0
+  inverse_sqrt(h, s);
+  CUDA_TRY(cudaMemcpyAsync(h->d_H, h->d_T, MM * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(launch_vmat_fp64(h, h->d_vext, h->d_H, s));
+  symmetrize_upper_kernel<<<256, 256, 0, s>>>(h->d_H, M);
+  CUDA_TRY(cudaGetLastError());
+  double *d_diag = dalloc<double>(h, M);
+  CUDA_TRY(launch_diag_quad(h->d_C0, h->d_H, d_diag, M, s));
+  std::vector<double> diag(M);
+  CUDA_TRY(cudaMemcpy(diag.data(), d_diag, M * 8, cudaMemcpyDeviceToHost));
+  for (double v : diag)
+    if (!std::isfinite(v)) throw Fail{ETDM_ERR_NUMERIC, "h_core diagonal is not finite"};
+  h->order.resize(M);
+  std::iota(h->order.begin(), h->order.end(), 0);
+  std::stable_sort(h->order.begin(), h->order.end(),
+                   [&](int x, int y) { return diag[x] < diag[y]; });
+  int *d_perm = dalloc<int>(h, M);
+  CUDA_TRY(cudaMemcpy(d_perm, h->order.data(), M * sizeof(int), cudaMemcpyHostToDevice));
+  double *d_tmpC = dalloc<double>(h, MM);
+  CUDA_TRY(cudaMemcpyAsync(d_tmpC, h->d_C0, MM * 8, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(launch_permute_cols(d_tmpC, d_perm, h->d_C0, M, s));
+
+  // orbital energies of Eq. 33 at A = 0
+  CUDA_TRY(cudaMemsetAsync(h->d_a, 0, nvar * 8, s));
+  evaluate(h, h->d_a, h->d_E, h->d_g, s);
+  check_flags(h, s);
+  CUDA_TRY(launch_diag_quad(h->d_C0, h->d_H, h->d_eps, M, s));
+  std::vector<double> st(4 + 32, 0.0);
+  st[3] = h->beta0;
+  CUDA_TRY(cudaMemcpy(h->d_lbstate, st.data(), st.size() * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaDeviceSynchronize());
+}
+
+// ---- line search (Eq. 25-29), same rules as the paper's description ----------
+constexpr double C1 = 1e-4, C2 = 0.9, DEL = 0.1, SIG = 0.9, EPSE = 1e-6;
+constexpr int MAX_TRIALS = 20;
+
+bool cubic_min(double a, double fa, double da, double b, double fb, double db, double *out) {
+  if (a == b) return false;
+  double d1 = da + db - 3.0 * (fa - fb) / (a - b);
+  double disc = d1 * d1 - da * db;
+  if (disc < 0.0) return false;
+  double d2 = copysign(sqrt(disc), b - a);
+  double den = db - da + 2.0 * d2;
+  if (den == 0.0) return false;
+  *out = b - (b - a) * (db + d2 - d1) / den;
+  return true;
+}
+
+bool wolfe_ok(double alpha, double E, double d, double E0, double d0) {
+  bool strong = (E <= E0 + C1 * alpha * d0) && (fabs(d) <= C2 * fabs(d0));
+  bool approx = ((2.0 * DEL - 1.0) * d0 >= d) && (d >= SIG * d0) && (E <= E0 + EPSE * fabs(E0));
+  return strong || approx;
+}
+
+struct Pt {
+  double a, E, d;
+};
+
+}  // namespace
+
+// ============================== C ABI =========================================
+extern "C" {
+
+void etdm_default_options(etdm_options *opt) {
+  if (!opt) return;
+  opt->precision = ETDM_PREC_FP64;
+  opt->lbfgs_m = 3;
+  opt->gamma = 0.25;
+  opt->beta0 = 1.0;
+  opt->device = 0;
+}
+
+int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {
+  if (!out) return set_err(nullptr, ETDM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  etdm_handle *h = new etdm_handle();
+  try {
+    init_impl(h, sys, opt);
+  } catch (const Fail &f) {
+    release(h);
+    delete h;
+    return set_err(nullptr, f.code, f.msg);
+  }
+  *out = h;
+  return ETDM_OK;
+}
+
+int etdm_energy_grad(etdm_handle *h, const double *a_dev, double *E_dev, double *g_dev,
+                     void *stream) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (!a_dev || !E_dev) return set_err(h, ETDM_ERR_INVALID_ARG, "a_dev and E_dev are required");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    evaluate(h, a_dev, E_dev, g_dev, (cudaStream_t)stream);
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_energy_grad_host(etdm_handle *h, const double *a_host, double *E_host,
+                          double *g_host) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (!a_host || !E_host) return set_err(h, ETDM_ERR_INVALID_ARG, "a_host and E_host are required");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    cudaStream_t s = 0;
+    const long nvar = (long)h->N * h->V;
+    CUDA_TRY(cudaMemcpyAsync(h->d_a, a_host, nvar * 8, cudaMemcpyHostToDevice, s));
+    evaluate(h, h->d_a, h->d_E, g_host ? h->d_g : nullptr, s);
+    CUDA_TRY(cudaMemcpyAsync(E_host, h->d_E, 8, cudaMemcpyDeviceToHost, s));
+    if (g_host) CUDA_TRY(cudaMemcpyAsync(g_host, h->d_g, nvar * 8, cudaMemcpyDeviceToHost, s));
+    check_flags(h, s);
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_precondition(etdm_handle *h, const double *g_dev, double *pg_dev, void *stream) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (!g_dev || !pg_dev) return set_err(h, ETDM_ERR_INVALID_ARG, "g_dev and pg_dev are required");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(launch_precond(h, g_dev, pg_dev, (cudaStream_t)stream));
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_lbfgs_step(etdm_handle *h, const double *a_dev, const double *g_dev, double *p_dev,
+                    void *stream) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (!a_dev || !g_dev || !p_dev)
+    return set_err(h, ETDM_ERR_INVALID_ARG, "a_dev, g_dev and p_dev are required");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    lbfgs(h, a_dev, g_dev, p_dev, (cudaStream_t)stream);
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_lbfgs_reset(etdm_handle *h) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    double st[4];
+    CUDA_TRY(cudaMemcpy(st, h->d_lbstate, sizeof(st), cudaMemcpyDeviceToHost));
+    st[0] = 0.0; st[1] = 0.0; st[2] = 0.0; st[3] = h->beta0;
+    CUDA_TRY(cudaMemcpy(h->d_lbstate, st, sizeof(st), cudaMemcpyHostToDevice));
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_check(etdm_handle *h, void *stream) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    check_flags(h, (cudaStream_t)stream);
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist,
+                  double *alpha_hist, int32_t *trials_hist, void *stream) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (!a_dev || n_steps < 0) return set_err(h, ETDM_ERR_INVALID_ARG, "bad a_dev or n_steps");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long nvar = (long)h->N * h->V;
+  double *hp = h->h_pinned;
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    // E and g at the start point
+    evaluate(h, a_dev, h->d_dot, h->d_g, s);
+    CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 8, cudaMemcpyDeviceToHost, s));
+    check_flags(h, s);
+    double E = hp[0];
+    if (E_hist) E_hist[0] = E;
+    if (alpha_hist) alpha_hist[0] = 0.0;
+    if (trials_hist) trials_hist[0] = 1;
+    // phi(alpha): E(a + alpha p) and grad . p, into hp[0], hp[1]
+    auto phi = [&](double alpha) -> Pt {
+      CUDA_TRY(launch_axpy(a_dev, alpha, h->d_p, h->d_at, nvar, s));
+      evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
+      CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, nullptr, s));
+      h->launches += 2;
+      CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 2 * 8, cudaMemcpyDeviceToHost, s));
+      check_flags(h, s);
+      return Pt{alpha, hp[0], hp[1]};
+    };
+    for (int it = 1; it <= n_steps; ++it) {
+      lbfgs(h, a_dev, h->d_g, h->d_p, s);
+      CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
+      h->launches += 1;
+      CUDA_TRY(cudaMemcpyAsync(hp + 2, h->d_dot + 2, 8, cudaMemcpyDeviceToHost, s));
+      check_flags(h, s);
+      double d0 = hp[2];
+      if (!(d0 < 0.0)) {  // not a descent direction: erase memory, precondition only
+        CUDA_TRY(cudaStreamSynchronize(s));
+        double st[3] = {0.0, 0.0, 0.0};
+        CUDA_TRY(cudaMemcpy(h->d_lbstate, st, sizeof(st), cudaMemcpyHostToDevice));
+        lbfgs(h, a_dev, h->d_g, h->d_p, s);
+        CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
+        h->launches += 1;
+        CUDA_TRY(cudaMemcpyAsync(hp + 2, h->d_dot + 2, 8, cudaMemcpyDeviceToHost, s));
+        check_flags(h, s);
+        d0 = hp[2];
+      }
+      const double E0 = E;
+      int trials = 0;
+      bool accepted = false, have_bracket = false;
+      Pt prev{0.0, E0, d0}, lo{}, hi{}, cur{};
+      double alpha = 1.0;
+      while (trials < MAX_TRIALS) {
+        cur = phi(alpha);
+        ++trials;
+        if (wolfe_ok(cur.a, cur.E, cur.d, E0, d0)) { accepted = true; break; }
+        if (cur.E > E0 + C1 * cur.a * d0 || (trials > 1 && cur.E >= prev.E)) {
+          lo = prev; hi = cur; have_bracket = true; break;
+        }
+        if (cur.d >= 0.0) { lo = cur; hi = prev; have_bracket = true; break; }
+        double nxt;
+        if (!cubic_min(prev.a, prev.E, prev.d, cur.a, cur.E, cur.d, &nxt) ||
+            !(1.1 * cur.a <= nxt && nxt <= 4.0 * cur.a))
+          nxt = 2.0 * cur.a;
+        prev = cur;
+        alpha = nxt;
+      }
+      while (!accepted && have_bracket && trials < MAX_TRIALS) {
+        double w = fabs(hi.a - lo.a), left = std::min(lo.a, hi.a), right = std::max(lo.a, hi.a);
+        double aj;
+        if (!cubic_min(lo.a, lo.E, lo.d, hi.a, hi.E, hi.d, &aj) ||
+            !(left + 0.1 * w <= aj && aj <= right - 0.1 * w))
+          aj = 0.5 * (lo.a + hi.a);
+        cur = phi(aj);
+        ++trials;
+        if (wolfe_ok(cur.a, cur.E, cur.d, E0, d0)) { accepted = true; break; }
+        if (cur.E > E0 + C1 * cur.a * d0 || cur.E >= lo.E) {
+          hi = cur;
+        } else {
+          if (cur.d * (hi.a - lo.a) >= 0.0) hi = lo;
+          lo = cur;
+        }
+      }
+      if (!accepted) {  // best point seen (the bracket's low end), re-evaluated
+        Pt best = have_bracket ? lo : prev;
+        if (best.a != 0.0) {
+          cur = phi(best.a);
+          accepted = true;
+        }
+      }
+      if (accepted) {
+        CUDA_TRY(cudaMemcpyAsync(a_dev, h->d_at, nvar * 8, cudaMemcpyDeviceToDevice, s));
+        std::swap(h->d_g, h->d_gt);
+        E = cur.E;
+      }
+      if (E_hist) E_hist[it] = E;
+      if (alpha_hist) alpha_hist[it] = accepted ? cur.a : 0.0;
+      if (trials_hist) trials_hist[it] = trials;
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_layout(const etdm_handle *h, int64_t *dims) {
+  if (!h || !dims) return ETDM_ERR_INVALID_ARG;
+  dims[0] = h->M; dims[1] = h->N; dims[2] = h->V; dims[3] = h->G;
+  dims[4] = h->n_tiles; dims[5] = h->n_entries; dims[6] = h->max_list;
+  dims[7] = h->geom.tx; dims[8] = h->geom.ty; dims[9] = h->geom.tz;
+  dims[10] = h->sum_npt2; dims[11] = h->precision;
+  return ETDM_OK;
+}
+
+int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
+  if (!h) return -1;
+  const int64_t M = h->M, N = h->N;
+  switch (which) {
+    case ETDM_ARR_S: case ETDM_ARR_T: case ETDM_ARR_C0: case ETDM_ARR_H: case ETDM_ARR_D:
+      return M * M * 8;
+    case ETDM_ARR_ORDER: return M * 4;
+    case ETDM_ARR_VEXT: case ETDM_ARR_RHO: case ETDM_ARR_VTOT: return (int64_t)h->G * 8;
+    case ETDM_ARR_UOCC: return M * N * 8;
+    case ETDM_ARR_TILE_PTR: return ((int64_t)h->n_tiles + 1) * 4;
+    case ETDM_ARR_TILE_KEYS: return (int64_t)h->n_entries * 4;
+    case ETDM_ARR_EPS: return M * 8;
+    case ETDM_ARR_ETERMS: return 32;
+    case ETDM_ARR_BETA: return 8;
+    default: return -1;
+  }
+}
+
+int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  int64_t want = etdm_array_bytes(h, which);
+  if (want < 0 || !dst || n_bytes != want)
+    return set_err(h, ETDM_ERR_INVALID_ARG, "unknown array or wrong byte count");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    const void *src = nullptr;
+    switch (which) {
+      case ETDM_ARR_S: src = h->d_S; break;
+      case ETDM_ARR_T: src = h->d_T; break;
+      case ETDM_ARR_C0: src = h->d_C0; break;
+      case ETDM_ARR_ORDER: memcpy(dst, h->order.data(), want); return ETDM_OK;
+      case ETDM_ARR_VEXT: src = h->d_vext; break;
+      case ETDM_ARR_RHO: src = h->d_rho; break;
+      case ETDM_ARR_VTOT: src = h->d_vtot; break;
+      case ETDM_ARR_H: src = h->d_H; break;
+      case ETDM_ARR_D: src = h->d_D; break;
+      case ETDM_ARR_UOCC: src = h->d_Uocc; break;
+      case ETDM_ARR_TILE_PTR: src = h->d_tile_ptr; break;
+      case ETDM_ARR_TILE_KEYS: src = h->d_keys; break;
+      case ETDM_ARR_EPS: src = h->d_eps; break;
+      case ETDM_ARR_ETERMS: src = h->d_eterms; break;
+      case ETDM_ARR_BETA: src = h->d_lbstate + 3; break;
+    }
+    if (want > 0) CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_set_profiling(etdm_handle *h, int on) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  h->profiling = on != 0;
+  return ETDM_OK;
+}
+
+int etdm_stage_times(etdm_handle *h, double *ms, int64_t *counts) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (auto &pe : h->prof_events) {
+      float t = 0.0f;
+      CUDA_TRY(cudaEventElapsedTime(&t, pe.second.first, pe.second.second));
+      h->stage_ms[pe.first] += t;
+      h->stage_n[pe.first] += 1;
+      cudaEventDestroy(pe.second.first);
+      cudaEventDestroy(pe.second.second);
+    }
+    h->prof_events.clear();
+    for (int i = 0; i < ETDM_NSTAGES; ++i) {
+      if (ms) ms[i] = h->stage_ms[i];
+      if (counts) counts[i] = h->stage_n[i];
+      h->stage_ms[i] = 0.0;
+      h->stage_n[i] = 0;
+    }
+    if (counts) counts[ETDM_NSTAGES - 1] = h->launches;
+    h->launches = 0;
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+const char *etdm_last_error(const etdm_handle *h) {
+  return h ? h->err.c_str() : g_init_err.c_str();
+}
+
+void etdm_free(etdm_handle *h) {
+  if (!h) return;
+  release(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,666 @@
+// Dense FP64 algebra of one ETDM evaluation: exp(A) for the occupied-virtual
+// parametrization (Eq. 36-37), O = C0 U, D = O F O^T (Eq. 12), and the
+// analytic gradient dE/dA_ov (Eq. 14) by reverse-mode differentiation of the
+// same steps; plus the L-BFGS two-loop update (Sec. 3.1) and the diagonal
+// preconditioner (Eq. 33-34).
+//
+// cos sqrt(P) and sin sqrt(P)/sqrt(P) (P = A_ov A_ov^T) are entire functions
+// of P.  They are evaluated without an eigendecomposition: Taylor series of
+// Q = P / 4^j with |Q|_F <= 1, then j doubling steps
+//   cos 2x = 1 + 4k + 2k^2 (k = cos x - 1),  sin 2x / 2x = (sin x / x) cos x,
+// which keep the small quantity k = cos x - 1 without cancellation.
+//
+// Each chain of small dependent products runs as ONE cooperative launch over
+// all SMs with a bounded grid barrier between products (FP64 is the scarce
+// resource on this GPU; spreading each product over every SM is what counts).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace etdm {
+
+constexpr int BM = 8, BN = 16, BK = 32, NT = 128;
+
+__device__ __forceinline__ double opA(const Prod &P, int i, int k) {
+  return P.ta ? P.A[(long)k * P.lda + i] : P.A[(long)i * P.lda + k];
+}
+__device__ __forceinline__ double opB(const Prod &P, int k, int j) {
+  return P.tb ? P.B[(long)j * P.ldb + k] : P.B[(long)k * P.ldb + j];
+}
+
+// One output tile (BM x BN) of a phase, computed by the 128 threads of a block.
+__device__ void phase_tile(const Phase &ph, int tile, double (*As)[BK + 1],
+                           double (*Bs)[BN + 1]) {
+  const int tilesN = (ph.n + BN - 1) / BN;
+  const int r0 = (tile / tilesN) * BM, c0 = (tile % tilesN) * BN;
+  const int tid = threadIdx.x, ty = tid / BN, tx = tid % BN;
+  const int i = r0 + ty, j = c0 + tx;
+  double acc = 0.0;
+  for (int q = 0; q < ph.np; ++q) {
+    const Prod &P = ph.p[q];
+    if (P.alpha == 0.0) continue;
+    double accq = 0.0;
+    for (int k0 = 0; k0 < ph.k; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += NT) {
+        int ii, kk;
+        if (P.ta) { kk = e / BM; ii = e % BM; } else { ii = e / BK; kk = e % BK; }
+        int gi = r0 + ii, gk = k0 + kk;
+        As[ii][kk] = (gi < ph.m && gk < ph.k) ? opA(P, gi, gk) : 0.0;
+      }
+      for (int e = tid; e < BK * BN; e += NT) {
+        int kk, jj;
+        if (P.tb) { jj = e / BK; kk = e % BK; } else { kk = e / BN; jj = e % BN; }
+        int gk = k0 + kk, gj = c0 + jj;
+        Bs[kk][jj] = (gk < ph.k && gj < ph.n) ? opB(P, gk, gj) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < BK; ++kk) accq = fma(As[ty][kk], Bs[kk][tx], accq);
+      __syncthreads();
+    }
+    acc += P.alpha * accq;
+  }
+  if (i < ph.m && j < ph.n) {
+    double v = acc;
+    if (ph.C1) v += ph.beta1 * ph.C1[(long)i * ph.ldc1 + j];
+    if (ph.C2) v += ph.beta2 * ph.C2[(long)i * ph.ldc2 + j];
+    if (i == j) v += ph.diag;
+    ph.out[(long)i * ph.ldo + j] = v;
+  }
+}
+
+__device__ __forceinline__ int phase_tiles(const Phase &ph) {
+  if (ph.m <= 0 || ph.n <= 0) return 0;
+  return ((ph.m + BM - 1) / BM) * ((ph.n + BN - 1) / BN);
+}
+
+// Run independent phases over one shared tile index space (no barrier).
+__device__ void run_phases(const Phase *ph, int count) {
+  __shared__ double As[BM][BK + 1];
+  __shared__ double Bs[BK][BN + 1];
+  int total = 0;
+  for (int c = 0; c < count; ++c) total += phase_tiles(ph[c]);
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    int c = 0, base = 0;
+    while (t - base >= phase_tiles(ph[c])) { base += phase_tiles(ph[c]); ++c; }
+    phase_tile(ph[c], t - base, As, Bs);
+  }
+}
+
+__device__ __forceinline__ Prod mk(const double *A, int lda, int ta, const double *B, int ldb,
+                                   int tb, double alpha) {
+  Prod p;
+  p.A = A; p.B = B; p.lda = lda; p.ldb = ldb; p.ta = ta; p.tb = tb; p.alpha = alpha;
+  return p;
+}
+
+__device__ __forceinline__ Phase mkphase(int m, int n, int k, double *out, int ldo) {
+  Phase ph;
+  ph.m = m; ph.n = n; ph.k = k; ph.np = 0;
+  ph.C1 = nullptr; ph.ldc1 = 0; ph.beta1 = 0.0;
+  ph.C2 = nullptr; ph.ldc2 = 0; ph.beta2 = 0.0;
+  ph.diag = 0.0; ph.out = out; ph.ldo = ldo;
+  return ph;
+}
+
+#define BARRIER_OR_RETURN()                      \
+  do {                                           \
+    if (!grid_barrier(a.bar, a.flags)) return;   \
+  } while (0)
+
+// Forward: P, j, Q^k, Taylor series, doublings, U_occ = [cos sqrt P; -A^T s(P)],
+// O = C0 U_occ, D = 2 O O^T, H <- T.
+__global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
+  const int M = a.M, N = a.N, V = a.V;
+  const long NN = (long)N * N;
+  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long gstride = (long)gridDim.x * blockDim.x;
+  __shared__ int sh_j;
+  __shared__ double sh_sc;
+
+  {  // P = A_ov A_ov^T
+    Phase ph = mkphase(N, N, V, a.P, N);
+    ph.np = 1; ph.p[0] = mk(a.A, V, 0, a.A, V, 1, 1.0);
+    run_phases(&ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  {
+    double s = 0.0;
+    for (long e = gtid; e < NN; e += gstride) s += a.P[e] * a.P[e];
+    s = block_sum(s);
+    if (threadIdx.x == 0) a.red[blockIdx.x] = s;
+  }
+  BARRIER_OR_RETURN();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += a.red[b];
+    double nrm = sqrt(t);
+    int j = 0;
+    while (nrm > 1.0 && j <= kJmax) { nrm *= 0.25; ++j; }
+    if (!(t == t) || isinf(t)) j = kJmax + 1;
+    sh_j = j;
+    sh_sc = ldexp(1.0, -2 * j);
+  }
+  __syncthreads();
+  const int J = sh_j;
+  const double sc = sh_sc;
+  if (J > kJmax) {
+    if (gtid == 0) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+    return;
+  }
+  if (gtid == 0) { a.flags[FLAG_J] = J; a.scal[0] = sc; }
+  for (long e = gtid; e < NN; e += gstride) a.Qk[e] = sc * a.P[e];
+  BARRIER_OR_RETURN();
+  for (int k = 2; k <= kTaylor; ++k) {  // Q^k = Q Q^(k-1)
+    Phase ph = mkphase(N, N, N, a.Qk + (long)(k - 1) * NN, N);
+    ph.np = 1; ph.p[0] = mk(a.Qk, N, 0, a.Qk + (long)(k - 2) * NN, N, 0, 1.0);
+    run_phases(&ph, 1);
+    BARRIER_OR_RETURN();
+  }
+  for (long e = gtid; e < NN; e += gstride) {
+    int i = (int)(e / N), c = (int)(e % N);
+    double kv = 0.0, sv = 0.0;
+    for (int k = kTaylor; k >= 1; --k) {
+      double q = a.Qk[(long)(k - 1) * NN + e];
+      kv += a.ck[k] * q;
+      sv += a.sk[k] * q;
+    }
+    a.Kt[e] = kv;
+    a.St[e] = sv + (i == c ? 1.0 : 0.0);
+  }
+  BARRIER_OR_RETURN();
+  for (int t = 0; t < J; ++t) {  // doubling: k' = 4k + 2k^2, s' = s + s k
+    const double *Kc = a.Kt + (long)t * NN, *Sc = a.St + (long)t * NN;
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, a.Kt + (long)(t + 1) * NN, N);
+    ph[0].np = 1; ph[0].p[0] = mk(Kc, N, 0, Kc, N, 0, 2.0);
+    ph[0].C1 = Kc; ph[0].ldc1 = N; ph[0].beta1 = 4.0;
+    ph[1] = mkphase(N, N, N, a.St + (long)(t + 1) * NN, N);
+    ph[1].np = 1; ph[1].p[0] = mk(Sc, N, 0, Kc, N, 0, 1.0);
+    ph[1].C1 = Sc; ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    run_phases(ph, 2);
+    BARRIER_OR_RETURN();
+  }
+  {
+    const double *KJ = a.Kt + (long)J * NN, *SJ = a.St + (long)J * NN;
+    for (long e = gtid; e < NN; e += gstride) {
+      int i = (int)(e / N), c = (int)(e % N);
+      a.Uocc[e] = KJ[e] + (i == c ? 1.0 : 0.0);
+    }
+    Phase ph = mkphase(V, N, N, a.Uocc + NN, N);  // -A^T s(P)
+    ph.np = 1; ph.p[0] = mk(a.A, V, 1, SJ, N, 0, -1.0);
+    run_phases(&ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  {
+    Phase ph = mkphase(M, N, M, a.O, N);  // O = C0 U_occ
+    ph.np = 1; ph.p[0] = mk(a.C0, M, 0, a.Uocc, N, 0, 1.0);
+    run_phases(&ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  {
+    Phase ph = mkphase(M, M, N, a.D, M);  // D = 2 O O^T (Eq. 12, f = 2)
+    ph.np = 1; ph.p[0] = mk(a.O, N, 0, a.O, N, 1, 2.0);
+    run_phases(&ph, 1);
+    const long MM = (long)M * M;
+    for (long e = gtid; e < MM; e += gstride) a.H[e] = a.T[e];
+  }
+}
+
+// Reverse: E = Tr(D T) + grid terms; dE/dO = 4 H O; dE/dU = C0^T (4 H O);
+// back through U_occ, the doublings, the Taylor powers and P = A A^T.
+__global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want_grad) {
+  const int M = a.M, N = a.N, V = a.V;
+  const long NN = (long)N * N, MM = (long)M * M;
+  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long gstride = (long)gridDim.x * blockDim.x;
+  {
+    double s = 0.0;
+    for (long e = gtid; e < MM; e += gstride) s += a.D[e] * a.T[e];
+    s = block_sum(s);
+    if (threadIdx.x == 0) a.red[blockIdx.x] = s;
+    if (want_grad) {  // the grid pass accumulated the upper triangle of H
+      for (long e = gtid; e < MM; e += gstride) {
+        int i = (int)(e / M), c = (int)(e % M);
+        if (i > c) a.H[e] = a.H[(long)c * M + i];
+      }
+    }
+  }
+  BARRIER_OR_RETURN();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double kin = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) kin += a.red[b];
+    double t3[3] = {0.0, 0.0, 0.0}, c3[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < a.n_gridpart; ++b) {  // compensated sums
+      for (int q = 0; q < 3; ++q) {
+        double y = a.gridpart[3 * b + q] - c3[q];
+        double tt = t3[q] + y;
+        c3[q] = (tt - t3[q]) - y;
+        t3[q] = tt;
+      }
+    }
+    double E = kin + t3[0] + t3[1] + t3[2];
+    a.eterms[0] = kin; a.eterms[1] = t3[0]; a.eterms[2] = t3[1]; a.eterms[3] = t3[2];
+    if (a.E) *a.E = E;
+    if (!(E == E) || isinf(E)) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+  }
+  if (!want_grad) return;
+  {
+    Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = 4 H O
+    ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
+    run_phases(&ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  {
+    Phase ph = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
+    ph.np = 1; ph.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
+    run_phases(&ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  const int J = a.flags[FLAG_J];
+  const double sc = a.scal[0];
+  const double *Ubv = a.Ubar + NN;  // rows N..M-1 (V x N)
+  {
+    Phase ph[2];
+    ph[0] = mkphase(N, N, V, a.Sbar[0], N);  // Sbar_J = -A Ubar_v
+    ph[0].np = 1; ph[0].p[0] = mk(a.A, V, 0, Ubv, N, 0, -1.0);
+    ph[1] = mkphase(N, V, N, a.Abar, V);     // Abar = -S_J Ubar_v^T
+    ph[1].np = 1; ph[1].p[0] = mk(a.St + (long)J * NN, N, 0, Ubv, N, 1, -1.0);
+    run_phases(ph, 2);
+  }
+  BARRIER_OR_RETURN();
+  const double *kb = a.Ubar;  // Kbar_J = cotangent of cos sqrt(P) = Ubar_o
+  const double *sb = a.Sbar[0];
+  int pp = 0;
+  for (int t = J - 1; t >= 0; --t) {
+    const double *Kc = a.Kt + (long)t * NN, *Sc = a.St + (long)t * NN;
+    double *kbo = a.Kbar[pp], *sbo = a.Sbar[1 - pp];
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, sbo, N);
+    ph[0].np = 1; ph[0].p[0] = mk(sb, N, 0, Kc, N, 0, 1.0);
+    ph[0].C1 = sb; ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    ph[1] = mkphase(N, N, N, kbo, N);
+    ph[1].np = 3;
+    ph[1].p[0] = mk(kb, N, 0, Kc, N, 0, 2.0);
+    ph[1].p[1] = mk(Kc, N, 0, kb, N, 0, 2.0);
+    ph[1].p[2] = mk(Sc, N, 0, sb, N, 0, 1.0);
+    ph[1].C1 = kb; ph[1].ldc1 = N; ph[1].beta1 = 4.0;
+    run_phases(ph, 2);
+    BARRIER_OR_RETURN();
+    kb = kbo; sb = sbo; pp = 1 - pp;
+  }
+  // Z_K = c_K Kbar_0 + s_K Sbar_0
+  for (long e = gtid; e < NN; e += gstride)
+    a.Z[0][e] = a.ck[kTaylor] * kb[e] + a.sk[kTaylor] * sb[e];
+  BARRIER_OR_RETURN();
+  int zp = 0;
+  for (int k = kTaylor - 1; k >= 1; --k) {
+    const double *Zin = a.Z[zp];
+    double *Zout = a.Z[1 - zp];
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, a.Qbar, N);  // Qbar += Z_{k+1} Q^k
+    ph[0].np = 1; ph[0].p[0] = mk(Zin, N, 0, a.Qk + (long)(k - 1) * NN, N, 0, 1.0);
+    if (k < kTaylor - 1) { ph[0].C1 = a.Qbar; ph[0].ldc1 = N; ph[0].beta1 = 1.0; }
+    ph[1] = mkphase(N, N, N, Zout, N);    // Z_k = Q Z_{k+1} + c_k Kbar_0 + s_k Sbar_0
+    ph[1].np = 1; ph[1].p[0] = mk(a.Qk, N, 0, Zin, N, 0, 1.0);
+    ph[1].C1 = kb; ph[1].ldc1 = N; ph[1].beta1 = a.ck[k];
+    ph[1].C2 = sb; ph[1].ldc2 = N; ph[1].beta2 = a.sk[k];
+    run_phases(ph, 2);
+    BARRIER_OR_RETURN();
+    zp = 1 - zp;
+  }
+  {
+    const double *Z1 = a.Z[zp];
+    for (long e = gtid; e < NN; e += gstride) {
+      int i = (int)(e / N), c = (int)(e % N);
+      long et = (long)c * N + i;
+      a.Psym[e] = sc * (a.Qbar[e] + Z1[e] + a.Qbar[et] + Z1[et]);
+    }
+  }
+  BARRIER_OR_RETURN();
+  {
+    Phase ph = mkphase(N, V, N, a.g, V);  // g = Abar + (Pbar + Pbar^T) A
+    ph.np = 1; ph.p[0] = mk(a.Psym, N, 0, a.A, V, 0, 1.0);
+    ph.C1 = a.Abar; ph.ldc1 = V; ph.beta1 = 1.0;
+    run_phases(&ph, 1);
+  }
+}
+
+// Plain (non-cooperative) product for set-up work.
+__global__ void __launch_bounds__(NT) gemm_kernel(Phase ph) { run_phases(&ph, 1); }
+
+// ---- L-BFGS two-loop (Sec. 3.1) with H0 = P^(k) (Eq. 33-34) ---------------
+__device__ __forceinline__ double precond_elem(const double *eps, int N, int V, long e,
+                                               double gamma, double beta) {
+  int i = (int)(e / V), jv = (int)(e % V);
+  double d = (eps[i] - eps[N + jv]) * 2.0;  // (e_i - e_j)(f_i - f_j), f = 2 / 0
+  return 1.0 / (2.0 * (1.0 - gamma) * fabs(d) + gamma * beta);
+}
+
+// Dot product of the whole grid: every block gets the same value.
+__device__ double grid_dot_finish(LbfgsArgs &a, double part, bool *ok) {
+  part = block_sum(part);
+  if (threadIdx.x == 0) a.red[blockIdx.x] = part;
+  if (!grid_barrier(a.bar, a.flags)) { *ok = false; return 0.0; }
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += a.red[b];
+    tot = t;
+  }
+  __syncthreads();
+  double r = tot;
+  // a second barrier keeps red[] from being overwritten before all blocks read it
+  if (!grid_barrier(a.bar, a.flags)) { *ok = false; return 0.0; }
+  return r;
+}
+
+__global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
+  const long n = a.n;
+  const int m = a.m;
+  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long gstride = (long)gridDim.x * blockDim.x;
+  double *st = a.state;
+  int count = (int)st[0], head = (int)st[1];
+  const bool have_prev = st[2] != 0.0;
+  double beta = st[3];
+  bool ok = true;
+  if (have_prev) {  // candidate pair into slot `head`
+    double *sn = a.s + (long)head * n, *yn = a.y + (long)head * n;
+    double p1 = 0.0, p2 = 0.0;
+    for (long e = gtid; e < n; e += gstride) {
+      double sv = a.a[e] - a.aprev[e], yv = a.g[e] - a.gprev[e];
+      sn[e] = sv; yn[e] = yv;
+      p1 += sv * yv; p2 += yv * yv;
+    }
+    double sy = grid_dot_finish(a, p1, &ok); if (!ok) return;
+    double yy = grid_dot_finish(a, p2, &ok); if (!ok) return;
+    if (sy > 1e-30) {
+      beta = yy / sy;
+      st[4 + head] = 1.0 / sy;  // rho of the slot (identical in every block)
+      head = (head + 1) % m;
+      count = count < m ? count + 1 : m;
+    }
+  }
+  for (long e = gtid; e < n; e += gstride) {
+    a.aprev[e] = a.a[e];
+    a.gprev[e] = a.g[e];
+    a.q[e] = a.g[e];
+  }
+  // first loop: newest to oldest
+  double alph[16];
+  for (int c = 0; c < count; ++c) {
+    int slot = (head - 1 - c + 2 * m) % m;
+    const double *sv = a.s + (long)slot * n, *yv = a.y + (long)slot * n;
+    double part = 0.0;
+    for (long e = gtid; e < n; e += gstride) part += sv[e] * a.q[e];
+    double sq = grid_dot_finish(a, part, &ok); if (!ok) return;
+    double al = st[4 + slot] * sq;
+    alph[c] = al;
+    for (long e = gtid; e < n; e += gstride) a.q[e] -= al * yv[e];
+  }
+  // r = H0 q
+  for (long e = gtid; e < n; e += gstride)
+    a.q[e] *= precond_elem(a.eps, a.N, a.V, e, a.gamma, beta);
+  // second loop: oldest to newest
+  for (int c = count - 1; c >= 0; --c) {
+    int slot = (head - 1 - c + 2 * m) % m;
+    const double *sv = a.s + (long)slot * n, *yv = a.y + (long)slot * n;
+    double part = 0.0;
+    for (long e = gtid; e < n; e += gstride) part += yv[e] * a.q[e];
+    double yr = grid_dot_finish(a, part, &ok); if (!ok) return;
+    double be = st[4 + slot] * yr;
+    double coef = alph[c] - be;
+    for (long e = gtid; e < n; e += gstride) a.q[e] += coef * sv[e];
+  }
+  for (long e = gtid; e < n; e += gstride) a.p[e] = -a.q[e];
+  if (!grid_barrier(a.bar, a.flags)) return;
+  if (gtid == 0) {
+    st[0] = count; st[1] = head; st[2] = 1.0; st[3] = beta;
+  }
+}
+
+__global__ void precond_kernel(const double *eps, int N, int V, double gamma,
+                               const double *state, const double *g, double *pg) {
+  long n = (long)N * V;
+  double beta = state[3];
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x)
+    pg[e] = precond_elem(eps, N, V, e, gamma, beta) * g[e];
+}
+
+// Deterministic single-block dot product (line-search scalars).
+__global__ void __launch_bounds__(1024) dot_kernel(const double *x, const double *y, long n,
+                                                   double *out) {
+  double s = 0.0;
+  for (long e = threadIdx.x; e < n; e += blockDim.x) s += x[e] * y[e];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void axpy_kernel(const double *x, double alpha, const double *p, double *out,
+                            long n) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x)
+    out[e] = x[e] + alpha * p[e];
+}
+
+__global__ void permute_cols_kernel(const double *src, const int *perm, double *dst, int M) {
+  long MM = (long)M * M;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
+       e += (long)gridDim.x * blockDim.x) {
+    int r = (int)(e / M), c = (int)(e % M);
+    dst[e] = src[(long)r * M + perm[c]];
+  }
+}
+
+// out[j] = sum_{m,n} C[m][j] Hm[m][n] C[n][j]
+__global__ void __launch_bounds__(256) diag_quad_kernel(const double *C, const double *Hm,
+                                                        double *out, int M) {
+  int j = blockIdx.x;
+  double s = 0.0;
+  for (long e = threadIdx.x; e < (long)M * M; e += blockDim.x) {
+    int r = (int)(e / M), c = (int)(e % M);
+    s += C[(long)r * M + j] * Hm[e] * C[(long)c * M + j];
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+__global__ void ns_prep_kernel(const double *S, double *Y, double *Zm, double c, int M) {
+  long MM = (long)M * M;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
+       e += (long)gridDim.x * blockDim.x) {
+    int r = (int)(e / M), q = (int)(e % M);
+    Y[e] = S[e] / c;
+    Zm[e] = (r == q) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(1024) resid_kernel(const double *ZY, double *out, int M) {
+  double mx = 0.0;
+  for (long e = threadIdx.x; e < (long)M * M; e += blockDim.x) {
+    int r = (int)(e / M), q = (int)(e % M);
+    double d = fabs(ZY[e] - (r == q ? 1.0 : 0.0));
+    if (!(d <= mx)) mx = d;  // NaN propagates
+  }
+  __shared__ double red[1024];
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double o = red[threadIdx.x + s];
+      if (!(o <= red[threadIdx.x])) red[threadIdx.x] = o;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void __launch_bounds__(1024) max_rowsum_kernel(const double *S, double *out, int M) {
+  double mx = 0.0;
+  for (int r = threadIdx.x; r < M; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < M; ++c) s += fabs(S[(long)r * M + c]);
+    mx = fmax(mx, s);
+  }
+  __shared__ double red[1024];
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void scale_copy_kernel(const double *src, double *dst, double c, long n) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x)
+    dst[e] = c * src[e];
+}
+
+// ---- host wrappers ----------------------------------------------------------
+
+static DenseArgs dense_args(etdm_handle *h, const double *a) {
+  DenseArgs d{};
+  d.M = h->M; d.N = h->N; d.V = h->V;
+  d.A = a;
+  d.P = h->d_P; d.Qk = h->d_Qk; d.Kt = h->d_Kt; d.St = h->d_St;
+  d.Uocc = h->d_Uocc; d.O = h->d_O; d.D = h->d_D; d.H = h->d_H;
+  d.C0 = h->d_C0; d.T = h->d_T;
+  d.Gbar = h->d_Gbar; d.Ubar = h->d_Ubar;
+  d.Kbar[0] = h->d_bar2[0]; d.Kbar[1] = h->d_bar2[1];
+  d.Sbar[0] = h->d_bar2[2]; d.Sbar[1] = h->d_bar2[3];
+  d.Z[0] = h->d_bar2[4]; d.Z[1] = h->d_bar2[5];
+  d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym;
+  d.eterms = h->d_eterms;
+  d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
+  d.red = h->d_red; d.flags = h->d_flags; d.bar = h->d_bar; d.scal = h->d_scal;
+  // c_k = (-1)^k/(2k)!, s_k = (-1)^k/(2k+1)!
+  double f = 1.0;
+  d.ck[0] = 0.0; d.sk[0] = 1.0;
+  for (int k = 1; k <= kTaylor; ++k) {
+    double f2k = f * (2 * k);                 // (2k)!  (f = (2k-1)!)
+    double f2k1 = f2k * (2 * k + 1);          // (2k+1)!
+    double sg = (k % 2) ? -1.0 : 1.0;
+    d.ck[k] = sg / f2k;
+    d.sk[k] = sg / f2k1;
+    f = f2k1;
+  }
+  return d;
+}
+
+cudaError_t launch_dense_forward(etdm_handle *h, const double *a, cudaStream_t s) {
+  DenseArgs d = dense_args(h, a);
+  void *args[] = {&d};
+  return cudaLaunchCooperativeKernel((void *)dense_forward_kernel, dim3(h->coop_blocks),
+                                     dim3(NT), args, 0, s);
+}
+
+cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, double *E,
+                                 cudaStream_t s) {
+  DenseArgs d = dense_args(h, a);
+  d.g = g; d.E = E;
+  int want = g != nullptr;
+  void *args[] = {&d, &want};
+  return cudaLaunchCooperativeKernel((void *)dense_reverse_kernel, dim3(h->coop_blocks),
+                                     dim3(NT), args, 0, s);
+}
+
+cudaError_t launch_gemm(const Phase &ph, cudaStream_t s) {
+  int tiles = ((ph.m + BM - 1) / BM) * ((ph.n + BN - 1) / BN);
+  if (tiles <= 0) return cudaSuccess;
+  gemm_kernel<<<tiles, NT, 0, s>>>(ph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs(etdm_handle *h, const double *a, const double *g, double *p,
+                         cudaStream_t s) {
+  LbfgsArgs d{};
+  d.n = (long)h->N * h->V; d.N = h->N; d.V = h->V; d.m = h->lbfgs_m;
+  d.a = a; d.g = g; d.p = p;
+  d.s = h->d_s; d.y = h->d_y; d.aprev = h->d_aprev; d.gprev = h->d_gprev; d.q = h->d_q;
+  d.state = h->d_lbstate; d.eps = h->d_eps; d.gamma = h->gamma;
+  d.red = h->d_red; d.bar = h->d_bar; d.flags = h->d_flags;
+  void *args[] = {&d};
+  return cudaLaunchCooperativeKernel((void *)lbfgs_kernel, dim3(h->lb_blocks), dim3(256), args,
+                                     0, s);
+}
+
+cudaError_t launch_precond(etdm_handle *h, const double *g, double *pg, cudaStream_t s) {
+  long n = (long)h->N * h->V;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+  if (blocks < 1) blocks = 1;
+  precond_kernel<<<blocks, 256, 0, s>>>(h->d_eps, h->N, h->V, h->gamma, h->d_lbstate, g, pg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double *x, const double *y, long n, double *out, double *,
+                       cudaStream_t s) {
+  dot_kernel<<<1, 1024, 0, s>>>(x, y, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(const double *x, double alpha, const double *p, double *out, long n,
+                        cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  axpy_kernel<<<blocks, 256, 0, s>>>(x, alpha, p, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_cols(const double *src, const int *perm, double *dst, int M,
+                                cudaStream_t s) {
+  permute_cols_kernel<<<256, 256, 0, s>>>(src, perm, dst, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_quad(const double *C, const double *Hm, double *out, int M,
+                             cudaStream_t s) {
+  diag_quad_kernel<<<M, 256, 0, s>>>(C, Hm, out, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_prep(const double *S, double *Y, double *Zm, double c, int M,
+                           cudaStream_t s) {
+  ns_prep_kernel<<<256, 256, 0, s>>>(S, Y, Zm, c, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid(const double *ZY, double *out, int M, cudaStream_t s) {
+  resid_kernel<<<1, 1024, 0, s>>>(ZY, out, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t s) {
+  max_rowsum_kernel<<<1, 1024, 0, s>>>(S, out, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n,
+                              cudaStream_t s) {
+  scale_copy_kernel<<<256, 256, 0, s>>>(src, dst, c, n);
+  return cudaGetLastError();
+}
+
+int occupancy_dense(int *bps) {
+  int a = 0, b = 0;
+  cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, dense_forward_kernel, NT, 0);
+  cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dense_reverse_kernel, NT, 0);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return -1;
+  *bps = a < b ? a : b;
+  return 0;
+}
+
+int occupancy_lbfgs(int *bps) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, lbfgs_kernel, 256, 0) != cudaSuccess)
+    return -1;
+  return 0;
+}
+
+}  // namespace etdm

@@ -1,0 +1,217 @@
+// Internal declarations shared by the translation units of libetdm.
+// Nothing here is part of the C ABI (include/etdm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/etdm.h"
+
+namespace etdm {
+
+constexpr int kImgMax = 3;          // |n| <= 3 lattice images per axis
+constexpr int kImgN = 2 * kImgMax + 1;
+constexpr int kTaylor = 10;         // Taylor terms of cos sqrt(Q), sin sqrt(Q)/sqrt(Q)
+constexpr int kJmax = 8;            // doublings: |P|_F <= 4^8
+constexpr int kMaxList = 200;       // max truncation-list length per tile (FP64 path)
+constexpr int kPotBlocks = 512;     // blocks (and energy partials) of the potential pass
+constexpr int kMaxFFT = 256;        // max grid points per axis
+constexpr long kSpinLimit = 2000000;   // bounded device waits (a few seconds at most)
+
+// device-side status words
+enum { FLAG_ERR = 0, FLAG_J = 1, FLAG_NFLAGS = 4 };
+
+struct GridGeom {
+  int nx, ny, nz;
+  int tx, ty, tz;      // tile edges
+  int nbx, nby, nbz;   // tiles per axis
+  int M;
+  double dV;
+};
+
+// Basis tables on the grid axes: for function mu, image n and axis point i,
+//   sq[a][mu][n+3][i] = (x_i - (d_mu + n L))^2   (exact op order)
+//   ex[a][mu][n+3][i] = exp(-alpha_mu * sq)
+struct Tables {
+  const double *sq[3];
+  const double *ex[3];
+  const double *norm;  // (2 alpha / pi)^(3/4)
+  const double *rc2;   // r_c * r_c
+};
+
+// One dense product term for the cooperative dense kernels.
+struct Prod {
+  const double *A;
+  const double *B;
+  int lda, ldb;
+  int ta, tb;   // op(A)[i][k] = ta ? A[k*lda+i] : A[i*lda+k]; same for B
+  double alpha;
+};
+
+// out[i][j] = sum_p alpha_p op(A_p) op(B_p) + beta1 C1 + beta2 C2 + diag * I
+struct Phase {
+  int m, n, k;
+  int np;
+  Prod p[3];
+  const double *C1; int ldc1; double beta1;
+  const double *C2; int ldc2; double beta2;
+  double diag;
+  double *out; int ldo;
+};
+
+struct DenseArgs {
+  int M, N, V;
+  const double *A;       // a, N x V
+  double *P;             // N x N
+  double *Qk;            // [kTaylor][N*N]  Q^1 .. Q^K
+  double *Kt;            // [kJmax+1][N*N] cos sqrt(Q_t) - I
+  double *St;            // [kJmax+1][N*N] sin sqrt(Q_t)/sqrt(Q_t)
+  double *Uocc;          // M x N
+  double *O;             // M x N
+  double *D;             // M x M
+  double *H;             // M x M
+  const double *C0;      // M x M
+  const double *T;       // M x M
+  double *Gbar, *Ubar;   // M x N
+  double *Kbar[2], *Sbar[2], *Z[2];
+  double *Qbar, *Abar, *Psym;
+  double *g;             // N x V output (may be null)
+  double *E;             // scalar output (may be null)
+  double *eterms;        // [4] kinetic, external, hartree, exchange
+  const double *gridpart;  // [n_gridpart][3] energy partials of the grid
+  int n_gridpart;
+  double *red;           // reduction scratch [gridDim][2]
+  int *flags;
+  unsigned *bar;         // grid barrier {count, generation}
+  double *scal;          // [0] = 4^-j
+  double ck[kTaylor + 1], sk[kTaylor + 1];
+};
+
+struct LbfgsArgs {
+  long n;
+  int N, V, m;
+  const double *a, *g;
+  double *p;
+  double *s, *y;         // [m][n]
+  double *aprev, *gprev, *q;
+  double *state;         // [0]=count [1]=head [2]=have_prev [3]=beta [4..4+m)=rho [..+m)=alpha
+  const double *eps;     // [M]
+  double gamma;
+  double *red;           // [2*gridDim]
+  unsigned *bar;
+  int *flags;
+};
+
+}  // namespace etdm
+
+struct etdm_handle {
+  int device = 0;
+  int precision = ETDM_PREC_FP64;
+  int lbfgs_m = 3;
+  double gamma = 0.25, beta0 = 1.0;
+  int M = 0, N = 0, V = 0, n_atoms = 0;
+  int n[3] = {0, 0, 0};
+  long G = 0;
+  double L[3], h[3], dV = 0, omega = 0, sigma = 0;
+  etdm::GridGeom geom{};
+  int n_tiles = 0;
+  long n_entries = 0;
+  int max_list = 0;
+  long long sum_npt2 = 0;
+  int num_sms = 0;
+  int coop_blocks = 0;
+  int lb_blocks = 0;
+  std::string err;
+  std::vector<int> order;
+
+  // system
+  double *d_center = nullptr, *d_alpha = nullptr, *d_norm = nullptr,
+         *d_rc2 = nullptr, *d_rcut = nullptr, *d_pos = nullptr, *d_Z = nullptr;
+  double *d_sq = nullptr, *d_ex = nullptr;
+  long tab_off[3] = {0, 0, 0};
+  int *d_tile_ptr = nullptr, *d_keys = nullptr;
+  // matrices
+  double *d_S = nullptr, *d_T = nullptr, *d_C0 = nullptr;
+  double *d_D = nullptr, *d_H = nullptr, *d_Uocc = nullptr, *d_O = nullptr;
+  double *d_P = nullptr, *d_Qk = nullptr, *d_Kt = nullptr, *d_St = nullptr;
+  double *d_Gbar = nullptr, *d_Ubar = nullptr;
+  double *d_bar2[6] = {nullptr};
+  double *d_Qbar = nullptr, *d_Abar = nullptr, *d_Psym = nullptr;
+  // grid
+  double *d_vext = nullptr, *d_rho = nullptr, *d_vtot = nullptr;
+  double2 *d_fft = nullptr;
+  double2 *d_tw = nullptr;   // twiddles per axis (n[0]+n[1]+n[2])
+  double *d_gridpart = nullptr;
+  int n_gridpart = 0;
+  // scalars / flags
+  double *d_E = nullptr, *d_eterms = nullptr, *d_scal = nullptr;
+  double *d_red = nullptr;
+  int *d_flags = nullptr;
+  unsigned *d_bar = nullptr;
+  double *d_eps = nullptr;
+  // L-BFGS
+  double *d_s = nullptr, *d_y = nullptr, *d_aprev = nullptr, *d_gprev = nullptr,
+         *d_q = nullptr, *d_lbstate = nullptr;
+  // host-API staging and line search buffers
+  double *d_a = nullptr, *d_g = nullptr, *d_at = nullptr, *d_gt = nullptr,
+         *d_p = nullptr, *d_dot = nullptr;
+  double *h_pinned = nullptr;
+  std::vector<void *> allocs;
+  // optional per-stage CUDA-event timing (etdm_set_profiling)
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+  double stage_ms[16] = {0};
+  long long stage_n[16] = {0};
+  long long launches = 0;
+};
+
+namespace etdm {
+
+// ---- launch wrappers (return cudaError_t of the launch) --------------------
+// grid basis and lists (grid.cu)
+cudaError_t launch_tables(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_list_count(etdm_handle *h, int *d_count, cudaStream_t s);
+cudaError_t launch_list_fill(etdm_handle *h, const long long *d_off, cudaStream_t s);
+cudaError_t launch_scan(const int *d_in, long long *d_out, long n, long long *d_tmp,
+                        cudaStream_t s);
+cudaError_t launch_npt2(etdm_handle *h, unsigned long long *d_sum, cudaStream_t s);
+cudaError_t launch_overlap_kinetic(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_rho_fp64(etdm_handle *h, const double *D, double *rho, cudaStream_t s);
+cudaError_t launch_vmat_fp64(etdm_handle *h, const double *v, double *Hacc, cudaStream_t s);
+// fft and potential (potential.cu)
+cudaError_t launch_twiddles(etdm_handle *h, cudaStream_t s);
+cudaError_t fft3d(etdm_handle *h, double2 *data, int sign, cudaStream_t s);
+cudaError_t launch_vext_recip(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_real_part(etdm_handle *h, const double2 *src, double *dst, cudaStream_t s);
+cudaError_t launch_pack_real(etdm_handle *h, const double *src, double2 *dst, cudaStream_t s);
+cudaError_t launch_poisson_scale(etdm_handle *h, double2 *data, cudaStream_t s);
+cudaError_t launch_potential(etdm_handle *h, cudaStream_t s);
+// dense (dense.cu)
+cudaError_t launch_gemm(const Phase &ph, cudaStream_t s);
+cudaError_t launch_dense_forward(etdm_handle *h, const double *a, cudaStream_t s);
+cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, double *E,
+                                 cudaStream_t s);
+cudaError_t launch_lbfgs(etdm_handle *h, const double *a, const double *g, double *p,
+                         cudaStream_t s);
+cudaError_t launch_precond(etdm_handle *h, const double *g, double *pg, cudaStream_t s);
+cudaError_t launch_dot(const double *x, const double *y, long n, double *out, double *red,
+                       cudaStream_t s);
+cudaError_t launch_axpy(const double *x, double alpha, const double *p, double *out, long n,
+                        cudaStream_t s);
+cudaError_t launch_permute_cols(const double *src, const int *d_perm, double *dst, int M,
+                                cudaStream_t s);
+cudaError_t launch_diag_quad(const double *C, const double *Hm, double *out, int M,
+                             cudaStream_t s);
+cudaError_t launch_ns_prep(const double *S, double *Y, double *Zm, double c, int M,
+                           cudaStream_t s);
+cudaError_t launch_resid(const double *ZY, double *out, int M, cudaStream_t s);
+cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n, cudaStream_t s);
+cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t s);
+int occupancy_dense(int *blocks_per_sm);
+int occupancy_lbfgs(int *blocks_per_sm);
+
+}  // namespace etdm

@@ -1,0 +1,297 @@
+"""Thin ctypes binding of libetdm (include/etdm.h).
+
+Argument marshalling only: every step of the ETDM evaluation runs in the CUDA
+library.  Tensors are torch CUDA tensors (FP64, contiguous); torch supplies
+device memory and streams.  There is no CPU fallback: if libetdm.so is missing
+or no GPU is present, construction fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libetdm.so")
+
+ETDM_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED",
+          -5: "TIMEOUT", -6: "STATE", -7: "NUMERIC"}
+PRECISION = {"fp64": 0, "mixed": 1}
+ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
+          "order": (3, np.int32), "vext": (4, np.float64), "rho": (5, np.float64),
+          "vtot": (6, np.float64), "H": (7, np.float64), "D": (8, np.float64),
+          "Uocc": (9, np.float64), "tile_ptr": (10, np.int32),
+          "tile_keys": (11, np.int32), "eps": (12, np.float64),
+          "eterms": (13, np.float64), "beta": (14, np.float64)}
+DIM_NAMES = ["M", "N", "V", "G", "n_tiles", "entries", "max_list", "tx", "ty",
+             "tz", "sum_npt2", "precision"]
+
+EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
+           "etdm_energy_grad_host", "etdm_precondition", "etdm_lbfgs_step",
+           "etdm_lbfgs_reset", "etdm_minimize", "etdm_check", "etdm_layout",
+           "etdm_array_bytes", "etdm_get_array", "etdm_set_profiling",
+           "etdm_stage_times", "etdm_last_error", "etdm_free"]
+STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
+
+
+class EtdmSystem(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32),
+                ("pos", ctypes.POINTER(ctypes.c_double)),
+                ("Z", ctypes.POINTER(ctypes.c_double)),
+                ("n_basis", ctypes.c_int32),
+                ("bf_atom", ctypes.POINTER(ctypes.c_int32)),
+                ("bf_exp", ctypes.POINTER(ctypes.c_double)),
+                ("bf_rcut", ctypes.POINTER(ctypes.c_double)),
+                ("box", ctypes.c_double * 3),
+                ("grid", ctypes.c_int32 * 3),
+                ("ion_sigma", ctypes.c_double),
+                ("n_electrons", ctypes.c_int32)]
+
+
+class EtdmOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32),
+                ("lbfgs_m", ctypes.c_int32),
+                ("gamma", ctypes.c_double),
+                ("beta0", ctypes.c_double),
+                ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libetdm.so and declare the C ABI.  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2101_12597_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.etdm_default_options.argtypes = [ctypes.POINTER(EtdmOptions)]
+    lib.etdm_default_options.restype = None
+    lib.etdm_init_basis.argtypes = [ctypes.POINTER(EtdmSystem), ctypes.POINTER(EtdmOptions),
+                                    ctypes.POINTER(P)]
+    lib.etdm_energy_grad.argtypes = [P, P, P, P, P]
+    lib.etdm_energy_grad_host.argtypes = [P, dp, dp, dp]
+    lib.etdm_precondition.argtypes = [P, P, P, P]
+    lib.etdm_lbfgs_step.argtypes = [P, P, P, P, P]
+    lib.etdm_lbfgs_reset.argtypes = [P]
+    lib.etdm_minimize.argtypes = [P, P, ctypes.c_int32, dp, dp,
+                                  ctypes.POINTER(ctypes.c_int32), P]
+    lib.etdm_check.argtypes = [P, P]
+    lib.etdm_layout.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.etdm_array_bytes.argtypes = [P, ctypes.c_int32]
+    lib.etdm_array_bytes.restype = ctypes.c_int64
+    lib.etdm_get_array.argtypes = [P, ctypes.c_int32, P, ctypes.c_int64]
+    lib.etdm_set_profiling.argtypes = [P, ctypes.c_int]
+    lib.etdm_stage_times.argtypes = [P, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.etdm_last_error.argtypes = [P]
+    lib.etdm_last_error.restype = ctypes.c_char_p
+    lib.etdm_free.argtypes = [P]
+    lib.etdm_free.restype = None
+    for name in EXPORTS:
+        if name not in ("etdm_default_options", "etdm_last_error", "etdm_free",
+                        "etdm_array_bytes"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class EtdmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ETDM_ERR_{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class ETDM:
+    """One system on one GPU: the handle of etdm_init_basis."""
+
+    def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
+                 device=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
+        self.lib = load_library()
+        self.device = device
+        self._keep = dict(
+            pos=np.ascontiguousarray(sysd["pos"], dtype=np.float64),
+            Z=np.ascontiguousarray(sysd["Z"], dtype=np.float64),
+            bf_atom=np.ascontiguousarray(sysd["bf_atom"], dtype=np.int32),
+            bf_exp=np.ascontiguousarray(sysd["bf_exp"], dtype=np.float64),
+            bf_rcut=np.ascontiguousarray(sysd["bf_rcut"], dtype=np.float64))
+        k = self._keep
+        s = EtdmSystem()
+        s.n_atoms = len(k["Z"])
+        s.pos = _dptr(k["pos"])
+        s.Z = _dptr(k["Z"])
+        s.n_basis = len(k["bf_exp"])
+        s.bf_atom = k["bf_atom"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        s.bf_exp = _dptr(k["bf_exp"])
+        s.bf_rcut = _dptr(k["bf_rcut"])
+        for a in range(3):
+            s.box[a] = float(sysd["box"][a])
+            s.grid[a] = int(sysd["grid"][a])
+        s.ion_sigma = float(sysd["ion_sigma"])
+        s.n_electrons = int(sysd["n_electrons"])
+        o = EtdmOptions()
+        self.lib.etdm_default_options(ctypes.byref(o))
+        o.precision = PRECISION[precision]
+        o.lbfgs_m = lbfgs_m
+        o.gamma = gamma
+        o.beta0 = beta0
+        o.device = device
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
+        if rc != ETDM_OK:
+            raise EtdmError(rc, self.lib.etdm_last_error(None).decode())
+        self.h = h
+        dims = (ctypes.c_int64 * 12)()
+        self.lib.etdm_layout(self.h, dims)
+        self.dims = dict(zip(DIM_NAMES, [int(x) for x in dims]))
+        self.M, self.N, self.V = self.dims["M"], self.dims["N"], self.dims["V"]
+        self.dev = torch.device("cuda", device)
+
+    # -- helpers ----------------------------------------------------------------
+    def _raise(self, rc):
+        if rc != ETDM_OK:
+            raise EtdmError(rc, self.lib.etdm_last_error(self.h).decode())
+
+    def _check_tensor(self, t, shape):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
+            raise ValueError(f"expected a contiguous cuda float64 tensor of shape {shape}")
+
+    # -- entry points -------------------------------------------------------------
+    def energy_grad(self, a, want_grad=True, E=None, g=None, stream=None):
+        """E and dE/dA_ov for a (N x V) on the device; returns (E[1], g or None)."""
+        import torch
+        self._check_tensor(a, (self.N, self.V))
+        if E is None:
+            E = torch.empty(1, dtype=torch.float64, device=self.dev)
+        if want_grad and g is None:
+            g = torch.empty((self.N, self.V), dtype=torch.float64, device=self.dev)
+        rc = self.lib.etdm_energy_grad(self.h, ctypes.c_void_p(a.data_ptr()),
+                                       ctypes.c_void_p(E.data_ptr()),
+                                       ctypes.c_void_p(g.data_ptr()) if want_grad else None,
+                                       _stream_ptr(stream))
+        self._raise(rc)
+        return E, (g if want_grad else None)
+
+    def energy_grad_host(self, a, want_grad=True):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == (self.N, self.V)
+        E = np.zeros(1)
+        g = np.zeros((self.N, self.V)) if want_grad else None
+        rc = self.lib.etdm_energy_grad_host(self.h, _dptr(a), _dptr(E),
+                                            _dptr(g) if want_grad else None)
+        self._raise(rc)
+        return float(E[0]), g
+
+    def precondition(self, g, out=None, stream=None):
+        import torch
+        self._check_tensor(g, (self.N, self.V))
+        out = torch.empty_like(g) if out is None else out
+        self._raise(self.lib.etdm_precondition(self.h, ctypes.c_void_p(g.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()),
+                                               _stream_ptr(stream)))
+        return out
+
+    def lbfgs_step(self, a, g, out=None, stream=None):
+        import torch
+        self._check_tensor(a, (self.N, self.V))
+        self._check_tensor(g, (self.N, self.V))
+        out = torch.empty_like(g) if out is None else out
+        self._raise(self.lib.etdm_lbfgs_step(self.h, ctypes.c_void_p(a.data_ptr()),
+                                             ctypes.c_void_p(g.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()),
+                                             _stream_ptr(stream)))
+        return out
+
+    def lbfgs_reset(self):
+        self._raise(self.lib.etdm_lbfgs_reset(self.h))
+
+    def minimize(self, a, n_steps, stream=None):
+        """Runs n_steps ETDM iterations in place on a; returns (E, alpha, trials)."""
+        self._check_tensor(a, (self.N, self.V))
+        E = np.zeros(n_steps + 1)
+        al = np.zeros(n_steps + 1)
+        tr = np.zeros(n_steps + 1, dtype=np.int32)
+        self._raise(self.lib.etdm_minimize(self.h, ctypes.c_void_p(a.data_ptr()), n_steps,
+                                           _dptr(E), _dptr(al),
+                                           tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           _stream_ptr(stream)))
+        return E, al, tr
+
+    def check(self, stream=None):
+        self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream)))
+
+    def get_array(self, name):
+        which, dt = ARRAYS[name]
+        nb = self.lib.etdm_array_bytes(self.h, which)
+        out = np.zeros(nb // np.dtype(dt).itemsize, dtype=dt)
+        self._raise(self.lib.etdm_get_array(self.h, which, out.ctypes.data_as(ctypes.c_void_p),
+                                            nb))
+        return out
+
+    def set_profiling(self, on=True):
+        self._raise(self.lib.etdm_set_profiling(self.h, 1 if on else 0))
+
+    def stage_times(self):
+        """(ms per stage, launches per stage, total kernel launches) since the last call."""
+        ms = np.zeros(8)
+        cnt = np.zeros(8, dtype=np.int64)
+        self._raise(self.lib.etdm_stage_times(self.h, _dptr(ms),
+                                              cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return (dict(zip(STAGES, ms[:len(STAGES)].tolist())),
+                dict(zip(STAGES, cnt[:len(STAGES)].tolist())), int(cnt[-1]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.etdm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def energy_function():
+    """torch.autograd.Function E(A_ov): forward evaluates the energy only;
+    backward re-runs the density (no grid is stored between the two) and the
+    analytic adjoint, and scales dE/dA_ov by grad_output."""
+    import torch
+
+    class ETDMEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a, solver):
+            E, _ = solver.energy_grad(a.contiguous(), want_grad=False)
+            ctx.solver = solver
+            ctx.save_for_backward(a)
+            return E[0].clone()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (a,) = ctx.saved_tensors
+            _, g = ctx.solver.energy_grad(a.contiguous(), want_grad=True)
+            return grad_out * g, None
+
+    return ETDMEnergy

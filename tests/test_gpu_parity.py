@@ -1,0 +1,248 @@
+"""GPU path (through the C ABI) against the FP64 oracle.
+
+Bars: truncation lists bit-exact; energy within 1e-6 Ha; gradient within
+1e-5 of max|g| (max-abs); intermediate FP64 arrays within the tolerances
+their arithmetic allows.
+"""
+import numpy as np
+import pytest
+
+import etdm_synth as synth
+from oracle.etdm_oracle import LBFGS, Oracle, minimize
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-6
+G_TOL = 1e-5
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+def _solver(d, precision="fp64"):
+    _torch()
+    from paper_2101_12597_gb300.etdm import ETDM
+    return ETDM(d, precision=precision)
+
+
+@pytest.fixture(scope="module")
+def small():
+    d = synth.config_small_molecule()
+    return d, Oracle(d), _solver(d)
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    d = synth.ragged_water()
+    return d, Oracle(d), _solver(d)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    d = synth.tiny()
+    return d, Oracle(d), _solver(d)
+
+
+def _grad_err(g, gref):
+    return float(np.abs(g - gref).max() / max(np.abs(gref).max(), 1e-300))
+
+
+# ---- set-up: lists, S, T, C0, v_ext ------------------------------------------
+
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+def test_truncation_lists_bit_exact(which, tiny, small, ragged):
+    d, o, s = dict(tiny=tiny, small=small, ragged=ragged)[which]
+    ptr = s.get_array("tile_ptr")
+    keys = s.get_array("tile_keys")
+    tile = (s.dims["tx"], s.dims["ty"], s.dims["tz"])
+    nt = o.n_tiles(tile)
+    assert len(ptr) == nt + 1
+    for t in range(nt):
+        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list(tile, t))
+
+
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+def test_overlap_kinetic_reference_vext(which, tiny, small, ragged):
+    d, o, s = dict(tiny=tiny, small=small, ragged=ragged)[which]
+    ref = o.reference()
+    M = o.M
+    np.testing.assert_allclose(s.get_array("S").reshape(M, M), ref["S"], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s.get_array("T").reshape(M, M), ref["T"], rtol=0, atol=1e-12)
+    assert s.get_array("order").tolist() == ref["order"].tolist()
+    np.testing.assert_allclose(s.get_array("C0").reshape(M, M), ref["C0"], rtol=0, atol=1e-10)
+    vext = s.get_array("vext").reshape(tuple(o.n))
+    np.testing.assert_allclose(vext, ref["vext"], rtol=0, atol=1e-11 * np.abs(ref["vext"]).max())
+
+
+# ---- one evaluation ----------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+def test_energy_gradient_parity(which, tiny, small, ragged):
+    torch = _torch()
+    d, o, s = dict(tiny=tiny, small=small, ragged=ragged)[which]
+    a = d["a0"]
+    E_ref, g_ref, ex = o.energy_grad(a, want=True)
+    at = torch.tensor(a, device="cuda")
+    E, g = s.energy_grad(at)
+    torch.cuda.synchronize()
+    s.check()
+    E = float(E.item())
+    g = g.cpu().numpy()
+    assert abs(E - E_ref) < E_TOL
+    assert _grad_err(g, g_ref) <= G_TOL
+    # the FP64 path is much tighter than the bar
+    assert abs(E - E_ref) < 1e-10 * max(1.0, abs(E_ref))
+    assert _grad_err(g, g_ref) < 1e-9
+    M = o.M
+    np.testing.assert_allclose(s.get_array("D").reshape(M, M), ex["D"], atol=1e-11)
+    rho = s.get_array("rho").reshape(tuple(o.n))
+    np.testing.assert_allclose(rho, ex["rho"], atol=1e-12 * ex["rho"].max())
+    np.testing.assert_allclose(s.get_array("H").reshape(M, M), ex["H"], atol=1e-10)
+    terms = s.get_array("eterms")
+    ref_terms = [ex["terms"][k] for k in ("kinetic", "external", "hartree", "exchange")]
+    np.testing.assert_allclose(terms, ref_terms, atol=1e-10)
+
+
+def test_energy_only_matches_and_host_api(small):
+    torch = _torch()
+    d, o, s = small
+    E_ref, g_ref = o.energy_grad(d["a0"])
+    at = torch.tensor(d["a0"], device="cuda")
+    E, g = s.energy_grad(at, want_grad=False)
+    assert g is None
+    assert abs(float(E.item()) - E_ref) < E_TOL
+    Eh, gh = s.energy_grad_host(d["a0"])
+    assert abs(Eh - E_ref) < E_TOL and _grad_err(gh, g_ref) <= G_TOL
+
+
+def test_large_rotation_exercises_doubling(small):
+    # |A_ov A_ov^T|_F > 1 forces the scaling-and-doubling branch of exp(A)
+    torch = _torch()
+    d, o, s = small
+    a = synth.direction(d["a0"].shape, seed=21, scale=0.9)
+    E_ref, g_ref = o.energy_grad(a)
+    E, g = s.energy_grad(torch.tensor(a, device="cuda"))
+    torch.cuda.synchronize()
+    s.check()
+    assert abs(float(E.item()) - E_ref) < 1e-9
+    assert _grad_err(g.cpu().numpy(), g_ref) < 1e-8
+    U = s.get_array("Uocc").reshape(o.M, o.N)
+    Uref = o.expm_eig(o.full_A(a)).real[:, : o.N]
+    np.testing.assert_allclose(U, Uref, atol=1e-12)
+
+
+def test_rotation_beyond_range_reports_numeric(small):
+    torch = _torch()
+    from paper_2101_12597_gb300.etdm import EtdmError
+    d, o, s = small
+    a = np.full(d["a0"].shape, 60.0)
+    s.energy_grad(torch.tensor(a, device="cuda"))
+    with pytest.raises(EtdmError) as ei:
+        s.check()
+    assert ei.value.code == -7
+    # the handle stays usable
+    E, _ = s.energy_grad(torch.tensor(d["a0"], device="cuda"))
+    s.check()
+
+
+# ---- preconditioner and L-BFGS ---------------------------------------------------
+
+def test_orbital_energies_and_precondition(small):
+    torch = _torch()
+    d, o, s = small
+    eps_ref = o.orbital_energies()
+    eps = s.get_array("eps")
+    np.testing.assert_allclose(eps, eps_ref, atol=1e-10)
+    s.lbfgs_reset()
+    g = synth.direction(d["a0"].shape, seed=5)
+    beta = float(s.get_array("beta")[0])
+    pg = s.precondition(torch.tensor(g, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(pg, o.precond(eps_ref, beta) * g, rtol=1e-12)
+
+
+def test_lbfgs_two_loop_parity(small):
+    torch = _torch()
+    d, o, s = small
+    s.lbfgs_reset()
+    eps = s.get_array("eps")
+    ref = LBFGS(lambda beta: o.precond(eps, beta), beta0=float(s.get_array("beta")[0]))
+    rng = np.random.default_rng(3)
+    Q = rng.normal(size=(48, 48)); A = Q @ Q.T + 48 * np.eye(48)
+    x = rng.normal(size=48)
+    for k in range(7):
+        gk = (A @ x).reshape(4, 12)
+        xk = x.reshape(4, 12)
+        p_ref = ref.step(xk, gk)
+        p = s.lbfgs_step(torch.tensor(xk, device="cuda"), torch.tensor(gk, device="cuda"))
+        p = p.cpu().numpy()
+        np.testing.assert_allclose(p, p_ref, rtol=1e-11, atol=1e-13)
+        assert abs(float(s.get_array("beta")[0]) - ref.beta) < 1e-12 * ref.beta
+        x = x + 0.7 * p.ravel()
+    s.lbfgs_reset()
+
+
+def test_minimization_trajectory_parity(small):
+    torch = _torch()
+    d, o, s = small
+    s.lbfgs_reset()
+    hist, a_ref = minimize(o, d["a0"], n_steps=20)
+    a = torch.tensor(d["a0"], device="cuda")
+    E, al, tr = s.minimize(a, 20)
+    for k in range(21):
+        assert abs(E[k] - hist[k][0]) < E_TOL, (k, E[k], hist[k][0])
+        assert al[k] == pytest.approx(hist[k][1], abs=1e-12)
+        assert tr[k] == hist[k][2]
+    np.testing.assert_allclose(a.cpu().numpy(), a_ref, atol=1e-8)
+    s.lbfgs_reset()
+
+
+def test_autograd_function(small):
+    torch = _torch()
+    from paper_2101_12597_gb300.etdm import energy_function
+    d, o, s = small
+    F = energy_function()
+    a = torch.tensor(d["a0"], device="cuda", requires_grad=True)
+    E = F.apply(a, s)
+    (3.0 * E).backward()
+    E_ref, g_ref = o.energy_grad(d["a0"])
+    assert abs(float(E.item()) - E_ref) < E_TOL
+    assert _grad_err(a.grad.cpu().numpy() / 3.0, g_ref) <= G_TOL
+    # central differences through the same Function
+    h = 1e-5
+    for (i, j) in [(0, 0), (2, 7), (3, 11)]:
+        ap = d["a0"].copy(); ap[i, j] += h
+        am = d["a0"].copy(); am[i, j] -= h
+        Ep = float(F.apply(torch.tensor(ap, device="cuda"), s).item())
+        Em = float(F.apply(torch.tensor(am, device="cuda"), s).item())
+        fd = (Ep - Em) / (2 * h)
+        assert abs(fd - g_ref[i, j]) <= max(1e-6, 1e-5 * abs(g_ref[i, j]))
+
+
+# ---- full-size workload: 96-atom water box, 96^3 grid ------------------------------
+
+@pytest.fixture(scope="module")
+def water32():
+    d = synth.config_water32()
+    return d, Oracle(d), _solver(d)
+
+
+def test_water32_full_size_parity(water32):
+    torch = _torch()
+    d, o, s = water32
+    E_ref, g_ref = o.energy_grad(d["a0"])
+    E, g = s.energy_grad(torch.tensor(d["a0"], device="cuda"))
+    torch.cuda.synchronize()
+    s.check()
+    assert abs(float(E.item()) - E_ref) < E_TOL
+    assert _grad_err(g.cpu().numpy(), g_ref) <= G_TOL
+    # sampled tiles of the truncation lists, bit-exact
+    ptr = s.get_array("tile_ptr")
+    keys = s.get_array("tile_keys")
+    tile = (s.dims["tx"], s.dims["ty"], s.dims["tz"])
+    nt = o.n_tiles(tile)
+    for t in list(range(0, nt, nt // 11)) + [nt - 1]:
+        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list(tile, t))
