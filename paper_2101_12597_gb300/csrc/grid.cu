@@ -267,17 +267,22 @@ __global__ void overlap_kinetic_kernel(const double *center, const double *alpha
     double a = alpha[mu], b = alpha[nu];
     double xi = a * b / (a + b);
     double pre = pow(2.0 * sqrt(a * b) / (a + b), 1.5);
-    double cut = rcut[mu] + rcut[nu];
-    double cut2 = cut * cut;
-    double d0 = center[mu * 3] - center[nu * 3];
-    double d1 = center[mu * 3 + 1] - center[nu * 3 + 1];
-    double d2 = center[mu * 3 + 2] - center[nu * 3 + 2];
+    // pair images with |d_mu - d_nu - R| < r_c,mu + r_c,nu; the inclusion test
+    // uses a fixed operation order without contraction (boundary pairs exist)
+    double cut = __dadd_rn(rcut[mu], rcut[nu]);
+    double cut2 = __dmul_rn(cut, cut);
+    double d0 = __dsub_rn(center[mu * 3], center[nu * 3]);
+    double d1 = __dsub_rn(center[mu * 3 + 1], center[nu * 3 + 1]);
+    double d2 = __dsub_rn(center[mu * 3 + 2], center[nu * 3 + 2]);
     double s = 0.0, t = 0.0;
     for (int ix = -kImgMax; ix <= kImgMax; ++ix)
       for (int iy = -kImgMax; iy <= kImgMax; ++iy)
         for (int iz = -kImgMax; iz <= kImgMax; ++iz) {
-          double r0 = d0 - ix * L0, r1 = d1 - iy * L1, r2 = d2 - iz * L2;
-          double R2 = r0 * r0 + r1 * r1 + r2 * r2;
+          double r0 = __dsub_rn(d0, __dmul_rn((double)ix, L0));
+          double r1 = __dsub_rn(d1, __dmul_rn((double)iy, L1));
+          double r2 = __dsub_rn(d2, __dmul_rn((double)iz, L2));
+          double R2 = __dadd_rn(__dadd_rn(__dmul_rn(r0, r0), __dmul_rn(r1, r1)),
+                                __dmul_rn(r2, r2));
           if (R2 < cut2) {
             double v = pre * exp(-xi * R2);
             s += v;
