@@ -160,7 +160,9 @@ enum {
   ETDM_ARR_EPS = 12,     /* [M] f64 orbital energies of Eq. 33 */
   ETDM_ARR_ETERMS = 13,  /* [4] f64 kinetic, external, Hartree, exchange */
   ETDM_ARR_BETA = 14,    /* [1] f64 current beta^(k) */
-  ETDM_NARR = 15
+  ETDM_ARR_TILE_PTR_TC = 15,  /* mixed precision: 4x4x8-tile list offsets (i32) */
+  ETDM_ARR_TILE_KEYS_TC = 16, /* mixed precision: 4x4x8-tile list keys (i32) */
+  ETDM_NARR = 17
 };
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);
 int etdm_get_array(etdm_handle *h, int32_t which, void *host_dst,

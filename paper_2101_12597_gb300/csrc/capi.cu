@@ -109,9 +109,16 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
     CUDA_TRY(launch_dense_forward(h, a, s));
     t.done();
   }
+  const bool mixed = h->precision == ETDM_PREC_MIXED && !h->in_setup;
   {
     StageTimer t(h, s, ETDM_STAGE_RHO);
-    CUDA_TRY(launch_rho_fp64(h, h->d_D, h->d_rho, s));
+    if (mixed) {
+      CUDA_TRY(launch_dslice(h, s));
+      CUDA_TRY(launch_rho_tc(h, s));
+      h->launches += 1;
+    } else {
+      CUDA_TRY(launch_rho_fp64(h, h->d_D, h->d_rho, s));
+    }
     t.done();
   }
   {
@@ -123,8 +130,13 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
     CUDA_TRY(launch_potential(h, s));
     t.done();
   }
-  h->launches += 11;
-  if (g) {
+  h->launches += 12;  // dense forward/reverse, density, pack, 2 x 3 FFT passes, scale, potential
+  if (mixed) {  // also needed for the energy: first-order correction of D's quantization
+    StageTimer t(h, s, ETDM_STAGE_VMAT);
+    CUDA_TRY(launch_vmat_tc(h, s));
+    t.done();
+    h->launches += 1;
+  } else if (g) {
     StageTimer t(h, s, ETDM_STAGE_VMAT);
     CUDA_TRY(launch_vmat_fp64(h, h->d_vtot, h->d_H, s));
     t.done();
@@ -251,6 +263,53 @@ __global__ void symmetrize_upper_kernel(double *H, int M) {
   }
 }
 
+GridGeom make_geom(etdm_handle *h, int tx, int ty, int tz, int *n_tiles) {
+  GridGeom g{};
+  g.nx = h->n[0]; g.ny = h->n[1]; g.nz = h->n[2];
+  g.tx = tx; g.ty = ty; g.tz = tz;
+  g.nbx = (g.nx + tx - 1) / tx;
+  g.nby = (g.ny + ty - 1) / ty;
+  g.nbz = (g.nz + tz - 1) / tz;
+  g.M = h->M;
+  g.dV = h->dV;
+  *n_tiles = g.nbx * g.nby * g.nbz;
+  return g;
+}
+
+// Truncation lists of one tile geometry: count per (tile, mu), exclusive scan,
+// fill in (tile, mu, image) order (sorted keys within a tile).
+void build_lists(etdm_handle *h, const GridGeom &g, int n_tiles, int **d_ptr, int **d_keys,
+                 long *n_entries, int *max_list, int limit, cudaStream_t s) {
+  const int M = h->M;
+  const long ncnt = (long)n_tiles * M;
+  int *d_count = dalloc<int>(h, ncnt);
+  long long *d_off = dalloc<long long>(h, ncnt);
+  long long *d_tmp = dalloc<long long>(h, ncnt / 1024 + 4);
+  CUDA_TRY(launch_list_count(h, g, n_tiles, d_count, s));
+  CUDA_TRY(launch_scan(d_count, d_off, ncnt, d_tmp, s));
+  long nb = (ncnt + 1023) / 1024;
+  if (nb < 1) nb = 1;
+  long long total = 0;
+  CUDA_TRY(cudaMemcpy(&total, d_tmp + nb, sizeof(long long), cudaMemcpyDeviceToHost));
+  if (total > 2000000000LL) throw Fail{ETDM_ERR_INVALID_ARG, "truncation lists too long"};
+  *n_entries = (long)total;
+  *d_keys = dalloc<int>(h, total);
+  *d_ptr = dalloc<int>(h, n_tiles + 1);
+  CUDA_TRY(launch_list_fill(h, g, n_tiles, d_off, *d_keys, s));
+  extract_ptr_kernel<<<(n_tiles + 256) / 256, 256, 0, s>>>(d_off, total, M, n_tiles, *d_ptr);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<int> ptr(n_tiles + 1);
+  CUDA_TRY(cudaMemcpy(ptr.data(), *d_ptr, (n_tiles + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  *max_list = 0;
+  for (int t = 0; t < n_tiles; ++t) *max_list = std::max(*max_list, ptr[t + 1] - ptr[t]);
+  if (*max_list > limit)
+    throw Fail{ETDM_ERR_INVALID_ARG,
+               "a " + std::to_string(g.tx) + "x" + std::to_string(g.ty) + "x" +
+                   std::to_string(g.tz) + " grid tile touches " + std::to_string(*max_list) +
+                   " function images (limit " + std::to_string(limit) +
+                   "): use a finer grid or shorter truncation radii"};
+}
+
 void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) {
   validate(sys, opt);
   etdm_options o;
@@ -321,44 +380,27 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   h->d_ex = dalloc<double>(h, tab);
   CUDA_TRY(launch_tables(h, s));
 
-  // tiles and truncation lists
-  GridGeom &g = h->geom;
-  g.nx = h->n[0]; g.ny = h->n[1]; g.nz = h->n[2];
-  g.tx = g.ty = g.tz = 4;
-  g.nbx = (g.nx + g.tx - 1) / g.tx;
-  g.nby = (g.ny + g.ty - 1) / g.ty;
-  g.nbz = (g.nz + g.tz - 1) / g.tz;
-  g.M = M;
-  g.dV = h->dV;
-  h->n_tiles = g.nbx * g.nby * g.nbz;
-  const long ncnt = (long)h->n_tiles * M;
-  int *d_count = dalloc<int>(h, ncnt);
-  long long *d_off = dalloc<long long>(h, ncnt);
-  long long *d_tmp = dalloc<long long>(h, ncnt / 1024 + 4);
-  CUDA_TRY(launch_list_count(h, d_count, s));
-  CUDA_TRY(launch_scan(d_count, d_off, ncnt, d_tmp, s));
-  long nb = (ncnt + 1023) / 1024;
-  if (nb < 1) nb = 1;
-  long long total = 0;
-  CUDA_TRY(cudaMemcpy(&total, d_tmp + nb, sizeof(long long), cudaMemcpyDeviceToHost));
-  if (total > 2000000000LL) throw Fail{ETDM_ERR_INVALID_ARG, "truncation lists too long"};
-  h->n_entries = (long)total;
-  h->d_keys = dalloc<int>(h, total);
-  h->d_tile_ptr = dalloc<int>(h, h->n_tiles + 1);
-  CUDA_TRY(launch_list_fill(h, d_off, s));
-  extract_ptr_kernel<<<(h->n_tiles + 256) / 256, 256, 0, s>>>(d_off, total, M, h->n_tiles,
-                                                               h->d_tile_ptr);
-  CUDA_TRY(cudaGetLastError());
-  std::vector<int> ptr(h->n_tiles + 1);
-  CUDA_TRY(cudaMemcpy(ptr.data(), h->d_tile_ptr, (h->n_tiles + 1) * sizeof(int),
-                      cudaMemcpyDeviceToHost));
-  h->max_list = 0;
-  for (int t = 0; t < h->n_tiles; ++t) h->max_list = std::max(h->max_list, ptr[t + 1] - ptr[t]);
-  if (h->max_list > kMaxList)
-    throw Fail{ETDM_ERR_INVALID_ARG,
-               "a grid tile touches " + std::to_string(h->max_list) +
-                   " function images (limit " + std::to_string(kMaxList) +
-                   "): use a finer grid or shorter truncation radii"};
+  // tiles and truncation lists (4^3 tiles for the FP64 passes)
+  h->geom = make_geom(h, 4, 4, 4, &h->n_tiles);
+  build_lists(h, h->geom, h->n_tiles, &h->d_tile_ptr, &h->d_keys, &h->n_entries, &h->max_list,
+              kMaxList, s);
+  if (h->precision == ETDM_PREC_MIXED) {  // 4 x 4 x 8 tiles for the tensor-core passes
+    h->geom_tc = make_geom(h, 4, 4, 8, &h->n_tiles_tc);
+    build_lists(h, h->geom_tc, h->n_tiles_tc, &h->d_tile_ptr_tc, &h->d_keys_tc,
+                &h->n_entries_tc, &h->max_list_tc, tc_max_list(), s);
+    h->d_tabf = dalloc<float2>(h, tab);
+    CUDA_TRY(launch_tables_f32(h, s));
+    std::vector<float> rc2f(M);
+    for (int m = 0; m < M; ++m) rc2f[m] = (float)rc2[m];
+    h->d_rc2f = dalloc<float>(h, M);
+    CUDA_TRY(cudaMemcpy(h->d_rc2f, rc2f.data(), M * sizeof(float), cudaMemcpyHostToDevice));
+    h->d_rowexp = dalloc<signed char>(h, h->G);
+    CUDA_TRY(launch_rowexp(h, s));
+    h->d_J = dalloc<uint32_t>(h, (long)M * M);
+    h->d_fscale = dalloc<float>(h, M);
+    h->d_dD = dalloc<double>(h, (long)M * M);
+    h->d_Vacc = dalloc<float>(h, (long)M * M);
+  }
   {
     unsigned long long *d_sum = dalloc<unsigned long long>(h, 1);
     CUDA_TRY(launch_npt2(h, d_sum, s));
@@ -461,7 +503,9 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
 
   // orbital energies of Eq. 33 at A = 0
   CUDA_TRY(cudaMemsetAsync(h->d_a, 0, nvar * 8, s));
+  h->in_setup = true;
   evaluate(h, h->d_a, h->d_E, h->d_g, s);
+  h->in_setup = false;
   check_flags(h, s);
   CUDA_TRY(launch_diag_quad(h->d_C0, h->d_H, h->d_eps, M, s));
   std::vector<double> st(4 + 32, 0.0);
@@ -736,6 +780,8 @@ int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
     case ETDM_ARR_EPS: return M * 8;
     case ETDM_ARR_ETERMS: return 32;
     case ETDM_ARR_BETA: return 8;
+    case ETDM_ARR_TILE_PTR_TC: return h->d_tile_ptr_tc ? ((int64_t)h->n_tiles_tc + 1) * 4 : 0;
+    case ETDM_ARR_TILE_KEYS_TC: return h->d_keys_tc ? (int64_t)h->n_entries_tc * 4 : 0;
     default: return -1;
   }
 }
@@ -765,6 +811,8 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_EPS: src = h->d_eps; break;
       case ETDM_ARR_ETERMS: src = h->d_eterms; break;
       case ETDM_ARR_BETA: src = h->d_lbstate + 3; break;
+      case ETDM_ARR_TILE_PTR_TC: src = h->d_tile_ptr_tc; break;
+      case ETDM_ARR_TILE_KEYS_TC: src = h->d_keys_tc; break;
     }
     if (want > 0) CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
   } catch (const Fail &f) {

@@ -217,21 +217,34 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long gstride = (long)gridDim.x * blockDim.x;
   {
-    double s = 0.0;
+    double s = 0.0, corr = 0.0;
     for (long e = gtid; e < MM; e += gstride) s += a.D[e] * a.T[e];
-    s = block_sum(s);
-    if (threadIdx.x == 0) a.red[blockIdx.x] = s;
-    if (want_grad) {  // the grid pass accumulated the upper triangle of H
+    if (a.Vacc) {  // mixed path: H = T + V (upper-triangle FP32 accumulation);
+                   // first-order correction of the D quantization: Tr(V (D - Dq))
+      for (long e = gtid; e < MM; e += gstride) {
+        int i = (int)(e / M), c = (int)(e % M);
+        double v = (double)(i <= c ? a.Vacc[e] : a.Vacc[(long)c * M + i]);
+        a.H[e] = a.T[e] + v;
+        corr += v * a.dD[e];
+      }
+    } else if (want_grad) {  // the grid pass accumulated the upper triangle of H
       for (long e = gtid; e < MM; e += gstride) {
         int i = (int)(e / M), c = (int)(e % M);
         if (i > c) a.H[e] = a.H[(long)c * M + i];
       }
     }
+    s = block_sum(s);
+    corr = block_sum(corr);
+    if (threadIdx.x == 0) {
+      a.red[blockIdx.x] = s;
+      a.red[gridDim.x + blockIdx.x] = corr;
+    }
   }
   BARRIER_OR_RETURN();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double kin = 0.0;
+    double kin = 0.0, corr = 0.0;
     for (int b = 0; b < (int)gridDim.x; ++b) kin += a.red[b];
+    for (int b = 0; b < (int)gridDim.x; ++b) corr += a.red[gridDim.x + b];
     double t3[3] = {0.0, 0.0, 0.0}, c3[3] = {0.0, 0.0, 0.0};
     for (int b = 0; b < a.n_gridpart; ++b) {  // compensated sums
       for (int q = 0; q < 3; ++q) {
@@ -241,8 +254,8 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
         t3[q] = tt;
       }
     }
-    double E = kin + t3[0] + t3[1] + t3[2];
-    a.eterms[0] = kin; a.eterms[1] = t3[0]; a.eterms[2] = t3[1]; a.eterms[3] = t3[2];
+    double E = kin + t3[0] + t3[1] + t3[2] + corr;
+    a.eterms[0] = kin; a.eterms[1] = t3[0]; a.eterms[2] = t3[1]; a.eterms[3] = t3[2] + corr;
     if (a.E) *a.E = E;
     if (!(E == E) || isinf(E)) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
   }
@@ -538,6 +551,7 @@ static DenseArgs dense_args(etdm_handle *h, const double *a) {
   d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym;
   d.eterms = h->d_eterms;
   d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
+  if (h->precision == ETDM_PREC_MIXED && !h->in_setup) { d.Vacc = h->d_Vacc; d.dD = h->d_dD; }
   d.red = h->d_red; d.flags = h->d_flags; d.bar = h->d_bar; d.scal = h->d_scal;
   // c_k = (-1)^k/(2k)!, s_k = (-1)^k/(2k+1)!
   double f = 1.0;

@@ -124,23 +124,25 @@ __global__ void list_fill_kernel(GridGeom g, const double *sqx, const double *sq
   }
 }
 
-cudaError_t launch_list_count(etdm_handle *h, int *d_count, cudaStream_t s) {
-  long total = (long)h->n_tiles * h->M;
+cudaError_t launch_list_count(etdm_handle *h, const GridGeom &g, int n_tiles, int *d_count,
+                              cudaStream_t s) {
+  long total = (long)n_tiles * h->M;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 8192) blocks = 8192;
   list_count_kernel<<<blocks, 256, 0, s>>>(
-      h->geom, h->d_sq + h->tab_off[0], h->d_sq + h->tab_off[1], h->d_sq + h->tab_off[2],
-      h->d_rcut, h->d_rc2, h->L[0], h->L[1], h->L[2], h->n_tiles, d_count);
+      g, h->d_sq + h->tab_off[0], h->d_sq + h->tab_off[1], h->d_sq + h->tab_off[2],
+      h->d_rcut, h->d_rc2, h->L[0], h->L[1], h->L[2], n_tiles, d_count);
   return cudaGetLastError();
 }
 
-cudaError_t launch_list_fill(etdm_handle *h, const long long *d_off, cudaStream_t s) {
-  long total = (long)h->n_tiles * h->M;
+cudaError_t launch_list_fill(etdm_handle *h, const GridGeom &g, int n_tiles, const long long *d_off,
+                             int *d_keys, cudaStream_t s) {
+  long total = (long)n_tiles * h->M;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 8192) blocks = 8192;
   list_fill_kernel<<<blocks, 256, 0, s>>>(
-      h->geom, h->d_sq + h->tab_off[0], h->d_sq + h->tab_off[1], h->d_sq + h->tab_off[2],
-      h->d_rcut, h->d_rc2, h->L[0], h->L[1], h->L[2], h->n_tiles, d_off, h->d_keys);
+      g, h->d_sq + h->tab_off[0], h->d_sq + h->tab_off[1], h->d_sq + h->tab_off[2],
+      h->d_rcut, h->d_rc2, h->L[0], h->L[1], h->L[2], n_tiles, d_off, d_keys);
   return cudaGetLastError();
 }
 

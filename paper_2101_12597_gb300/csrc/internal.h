@@ -83,6 +83,8 @@ struct DenseArgs {
   double *E;             // scalar output (may be null)
   double *eterms;        // [4] kinetic, external, hartree, exchange
   const double *gridpart;  // [n_gridpart][3] energy partials of the grid
+  const float *Vacc;     // mixed path: upper-triangle V (FP32), else null
+  const double *dD;      // mixed path: D - Dq for the first-order energy correction
   int n_gridpart;
   double *red;           // reduction scratch [gridDim][2]
   int *flags;
@@ -111,6 +113,7 @@ struct LbfgsArgs {
 struct etdm_handle {
   int device = 0;
   int precision = ETDM_PREC_FP64;
+  bool in_setup = false;  // set-up evaluations use the FP64 passes
   int lbfgs_m = 3;
   double gamma = 0.25, beta0 = 1.0;
   int M = 0, N = 0, V = 0, n_atoms = 0;
@@ -134,6 +137,18 @@ struct etdm_handle {
   double *d_sq = nullptr, *d_ex = nullptr;
   long tab_off[3] = {0, 0, 0};
   int *d_tile_ptr = nullptr, *d_keys = nullptr;
+  // mixed-precision grid passes: 4 x 4 x 8 tiles and their lists
+  etdm::GridGeom geom_tc{};
+  int n_tiles_tc = 0, max_list_tc = 0;
+  long n_entries_tc = 0;
+  int *d_tile_ptr_tc = nullptr, *d_keys_tc = nullptr;
+  float2 *d_tabf = nullptr;
+  float *d_rc2f = nullptr;
+  signed char *d_rowexp = nullptr;
+  uint32_t *d_J = nullptr;
+  float *d_fscale = nullptr;
+  double *d_dD = nullptr;
+  float *d_Vacc = nullptr;
   // matrices
   double *d_S = nullptr, *d_T = nullptr, *d_C0 = nullptr;
   double *d_D = nullptr, *d_H = nullptr, *d_Uocc = nullptr, *d_O = nullptr;
@@ -174,8 +189,10 @@ namespace etdm {
 // ---- launch wrappers (return cudaError_t of the launch) --------------------
 // grid basis and lists (grid.cu)
 cudaError_t launch_tables(etdm_handle *h, cudaStream_t s);
-cudaError_t launch_list_count(etdm_handle *h, int *d_count, cudaStream_t s);
-cudaError_t launch_list_fill(etdm_handle *h, const long long *d_off, cudaStream_t s);
+cudaError_t launch_list_count(etdm_handle *h, const GridGeom &g, int n_tiles, int *d_count,
+                              cudaStream_t s);
+cudaError_t launch_list_fill(etdm_handle *h, const GridGeom &g, int n_tiles, const long long *d_off,
+                             int *d_keys, cudaStream_t s);
 cudaError_t launch_scan(const int *d_in, long long *d_out, long n, long long *d_tmp,
                         cudaStream_t s);
 cudaError_t launch_npt2(etdm_handle *h, unsigned long long *d_sum, cudaStream_t s);
@@ -211,6 +228,13 @@ cudaError_t launch_ns_prep(const double *S, double *Y, double *Zm, double c, int
 cudaError_t launch_resid(const double *ZY, double *out, int M, cudaStream_t s);
 cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n, cudaStream_t s);
 cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t s);
+// mixed-precision grid passes (mixed.cu)
+cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_rowexp(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_dslice(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);
+int tc_max_list();
 int occupancy_dense(int *blocks_per_sm);
 int occupancy_lbfgs(int *blocks_per_sm);
 

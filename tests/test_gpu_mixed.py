@@ -1,0 +1,118 @@
+"""Mixed-precision path (tensor-core grid passes) against the FP64 oracle.
+
+Bars: truncation lists of the 4x4x8 tiles bit-exact; energy within 1e-6 Ha;
+gradient within 1e-5 of max|g| (max-abs); the minimization trajectory of the
+8-atom system identical in accepted steps and within 1e-6 Ha per step.
+"""
+import numpy as np
+import pytest
+
+import etdm_synth as synth
+from oracle.etdm_oracle import Oracle, minimize
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-6
+G_TOL = 1e-5
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+def _solver(d):
+    _torch()
+    from paper_2101_12597_gb300.etdm import ETDM
+    return ETDM(d, precision="mixed")
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for name, fn in [("tiny", synth.tiny), ("small", synth.config_small_molecule),
+                     ("ragged", synth.ragged_water)]:
+        d = fn()
+        out[name] = (d, Oracle(d), _solver(d))
+    return out
+
+
+def _grad_err(g, gref):
+    return float(np.abs(g - gref).max() / max(np.abs(gref).max(), 1e-300))
+
+
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+def test_tc_truncation_lists_bit_exact(which, cases):
+    d, o, s = cases[which]
+    ptr = s.get_array("tile_ptr_tc")
+    keys = s.get_array("tile_keys_tc")
+    tile = (4, 4, 8)
+    nt = o.n_tiles(tile)
+    assert len(ptr) == nt + 1
+    for t in range(nt):
+        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list(tile, t))
+
+
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+def test_mixed_energy_gradient_parity(which, cases):
+    torch = _torch()
+    d, o, s = cases[which]
+    for a in (d["a0"], synth.direction(d["a0"].shape, seed=31, scale=0.3)):
+        E_ref, g_ref, ex = o.energy_grad(a, want=True)
+        E, g = s.energy_grad(torch.tensor(a, device="cuda"))
+        torch.cuda.synchronize()
+        s.check()
+        dE = abs(float(E.item()) - E_ref)
+        dg = _grad_err(g.cpu().numpy(), g_ref)
+        print(f"{which}: |dE|={dE:.3e} Ha  grad err={dg:.3e}")
+        assert dE < E_TOL
+        assert dg <= G_TOL
+        rho = s.get_array("rho").reshape(tuple(o.n))
+        assert np.abs(rho - ex["rho"]).max() < 1e-5 * ex["rho"].max()
+
+
+def test_mixed_energy_only_call(cases):
+    torch = _torch()
+    d, o, s = cases["small"]
+    E_ref, _ = o.energy_grad(d["a0"])
+    E, g = s.energy_grad(torch.tensor(d["a0"], device="cuda"), want_grad=False)
+    s.check()
+    assert g is None and abs(float(E.item()) - E_ref) < E_TOL
+
+
+def test_mixed_minimization_trajectory(cases):
+    torch = _torch()
+    d, o, s = cases["small"]
+    s.lbfgs_reset()
+    hist, a_ref = minimize(o, d["a0"], n_steps=20)
+    a = torch.tensor(d["a0"], device="cuda")
+    E, al, tr = s.minimize(a, 20)
+    for k in range(21):
+        assert abs(E[k] - hist[k][0]) < E_TOL, (k, E[k], hist[k][0])
+        assert tr[k] == hist[k][2]
+        assert al[k] == pytest.approx(hist[k][1], abs=1e-9)
+    s.lbfgs_reset()
+
+
+def test_water32_mixed_full_size(cases):
+    torch = _torch()
+    d = synth.config_water32()
+    o = Oracle(d)
+    s = _solver(d)
+    E_ref, g_ref = o.energy_grad(d["a0"])
+    E, g = s.energy_grad(torch.tensor(d["a0"], device="cuda"))
+    torch.cuda.synchronize()
+    s.check()
+    dE = abs(float(E.item()) - E_ref)
+    dg = _grad_err(g.cpu().numpy(), g_ref)
+    print(f"water32 mixed: |dE|={dE:.3e} Ha  grad err={dg:.3e}")
+    assert dE < E_TOL
+    assert dg <= G_TOL
+    ptr = s.get_array("tile_ptr_tc")
+    keys = s.get_array("tile_keys_tc")
+    nt = o.n_tiles((4, 4, 8))
+    for t in list(range(0, nt, nt // 9)) + [nt - 1]:
+        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list((4, 4, 8), t))
+    s.close()
