@@ -113,7 +113,7 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
   {
     StageTimer t(h, s, ETDM_STAGE_RHO);
     if (mixed) {
-      CUDA_TRY(launch_dslice(h, s));
+      CUDA_TRY(launch_oslice(h, s));
       CUDA_TRY(launch_rho_tc(h, s));
       h->launches += 1;
     } else {
@@ -388,7 +388,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->geom_tc = make_geom(h, 4, 4, 8, &h->n_tiles_tc);
     build_lists(h, h->geom_tc, h->n_tiles_tc, &h->d_tile_ptr_tc, &h->d_keys_tc,
                 &h->n_entries_tc, &h->max_list_tc, tc_max_list(), s);
-    h->d_tabf = dalloc<float2>(h, tab);
+    h->d_tabf = dalloc<float4>(h, tab);
     CUDA_TRY(launch_tables_f32(h, s));
     std::vector<float> rc2f(M);
     for (int m = 0; m < M; ++m) rc2f[m] = (float)rc2[m];
@@ -396,10 +396,14 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     CUDA_TRY(cudaMemcpy(h->d_rc2f, rc2f.data(), M * sizeof(float), cudaMemcpyHostToDevice));
     h->d_rowexp = dalloc<signed char>(h, h->G);
     CUDA_TRY(launch_rowexp(h, s));
-    h->d_J = dalloc<uint32_t>(h, (long)M * M);
-    h->d_fscale = dalloc<float>(h, M);
-    h->d_dD = dalloc<double>(h, (long)M * M);
-    h->d_Vacc = dalloc<float>(h, (long)M * M);
+    h->d_Osl = dalloc<uint2>(h, (long)M * h->N);
+    h->d_oscale = dalloc<float>(h, h->N);
+    h->d_dO = dalloc<double>(h, (long)M * h->N);
+    // per-CTA copies of V for the grid -> basis pass: at most ~2 GB of them
+    const double per_copy = (double)M * M * sizeof(float2);
+    h->n_vcopies = (int)std::max(1.0, std::min((double)h->num_sms, 2.0e9 / per_copy));
+    h->d_Vpriv = dalloc<float2>(h, (long)h->n_vcopies * M * M);
+    h->d_Vfin = dalloc<double>(h, (long)M * M);
   }
   {
     unsigned long long *d_sum = dalloc<unsigned long long>(h, 1);

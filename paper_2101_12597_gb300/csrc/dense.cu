@@ -216,16 +216,14 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   const long NN = (long)N * N, MM = (long)M * M;
   const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long gstride = (long)gridDim.x * blockDim.x;
+  const bool mixed = a.Vacc != nullptr;
   {
-    double s = 0.0, corr = 0.0;
+    double s = 0.0;
     for (long e = gtid; e < MM; e += gstride) s += a.D[e] * a.T[e];
-    if (a.Vacc) {  // mixed path: H = T + V (upper-triangle FP32 accumulation);
-                   // first-order correction of the D quantization: Tr(V (D - Dq))
+    if (mixed) {  // H = T + V from the upper-triangle FP32 accumulation
       for (long e = gtid; e < MM; e += gstride) {
         int i = (int)(e / M), c = (int)(e % M);
-        double v = (double)(i <= c ? a.Vacc[e] : a.Vacc[(long)c * M + i]);
-        a.H[e] = a.T[e] + v;
-        corr += v * a.dD[e];
+        a.H[e] = a.T[e] + (double)(i <= c ? a.Vacc[e] : a.Vacc[(long)c * M + i]);
       }
     } else if (want_grad) {  // the grid pass accumulated the upper triangle of H
       for (long e = gtid; e < MM; e += gstride) {
@@ -234,17 +232,35 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
       }
     }
     s = block_sum(s);
-    corr = block_sum(corr);
-    if (threadIdx.x == 0) {
-      a.red[blockIdx.x] = s;
-      a.red[gridDim.x + blockIdx.x] = corr;
-    }
+    if (threadIdx.x == 0) a.red[blockIdx.x] = s;
   }
   BARRIER_OR_RETURN();
+  if (mixed || want_grad) {
+    Phase ph[2];
+    ph[0] = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
+    ph[0].np = 1; ph[0].p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
+    // mixed path: dE_pot/dO = 4 (H - T) O into Ubar (scratch until Ubar is formed);
+    // the kinetic energy is exact (FP64 D), only the grid energy saw Oq
+    ph[1] = mkphase(M, N, M, a.Ubar, N);
+    ph[1].np = 2;
+    ph[1].p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
+    ph[1].p[1] = mk(a.T, M, 0, a.O, N, 0, -4.0);
+    run_phases(ph, mixed ? 2 : 1);
+    BARRIER_OR_RETURN();
+  }
+  if (mixed) {  // first-order correction of the density's O quantization
+    double c = 0.0;
+    const long MN = (long)M * N;
+    for (long e = gtid; e < MN; e += gstride) c += a.Ubar[e] * a.dO[e];
+    c = block_sum(c);
+    if (threadIdx.x == 0) a.red[gridDim.x + blockIdx.x] = c;
+    BARRIER_OR_RETURN();
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double kin = 0.0, corr = 0.0;
     for (int b = 0; b < (int)gridDim.x; ++b) kin += a.red[b];
-    for (int b = 0; b < (int)gridDim.x; ++b) corr += a.red[gridDim.x + b];
+    if (mixed)
+      for (int b = 0; b < (int)gridDim.x; ++b) corr += a.red[gridDim.x + b];
     double t3[3] = {0.0, 0.0, 0.0}, c3[3] = {0.0, 0.0, 0.0};
     for (int b = 0; b < a.n_gridpart; ++b) {  // compensated sums
       for (int q = 0; q < 3; ++q) {
@@ -260,12 +276,6 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     if (!(E == E) || isinf(E)) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
   }
   if (!want_grad) return;
-  {
-    Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = 4 H O
-    ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    run_phases(&ph, 1);
-  }
-  BARRIER_OR_RETURN();
   {
     Phase ph = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
     ph.np = 1; ph.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
@@ -551,7 +561,7 @@ static DenseArgs dense_args(etdm_handle *h, const double *a) {
   d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym;
   d.eterms = h->d_eterms;
   d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
-  if (h->precision == ETDM_PREC_MIXED && !h->in_setup) { d.Vacc = h->d_Vacc; d.dD = h->d_dD; }
+  if (h->precision == ETDM_PREC_MIXED && !h->in_setup) { d.Vacc = h->d_Vfin; d.dO = h->d_dO; }
   d.red = h->d_red; d.flags = h->d_flags; d.bar = h->d_bar; d.scal = h->d_scal;
   // c_k = (-1)^k/(2k)!, s_k = (-1)^k/(2k+1)!
   double f = 1.0;

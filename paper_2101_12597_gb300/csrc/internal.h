@@ -83,8 +83,8 @@ struct DenseArgs {
   double *E;             // scalar output (may be null)
   double *eterms;        // [4] kinetic, external, hartree, exchange
   const double *gridpart;  // [n_gridpart][3] energy partials of the grid
-  const float *Vacc;     // mixed path: upper-triangle V (FP32), else null
-  const double *dD;      // mixed path: D - Dq for the first-order energy correction
+  const double *Vacc;    // mixed path: upper-triangle V from the grid pass, else null
+  const double *dO;      // mixed path: O - Oq for the first-order energy correction
   int n_gridpart;
   double *red;           // reduction scratch [gridDim][2]
   int *flags;
@@ -142,13 +142,15 @@ struct etdm_handle {
   int n_tiles_tc = 0, max_list_tc = 0;
   long n_entries_tc = 0;
   int *d_tile_ptr_tc = nullptr, *d_keys_tc = nullptr;
-  float2 *d_tabf = nullptr;
+  float4 *d_tabf = nullptr;
   float *d_rc2f = nullptr;
   signed char *d_rowexp = nullptr;
-  uint32_t *d_J = nullptr;
-  float *d_fscale = nullptr;
-  double *d_dD = nullptr;
-  float *d_Vacc = nullptr;
+  uint2 *d_Osl = nullptr;     // [M][N] BF16 slices of O
+  float *d_oscale = nullptr;  // [N]
+  double *d_dO = nullptr;     // [M][N] O - Oq
+  float2 *d_Vpriv = nullptr;  // [n_vcopies][M][M] per-CTA V accumulations
+  int n_vcopies = 0;
+  double *d_Vfin = nullptr;   // [M][M] V (upper triangle), FP64
   // matrices
   double *d_S = nullptr, *d_T = nullptr, *d_C0 = nullptr;
   double *d_D = nullptr, *d_H = nullptr, *d_Uocc = nullptr, *d_O = nullptr;
@@ -231,7 +233,7 @@ cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t 
 // mixed-precision grid passes (mixed.cu)
 cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_rowexp(etdm_handle *h, cudaStream_t s);
-cudaError_t launch_dslice(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);
 int tc_max_list();

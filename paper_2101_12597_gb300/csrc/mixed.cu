@@ -1,22 +1,30 @@
 // Mixed-precision grid passes on the 5th-generation tensor cores (tcgen05).
 //
-// basis -> grid density (Eq. 2, 12): per 128-point tile (4 x 4 x 8) with a
-// truncation list of n <= 128 function images,
-//     Y = X D_loc  (128 x n x n),  rho_p = sum_b X_pb Y_pb .
-// X rows and D columns are cut into exact integer slices held in BF16
-// ("Ozaki" splitting): X_pa = 2^(e_p-8) (I0 + I1/2^8 + I2/2^16),
-// D_ab = 2^(f_b-8) (J0 + J1/2^8), |I|, |J| <= 128.  Every product of slices is
-// an integer and every sum over a (<= 128 terms of <= 2^14) stays below 2^24,
-// so the three FP32 accumulators in tensor memory
-//     acc0 = I0 J0,  acc1 = I0 J1 + I1 J0,  acc2 = I1 J1 + I2 J0
-// are exact whatever rounding the accumulator applies.  The remaining errors
-// (dropped 2^-24 terms, FP32 row dot) are unbiased and incoherent across grid
-// points; the quantization of D (16 bits) is coherent and is removed to first
-// order in the energy with Tr(V (D - Dq)) (dense reverse kernel).
+// basis -> grid density (Eq. 2, 3, 12) in orbital form: per 128-point tile
+// (4 x 4 x 8) with a truncation list of n <= 128 function images,
+//     phi = X O_loc  (128 x n x N_occ),  rho_p = 2 sum_m phi_pm^2 ,
+// a sum of positive terms (the same density as sum X D X, whose terms cancel
+// heavily in a non-orthogonal basis).  X rows and O columns are cut into exact
+// integer slices held in BF16 ("Ozaki" splitting):
+//     X_pa = 2^(e_p-8) (I0 + I1/2^8 + I2/2^16 + I3/2^24)   (X as a float pair),
+//     O_am = 2^(g_m-8) (K0 + K1/2^8 + K2/2^16),    |I|, |K| <= 128.
+// Every product of slices is an integer, and every accumulator (at most three
+// products per K step, <= 128 entries of <= 2^14) stays below 2^24, so the
+// four FP32 accumulators of slice order 0..3 in tensor memory are exact
+// whatever rounding the accumulator applies (the tensor-core accumulator
+// truncates).  X is resolved to about 2^-31 of its row maximum, which the
+// cancellation in X O needs; the 24-bit quantization of O is coherent and is
+// removed to first order in the energy by sum (4 V O) o (O - Oq) (dense
+// reverse kernel); the rest (order >= 4 terms, FP32 square sums) is unbiased
+// and incoherent across grid points.
 //
 // grid -> basis potential matrix (Eq. 11): V_ab = dV sum_p X_pa v_p X_pb with
-// X and v X as BF16 hi + lo pairs (three products, one FP32 accumulator); it
-// only feeds the gradient and the first-order energy correction.
+// X^T and (v X)^T rows cut into four exact integer slices each (exponent per
+// list entry from a separable bound over the tile) and slice orders 0..3 in
+// four exact accumulators.  The gradient amplifies errors of V by the large
+// Loewdin coefficients (O^T V O), so V is kept to about 2^-31 of its row
+// scale; tiles are summed in per-CTA float-pair copies (no atomics) and the
+// copies in FP64.
 //
 // Operands are staged in shared memory in the canonical no-swizzle K-major
 // layout (8-row x 16-byte core matrices); one thread issues tcgen05.mma, the
@@ -37,7 +45,6 @@ constexpr int kTcThreads = 256;
 constexpr int kTP = 128;     // points per tile
 constexpr int kNmax = 128;   // max padded list length
 constexpr int kTmemCols = 512;
-constexpr int kSliceBytes = kTP * kNmax * 2;  // one 128 x 128 BF16 operand
 constexpr long kMbarSpin = 4000000;
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -48,9 +55,15 @@ __device__ __forceinline__ uint32_t su32(const void *p) {
 __device__ __forceinline__ int kmaj_off(int row, int k) {
   return (((row >> 3) * (kNmax / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
 }
+// the same for a 128-row operand holding a K chunk of 64 columns
+constexpr int kKc = 64;
+constexpr int kChunkBytes = kTP * kKc * 2;
+__device__ __forceinline__ int kmaj_off64(int row, int k) {
+  return (((row >> 3) * (kKc / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  const uint32_t lbo = 128, sbo = (kNmax / 8) * 128;
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo = (kNmax / 8) * 128) {
+  const uint32_t lbo = 128;
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
@@ -120,14 +133,16 @@ struct TcArgs {
   GridGeom g;  // 4 x 4 x 8 tiles
   int n_tiles;
   const int *tile_ptr, *keys;
-  const float2 *tab[3];        // per axis [mu][img][i]: (sq, norm^(1/3) exp(-alpha sq))
+  const float4 *tab[3];        // per axis [mu][img][i]: (sq, c hi, c lo, 0),
+                               // c = norm^(1/3) exp(-alpha sq) as a float pair
   const float *rc2f;           // [M]
   const signed char *rowexp;   // [G]
-  const uint32_t *J;           // [M][M] bf16 pairs (J0 low, J1 high) of row-scaled D
-  const float *fscale;         // [M] 2^f_nu
+  const uint2 *Osl;            // [M][N] bf16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
+  const float *oscale;         // [N] 2^g_m
+  int Nocc;
   double *rho;                 // [G]
   const double *v;             // [G]
-  float *Vacc;                 // [M][M] upper triangle
+  float2 *Vpriv;               // [gridDim][M][M] per-CTA float-pair V (upper triangle)
   double dV;
   int *flags;
 };
@@ -135,7 +150,7 @@ struct TcArgs {
 struct TileShared {
   int mu[kNmax];
   float fs[kNmax];
-  float2 stage[kNmax][16];  // per entry: 4 x-values, 4 y-values, 8 z-values
+  float4 stage[kNmax][16];  // per entry: 4 x-values, 4 y-values, 8 z-values
   float part[kTP];
   uint64_t mbar;
   uint32_t tbase;
@@ -153,22 +168,20 @@ __device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n)
     int mu = key >> 9;
     int ix = ((key >> 6) & 7) - 4 + kImgMax, iy = ((key >> 3) & 7) - 4 + kImgMax,
         iz = (key & 7) - 4 + kImgMax;
-    float2 val;
+    const float4 out = make_float4(INFINITY, 0.f, 0.f, 0.f);
+    float4 val;
     if (s < 4) {
       int i = i0 + s;
-      val = i < g.nx ? A.tab[0][((long)mu * kImgN + ix) * g.nx + i] : make_float2(INFINITY, 0.f);
+      val = i < g.nx ? A.tab[0][((long)mu * kImgN + ix) * g.nx + i] : out;
     } else if (s < 8) {
       int j = j0 + s - 4;
-      val = j < g.ny ? A.tab[1][((long)mu * kImgN + iy) * g.ny + j] : make_float2(INFINITY, 0.f);
+      val = j < g.ny ? A.tab[1][((long)mu * kImgN + iy) * g.ny + j] : out;
     } else {
       int k = k0 + s - 8;
-      val = k < g.nz ? A.tab[2][((long)mu * kImgN + iz) * g.nz + k] : make_float2(INFINITY, 0.f);
+      val = k < g.nz ? A.tab[2][((long)mu * kImgN + iz) * g.nz + k] : out;
     }
     S.stage[e][s] = val;
-    if (s == 0) {
-      S.mu[e] = mu;
-      S.fs[e] = A.fscale ? A.fscale[mu] : 0.f;
-    }
+    if (s == 0) S.mu[e] = mu;
   }
   for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
     int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
@@ -180,9 +193,29 @@ __device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n)
 
 __device__ __forceinline__ float basis_val(const TileShared &S, const float *rc2f, int e, int p) {
   int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
-  float2 x = S.stage[e][li], y = S.stage[e][4 + lj], z = S.stage[e][8 + lk];
+  float4 x = S.stage[e][li], y = S.stage[e][4 + lj], z = S.stage[e][8 + lk];
   float r2 = (x.x + y.x) + z.x;
   return r2 < rc2f[S.mu[e]] ? x.y * y.y * z.y : 0.f;
+}
+
+// float-pair (hi + lo) arithmetic: exact product by FMA, then renormalization
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p);
+  const float t = e + fmaf(a.x, b.y, a.y * b.x);
+  const float s = p + t;
+  return make_float2(s, t - (s - p));
+}
+
+// the same basis value as a float pair (about 44 significant bits); the hi
+// part equals basis_val up to rounding
+__device__ __forceinline__ float2 basis_val_df(const TileShared &S, const float *rc2f, int e,
+                                               int p) {
+  int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
+  float4 x = S.stage[e][li], y = S.stage[e][4 + lj], z = S.stage[e][8 + lk];
+  float r2 = (x.x + y.x) + z.x;
+  if (!(r2 < rc2f[S.mu[e]])) return make_float2(0.f, 0.f);
+  return df_mul(df_mul(make_float2(x.y, x.z), make_float2(y.y, y.z)), make_float2(z.y, z.z));
 }
 
 __device__ __forceinline__ void tmem_alloc(TileShared &S) {
@@ -214,151 +247,224 @@ __device__ __forceinline__ void tmem_free(TileShared &S) {
 
 // ---- density ---------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) rho_tc_kernel(TcArgs A) {
+  // one K chunk (64 list entries) of the operands at a time:
+  // A = X slices I0..I3 (128 points x 64), B = O slices K0..K2 (<= 128 orbitals x 64)
   extern __shared__ __align__(1024) uint8_t dsm[];
-  uint8_t *sA = dsm;                     // 3 slices I0, I1, I2
-  uint8_t *sB = dsm + 3 * kSliceBytes;   // 2 slices J0, J1
+  uint8_t *sA = dsm;
+  uint8_t *sB = dsm + 4 * kChunkBytes;
   __shared__ TileShared S;
   tmem_alloc(S);
   const uint32_t tmem = S.tbase;
   uint32_t phase = 0;
   bool ok = true;
+  const int w = threadIdx.x >> 5, quad = w & 3, half = w >> 2;
+  const int pe = quad * 32 + (threadIdx.x & 31);  // epilogue point (TMEM lane)
+  const uint32_t lane = (uint32_t)(quad * 32) << 16;
   for (int t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
     const int kb = A.tile_ptr[t], n = A.tile_ptr[t + 1] - kb;
-    const int npad = n <= 32 ? 32 : ((n + 31) / 32) * 32;
     if (n > kNmax) {  // rejected at set-up; never reached
       if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
       continue;
     }
+    const int nk = n <= 32 ? 2 : (n + 15) / 16;  // K steps of 16
+    const int nkc = (nk + 3) / 4;                // K chunks of 64
     stage_tile(A, S, t, kb, n);
     __syncthreads();
-    // A slices: items (p, 8 consecutive entries)
-    for (int q = threadIdx.x; q < kTP * (npad / 8); q += blockDim.x) {
-      const int p = q % kTP, a0 = (q / kTP) * 8;
-      const int gp = S.inside[p];
-      const int ep = gp >= 0 ? (int)A.rowexp[gp] : 0;
-      uint16_t s0[8], s1[8], s2[8];
+    float rsum = 0.f;
+    // occupied orbitals in chunks of up to 128 columns
+    for (int m0 = 0; m0 < A.Nocc && ok; m0 += kNmax) {
+      const int nm = min(kNmax, A.Nocc - m0);
+      const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
+      for (int m = threadIdx.x; m < nmpad; m += blockDim.x)
+        S.fs[m] = m < nm ? A.oscale[m0 + m] : 0.f;
+      for (int kc = 0; kc < nkc && ok; ++kc) {
+        const int k0 = kc * kKc;
+        // A: X slices of entries k0 .. k0 + 63; items (point, 8 entries)
+        for (int q = threadIdx.x; q < kTP * (kKc / 8); q += blockDim.x) {
+          const int p = q % kTP, c0 = (q / kTP) * 8;
+          const int gp = S.inside[p];
+          const int ep = gp >= 0 ? (int)A.rowexp[gp] : 0;
+          uint16_t sl[4][8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        int a = a0 + u;
-        float x = (a < n && gp >= 0) ? basis_val(S, A.rc2f, a, p) : 0.f;
-        float t0 = ldexpf(x, 8 - ep);
-        float r0 = rintf(t0);
-        float t1 = (t0 - r0) * 256.f;
-        float r1 = rintf(t1);
-        float t2 = (t1 - r1) * 256.f;
-        float r2 = rintf(t2);
-        s0[u] = bf16_bits(r0); s1[u] = bf16_bits(r1); s2[u] = bf16_bits(r2);
-      }
-      const int off = kmaj_off(p, a0);
-      uint4 v0, v1, v2;
-      v0.x = s0[0] | (s0[1] << 16); v0.y = s0[2] | (s0[3] << 16);
-      v0.z = s0[4] | (s0[5] << 16); v0.w = s0[6] | (s0[7] << 16);
-      v1.x = s1[0] | (s1[1] << 16); v1.y = s1[2] | (s1[3] << 16);
-      v1.z = s1[4] | (s1[5] << 16); v1.w = s1[6] | (s1[7] << 16);
-      v2.x = s2[0] | (s2[1] << 16); v2.y = s2[2] | (s2[3] << 16);
-      v2.z = s2[4] | (s2[5] << 16); v2.w = s2[6] | (s2[7] << 16);
-      *(uint4 *)(sA + off) = v0;
-      *(uint4 *)(sA + kSliceBytes + off) = v1;
-      *(uint4 *)(sA + 2 * kSliceBytes + off) = v2;
-    }
-    // B slices: B[b][a] = J[mu_b][mu_a]
-    for (int q = threadIdx.x; q < npad * (npad / 8); q += blockDim.x) {
-      const int b = q % npad, a0 = (q / npad) * 8;
-      uint32_t w[8];
+          for (int u = 0; u < 8; ++u) {
+            const int a = k0 + c0 + u;
+            float2 x = (a < n && gp >= 0) ? basis_val_df(S, A.rc2f, a, p) : make_float2(0.f, 0.f);
+            // x 2^(8 - e_p) = r0 + r1/256 + r2/256^2 + r3/256^3 + O(2^-25)
+            float h = ldexpf(x.x, 8 - ep), l = ldexpf(x.y, 8 - ep);
+            float r0 = rintf(h);
+            float tt = ((h - r0) + l) * 256.f;
+            float r1 = rintf(tt);
+            tt = (tt - r1) * 256.f;
+            float r2 = rintf(tt);
+            tt = (tt - r2) * 256.f;
+            float r3 = rintf(tt);
+            sl[0][u] = bf16_bits(r0); sl[1][u] = bf16_bits(r1);
+            sl[2][u] = bf16_bits(r2); sl[3][u] = bf16_bits(r3);
+          }
+          const int off = kmaj_off64(p, c0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        int a = a0 + u;
-        w[u] = (a < n && b < n) ? A.J[(long)S.mu[b] * A.g.M + S.mu[a]] : 0u;
+          for (int k = 0; k < 4; ++k) {
+            uint4 v;
+            v.x = sl[k][0] | (sl[k][1] << 16); v.y = sl[k][2] | (sl[k][3] << 16);
+            v.z = sl[k][4] | (sl[k][5] << 16); v.w = sl[k][6] | (sl[k][7] << 16);
+            *(uint4 *)(sA + k * kChunkBytes + off) = v;
+          }
+        }
+        // B: O slices, B[m][a] = O-slice[mu_a][m0 + m]; items (orbital, 8 entries)
+        for (int q = threadIdx.x; q < nmpad * (kKc / 8); q += blockDim.x) {
+          const int m = q % nmpad, c0 = (q / nmpad) * 8;
+          uint32_t w01[8], w2[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int a = k0 + c0 + u;
+            uint2 kk = (a < n && m < nm) ? A.Osl[(long)S.mu[a] * A.Nocc + m0 + m]
+                                         : make_uint2(0u, 0u);
+            w01[u] = kk.x;
+            w2[u] = kk.y;
+          }
+          const int off = kmaj_off64(m, c0);
+          uint4 v0, v1, v2;
+          v0.x = (w01[0] & 0xFFFF) | (w01[1] << 16); v0.y = (w01[2] & 0xFFFF) | (w01[3] << 16);
+          v0.z = (w01[4] & 0xFFFF) | (w01[5] << 16); v0.w = (w01[6] & 0xFFFF) | (w01[7] << 16);
+          v1.x = (w01[0] >> 16) | (w01[1] & 0xFFFF0000u);
+          v1.y = (w01[2] >> 16) | (w01[3] & 0xFFFF0000u);
+          v1.z = (w01[4] >> 16) | (w01[5] & 0xFFFF0000u);
+          v1.w = (w01[6] >> 16) | (w01[7] & 0xFFFF0000u);
+          v2.x = w2[0] | (w2[1] << 16); v2.y = w2[2] | (w2[3] << 16);
+          v2.z = w2[4] | (w2[5] << 16); v2.w = w2[6] | (w2[7] << 16);
+          *(uint4 *)(sB + off) = v0;
+          *(uint4 *)(sB + kChunkBytes + off) = v1;
+          *(uint4 *)(sB + 2 * kChunkBytes + off) = v2;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t idesc = idesc_bf16(nmpad);
+          const uint32_t a0 = su32(sA), b0 = su32(sB);
+          const uint32_t sbo = (kKc / 8) * 128;
+          const int ksteps = min(4, nk - kc * 4);
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const uint32_t off = kk * 256;
+            const uint64_t I0 = smem_desc(a0 + off, sbo), I1 = smem_desc(a0 + kChunkBytes + off, sbo),
+                           I2 = smem_desc(a0 + 2 * kChunkBytes + off, sbo),
+                           I3 = smem_desc(a0 + 3 * kChunkBytes + off, sbo);
+            const uint64_t K0 = smem_desc(b0 + off, sbo), K1 = smem_desc(b0 + kChunkBytes + off, sbo),
+                           K2 = smem_desc(b0 + 2 * kChunkBytes + off, sbo);
+            const uint32_t acc = (kc > 0 || kk > 0);
+            mma_bf16(tmem, I0, K0, idesc, acc);                  // order 0
+            mma_bf16(tmem + kNmax, I0, K1, idesc, acc);          // order 1
+            mma_bf16(tmem + kNmax, I1, K0, idesc, 1u);
+            mma_bf16(tmem + 2 * kNmax, I0, K2, idesc, acc);      // order 2
+            mma_bf16(tmem + 2 * kNmax, I1, K1, idesc, 1u);
+            mma_bf16(tmem + 2 * kNmax, I2, K0, idesc, 1u);
+            mma_bf16(tmem + 3 * kNmax, I1, K2, idesc, acc);      // order 3
+            mma_bf16(tmem + 3 * kNmax, I2, K1, idesc, 1u);
+            mma_bf16(tmem + 3 * kNmax, I3, K0, idesc, 1u);
+          }
+          mma_commit(&S.mbar);
+        }
+        ok = __syncthreads_and(mbar_wait(&S.mbar, phase)) != 0;
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
-      const int off = kmaj_off(b, a0);
-      uint4 v0, v1;
-      v0.x = (w[0] & 0xFFFF) | (w[1] << 16); v0.y = (w[2] & 0xFFFF) | (w[3] << 16);
-      v0.z = (w[4] & 0xFFFF) | (w[5] << 16); v0.w = (w[6] & 0xFFFF) | (w[7] << 16);
-      v1.x = (w[0] >> 16) | (w[1] & 0xFFFF0000u); v1.y = (w[2] >> 16) | (w[3] & 0xFFFF0000u);
-      v1.z = (w[4] >> 16) | (w[5] & 0xFFFF0000u); v1.w = (w[6] >> 16) | (w[7] & 0xFFFF0000u);
-      *(uint4 *)(sB + off) = v0;
-      *(uint4 *)(sB + kSliceBytes + off) = v1;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t idesc = idesc_bf16(npad);
-      const uint32_t a0 = su32(sA), b0 = su32(sB);
-      for (int kk = 0; kk < npad / 16; ++kk) {
-        const uint32_t off = kk * 256;
-        const uint64_t I0 = smem_desc(a0 + off), I1 = smem_desc(a0 + kSliceBytes + off),
-                       I2 = smem_desc(a0 + 2 * kSliceBytes + off);
-        const uint64_t J0 = smem_desc(b0 + off), J1 = smem_desc(b0 + kSliceBytes + off);
-        const uint32_t acc = kk > 0;
-        mma_bf16(tmem, I0, J0, idesc, acc);
-        mma_bf16(tmem + kNmax, I0, J1, idesc, acc);
-        mma_bf16(tmem + kNmax, I1, J0, idesc, 1u);
-        mma_bf16(tmem + 2 * kNmax, I1, J1, idesc, acc);
-        mma_bf16(tmem + 2 * kNmax, I2, J0, idesc, 1u);
+      if (ok) {
+        // phi_pm = 2^(e_p + g_m - 16) y with y = acc0 + (acc1 + (acc2 + acc3/256)/256)/256;
+        // rho_p = 2 sum_m phi_pm^2 (every term positive)
+        const int cw = nmpad / 2;
+        for (int c0 = half * cw; c0 < half * cw + cw; c0 += 16) {
+          float y0[16], y1[16], y2[16], y3[16];
+          tmem_ld16(tmem + lane + c0, y0);
+          tmem_ld16(tmem + lane + kNmax + c0, y1);
+          tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
+          tmem_ld16(tmem + lane + 3 * kNmax + c0, y3);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float y = y0[j] + (y1[j] + (y2[j] + y3[j] * (1.f / 256.f)) * (1.f / 256.f)) *
+                                  (1.f / 256.f);
+            y *= S.fs[c0 + j];
+            rsum = fmaf(y, y, rsum);
+          }
+        }
       }
-      mma_commit(&S.mbar);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
     }
-    ok = __syncthreads_and(mbar_wait(&S.mbar, phase)) != 0;
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) {
       if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
       break;
     }
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; warps 0-3 and 4-7 split columns
-    {
-      const int w = threadIdx.x >> 5, quad = w & 3, half = w >> 2;
-      const int p = quad * 32 + (threadIdx.x & 31);
-      const uint32_t lane = (uint32_t)(quad * 32) << 16;
-      const int cw = npad / 2;
-      float sum = 0.f;
-      for (int c0 = half * cw; c0 < half * cw + cw; c0 += 16) {
-        float y0[16], y1[16], y2[16];
-        tmem_ld16(tmem + lane + c0, y0);
-        tmem_ld16(tmem + lane + kNmax + c0, y1);
-        tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int b = c0 + j;
-          const int off = kmaj_off(p, b);
-          float x = bf16_val(*(const uint16_t *)(sA + off)) +
-                    bf16_val(*(const uint16_t *)(sA + kSliceBytes + off)) * (1.f / 256.f) +
-                    bf16_val(*(const uint16_t *)(sA + 2 * kSliceBytes + off)) * (1.f / 65536.f);
-          float y = y0[j] + (y1[j] + y2[j] * (1.f / 256.f)) * (1.f / 256.f);
-          float fsb = b < n ? S.fs[b] : 0.f;
-          sum = fmaf(x * y, fsb, sum);
-        }
-      }
-      if (half == 1) S.part[p] = sum;
-      __syncthreads();
-      if (half == 0) {
-        const int gp = S.inside[p];
-        if (gp >= 0) {
-          const int ep = (int)A.rowexp[gp];
-          double r = (double)sum + (double)S.part[p];
-          A.rho[gp] = ldexp(r, 2 * ep - 24);
-        }
+    if (half == 1) S.part[pe] = rsum;
+    __syncthreads();
+    if (half == 0) {
+      const int gp = S.inside[pe];
+      if (gp >= 0) {
+        const int ep = (int)A.rowexp[gp];
+        double r = (double)rsum + (double)S.part[pe];
+        A.rho[gp] = ldexp(r, 2 * ep - 31);
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
   tmem_free(S);
 }
 
+
 // ---- potential matrix ---------------------------------------------------------
+// sum of two float pairs (hi, lo) with an exact TwoSum of the high parts
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = (a.x - (s - bb)) + (b.x - bb);
+  const float t = e + a.y + b.y;
+  const float h = s + t;
+  return make_float2(h, t - (h - s));
+}
+
+// exponent e with |x| 2^(8-e) < 128 for every |x| <= bound (0 for bound 0)
+__device__ __forceinline__ int slice_exp(float bound) {
+  return bound > 0.f ? ilogbf(bound) + 2 : 0;
+}
+
+// 4 integer slices of the float pair x 2^(8 - e) (|.| < 128): x 2^(8-e) =
+// r0 + r1/256 + r2/256^2 + r3/256^3 + O(2^-25)
+__device__ __forceinline__ void slice4(float2 x, int e, uint16_t *s) {
+  float h = ldexpf(x.x, 8 - e), l = ldexpf(x.y, 8 - e);
+  float r0 = rintf(h);
+  float tt = ((h - r0) + l) * 256.f;
+  float r1 = rintf(tt);
+  tt = (tt - r1) * 256.f;
+  float r2 = rintf(tt);
+  tt = (tt - r2) * 256.f;
+  float r3 = rintf(tt);
+  s[0] = bf16_bits(r0); s[1] = bf16_bits(r1); s[2] = bf16_bits(r2); s[3] = bf16_bits(r3);
+}
+
+// V_loc[a][b] = dV sum_p X_pa v_p X_pb on tensor cores with exact integer slices
+// of X^T (rows a, exponent per entry from a bound over the tile) and (v X)^T
+// (rows b); slice orders 0..3 in four FP32 accumulators (exact).  Each CTA adds
+// its tiles into a private float-pair copy of the upper triangle of V (no
+// atomics: one thread owns each target row); a reduction kernel sums the copies.
 __global__ void __launch_bounds__(kTcThreads, 1) vmat_tc_kernel(TcArgs A) {
   extern __shared__ __align__(1024) uint8_t dsm[];
-  uint8_t *sA = dsm;                     // X^T hi, lo  (rows a, K = points)
-  uint8_t *sB = dsm + 2 * kSliceBytes;   // (v X)^T hi, lo
+  uint8_t *sA = dsm;                     // X^T slices 0..3 (rows a, K = 64 points)
+  uint8_t *sB = dsm + 4 * kChunkBytes;   // (v X)^T slices 0..3
+  float2 *sV = (float2 *)dsm;            // V_loc (n x n) after the products
   __shared__ TileShared S;
-  __shared__ float vp[kTP];
+  __shared__ float2 vp[kTP];
+  __shared__ int ea[kNmax], eb[kNmax];
+  __shared__ int gstart[kNmax + 1];
+  __shared__ int ngroups;
+  __shared__ float vmax_s;
   tmem_alloc(S);
   const uint32_t tmem = S.tbase;
   uint32_t phase = 0;
   bool ok = true;
   const int M = A.g.M;
+  float2 *Vpriv = A.Vpriv + (long)blockIdx.x * M * M;
+  const int w = threadIdx.x >> 5, quad = w & 3, half = w >> 2;
+  const int ae = quad * 32 + (threadIdx.x & 31);  // epilogue row (TMEM lane)
+  const uint32_t lane = (uint32_t)(quad * 32) << 16;
   for (int t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
     const int kb = A.tile_ptr[t], n = A.tile_ptr[t + 1] - kb;
     const int npad = n <= 32 ? 32 : ((n + 31) / 32) * 32;
@@ -367,108 +473,179 @@ __global__ void __launch_bounds__(kTcThreads, 1) vmat_tc_kernel(TcArgs A) {
       continue;
     }
     stage_tile(A, S, t, kb, n);
+    if (threadIdx.x == 0) vmax_s = 0.f;
     __syncthreads();
     for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
       const int gp = S.inside[p];
-      vp[p] = gp >= 0 ? (float)(A.v[gp] * A.dV) : 0.f;
+      const double vv = gp >= 0 ? A.v[gp] * A.dV : 0.0;
+      const float hi = (float)vv;
+      vp[p] = make_float2(hi, (float)(vv - (double)hi));
+      atomicMax((int *)&vmax_s, __float_as_int(fabsf(hi)));  // non-negative floats order as ints
     }
     __syncthreads();
-    // items (entry a, 8 consecutive points)
-    for (int q = threadIdx.x; q < npad * (kTP / 8); q += blockDim.x) {
-      const int a = q % npad, p0 = (q / npad) * 8;
-      uint16_t xh[8], xl[8], wh[8], wl[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int p = p0 + u;
-        float x = (a < n && S.inside[p] >= 0) ? basis_val(S, A.rc2f, a, p) : 0.f;
-        float w = x * vp[p];
-        xh[u] = bf16_bits(x);
-        xl[u] = bf16_bits(x - bf16_val(xh[u]));
-        wh[u] = bf16_bits(w);
-        wl[u] = bf16_bits(w - bf16_val(wh[u]));
+    // per-entry exponents from separable bounds of X over the tile
+    for (int a = threadIdx.x; a < kNmax; a += blockDim.x) {
+      float bnd = 0.f;
+      if (a < n) {
+        float mx = 0.f, my = 0.f, mz = 0.f;
+        for (int s = 0; s < 4; ++s) mx = fmaxf(mx, S.stage[a][s].y);
+        for (int s = 4; s < 8; ++s) my = fmaxf(my, S.stage[a][s].y);
+        for (int s = 8; s < 16; ++s) mz = fmaxf(mz, S.stage[a][s].y);
+        bnd = mx * my * mz * 1.0001f;
       }
-      const int off = kmaj_off(a, p0);
-      uint4 v;
-      v.x = xh[0] | (xh[1] << 16); v.y = xh[2] | (xh[3] << 16);
-      v.z = xh[4] | (xh[5] << 16); v.w = xh[6] | (xh[7] << 16);
-      *(uint4 *)(sA + off) = v;
-      v.x = xl[0] | (xl[1] << 16); v.y = xl[2] | (xl[3] << 16);
-      v.z = xl[4] | (xl[5] << 16); v.w = xl[6] | (xl[7] << 16);
-      *(uint4 *)(sA + kSliceBytes + off) = v;
-      v.x = wh[0] | (wh[1] << 16); v.y = wh[2] | (wh[3] << 16);
-      v.z = wh[4] | (wh[5] << 16); v.w = wh[6] | (wh[7] << 16);
-      *(uint4 *)(sB + off) = v;
-      v.x = wl[0] | (wl[1] << 16); v.y = wl[2] | (wl[3] << 16);
-      v.z = wl[4] | (wl[5] << 16); v.w = wl[6] | (wl[7] << 16);
-      *(uint4 *)(sB + kSliceBytes + off) = v;
+      ea[a] = slice_exp(bnd);
+      eb[a] = slice_exp(bnd * vmax_s * 1.0001f);
     }
-    // rows a >= npad of the M = 128 operand stay as set below
-    for (int q = threadIdx.x; q < (kNmax - npad) * (kTP / 8); q += blockDim.x) {
-      const int a = npad + q % (kNmax - npad), p0 = (q / (kNmax - npad)) * 8;
-      const int off = kmaj_off(a, p0);
-      *(uint4 *)(sA + off) = make_uint4(0, 0, 0, 0);
-      *(uint4 *)(sA + kSliceBytes + off) = make_uint4(0, 0, 0, 0);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    // groups of equal mu (keys are sorted): thread-owned accumulation targets
     if (threadIdx.x == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t idesc = idesc_bf16(npad);
-      const uint32_t a0 = su32(sA), b0 = su32(sB);
-      for (int kk = 0; kk < kTP / 16; ++kk) {
-        const uint32_t off = kk * 256;
-        const uint64_t Xh = smem_desc(a0 + off), Xl = smem_desc(a0 + kSliceBytes + off);
-        const uint64_t Wh = smem_desc(b0 + off), Wl = smem_desc(b0 + kSliceBytes + off);
-        mma_bf16(tmem, Xh, Wh, idesc, kk > 0);
-        mma_bf16(tmem, Xh, Wl, idesc, 1u);
-        mma_bf16(tmem, Xl, Wh, idesc, 1u);
-      }
-      mma_commit(&S.mbar);
+      int g = 0;
+      for (int a = 0; a < n; ++a)
+        if (a == 0 || S.mu[a] != S.mu[a - 1]) gstart[g++] = a;
+      gstart[g] = n;
+      ngroups = g;
     }
-    ok = __syncthreads_and(mbar_wait(&S.mbar, phase)) != 0;
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    for (int kc = 0; kc < kTP / kKc && ok; ++kc) {
+      // items (entry a, 8 consecutive points of the chunk); rows a >= n are zero
+      for (int q = threadIdx.x; q < kNmax * (kKc / 8); q += blockDim.x) {
+        const int a = q % kNmax, c0 = (q / kNmax) * 8;
+        uint16_t xs[4][8], ws[4][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int p = kc * kKc + c0 + u;
+          float2 x = (a < n && S.inside[p] >= 0) ? basis_val_df(S, A.rc2f, a, p)
+                                                 : make_float2(0.f, 0.f);
+          float2 wv = df_mul(x, vp[p]);
+          uint16_t s4[4];
+          slice4(x, ea[a], s4);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) xs[k][u] = s4[k];
+          slice4(wv, eb[a], s4);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) ws[k][u] = s4[k];
+        }
+        const int off = kmaj_off64(a, c0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          uint4 v;
+          v.x = xs[k][0] | (xs[k][1] << 16); v.y = xs[k][2] | (xs[k][3] << 16);
+          v.z = xs[k][4] | (xs[k][5] << 16); v.w = xs[k][6] | (xs[k][7] << 16);
+          *(uint4 *)(sA + k * kChunkBytes + off) = v;
+          if (a < npad) {
+            v.x = ws[k][0] | (ws[k][1] << 16); v.y = ws[k][2] | (ws[k][3] << 16);
+            v.z = ws[k][4] | (ws[k][5] << 16); v.w = ws[k][6] | (ws[k][7] << 16);
+            *(uint4 *)(sB + k * kChunkBytes + off) = v;
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = idesc_bf16(npad);
+        const uint32_t a0 = su32(sA), b0 = su32(sB);
+        const uint32_t sbo = (kKc / 8) * 128;
+        for (int kk = 0; kk < kKc / 16; ++kk) {
+          const uint32_t off = kk * 256;
+          uint64_t X[4], W[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            X[k] = smem_desc(a0 + k * kChunkBytes + off, sbo);
+            W[k] = smem_desc(b0 + k * kChunkBytes + off, sbo);
+          }
+          const uint32_t acc = (kc > 0 || kk > 0);
+          mma_bf16(tmem, X[0], W[0], idesc, acc);                 // order 0
+          mma_bf16(tmem + kNmax, X[0], W[1], idesc, acc);         // order 1
+          mma_bf16(tmem + kNmax, X[1], W[0], idesc, 1u);
+          mma_bf16(tmem + 2 * kNmax, X[0], W[2], idesc, acc);     // order 2
+          mma_bf16(tmem + 2 * kNmax, X[1], W[1], idesc, 1u);
+          mma_bf16(tmem + 2 * kNmax, X[2], W[0], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, X[0], W[3], idesc, acc);     // order 3
+          mma_bf16(tmem + 3 * kNmax, X[1], W[2], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, X[2], W[1], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, X[3], W[0], idesc, 1u);
+        }
+        mma_commit(&S.mbar);
+      }
+      ok = __syncthreads_and(mbar_wait(&S.mbar, phase)) != 0;
+      phase ^= 1;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
     if (!ok) {
       if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
       break;
     }
+    // V_loc[a][b] = 2^(e_a + e_b - 16) (acc0 + (acc1 + (acc2 + acc3/256)/256)/256) as a pair
     {
-      const int w = threadIdx.x >> 5, quad = w & 3, half = w >> 2;
-      const int a = quad * 32 + (threadIdx.x & 31);
-      const uint32_t lane = (uint32_t)(quad * 32) << 16;
       const int cw = npad / 2;
-      const int ma = a < n ? S.mu[a] : 0;
       for (int c0 = half * cw; c0 < half * cw + cw; c0 += 16) {
-        float val[16];
-        tmem_ld16(tmem + lane + c0, val);  // whole warp, converged (.sync.aligned)
+        float y0[16], y1[16], y2[16], y3[16];
+        tmem_ld16(tmem + lane + c0, y0);
+        tmem_ld16(tmem + lane + kNmax + c0, y1);
+        tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
+        tmem_ld16(tmem + lane + 3 * kNmax + c0, y3);
+        if (ae < n) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int b = c0 + j;
-          if (a < n && b >= a && b < n) {
-            const int mb = S.mu[b];
-            float s = val[j];
-            if (ma == mb && a != b) s *= 2.f;
-            if (s != 0.f) atomicAdd(A.Vacc + (long)ma * M + mb, s);
+          for (int j = 0; j < 16; ++j) {
+            const int b = c0 + j;
+            if (b < n) {
+              const int sc = ea[ae] + eb[b] - 16;
+              float lo = (y1[j] + (y2[j] + y3[j] * (1.f / 256.f)) * (1.f / 256.f)) * (1.f / 256.f);
+              float hi = y0[j] + lo;  // fold into a normalized pair
+              lo = lo - (hi - y0[j]);
+              sV[ae * n + b] = make_float2(ldexpf(hi, sc), ldexpf(lo, sc));
+            }
           }
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    // one thread per group u of equal mu: targets (mu_u, mu_w) with w >= u, summed
+    // over the ordered entry pairs of the two groups (V_loc is symmetric)
+    for (int u = threadIdx.x; u < ngroups; u += blockDim.x) {
+      const int mu = S.mu[gstart[u]];
+      for (int wg = u; wg < ngroups; ++wg) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int a = gstart[u]; a < gstart[u + 1]; ++a)
+          for (int b = gstart[wg]; b < gstart[wg + 1]; ++b) acc = df_add(acc, sV[a * n + b]);
+        float2 *dst = Vpriv + (long)mu * M + S.mu[gstart[wg]];
+        *dst = df_add(*dst, acc);
+      }
+    }
+    __syncthreads();
   }
   tmem_free(S);
+}
+
+// H_upper[mu][nu] = sum over CTA copies of (hi + lo), FP64, mu <= nu
+__global__ void vpriv_reduce_kernel(const float2 *Vpriv, int ncopies, int M, double *Vout) {
+  const long MM = (long)M * M;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
+       e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / M), c = (int)(e % M);
+    if (i > c) continue;
+    double s = 0.0;
+    for (int k = 0; k < ncopies; ++k) {
+      const float2 v = Vpriv[(long)k * MM + e];
+      s += (double)v.x + (double)v.y;
+    }
+    Vout[e] = s;
+  }
 }
 
 // ---- set-up and per-evaluation helpers ------------------------------------------
 
 // FP32 copies of the basis tables with norm^(1/3) folded into each factor
 __global__ void tables_f32_kernel(const double *sq, const double *ex, const double *norm,
-                                  int M, int n_ax, float2 *out) {
+                                  int M, int n_ax, float4 *out) {
   long total = (long)M * kImgN * n_ax;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
     int mu = (int)(e / ((long)n_ax * kImgN));
-    out[e] = make_float2((float)sq[e], (float)(cbrt(norm[mu]) * ex[e]));
+    const double c = cbrt(norm[mu]) * ex[e];
+    const float hi = (float)c;
+    out[e] = make_float4((float)sq[e], hi, (float)(c - (double)hi), 0.f);
   }
 }
 
@@ -491,13 +668,14 @@ __global__ void __launch_bounds__(kTcThreads) rowexp_kernel(TcArgs A, signed cha
   }
 }
 
-// Row slices of D: f_nu = ilogb(max |D_nu,:|) + 2, J0 + J1/256 = D 2^(8 - f) to
-// 16 bits; dD = D - Dq (FP64) for the first-order energy correction.
-__global__ void __launch_bounds__(256) dslice_kernel(const double *D, int M, uint32_t *J,
-                                                     float *fscale, double *dD) {
-  const int nu = blockIdx.x;
+// Column slices of the occupied orbitals O (M x N): g_m = ilogb(max_mu |O_mu,m|)
+// + 2, K0 + K1/256 + K2/65536 = O 2^(8 - g) to 24 bits; dO = O - Oq (FP64) for
+// the first-order energy correction sum (4 H O) o dO.
+__global__ void __launch_bounds__(256) oslice_kernel(const double *O, int M, int N, uint2 *Osl,
+                                                     float *oscale, double *dO) {
+  const int m = blockIdx.x;
   double mx = 0.0;
-  for (int c = threadIdx.x; c < M; c += blockDim.x) mx = fmax(mx, fabs(D[(long)nu * M + c]));
+  for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(O[(long)r * N + m]));
   __shared__ double red[256];
   red[threadIdx.x] = mx;
   __syncthreads();
@@ -506,17 +684,21 @@ __global__ void __launch_bounds__(256) dslice_kernel(const double *D, int M, uin
     __syncthreads();
   }
   mx = red[0];
-  const int f = mx > 0.0 ? ilogb(mx) + 2 : 0;
-  if (threadIdx.x == 0) fscale[nu] = ldexpf(1.f, f);
-  for (int c = threadIdx.x; c < M; c += blockDim.x) {
-    const double d = D[(long)nu * M + c];
-    const double t0 = ldexp(d, 8 - f);
+  const int g = mx > 0.0 ? ilogb(mx) + 2 : 0;
+  if (threadIdx.x == 0) oscale[m] = ldexpf(1.f, g);
+  for (int r = threadIdx.x; r < M; r += blockDim.x) {
+    const double o = O[(long)r * N + m];
+    const double t0 = ldexp(o, 8 - g);
     const double r0 = rint(t0);
     const double t1 = (t0 - r0) * 256.0;
     const double r1 = rint(t1);
-    const double q = ldexp(r0 + r1 * (1.0 / 256.0), f - 8);
-    dD[(long)nu * M + c] = d - q;
-    J[(long)nu * M + c] = (uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)r1) << 16);
+    const double t2 = (t1 - r1) * 256.0;
+    const double r2 = rint(t2);
+    const double q = ldexp(r0 + (r1 + r2 * (1.0 / 256.0)) * (1.0 / 256.0), g - 8);
+    dO[(long)r * N + m] = o - q;
+    Osl[(long)r * N + m] =
+        make_uint2((uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)r1) << 16),
+                   (uint32_t)bf16_bits((float)r2));
   }
 }
 
@@ -529,11 +711,12 @@ static TcArgs tc_args(etdm_handle *h) {
   for (int ax = 0; ax < 3; ++ax) a.tab[ax] = h->d_tabf + h->tab_off[ax];
   a.rc2f = h->d_rc2f;
   a.rowexp = h->d_rowexp;
-  a.J = h->d_J;
-  a.fscale = h->d_fscale;
+  a.Osl = h->d_Osl;
+  a.oscale = h->d_oscale;
+  a.Nocc = h->N;
   a.rho = h->d_rho;
   a.v = h->d_vtot;
-  a.Vacc = h->d_Vacc;
+  a.Vpriv = h->d_Vpriv;
   a.dV = h->dV;
   a.flags = h->d_flags;
   return a;
@@ -556,13 +739,13 @@ cudaError_t launch_rowexp(etdm_handle *h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_dslice(etdm_handle *h, cudaStream_t s) {
-  dslice_kernel<<<h->M, 256, 0, s>>>(h->d_D, h->M, h->d_J, h->d_fscale, h->d_dD);
+cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
+  oslice_kernel<<<h->N, 256, 0, s>>>(h->d_O, h->M, h->N, h->d_Osl, h->d_oscale, h->d_dO);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = 5 * (size_t)kSliceBytes;
+  const size_t sm = 7 * (size_t)kChunkBytes;
   cudaError_t e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
@@ -571,13 +754,18 @@ cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
 }
 
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = 4 * (size_t)kSliceBytes;
+  const size_t sm = 8 * (size_t)kChunkBytes;
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(h->d_Vacc, 0, (size_t)h->M * h->M * sizeof(float), s);
+  const int copies = std::min(h->n_tiles_tc, h->n_vcopies);
+  const size_t MM = (size_t)h->M * h->M;
+  e = cudaMemsetAsync(h->d_Vpriv, 0, (size_t)copies * MM * sizeof(float2), s);
   if (e != cudaSuccess) return e;
-  vmat_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kTcThreads, sm, s>>>(tc_args(h));
+  vmat_tc_kernel<<<copies, kTcThreads, sm, s>>>(tc_args(h));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  vpriv_reduce_kernel<<<256, 256, 0, s>>>(h->d_Vpriv, copies, h->M, h->d_Vfin);
   return cudaGetLastError();
 }
 
