@@ -186,9 +186,33 @@ enum {
 int etdm_set_profiling(etdm_handle *h, int on);
 int etdm_stage_times(etdm_handle *h, double *ms, int64_t *counts);
 
-/* Message of the last failed call on h (or of the last failed init when h
- * is NULL).  Valid until the next call on the same handle. */
+/* Message of the last failed call on h (or, when h is NULL, of the last failed
+ * init or handle-free call).  Valid until the next call on the same handle. */
 const char *etdm_last_error(const etdm_handle *h);
+
+/* Allocation-free L-BFGS direction.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory where they need
+ * a direction (inside a stream capture with a frozen memory pool, frameworks
+ * that only hand out pre-registered buffers, drivers that forbid cudaMalloc
+ * after start-up).  It computes p = -H g with the same two-loop recursion as
+ * etdm_lbfgs_step, from a pair history the caller keeps, and allocates
+ * nothing: its reduction scratch is a fixed 2.3 KB file-scope device array.
+ *   g_dev  [n]      gradient
+ *   s_dev  [m*n]    steps s_i = a_(i+1) - a_i, oldest (i = 0) to newest
+ *   y_dev  [m*n]    gradient changes y_i; every pair needs y_i . s_i > 0
+ *   h0_dev [n]      diagonal initial inverse Hessian (e.g. the Eq. 33
+ *                   preconditioner, etdm_precondition applied to ones)
+ *   p_dev  [n]      output direction (may not alias the inputs)
+ * Limits: 0 <= m <= 16 and 0 <= n <= 2^40; larger m returns
+ * ETDM_ERR_INVALID_ARG with a message for etdm_last_error(NULL).  The first
+ * call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call clears the array's barrier words and
+ * shares the array, so calls that overlap on the GPU (two streams or host
+ * threads at once) race.  Asynchronous on `stream`. */
+int etdm_lbfgs_direction_noalloc(const double *g_dev, const double *s_dev,
+                                 const double *y_dev, int32_t m, int64_t n,
+                                 const double *h0_dev, double *p_dev, void *stream);
 
 /* Release all device memory of h (NULL is a no-op). */
 void etdm_free(etdm_handle *h);

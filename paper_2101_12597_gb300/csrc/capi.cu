@@ -546,6 +546,8 @@ struct Pt {
 
 }  // namespace
 
+void etdm::set_unbound_error(const std::string &msg) { g_init_err = msg; }
+
 // ============================== C ABI =========================================
 extern "C" {
 

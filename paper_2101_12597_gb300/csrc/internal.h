@@ -237,6 +237,8 @@ cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);
 int tc_max_list();
+// message for etdm_last_error(NULL) from calls that take no handle
+void set_unbound_error(const std::string &msg);
 int occupancy_dense(int *blocks_per_sm);
 int occupancy_lbfgs(int *blocks_per_sm);
 

@@ -33,7 +33,8 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_energy_grad_host", "etdm_precondition", "etdm_lbfgs_step",
            "etdm_lbfgs_reset", "etdm_minimize", "etdm_check", "etdm_layout",
            "etdm_array_bytes", "etdm_get_array", "etdm_set_profiling",
-           "etdm_stage_times", "etdm_last_error", "etdm_free"]
+           "etdm_stage_times", "etdm_last_error", "etdm_free",
+           "etdm_lbfgs_direction_noalloc"]
 STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
 
 
@@ -91,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.etdm_get_array.argtypes = [P, ctypes.c_int32, P, ctypes.c_int64]
     lib.etdm_set_profiling.argtypes = [P, ctypes.c_int]
     lib.etdm_stage_times.argtypes = [P, dp, ctypes.POINTER(ctypes.c_int64)]
+    lib.etdm_lbfgs_direction_noalloc.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int64,
+                                                 P, P, P]
     lib.etdm_last_error.argtypes = [P]
     lib.etdm_last_error.restype = ctypes.c_char_p
     lib.etdm_free.argtypes = [P]
@@ -273,6 +276,32 @@ class ETDM:
             self.close()
         except Exception:
             pass
+
+
+def lbfgs_direction_noalloc(g, S, Y, h0, out=None, stream=None):
+    """p = -H g by the L-BFGS two-loop recursion over the pairs S[i], Y[i]
+    (oldest first) with the diagonal initial inverse Hessian h0, through the
+    allocation-free entry point: for callers that cannot allocate device
+    memory where they need a direction.  All tensors are contiguous CUDA FP64;
+    S and Y have shape (m, n) with m <= 16.  `out` must be preallocated by such
+    callers (here it is created when None)."""
+    import torch
+    lib = load_library()
+    n = g.numel()
+    m = 0 if S is None else S.shape[0]
+    for t in [g, h0] + ([S, Y] if m else []):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("contiguous cuda float64 tensors expected")
+    out = torch.empty_like(g) if out is None else out
+    rc = lib.etdm_lbfgs_direction_noalloc(
+        ctypes.c_void_p(g.data_ptr()),
+        ctypes.c_void_p(S.data_ptr()) if m else None,
+        ctypes.c_void_p(Y.data_ptr()) if m else None,
+        m, n, ctypes.c_void_p(h0.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+        _stream_ptr(stream))
+    if rc != ETDM_OK:
+        raise EtdmError(rc, lib.etdm_last_error(None).decode())
+    return out
 
 
 def energy_function():
