@@ -202,6 +202,12 @@ def run_ours(args):
     solver = ETDM(d, precision=args.precision, device=local)
     dims = solver.dims
     a = torch.tensor(d["a0"], dtype=torch.float64, device=dev)
+    if args.profile_once:  # one evaluation after set-up, for profiler captures
+        solver.energy_grad(a)
+        torch.cuda.synchronize()
+        solver.check()
+        print(json.dumps({"profile_once": True, "precision": args.precision}))
+        return
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     for _ in range(args.warmup):
@@ -327,6 +333,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="set up, run one energy+gradient evaluation, exit (for ncu)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

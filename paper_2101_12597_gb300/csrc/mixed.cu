@@ -41,7 +41,8 @@
 
 namespace etdm {
 
-constexpr int kTcThreads = 256;
+constexpr int kRhoThreads = 512;   // 16 warps: 8 build-only, 8 also read TMEM
+constexpr int kVThreads = 384;     // 12 warps (register budget of the V pass)
 constexpr int kTP = 128;     // points per tile
 constexpr int kNmax = 128;   // max padded list length
 constexpr int kTmemCols = 512;
@@ -150,19 +151,29 @@ struct TcArgs {
 struct TileShared {
   int mu[kNmax];
   float fs[kNmax];
-  float4 stage[kNmax][16];  // per entry: 4 x-values, 4 y-values, 8 z-values
+  float4 stage[kNmax * 16];  // per entry: 4 x-values, 4 y-values, 8 z-values
   float part[kTP];
   uint64_t mbar;
   uint32_t tbase;
   int n, npad, inside[kTP];
 };
 
+// index of slot s of entry e in the staged table: entry-major for the density
+// pass (a warp shares the entry), slot-major for the V pass (a warp spans entries)
+template <bool TR>
+__device__ __forceinline__ int sidx(int e, int s) {
+  return TR ? s * kNmax + e : e * 16 + s;
+}
+
 // stage the per-axis (sq, c exp(-alpha sq)) values of the tile for every entry
-__device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n) {
+// (by the threads tid = 0 .. nthr-1 of the calling group)
+template <bool TR>
+__device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n, int tid,
+                           int nthr) {
   const GridGeom &g = A.g;
   int bz = t % g.nbz, by = (t / g.nbz) % g.nby, bx = t / (g.nbz * g.nby);
   int i0 = bx * 4, j0 = by * 4, k0 = bz * 8;
-  for (int q = threadIdx.x; q < n * 16; q += blockDim.x) {
+  for (int q = tid; q < n * 16; q += nthr) {
     int e = q >> 4, s = q & 15;
     int key = A.keys[kb + e];
     int mu = key >> 9;
@@ -180,10 +191,10 @@ __device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n)
       int k = k0 + s - 8;
       val = k < g.nz ? A.tab[2][((long)mu * kImgN + iz) * g.nz + k] : out;
     }
-    S.stage[e][s] = val;
+    S.stage[sidx<TR>(e, s)] = val;
     if (s == 0) S.mu[e] = mu;
   }
-  for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
+  for (int p = tid; p < kTP; p += nthr) {
     int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
     S.inside[p] = (i0 + li < g.nx && j0 + lj < g.ny && k0 + lk < g.nz)
                       ? ((i0 + li) * g.ny + (j0 + lj)) * g.nz + (k0 + lk)
@@ -191,9 +202,11 @@ __device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n)
   }
 }
 
+template <bool TR>
 __device__ __forceinline__ float basis_val(const TileShared &S, const float *rc2f, int e, int p) {
   int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
-  float4 x = S.stage[e][li], y = S.stage[e][4 + lj], z = S.stage[e][8 + lk];
+  float4 x = S.stage[sidx<TR>(e, li)], y = S.stage[sidx<TR>(e, 4 + lj)],
+         z = S.stage[sidx<TR>(e, 8 + lk)];
   float r2 = (x.x + y.x) + z.x;
   return r2 < rc2f[S.mu[e]] ? x.y * y.y * z.y : 0.f;
 }
@@ -209,10 +222,12 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
 
 // the same basis value as a float pair (about 44 significant bits); the hi
 // part equals basis_val up to rounding
+template <bool TR>
 __device__ __forceinline__ float2 basis_val_df(const TileShared &S, const float *rc2f, int e,
                                                int p) {
   int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
-  float4 x = S.stage[e][li], y = S.stage[e][4 + lj], z = S.stage[e][8 + lk];
+  float4 x = S.stage[sidx<TR>(e, li)], y = S.stage[sidx<TR>(e, 4 + lj)],
+         z = S.stage[sidx<TR>(e, 8 + lk)];
   float r2 = (x.x + y.x) + z.x;
   if (!(r2 < rc2f[S.mu[e]])) return make_float2(0.f, 0.f);
   return df_mul(df_mul(make_float2(x.y, x.z), make_float2(y.y, y.z)), make_float2(z.y, z.z));
@@ -246,7 +261,7 @@ __device__ __forceinline__ void tmem_free(TileShared &S) {
 }
 
 // ---- density ---------------------------------------------------------------
-__global__ void __launch_bounds__(kTcThreads, 1) rho_tc_kernel(TcArgs A) {
+__global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
   // one K chunk (64 list entries) of the operands at a time:
   // A = X slices I0..I3 (128 points x 64), B = O slices K0..K2 (<= 128 orbitals x 64)
   extern __shared__ __align__(1024) uint8_t dsm[];
@@ -268,7 +283,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rho_tc_kernel(TcArgs A) {
     }
     const int nk = n <= 32 ? 2 : (n + 15) / 16;  // K steps of 16
     const int nkc = (nk + 3) / 4;                // K chunks of 64
-    stage_tile(A, S, t, kb, n);
+    stage_tile<false>(A, S, t, kb, n, threadIdx.x, blockDim.x);
     __syncthreads();
     float rsum = 0.f;
     // occupied orbitals in chunks of up to 128 columns
@@ -288,7 +303,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rho_tc_kernel(TcArgs A) {
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int a = k0 + c0 + u;
-            float2 x = (a < n && gp >= 0) ? basis_val_df(S, A.rc2f, a, p) : make_float2(0.f, 0.f);
+            float2 x = (a < n && gp >= 0) ? basis_val_df<false>(S, A.rc2f, a, p) : make_float2(0.f, 0.f);
             // x 2^(8 - e_p) = r0 + r1/256 + r2/256^2 + r3/256^3 + O(2^-25)
             float h = ldexpf(x.x, 8 - ep), l = ldexpf(x.y, 8 - ep);
             float r0 = rintf(h);
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rho_tc_kernel(TcArgs A) {
         phase ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
-      if (ok) {
+      if (ok && w < 8) {  // warps 0..7 read TMEM (lane quarter w % 4, column half w / 4)
         // phi_pm = 2^(e_p + g_m - 16) y with y = acc0 + (acc1 + (acc2 + acc3/256)/256)/256;
         // rho_p = 2 sum_m phi_pm^2 (every term positive)
         const int cw = nmpad / 2;
@@ -440,181 +455,261 @@ __device__ __forceinline__ void slice4(float2 x, int e, uint16_t *s) {
   s[0] = bf16_bits(r0); s[1] = bf16_bits(r1); s[2] = bf16_bits(r2); s[3] = bf16_bits(r3);
 }
 
+// ---- mbarrier helpers for the warp-specialized pipelines ---------------------
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // V_loc[a][b] = dV sum_p X_pa v_p X_pb on tensor cores with exact integer slices
 // of X^T (rows a, exponent per entry from a bound over the tile) and (v X)^T
-// (rows b); slice orders 0..3 in four FP32 accumulators (exact).  Each CTA adds
-// its tiles into a private float-pair copy of the upper triangle of V (no
-// atomics: one thread owns each target row); a reduction kernel sums the copies.
-__global__ void __launch_bounds__(kTcThreads, 1) vmat_tc_kernel(TcArgs A) {
+// (rows b); slice orders 0..3 in four FP32 accumulators (exact).  Warp roles:
+// warps 0-7 build the operand slices of 32-point K chunks into two shared-memory
+// stages; lane 0 of warp 8 issues the MMAs; warps 8-11 read the accumulators
+// (lane quarter = warp % 4) and add V_loc into the CTA's private float-pair copy
+// of the upper triangle of V.  A tile's MMAs start once the previous tile's
+// accumulators are read; building overlaps both.
+constexpr int kVProd = 256;              // producer threads (warps 0-7)
+constexpr int kVEpi = 128;               // epilogue threads (warps 8-11)
+constexpr int kVKc = 32;                 // points per K chunk
+constexpr int kVSlice = kTP * kVKc * 2;  // one slice of one K chunk (8 KB)
+constexpr int kVStage = 8 * kVSlice;     // X^T and (v X)^T, 4 slices each
+constexpr int kVStages = 2;
+
+__device__ __forceinline__ int kmaj_off32(int row, int k) {
+  return (((row >> 3) * (kVKc / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+struct VMeta {  // per-tile data the epilogue needs (double-buffered)
+  int mu[kNmax];
+  int ea[kNmax], eb[kNmax];
+  int rank[kNmax];
+  int n, npad, maxrank;
+};
+
+__global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   extern __shared__ __align__(1024) uint8_t dsm[];
-  uint8_t *sA = dsm;                     // X^T slices 0..3 (rows a, K = 64 points)
-  uint8_t *sB = dsm + 4 * kChunkBytes;   // (v X)^T slices 0..3
-  float2 *sV = (float2 *)dsm;            // V_loc (n x n) after the products
-  __shared__ TileShared S;
+  __shared__ TileShared S;  // producer-side staging (tables, points)
+  __shared__ VMeta meta[2];
   __shared__ float2 vp[kTP];
-  __shared__ int ea[kNmax], eb[kNmax];
-  __shared__ int gstart[kNmax + 1];
-  __shared__ int ngroups;
   __shared__ float vmax_s;
-  tmem_alloc(S);
-  const uint32_t tmem = S.tbase;
-  uint32_t phase = 0;
-  bool ok = true;
+  __shared__ __align__(8) uint64_t bar_full[kVStages], bar_empty[kVStages], bar_acc_full,
+      bar_acc_empty, bar_meta_full[2], bar_meta_empty[2];
+  __shared__ int stop;
+  const int tid = threadIdx.x, w = tid >> 5;
   const int M = A.g.M;
   float2 *Vpriv = A.Vpriv + (long)blockIdx.x * M * M;
-  const int w = threadIdx.x >> 5, quad = w & 3, half = w >> 2;
-  const int ae = quad * 32 + (threadIdx.x & 31);  // epilogue row (TMEM lane)
-  const uint32_t lane = (uint32_t)(quad * 32) << 16;
-  for (int t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
-    const int kb = A.tile_ptr[t], n = A.tile_ptr[t + 1] - kb;
-    const int npad = n <= 32 ? 32 : ((n + 31) / 32) * 32;
-    if (n > kNmax) {
-      if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
-      continue;
-    }
-    stage_tile(A, S, t, kb, n);
-    if (threadIdx.x == 0) vmax_s = 0.f;
-    __syncthreads();
-    for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
-      const int gp = S.inside[p];
-      const double vv = gp >= 0 ? A.v[gp] * A.dV : 0.0;
-      const float hi = (float)vv;
-      vp[p] = make_float2(hi, (float)(vv - (double)hi));
-      atomicMax((int *)&vmax_s, __float_as_int(fabsf(hi)));  // non-negative floats order as ints
-    }
-    __syncthreads();
-    // per-entry exponents from separable bounds of X over the tile
-    for (int a = threadIdx.x; a < kNmax; a += blockDim.x) {
-      float bnd = 0.f;
-      if (a < n) {
-        float mx = 0.f, my = 0.f, mz = 0.f;
-        for (int s = 0; s < 4; ++s) mx = fmaxf(mx, S.stage[a][s].y);
-        for (int s = 4; s < 8; ++s) my = fmaxf(my, S.stage[a][s].y);
-        for (int s = 8; s < 16; ++s) mz = fmaxf(mz, S.stage[a][s].y);
-        bnd = mx * my * mz * 1.0001f;
+  if (tid == 0) {
+    for (int s = 0; s < kVStages; ++s) { mbar_init(&bar_full[s], kVProd); mbar_init(&bar_empty[s], 1); }
+    mbar_init(&bar_acc_full, 1);
+    mbar_init(&bar_acc_empty, kVEpi);
+    for (int s = 0; s < 2; ++s) { mbar_init(&bar_meta_full[s], kVProd); mbar_init(&bar_meta_empty[s], kVEpi); }
+    stop = 0;
+  }
+  tmem_alloc(S);  // also fences the barrier initialization
+  const uint32_t tmem = S.tbase;
+  const int ntiles_cta = A.n_tiles > (int)blockIdx.x
+                             ? (A.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                             : 0;
+  if (w < 8) {
+    // ------------------------------- producers -----------------------------------
+    int fill = 0;  // K-chunk stage fills so far
+    for (int it = 0; it < ntiles_cta; ++it) {
+      const int t = blockIdx.x + it * gridDim.x;
+      const int kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
+      const int npad = n <= 32 ? 32 : ((n + 31) / 32) * 32;
+      const int mb = it & 1;
+      if (it >= 2 && !mbar_wait(&bar_meta_empty[mb], ((it >> 1) - 1) & 1)) { atomicExch(&stop, 1); }
+      if (*(volatile int *)&stop) break;
+      VMeta &m = meta[mb];
+      stage_tile<true>(A, S, t, kb, n, tid, kVProd);
+      if (tid == 0) vmax_s = 0.f;
+      named_sync(1, kVProd);
+      for (int p = tid; p < kTP; p += kVProd) {
+        const int gp = S.inside[p];
+        const double vv = gp >= 0 ? A.v[gp] * A.dV : 0.0;
+        const float hi = (float)vv;
+        vp[p] = make_float2(hi, (float)(vv - (double)hi));
+        atomicMax((int *)&vmax_s, __float_as_int(fabsf(hi)));  // non-negative floats order as ints
       }
-      ea[a] = slice_exp(bnd);
-      eb[a] = slice_exp(bnd * vmax_s * 1.0001f);
-    }
-    // groups of equal mu (keys are sorted): thread-owned accumulation targets
-    if (threadIdx.x == 0) {
-      int g = 0;
-      for (int a = 0; a < n; ++a)
-        if (a == 0 || S.mu[a] != S.mu[a - 1]) gstart[g++] = a;
-      gstart[g] = n;
-      ngroups = g;
-    }
-    __syncthreads();
-    for (int kc = 0; kc < kTP / kKc && ok; ++kc) {
-      // items (entry a, 8 consecutive points of the chunk); rows a >= n are zero
-      for (int q = threadIdx.x; q < kNmax * (kKc / 8); q += blockDim.x) {
-        const int a = q % kNmax, c0 = (q / kNmax) * 8;
-        uint16_t xs[4][8], ws[4][8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int p = kc * kKc + c0 + u;
-          float2 x = (a < n && S.inside[p] >= 0) ? basis_val_df(S, A.rc2f, a, p)
-                                                 : make_float2(0.f, 0.f);
-          float2 wv = df_mul(x, vp[p]);
-          uint16_t s4[4];
-          slice4(x, ea[a], s4);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) xs[k][u] = s4[k];
-          slice4(wv, eb[a], s4);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) ws[k][u] = s4[k];
+      named_sync(1, kVProd);
+      for (int a = tid; a < kNmax; a += kVProd) {
+        float bnd = 0.f;
+        int rk = 0;
+        if (a < n) {
+          float mx = 0.f, my = 0.f, mz = 0.f;
+          for (int s = 0; s < 4; ++s) mx = fmaxf(mx, S.stage[sidx<true>(a, s)].y);
+          for (int s = 4; s < 8; ++s) my = fmaxf(my, S.stage[sidx<true>(a, s)].y);
+          for (int s = 8; s < 16; ++s) mz = fmaxf(mz, S.stage[sidx<true>(a, s)].y);
+          bnd = mx * my * mz * 1.0001f;
+          while (rk < a && S.mu[a - rk - 1] == S.mu[a]) ++rk;  // image rank among equal mu
         }
-        const int off = kmaj_off64(a, c0);
+        m.mu[a] = a < n ? S.mu[a] : 0;
+        m.ea[a] = slice_exp(bnd);
+        m.eb[a] = slice_exp(bnd * vmax_s * 1.0001f);
+        m.rank[a] = rk;
+      }
+      named_sync(1, kVProd);
+      if (tid == 0) {
+        int mr = 0;
+        for (int a = 0; a < n; ++a) mr = max(mr, m.rank[a]);
+        m.maxrank = mr;
+        m.n = n;
+        m.npad = npad;
+      }
+      for (int kc = 0; kc < kTP / kVKc; ++kc, ++fill) {
+        const int s = fill % kVStages, use = fill / kVStages;
+        if (use > 0 && !mbar_wait(&bar_empty[s], (use - 1) & 1)) { atomicExch(&stop, 1); break; }
+        uint8_t *sA = dsm + s * kVStage, *sB = sA + 4 * kVSlice;
+        for (int q = tid; q < npad * (kVKc / 8); q += kVProd) {
+          const int a = q % npad, c0 = (q / npad) * 8;
+          uint16_t xs[4][8], ws[4][8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          uint4 v;
-          v.x = xs[k][0] | (xs[k][1] << 16); v.y = xs[k][2] | (xs[k][3] << 16);
-          v.z = xs[k][4] | (xs[k][5] << 16); v.w = xs[k][6] | (xs[k][7] << 16);
-          *(uint4 *)(sA + k * kChunkBytes + off) = v;
-          if (a < npad) {
-            v.x = ws[k][0] | (ws[k][1] << 16); v.y = ws[k][2] | (ws[k][3] << 16);
-            v.z = ws[k][4] | (ws[k][5] << 16); v.w = ws[k][6] | (ws[k][7] << 16);
-            *(uint4 *)(sB + k * kChunkBytes + off) = v;
+          for (int u = 0; u < 8; ++u) {
+            const int p = kc * kVKc + c0 + u;
+            float2 x = (a < n && S.inside[p] >= 0) ? basis_val_df<true>(S, A.rc2f, a, p)
+                                                   : make_float2(0.f, 0.f);
+            float2 wv = df_mul(x, vp[p]);
+            uint16_t s4[4];
+            slice4(x, m.ea[a], s4);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xs[k][u] = s4[k];
+            slice4(wv, m.eb[a], s4);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ws[k][u] = s4[k];
           }
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t idesc = idesc_bf16(npad);
-        const uint32_t a0 = su32(sA), b0 = su32(sB);
-        const uint32_t sbo = (kKc / 8) * 128;
-        for (int kk = 0; kk < kKc / 16; ++kk) {
-          const uint32_t off = kk * 256;
-          uint64_t X[4], W[4];
+          const int off = kmaj_off32(a, c0);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            X[k] = smem_desc(a0 + k * kChunkBytes + off, sbo);
-            W[k] = smem_desc(b0 + k * kChunkBytes + off, sbo);
+            uint4 v;
+            v.x = xs[k][0] | (xs[k][1] << 16); v.y = xs[k][2] | (xs[k][3] << 16);
+            v.z = xs[k][4] | (xs[k][5] << 16); v.w = xs[k][6] | (xs[k][7] << 16);
+            *(uint4 *)(sA + k * kVSlice + off) = v;
+            v.x = ws[k][0] | (ws[k][1] << 16); v.y = ws[k][2] | (ws[k][3] << 16);
+            v.z = ws[k][4] | (ws[k][5] << 16); v.w = ws[k][6] | (ws[k][7] << 16);
+            *(uint4 *)(sB + k * kVSlice + off) = v;
           }
-          const uint32_t acc = (kc > 0 || kk > 0);
-          mma_bf16(tmem, X[0], W[0], idesc, acc);                 // order 0
-          mma_bf16(tmem + kNmax, X[0], W[1], idesc, acc);         // order 1
-          mma_bf16(tmem + kNmax, X[1], W[0], idesc, 1u);
-          mma_bf16(tmem + 2 * kNmax, X[0], W[2], idesc, acc);     // order 2
-          mma_bf16(tmem + 2 * kNmax, X[1], W[1], idesc, 1u);
-          mma_bf16(tmem + 2 * kNmax, X[2], W[0], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, X[0], W[3], idesc, acc);     // order 3
-          mma_bf16(tmem + 3 * kNmax, X[1], W[2], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, X[2], W[1], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, X[3], W[0], idesc, 1u);
         }
-        mma_commit(&S.mbar);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (kc == 0) mbar_arrive(&bar_meta_full[mb]);  // metadata written before chunk 0 is out
+        mbar_arrive(&bar_full[s]);
       }
-      ok = __syncthreads_and(mbar_wait(&S.mbar, phase)) != 0;
-      phase ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (*(volatile int *)&stop) break;
+      named_sync(1, kVProd);  // the table buffer is reused by the next tile
     }
-    if (!ok) {
-      if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
-      break;
-    }
-    // V_loc[a][b] = 2^(e_a + e_b - 16) (acc0 + (acc1 + (acc2 + acc3/256)/256)/256) as a pair
-    {
-      const int cw = npad / 2;
-      for (int c0 = half * cw; c0 < half * cw + cw; c0 += 16) {
-        float y0[16], y1[16], y2[16], y3[16];
-        tmem_ld16(tmem + lane + c0, y0);
-        tmem_ld16(tmem + lane + kNmax + c0, y1);
-        tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
-        tmem_ld16(tmem + lane + 3 * kNmax + c0, y3);
-        if (ae < n) {
+  } else {
+    // ------------------------- MMA issue and epilogue ------------------------------
+    const int quad = w & 3;
+    const int ae = quad * 32 + (tid & 31);
+    const uint32_t lane = (uint32_t)(quad * 32) << 16;
+    int fill = 0;
+    for (int it = 0; it < ntiles_cta; ++it) {
+      const int mb = it & 1;
+      bool ok = true;
+      if (tid == kVProd) {  // lane 0 of warp 8
+        if (it > 0) ok = mbar_wait(&bar_acc_empty, (it - 1) & 1);
+        if (ok) ok = mbar_wait(&bar_meta_full[mb], (it >> 1) & 1);
+        const int npad = ok ? meta[mb].npad : 32;
+        for (int kc = 0; ok && kc < kTP / kVKc; ++kc) {
+          const int s = (fill + kc) % kVStages, use = (fill + kc) / kVStages;
+          ok = mbar_wait(&bar_full[s], use & 1);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t idesc = idesc_bf16(npad);
+          const uint32_t a0 = su32(dsm + s * kVStage), b0 = a0 + 4 * kVSlice;
+          const uint32_t sbo = (kVKc / 8) * 128;
+          for (int kk = 0; kk < kVKc / 16; ++kk) {
+            const uint32_t off = kk * 256;
+            uint64_t X[4], W[4];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int b = c0 + j;
-            if (b < n) {
-              const int sc = ea[ae] + eb[b] - 16;
-              float lo = (y1[j] + (y2[j] + y3[j] * (1.f / 256.f)) * (1.f / 256.f)) * (1.f / 256.f);
-              float hi = y0[j] + lo;  // fold into a normalized pair
-              lo = lo - (hi - y0[j]);
-              sV[ae * n + b] = make_float2(ldexpf(hi, sc), ldexpf(lo, sc));
+            for (int k = 0; k < 4; ++k) {
+              X[k] = smem_desc(a0 + k * kVSlice + off, sbo);
+              W[k] = smem_desc(b0 + k * kVSlice + off, sbo);
             }
+            const uint32_t acc = (kc > 0 || kk > 0);
+            mma_bf16(tmem, X[0], W[0], idesc, acc);                 // order 0
+            mma_bf16(tmem + kNmax, X[0], W[1], idesc, acc);         // order 1
+            mma_bf16(tmem + kNmax, X[1], W[0], idesc, 1u);
+            mma_bf16(tmem + 2 * kNmax, X[0], W[2], idesc, acc);     // order 2
+            mma_bf16(tmem + 2 * kNmax, X[1], W[1], idesc, 1u);
+            mma_bf16(tmem + 2 * kNmax, X[2], W[0], idesc, 1u);
+            mma_bf16(tmem + 3 * kNmax, X[0], W[3], idesc, acc);     // order 3
+            mma_bf16(tmem + 3 * kNmax, X[1], W[2], idesc, 1u);
+            mma_bf16(tmem + 3 * kNmax, X[2], W[1], idesc, 1u);
+            mma_bf16(tmem + 3 * kNmax, X[3], W[0], idesc, 1u);
+          }
+          mma_commit(&bar_empty[s]);  // the stage is free once these MMAs complete
+        }
+        if (ok) mma_commit(&bar_acc_full);
+        if (!ok) atomicExch(&stop, 1);
+      }
+      fill += kTP / kVKc;
+      __syncwarp();
+      if (*(volatile int *)&stop) break;
+      // all epilogue threads: wait for the accumulators and the tile's metadata
+      ok = mbar_wait(&bar_acc_full, it & 1) && mbar_wait(&bar_meta_full[mb], (it >> 1) & 1);
+      if (!ok) { atomicExch(&stop, 1); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const VMeta &m = meta[mb];
+      const int n = m.n, npad = m.npad;
+      const int ma = ae < n ? m.mu[ae] : 0, ra = ae < n ? m.rank[ae] : -1;
+      // values of row ae, in 16-column chunks; rows of equal mu (images) add into
+      // the same targets, so they take turns by image rank
+      for (int r = 0; r <= m.maxrank; ++r) {
+        for (int c0 = 0; c0 < npad; c0 += 16) {
+          float y0[16], y1[16], y2[16], y3[16];
+          tmem_ld16(tmem + lane + c0, y0);
+          tmem_ld16(tmem + lane + kNmax + c0, y1);
+          tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
+          tmem_ld16(tmem + lane + 3 * kNmax + c0, y3);
+          if (ra == r) {
+            float2 val[16], old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int b = c0 + j;
+              const int sc = m.ea[ae] + m.eb[b < n ? b : 0] - 16;
+              float lo = (y1[j] + (y2[j] + y3[j] * (1.f / 256.f)) * (1.f / 256.f)) * (1.f / 256.f);
+              float hi = y0[j] + lo;
+              lo = lo - (hi - y0[j]);
+              val[j] = make_float2(ldexpf(hi, sc), ldexpf(lo, sc));
+              if (b < n && b >= ae && m.mu[b] == ma && b != ae) {  // both orders of an image pair
+                val[j].x *= 2.f;
+                val[j].y *= 2.f;
+              }
+            }
+            // adjacent columns of equal mu (images) share a target: fold them first
+            bool live[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) live[j] = (c0 + j >= ae && c0 + j < n);
+            if (m.maxrank > 0) {
+#pragma unroll
+              for (int j = 15; j > 0; --j)
+                if (live[j] && live[j - 1] && m.mu[c0 + j] == m.mu[c0 + j - 1]) {
+                  val[j - 1] = df_add(val[j - 1], val[j]);
+                  live[j] = false;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              old[j] = live[j] ? Vpriv[(long)ma * M + m.mu[c0 + j]] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (live[j]) Vpriv[(long)ma * M + m.mu[c0 + j]] = df_add(old[j], val[j]);
           }
         }
+        if (m.maxrank > 0) named_sync(2, kVEpi);
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&bar_acc_empty);
+      mbar_arrive(&bar_meta_empty[mb]);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    // one thread per group u of equal mu: targets (mu_u, mu_w) with w >= u, summed
-    // over the ordered entry pairs of the two groups (V_loc is symmetric)
-    for (int u = threadIdx.x; u < ngroups; u += blockDim.x) {
-      const int mu = S.mu[gstart[u]];
-      for (int wg = u; wg < ngroups; ++wg) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int a = gstart[u]; a < gstart[u + 1]; ++a)
-          for (int b = gstart[wg]; b < gstart[wg + 1]; ++b) acc = df_add(acc, sV[a * n + b]);
-        float2 *dst = Vpriv + (long)mu * M + S.mu[gstart[wg]];
-        *dst = df_add(*dst, acc);
-      }
-    }
-    __syncthreads();
   }
+  if (*(volatile int *)&stop && tid == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
   tmem_free(S);
 }
 
@@ -651,17 +746,17 @@ __global__ void tables_f32_kernel(const double *sq, const double *ex, const doub
 
 // per grid point: exponent e_p with max_a |X_pa| < 2^(e_p - 1) (same FP32 values
 // as the density kernel computes)
-__global__ void __launch_bounds__(kTcThreads) rowexp_kernel(TcArgs A, signed char *rowexp) {
+__global__ void __launch_bounds__(256) rowexp_kernel(TcArgs A, signed char *rowexp) {
   __shared__ TileShared S;
   for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
     const int kb = A.tile_ptr[t], n = A.tile_ptr[t + 1] - kb;
-    stage_tile(A, S, t, kb, min(n, kNmax));
+    stage_tile<false>(A, S, t, kb, min(n, kNmax), threadIdx.x, blockDim.x);
     __syncthreads();
     for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
       const int gp = S.inside[p];
       if (gp < 0) continue;
       float mx = 0.f;
-      for (int a = 0; a < min(n, kNmax); ++a) mx = fmaxf(mx, fabsf(basis_val(S, A.rc2f, a, p)));
+      for (int a = 0; a < min(n, kNmax); ++a) mx = fmaxf(mx, fabsf(basis_val<false>(S, A.rc2f, a, p)));
       rowexp[gp] = (signed char)(mx > 0.f ? ilogbf(mx) + 2 : 0);
     }
     __syncthreads();
@@ -735,7 +830,7 @@ cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s) {
 
 cudaError_t launch_rowexp(etdm_handle *h, cudaStream_t s) {
   TcArgs a = tc_args(h);
-  rowexp_kernel<<<std::min(h->n_tiles_tc, 8 * h->num_sms), kTcThreads, 0, s>>>(a, h->d_rowexp);
+  rowexp_kernel<<<std::min(h->n_tiles_tc, 8 * h->num_sms), 256, 0, s>>>(a, h->d_rowexp);
   return cudaGetLastError();
 }
 
@@ -749,12 +844,12 @@ cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
-  rho_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kTcThreads, sm, s>>>(tc_args(h));
+  rho_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kRhoThreads, sm, s>>>(tc_args(h));
   return cudaGetLastError();
 }
 
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = 8 * (size_t)kChunkBytes;
+  const size_t sm = (size_t)kVStages * kVStage;
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -762,7 +857,7 @@ cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
   const size_t MM = (size_t)h->M * h->M;
   e = cudaMemsetAsync(h->d_Vpriv, 0, (size_t)copies * MM * sizeof(float2), s);
   if (e != cudaSuccess) return e;
-  vmat_tc_kernel<<<copies, kTcThreads, sm, s>>>(tc_args(h));
+  vmat_tc_kernel<<<copies, kVThreads, sm, s>>>(tc_args(h));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   vpriv_reduce_kernel<<<256, 256, 0, s>>>(h->d_Vpriv, copies, h->M, h->d_Vfin);
