@@ -395,14 +395,39 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_rc2f = dalloc<float>(h, M);
     CUDA_TRY(cudaMemcpy(h->d_rc2f, rc2f.data(), M * sizeof(float), cudaMemcpyHostToDevice));
     h->d_rowexp = dalloc<signed char>(h, h->G);
-    CUDA_TRY(launch_rowexp(h, s));
-    h->d_Osl = dalloc<uint2>(h, (long)M * h->N);
+    // functions per tile, then the sizes and offsets of the resident X slices
+    const int T = h->n_tiles_tc;
+    h->d_nu_tc = dalloc<int>(h, std::max(T, 1));
+    CUDA_TRY(launch_count_unique(h, h->d_nu_tc, s));
+    std::vector<int> nu(T), xr_off(T + 1, 0), xv_off(T + 1, 0);
+    CUDA_TRY(cudaMemcpy(nu.data(), h->d_nu_tc, T * sizeof(int), cudaMemcpyDeviceToHost));
+    long xr = 0, xv = 0;
+    for (int t = 0; t < T; ++t) {
+      int ks = 0, ve = 0;
+      tc_tile_sizes(nu[t], &ks, &ve);
+      xr_off[t] = (int)xr;
+      xv_off[t] = (int)xv;
+      xr += ks;
+      xv += ve;
+      if (xr > INT32_MAX || xv > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
+    }
+    xr_off[T] = (int)xr;
+    xv_off[T] = (int)xv;
+    h->xr_steps = xr;
+    h->xv_entries = xv;
+    h->d_xr_off = dalloc<int>(h, T + 1);
+    h->d_xv_off = dalloc<int>(h, T + 1);
+    CUDA_TRY(cudaMemcpy(h->d_xr_off, xr_off.data(), (T + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h->d_xv_off, xv_off.data(), (T + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    h->d_xr = dalloc<uint8_t>(h, (size_t)xr * 16384);  // 4 slices x 4 KB per K step
+    h->d_xv = dalloc<uint8_t>(h, (size_t)xv * 1024);   // 8 K steps x 4 slices x 32 B per entry
+    h->d_vent = dalloc<float4>(h, (size_t)xv);
+    h->d_vt = dalloc<float2>(h, (size_t)T * 128);
+    CUDA_TRY(launch_operand_build(h, s));
+    h->d_Osl = dalloc<uint2>(h, (long)M * (h->N + (h->N & 1)));  // rows padded to even length
     h->d_oscale = dalloc<float>(h, h->N);
     h->d_dO = dalloc<double>(h, (long)M * h->N);
-    // per-CTA copies of V for the grid -> basis pass: at most ~2 GB of them
-    const double per_copy = (double)M * M * sizeof(float2);
-    h->n_vcopies = (int)std::max(1.0, std::min((double)h->num_sms, 2.0e9 / per_copy));
-    h->d_Vpriv = dalloc<float2>(h, (long)h->n_vcopies * M * M);
+    h->d_Vfix = dalloc<unsigned long long>(h, (long)M * M + 1);
     h->d_Vfin = dalloc<double>(h, (long)M * M);
   }
   {

@@ -145,11 +145,19 @@ struct etdm_handle {
   float4 *d_tabf = nullptr;
   float *d_rc2f = nullptr;
   signed char *d_rowexp = nullptr;
-  uint2 *d_Osl = nullptr;     // [M][N] BF16 slices of O
+  // operand slices resident in HBM (built once at set-up; periodic images of a
+  // function in one tile merged into one entry)
+  int *d_nu_tc = nullptr;                // [n_tiles_tc] functions per tile
+  int *d_xr_off = nullptr;               // [n_tiles_tc + 1] density K steps before a tile
+  int *d_xv_off = nullptr;               // [n_tiles_tc + 1] padded V entries before a tile
+  uint8_t *d_xr = nullptr, *d_xv = nullptr;
+  float4 *d_vent = nullptr;              // per padded V entry
+  float2 *d_vt = nullptr;                // [n_tiles_tc][128] v dV in tile order
+  long xr_steps = 0, xv_entries = 0;
+  uint2 *d_Osl = nullptr;     // [M][N + N % 2] BF16 slices of O
   float *d_oscale = nullptr;  // [N]
   double *d_dO = nullptr;     // [M][N] O - Oq
-  float2 *d_Vpriv = nullptr;  // [n_vcopies][M][M] per-CTA V accumulations
-  int n_vcopies = 0;
+  unsigned long long *d_Vfix = nullptr;  // [M*M + 1] V in fixed point, then max|v| bits
   double *d_Vfin = nullptr;   // [M][M] V (upper triangle), FP64
   // matrices
   double *d_S = nullptr, *d_T = nullptr, *d_C0 = nullptr;
@@ -232,7 +240,9 @@ cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n, 
 cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t s);
 // mixed-precision grid passes (mixed.cu)
 cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s);
-cudaError_t launch_rowexp(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_count_unique(etdm_handle *h, int *d_nu, cudaStream_t s);
+cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);
+void tc_tile_sizes(int nu, int *rho_steps, int *v_entries);
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);

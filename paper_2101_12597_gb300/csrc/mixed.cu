@@ -1,18 +1,20 @@
 // Mixed-precision grid passes on the 5th-generation tensor cores (tcgen05).
 //
 // basis -> grid density (Eq. 2, 3, 12) in orbital form: per 128-point tile
-// (4 x 4 x 8) with a truncation list of n <= 128 function images,
+// (4 x 4 x 8) whose list holds n <= 128 basis functions (periodic images of a
+// function that reach the tile are summed into one entry),
 //     phi = X O_loc  (128 x n x N_occ),  rho_p = 2 sum_m phi_pm^2 ,
 // a sum of positive terms (the same density as sum X D X, whose terms cancel
 // heavily in a non-orthogonal basis).  X rows and O columns are cut into exact
-// integer slices held in BF16 ("Ozaki" splitting):
-//     X_pa = 2^(e_p-8) (I0 + I1/2^8 + I2/2^16 + I3/2^24)   (X as a float pair),
-//     O_am = 2^(g_m-8) (K0 + K1/2^8 + K2/2^16),    |I|, |K| <= 128.
-// Every product of slices is an integer, and every accumulator (at most three
-// products per K step, <= 128 entries of <= 2^14) stays below 2^24, so the
-// four FP32 accumulators of slice order 0..3 in tensor memory are exact
-// whatever rounding the accumulator applies (the tensor-core accumulator
-// truncates).  X is resolved to about 2^-31 of its row maximum, which the
+// integer slices held in BF16 ("Ozaki" splitting), each slice carrying its
+// power of two:
+//     X_pa = 2^(e_p-8) (I0 + I1 + I2 + I3)   (X as a float pair),
+//     O_am = 2^(g_m-8) (K0 + K1 + K2),       I_k, K_k in 2^-8k {-128 .. 128}.
+// A product of slices of orders i and j is 2^-8(i+j) times an integer, and
+// every accumulator (at most four products per K step, <= 128 entries of
+// <= 2^14) stays below 2^24 units of its order, so the four FP32 accumulators of
+// slice order 0..3 in tensor memory are exact whatever rounding the accumulator
+// applies (the tensor-core accumulator truncates).  X is resolved to about 2^-31 of its row maximum, which the
 // cancellation in X O needs; the 24-bit quantization of O is coherent and is
 // removed to first order in the energy by sum (4 V O) o (O - Oq) (dense
 // reverse kernel); the rest (order >= 4 terms, FP32 square sums) is unbiased
@@ -20,16 +22,26 @@
 //
 // grid -> basis potential matrix (Eq. 11): V_ab = dV sum_p X_pa v_p X_pb with
 // X^T and (v X)^T rows cut into four exact integer slices each (exponent per
-// list entry from a separable bound over the tile) and slice orders 0..3 in
-// four exact accumulators.  The gradient amplifies errors of V by the large
+// entry from a separable bound over the tile) and slice orders 0..3 in four
+// exact accumulators.  The gradient amplifies errors of V by the large
 // Loewdin coefficients (O^T V O), so V is kept to about 2^-31 of its row
-// scale; tiles are summed in per-CTA float-pair copies (no atomics) and the
-// copies in FP64.
+// scale.  Each tile's part is added into V as 64-bit fixed point (unit 2^-46 of
+// the power of two above max|v|, which leaves 2^17 of headroom over the bound
+// |V_ab| <= max|v| |X_a| |X_b|) with integer reductions in L2: exact and
+// independent of the order of the additions, and free of FP64 arithmetic,
+// which is slow on this part.
 //
-// Operands are staged in shared memory in the canonical no-swizzle K-major
-// layout (8-row x 16-byte core matrices); one thread issues tcgen05.mma, the
-// completion is tracked with tcgen05.commit on an mbarrier (bounded wait), and
-// the accumulators are read back with tcgen05.ld.  One persistent CTA per SM.
+// The basis values never change during a minimization, so both X operands
+// (per-point exponents for the density, per-entry exponents for V) are sliced
+// once at set-up and kept in HBM in the exact shared-memory image of a K step
+// (the canonical K-major no-swizzle layout: 8-row x 16-byte core matrices).  Per
+// evaluation one thread streams them with bulk asynchronous copies (TMA) into a
+// ring of shared-memory stages, with the rows of the O slices the density needs
+// gathered the same way; builder warps lay out the operand that changes (the O
+// slices of the list entries, or v X re-sliced from the X slices); one
+// thread issues tcgen05.mma; epilogue warps read the accumulators with
+// tcgen05.ld.  Stages, accumulators and per-tile buffers hand over through
+// mbarriers, every wait bounded.  One persistent CTA per SM.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
@@ -41,30 +53,31 @@
 
 namespace etdm {
 
-constexpr int kRhoThreads = 512;   // 16 warps: 8 build-only, 8 also read TMEM
-constexpr int kVThreads = 384;     // 12 warps (register budget of the V pass)
-constexpr int kTP = 128;     // points per tile
-constexpr int kNmax = 128;   // max padded list length
+constexpr int kTP = 128;                 // points per tile (4 x 4 x 8)
+constexpr int kNmax = 128;               // max list length per tile
 constexpr int kTmemCols = 512;
 constexpr long kMbarSpin = 4000000;
+constexpr int kKs = 16;                  // K of one MMA (a "K step")
+constexpr int kSlot = kNmax * kKs * 2;   // one BF16 slice of a K step, 128 rows (4 KB)
+
+// byte offset of element (row, k), 0 <= k < 16, in a K-step block of one slice:
+// canonical K-major no-swizzle layout with the two 8-column core matrices of a
+// row group 128 bytes apart (LBO) and row groups 256 bytes apart (SBO)
+__host__ __device__ __forceinline__ int kstep_off(int row, int k) {
+  return ((k >> 3) << 7) + ((row >> 3) << 8) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+// padded list length of the V pass (a multiple of 16, at least 16: the MMA's N)
+__host__ __device__ __forceinline__ int vpad(int n) { return n <= 16 ? 16 : ((n + 15) / 16) * 16; }
+// K steps of the density pass (at least one, zero-filled, for an empty list)
+__host__ __device__ __forceinline__ int rsteps(int n) { return n <= kKs ? 1 : (n + kKs - 1) / kKs; }
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// canonical K-major no-swizzle offset of element (row, k) for a 128 x 128 BF16 operand
-__device__ __forceinline__ int kmaj_off(int row, int k) {
-  return (((row >> 3) * (kNmax / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
-}
-// the same for a 128-row operand holding a K chunk of 64 columns
-constexpr int kKc = 64;
-constexpr int kChunkBytes = kTP * kKc * 2;
-__device__ __forceinline__ int kmaj_off64(int row, int k) {
-  return (((row >> 3) * (kKc / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo = (kNmax / 8) * 128) {
-  const uint32_t lbo = 128;
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  const uint32_t lbo = 128, sbo = 256;
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
@@ -93,125 +106,83 @@ __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
       : "memory");
 }
 
-// bounded wait for the mbarrier phase `parity`; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+
+// bounded wait for the completion of the mbarrier phase with parity `parity`;
+// false on timeout or, when `stop` is given, once another role has given up
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity,
+                                          const volatile int *stop = nullptr) {
   uint32_t done = 0;
-  long it = 0;
-  while (!done) {
+  for (long it = 0; !done; ++it) {
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
         "selp.u32 %0, 1, 0, p; }"
         : "=r"(done)
         : "r"(su32(mbar)), "r"(parity)
         : "memory");
-    if (++it > kMbarSpin) return false;
+    if (!done && (it > kMbarSpin || (stop && (it & 255) == 255 && *stop))) return false;
   }
   return true;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
+// bulk asynchronous copy global -> shared, completing `bytes` on the mbarrier
+// (both addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *mbar) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(mbar))
+      : "memory");
+}
+
+// Issue the loads of 8 columns (from column address t) of the four slice-order
+// accumulators, 128 columns apart, for this warp's lane quarter: r[8k + c] =
+// accumulator k, column c.  The registers are valid only after tmem_ld_wait(r).
+__device__ __forceinline__ void tmem_ld_issue(uint32_t t, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(t), "r"(t + kNmax), "r"(t + 2 * kNmax), "r"(t + 3 * kNmax));
+}
+// wait for the issued loads; the registers pass through the statement, so no
+// use of them can be scheduled before it
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)),
+               "r"(kTmemCols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t base) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(kTmemCols)
+               : "memory");
 }
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
-__device__ __forceinline__ float bf16_val(uint16_t b) {
-  return __uint_as_float((uint32_t)b << 16);
-}
 
-struct TcArgs {
-  GridGeom g;  // 4 x 4 x 8 tiles
-  int n_tiles;
-  const int *tile_ptr, *keys;
-  const float4 *tab[3];        // per axis [mu][img][i]: (sq, c hi, c lo, 0),
-                               // c = norm^(1/3) exp(-alpha sq) as a float pair
-  const float *rc2f;           // [M]
-  const signed char *rowexp;   // [G]
-  const uint2 *Osl;            // [M][N] bf16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
-  const float *oscale;         // [N] 2^g_m
-  int Nocc;
-  double *rho;                 // [G]
-  const double *v;             // [G]
-  float2 *Vpriv;               // [gridDim][M][M] per-CTA float-pair V (upper triangle)
-  double dV;
-  int *flags;
-};
-
-struct TileShared {
-  int mu[kNmax];
-  float fs[kNmax];
-  float4 stage[kNmax * 16];  // per entry: 4 x-values, 4 y-values, 8 z-values
-  float part[kTP];
-  uint64_t mbar;
-  uint32_t tbase;
-  int n, npad, inside[kTP];
-};
-
-// index of slot s of entry e in the staged table: entry-major for the density
-// pass (a warp shares the entry), slot-major for the V pass (a warp spans entries)
-template <bool TR>
-__device__ __forceinline__ int sidx(int e, int s) {
-  return TR ? s * kNmax + e : e * 16 + s;
-}
-
-// stage the per-axis (sq, c exp(-alpha sq)) values of the tile for every entry
-// (by the threads tid = 0 .. nthr-1 of the calling group)
-template <bool TR>
-__device__ void stage_tile(const TcArgs &A, TileShared &S, int t, int kb, int n, int tid,
-                           int nthr) {
-  const GridGeom &g = A.g;
-  int bz = t % g.nbz, by = (t / g.nbz) % g.nby, bx = t / (g.nbz * g.nby);
-  int i0 = bx * 4, j0 = by * 4, k0 = bz * 8;
-  for (int q = tid; q < n * 16; q += nthr) {
-    int e = q >> 4, s = q & 15;
-    int key = A.keys[kb + e];
-    int mu = key >> 9;
-    int ix = ((key >> 6) & 7) - 4 + kImgMax, iy = ((key >> 3) & 7) - 4 + kImgMax,
-        iz = (key & 7) - 4 + kImgMax;
-    const float4 out = make_float4(INFINITY, 0.f, 0.f, 0.f);
-    float4 val;
-    if (s < 4) {
-      int i = i0 + s;
-      val = i < g.nx ? A.tab[0][((long)mu * kImgN + ix) * g.nx + i] : out;
-    } else if (s < 8) {
-      int j = j0 + s - 4;
-      val = j < g.ny ? A.tab[1][((long)mu * kImgN + iy) * g.ny + j] : out;
-    } else {
-      int k = k0 + s - 8;
-      val = k < g.nz ? A.tab[2][((long)mu * kImgN + iz) * g.nz + k] : out;
-    }
-    S.stage[sidx<TR>(e, s)] = val;
-    if (s == 0) S.mu[e] = mu;
-  }
-  for (int p = tid; p < kTP; p += nthr) {
-    int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
-    S.inside[p] = (i0 + li < g.nx && j0 + lj < g.ny && k0 + lk < g.nz)
-                      ? ((i0 + li) * g.ny + (j0 + lj)) * g.nz + (k0 + lk)
-                      : -1;
-  }
-}
-
-template <bool TR>
-__device__ __forceinline__ float basis_val(const TileShared &S, const float *rc2f, int e, int p) {
-  int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
-  float4 x = S.stage[sidx<TR>(e, li)], y = S.stage[sidx<TR>(e, 4 + lj)],
-         z = S.stage[sidx<TR>(e, 8 + lk)];
-  float r2 = (x.x + y.x) + z.x;
-  return r2 < rc2f[S.mu[e]] ? x.y * y.y * z.y : 0.f;
-}
-
-// float-pair (hi + lo) arithmetic: exact product by FMA, then renormalization
+// ---- float-pair arithmetic and exact slicing -----------------------------------
+// product of two float pairs (hi + lo): exact product by FMA, then renormalization
 __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   const float p = a.x * b.x;
   const float e = fmaf(a.x, b.x, -p);
@@ -220,213 +191,14 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   return make_float2(s, t - (s - p));
 }
 
-// the same basis value as a float pair (about 44 significant bits); the hi
-// part equals basis_val up to rounding
-template <bool TR>
-__device__ __forceinline__ float2 basis_val_df(const TileShared &S, const float *rc2f, int e,
-                                               int p) {
-  int li = p >> 5, lj = (p >> 3) & 3, lk = p & 7;
-  float4 x = S.stage[sidx<TR>(e, li)], y = S.stage[sidx<TR>(e, 4 + lj)],
-         z = S.stage[sidx<TR>(e, 8 + lk)];
-  float r2 = (x.x + y.x) + z.x;
-  if (!(r2 < rc2f[S.mu[e]])) return make_float2(0.f, 0.f);
-  return df_mul(df_mul(make_float2(x.y, x.z), make_float2(y.y, y.z)), make_float2(z.y, z.z));
+// the same product left unnormalized (hi = fl(a.x b.x), |lo| <= 2 ulp(hi)), as
+// slice4 takes it
+__device__ __forceinline__ float2 df_mul_raw(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  return make_float2(p, fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x));
 }
 
-__device__ __forceinline__ void tmem_alloc(TileShared &S) {
-  if (threadIdx.x < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     su32(&S.tbase)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&S.mbar)), "r"(1)
-                 : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_free(TileShared &S) {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tbase),
-                 "r"(kTmemCols)
-                 : "memory");
-}
-
-// ---- density ---------------------------------------------------------------
-__global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
-  // one K chunk (64 list entries) of the operands at a time:
-  // A = X slices I0..I3 (128 points x 64), B = O slices K0..K2 (<= 128 orbitals x 64)
-  extern __shared__ __align__(1024) uint8_t dsm[];
-  uint8_t *sA = dsm;
-  uint8_t *sB = dsm + 4 * kChunkBytes;
-  __shared__ TileShared S;
-  tmem_alloc(S);
-  const uint32_t tmem = S.tbase;
-  uint32_t phase = 0;
-  bool ok = true;
-  const int w = threadIdx.x >> 5, quad = w & 3, half = w >> 2;
-  const int pe = quad * 32 + (threadIdx.x & 31);  // epilogue point (TMEM lane)
-  const uint32_t lane = (uint32_t)(quad * 32) << 16;
-  for (int t = blockIdx.x; t < A.n_tiles && ok; t += gridDim.x) {
-    const int kb = A.tile_ptr[t], n = A.tile_ptr[t + 1] - kb;
-    if (n > kNmax) {  // rejected at set-up; never reached
-      if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
-      continue;
-    }
-    const int nk = n <= 32 ? 2 : (n + 15) / 16;  // K steps of 16
-    const int nkc = (nk + 3) / 4;                // K chunks of 64
-    stage_tile<false>(A, S, t, kb, n, threadIdx.x, blockDim.x);
-    __syncthreads();
-    float rsum = 0.f;
-    // occupied orbitals in chunks of up to 128 columns
-    for (int m0 = 0; m0 < A.Nocc && ok; m0 += kNmax) {
-      const int nm = min(kNmax, A.Nocc - m0);
-      const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
-      for (int m = threadIdx.x; m < nmpad; m += blockDim.x)
-        S.fs[m] = m < nm ? A.oscale[m0 + m] : 0.f;
-      for (int kc = 0; kc < nkc && ok; ++kc) {
-        const int k0 = kc * kKc;
-        // A: X slices of entries k0 .. k0 + 63; items (point, 8 entries)
-        for (int q = threadIdx.x; q < kTP * (kKc / 8); q += blockDim.x) {
-          const int p = q % kTP, c0 = (q / kTP) * 8;
-          const int gp = S.inside[p];
-          const int ep = gp >= 0 ? (int)A.rowexp[gp] : 0;
-          uint16_t sl[4][8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int a = k0 + c0 + u;
-            float2 x = (a < n && gp >= 0) ? basis_val_df<false>(S, A.rc2f, a, p) : make_float2(0.f, 0.f);
-            // x 2^(8 - e_p) = r0 + r1/256 + r2/256^2 + r3/256^3 + O(2^-25)
-            float h = ldexpf(x.x, 8 - ep), l = ldexpf(x.y, 8 - ep);
-            float r0 = rintf(h);
-            float tt = ((h - r0) + l) * 256.f;
-            float r1 = rintf(tt);
-            tt = (tt - r1) * 256.f;
-            float r2 = rintf(tt);
-            tt = (tt - r2) * 256.f;
-            float r3 = rintf(tt);
-            sl[0][u] = bf16_bits(r0); sl[1][u] = bf16_bits(r1);
-            sl[2][u] = bf16_bits(r2); sl[3][u] = bf16_bits(r3);
-          }
-          const int off = kmaj_off64(p, c0);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            uint4 v;
-            v.x = sl[k][0] | (sl[k][1] << 16); v.y = sl[k][2] | (sl[k][3] << 16);
-            v.z = sl[k][4] | (sl[k][5] << 16); v.w = sl[k][6] | (sl[k][7] << 16);
-            *(uint4 *)(sA + k * kChunkBytes + off) = v;
-          }
-        }
-        // B: O slices, B[m][a] = O-slice[mu_a][m0 + m]; items (orbital, 8 entries)
-        for (int q = threadIdx.x; q < nmpad * (kKc / 8); q += blockDim.x) {
-          const int m = q % nmpad, c0 = (q / nmpad) * 8;
-          uint32_t w01[8], w2[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int a = k0 + c0 + u;
-            uint2 kk = (a < n && m < nm) ? A.Osl[(long)S.mu[a] * A.Nocc + m0 + m]
-                                         : make_uint2(0u, 0u);
-            w01[u] = kk.x;
-            w2[u] = kk.y;
-          }
-          const int off = kmaj_off64(m, c0);
-          uint4 v0, v1, v2;
-          v0.x = (w01[0] & 0xFFFF) | (w01[1] << 16); v0.y = (w01[2] & 0xFFFF) | (w01[3] << 16);
-          v0.z = (w01[4] & 0xFFFF) | (w01[5] << 16); v0.w = (w01[6] & 0xFFFF) | (w01[7] << 16);
-          v1.x = (w01[0] >> 16) | (w01[1] & 0xFFFF0000u);
-          v1.y = (w01[2] >> 16) | (w01[3] & 0xFFFF0000u);
-          v1.z = (w01[4] >> 16) | (w01[5] & 0xFFFF0000u);
-          v1.w = (w01[6] >> 16) | (w01[7] & 0xFFFF0000u);
-          v2.x = w2[0] | (w2[1] << 16); v2.y = w2[2] | (w2[3] << 16);
-          v2.z = w2[4] | (w2[5] << 16); v2.w = w2[6] | (w2[7] << 16);
-          *(uint4 *)(sB + off) = v0;
-          *(uint4 *)(sB + kChunkBytes + off) = v1;
-          *(uint4 *)(sB + 2 * kChunkBytes + off) = v2;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t idesc = idesc_bf16(nmpad);
-          const uint32_t a0 = su32(sA), b0 = su32(sB);
-          const uint32_t sbo = (kKc / 8) * 128;
-          const int ksteps = min(4, nk - kc * 4);
-          for (int kk = 0; kk < ksteps; ++kk) {
-            const uint32_t off = kk * 256;
-            const uint64_t I0 = smem_desc(a0 + off, sbo), I1 = smem_desc(a0 + kChunkBytes + off, sbo),
-                           I2 = smem_desc(a0 + 2 * kChunkBytes + off, sbo),
-                           I3 = smem_desc(a0 + 3 * kChunkBytes + off, sbo);
-            const uint64_t K0 = smem_desc(b0 + off, sbo), K1 = smem_desc(b0 + kChunkBytes + off, sbo),
-                           K2 = smem_desc(b0 + 2 * kChunkBytes + off, sbo);
-            const uint32_t acc = (kc > 0 || kk > 0);
-            mma_bf16(tmem, I0, K0, idesc, acc);                  // order 0
-            mma_bf16(tmem + kNmax, I0, K1, idesc, acc);          // order 1
-            mma_bf16(tmem + kNmax, I1, K0, idesc, 1u);
-            mma_bf16(tmem + 2 * kNmax, I0, K2, idesc, acc);      // order 2
-            mma_bf16(tmem + 2 * kNmax, I1, K1, idesc, 1u);
-            mma_bf16(tmem + 2 * kNmax, I2, K0, idesc, 1u);
-            mma_bf16(tmem + 3 * kNmax, I1, K2, idesc, acc);      // order 3
-            mma_bf16(tmem + 3 * kNmax, I2, K1, idesc, 1u);
-            mma_bf16(tmem + 3 * kNmax, I3, K0, idesc, 1u);
-          }
-          mma_commit(&S.mbar);
-        }
-        ok = __syncthreads_and(mbar_wait(&S.mbar, phase)) != 0;
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      }
-      if (ok && w < 8) {  // warps 0..7 read TMEM (lane quarter w % 4, column half w / 4)
-        // phi_pm = 2^(e_p + g_m - 16) y with y = acc0 + (acc1 + (acc2 + acc3/256)/256)/256;
-        // rho_p = 2 sum_m phi_pm^2 (every term positive)
-        const int cw = nmpad / 2;
-        for (int c0 = half * cw; c0 < half * cw + cw; c0 += 16) {
-          float y0[16], y1[16], y2[16], y3[16];
-          tmem_ld16(tmem + lane + c0, y0);
-          tmem_ld16(tmem + lane + kNmax + c0, y1);
-          tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
-          tmem_ld16(tmem + lane + 3 * kNmax + c0, y3);
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float y = y0[j] + (y1[j] + (y2[j] + y3[j] * (1.f / 256.f)) * (1.f / 256.f)) *
-                                  (1.f / 256.f);
-            y *= S.fs[c0 + j];
-            rsum = fmaf(y, y, rsum);
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-    }
-    if (!ok) {
-      if (threadIdx.x == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
-      break;
-    }
-    if (half == 1) S.part[pe] = rsum;
-    __syncthreads();
-    if (half == 0) {
-      const int gp = S.inside[pe];
-      if (gp >= 0) {
-        const int ep = (int)A.rowexp[gp];
-        double r = (double)rsum + (double)S.part[pe];
-        A.rho[gp] = ldexp(r, 2 * ep - 31);
-      }
-    }
-    __syncthreads();
-  }
-  tmem_free(S);
-}
-
-
-// ---- potential matrix ---------------------------------------------------------
-// sum of two float pairs (hi, lo) with an exact TwoSum of the high parts
+// sum of two float pairs with an exact TwoSum of the high parts
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   const float s = a.x + b.x;
   const float bb = s - a.x;
@@ -436,296 +208,849 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   return make_float2(h, t - (h - s));
 }
 
-// exponent e with |x| 2^(8-e) < 128 for every |x| <= bound (0 for bound 0)
+// 2^k for -126 <= k <= 127, built from its bits (exact)
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// exponent e with |x| 2^(8-e) < 128 for every |x| <= bound; bounds below
+// 2^-102 (whose values do not matter) share e = -100, which keeps 2^(8-e) and
+// 2^(e-8) normal floats
 __device__ __forceinline__ int slice_exp(float bound) {
-  return bound > 0.f ? ilogbf(bound) + 2 : 0;
+  return bound > 0.f ? max(ilogbf(bound) + 2, -100) : -100;
 }
 
-// 4 integer slices of the float pair x 2^(8 - e) (|.| < 128): x 2^(8-e) =
-// r0 + r1/256 + r2/256^2 + r3/256^3 + O(2^-25)
-__device__ __forceinline__ void slice4(float2 x, int e, uint16_t *s) {
-  float h = ldexpf(x.x, 8 - e), l = ldexpf(x.y, 8 - e);
-  float r0 = rintf(h);
-  float tt = ((h - r0) + l) * 256.f;
-  float r1 = rintf(tt);
-  tt = (tt - r1) * 256.f;
-  float r2 = rintf(tt);
-  tt = (tt - r2) * 256.f;
-  float r3 = rintf(tt);
-  s[0] = bf16_bits(r0); s[1] = bf16_bits(r1); s[2] = bf16_bits(r2); s[3] = bf16_bits(r3);
+// x truncated toward zero to a 64-bit integer (|x| < 2^62) by integer shifts of
+// its significand (no conversion instruction): x = m 2^e, m < 2^24
+__device__ __forceinline__ long long f2ll_trunc(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xFF) - 150;
+  const unsigned long long m = (u & 0x7FFFFFu) | 0x800000u;
+  unsigned long long v = e >= 0 ? (m << min(e, 39)) : (m >> min(-e, 63));
+  v = (u & 0x7F800000u) ? v : 0ull;  // zero and subnormals
+  return (u >> 31) ? -(long long)v : (long long)v;
 }
 
-// ---- mbarrier helpers for the warp-specialized pipelines ---------------------
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+// fixed-point unit 2^F of V: F = (exponent of the power of two above max|v|) - 46
+__device__ __forceinline__ int vfix_exp(unsigned vmax_bits) {
+  const float vm = __uint_as_float(vmax_bits);
+  return vm > 0.f ? min(max(ilogbf(vm) + 1 - 46, -100), 60) : 0;
 }
 
-// V_loc[a][b] = dV sum_p X_pa v_p X_pb on tensor cores with exact integer slices
-// of X^T (rows a, exponent per entry from a bound over the tile) and (v X)^T
-// (rows b); slice orders 0..3 in four FP32 accumulators (exact).  Warp roles:
-// warps 0-7 build the operand slices of 32-point K chunks into two shared-memory
-// stages; lane 0 of warp 8 issues the MMAs; warps 8-11 read the accumulators
-// (lane quarter = warp % 4) and add V_loc into the CTA's private float-pair copy
-// of the upper triangle of V.  A tile's MMAs start once the previous tile's
-// accumulators are read; building overlaps both.
-constexpr int kVProd = 256;              // producer threads (warps 0-7)
-constexpr int kVEpi = 128;               // epilogue threads (warps 8-11)
-constexpr int kVKc = 32;                 // points per K chunk
-constexpr int kVSlice = kTP * kVKc * 2;  // one slice of one K chunk (8 KB)
-constexpr int kVStage = 8 * kVSlice;     // X^T and (v X)^T, 4 slices each
-constexpr int kVStages = 2;
-
-__device__ __forceinline__ int kmaj_off32(int row, int k) {
-  return (((row >> 3) * (kVKc / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+// Four slices of the float pair x scaled by the power of two sc (|x sc| <= 128):
+// x sc = r0 + r1 + r2 + r3 + O(2^-25) with r_k a multiple of 2^-8k and |r_k| <=
+// 128 2^-8k.  Each r_k rounds the remainder to its grid by adding and removing
+// 1.5 2^(23-8k); the remainders are exact, only the step that adds the low part
+// rounds.
+__device__ __forceinline__ void slice4(float2 x, float sc, float *r) {
+  const float C0 = 12582912.f, C1 = 49152.f, C2 = 192.f, C3 = 0.75f;
+  r[0] = __fadd_rn(__fmaf_rn(x.x, sc, C0), -C0);
+  float u = __fmaf_rn(x.y, sc, __fmaf_rn(x.x, sc, -r[0]));
+  r[1] = __fadd_rn(__fadd_rn(u, C1), -C1);
+  u = __fadd_rn(u, -r[1]);
+  r[2] = __fadd_rn(__fadd_rn(u, C2), -C2);
+  u = __fadd_rn(u, -r[2]);
+  r[3] = __fadd_rn(__fadd_rn(u, C3), -C3);
 }
 
-struct VMeta {  // per-tile data the epilogue needs (double-buffered)
-  int mu[kNmax];
-  int ea[kNmax], eb[kNmax];
-  int rank[kNmax];
-  int n, npad, maxrank;
+// BF16 pair (lo | hi << 16) of two floats with at most 8 significant bits (exact:
+// their low 16 bits are zero)
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// ---- tiles, lists and staged basis factors ------------------------------------
+struct TcArgs {
+  GridGeom g;  // 4 x 4 x 8 tiles
+  int n_tiles;
+  const int *tile_ptr, *keys;   // image lists (set-up only)
+  const float4 *tab[3];         // per axis [mu][img][i]: (sq, c hi, c lo, 0),
+                                // c = norm^(1/3) exp(-alpha sq) as a float pair
+  const float *rc2f;            // [M]
+  const int *nu;                // [n_tiles] functions per tile (images merged)
+  const int *xr_off;            // [n_tiles + 1] density K steps before each tile
+  const int *xv_off;            // [n_tiles + 1] padded V entries before each tile
+  uint8_t *xr;                  // density X slices, 16 KB per K step
+  uint8_t *xv;                  // V X^T slices, 1 KB per padded entry
+  float4 *vent;                 // per padded entry: (mu bits, 2^(e_a - 8), bound, 0)
+  signed char *rowexp;          // [G] density row exponents e_p
+  const uint2 *Osl;             // [M][NoccP] BF16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
+  const float *oscale;          // [N] 2^g_m
+  int Nocc, NoccP;              // occupied orbitals; O-slice row length (even)
+  double *rho;                  // [G]
+  const double *v;              // [G]
+  float2 *vt;                   // [n_tiles][128] v dV at the tile points (float pairs)
+  unsigned long long *Vfix;     // [M][M] V (upper triangle) in fixed point, then [M*M] = max|v| bits
+  double *Vout;                 // [M][M] V, upper triangle
+  double dV;
+  int *flags;
 };
+
+__device__ __forceinline__ int tile_point(const GridGeom &g, int t, int p) {
+  const int bz = t % g.nbz, by = (t / g.nbz) % g.nby, bx = t / (g.nbz * g.nby);
+  const int i = bx * 4 + (p >> 5), j = by * 4 + ((p >> 3) & 3), k = bz * 8 + (p & 7);
+  return (i < g.nx && j < g.ny && k < g.nz) ? (i * g.ny + j) * g.nz + k : -1;
+}
+
+// Per-tile staging of the separable basis factors (dynamic shared memory):
+//   xy[(e, li*4+lj)] = (sq_x + sq_y, c_x c_y as a float pair, r_c^2 of the entry)
+//   z [(e, lk)]      = (sq_z, c_z as a float pair, 0)
+// so that a basis value costs one float-pair product and one cutoff test.
+// Entry-major for the density slices, slot-major for the V slices.
+constexpr int kStageXY = kNmax * 16;
+constexpr int kStageBytes = (kNmax * 16 + kNmax * 8) * 16;  // 48 KB
+
+template <bool TR>
+__device__ __forceinline__ int xy_idx(int e, int s) { return TR ? s * kNmax + e : e * 16 + s; }
+template <bool TR>
+__device__ __forceinline__ int z_idx(int e, int s) { return TR ? s * kNmax + e : e * 8 + s; }
+
+struct BuildShared {
+  int mu[kNmax];          // image entries of the tile
+  int ustart[kNmax + 1];  // first image entry of each function
+  int nu;
+  float sc[kTP];
+};
+
+// stage the tile's factors for its n image entries; points outside the grid
+// get sq = inf, hence value 0; then group the entries by function
+template <bool TR>
+__device__ void stage_tile(const TcArgs &A, BuildShared &S, float4 *xy, float4 *zs, int t, int kb,
+                           int n) {
+  const GridGeom &g = A.g;
+  const int bz = t % g.nbz, by = (t / g.nbz) % g.nby, bx = t / (g.nbz * g.nby);
+  const int i0 = bx * 4, j0 = by * 4, k0 = bz * 8;
+  const float4 out = make_float4(INFINITY, 0.f, 0.f, 0.f);
+  for (int q = threadIdx.x; q < n * 24; q += blockDim.x) {
+    const int e = TR ? q % n : q / 24, s = TR ? q / n : q % 24;
+    const int key = A.keys[kb + e];
+    const int mu = key >> 9;
+    if (s < 16) {
+      const int ix = ((key >> 6) & 7) - 4 + kImgMax, iy = ((key >> 3) & 7) - 4 + kImgMax;
+      const int i = i0 + (s >> 2), j = j0 + (s & 3);
+      const float4 xv = i < g.nx ? A.tab[0][((long)mu * kImgN + ix) * g.nx + i] : out;
+      const float4 yv = j < g.ny ? A.tab[1][((long)mu * kImgN + iy) * g.ny + j] : out;
+      const float2 c = df_mul(make_float2(xv.y, xv.z), make_float2(yv.y, yv.z));
+      xy[xy_idx<TR>(e, s)] = make_float4(xv.x + yv.x, c.x, c.y, A.rc2f[mu]);
+    } else {
+      const int iz = (key & 7) - 4 + kImgMax;
+      const int k = k0 + s - 16;
+      zs[z_idx<TR>(e, s - 16)] = k < g.nz ? A.tab[2][((long)mu * kImgN + iz) * g.nz + k] : out;
+    }
+    if (s == 0) S.mu[e] = mu;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // the list is sorted by function: images are adjacent
+    int u = 0;
+    for (int e = 0; e < n; ++e)
+      if (e == 0 || S.mu[e] != S.mu[e - 1]) S.ustart[u++] = e;
+    S.ustart[u] = n;
+    S.nu = u;
+  }
+  __syncthreads();
+}
+
+// basis value of image entry e at tile point p as a float pair (about 44
+// significant bits), zero beyond the cutoff radius
+template <bool TR>
+__device__ __forceinline__ float2 basis_val_df(const float4 *xy, const float4 *zs, int e, int p) {
+  const int lxy = p >> 3, lk = p & 7;  // p = (li*4 + lj)*8 + lk
+  const float4 a = xy[xy_idx<TR>(e, lxy)], b = zs[z_idx<TR>(e, lk)];
+  if (!(a.x + b.x < a.w)) return make_float2(0.f, 0.f);
+  return df_mul(make_float2(a.y, a.z), make_float2(b.y, b.z));
+}
+
+// value of function u (the sum of its images) at tile point p
+template <bool TR>
+__device__ __forceinline__ float2 func_val(const BuildShared &S, const float4 *xy, const float4 *zs,
+                                           int u, int p) {
+  float2 x = basis_val_df<TR>(xy, zs, S.ustart[u], p);
+  for (int e = S.ustart[u] + 1; e < S.ustart[u + 1]; ++e) x = df_add(x, basis_val_df<TR>(xy, zs, e, p));
+  return x;
+}
+
+// functions per tile (distinct mu in its sorted image list)
+__global__ void count_unique_kernel(const int *tile_ptr, const int *keys, int n_tiles, int *nu) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+    int c = 0, last = -1;
+    for (int e = tile_ptr[t]; e < tile_ptr[t + 1]; ++e) {
+      const int mu = keys[e] >> 9;
+      c += mu != last;
+      last = mu;
+    }
+    nu[t] = c;
+  }
+}
+
+// ---- set-up: density X slices (per-point exponents) ---------------------------
+// For tile t, K step kk (functions kk*16 .. kk*16+15), slice k: block
+// xr + (xr_off[t] + kk) * 16 KB + k * 4 KB, element (p, c) at kstep_off(p, c).
+// Also writes the row exponents e_p (max_a |X_pa| < 2^(e_p - 1)).
+__global__ void __launch_bounds__(256) xr_build_kernel(TcArgs A) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  float4 *xy = (float4 *)dsm, *zs = xy + kStageXY;
+  __shared__ BuildShared S;
+  for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
+    const int kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
+    stage_tile<false>(A, S, xy, zs, t, kb, n);
+    const int nu = S.nu, nk = rsteps(nu);
+    for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
+      float mx = 0.f;
+      for (int u = 0; u < nu; ++u) mx = fmaxf(mx, fabsf(func_val<false>(S, xy, zs, u, p).x));
+      const int e = slice_exp(mx);
+      S.sc[p] = pow2f(8 - e);
+      const int gp = tile_point(A.g, t, p);
+      if (gp >= 0) A.rowexp[gp] = (signed char)e;
+    }
+    __syncthreads();
+    uint8_t *dst = A.xr + (size_t)A.xr_off[t] * (4 * kSlot);
+    for (int q = threadIdx.x; q < kTP * 2 * nk; q += blockDim.x) {
+      const int p = q % kTP, gq = q / kTP;  // functions gq*8 .. gq*8+7
+      const float sc = S.sc[p];
+      uint32_t wd[4][4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        float r[2][4];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int a = gq * 8 + u + v;
+          slice4(a < nu ? func_val<false>(S, xy, zs, a, p) : make_float2(0.f, 0.f), sc, r[v]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wd[k][u >> 1] = pack_bf16(r[0][k], r[1][k]);
+      }
+      uint8_t *blk = dst + (size_t)(gq >> 1) * (4 * kSlot);
+      const int off = kstep_off(p, (gq & 1) * 8);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        *(uint4 *)(blk + k * kSlot + off) = make_uint4(wd[k][0], wd[k][1], wd[k][2], wd[k][3]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- set-up: V X^T slices (per-function exponents) -----------------------------
+// For tile t with padded length np, K step kk (points kk*16 .. kk*16+15), slice
+// k: block xv + xv_off[t] KB + kk * np * 128 + k * np * 32, element (a, c) at
+// kstep_off(a, c); rows a >= nu are zero.  vent[xv_off[t] + a] = (mu, 2^(e_a-8),
+// bound of |X_pa| over the tile, 0).
+__global__ void __launch_bounds__(256) xv_build_kernel(TcArgs A) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  float4 *xy = (float4 *)dsm, *zs = xy + kStageXY;
+  __shared__ BuildShared S;
+  __shared__ float sa_s[kNmax];
+  for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
+    const int kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
+    stage_tile<true>(A, S, xy, zs, t, kb, n);
+    const int nu = S.nu, np = vpad(nu);
+    for (int a = threadIdx.x; a < np; a += blockDim.x) {
+      float bnd = 0.f;
+      if (a < nu) {  // separable bound of |X_pa| over the tile, summed over images
+        for (int e = S.ustart[a]; e < S.ustart[a + 1]; ++e) {
+          float mxy = 0.f, mz = 0.f;
+          for (int s = 0; s < 16; ++s) mxy = fmaxf(mxy, xy[xy_idx<true>(e, s)].y);
+          for (int s = 0; s < 8; ++s) mz = fmaxf(mz, zs[z_idx<true>(e, s)].y);
+          bnd += mxy * mz * 1.0001f;
+        }
+        bnd *= 1.0001f;
+      }
+      const int ea = slice_exp(bnd);
+      sa_s[a] = pow2f(8 - ea);
+      A.vent[A.xv_off[t] + a] =
+          make_float4(__int_as_float(a < nu ? S.mu[S.ustart[a]] : 0), pow2f(ea - 8), bnd, 0.f);
+    }
+    __syncthreads();
+    uint8_t *base = A.xv + (size_t)A.xv_off[t] * 1024;
+    for (int q = threadIdx.x; q < np * 16; q += blockDim.x) {
+      const int a = q % np, gq = q / np;  // points gq*8 .. gq*8+7
+      const float sa = sa_s[a];
+      uint32_t wd[4][4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        float r[2][4];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int p = gq * 8 + u + v;
+          slice4(a < nu ? func_val<true>(S, xy, zs, a, p) : make_float2(0.f, 0.f), sa, r[v]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wd[k][u >> 1] = pack_bf16(r[0][k], r[1][k]);
+      }
+      uint8_t *blk = base + (size_t)(gq >> 1) * np * 128;
+      const int off = kstep_off(a, (gq & 1) * 8);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        *(uint4 *)(blk + k * np * 32 + off) = make_uint4(wd[k][0], wd[k][1], wd[k][2], wd[k][3]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- density ---------------------------------------------------------------
+// Warp roles: 0-7 read the accumulators (lane quarter w % 4, column half w / 4),
+// 8-11 lay out the O-slice operand of each K step, 12 streams the X slices and
+// gathers the O-slice rows of the K step's 16 functions, 13 issues the MMAs.
+// A job is (tile, chunk of <= 128 occupied orbitals).
+constexpr int kRhoStages = 4;
+constexpr int kRhoA = 4 * kSlot;        // X slices I0..I3 of a K step (16 KB, as stored)
+constexpr int kRhoB = 3 * kSlot;        // O slices K0..K2 of a K step (12 KB)
+constexpr int kRhoRow = kNmax * 8;      // one gathered O-slice row (<= 128 orbitals, 1 KB)
+constexpr int kRhoG = kKs * kRhoRow;    // the K step's 16 rows (16 KB)
+constexpr int kRhoStage = kRhoA + kRhoB + kRhoG;
+constexpr int kRhoEpi = 256, kRhoBld = 128;
+constexpr int kRhoThreads = kRhoEpi + kRhoBld + 64;
+
+struct RhoBars {
+  uint64_t tma_full[kRhoStages], bld_full[kRhoStages], empty[kRhoStages];
+  uint64_t acc_full, acc_empty, part_full, part_empty, fin;
+  uint32_t tbase;
+  int stop;
+  float part[kTP];
+};
+
+// phi = (acc0 + acc1 + acc2 + acc3) 2^g for 8 columns; adds phi^2
+__device__ __forceinline__ float rho_sum8(const uint32_t (&r)[32], const float *f, float rsum) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float y = __uint_as_float(r[c]) +
+              (__uint_as_float(r[8 + c]) + (__uint_as_float(r[16 + c]) + __uint_as_float(r[24 + c])));
+    y *= f[c];
+    rsum = fmaf(y, y, rsum);
+  }
+  return rsum;
+}
+
+__global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  float *fs = (float *)(dsm + kRhoStages * kRhoStage);  // column scales 2^g_m, zero-padded
+  __shared__ RhoBars R;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int nmc = (A.Nocc + kNmax - 1) / kNmax;
+  if (tid == 0) {
+    for (int s = 0; s < kRhoStages; ++s) {
+      mbar_init(&R.tma_full[s], 1);
+      mbar_init(&R.bld_full[s], kRhoBld);
+      mbar_init(&R.empty[s], 1);
+    }
+    mbar_init(&R.acc_full, 1);
+    mbar_init(&R.acc_empty, kRhoEpi);
+    mbar_init(&R.part_full, kRhoEpi / 2);
+    mbar_init(&R.part_empty, kRhoEpi / 2);
+    mbar_init(&R.fin, 1);
+    R.stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) tmem_alloc(&R.tbase);
+  for (int m = tid; m < nmc * kNmax; m += blockDim.x) fs[m] = m < A.Nocc ? A.oscale[m] : 0.f;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = R.tbase;
+  const int ntl = A.n_tiles > (int)blockIdx.x
+                      ? (A.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                      : 0;
+  const int njobs = ntl * nmc;
+  volatile int *stop = &R.stop;
+
+  if (w == 12) {
+    // ------------- bulk copies: X slices and the O-slice rows of each K step -------------
+    int fill = 0;
+    bool ok = true;
+    for (int j = 0; j < njobs && ok; ++j) {
+      const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+      const int k0 = A.xr_off[t], nk = A.xr_off[t + 1] - k0, nu = A.nu[t];
+      const int m0 = mc * kNmax, nme = min(kNmax, A.NoccP - m0);  // even
+      // functions of the tile: lane l holds entries l, l + 32, l + 64, l + 96
+      int mu4[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int a = lane + 32 * r;
+        mu4[r] = a < nu ? __float_as_int(A.vent[A.xv_off[t] + a].x) : 0;
+      }
+      for (int kk = 0; kk < nk; ++kk, ++fill) {
+        const int s = fill % kRhoStages, use = fill / kRhoStages;
+        bool got = true;
+        if (lane == 0 && use > 0) got = mbar_wait(&R.empty[s], (use - 1) & 1, stop);
+        if (!__shfl_sync(0xffffffffu, got, 0)) { ok = false; break; }
+        const int nrow = max(0, min(kKs, nu - kk * kKs));
+        uint8_t *st = dsm + s * kRhoStage;
+        if (lane == 0) {
+          mbar_expect_tx(&R.tma_full[s], kRhoA + nrow * nme * 8);
+          bulk_g2s(st, A.xr + (size_t)(k0 + kk) * kRhoA, kRhoA, &R.tma_full[s]);
+        }
+        __syncwarp();
+        const int a = kk * kKs + (lane & 15), r = a >> 5;  // r is the same for the warp
+        const int mv = r == 0 ? mu4[0] : r == 1 ? mu4[1] : r == 2 ? mu4[2] : mu4[3];
+        const int mu = __shfl_sync(0xffffffffu, mv, a & 31);
+        if (lane < nrow)
+          bulk_g2s(st + kRhoA + kRhoB + lane * kRhoRow, A.Osl + (size_t)mu * A.NoccP + m0, nme * 8,
+                   &R.tma_full[s]);
+      }
+    }
+    if (lane == 0) {
+      if (!ok) atomicExch((int *)stop, 1);
+      // the copies still in flight land before the CTA exits
+      for (int s = 0; s < kRhoStages && s < fill; ++s)
+        mbar_wait(&R.tma_full[s], ((fill - 1 - s) / kRhoStages) & 1);
+    }
+  } else if (w == 13) {
+    // ---------------------------------- MMA issue ----------------------------------
+    if (lane == 0) {
+      int fill = 0;
+      bool ok = true;
+      for (int j = 0; j < njobs && ok; ++j) {
+        const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+        const int nk = A.xr_off[t + 1] - A.xr_off[t];
+        const int nm = min(kNmax, A.Nocc - mc * kNmax);
+        const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
+        if (j > 0 && !mbar_wait(&R.acc_empty, (j - 1) & 1, stop)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = idesc_bf16(nmpad);
+        for (int kk = 0; kk < nk; ++kk, ++fill) {
+          const int s = fill % kRhoStages, use = fill / kRhoStages;
+          if (!mbar_wait(&R.tma_full[s], use & 1, stop) || !mbar_wait(&R.bld_full[s], use & 1, stop)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = su32(dsm + s * kRhoStage), b0 = a0 + kRhoA;
+          uint64_t I[4], K[3];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) I[k] = smem_desc(a0 + k * kSlot);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) K[k] = smem_desc(b0 + k * kSlot);
+          const uint32_t acc = kk > 0;
+          mma_bf16(tmem, I[0], K[0], idesc, acc);                  // order 0
+          mma_bf16(tmem + kNmax, I[0], K[1], idesc, acc);          // order 1
+          mma_bf16(tmem + kNmax, I[1], K[0], idesc, 1u);
+          mma_bf16(tmem + 2 * kNmax, I[0], K[2], idesc, acc);      // order 2
+          mma_bf16(tmem + 2 * kNmax, I[1], K[1], idesc, 1u);
+          mma_bf16(tmem + 2 * kNmax, I[2], K[0], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, I[1], K[2], idesc, acc);      // order 3
+          mma_bf16(tmem + 3 * kNmax, I[2], K[1], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, I[3], K[0], idesc, 1u);
+          mma_commit(&R.empty[s]);  // the stage is free once these MMAs complete
+        }
+        if (ok) mma_commit(&R.acc_full);
+      }
+      if (!ok) atomicExch((int *)stop, 1);
+      mma_commit(&R.fin);  // every MMA issued has completed before the TMEM is released
+      mbar_wait(&R.fin, 0);
+    }
+  } else if (w >= 8) {
+    // -------------- O-slice operand, B[m][a] = Oq[mu_a][m], from the gathered rows --------------
+    const int bt = tid - kRhoEpi;
+    int fill = 0;
+    bool ok = true;
+    for (int j = 0; j < njobs && ok; ++j) {
+      const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+      const int nk = A.xr_off[t + 1] - A.xr_off[t], nu = A.nu[t];
+      const int nm = min(kNmax, A.Nocc - mc * kNmax);
+      const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
+      for (int kk = 0; kk < nk; ++kk, ++fill) {
+        const int s = fill % kRhoStages, use = fill / kRhoStages;
+        if (!mbar_wait(&R.tma_full[s], use & 1, stop)) { ok = false; break; }
+        uint8_t *B = dsm + s * kRhoStage + kRhoA;
+        const uint8_t *G = B + kRhoB;
+        const int nrow = max(0, min(kKs, nu - kk * kKs));
+        for (int q = bt; q < nmpad * 2; q += kRhoBld) {  // items (orbital, 8 functions)
+          const int m = q % nmpad, h = q / nmpad;
+          uint32_t w01[8], w2[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int c = h * 8 + u;
+            uint2 o = make_uint2(0u, 0u);
+            if (c < nrow && m < nm) o = *(const uint2 *)(G + c * kRhoRow + m * 8);
+            w01[u] = o.x;
+            w2[u] = o.y;
+          }
+          const int off = kstep_off(m, h * 8);
+          uint4 v0, v1, v2;
+          v0.x = __byte_perm(w01[0], w01[1], 0x5410); v0.y = __byte_perm(w01[2], w01[3], 0x5410);
+          v0.z = __byte_perm(w01[4], w01[5], 0x5410); v0.w = __byte_perm(w01[6], w01[7], 0x5410);
+          v1.x = __byte_perm(w01[0], w01[1], 0x7632); v1.y = __byte_perm(w01[2], w01[3], 0x7632);
+          v1.z = __byte_perm(w01[4], w01[5], 0x7632); v1.w = __byte_perm(w01[6], w01[7], 0x7632);
+          v2.x = __byte_perm(w2[0], w2[1], 0x5410); v2.y = __byte_perm(w2[2], w2[3], 0x5410);
+          v2.z = __byte_perm(w2[4], w2[5], 0x5410); v2.w = __byte_perm(w2[6], w2[7], 0x5410);
+          *(uint4 *)(B + off) = v0;
+          *(uint4 *)(B + kSlot + off) = v1;
+          *(uint4 *)(B + 2 * kSlot + off) = v2;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&R.bld_full[s]);
+      }
+    }
+    if (!ok) atomicExch((int *)stop, 1);
+  } else {
+    // ---------------------------- accumulator read-out ------------------------------
+    // phi_pm = 2^(e_p + g_m - 16) y with y = acc0 + acc1 + acc2 + acc3;
+    // rho_p = 2 sum_m phi_pm^2 (every term positive)
+    const int quad = w & 3, half = w >> 2;
+    const int pe = quad * 32 + lane;
+    const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
+    float rsum = 0.f;
+    int ntile = 0;  // tiles finished (part buffer hand-overs)
+    bool ok = true;
+    for (int j = 0; j < njobs && ok; ++j) {
+      const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+      const int nm = min(kNmax, A.Nocc - mc * kNmax);
+      const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
+      const int gp = tile_point(A.g, t, pe);
+      const int ep = gp >= 0 ? (int)A.rowexp[gp] : 0;
+      ok = __all_sync(0xffffffffu, mbar_wait(&R.acc_full, j & 1, stop));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // this warp's column half in chunks of 8, the next chunk's loads in flight
+      // while the current one is summed
+      const int cb = half * (nmpad / 2), ce = cb + nmpad / 2;
+      const float *f = fs + mc * kNmax;
+      uint32_t ra[32], rb[32];
+      tmem_ld_issue(tmem + lanebits + cb, ra);
+      for (int c0 = cb; c0 < ce; c0 += 16) {
+        tmem_ld_wait(ra);
+        if (c0 + 8 < ce) tmem_ld_issue(tmem + lanebits + c0 + 8, rb);
+        rsum = rho_sum8(ra, f + c0, rsum);
+        if (c0 + 8 >= ce) break;
+        tmem_ld_wait(rb);
+        if (c0 + 16 < ce) tmem_ld_issue(tmem + lanebits + c0 + 16, ra);
+        rsum = rho_sum8(rb, f + c0 + 8, rsum);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&R.acc_empty);
+      if (mc == nmc - 1) {  // the tile is done: add the two column halves
+        if (half == 1) {
+          if (ntile > 0) ok = mbar_wait(&R.part_empty, (ntile - 1) & 1, stop);
+          R.part[pe] = rsum;
+          mbar_arrive(&R.part_full);
+        } else {
+          ok = mbar_wait(&R.part_full, ntile & 1, stop);
+          const float other = R.part[pe];
+          mbar_arrive(&R.part_empty);
+          if (ok && gp >= 0) A.rho[gp] = ldexp((double)rsum + (double)other, 2 * ep - 31);
+        }
+        rsum = 0.f;
+        ++ntile;
+        ok = __all_sync(0xffffffffu, ok);
+      }
+    }
+    if (!ok) atomicExch((int *)stop, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0) tmem_dealloc(tmem);
+  if (tid == 0 && R.stop) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
+}
+
+// ---- potential matrix ---------------------------------------------------------
+// V_loc = dV X^T diag(v) X per tile as D = W X^T on the tensor cores, W = (v X)^T
+// (rows = list functions i, the accumulator lanes) and X^T (columns j), both
+// in four exact integer slices, slice orders 0..3 in four FP32 accumulators.
+// Warp roles: 0-15 read the accumulators (lane quarter w % 4, every fourth
+// 8-column chunk by w / 4) and add them into V by fixed-point reductions; 16-23
+// build W from the X^T slices and v; 24 streams the X^T slices and the tile
+// buffers (v at the points, list entries); 25 issues the MMAs.  Lane i takes the
+// columns j <= i and adds into V[mu_j][mu_i] (mu_j <= mu_i), so a warp's
+// reductions run along a row of V.
+constexpr int kVStages = 4;
+constexpr int kVA = 4 * kSlot;   // W slices (128 rows)
+constexpr int kVB = 4 * kSlot;   // X^T slices (np rows each, packed as stored)
+constexpr int kVStage = kVA + kVB;
+constexpr int kVEpiW = 16, kVBldW = 8;  // warps: 0-15 read-out, 16-23 build W
+constexpr int kVEpi = kVEpiW * 32, kVBld = kVBldW * 32;
+constexpr int kVThreads = kVEpi + kVBld + 64;
+constexpr int kVTileBuf = kTP * 8 + kNmax * 16;  // v pairs + list entries (3 KB)
+
+struct VBars {
+  uint64_t tma_full[kVStages], bld_full[kVStages], empty[kVStages];
+  uint64_t tile_full[2], tile_empty[2], acc_full, acc_empty, fin;
+  uint32_t tbase;
+  int stop;
+};
+
+// max |v dV| over a tile's points (all lanes of the calling warp get it)
+__device__ __forceinline__ float tile_vmax(const float2 *vt) {
+  float m = 0.f;
+  for (int p = (threadIdx.x & 31); p < kTP; p += 32) m = fmaxf(m, fabsf(vt[p].x));
+  // non-negative floats order as their bit patterns
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+}
+
+// V_loc = 2^(e_i + e_j - 16) y, y = acc0 + acc1 + acc2 + acc3, for 8 columns
+// j = c0 .. c0+7 <= i of lane i, added into V[mu_j][mu_i] in fixed point (ub =
+// 2^(e_i - 8 - F), ve[j].y = 2^(e_j - 8)).  The column entries are read and all
+// eight values formed before the first reduction is issued.
+__device__ __forceinline__ void vfix_add8(const TcArgs &A, const uint32_t (&r)[32], const float4 *ve,
+                                          int c0, int i, int nu, int mui, float ub, int M) {
+  float2 e[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) e[c] = *(const float2 *)&ve[c0 + c];  // (mu bits, 2^(e_j - 8))
+  long long val[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float y0 = __uint_as_float(r[c]);
+    float lo = __uint_as_float(r[8 + c]) + (__uint_as_float(r[16 + c]) + __uint_as_float(r[24 + c]));
+    const float hi = y0 + lo;
+    lo = lo - (hi - y0);
+    const float f = ub * e[c].y;  // exact: a product of powers of two
+    val[c] = f2ll_trunc(hi * f) + f2ll_trunc(lo * f);
+  }
+  if (i < nu) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c0 + c <= i)
+        atomicAdd(A.Vfix + (long)__float_as_int(e[c].x) * M + mui, (unsigned long long)val[c]);
+  }
+}
 
 __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   extern __shared__ __align__(1024) uint8_t dsm[];
-  __shared__ TileShared S;  // producer-side staging (tables, points)
-  __shared__ VMeta meta[2];
-  __shared__ float2 vp[kTP];
-  __shared__ float vmax_s;
-  __shared__ __align__(8) uint64_t bar_full[kVStages], bar_empty[kVStages], bar_acc_full,
-      bar_acc_empty, bar_meta_full[2], bar_meta_empty[2];
-  __shared__ int stop;
-  const int tid = threadIdx.x, w = tid >> 5;
+  uint8_t *tbuf = dsm + kVStages * kVStage;  // 2 tile buffers: vt[128] float2, vent[np] float4
+  __shared__ VBars R;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int M = A.g.M;
-  float2 *Vpriv = A.Vpriv + (long)blockIdx.x * M * M;
   if (tid == 0) {
-    for (int s = 0; s < kVStages; ++s) { mbar_init(&bar_full[s], kVProd); mbar_init(&bar_empty[s], 1); }
-    mbar_init(&bar_acc_full, 1);
-    mbar_init(&bar_acc_empty, kVEpi);
-    for (int s = 0; s < 2; ++s) { mbar_init(&bar_meta_full[s], kVProd); mbar_init(&bar_meta_empty[s], kVEpi); }
-    stop = 0;
+    for (int s = 0; s < kVStages; ++s) {
+      mbar_init(&R.tma_full[s], 1);
+      mbar_init(&R.bld_full[s], kVBld);
+      mbar_init(&R.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&R.tile_full[b], 1);
+      mbar_init(&R.tile_empty[b], (kVEpi + kVBld) / 32);
+    }
+    mbar_init(&R.acc_full, 1);
+    mbar_init(&R.acc_empty, kVEpi);
+    mbar_init(&R.fin, 1);
+    R.stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  tmem_alloc(S);  // also fences the barrier initialization
-  const uint32_t tmem = S.tbase;
-  const int ntiles_cta = A.n_tiles > (int)blockIdx.x
-                             ? (A.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
-                             : 0;
-  if (w < 8) {
-    // ------------------------------- producers -----------------------------------
-    int fill = 0;  // K-chunk stage fills so far
-    for (int it = 0; it < ntiles_cta; ++it) {
-      const int t = blockIdx.x + it * gridDim.x;
-      const int kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
-      const int npad = n <= 32 ? 32 : ((n + 31) / 32) * 32;
-      const int mb = it & 1;
-      if (it >= 2 && !mbar_wait(&bar_meta_empty[mb], ((it >> 1) - 1) & 1)) { atomicExch(&stop, 1); }
-      if (*(volatile int *)&stop) break;
-      VMeta &m = meta[mb];
-      stage_tile<true>(A, S, t, kb, n, tid, kVProd);
-      if (tid == 0) vmax_s = 0.f;
-      named_sync(1, kVProd);
-      for (int p = tid; p < kTP; p += kVProd) {
-        const int gp = S.inside[p];
-        const double vv = gp >= 0 ? A.v[gp] * A.dV : 0.0;
-        const float hi = (float)vv;
-        vp[p] = make_float2(hi, (float)(vv - (double)hi));
-        atomicMax((int *)&vmax_s, __float_as_int(fabsf(hi)));  // non-negative floats order as ints
-      }
-      named_sync(1, kVProd);
-      for (int a = tid; a < kNmax; a += kVProd) {
-        float bnd = 0.f;
-        int rk = 0;
-        if (a < n) {
-          float mx = 0.f, my = 0.f, mz = 0.f;
-          for (int s = 0; s < 4; ++s) mx = fmaxf(mx, S.stage[sidx<true>(a, s)].y);
-          for (int s = 4; s < 8; ++s) my = fmaxf(my, S.stage[sidx<true>(a, s)].y);
-          for (int s = 8; s < 16; ++s) mz = fmaxf(mz, S.stage[sidx<true>(a, s)].y);
-          bnd = mx * my * mz * 1.0001f;
-          while (rk < a && S.mu[a - rk - 1] == S.mu[a]) ++rk;  // image rank among equal mu
+  if (w == 0) tmem_alloc(&R.tbase);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = R.tbase;
+  // a contiguous run of tiles per CTA: CTAs running at the same time work in
+  // different parts of the box and rarely add into the same entries of V
+  const int tbeg = (int)((long)A.n_tiles * blockIdx.x / gridDim.x);
+  const int ntl = (int)((long)A.n_tiles * (blockIdx.x + 1) / gridDim.x) - tbeg;
+  volatile int *stop = &R.stop;
+  constexpr int kSteps = kTP / kKs;  // 8 K steps of 16 points per tile
+
+  if (w == kVEpiW + kVBldW) {
+    // ------------------------ bulk copies: tile buffers and X^T ------------------------
+    if (lane == 0) {
+      int fill = 0, it = 0;
+      bool ok = true;
+      for (; it < ntl && ok; ++it) {
+        const int t = tbeg + it, mb = it & 1;
+        const int x0 = A.xv_off[t], np = A.xv_off[t + 1] - x0;
+        if (it >= 2 && !mbar_wait(&R.tile_empty[mb], ((it >> 1) - 1) & 1, stop)) { ok = false; break; }
+        uint8_t *tb = tbuf + mb * kVTileBuf;
+        mbar_expect_tx(&R.tile_full[mb], kTP * 8 + np * 16);
+        bulk_g2s(tb, A.vt + (size_t)t * kTP, kTP * 8, &R.tile_full[mb]);
+        bulk_g2s(tb + kTP * 8, A.vent + x0, np * 16, &R.tile_full[mb]);
+        const uint8_t *src = A.xv + (size_t)x0 * 1024;
+        for (int kk = 0; kk < kSteps; ++kk, ++fill) {
+          const int s = fill % kVStages, use = fill / kVStages;
+          if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
+          mbar_expect_tx(&R.tma_full[s], np * 128);
+          bulk_g2s(dsm + s * kVStage + kVA, src + (size_t)kk * np * 128, np * 128, &R.tma_full[s]);
         }
-        m.mu[a] = a < n ? S.mu[a] : 0;
-        m.ea[a] = slice_exp(bnd);
-        m.eb[a] = slice_exp(bnd * vmax_s * 1.0001f);
-        m.rank[a] = rk;
       }
-      named_sync(1, kVProd);
-      if (tid == 0) {
-        int mr = 0;
-        for (int a = 0; a < n; ++a) mr = max(mr, m.rank[a]);
-        m.maxrank = mr;
-        m.n = n;
-        m.npad = npad;
-      }
-      for (int kc = 0; kc < kTP / kVKc; ++kc, ++fill) {
-        const int s = fill % kVStages, use = fill / kVStages;
-        if (use > 0 && !mbar_wait(&bar_empty[s], (use - 1) & 1)) { atomicExch(&stop, 1); break; }
-        uint8_t *sA = dsm + s * kVStage, *sB = sA + 4 * kVSlice;
-        for (int q = tid; q < npad * (kVKc / 8); q += kVProd) {
-          const int a = q % npad, c0 = (q / npad) * 8;
-          uint16_t xs[4][8], ws[4][8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int p = kc * kVKc + c0 + u;
-            float2 x = (a < n && S.inside[p] >= 0) ? basis_val_df<true>(S, A.rc2f, a, p)
-                                                   : make_float2(0.f, 0.f);
-            float2 wv = df_mul(x, vp[p]);
-            uint16_t s4[4];
-            slice4(x, m.ea[a], s4);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) xs[k][u] = s4[k];
-            slice4(wv, m.eb[a], s4);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) ws[k][u] = s4[k];
+      if (!ok) atomicExch((int *)stop, 1);
+      // the copies still in flight land before the CTA exits
+      for (int s = 0; s < kVStages && s < fill; ++s)
+        mbar_wait(&R.tma_full[s], ((fill - 1 - s) / kVStages) & 1);
+      for (int b = 0; b < 2 && b < it; ++b) mbar_wait(&R.tile_full[b], ((it - 1 - b) >> 1) & 1);
+    }
+  } else if (w == kVEpiW + kVBldW + 1) {
+    // ---------------------------------- MMA issue ----------------------------------
+    if (lane == 0) {
+      int fill = 0;
+      bool ok = true;
+      for (int it = 0; it < ntl && ok; ++it) {
+        const int t = tbeg + it;
+        const int np = A.xv_off[t + 1] - A.xv_off[t];
+        if (it > 0 && !mbar_wait(&R.acc_empty, (it - 1) & 1, stop)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = idesc_bf16(np);
+        for (int kk = 0; kk < kSteps; ++kk, ++fill) {
+          const int s = fill % kVStages, use = fill / kVStages;
+          if (!mbar_wait(&R.tma_full[s], use & 1, stop) || !mbar_wait(&R.bld_full[s], use & 1, stop)) {
+            ok = false;
+            break;
           }
-          const int off = kmaj_off32(a, c0);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = su32(dsm + s * kVStage), b0 = a0 + kVA;
+          uint64_t W[4], X[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            uint4 v;
-            v.x = xs[k][0] | (xs[k][1] << 16); v.y = xs[k][2] | (xs[k][3] << 16);
-            v.z = xs[k][4] | (xs[k][5] << 16); v.w = xs[k][6] | (xs[k][7] << 16);
-            *(uint4 *)(sA + k * kVSlice + off) = v;
-            v.x = ws[k][0] | (ws[k][1] << 16); v.y = ws[k][2] | (ws[k][3] << 16);
-            v.z = ws[k][4] | (ws[k][5] << 16); v.w = ws[k][6] | (ws[k][7] << 16);
-            *(uint4 *)(sB + k * kVSlice + off) = v;
+            W[k] = smem_desc(a0 + k * kSlot);
+            X[k] = smem_desc(b0 + k * np * 32);
           }
+          const uint32_t acc = kk > 0;
+          mma_bf16(tmem, W[0], X[0], idesc, acc);                 // order 0
+          mma_bf16(tmem + kNmax, W[0], X[1], idesc, acc);         // order 1
+          mma_bf16(tmem + kNmax, W[1], X[0], idesc, 1u);
+          mma_bf16(tmem + 2 * kNmax, W[0], X[2], idesc, acc);     // order 2
+          mma_bf16(tmem + 2 * kNmax, W[1], X[1], idesc, 1u);
+          mma_bf16(tmem + 2 * kNmax, W[2], X[0], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, W[0], X[3], idesc, acc);     // order 3
+          mma_bf16(tmem + 3 * kNmax, W[1], X[2], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, W[2], X[1], idesc, 1u);
+          mma_bf16(tmem + 3 * kNmax, W[3], X[0], idesc, 1u);
+          mma_commit(&R.empty[s]);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        if (kc == 0) mbar_arrive(&bar_meta_full[mb]);  // metadata written before chunk 0 is out
-        mbar_arrive(&bar_full[s]);
+        if (ok) mma_commit(&R.acc_full);
       }
-      if (*(volatile int *)&stop) break;
-      named_sync(1, kVProd);  // the table buffer is reused by the next tile
+      if (!ok) atomicExch((int *)stop, 1);
+      mma_commit(&R.fin);
+      mbar_wait(&R.fin, 0);
     }
-  } else {
-    // ------------------------- MMA issue and epilogue ------------------------------
-    const int quad = w & 3;
-    const int ae = quad * 32 + (tid & 31);
-    const uint32_t lane = (uint32_t)(quad * 32) << 16;
+  } else if (w >= kVEpiW) {
+    // -------------------- W = (v X)^T: rows b, 8 points of each K step ----------------------
+    const int bt = tid - kVEpi;
+    const int b = bt & 127, h = bt >> 7;
     int fill = 0;
-    for (int it = 0; it < ntiles_cta; ++it) {
-      const int mb = it & 1;
-      bool ok = true;
-      if (tid == kVProd) {  // lane 0 of warp 8
-        if (it > 0) ok = mbar_wait(&bar_acc_empty, (it - 1) & 1);
-        if (ok) ok = mbar_wait(&bar_meta_full[mb], (it >> 1) & 1);
-        const int npad = ok ? meta[mb].npad : 32;
-        for (int kc = 0; ok && kc < kTP / kVKc; ++kc) {
-          const int s = (fill + kc) % kVStages, use = (fill + kc) / kVStages;
-          ok = mbar_wait(&bar_full[s], use & 1);
-          if (!ok) break;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t idesc = idesc_bf16(npad);
-          const uint32_t a0 = su32(dsm + s * kVStage), b0 = a0 + 4 * kVSlice;
-          const uint32_t sbo = (kVKc / 8) * 128;
-          for (int kk = 0; kk < kVKc / 16; ++kk) {
-            const uint32_t off = kk * 256;
-            uint64_t X[4], W[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              X[k] = smem_desc(a0 + k * kVSlice + off, sbo);
-              W[k] = smem_desc(b0 + k * kVSlice + off, sbo);
-            }
-            const uint32_t acc = (kc > 0 || kk > 0);
-            mma_bf16(tmem, X[0], W[0], idesc, acc);                 // order 0
-            mma_bf16(tmem + kNmax, X[0], W[1], idesc, acc);         // order 1
-            mma_bf16(tmem + kNmax, X[1], W[0], idesc, 1u);
-            mma_bf16(tmem + 2 * kNmax, X[0], W[2], idesc, acc);     // order 2
-            mma_bf16(tmem + 2 * kNmax, X[1], W[1], idesc, 1u);
-            mma_bf16(tmem + 2 * kNmax, X[2], W[0], idesc, 1u);
-            mma_bf16(tmem + 3 * kNmax, X[0], W[3], idesc, acc);     // order 3
-            mma_bf16(tmem + 3 * kNmax, X[1], W[2], idesc, 1u);
-            mma_bf16(tmem + 3 * kNmax, X[2], W[1], idesc, 1u);
-            mma_bf16(tmem + 3 * kNmax, X[3], W[0], idesc, 1u);
-          }
-          mma_commit(&bar_empty[s]);  // the stage is free once these MMAs complete
-        }
-        if (ok) mma_commit(&bar_acc_full);
-        if (!ok) atomicExch(&stop, 1);
+    bool ok = true;
+    for (int it = 0; it < ntl && ok; ++it) {
+      const int t = tbeg + it, mb = it & 1;
+      const int np = A.xv_off[t + 1] - A.xv_off[t];
+      const int nu = A.nu[t];
+      ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop));
+      if (!ok) break;
+      const uint8_t *tb = tbuf + mb * kVTileBuf;
+      const float2 *vt = (const float2 *)tb;
+      const float4 *ve = (const float4 *)(tb + kTP * 8);
+      const float vmax = tile_vmax(vt);
+      // row b: X^T slices of x 2^(8 - e_b); W row exponent from the bound of
+      // |v x| over the tile
+      float sb = 0.f;  // 2^(8 - e_w) 2^(e_b - 8): the X^T slices hold x 2^(8 - e_b)
+      if (b < nu) {
+        const float4 e = ve[b];
+        sb = pow2f(8 - slice_exp(e.z * vmax * 1.0001f)) * e.y;
       }
-      fill += kTP / kVKc;
-      __syncwarp();
-      if (*(volatile int *)&stop) break;
-      // all epilogue threads: wait for the accumulators and the tile's metadata
-      ok = mbar_wait(&bar_acc_full, it & 1) && mbar_wait(&bar_meta_full[mb], (it >> 1) & 1);
-      if (!ok) { atomicExch(&stop, 1); break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const VMeta &m = meta[mb];
-      const int n = m.n, npad = m.npad;
-      const int ma = ae < n ? m.mu[ae] : 0, ra = ae < n ? m.rank[ae] : -1;
-      // values of row ae, in 16-column chunks; rows of equal mu (images) add into
-      // the same targets, so they take turns by image rank
-      for (int r = 0; r <= m.maxrank; ++r) {
-        for (int c0 = 0; c0 < npad; c0 += 16) {
-          float y0[16], y1[16], y2[16], y3[16];
-          tmem_ld16(tmem + lane + c0, y0);
-          tmem_ld16(tmem + lane + kNmax + c0, y1);
-          tmem_ld16(tmem + lane + 2 * kNmax + c0, y2);
-          tmem_ld16(tmem + lane + 3 * kNmax + c0, y3);
-          if (ra == r) {
-            float2 val[16], old[16];
+      for (int kk = 0; kk < kSteps; ++kk, ++fill) {
+        const int s = fill % kVStages, use = fill / kVStages;
+        if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
+        if (!mbar_wait(&R.tma_full[s], use & 1, stop)) { ok = false; break; }
+        uint8_t *Ast = dsm + s * kVStage;
+        const uint8_t *Bst = Ast + kVA;
+        const int off = kstep_off(b, h * 8);
+        uint4 o[4];
+        if (b < nu) {
+          uint4 xs[4];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int b = c0 + j;
-              const int sc = m.ea[ae] + m.eb[b < n ? b : 0] - 16;
-              float lo = (y1[j] + (y2[j] + y3[j] * (1.f / 256.f)) * (1.f / 256.f)) * (1.f / 256.f);
-              float hi = y0[j] + lo;
-              lo = lo - (hi - y0[j]);
-              val[j] = make_float2(ldexpf(hi, sc), ldexpf(lo, sc));
-              if (b < n && b >= ae && m.mu[b] == ma && b != ae) {  // both orders of an image pair
-                val[j].x *= 2.f;
-                val[j].y *= 2.f;
-              }
-            }
-            // adjacent columns of equal mu (images) share a target: fold them first
-            bool live[16];
+          for (int k = 0; k < 4; ++k) xs[k] = *(const uint4 *)(Bst + k * np * 32 + off);
+          uint32_t ww[4][4];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) live[j] = (c0 + j >= ae && c0 + j < n);
-            if (m.maxrank > 0) {
+          for (int u = 0; u < 4; ++u) {  // point pairs (2u, 2u + 1)
+            const uint32_t s0 = (&xs[0].x)[u], s1 = (&xs[1].x)[u], s2 = (&xs[2].x)[u],
+                           s3 = (&xs[3].x)[u];
+            float r[2][4];
 #pragma unroll
-              for (int j = 15; j > 0; --j)
-                if (live[j] && live[j - 1] && m.mu[c0 + j] == m.mu[c0 + j - 1]) {
-                  val[j - 1] = df_add(val[j - 1], val[j]);
-                  live[j] = false;
-                }
+            for (int v = 0; v < 2; ++v) {
+              const float i0 = __uint_as_float(v ? (s0 & 0xFFFF0000u) : (s0 << 16));
+              const float i1 = __uint_as_float(v ? (s1 & 0xFFFF0000u) : (s1 << 16));
+              const float i2 = __uint_as_float(v ? (s2 & 0xFFFF0000u) : (s2 << 16));
+              const float i3 = __uint_as_float(v ? (s3 & 0xFFFF0000u) : (s3 << 16));
+              // the sliced x 2^(8 - e_b), exact: i0 + i1 + i2 on the 2^-16 grid below 2^8
+              const float2 x = make_float2((i0 + i1) + i2, i3);
+              slice4(df_mul_raw(x, vt[kk * kKs + h * 8 + 2 * u + v]), sb, r[v]);
             }
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              old[j] = live[j] ? Vpriv[(long)ma * M + m.mu[c0 + j]] : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (live[j]) Vpriv[(long)ma * M + m.mu[c0 + j]] = df_add(old[j], val[j]);
+            for (int k = 0; k < 4; ++k) ww[k][u] = pack_bf16(r[0][k], r[1][k]);
           }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) o[k] = make_uint4(ww[k][0], ww[k][1], ww[k][2], ww[k][3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) o[k] = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (m.maxrank > 0) named_sync(2, kVEpi);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) *(uint4 *)(Ast + k * kSlot + off) = o[k];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&R.bld_full[s]);
+      }
+      ok = __all_sync(0xffffffffu, ok);
+      if (lane == 0) mbar_arrive(&R.tile_empty[mb]);
+    }
+    if (!ok) atomicExch((int *)stop, 1);
+  } else {
+    // ------------------------- accumulator read-out into V ----------------------------
+    const int quad = w & 3, part = w >> 2;
+    const int i = quad * 32 + lane;  // accumulator lane = W row
+    const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
+    const int fixe = vfix_exp((unsigned)A.Vfix[(long)M * M]);
+    bool ok = true;
+    for (int it = 0; it < ntl && ok; ++it) {
+      const int t = tbeg + it, mb = it & 1;
+      const int nu = A.nu[t];
+      ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop) &&
+                                       mbar_wait(&R.acc_full, it & 1, stop));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint8_t *tb = tbuf + mb * kVTileBuf;
+      const float4 *ve = (const float4 *)(tb + kTP * 8);
+      const float vmax = tile_vmax((const float2 *)tb);
+      int mui = 0;
+      float ub = 0.f;  // 2^(e_i - 8 - F): W row scale over the fixed-point unit
+      if (i < nu) {
+        const float4 e = ve[i];
+        mui = __float_as_int(e.x);
+        ub = pow2f(max(slice_exp(e.z * vmax * 1.0001f) - 8 - fixe, -126));
+      }
+      // columns j <= i of this warp's lanes, every fourth 8-column chunk
+      const int jend = quad * 32 < nu ? min(quad * 32 + 32, nu) : 0;
+      for (int c0 = part * 8; c0 < jend; c0 += 32) {
+        uint32_t ra[32];
+        tmem_ld_issue(tmem + lanebits + c0, ra);
+        tmem_ld_wait(ra);
+        vfix_add8(A, ra, ve, c0, i, nu, mui, ub, M);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&bar_acc_empty);
-      mbar_arrive(&bar_meta_empty[mb]);
+      mbar_arrive(&R.acc_empty);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&R.tile_empty[mb]);
     }
+    if (!ok) atomicExch((int *)stop, 1);
   }
-  if (*(volatile int *)&stop && tid == 0) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
-  tmem_free(S);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0) tmem_dealloc(tmem);
+  if (tid == 0 && R.stop) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
 }
 
-// H_upper[mu][nu] = sum over CTA copies of (hi + lo), FP64, mu <= nu
-__global__ void vpriv_reduce_kernel(const float2 *Vpriv, int ncopies, int M, double *Vout) {
+// v dV at the points of every 4 x 4 x 8 tile, as float pairs in tile order, and
+// max|v| over the grid (as float bits; non-negative floats order as integers)
+__global__ void __launch_bounds__(256) vtile_kernel(TcArgs A) {
+  const long total = (long)A.n_tiles * kTP;
+  float m = 0.f;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int gp = tile_point(A.g, (int)(e / kTP), (int)(e % kTP));
+    const double v = gp >= 0 ? A.v[gp] : 0.0;
+    const double vv = v * A.dV;
+    const float hi = (float)vv;
+    A.vt[e] = make_float2(hi, (float)(vv - (double)hi));
+    m = fmaxf(m, (float)fabs(v) * 1.0001f);
+  }
+  unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+  __shared__ unsigned wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < 8; ++k) b = max(b, wm[k]);
+    atomicMax((unsigned *)(A.Vfix + (long)A.g.M * A.g.M), b);
+  }
+}
+
+// V (upper triangle) from its fixed-point sums
+__global__ void vfix_kernel(const unsigned long long *Vfix, int M, double *Vout) {
+  const int F = vfix_exp((unsigned)Vfix[(long)M * M]);
   const long MM = (long)M * M;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
        e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / M), c = (int)(e % M);
-    if (i > c) continue;
-    double s = 0.0;
-    for (int k = 0; k < ncopies; ++k) {
-      const float2 v = Vpriv[(long)k * MM + e];
-      s += (double)v.x + (double)v.y;
-    }
-    Vout[e] = s;
+    if (e / M > e % M) continue;
+    Vout[e] = ldexp((double)(long long)Vfix[e], F);
   }
 }
 
@@ -744,30 +1069,11 @@ __global__ void tables_f32_kernel(const double *sq, const double *ex, const doub
   }
 }
 
-// per grid point: exponent e_p with max_a |X_pa| < 2^(e_p - 1) (same FP32 values
-// as the density kernel computes)
-__global__ void __launch_bounds__(256) rowexp_kernel(TcArgs A, signed char *rowexp) {
-  __shared__ TileShared S;
-  for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
-    const int kb = A.tile_ptr[t], n = A.tile_ptr[t + 1] - kb;
-    stage_tile<false>(A, S, t, kb, min(n, kNmax), threadIdx.x, blockDim.x);
-    __syncthreads();
-    for (int p = threadIdx.x; p < kTP; p += blockDim.x) {
-      const int gp = S.inside[p];
-      if (gp < 0) continue;
-      float mx = 0.f;
-      for (int a = 0; a < min(n, kNmax); ++a) mx = fmaxf(mx, fabsf(basis_val<false>(S, A.rc2f, a, p)));
-      rowexp[gp] = (signed char)(mx > 0.f ? ilogbf(mx) + 2 : 0);
-    }
-    __syncthreads();
-  }
-}
-
 // Column slices of the occupied orbitals O (M x N): g_m = ilogb(max_mu |O_mu,m|)
-// + 2, K0 + K1/256 + K2/65536 = O 2^(8 - g) to 24 bits; dO = O - Oq (FP64) for
+// + 2, K0 + K1 + K2 = O 2^(8 - g) to 24 bits (K_k on the 2^-8k grid); dO = O - Oq (FP64) for
 // the first-order energy correction sum (4 H O) o dO.
-__global__ void __launch_bounds__(256) oslice_kernel(const double *O, int M, int N, uint2 *Osl,
-                                                     float *oscale, double *dO) {
+__global__ void __launch_bounds__(256) oslice_kernel(const double *O, int M, int N, int NP,
+                                                     uint2 *Osl, float *oscale, double *dO) {
   const int m = blockIdx.x;
   double mx = 0.0;
   for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(O[(long)r * N + m]));
@@ -791,9 +1097,9 @@ __global__ void __launch_bounds__(256) oslice_kernel(const double *O, int M, int
     const double r2 = rint(t2);
     const double q = ldexp(r0 + (r1 + r2 * (1.0 / 256.0)) * (1.0 / 256.0), g - 8);
     dO[(long)r * N + m] = o - q;
-    Osl[(long)r * N + m] =
-        make_uint2((uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)r1) << 16),
-                   (uint32_t)bf16_bits((float)r2));
+    Osl[(long)r * NP + m] = make_uint2(
+        (uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)(r1 * (1.0 / 256.0))) << 16),
+        (uint32_t)bf16_bits((float)(r2 * (1.0 / 65536.0))));
   }
 }
 
@@ -803,15 +1109,24 @@ static TcArgs tc_args(etdm_handle *h) {
   a.n_tiles = h->n_tiles_tc;
   a.tile_ptr = h->d_tile_ptr_tc;
   a.keys = h->d_keys_tc;
-  for (int ax = 0; ax < 3; ++ax) a.tab[ax] = h->d_tabf + h->tab_off[ax];
+  for (int ax = 0; ax < 3; ++ax) a.tab[ax] = h->d_tabf ? h->d_tabf + h->tab_off[ax] : nullptr;
   a.rc2f = h->d_rc2f;
+  a.nu = h->d_nu_tc;
+  a.xr_off = h->d_xr_off;
+  a.xv_off = h->d_xv_off;
+  a.xr = h->d_xr;
+  a.xv = h->d_xv;
+  a.vent = h->d_vent;
   a.rowexp = h->d_rowexp;
   a.Osl = h->d_Osl;
   a.oscale = h->d_oscale;
   a.Nocc = h->N;
+  a.NoccP = h->N + (h->N & 1);
   a.rho = h->d_rho;
   a.v = h->d_vtot;
-  a.Vpriv = h->d_Vpriv;
+  a.vt = h->d_vt;
+  a.Vfix = h->d_Vfix;
+  a.Vout = h->d_Vfin;
   a.dV = h->dV;
   a.flags = h->d_flags;
   return a;
@@ -828,19 +1143,42 @@ cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rowexp(etdm_handle *h, cudaStream_t s) {
-  TcArgs a = tc_args(h);
-  rowexp_kernel<<<std::min(h->n_tiles_tc, 8 * h->num_sms), 256, 0, s>>>(a, h->d_rowexp);
+cudaError_t launch_count_unique(etdm_handle *h, int *d_nu, cudaStream_t s) {
+  const int blocks = (h->n_tiles_tc + 255) / 256;
+  count_unique_kernel<<<std::max(blocks, 1), 256, 0, s>>>(h->d_tile_ptr_tc, h->d_keys_tc,
+                                                          h->n_tiles_tc, d_nu);
   return cudaGetLastError();
 }
 
+cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(xr_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStageBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(xv_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kStageBytes);
+  if (e != cudaSuccess) return e;
+  const int blocks = std::min(h->n_tiles_tc, 4 * h->num_sms);
+  xr_build_kernel<<<blocks, 256, kStageBytes, s>>>(tc_args(h));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  xv_build_kernel<<<blocks, 256, kStageBytes, s>>>(tc_args(h));
+  return cudaGetLastError();
+}
+
+void tc_tile_sizes(int nu, int *rho_steps, int *v_entries) {
+  *rho_steps = rsteps(nu);
+  *v_entries = vpad(nu);
+}
+
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
-  oslice_kernel<<<h->N, 256, 0, s>>>(h->d_O, h->M, h->N, h->d_Osl, h->d_oscale, h->d_dO);
+  oslice_kernel<<<h->N, 256, 0, s>>>(h->d_O, h->M, h->N, h->N + (h->N & 1), h->d_Osl, h->d_oscale,
+                                     h->d_dO);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = 7 * (size_t)kChunkBytes;
+  const int nmc = (h->N + kNmax - 1) / kNmax;
+  const size_t sm = (size_t)kRhoStages * kRhoStage + (size_t)nmc * kNmax * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
@@ -849,18 +1187,22 @@ cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
 }
 
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = (size_t)kVStages * kVStage;
+  const size_t sm = (size_t)kVStages * kVStage + 2 * (size_t)kVTileBuf;
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int copies = std::min(h->n_tiles_tc, h->n_vcopies);
+  const TcArgs a = tc_args(h);
+  const long total = (long)h->n_tiles_tc * kTP;
   const size_t MM = (size_t)h->M * h->M;
-  e = cudaMemsetAsync(h->d_Vpriv, 0, (size_t)copies * MM * sizeof(float2), s);
+  e = cudaMemsetAsync(h->d_Vfix, 0, (MM + 1) * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  vmat_tc_kernel<<<copies, kVThreads, sm, s>>>(tc_args(h));
+  vtile_kernel<<<(int)std::min<long>((total + 255) / 256, 8 * h->num_sms), 256, 0, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  vpriv_reduce_kernel<<<256, 256, 0, s>>>(h->d_Vpriv, copies, h->M, h->d_Vfin);
+  vmat_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kVThreads, sm, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  vfix_kernel<<<(int)std::min<size_t>((MM + 255) / 256, 1024), 256, 0, s>>>(h->d_Vfix, h->M, h->d_Vfin);
   return cudaGetLastError();
 }
 
