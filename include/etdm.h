@@ -152,8 +152,10 @@ enum {
   ETDM_ARR_VEXT = 4,     /* [G] f64 external potential on the grid */
   ETDM_ARR_RHO = 5,      /* [G] f64 density of the last evaluation */
   ETDM_ARR_VTOT = 6,     /* [G] f64 v_ext + v_H + v_x of the last evaluation */
-  ETDM_ARR_H = 7,        /* [M*M] f64 Hamiltonian matrix, last evaluation */
-  ETDM_ARR_D = 8,        /* [M*M] f64 density matrix, last evaluation */
+  ETDM_ARR_H = 7,        /* [M*M] f64 Hamiltonian matrix, last evaluation (mixed
+                            precision: its grid part V only) */
+  ETDM_ARR_D = 8,        /* [M*M] f64 density matrix, last FP64-path evaluation
+                            (the mixed path forms the density from O instead) */
   ETDM_ARR_UOCC = 9,     /* [M*N] f64 occupied columns of exp(A) */
   ETDM_ARR_TILE_PTR = 10,/* [n_tiles+1] i32 list offsets */
   ETDM_ARR_TILE_KEYS = 11,/* [entries] i32 keys mu*512 + (nx+4)*64 + (ny+4)*8 + (nz+4) */

@@ -427,6 +427,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_Osl = dalloc<uint2>(h, (long)M * (h->N + (h->N & 1)));  // rows padded to even length
     h->d_oscale = dalloc<float>(h, h->N);
     h->d_dO = dalloc<double>(h, (long)M * h->N);
+    h->d_TO = dalloc<double>(h, (long)M * h->N);
     h->d_Vfix = dalloc<unsigned long long>(h, (long)M * M + 1);
     h->d_Vfin = dalloc<double>(h, (long)M * M);
   }
@@ -466,7 +467,8 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   h->d_Uocc = dalloc<double>(h, (long)M * N);
   h->d_O = dalloc<double>(h, (long)M * N);
   h->d_P = dalloc<double>(h, NN);
-  h->d_Qk = dalloc<double>(h, NN * kTaylor);
+  h->d_Qk = dalloc<double>(h, NN * 12);  // series workspace (Paterson-Stockmeyer)
+  h->d_Wr = dalloc<double>(h, NN * 11);  // its reverse workspace
   h->d_Kt = dalloc<double>(h, NN * (kJmax + 1));
   h->d_St = dalloc<double>(h, NN * (kJmax + 1));
   h->d_Gbar = dalloc<double>(h, (long)M * N);

@@ -8,7 +8,12 @@
 // of P.  They are evaluated without an eigendecomposition: Taylor series of
 // Q = P / 4^j with |Q|_F <= 1, then j doubling steps
 //   cos 2x = 1 + 4k + 2k^2 (k = cos x - 1),  sin 2x / 2x = (sin x / x) cos x,
-// which keep the small quantity k = cos x - 1 without cancellation.
+// which keep the small quantity k = cos x - 1 without cancellation.  The two
+// degree-10 series are evaluated by Paterson-Stockmeyer blocking: Q^2, Q^3,
+// Q^4, blocks B_i = sum_r c_{4i+r} Q^r (r < 4), and Horner in Q^4,
+//   p(Q) = B_0 + Q^4 (B_1 + Q^4 B_2),
+// four dependent product steps instead of nine; the reverse pass follows the
+// same graph backwards.
 //
 // Each chain of small dependent products runs as ONE cooperative launch over
 // all SMs with a bounded grid barrier between products (FP64 is the scarce
@@ -21,7 +26,13 @@
 
 namespace etdm {
 
-constexpr int BM = 8, BN = 16, BK = 32, NT = 128;
+constexpr int BM = 8, BN = 16, BK = 32, NT = 256;
+constexpr int NG = 128;  // threads of one K group: a tile's K chunks alternate between two groups
+static_assert(kTaylor >= 8 && kTaylor <= 11, "Paterson-Stockmeyer blocks assume degree 8..11");
+// slots of the forward series workspace Qk
+enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc0, kBc1, kBc2, kBs0, kBs1, kBs2, kTc, kTs, kQslots };
+// slots of the reverse workspace Wr
+enum { kQ4b = 0, kTcb, kTsb, kBc2b, kBs2b, kQ1bB, kQ2bB, kQ3b, kQ2b, kQ1bt, kQ1b, kWslots };
 
 __device__ __forceinline__ double opA(const Prod &P, int i, int k) {
   return P.ta ? P.A[(long)k * P.lda + i] : P.A[(long)i * P.lda + k];
@@ -30,45 +41,85 @@ __device__ __forceinline__ double opB(const Prod &P, int k, int j) {
   return P.tb ? P.B[(long)j * P.ldb + k] : P.B[(long)k * P.ldb + j];
 }
 
-// One output tile (BM x BN) of a phase, computed by the 128 threads of a block.
-__device__ void phase_tile(const Phase &ph, int tile, double (*As)[BK + 1],
-                           double (*Bs)[BN + 1]) {
+// One output tile (BM x BN) of a phase.  The block's two groups of 128 threads
+// (one output each) take alternate K chunks and add their partial sums at the
+// end, which doubles the FP64 work in flight per SM.  Each group double-buffers
+// its chunks in shared memory: the next chunk's global loads are in flight in
+// registers while the current one is multiplied.
+constexpr int kLa = BM * BK / NG, kLb = BK * BN / NG;  // elements per thread per chunk
+__device__ void phase_tile(const Phase &ph, int tile, double (*As)[2][BM][BK + 1],
+                           double (*Bs)[2][BK][BN + 1], double *part) {
   const int tilesN = (ph.n + BN - 1) / BN;
   const int r0 = (tile / tilesN) * BM, c0 = (tile % tilesN) * BN;
-  const int tid = threadIdx.x, ty = tid / BN, tx = tid % BN;
+  const int tid = threadIdx.x % NG, grp = threadIdx.x / NG;
+  const int ty = tid / BN, tx = tid % BN;
   const int i = r0 + ty, j = c0 + tx;
+  const int nch = (ph.k + BK - 1) / BK, nit = (nch + 1) / 2;
   double acc = 0.0;
   for (int q = 0; q < ph.np; ++q) {
-    const Prod &P = ph.p[q];
+    const Prod P = ph.p[q];
     if (P.alpha == 0.0) continue;
-    double accq = 0.0;
-    for (int k0 = 0; k0 < ph.k; k0 += BK) {
-      for (int e = tid; e < BM * BK; e += NT) {
-        int ii, kk;
-        if (P.ta) { kk = e / BM; ii = e % BM; } else { ii = e / BK; kk = e % BK; }
-        int gi = r0 + ii, gk = k0 + kk;
-        As[ii][kk] = (gi < ph.m && gk < ph.k) ? opA(P, gi, gk) : 0.0;
+    // this thread's load slots: (row, k) of A and (k, col) of B within a chunk
+    int ai[kLa], ak[kLa], bk[kLb], bj[kLb];
+#pragma unroll
+    for (int u = 0; u < kLa; ++u) {
+      const int e = tid + u * NG;
+      if (P.ta) { ak[u] = e / BM; ai[u] = e % BM; } else { ai[u] = e / BK; ak[u] = e % BK; }
+    }
+#pragma unroll
+    for (int u = 0; u < kLb; ++u) {
+      const int e = tid + u * NG;
+      if (P.tb) { bj[u] = e / BK; bk[u] = e % BK; } else { bk[u] = e / BN; bj[u] = e % BN; }
+    }
+    double ra[kLa], rb[kLb];
+    auto load = [&](int c) {  // chunk c (zeros beyond K)
+      const int k0 = c * BK;
+#pragma unroll
+      for (int u = 0; u < kLa; ++u) {
+        const int gi = r0 + ai[u], gk = k0 + ak[u];
+        ra[u] = (gi < ph.m && gk < ph.k) ? opA(P, gi, gk) : 0.0;
       }
-      for (int e = tid; e < BK * BN; e += NT) {
-        int kk, jj;
-        if (P.tb) { jj = e / BK; kk = e % BK; } else { kk = e / BN; jj = e % BN; }
-        int gk = k0 + kk, gj = c0 + jj;
-        Bs[kk][jj] = (gk < ph.k && gj < ph.n) ? opB(P, gk, gj) : 0.0;
+#pragma unroll
+      for (int u = 0; u < kLb; ++u) {
+        const int gk = k0 + bk[u], gj = c0 + bj[u];
+        rb[u] = (gk < ph.k && gj < ph.n) ? opB(P, gk, gj) : 0.0;
       }
-      __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < BK; ++kk) accq = fma(As[ty][kk], Bs[kk][tx], accq);
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int u = 0; u < kLa; ++u) As[grp][buf][ai[u]][ak[u]] = ra[u];
+#pragma unroll
+      for (int u = 0; u < kLb; ++u) Bs[grp][buf][bk[u]][bj[u]] = rb[u];
+    };
+    load(grp);
+    store(0);
+    __syncthreads();
+    double ac[4] = {0.0, 0.0, 0.0, 0.0};  // four independent FMA chains
+    for (int it = 0; it < nit; ++it) {  // this group's chunks grp, grp + 2, ...
+      const int buf = it & 1;
+      const bool more = it + 1 < nit;
+      if (more) load(2 * (it + 1) + grp);
+#pragma unroll
+      for (int kk = 0; kk < BK; kk += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          ac[u] = fma(As[grp][buf][ty][kk + u], Bs[grp][buf][kk + u][tx], ac[u]);
+      }
+      if (more) store(buf ^ 1);
       __syncthreads();
     }
-    acc += P.alpha * accq;
+    acc += P.alpha * ((ac[0] + ac[1]) + (ac[2] + ac[3]));
   }
-  if (i < ph.m && j < ph.n) {
-    double v = acc;
+  if (grp == 1) part[tid] = acc;
+  __syncthreads();
+  if (grp == 0 && i < ph.m && j < ph.n) {
+    double v = acc + part[tid];
     if (ph.C1) v += ph.beta1 * ph.C1[(long)i * ph.ldc1 + j];
     if (ph.C2) v += ph.beta2 * ph.C2[(long)i * ph.ldc2 + j];
     if (i == j) v += ph.diag;
     ph.out[(long)i * ph.ldo + j] = v;
   }
+  __syncthreads();
 }
 
 __device__ __forceinline__ int phase_tiles(const Phase &ph) {
@@ -78,14 +129,15 @@ __device__ __forceinline__ int phase_tiles(const Phase &ph) {
 
 // Run independent phases over one shared tile index space (no barrier).
 __device__ void run_phases(const Phase *ph, int count) {
-  __shared__ double As[BM][BK + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ double As[2][2][BM][BK + 1];
+  __shared__ double Bs[2][2][BK][BN + 1];
+  __shared__ double part[NG];
   int total = 0;
   for (int c = 0; c < count; ++c) total += phase_tiles(ph[c]);
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int c = 0, base = 0;
     while (t - base >= phase_tiles(ph[c])) { base += phase_tiles(ph[c]); ++c; }
-    phase_tile(ph[c], t - base, As, Bs);
+    phase_tile(ph[c], t - base, As, Bs, part);
   }
 }
 
@@ -111,7 +163,7 @@ __device__ __forceinline__ Phase mkphase(int m, int n, int k, double *out, int l
   } while (0)
 
 // Forward: P, j, Q^k, Taylor series, doublings, U_occ = [cos sqrt P; -A^T s(P)],
-// O = C0 U_occ, D = 2 O O^T, H <- T.
+// O = C0 U_occ, then D = 2 O O^T and H <- T (FP64 grid passes) or T O (mixed).
 __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
   const int M = a.M, N = a.N, V = a.V;
   const long NN = (long)N * N;
@@ -151,24 +203,59 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     return;
   }
   if (gtid == 0) { a.flags[FLAG_J] = J; a.scal[0] = sc; }
-  for (long e = gtid; e < NN; e += gstride) a.Qk[e] = sc * a.P[e];
+  double *const Qs = a.Qk;
+  auto slot = [&](int k) { return Qs + (long)k * NN; };
+  for (long e = gtid; e < NN; e += gstride) slot(kQ1)[e] = sc * a.P[e];
   BARRIER_OR_RETURN();
-  for (int k = 2; k <= kTaylor; ++k) {  // Q^k = Q Q^(k-1)
-    Phase ph = mkphase(N, N, N, a.Qk + (long)(k - 1) * NN, N);
-    ph.np = 1; ph.p[0] = mk(a.Qk, N, 0, a.Qk + (long)(k - 2) * NN, N, 0, 1.0);
+  {  // Q^2
+    Phase ph = mkphase(N, N, N, slot(kQ2), N);
+    ph.np = 1; ph.p[0] = mk(slot(kQ1), N, 0, slot(kQ1), N, 0, 1.0);
     run_phases(&ph, 1);
-    BARRIER_OR_RETURN();
   }
-  for (long e = gtid; e < NN; e += gstride) {
-    int i = (int)(e / N), c = (int)(e % N);
-    double kv = 0.0, sv = 0.0;
-    for (int k = kTaylor; k >= 1; --k) {
-      double q = a.Qk[(long)(k - 1) * NN + e];
-      kv += a.ck[k] * q;
-      sv += a.sk[k] * q;
+  BARRIER_OR_RETURN();
+  {  // Q^3 = Q Q^2, Q^4 = Q^2 Q^2
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, slot(kQ3), N);
+    ph[0].np = 1; ph[0].p[0] = mk(slot(kQ1), N, 0, slot(kQ2), N, 0, 1.0);
+    ph[1] = mkphase(N, N, N, slot(kQ4), N);
+    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
+    run_phases(ph, 2);
+  }
+  BARRIER_OR_RETURN();
+  for (long e = gtid; e < NN; e += gstride) {  // blocks B_i = sum_r c_{4i+r} Q^r
+    const int i = (int)(e / N), c = (int)(e % N);
+    const double q[4] = {i == c ? 1.0 : 0.0, slot(kQ1)[e], slot(kQ2)[e], slot(kQ3)[e]};
+    for (int b = 0; b < 3; ++b) {
+      double bc = 0.0, bs = 0.0;
+      for (int r = 0; r < 4; ++r) {
+        const int k = 4 * b + r;
+        if (k <= kTaylor) { bc += a.ck[k] * q[r]; bs += a.sk[k] * q[r]; }
+      }
+      slot(kBc0 + b)[e] = bc;
+      slot(kBs0 + b)[e] = bs;
     }
-    a.Kt[e] = kv;
-    a.St[e] = sv + (i == c ? 1.0 : 0.0);
+  }
+  BARRIER_OR_RETURN();
+  {  // T = B_1 + Q^4 B_2 for both series
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, slot(kTc), N);
+    ph[0].np = 1; ph[0].p[0] = mk(slot(kQ4), N, 0, slot(kBc2), N, 0, 1.0);
+    ph[0].C1 = slot(kBc1); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    ph[1] = mkphase(N, N, N, slot(kTs), N);
+    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, slot(kBs2), N, 0, 1.0);
+    ph[1].C1 = slot(kBs1); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    run_phases(ph, 2);
+  }
+  BARRIER_OR_RETURN();
+  {  // k = cos sqrt(Q) - 1 = B_0 + Q^4 T_c, s = sin sqrt(Q) / sqrt(Q) = B_0 + Q^4 T_s
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, a.Kt, N);
+    ph[0].np = 1; ph[0].p[0] = mk(slot(kQ4), N, 0, slot(kTc), N, 0, 1.0);
+    ph[0].C1 = slot(kBc0); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    ph[1] = mkphase(N, N, N, a.St, N);
+    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, slot(kTs), N, 0, 1.0);
+    ph[1].C1 = slot(kBs0); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    run_phases(ph, 2);
   }
   BARRIER_OR_RETURN();
   for (int t = 0; t < J; ++t) {  // doubling: k' = 4k + 2k^2, s' = s + s k
@@ -200,7 +287,11 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     run_phases(&ph, 1);
   }
   BARRIER_OR_RETURN();
-  {
+  if (a.Vacc) {  // mixed path: the density comes from O on the grid; T O for the kinetic energy and dE/dO
+    Phase ph = mkphase(M, N, M, a.TO, N);
+    ph.np = 1; ph.p[0] = mk(a.T, M, 0, a.O, N, 0, 1.0);
+    run_phases(&ph, 1);
+  } else {
     Phase ph = mkphase(M, M, N, a.D, M);  // D = 2 O O^T (Eq. 12, f = 2)
     ph.np = 1; ph.p[0] = mk(a.O, N, 0, a.O, N, 1, 2.0);
     run_phases(&ph, 1);
@@ -210,6 +301,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
 }
 
 // Reverse: E = Tr(D T) + grid terms; dE/dO = 4 H O; dE/dU = C0^T (4 H O);
+// (mixed path: Tr(D T) = 2 sum O o (T O), 4 H O = 4 T O + 4 V O);
 // back through U_occ, the doublings, the Taylor powers and P = A A^T.
 __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want_grad) {
   const int M = a.M, N = a.N, V = a.V;
@@ -217,63 +309,69 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long gstride = (long)gridDim.x * blockDim.x;
   const bool mixed = a.Vacc != nullptr;
+  const long MN = (long)M * N;
   {
     double s = 0.0;
-    for (long e = gtid; e < MM; e += gstride) s += a.D[e] * a.T[e];
-    if (mixed) {  // H = T + V from the upper-triangle FP32 accumulation
+    if (mixed) {  // Tr(D T) = 2 sum O o (T O); H <- V (symmetric, from the upper triangle)
+      for (long e = gtid; e < MN; e += gstride) s += 2.0 * a.O[e] * a.TO[e];
       for (long e = gtid; e < MM; e += gstride) {
         int i = (int)(e / M), c = (int)(e % M);
-        a.H[e] = a.T[e] + (double)(i <= c ? a.Vacc[e] : a.Vacc[(long)c * M + i]);
+        a.H[e] = i <= c ? a.Vacc[e] : a.Vacc[(long)c * M + i];
       }
-    } else if (want_grad) {  // the grid pass accumulated the upper triangle of H
-      for (long e = gtid; e < MM; e += gstride) {
-        int i = (int)(e / M), c = (int)(e % M);
-        if (i > c) a.H[e] = a.H[(long)c * M + i];
+    } else {
+      for (long e = gtid; e < MM; e += gstride) s += a.D[e] * a.T[e];
+      if (want_grad) {  // the grid pass accumulated the upper triangle of H
+        for (long e = gtid; e < MM; e += gstride) {
+          int i = (int)(e / M), c = (int)(e % M);
+          if (i > c) a.H[e] = a.H[(long)c * M + i];
+        }
       }
     }
     s = block_sum(s);
     if (threadIdx.x == 0) a.red[blockIdx.x] = s;
   }
   BARRIER_OR_RETURN();
-  if (mixed || want_grad) {
-    Phase ph[2];
-    ph[0] = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
-    ph[0].np = 1; ph[0].p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    // mixed path: dE_pot/dO = 4 (H - T) O into Ubar (scratch until Ubar is formed);
-    // the kinetic energy is exact (FP64 D), only the grid energy saw Oq
-    ph[1] = mkphase(M, N, M, a.Ubar, N);
-    ph[1].np = 2;
-    ph[1].p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    ph[1].p[1] = mk(a.T, M, 0, a.O, N, 0, -4.0);
-    run_phases(ph, mixed ? 2 : 1);
+  if (mixed) {
+    // dE_pot/dO = 4 V O into Ubar (scratch until Ubar is formed); the kinetic
+    // energy is exact (FP64 O), only the grid energy saw Oq
+    Phase ph = mkphase(M, N, M, a.Ubar, N);
+    ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
+    run_phases(&ph, 1);
     BARRIER_OR_RETURN();
-  }
-  if (mixed) {  // first-order correction of the density's O quantization
+    // Gbar = dE/dO = 4 T O + 4 V O; first-order correction of the density's O
+    // quantization, sum (4 V O) o (O - Oq)
     double c = 0.0;
-    const long MN = (long)M * N;
-    for (long e = gtid; e < MN; e += gstride) c += a.Ubar[e] * a.dO[e];
+    for (long e = gtid; e < MN; e += gstride) {
+      const double u = a.Ubar[e];
+      a.Gbar[e] = 4.0 * a.TO[e] + u;
+      c += u * a.dO[e];
+    }
     c = block_sum(c);
     if (threadIdx.x == 0) a.red[gridDim.x + blockIdx.x] = c;
     BARRIER_OR_RETURN();
+  } else if (want_grad) {
+    Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
+    ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
+    run_phases(&ph, 1);
+    BARRIER_OR_RETURN();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double kin = 0.0, corr = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) kin += a.red[b];
-    if (mixed)
-      for (int b = 0; b < (int)gridDim.x; ++b) corr += a.red[gridDim.x + b];
-    double t3[3] = {0.0, 0.0, 0.0}, c3[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < a.n_gridpart; ++b) {  // compensated sums
-      for (int q = 0; q < 3; ++q) {
-        double y = a.gridpart[3 * b + q] - c3[q];
-        double tt = t3[q] + y;
-        c3[q] = (tt - t3[q]) - y;
-        t3[q] = tt;
-      }
+  if (blockIdx.x == 0) {  // energy terms: tree sums over the block partials, all threads of block 0
+    double kin = 0.0, corr = 0.0, t3[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      kin += a.red[b];
+      if (mixed) corr += a.red[gridDim.x + b];
     }
-    double E = kin + t3[0] + t3[1] + t3[2] + corr;
-    a.eterms[0] = kin; a.eterms[1] = t3[0]; a.eterms[2] = t3[1]; a.eterms[3] = t3[2] + corr;
-    if (a.E) *a.E = E;
-    if (!(E == E) || isinf(E)) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+    for (int b = threadIdx.x; b < a.n_gridpart; b += blockDim.x)
+      for (int q = 0; q < 3; ++q) t3[q] += a.gridpart[3 * b + q];
+    kin = block_sum(kin);
+    corr = block_sum(corr);
+    for (int q = 0; q < 3; ++q) t3[q] = block_sum(t3[q]);
+    if (threadIdx.x == 0) {
+      const double E = kin + t3[0] + t3[1] + t3[2] + corr;
+      a.eterms[0] = kin; a.eterms[1] = t3[0]; a.eterms[2] = t3[1]; a.eterms[3] = t3[2] + corr;
+      if (a.E) *a.E = E;
+      if (!(E == E) || isinf(E)) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+    }
   }
   if (!want_grad) return;
   {
@@ -314,32 +412,81 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     BARRIER_OR_RETURN();
     kb = kbo; sb = sbo; pp = 1 - pp;
   }
-  // Z_K = c_K Kbar_0 + s_K Sbar_0
-  for (long e = gtid; e < NN; e += gstride)
-    a.Z[0][e] = a.ck[kTaylor] * kb[e] + a.sk[kTaylor] * sb[e];
-  BARRIER_OR_RETURN();
-  int zp = 0;
-  for (int k = kTaylor - 1; k >= 1; --k) {
-    const double *Zin = a.Z[zp];
-    double *Zout = a.Z[1 - zp];
-    Phase ph[2];
-    ph[0] = mkphase(N, N, N, a.Qbar, N);  // Qbar += Z_{k+1} Q^k
-    ph[0].np = 1; ph[0].p[0] = mk(Zin, N, 0, a.Qk + (long)(k - 1) * NN, N, 0, 1.0);
-    if (k < kTaylor - 1) { ph[0].C1 = a.Qbar; ph[0].ldc1 = N; ph[0].beta1 = 1.0; }
-    ph[1] = mkphase(N, N, N, Zout, N);    // Z_k = Q Z_{k+1} + c_k Kbar_0 + s_k Sbar_0
-    ph[1].np = 1; ph[1].p[0] = mk(a.Qk, N, 0, Zin, N, 0, 1.0);
-    ph[1].C1 = kb; ph[1].ldc1 = N; ph[1].beta1 = a.ck[k];
-    ph[1].C2 = sb; ph[1].ldc2 = N; ph[1].beta2 = a.sk[k];
-    run_phases(ph, 2);
-    BARRIER_OR_RETURN();
-    zp = 1 - zp;
-  }
+  // back through k = B_0 + Q^4 T_c, s = B_0 + Q^4 T_s (all forward matrices are
+  // symmetric, so for C = X Y: Xbar += Cbar Y, Ybar += X Cbar)
+  const double *const Qs = a.Qk;
+  auto slot = [&](int k) { return Qs + (long)k * NN; };
+  auto wr = [&](int k) { return a.Wr + (long)k * NN; };
   {
-    const double *Z1 = a.Z[zp];
+    Phase ph[3];
+    ph[0] = mkphase(N, N, N, wr(kQ4b), N);  // Q4bar = kbar T_c + sbar T_s
+    ph[0].np = 2;
+    ph[0].p[0] = mk(kb, N, 0, slot(kTc), N, 0, 1.0);
+    ph[0].p[1] = mk(sb, N, 0, slot(kTs), N, 0, 1.0);
+    ph[1] = mkphase(N, N, N, wr(kTcb), N);  // T_c bar = Q^4 kbar
+    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, kb, N, 0, 1.0);
+    ph[2] = mkphase(N, N, N, wr(kTsb), N);  // T_s bar = Q^4 sbar
+    ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, sb, N, 0, 1.0);
+    run_phases(ph, 3);
+  }
+  BARRIER_OR_RETURN();
+  {  // back through T = B_1 + Q^4 B_2
+    Phase ph[3];
+    ph[0] = mkphase(N, N, N, wr(kQ4b), N);  // Q4bar += T_c bar B_c2 + T_s bar B_s2
+    ph[0].np = 2;
+    ph[0].p[0] = mk(wr(kTcb), N, 0, slot(kBc2), N, 0, 1.0);
+    ph[0].p[1] = mk(wr(kTsb), N, 0, slot(kBs2), N, 0, 1.0);
+    ph[0].C1 = wr(kQ4b); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    ph[1] = mkphase(N, N, N, wr(kBc2b), N);  // B_c2 bar = Q^4 T_c bar
+    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, wr(kTcb), N, 0, 1.0);
+    ph[2] = mkphase(N, N, N, wr(kBs2b), N);  // B_s2 bar = Q^4 T_s bar
+    ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, wr(kTsb), N, 0, 1.0);
+    run_phases(ph, 3);
+  }
+  BARRIER_OR_RETURN();
+  // the blocks' cotangents to the powers: Q^r bar = sum_i c_{4i+r} B_ci bar + s_{4i+r} B_si bar
+  for (long e = gtid; e < NN; e += gstride) {
+    const double bcb[3] = {kb[e], wr(kTcb)[e], wr(kBc2b)[e]};
+    const double bsb[3] = {sb[e], wr(kTsb)[e], wr(kBs2b)[e]};
+    double qb[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < 3; ++b)
+      for (int r = 1; r < 4; ++r) {
+        const int k = 4 * b + r;
+        if (k <= kTaylor) qb[r] += a.ck[k] * bcb[b] + a.sk[k] * bsb[b];
+      }
+    wr(kQ1bB)[e] = qb[1];
+    wr(kQ2bB)[e] = qb[2];
+    wr(kQ3b)[e] = qb[3];
+  }
+  BARRIER_OR_RETURN();
+  {  // back through Q^4 = Q^2 Q^2 and Q^3 = Q Q^2
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, wr(kQ2b), N);  // Q2bar = Q2bar_B + Q4bar Q^2 + Q^2 Q4bar + Q Q3bar
+    ph[0].np = 3;
+    ph[0].p[0] = mk(wr(kQ4b), N, 0, slot(kQ2), N, 0, 1.0);
+    ph[0].p[1] = mk(slot(kQ2), N, 0, wr(kQ4b), N, 0, 1.0);
+    ph[0].p[2] = mk(slot(kQ1), N, 0, wr(kQ3b), N, 0, 1.0);
+    ph[0].C1 = wr(kQ2bB); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    ph[1] = mkphase(N, N, N, wr(kQ1bt), N);  // Qbar_t = Q1bar_B + Q3bar Q^2
+    ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 1.0);
+    ph[1].C1 = wr(kQ1bB); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    run_phases(ph, 2);
+  }
+  BARRIER_OR_RETURN();
+  {  // back through Q^2 = Q Q: Qbar = Qbar_t + Q2bar Q + Q Q2bar
+    Phase ph = mkphase(N, N, N, wr(kQ1b), N);
+    ph.np = 2;
+    ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
+    ph.p[1] = mk(slot(kQ1), N, 0, wr(kQ2b), N, 0, 1.0);
+    ph.C1 = wr(kQ1bt); ph.ldc1 = N; ph.beta1 = 1.0;
+    run_phases(&ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  {  // Q = sc P: Pbar + Pbar^T = sc (Qbar + Qbar^T)
+    const double *Qb = wr(kQ1b);
     for (long e = gtid; e < NN; e += gstride) {
       int i = (int)(e / N), c = (int)(e % N);
-      long et = (long)c * N + i;
-      a.Psym[e] = sc * (a.Qbar[e] + Z1[e] + a.Qbar[et] + Z1[et]);
+      a.Psym[e] = sc * (Qb[e] + Qb[(long)c * N + i]);
     }
   }
   BARRIER_OR_RETURN();
@@ -552,13 +699,13 @@ static DenseArgs dense_args(etdm_handle *h, const double *a) {
   d.M = h->M; d.N = h->N; d.V = h->V;
   d.A = a;
   d.P = h->d_P; d.Qk = h->d_Qk; d.Kt = h->d_Kt; d.St = h->d_St;
-  d.Uocc = h->d_Uocc; d.O = h->d_O; d.D = h->d_D; d.H = h->d_H;
+  d.Uocc = h->d_Uocc; d.O = h->d_O; d.D = h->d_D; d.H = h->d_H; d.TO = h->d_TO;
   d.C0 = h->d_C0; d.T = h->d_T;
   d.Gbar = h->d_Gbar; d.Ubar = h->d_Ubar;
   d.Kbar[0] = h->d_bar2[0]; d.Kbar[1] = h->d_bar2[1];
   d.Sbar[0] = h->d_bar2[2]; d.Sbar[1] = h->d_bar2[3];
   d.Z[0] = h->d_bar2[4]; d.Z[1] = h->d_bar2[5];
-  d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym;
+  d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym; d.Wr = h->d_Wr;
   d.eterms = h->d_eterms;
   d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
   if (h->precision == ETDM_PREC_MIXED && !h->in_setup) { d.Vacc = h->d_Vfin; d.dO = h->d_dO; }

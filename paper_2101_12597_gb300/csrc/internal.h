@@ -67,18 +67,20 @@ struct DenseArgs {
   int M, N, V;
   const double *A;       // a, N x V
   double *P;             // N x N
-  double *Qk;            // [kTaylor][N*N]  Q^1 .. Q^K
+  double *Qk;            // [12][N*N] series workspace: Q^1..Q^4, blocks, Horner terms
   double *Kt;            // [kJmax+1][N*N] cos sqrt(Q_t) - I
   double *St;            // [kJmax+1][N*N] sin sqrt(Q_t)/sqrt(Q_t)
   double *Uocc;          // M x N
   double *O;             // M x N
   double *D;             // M x M
   double *H;             // M x M
+  double *TO;            // M x N, T O (mixed path)
   const double *C0;      // M x M
   const double *T;       // M x M
   double *Gbar, *Ubar;   // M x N
   double *Kbar[2], *Sbar[2], *Z[2];
   double *Qbar, *Abar, *Psym;
+  double *Wr;            // [11][N*N] reverse workspace of the series
   double *g;             // N x V output (may be null)
   double *E;             // scalar output (may be null)
   double *eterms;        // [4] kinetic, external, hartree, exchange
@@ -157,6 +159,7 @@ struct etdm_handle {
   uint2 *d_Osl = nullptr;     // [M][N + N % 2] BF16 slices of O
   float *d_oscale = nullptr;  // [N]
   double *d_dO = nullptr;     // [M][N] O - Oq
+  double *d_TO = nullptr;     // [M][N] T O
   unsigned long long *d_Vfix = nullptr;  // [M*M + 1] V in fixed point, then max|v| bits
   double *d_Vfin = nullptr;   // [M][M] V (upper triangle), FP64
   // matrices
@@ -165,6 +168,7 @@ struct etdm_handle {
   double *d_P = nullptr, *d_Qk = nullptr, *d_Kt = nullptr, *d_St = nullptr;
   double *d_Gbar = nullptr, *d_Ubar = nullptr;
   double *d_bar2[6] = {nullptr};
+  double *d_Wr = nullptr;
   double *d_Qbar = nullptr, *d_Abar = nullptr, *d_Psym = nullptr;
   // grid
   double *d_vext = nullptr, *d_rho = nullptr, *d_vtot = nullptr;
