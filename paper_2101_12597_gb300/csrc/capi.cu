@@ -115,7 +115,6 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
     if (mixed) {
       CUDA_TRY(launch_oslice(h, s));
       CUDA_TRY(launch_rho_tc(h, s));
-      h->launches += 1;
     } else {
       CUDA_TRY(launch_rho_fp64(h, h->d_D, h->d_rho, s));
     }
@@ -123,19 +122,28 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
   }
   {
     StageTimer t(h, s, ETDM_STAGE_POTENTIAL);
-    CUDA_TRY(launch_pack_real(h, h->d_rho, h->d_fft, s));
-    CUDA_TRY(fft3d(h, h->d_fft, -1, s));
-    CUDA_TRY(launch_poisson_scale(h, h->d_fft, s));
-    CUDA_TRY(fft3d(h, h->d_fft, +1, s));
-    CUDA_TRY(launch_potential(h, s));
+    if (mixed) {  // float-pair half-spectrum pipeline; also resets V's fixed-point sums
+      CUDA_TRY(cudaMemsetAsync(h->d_Vfix, 0, ((size_t)h->M * h->M + 1) * sizeof(unsigned long long), s));
+      CUDA_TRY(launch_df_potential(h, s));
+      h->n_gridpart = df_pot_blocks(h);
+    } else {
+      CUDA_TRY(launch_pack_real(h, h->d_rho, h->d_fft, s));
+      CUDA_TRY(fft3d(h, h->d_fft, -1, s));
+      CUDA_TRY(launch_poisson_scale(h, h->d_fft, s));
+      CUDA_TRY(fft3d(h, h->d_fft, +1, s));
+      CUDA_TRY(launch_potential(h, s));
+      h->n_gridpart = kPotBlocks;
+    }
     t.done();
   }
-  h->launches += 12;  // dense forward/reverse, density, pack, 2 x 3 FFT passes, scale, potential
+  // kernels: dense forward and reverse; mixed: O slices, density, 5 potential
+  // passes, V and its fixed-point conversion; FP64: density, pack, 2 x 3 FFT
+  // passes, scale, potential (+ V with the gradient)
+  h->launches += mixed ? 11 : 12;
   if (mixed) {  // also needed for the energy: first-order correction of D's quantization
     StageTimer t(h, s, ETDM_STAGE_VMAT);
     CUDA_TRY(launch_vmat_tc(h, s));
     t.done();
-    h->launches += 1;
   } else if (g) {
     StageTimer t(h, s, ETDM_STAGE_VMAT);
     CUDA_TRY(launch_vmat_fp64(h, h->d_vtot, h->d_H, s));
@@ -430,6 +438,12 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_TO = dalloc<double>(h, (long)M * h->N);
     h->d_Vfix = dalloc<unsigned long long>(h, (long)M * M + 1);
     h->d_Vfin = dalloc<double>(h, (long)M * M);
+    const long half = (long)h->n[0] * h->n[1] * (h->n[2] / 2 + 1);
+    h->d_twf = dalloc<float4>(h, h->n[0] + h->n[1] + h->n[2]);
+    h->d_half = dalloc<float4>(h, half);
+    h->d_rhof = dalloc<float2>(h, h->G);
+    h->d_vextf = dalloc<float2>(h, h->G);
+    h->d_kpois = dalloc<float2>(h, half);
   }
   {
     unsigned long long *d_sum = dalloc<unsigned long long>(h, 1);
@@ -453,11 +467,12 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   h->d_fft = dalloc<double2>(h, h->G);
   h->d_tw = dalloc<double2>(h, h->n[0] + h->n[1] + h->n[2]);
   h->n_gridpart = kPotBlocks;
-  h->d_gridpart = dalloc<double>(h, 3 * kPotBlocks);
+  h->d_gridpart = dalloc<double>(h, 3 * std::max(kPotBlocks, df_pot_blocks(h)));
   CUDA_TRY(launch_twiddles(h, s));
   CUDA_TRY(launch_vext_recip(h, s));
   CUDA_TRY(fft3d(h, h->d_fft, +1, s));
   CUDA_TRY(launch_real_part(h, h->d_fft, h->d_vext, s));
+  if (h->precision == ETDM_PREC_MIXED) CUDA_TRY(launch_df_setup(h, s));  // twiddles, v_ext, Poisson kernel
 
   // dense workspaces
   const int N = h->N, V = h->V;

@@ -161,6 +161,12 @@ struct etdm_handle {
   double *d_dO = nullptr;     // [M][N] O - Oq
   double *d_TO = nullptr;     // [M][N] T O
   unsigned long long *d_Vfix = nullptr;  // [M*M + 1] V in fixed point, then max|v| bits
+  // float-pair potential pipeline of the mixed path
+  float4 *d_twf = nullptr;    // twiddles of the three axes, float-pair complex
+  float4 *d_half = nullptr;   // [nx][ny][nz/2+1] half spectrum
+  float2 *d_rhof = nullptr;   // [G] rho as float pairs
+  float2 *d_vextf = nullptr;  // [G] v_ext as float pairs
+  float2 *d_kpois = nullptr;  // [nx][ny][nz/2+1] Poisson kernel
   double *d_Vfin = nullptr;   // [M][M] V (upper triangle), FP64
   // matrices
   double *d_S = nullptr, *d_T = nullptr, *d_C0 = nullptr;
@@ -245,6 +251,9 @@ cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t 
 // mixed-precision grid passes (mixed.cu)
 cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_count_unique(etdm_handle *h, int *d_nu, cudaStream_t s);
+cudaError_t launch_df_setup(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_df_potential(etdm_handle *h, cudaStream_t s);
+int df_pot_blocks(etdm_handle *h);
 cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);
 void tc_tile_sizes(int nu, int *rho_steps, int *v_entries);
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);

@@ -276,6 +276,7 @@ struct TcArgs {
   const float *oscale;          // [N] 2^g_m
   int Nocc, NoccP;              // occupied orbitals; O-slice row length (even)
   double *rho;                  // [G]
+  float2 *rhof;                 // [G] rho as float pairs
   const double *v;              // [G]
   float2 *vt;                   // [n_tiles][128] v dV at the tile points (float pairs)
   unsigned long long *Vfix;     // [M][M] V (upper triangle) in fixed point, then [M*M] = max|v| bits
@@ -724,7 +725,14 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
           ok = mbar_wait(&R.part_full, ntile & 1, stop);
           const float other = R.part[pe];
           mbar_arrive(&R.part_empty);
-          if (ok && gp >= 0) A.rho[gp] = ldexp((double)rsum + (double)other, 2 * ep - 31);
+          if (ok && gp >= 0) {
+            A.rho[gp] = ldexp((double)rsum + (double)other, 2 * ep - 31);
+            const int e2 = 2 * ep - 31;  // rho below 2^-100 is left out of the float pair
+            const float2 r = e2 >= -100 ? df_add(make_float2(rsum, 0.f), make_float2(other, 0.f))
+                                        : make_float2(0.f, 0.f);
+            const float sc = pow2f(max(e2, -100));
+            A.rhof[gp] = make_float2(r.x * sc, r.y * sc);
+          }
         }
         rsum = 0.f;
         ++ntile;
@@ -1019,30 +1027,6 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   if (tid == 0 && R.stop) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
 }
 
-// v dV at the points of every 4 x 4 x 8 tile, as float pairs in tile order, and
-// max|v| over the grid (as float bits; non-negative floats order as integers)
-__global__ void __launch_bounds__(256) vtile_kernel(TcArgs A) {
-  const long total = (long)A.n_tiles * kTP;
-  float m = 0.f;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const int gp = tile_point(A.g, (int)(e / kTP), (int)(e % kTP));
-    const double v = gp >= 0 ? A.v[gp] : 0.0;
-    const double vv = v * A.dV;
-    const float hi = (float)vv;
-    A.vt[e] = make_float2(hi, (float)(vv - (double)hi));
-    m = fmaxf(m, (float)fabs(v) * 1.0001f);
-  }
-  unsigned b = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-  __shared__ unsigned wm[8];
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = b;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 1; k < 8; ++k) b = max(b, wm[k]);
-    atomicMax((unsigned *)(A.Vfix + (long)A.g.M * A.g.M), b);
-  }
-}
-
 // V (upper triangle) from its fixed-point sums
 __global__ void vfix_kernel(const unsigned long long *Vfix, int M, double *Vout) {
   const int F = vfix_exp((unsigned)Vfix[(long)M * M]);
@@ -1123,6 +1107,7 @@ static TcArgs tc_args(etdm_handle *h) {
   a.Nocc = h->N;
   a.NoccP = h->N + (h->N & 1);
   a.rho = h->d_rho;
+  a.rhof = h->d_rhof;
   a.v = h->d_vtot;
   a.vt = h->d_vt;
   a.Vfix = h->d_Vfix;
@@ -1191,14 +1176,10 @@ cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
+  // the fixed-point sums and max|v| were reset, and v dV laid out in tile
+  // order, by the potential pass
   const TcArgs a = tc_args(h);
-  const long total = (long)h->n_tiles_tc * kTP;
   const size_t MM = (size_t)h->M * h->M;
-  e = cudaMemsetAsync(h->d_Vfix, 0, (MM + 1) * sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  vtile_kernel<<<(int)std::min<long>((total + 255) / 256, 8 * h->num_sms), 256, 0, s>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   vmat_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kVThreads, sm, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
