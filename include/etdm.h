@@ -164,6 +164,8 @@ enum {
   ETDM_ARR_BETA = 14,    /* [1] f64 current beta^(k) */
   ETDM_ARR_TILE_PTR_TC = 15,  /* mixed precision: 4x4x8-tile list offsets (i32) */
   ETDM_ARR_TILE_KEYS_TC = 16, /* mixed precision: 4x4x8-tile list keys (i32) */
+  ETDM_ARR_TILE_NU_TC = 17,   /* mixed precision: functions per 4x4x8 tile, periodic
+                                 images merged (i32, n_tiles entries) */
   ETDM_NARR = 17
 };
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);

@@ -830,6 +830,7 @@ int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
     case ETDM_ARR_BETA: return 8;
     case ETDM_ARR_TILE_PTR_TC: return h->d_tile_ptr_tc ? ((int64_t)h->n_tiles_tc + 1) * 4 : 0;
     case ETDM_ARR_TILE_KEYS_TC: return h->d_keys_tc ? (int64_t)h->n_entries_tc * 4 : 0;
+    case ETDM_ARR_TILE_NU_TC: return h->d_nu_tc ? (int64_t)h->n_tiles_tc * 4 : 0;
     default: return -1;
   }
 }
@@ -861,6 +862,7 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_BETA: src = h->d_lbstate + 3; break;
       case ETDM_ARR_TILE_PTR_TC: src = h->d_tile_ptr_tc; break;
       case ETDM_ARR_TILE_KEYS_TC: src = h->d_keys_tc; break;
+      case ETDM_ARR_TILE_NU_TC: src = h->d_nu_tc; break;
     }
     if (want > 0) CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
   } catch (const Fail &f) {
