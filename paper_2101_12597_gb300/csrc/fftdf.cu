@@ -148,7 +148,9 @@ struct DfPlan {
 };
 
 // In-place (ping-pong) transform of `lines` lines held in b0; returns the buffer
-// holding the result.  Ends with a block barrier.
+// holding the result.  Ends with a block barrier.  BIG: radices 7, 11, 13 are
+// compiled in (only grids with those factors need them; they cost registers).
+template <bool BIG>
 __device__ float4 *df_fft(float4 *b0, float4 *b1, const DfPlan &pl, int lines, const float4 *tw,
                           int sign) {
   int Ns = 1;
@@ -160,9 +162,13 @@ __device__ float4 *df_fft(float4 *b0, float4 *b1, const DfPlan &pl, int lines, c
       case 3: df_stage<3>(in, out, pl.n, Ns, lines, tw, sign); break;
       case 4: df_stage<4>(in, out, pl.n, Ns, lines, tw, sign); break;
       case 5: df_stage<5>(in, out, pl.n, Ns, lines, tw, sign); break;
-      case 7: df_stage<7>(in, out, pl.n, Ns, lines, tw, sign); break;
-      case 11: df_stage<11>(in, out, pl.n, Ns, lines, tw, sign); break;
-      default: df_stage<13>(in, out, pl.n, Ns, lines, tw, sign); break;
+      default:
+        if constexpr (BIG) {
+          if (R == 7) df_stage<7>(in, out, pl.n, Ns, lines, tw, sign);
+          else if (R == 11) df_stage<11>(in, out, pl.n, Ns, lines, tw, sign);
+          else df_stage<13>(in, out, pl.n, Ns, lines, tw, sign);
+        }
+        break;
     }
     __syncthreads();
     Ns *= R;
@@ -195,6 +201,7 @@ struct DfArgs {
 };
 
 // ---- pass 1: z lines, forward, real pairs -> half spectra ----------------------
+template <bool BIG>
 __global__ void __launch_bounds__(kDfThreads) zfwd_kernel(DfArgs a) {
   extern __shared__ __align__(16) float4 zsm[];
   const int nz = a.nz, nzh = a.nzh;
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(kDfThreads) zfwd_kernel(DfArgs a) {
     b0[q] = make_float4(re.x, re.y, im.x, im.y);
   }
   __syncthreads();
-  const float4 *X = df_fft(b0, b1, a.pz, kZPairs, tw, -1);
+  const float4 *X = df_fft<BIG>(b0, b1, a.pz, kZPairs, tw, -1);
   // F_a(k) = (X(k) + conj X(-k)) / 2,  F_b(k) = (X(k) - conj X(-k)) / (2i)
   for (int q = threadIdx.x; q < kZPairs * nzh; q += blockDim.x) {
     const int p = q / nzh, k = q % nzh;
@@ -225,6 +232,7 @@ __global__ void __launch_bounds__(kDfThreads) zfwd_kernel(DfArgs a) {
 }
 
 // ---- passes 2 and 4: y lines (fixed x, kz) --------------------------------------
+template <bool BIG>
 __global__ void __launch_bounds__(kDfThreads) yfft_kernel(DfArgs a, int sign) {
   extern __shared__ __align__(16) float4 ysm[];
   const int ny = a.ny, nzh = a.nzh;
@@ -241,7 +249,7 @@ __global__ void __launch_bounds__(kDfThreads) yfft_kernel(DfArgs a, int sign) {
     }
   }
   __syncthreads();
-  const float4 *Y = df_fft(b0, b1, a.py, lines, tw, sign);
+  const float4 *Y = df_fft<BIG>(b0, b1, a.py, lines, tw, sign);
   for (int q = threadIdx.x; q < kXYLines * ny; q += blockDim.x) {
     const int y = q / kXYLines, l = q % kXYLines;
     if (l < lines) {
@@ -252,6 +260,7 @@ __global__ void __launch_bounds__(kDfThreads) yfft_kernel(DfArgs a, int sign) {
 }
 
 // ---- pass 3: x lines, forward, Poisson kernel, inverse ---------------------------
+template <bool BIG>
 __global__ void __launch_bounds__(kDfThreads) xpois_kernel(DfArgs a) {
   extern __shared__ __align__(16) float4 xsm[];
   const int nx = a.nx, ny = a.ny, nzh = a.nzh;
@@ -266,7 +275,7 @@ __global__ void __launch_bounds__(kDfThreads) xpois_kernel(DfArgs a) {
     if (l < lines) b0[l * nx + x] = a.H[x * stride + q0 + l];
   }
   __syncthreads();
-  float4 *Xf = df_fft(b0, b1, a.px, lines, tw, -1);
+  float4 *Xf = df_fft<BIG>(b0, b1, a.px, lines, tw, -1);
   for (int q = threadIdx.x; q < kXYLines * nx; q += blockDim.x) {
     const int x = q / kXYLines, l = q % kXYLines;
     if (l < lines) {
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(kDfThreads) xpois_kernel(DfArgs a) {
   }
   __syncthreads();
   float4 *other = Xf == b0 ? b1 : b0;
-  const float4 *Xi = df_fft(Xf, other, a.px, lines, tw, +1);
+  const float4 *Xi = df_fft<BIG>(Xf, other, a.px, lines, tw, +1);
   for (int q = threadIdx.x; q < kXYLines * nx; q += blockDim.x) {
     const int x = q / kXYLines, l = q % kXYLines;
     if (l < lines) a.H[x * stride + q0 + l] = Xi[l * nx + x];
@@ -304,6 +313,7 @@ __device__ __forceinline__ float2 warp_fdf_sum(float2 v) {
 }
 
 // ---- pass 5: z lines, inverse, half spectra pairs -> real potentials; potential --
+template <bool BIG>
 __global__ void __launch_bounds__(kDfThreads) zinv_pot_kernel(DfArgs a) {
   extern __shared__ __align__(16) float4 zsm[];
   const int nz = a.nz, nzh = a.nzh;
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(kDfThreads) zinv_pot_kernel(DfArgs a) {
     b0[q] = cx_st(cx_add(va, cx_rot(vb, +1)));
   }
   __syncthreads();
-  const float4 *Zr = df_fft(b0, b1, a.pz, kZPairs, tw, +1);
+  const float4 *Zr = df_fft<BIG>(b0, b1, a.pz, kZPairs, tw, +1);
   const float2 cxp = a.cx;  // (3 / pi)^(1/3)
   float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0;
   float vm = 0.f;
@@ -465,25 +475,33 @@ cudaError_t launch_df_setup(etdm_handle *h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_df_potential(etdm_handle *h, cudaStream_t s) {
-  const DfArgs a = df_args(h);
+template <bool BIG>
+static cudaError_t df_potential(const DfArgs &a, int zb, cudaStream_t s) {
   const size_t smz = (size_t)(a.nz + 2 * kZPairs * a.nz) * sizeof(float4);
   const size_t smy = (size_t)(a.ny + 2 * kXYLines * a.ny) * sizeof(float4);
   const size_t smx = (size_t)(a.nx + 2 * kXYLines * a.nx) * sizeof(float4);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(zfwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(zinv_pot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(yfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(xpois_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
-  const int zb = df_pot_blocks(h);
+  if ((e = cudaFuncSetAttribute(zfwd_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(zinv_pot_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(yfft_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(xpois_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
   const int yb = (int)(((long)a.nx * a.nzh + kXYLines - 1) / kXYLines);
   const int xb = (int)(((long)a.ny * a.nzh + kXYLines - 1) / kXYLines);
-  zfwd_kernel<<<zb, kDfThreads, smz, s>>>(a);
-  yfft_kernel<<<yb, kDfThreads, smy, s>>>(a, -1);
-  xpois_kernel<<<xb, kDfThreads, smx, s>>>(a);
-  yfft_kernel<<<yb, kDfThreads, smy, s>>>(a, +1);
-  zinv_pot_kernel<<<zb, kDfThreads, smz, s>>>(a);
+  zfwd_kernel<BIG><<<zb, kDfThreads, smz, s>>>(a);
+  yfft_kernel<BIG><<<yb, kDfThreads, smy, s>>>(a, -1);
+  xpois_kernel<BIG><<<xb, kDfThreads, smx, s>>>(a);
+  yfft_kernel<BIG><<<yb, kDfThreads, smy, s>>>(a, +1);
+  zinv_pot_kernel<BIG><<<zb, kDfThreads, smz, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_df_potential(etdm_handle *h, cudaStream_t s) {
+  const DfArgs a = df_args(h);
+  bool big = false;
+  for (const DfPlan *p : {&a.px, &a.py, &a.pz})
+    for (int i = 0; i < p->nst; ++i) big = big || p->radix[i] > 5;
+  const int zb = df_pot_blocks(h);
+  return big ? df_potential<true>(a, zb, s) : df_potential<false>(a, zb, s);
 }
 
 }  // namespace etdm

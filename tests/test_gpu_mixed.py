@@ -32,8 +32,11 @@ def _solver(d):
 @pytest.fixture(scope="module")
 def cases():
     out = {}
+    # "odd": every grid extent odd (an unpaired real z line, odd half spectrum,
+    # ragged tiles in all three directions)
     for name, fn in [("tiny", synth.tiny), ("small", synth.config_small_molecule),
-                     ("ragged", synth.ragged_water)]:
+                     ("ragged", synth.ragged_water),
+                     ("odd", lambda: synth.ragged_water(grid=(27, 25, 45), seed=12))]:
         d = fn()
         out[name] = (d, Oracle(d), _solver(d))
     return out
@@ -43,19 +46,23 @@ def _grad_err(g, gref):
     return float(np.abs(g - gref).max() / max(np.abs(gref).max(), 1e-300))
 
 
-@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged", "odd"])
 def test_tc_truncation_lists_bit_exact(which, cases):
     d, o, s = cases[which]
     ptr = s.get_array("tile_ptr_tc")
     keys = s.get_array("tile_keys_tc")
+    nu = s.get_array("tile_nu_tc")
     tile = (4, 4, 8)
     nt = o.n_tiles(tile)
-    assert len(ptr) == nt + 1
+    assert len(ptr) == nt + 1 and len(nu) == nt
     for t in range(nt):
-        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list(tile, t))
+        ref = o.tile_list(tile, t)
+        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], ref)
+        # functions per tile: periodic images of one function merged
+        assert nu[t] == len(np.unique(np.asarray(ref, dtype=np.int64) // 512))
 
 
-@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged", "odd"])
 def test_mixed_energy_gradient_parity(which, cases):
     torch = _torch()
     d, o, s = cases[which]
