@@ -488,15 +488,19 @@ __global__ void __launch_bounds__(256) xv_build_kernel(TcArgs A) {
 // ---- density ---------------------------------------------------------------
 // Warp roles: 0-7 read the accumulators (lane quarter w % 4, column half w / 4),
 // 8-11 lay out the O-slice operand of each K step, 12 streams the X slices and
-// gathers the O-slice rows of the K step's 16 functions, 13 issues the MMAs.
-// A job is (tile, chunk of <= 128 occupied orbitals).
-constexpr int kRhoStages = 4;
+// gathers the O-slice rows of the K step's 16 functions (one bulk copy per run
+// of consecutive function indices when all orbitals fit one chunk: the copy
+// engine's cost is per request), 13 issues the MMAs.  A job is (tile, chunk of
+// <= 128 occupied orbitals).
+constexpr int kRhoStages = 5;
 constexpr int kRhoA = 4 * kSlot;        // X slices I0..I3 of a K step (16 KB, as stored)
 constexpr int kRhoB = 3 * kSlot;        // O slices K0..K2 of a K step (12 KB)
-constexpr int kRhoRow = kNmax * 8;      // one gathered O-slice row (<= 128 orbitals, 1 KB)
+constexpr int kRhoRow = kNmax * 8;      // room for one gathered O-slice row (<= 128 orbitals)
 constexpr int kRhoG = kKs * kRhoRow;    // the K step's 16 rows (16 KB)
 constexpr int kRhoStage = kRhoA + kRhoB + kRhoG;
-constexpr int kRhoEpi = 256, kRhoBld = 128;
+constexpr int kRhoEpiW = 8, kRhoBldW = 4;
+constexpr int kRhoParts = kRhoEpiW / 4;  // column parts per lane quarter
+constexpr int kRhoEpi = kRhoEpiW * 32, kRhoBld = kRhoBldW * 32;
 constexpr int kRhoThreads = kRhoEpi + kRhoBld + 64;
 
 struct RhoBars {
@@ -504,7 +508,7 @@ struct RhoBars {
   uint64_t acc_full, acc_empty, part_full, part_empty, fin;
   uint32_t tbase;
   int stop;
-  float part[kTP];
+  float part[kRhoParts - 1][kTP];
 };
 
 // phi = (acc0 + acc1 + acc2 + acc3) 2^g for 8 columns; adds phi^2
@@ -533,8 +537,8 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     }
     mbar_init(&R.acc_full, 1);
     mbar_init(&R.acc_empty, kRhoEpi);
-    mbar_init(&R.part_full, kRhoEpi / 2);
-    mbar_init(&R.part_empty, kRhoEpi / 2);
+    mbar_init(&R.part_full, (kRhoParts - 1) * kTP);
+    mbar_init(&R.part_empty, kTP);
     mbar_init(&R.fin, 1);
     R.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
   const int njobs = ntl * nmc;
   volatile int *stop = &R.stop;
 
-  if (w == 12) {
+  if (w == kRhoEpiW + kRhoBldW) {
     // ------------- bulk copies: X slices and the O-slice rows of each K step -------------
     int fill = 0;
     bool ok = true;
@@ -581,9 +585,16 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
         const int a = kk * kKs + (lane & 15), r = a >> 5;  // r is the same for the warp
         const int mv = r == 0 ? mu4[0] : r == 1 ? mu4[1] : r == 2 ? mu4[2] : mu4[3];
         const int mu = __shfl_sync(0xffffffffu, mv, a & 31);
-        if (lane < nrow)
-          bulk_g2s(st + kRhoA + kRhoB + lane * kRhoRow, A.Osl + (size_t)mu * A.NoccP + m0, nme * 8,
-                   &R.tma_full[s]);
+        // row c of the staging area (rows nme * 8 bytes apart) <- O-slice row mu_c
+        const int mup = __shfl_up_sync(0xffffffffu, mu, 1);
+        const bool cont = nmc == 1 && lane > 0 && lane < nrow && mu == mup + 1;
+        const unsigned cb = __ballot_sync(0xffffffffu, cont);
+        if (lane < nrow && !cont) {  // a run starts here: rows lane .. lane + len - 1
+          const unsigned after = ~(cb >> (lane + 1));
+          const int len = __ffs(after);  // 1 + the run's continued rows
+          bulk_g2s(st + kRhoA + kRhoB + lane * nme * 8, A.Osl + (size_t)mu * A.NoccP + m0,
+                   len * nme * 8, &R.tma_full[s]);
+        }
       }
     }
     if (lane == 0) {
@@ -592,7 +603,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       for (int s = 0; s < kRhoStages && s < fill; ++s)
         mbar_wait(&R.tma_full[s], ((fill - 1 - s) / kRhoStages) & 1);
     }
-  } else if (w == 13) {
+  } else if (w == kRhoEpiW + kRhoBldW + 1) {
     // ---------------------------------- MMA issue ----------------------------------
     if (lane == 0) {
       int fill = 0;
@@ -636,7 +647,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       mma_commit(&R.fin);  // every MMA issued has completed before the TMEM is released
       mbar_wait(&R.fin, 0);
     }
-  } else if (w >= 8) {
+  } else if (w >= kRhoEpiW) {
     // -------------- O-slice operand, B[m][a] = Oq[mu_a][m], from the gathered rows --------------
     const int bt = tid - kRhoEpi;
     int fill = 0;
@@ -645,6 +656,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
       const int nk = A.xr_off[t + 1] - A.xr_off[t], nu = A.nu[t];
       const int nm = min(kNmax, A.Nocc - mc * kNmax);
+      const int nme = min(kNmax, A.NoccP - mc * kNmax);  // staged row length (even)
       const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
       for (int kk = 0; kk < nk; ++kk, ++fill) {
         const int s = fill % kRhoStages, use = fill / kRhoStages;
@@ -659,7 +671,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
           for (int u = 0; u < 8; ++u) {
             const int c = h * 8 + u;
             uint2 o = make_uint2(0u, 0u);
-            if (c < nrow && m < nm) o = *(const uint2 *)(G + c * kRhoRow + m * 8);
+            if (c < nrow && m < nm) o = *(const uint2 *)(G + (c * nme + m) * 8);
             w01[u] = o.x;
             w2[u] = o.y;
           }
@@ -684,7 +696,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     // ---------------------------- accumulator read-out ------------------------------
     // phi_pm = 2^(e_p + g_m - 16) y with y = acc0 + acc1 + acc2 + acc3;
     // rho_p = 2 sum_m phi_pm^2 (every term positive)
-    const int quad = w & 3, half = w >> 2;
+    const int quad = w & 3, part = w >> 2;
     const int pe = quad * 32 + lane;
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
     float rsum = 0.f;
@@ -699,9 +711,9 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       ok = __all_sync(0xffffffffu, mbar_wait(&R.acc_full, j & 1, stop));
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // this warp's column half in chunks of 8, the next chunk's loads in flight
-      // while the current one is summed
-      const int cb = half * (nmpad / 2), ce = cb + nmpad / 2;
+      // this warp's column part in chunks of 8, the next chunk's loads in
+      // flight while the current one is summed
+      const int cb = part * (nmpad / kRhoParts), ce = cb + nmpad / kRhoParts;
       const float *f = fs + mc * kNmax;
       uint32_t ra[32], rb[32];
       tmem_ld_issue(tmem + lanebits + cb, ra);
@@ -716,20 +728,21 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&R.acc_empty);
-      if (mc == nmc - 1) {  // the tile is done: add the two column halves
-        if (half == 1) {
+      if (mc == nmc - 1) {  // the tile is done: add the column parts
+        if (part > 0) {
           if (ntile > 0) ok = mbar_wait(&R.part_empty, (ntile - 1) & 1, stop);
-          R.part[pe] = rsum;
+          R.part[part - 1][pe] = rsum;
           mbar_arrive(&R.part_full);
         } else {
           ok = mbar_wait(&R.part_full, ntile & 1, stop);
-          const float other = R.part[pe];
+          float2 r = make_float2(rsum, 0.f);
+#pragma unroll
+          for (int q = 0; q < kRhoParts - 1; ++q) r = df_add(r, make_float2(R.part[q][pe], 0.f));
           mbar_arrive(&R.part_empty);
           if (ok && gp >= 0) {
-            A.rho[gp] = ldexp((double)rsum + (double)other, 2 * ep - 31);
+            A.rho[gp] = ldexp((double)r.x + (double)r.y, 2 * ep - 31);
             const int e2 = 2 * ep - 31;  // rho below 2^-100 is left out of the float pair
-            const float2 r = e2 >= -100 ? df_add(make_float2(rsum, 0.f), make_float2(other, 0.f))
-                                        : make_float2(0.f, 0.f);
+            if (e2 < -100) r = make_float2(0.f, 0.f);
             const float sc = pow2f(max(e2, -100));
             A.rhof[gp] = make_float2(r.x * sc, r.y * sc);
           }
@@ -752,7 +765,8 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
 // (rows = list functions i, the accumulator lanes) and X^T (columns j), both
 // in four exact integer slices, slice orders 0..3 in four FP32 accumulators.
 // Warp roles: 0-15 read the accumulators (lane quarter w % 4, every fourth
-// 8-column chunk by w / 4) and add them into V by fixed-point reductions; 16-23
+// 8-column chunk by w / 4) into a staged triangle, hand them back, and add the
+// staged values into V by fixed-point reductions; 16-23
 // build W from the X^T slices and v; 24 streams the X^T slices and the tile
 // buffers (v at the points, list entries); 25 issues the MMAs.  Lane i takes the
 // columns j <= i and adds into V[mu_j][mu_i] (mu_j <= mu_i), so a warp's
@@ -765,10 +779,15 @@ constexpr int kVEpiW = 16, kVBldW = 8;  // warps: 0-15 read-out, 16-23 build W
 constexpr int kVEpi = kVEpiW * 32, kVBld = kVBldW * 32;
 constexpr int kVThreads = kVEpi + kVBld + 64;
 constexpr int kVTileBuf = kTP * 8 + kNmax * 16;  // v pairs + list entries (3 KB)
+constexpr int kVTri = kNmax * (kNmax + 1) / 2;     // lower triangle of V_loc (float pairs)
+
+// start of column j of the column-major lower triangle of an n x n matrix
+__device__ __forceinline__ int tri_col(int j, int n) { return j * n - (j * (j - 1)) / 2; }
 
 struct VBars {
   uint64_t tma_full[kVStages], bld_full[kVStages], empty[kVStages];
   uint64_t tile_full[2], tile_empty[2], acc_full, acc_empty, fin;
+  uint64_t stage_full, stage_free;  // read-out phases 1 -> 2 and 2 -> next 1
   uint32_t tbase;
   int stop;
 };
@@ -779,33 +798,6 @@ __device__ __forceinline__ float tile_vmax(const float2 *vt) {
   for (int p = (threadIdx.x & 31); p < kTP; p += 32) m = fmaxf(m, fabsf(vt[p].x));
   // non-negative floats order as their bit patterns
   return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-}
-
-// V_loc = 2^(e_i + e_j - 16) y, y = acc0 + acc1 + acc2 + acc3, for 8 columns
-// j = c0 .. c0+7 <= i of lane i, added into V[mu_j][mu_i] in fixed point (ub =
-// 2^(e_i - 8 - F), ve[j].y = 2^(e_j - 8)).  The column entries are read and all
-// eight values formed before the first reduction is issued.
-__device__ __forceinline__ void vfix_add8(const TcArgs &A, const uint32_t (&r)[32], const float4 *ve,
-                                          int c0, int i, int nu, int mui, float ub, int M) {
-  float2 e[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) e[c] = *(const float2 *)&ve[c0 + c];  // (mu bits, 2^(e_j - 8))
-  long long val[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float y0 = __uint_as_float(r[c]);
-    float lo = __uint_as_float(r[8 + c]) + (__uint_as_float(r[16 + c]) + __uint_as_float(r[24 + c]));
-    const float hi = y0 + lo;
-    lo = lo - (hi - y0);
-    const float f = ub * e[c].y;  // exact: a product of powers of two
-    val[c] = f2ll_trunc(hi * f) + f2ll_trunc(lo * f);
-  }
-  if (i < nu) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      if (c0 + c <= i)
-        atomicAdd(A.Vfix + (long)__float_as_int(e[c].x) * M + mui, (unsigned long long)val[c]);
-  }
 }
 
 __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
@@ -827,6 +819,8 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     mbar_init(&R.acc_full, 1);
     mbar_init(&R.acc_empty, kVEpi);
     mbar_init(&R.fin, 1);
+    mbar_init(&R.stage_full, kVEpi);
+    mbar_init(&R.stage_free, kVEpi);
     R.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -835,6 +829,8 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = R.tbase;
+  float2 *vst = (float2 *)(tbuf + 2 * kVTileBuf);  // staged V_loc, column-major lower triangle
+  float *ubs = (float *)(vst + kVTri);              // per-row scales of the tile
   // a contiguous run of tiles per CTA: CTAs running at the same time work in
   // different parts of the box and rarely add into the same entries of V
   const int tbeg = (int)((long)A.n_tiles * blockIdx.x / gridDim.x);
@@ -984,6 +980,11 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     if (!ok) atomicExch((int *)stop, 1);
   } else {
     // ------------------------- accumulator read-out into V ----------------------------
+    // phase 1 (holds the accumulators): V_loc as float pairs (hi, lo) of y =
+    // acc0 + acc1 + acc2 + acc3 into the staged lower triangle, then the
+    // accumulators go back to the MMA thread; phase 2 (overlaps the next tile's
+    // MMAs): scale, convert to fixed point and add into V, a warp per column j,
+    // lanes along i, so the reductions into V[mu_j][mu_i] run along a row of V
     const int quad = w & 3, part = w >> 2;
     const int i = quad * 32 + lane;  // accumulator lane = W row
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
@@ -993,29 +994,55 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
       const int t = tbeg + it, mb = it & 1;
       const int nu = A.nu[t];
       ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop) &&
-                                       mbar_wait(&R.acc_full, it & 1, stop));
+                                       mbar_wait(&R.acc_full, it & 1, stop) &&
+                                       (it == 0 || mbar_wait(&R.stage_free, (it - 1) & 1, stop)));
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint8_t *tb = tbuf + mb * kVTileBuf;
       const float4 *ve = (const float4 *)(tb + kTP * 8);
-      const float vmax = tile_vmax((const float2 *)tb);
-      int mui = 0;
-      float ub = 0.f;  // 2^(e_i - 8 - F): W row scale over the fixed-point unit
-      if (i < nu) {
-        const float4 e = ve[i];
-        mui = __float_as_int(e.x);
-        ub = pow2f(max(slice_exp(e.z * vmax * 1.0001f) - 8 - fixe, -126));
+      if (part == 0) {  // 2^(e_i - 8 - F): W row scale over the fixed-point unit
+        const float vmax = tile_vmax((const float2 *)tb);
+        ubs[i] = i < nu ? pow2f(max(slice_exp(ve[i].z * vmax * 1.0001f) - 8 - fixe, -126)) : 0.f;
       }
-      // columns j <= i of this warp's lanes, every fourth 8-column chunk
+      // phase 1: columns j <= i of this warp's lanes, every fourth 8-column chunk
       const int jend = quad * 32 < nu ? min(quad * 32 + 32, nu) : 0;
       for (int c0 = part * 8; c0 < jend; c0 += 32) {
         uint32_t ra[32];
         tmem_ld_issue(tmem + lanebits + c0, ra);
         tmem_ld_wait(ra);
-        vfix_add8(A, ra, ve, c0, i, nu, mui, ub, M);
+        if (i < nu) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int j = c0 + c;
+            if (j <= i) {
+              const float y0 = __uint_as_float(ra[c]);
+              float lo = __uint_as_float(ra[8 + c]) +
+                         (__uint_as_float(ra[16 + c]) + __uint_as_float(ra[24 + c]));
+              const float hi = y0 + lo;
+              lo = lo - (hi - y0);
+              vst[tri_col(j, nu) + i - j] = make_float2(hi, lo);
+            }
+          }
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&R.acc_empty);
+      mbar_arrive(&R.stage_full);
+      ok = __all_sync(0xffffffffu, mbar_wait(&R.stage_full, it & 1, stop));
+      if (!ok) break;
+      // phase 2: column j = w, w + 16, ..; rows i = j + lane, j + lane + 32, ..
+      for (int j = w; j < nu; j += kVEpiW) {
+        const float4 ej = ve[j];
+        const int muj = __float_as_int(ej.x);
+        const float2 *col = vst + tri_col(j, nu) - j;
+        for (int r = j + lane; r < nu; r += 32) {
+          const float2 y = col[r];
+          const float f = ubs[r] * ej.y;  // exact: a product of powers of two
+          const long long val = f2ll_trunc(y.x * f) + f2ll_trunc(y.y * f);
+          atomicAdd(A.Vfix + (long)muj * M + __float_as_int(ve[r].x), (unsigned long long)val);
+        }
+      }
+      mbar_arrive(&R.stage_free);
       __syncwarp();
       if (lane == 0) mbar_arrive(&R.tile_empty[mb]);
     }
@@ -1172,7 +1199,8 @@ cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
 }
 
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = (size_t)kVStages * kVStage + 2 * (size_t)kVTileBuf;
+  const size_t sm = (size_t)kVStages * kVStage + 2 * (size_t)kVTileBuf +
+                    (size_t)kVTri * sizeof(float2) + kNmax * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
