@@ -148,6 +148,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // Issue the loads of 8 columns (from column address t) of the four slice-order
 // accumulators, 128 columns apart, for this warp's lane quarter: r[8k + c] =
 // accumulator k, column c.  The registers are valid only after tmem_ld_wait(r).
+// the same for streams read once: the lines are marked first for eviction from
+// L2, which keeps data that is reused (V's fixed-point sums, O slices) resident
+__device__ __forceinline__ void bulk_g2s_stream(void *dst, const void *src, uint32_t bytes,
+                                                uint64_t *mbar) {
+  asm volatile(
+      "{ .reg .b64 pol; createpolicy.fractional.L2::evict_first.b64 pol, 1.0; "
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], pol; }" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(mbar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_issue(uint32_t t, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
@@ -579,7 +591,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
         uint8_t *st = dsm + s * kRhoStage;
         if (lane == 0) {
           mbar_expect_tx(&R.tma_full[s], kRhoA + nrow * nme * 8);
-          bulk_g2s(st, A.xr + (size_t)(k0 + kk) * kRhoA, kRhoA, &R.tma_full[s]);
+          bulk_g2s_stream(st, A.xr + (size_t)(k0 + kk) * kRhoA, kRhoA, &R.tma_full[s]);
         }
         __syncwarp();
         const int a = kk * kKs + (lane & 15), r = a >> 5;  // r is the same for the warp
@@ -856,7 +868,8 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
           const int s = fill % kVStages, use = fill / kVStages;
           if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
           mbar_expect_tx(&R.tma_full[s], np * 128);
-          bulk_g2s(dsm + s * kVStage + kVA, src + (size_t)kk * np * 128, np * 128, &R.tma_full[s]);
+          bulk_g2s_stream(dsm + s * kVStage + kVA, src + (size_t)kk * np * 128, np * 128,
+                          &R.tma_full[s]);
         }
       }
       if (!ok) atomicExch((int *)stop, 1);
@@ -1038,6 +1051,8 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
         for (int r = j + lane; r < nu; r += 32) {
           const float2 y = col[r];
           const float f = ubs[r] * ej.y;  // exact: a product of powers of two
+          // a contribution below the fixed-point unit truncates to zero: nothing to add
+          if (!(fabsf(y.x * f) >= 1.f)) continue;
           const long long val = f2ll_trunc(y.x * f) + f2ll_trunc(y.y * f);
           atomicAdd(A.Vfix + (long)muj * M + __float_as_int(ve[r].x), (unsigned long long)val);
         }
