@@ -33,7 +33,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ETDM energy+gradient evals/sec vs plain FP64 GPU path at |dE|<1e-6 Ha"
-WORKLOAD = "water32: 96 atoms, M=256, N=128, 96^3 grid, 9.9 A box, r_c=4 A"
+WORKLOADS = {
+    "water32": "water32: 96 atoms, M=256, N=128, 96^3 grid, 9.9 A box, r_c=4 A",
+    "small": "small molecule: 8 atoms, M=16, N=4, 32^3 grid, 6.4 A box",
+}
+WORKLOAD = WORKLOADS["water32"]
+
+
+def workload_system(name):
+    import etdm_synth as synth
+    return synth.config_water32() if name == "water32" else synth.config_small_molecule()
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 rate of a GB300 (no measured figure)
 HBM_FALLBACK_GBS = 6800.0
 BF16_FALLBACK_TFLOPS = 1900.0
@@ -135,9 +144,10 @@ def reduce_sum(x, world, device):
     return float(t.item())
 
 
-def cpu_baseline(d, budget_s=20.0, max_evals=6):
+def cpu_baseline(d, budget_s=20.0, max_evals=6, workload=None):
     """The oracle as it stands on this host's cores: energy+gradient evaluations
     of the same workload (set-up not timed)."""
+    workload = workload or WORKLOAD
     from oracle.etdm_oracle import Oracle
     o = Oracle(d)
     o.reference()
@@ -151,7 +161,7 @@ def cpu_baseline(d, budget_s=20.0, max_evals=6):
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} oracle energy+gradient evaluations of {WORKLOAD} at A_ov = a0 "
+            "sample": f"{n} oracle energy+gradient evaluations of {workload} at A_ov = a0 "
                       "(numpy FP64; basis matrix and reference set up before timing)"}
 
 
@@ -161,7 +171,7 @@ def run_reference(args):
         return
     import etdm_synth as synth
     from oracle.etdm_oracle import Oracle
-    d = synth.config_water32()
+    d = workload_system(args.workload)
     o = Oracle(d)
     o.reference()
     a = d["a0"]
@@ -177,10 +187,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+        "config": {"workload": WORKLOADS[args.workload], "parallelism": "replicas"},
         "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(),
                          "kind": "oracle",
-                         "sample": f"each step: 1 oracle energy+gradient evaluation of {WORKLOAD}"},
+                         "sample": "each step: 1 oracle energy+gradient evaluation of "
+                                   f"{WORKLOADS[args.workload]}"},
         "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -215,7 +226,7 @@ def run_ours(args):
     b.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    d = synth.config_water32()
+    d = workload_system(args.workload)
     solver = ETDM(d, precision=args.precision, device=local)
     dims = solver.dims
     a = torch.tensor(d["a0"], dtype=torch.float64, device=dev)
@@ -330,7 +341,7 @@ def run_ours(args):
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+bf16",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision,
+        "config": {"workload": WORKLOADS[args.workload], "precision": args.precision,
                    "parallelism": f"replicas{world}",
                    "l2": "flushed (512 MB write) before every timed step",
                    "evals_timed": int(all_evals), "E_last": Es[-1] if Es else None,
@@ -344,7 +355,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(d)
+        line["cpu_baseline"] = cpu_baseline(d, workload=WORKLOADS[args.workload])
     print(json.dumps(line))
 
 
@@ -355,6 +366,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="water32",
+                    help="water32 (the metric's configuration) or the 8-atom molecule")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--profile-once", action="store_true",
                     help="set up, run one energy+gradient evaluation, exit (for ncu)")

@@ -63,11 +63,12 @@ int set_err(etdm_handle *h, int code, const std::string &msg) {
   return code;
 }
 
-// deferred device-side status
+// deferred device-side status (copied with the stream's other results: one
+// synchronization)
 int check_flags(etdm_handle *h, cudaStream_t s) {
+  int *f = (int *)(h->h_pinned + 8);
+  CUDA_TRY(cudaMemcpyAsync(f, h->d_flags, FLAG_NFLAGS * sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-  int f[FLAG_NFLAGS];
-  CUDA_TRY(cudaMemcpy(f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost));
   if (f[FLAG_ERR] != 0) {
     int code = f[FLAG_ERR];
     int zero = 0;
@@ -523,7 +524,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   h->d_gt = dalloc<double>(h, nvar);
   h->d_p = dalloc<double>(h, nvar);
   h->d_dot = dalloc<double>(h, 4);
-  CUDA_TRY(cudaMallocHost(&h->h_pinned, 8 * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&h->h_pinned, 16 * sizeof(double)));  // [0, 8) values, [8, 16) status words
 
   // reference orbitals: Loewdin S^(-1/2), columns by ascending diag of C0^T h_core C0
   inverse_sqrt(h, s);
@@ -732,9 +733,17 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
       lbfgs(h, a_dev, h->d_g, h->d_p, s);
       CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
       h->launches += 1;
-      CUDA_TRY(cudaMemcpyAsync(hp + 2, h->d_dot + 2, 8, cudaMemcpyDeviceToHost, s));
+      // the first trial (alpha = 1) is queued before the direction is checked:
+      // one synchronization for both; discarded if p is not a descent direction
+      CUDA_TRY(launch_axpy(a_dev, 1.0, h->d_p, h->d_at, nvar, s));
+      evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
+      CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, nullptr, s));
+      h->launches += 2;
+      CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 3 * 8, cudaMemcpyDeviceToHost, s));
       check_flags(h, s);
       double d0 = hp[2];
+      const Pt first{1.0, hp[0], hp[1]};
+      const bool have_first = d0 < 0.0;
       if (!(d0 < 0.0)) {  // not a descent direction: erase memory, precondition only
         CUDA_TRY(cudaStreamSynchronize(s));
         double st[3] = {0.0, 0.0, 0.0};
@@ -752,7 +761,7 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
       Pt prev{0.0, E0, d0}, lo{}, hi{}, cur{};
       double alpha = 1.0;
       while (trials < MAX_TRIALS) {
-        cur = phi(alpha);
+        cur = (trials == 0 && have_first) ? first : phi(alpha);
         ++trials;
         if (wolfe_ok(cur.a, cur.E, cur.d, E0, d0)) { accepted = true; break; }
         if (cur.E > E0 + C1 * cur.a * d0 || (trials > 1 && cur.E >= prev.E)) {

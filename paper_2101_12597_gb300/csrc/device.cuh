@@ -7,43 +7,56 @@
 
 namespace etdm {
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier for kernels launched cooperatively (all blocks resident).
-// bar[0] counts arrivals, bar[1] is the generation.  The wait is bounded:
-// after kSpinLimit polls the block records ETDM_ERR_TIMEOUT in flags[FLAG_ERR]
-// and the barrier returns false; callers then return.
+// bar[0] counts arrivals, bar[1] is the generation.  The block's writes are
+// published by thread 0's release-ordered arrival (after the block barrier) and
+// seen by the other blocks through their acquire loads of the generation.  The
+// wait is bounded: after kSpinLimit polls the block records ETDM_ERR_TIMEOUT in
+// flags[FLAG_ERR] and the barrier returns false; callers then return.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *flags) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned *gen = bar + 1;
-    unsigned g = *gen;
-    __threadfence();
-    unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-    unsigned arrived = atomicAdd(bar, 1u);
+    const unsigned g = ld_acquire_gpu(bar + 1);
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned arrived = atom_add_acq_rel_gpu(bar, 1u);
     if (arrived == nb - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      st_relaxed_gpu(bar, 0u);          // reset for the next use, ordered before
+      st_release_gpu(bar + 1, g + 1);   // the release of the new generation
     } else {
       long it = 0;
-      while (*gen == g) {
+      while (ld_acquire_gpu(bar + 1) == g) {
         if (++it > kSpinLimit) {
           atomicExch(flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
     if (*(volatile int *)(flags + FLAG_ERR) == ETDM_ERR_TIMEOUT) ok = 0;
   }
   __syncthreads();
   return ok != 0;
 }
 
-// Sum of v over the block (all threads get the result).  blockDim.x <= 1024.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
