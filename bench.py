@@ -315,7 +315,8 @@ def run_ours(args):
                 "kernel": f"{dom}_fp64 (FP64 DFMA)",
                 "peak_source": "nominal FP64 rate of a GB300 (no measured FP64 figure)"}
     else:
-        pk = peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS)
+        # the stage is timed inside a long step: the sustained BF16 figure
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
         nu = solver.get_array("tile_nu_tc").astype(np.int64)  # functions per 128-point tile
         if dom == "vmat":  # 10 slice products per 16-point K step, N = list padded to 16
             npad = np.maximum(16, ((nu + 15) // 16) * 16)
@@ -329,7 +330,7 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                 "frac": achieved / pk, "traffic": captured_traffic(f"{dom}_tc_kernel"),
                 "kernel": f"{dom}_tc_kernel",
-                "peak_source": f"{src} dense bf16",
+                "peak_source": f"{src} dense bf16" + (" (sustained)" if "bf16_tflops_sustained" in peaks else ""),
                 "executed_tflops": executed / (per_launch_ms * 1e-3) / 1e12,
                 "executed_frac": executed / (per_launch_ms * 1e-3) / 1e12 / pk}
 

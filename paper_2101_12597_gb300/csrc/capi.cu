@@ -502,7 +502,14 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   int bps = 0;
   if (occupancy_dense(&bps) != 0 || bps < 1)
     throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative dense kernels"};
-  h->coop_blocks = h->num_sms;
+  // the dense chains' grid: as many blocks as the largest product has 8 x 16
+  // output tiles (every SM at water32); one block for small systems, where a
+  // grid barrier is then a block barrier
+  {
+    auto tiles = [](long m, long n) { return ((m + 7) / 8) * ((n + 15) / 16); };
+    const long mt = std::max({tiles(N, N), tiles(N, V), tiles(V, N), tiles(M, N), tiles(M, M)});
+    h->coop_blocks = mt <= 8 ? 1 : (int)std::min<long>(h->num_sms, mt);
+  }
   int bpl = 0;
   if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
     throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};

@@ -29,9 +29,11 @@ __device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned v) {
 // published by thread 0's release-ordered arrival (after the block barrier) and
 // seen by the other blocks through their acquire loads of the generation.  The
 // wait is bounded: after kSpinLimit polls the block records ETDM_ERR_TIMEOUT in
-// flags[FLAG_ERR] and the barrier returns false; callers then return.
+// flags[FLAG_ERR] and the barrier returns false; callers then return.  A grid of
+// one block needs only the block barrier.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *flags) {
   __syncthreads();
+  if (gridDim.x * gridDim.y * gridDim.z == 1) return true;  // one block: the block barrier is all
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
