@@ -438,7 +438,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_dO = dalloc<double>(h, (long)M * h->N);
     h->d_TO = dalloc<double>(h, (long)M * h->N);
     h->d_Vfix = dalloc<unsigned long long>(h, (long)M * M + 1);
-    h->d_Vfin = dalloc<double>(h, (long)M * M);
+    h->d_Vfin = dalloc<float2>(h, (long)M * M);
     const long half = (long)h->n[0] * h->n[1] * (h->n[2] / 2 + 1);
     h->d_twf = dalloc<float4>(h, h->n[0] + h->n[1] + h->n[2]);
     h->d_half = dalloc<float4>(h, half);
@@ -554,6 +554,13 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   double *d_tmpC = dalloc<double>(h, MM);
   CUDA_TRY(cudaMemcpyAsync(d_tmpC, h->d_C0, MM * 8, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(launch_permute_cols(d_tmpC, d_perm, h->d_C0, M, s));
+  if (h->precision == ETDM_PREC_MIXED) {  // the mixed path's dense chains run on float pairs
+    h->d_C0p = dalloc<float2>(h, MM);
+    h->d_Tp = dalloc<float2>(h, MM);
+    h->d_Af = dalloc<float2>(h, nvar);
+    CUDA_TRY(launch_to_pairs(h->d_C0, h->d_C0p, MM, s));
+    CUDA_TRY(launch_to_pairs(h->d_T, h->d_Tp, MM, s));
+  }
 
   // orbital energies of Eq. 33 at A = 0
   CUDA_TRY(cudaMemsetAsync(h->d_a, 0, nvar * 8, s));
@@ -868,9 +875,19 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_VEXT: src = h->d_vext; break;
       case ETDM_ARR_RHO: src = h->d_rho; break;
       case ETDM_ARR_VTOT: src = h->d_vtot; break;
-      case ETDM_ARR_H: src = h->d_H; break;
+      case ETDM_ARR_H: case ETDM_ARR_UOCC:
+        src = which == ETDM_ARR_H ? h->d_H : h->d_Uocc;
+        if (h->pairs_last) {  // the mixed path's dense chains left float pairs there
+          double *tmp = nullptr;
+          CUDA_TRY(cudaMalloc(&tmp, want));
+          cudaError_t e = launch_from_pairs(static_cast<const float2 *>(src), tmp, want / 8, 0);
+          if (e == cudaSuccess) e = cudaMemcpy(dst, tmp, want, cudaMemcpyDeviceToHost);
+          cudaFree(tmp);
+          CUDA_TRY(e);
+          return ETDM_OK;
+        }
+        break;
       case ETDM_ARR_D: src = h->d_D; break;
-      case ETDM_ARR_UOCC: src = h->d_Uocc; break;
       case ETDM_ARR_TILE_PTR: src = h->d_tile_ptr; break;
       case ETDM_ARR_TILE_KEYS: src = h->d_keys; break;
       case ETDM_ARR_EPS: src = h->d_eps; break;

@@ -1,4 +1,4 @@
-// Dense FP64 algebra of one ETDM evaluation: exp(A) for the occupied-virtual
+// Dense algebra of one ETDM evaluation: exp(A) for the occupied-virtual
 // parametrization (Eq. 36-37), O = C0 U, D = O F O^T (Eq. 12), and the
 // analytic gradient dE/dA_ov (Eq. 14) by reverse-mode differentiation of the
 // same steps; plus the L-BFGS two-loop update (Sec. 3.1) and the diagonal
@@ -16,13 +16,20 @@
 // same graph backwards.
 //
 // Each chain of small dependent products runs as ONE cooperative launch over
-// all SMs with a bounded grid barrier between products (FP64 is the scarce
-// resource on this GPU; spreading each product over every SM is what counts).
+// all SMs with a bounded grid barrier between products.  The chains are
+// written once over an element type R: double for the FP64 path, and float
+// pairs (pair.cuh) for the mixed path, whose products then run on the FP32
+// pipes (FP64 is the scarce resource on this GPU: about 1.7 FMA per clock per
+// SM).  Both element types are 8 bytes, so the workspaces are shared; in the
+// float-pair instantiation the matrices of the chain hold (hi, lo) pairs and
+// only A (in), g (out), dO and the energy terms stay FP64.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <math.h>
 
 #include "device.cuh"
 #include "internal.h"
+#include "pair.cuh"
 
 namespace etdm {
 
@@ -34,28 +41,89 @@ enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc0, kBc1, kBc2, kBs0, kBs1, kBs2, kTc, kTs, kQs
 // slots of the reverse workspace Wr
 enum { kQ4b = 0, kTcb, kTsb, kBc2b, kBs2b, kQ1bB, kQ2bB, kQ3b, kQ2b, kQ1bt, kQ1b, kWslots };
 
-__device__ __forceinline__ double opA(const Prod &P, int i, int k) {
-  return P.ta ? P.A[(long)k * P.lda + i] : P.A[(long)i * P.lda + k];
+// ---- the two element types --------------------------------------------------
+// ld/st: an element of a matrix held in R; ld_f64: an element of an FP64 matrix
+// converted to R; dbl: the value as FP64; fma(s, x, y) = s x + y with an FP64
+// scalar s; scale2: multiplication by a power of two.
+template <class R> struct Num;
+template <> struct Num<double> {
+  static constexpr bool kPair = false;
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double dbl(double x) { return x; }
+  static __device__ __forceinline__ double ld(const void *p, long e) { return static_cast<const double *>(p)[e]; }
+  static __device__ __forceinline__ double ld_f64(const void *p, long e) { return static_cast<const double *>(p)[e]; }
+  static __device__ __forceinline__ void st(void *p, long e, double v) { static_cast<double *>(p)[e] = v; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double fma(double s, double x, double y) { return s * x + y; }
+  static __device__ __forceinline__ double scale2(double x, double s) { return s * x; }
+};
+template <> struct Num<float2> {
+  static constexpr bool kPair = true;
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ float2 from(double x) { return pair::split(x); }
+  static __device__ __forceinline__ double dbl(float2 x) { return pair::to_double(x); }
+  static __device__ __forceinline__ float2 ld(const void *p, long e) { return static_cast<const float2 *>(p)[e]; }
+  static __device__ __forceinline__ float2 ld_f64(const void *p, long e) {
+    return pair::split(static_cast<const double *>(p)[e]);
+  }
+  static __device__ __forceinline__ void st(void *p, long e, float2 v) { static_cast<float2 *>(p)[e] = v; }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return pair::add(a, b); }
+  static __device__ __forceinline__ float2 fma(double s, float2 x, float2 y) {
+    return pair::add(pair::mul(pair::split(s), x), y);
+  }
+  static __device__ __forceinline__ float2 scale2(float2 x, double s) { return pair::scale2(x, (float)s); }
+};
+
+// Four independent multiply-add chains of one output (latency hiding).
+template <class R> struct Mac;
+template <> struct Mac<double> {
+  double c[4];
+  __device__ __forceinline__ Mac() : c{0.0, 0.0, 0.0, 0.0} {}
+  __device__ __forceinline__ void step(int u, double a, double b) { c[u] = fma(a, b, c[u]); }
+  __device__ __forceinline__ double total() const { return (c[0] + c[1]) + (c[2] + c[3]); }
+};
+template <> struct Mac<float2> {
+  float h[4], l[4];
+  __device__ __forceinline__ Mac() : h{0.f, 0.f, 0.f, 0.f}, l{0.f, 0.f, 0.f, 0.f} {}
+  __device__ __forceinline__ void step(int u, float2 a, float2 b) { pair::mac(h[u], l[u], a, b); }
+  __device__ __forceinline__ float2 total() const {
+    return pair::add(pair::add(make_float2(h[0], l[0]), make_float2(h[1], l[1])),
+                     pair::add(make_float2(h[2], l[2]), make_float2(h[3], l[3])));
+  }
+};
+
+template <class R>
+__device__ __forceinline__ R opA(const Prod &P, int i, int k) {
+  const long e = P.ta ? (long)k * P.lda + i : (long)i * P.lda + k;
+  return (P.f64 & 1) ? Num<R>::ld_f64(P.A, e) : Num<R>::ld(P.A, e);
 }
-__device__ __forceinline__ double opB(const Prod &P, int k, int j) {
-  return P.tb ? P.B[(long)j * P.ldb + k] : P.B[(long)k * P.ldb + j];
+template <class R>
+__device__ __forceinline__ R opB(const Prod &P, int k, int j) {
+  const long e = P.tb ? (long)j * P.ldb + k : (long)k * P.ldb + j;
+  return (P.f64 & 2) ? Num<R>::ld_f64(P.B, e) : Num<R>::ld(P.B, e);
 }
 
 // One output tile (BM x BN) of a phase.  The block's two groups of 128 threads
 // (one output each) take alternate K chunks and add their partial sums at the
-// end, which doubles the FP64 work in flight per SM.  Each group double-buffers
-// its chunks in shared memory: the next chunk's global loads are in flight in
-// registers while the current one is multiplied.
+// end, which doubles the work in flight per SM.  Each group double-buffers its
+// chunks in shared memory: the next chunk's global loads are in flight in
+// registers while the current one is multiplied.  Not inlined: every phase of
+// a chain runs the same copy of this code, which stays in the instruction
+// cache (inlined at each of the chain's call sites, the first chunk of every
+// phase waited on instruction fetch for several microseconds).
 constexpr int kLa = BM * BK / NG, kLb = BK * BN / NG;  // elements per thread per chunk
-__device__ void phase_tile(const Phase &ph, int tile, double (*As)[2][BM][BK + 1],
-                           double (*Bs)[2][BK][BN + 1], double *part) {
+template <class R>
+__device__ __noinline__ void phase_tile(const Phase &ph, int tile, R (*As)[2][BM][BK + 1],
+                           R (*Bs)[2][BK][BN + 1], R *part) {
+  using X = Num<R>;
   const int tilesN = (ph.n + BN - 1) / BN;
   const int r0 = (tile / tilesN) * BM, c0 = (tile % tilesN) * BN;
   const int tid = threadIdx.x % NG, grp = threadIdx.x / NG;
   const int ty = tid / BN, tx = tid % BN;
   const int i = r0 + ty, j = c0 + tx;
   const int nch = (ph.k + BK - 1) / BK, nit = (nch + 1) / 2;
-  double acc = 0.0;
+  R acc = X::zero();
   for (int q = 0; q < ph.np; ++q) {
     const Prod P = ph.p[q];
     if (P.alpha == 0.0) continue;
@@ -71,18 +139,18 @@ __device__ void phase_tile(const Phase &ph, int tile, double (*As)[2][BM][BK + 1
       const int e = tid + u * NG;
       if (P.tb) { bj[u] = e / BK; bk[u] = e % BK; } else { bk[u] = e / BN; bj[u] = e % BN; }
     }
-    double ra[kLa], rb[kLb];
+    R ra[kLa], rb[kLb];
     auto load = [&](int c) {  // chunk c (zeros beyond K)
       const int k0 = c * BK;
 #pragma unroll
       for (int u = 0; u < kLa; ++u) {
         const int gi = r0 + ai[u], gk = k0 + ak[u];
-        ra[u] = (gi < ph.m && gk < ph.k) ? opA(P, gi, gk) : 0.0;
+        ra[u] = (gi < ph.m && gk < ph.k) ? opA<R>(P, gi, gk) : X::zero();
       }
 #pragma unroll
       for (int u = 0; u < kLb; ++u) {
         const int gk = k0 + bk[u], gj = c0 + bj[u];
-        rb[u] = (gk < ph.k && gj < ph.n) ? opB(P, gk, gj) : 0.0;
+        rb[u] = (gk < ph.k && gj < ph.n) ? opB<R>(P, gk, gj) : X::zero();
       }
     };
     auto store = [&](int buf) {
@@ -94,7 +162,7 @@ __device__ void phase_tile(const Phase &ph, int tile, double (*As)[2][BM][BK + 1
     load(grp);
     store(0);
     __syncthreads();
-    double ac[4] = {0.0, 0.0, 0.0, 0.0};  // four independent FMA chains
+    Mac<R> mac;
     for (int it = 0; it < nit; ++it) {  // this group's chunks grp, grp + 2, ...
       const int buf = it & 1;
       const bool more = it + 1 < nit;
@@ -102,22 +170,23 @@ __device__ void phase_tile(const Phase &ph, int tile, double (*As)[2][BM][BK + 1
 #pragma unroll
       for (int kk = 0; kk < BK; kk += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          ac[u] = fma(As[grp][buf][ty][kk + u], Bs[grp][buf][kk + u][tx], ac[u]);
+        for (int u = 0; u < 4; ++u) mac.step(u, As[grp][buf][ty][kk + u], Bs[grp][buf][kk + u][tx]);
       }
       if (more) store(buf ^ 1);
       __syncthreads();
     }
-    acc += P.alpha * ((ac[0] + ac[1]) + (ac[2] + ac[3]));
+    acc = X::fma(P.alpha, mac.total(), acc);
   }
   if (grp == 1) part[tid] = acc;
   __syncthreads();
   if (grp == 0 && i < ph.m && j < ph.n) {
-    double v = acc + part[tid];
-    if (ph.C1) v += ph.beta1 * ph.C1[(long)i * ph.ldc1 + j];
-    if (ph.C2) v += ph.beta2 * ph.C2[(long)i * ph.ldc2 + j];
-    if (i == j) v += ph.diag;
-    ph.out[(long)i * ph.ldo + j] = v;
+    R v = X::add(acc, part[tid]);
+    if (ph.C1) v = X::fma(ph.beta1, X::ld(ph.C1, (long)i * ph.ldc1 + j), v);
+    if (ph.C2) v = X::fma(ph.beta2, X::ld(ph.C2, (long)i * ph.ldc2 + j), v);
+    if (i == j) v = X::add(v, X::from(ph.diag));
+    const long o = (long)i * ph.ldo + j;
+    if (ph.out64) static_cast<double *>(ph.out)[o] = X::dbl(v);
+    else X::st(ph.out, o, v);
   }
   __syncthreads();
 }
@@ -128,32 +197,33 @@ __device__ __forceinline__ int phase_tiles(const Phase &ph) {
 }
 
 // Run independent phases over one shared tile index space (no barrier).
+template <class R>
 __device__ void run_phases(const Phase *ph, int count) {
-  __shared__ double As[2][2][BM][BK + 1];
-  __shared__ double Bs[2][2][BK][BN + 1];
-  __shared__ double part[NG];
+  __shared__ R As[2][2][BM][BK + 1];
+  __shared__ R Bs[2][2][BK][BN + 1];
+  __shared__ R part[NG];
   int total = 0;
   for (int c = 0; c < count; ++c) total += phase_tiles(ph[c]);
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int c = 0, base = 0;
     while (t - base >= phase_tiles(ph[c])) { base += phase_tiles(ph[c]); ++c; }
-    phase_tile(ph[c], t - base, As, Bs, part);
+    phase_tile<R>(ph[c], t - base, As, Bs, part);
   }
 }
 
-__device__ __forceinline__ Prod mk(const double *A, int lda, int ta, const double *B, int ldb,
+__device__ __forceinline__ Prod mk(const void *A, int lda, int ta, const void *B, int ldb,
                                    int tb, double alpha) {
   Prod p;
-  p.A = A; p.B = B; p.lda = lda; p.ldb = ldb; p.ta = ta; p.tb = tb; p.alpha = alpha;
+  p.A = A; p.B = B; p.lda = lda; p.ldb = ldb; p.ta = ta; p.tb = tb; p.alpha = alpha; p.f64 = 0;
   return p;
 }
 
-__device__ __forceinline__ Phase mkphase(int m, int n, int k, double *out, int ldo) {
+__device__ __forceinline__ Phase mkphase(int m, int n, int k, void *out, int ldo) {
   Phase ph;
   ph.m = m; ph.n = n; ph.k = k; ph.np = 0;
   ph.C1 = nullptr; ph.ldc1 = 0; ph.beta1 = 0.0;
   ph.C2 = nullptr; ph.ldc2 = 0; ph.beta2 = 0.0;
-  ph.diag = 0.0; ph.out = out; ph.ldo = ldo;
+  ph.diag = 0.0; ph.out = out; ph.ldo = ldo; ph.out64 = 0;
   return ph;
 }
 
@@ -164,36 +234,46 @@ __device__ __forceinline__ Phase mkphase(int m, int n, int k, double *out, int l
 
 // Forward: P, j, Q^k, Taylor series, doublings, U_occ = [cos sqrt P; -A^T s(P)],
 // O = C0 U_occ, then D = 2 O O^T and H <- T (FP64 grid passes) or T O (mixed).
+template <class R>
 __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
+  using X = Num<R>;
   const int M = a.M, N = a.N, V = a.V;
   const long NN = (long)N * N;
   const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long gstride = (long)gridDim.x * blockDim.x;
   __shared__ int sh_j;
   __shared__ double sh_sc;
+  // A_ov as R: the float-pair engine converts the FP64 input once, in the first phase
+  const void *const Ar = X::kPair ? (const void *)a.Af : (const void *)a.A;
 
-  {  // P = A_ov A_ov^T
+  {  // P = A_ov A_ov^T (reads the FP64 A)
+    if (X::kPair)
+      for (long e = gtid; e < (long)N * V; e += gstride) X::st(a.Af, e, X::ld_f64(a.A, e));
     Phase ph = mkphase(N, N, V, a.P, N);
-    ph.np = 1; ph.p[0] = mk(a.A, V, 0, a.A, V, 1, 1.0);
-    run_phases(&ph, 1);
+    ph.np = 1; ph.p[0] = mk(a.A, V, 0, a.A, V, 1, 1.0); ph.p[0].f64 = 3;
+    run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
   {
     double s = 0.0;
-    for (long e = gtid; e < NN; e += gstride) s += a.P[e] * a.P[e];
+    for (long e = gtid; e < NN; e += gstride) {
+      const double p = X::dbl(X::ld(a.P, e));
+      s += p * p;
+    }
     s = block_sum(s);
     if (threadIdx.x == 0) a.red[blockIdx.x] = s;
   }
   BARRIER_OR_RETURN();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += a.red[b];
+  {
+    const double t = block_sum_of(a.red, gridDim.x);
     double nrm = sqrt(t);
     int j = 0;
     while (nrm > 1.0 && j <= kJmax) { nrm *= 0.25; ++j; }
     if (!(t == t) || isinf(t)) j = kJmax + 1;
-    sh_j = j;
-    sh_sc = ldexp(1.0, -2 * j);
+    if (threadIdx.x == 0) {
+      sh_j = j;
+      sh_sc = ldexp(1.0, -2 * j);
+    }
   }
   __syncthreads();
   const int J = sh_j;
@@ -205,12 +285,12 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
   if (gtid == 0) { a.flags[FLAG_J] = J; a.scal[0] = sc; }
   double *const Qs = a.Qk;
   auto slot = [&](int k) { return Qs + (long)k * NN; };
-  for (long e = gtid; e < NN; e += gstride) slot(kQ1)[e] = sc * a.P[e];
+  for (long e = gtid; e < NN; e += gstride) X::st(slot(kQ1), e, X::scale2(X::ld(a.P, e), sc));
   BARRIER_OR_RETURN();
   {  // Q^2
     Phase ph = mkphase(N, N, N, slot(kQ2), N);
     ph.np = 1; ph.p[0] = mk(slot(kQ1), N, 0, slot(kQ1), N, 0, 1.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
   {  // Q^3 = Q Q^2, Q^4 = Q^2 Q^2
@@ -219,20 +299,21 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     ph[0].np = 1; ph[0].p[0] = mk(slot(kQ1), N, 0, slot(kQ2), N, 0, 1.0);
     ph[1] = mkphase(N, N, N, slot(kQ4), N);
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
   for (long e = gtid; e < NN; e += gstride) {  // blocks B_i = sum_r c_{4i+r} Q^r
     const int i = (int)(e / N), c = (int)(e % N);
-    const double q[4] = {i == c ? 1.0 : 0.0, slot(kQ1)[e], slot(kQ2)[e], slot(kQ3)[e]};
+    const R q[4] = {X::from(i == c ? 1.0 : 0.0), X::ld(slot(kQ1), e), X::ld(slot(kQ2), e),
+                    X::ld(slot(kQ3), e)};
     for (int b = 0; b < 3; ++b) {
-      double bc = 0.0, bs = 0.0;
+      R bc = X::zero(), bs = X::zero();
       for (int r = 0; r < 4; ++r) {
         const int k = 4 * b + r;
-        if (k <= kTaylor) { bc += a.ck[k] * q[r]; bs += a.sk[k] * q[r]; }
+        if (k <= kTaylor) { bc = X::fma(a.ck[k], q[r], bc); bs = X::fma(a.sk[k], q[r], bs); }
       }
-      slot(kBc0 + b)[e] = bc;
-      slot(kBs0 + b)[e] = bs;
+      X::st(slot(kBc0 + b), e, bc);
+      X::st(slot(kBs0 + b), e, bs);
     }
   }
   BARRIER_OR_RETURN();
@@ -244,7 +325,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     ph[1] = mkphase(N, N, N, slot(kTs), N);
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, slot(kBs2), N, 0, 1.0);
     ph[1].C1 = slot(kBs1); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // k = cos sqrt(Q) - 1 = B_0 + Q^4 T_c, s = sin sqrt(Q) / sqrt(Q) = B_0 + Q^4 T_s
@@ -255,7 +336,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     ph[1] = mkphase(N, N, N, a.St, N);
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, slot(kTs), N, 0, 1.0);
     ph[1].C1 = slot(kBs0); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
   for (int t = 0; t < J; ++t) {  // doubling: k' = 4k + 2k^2, s' = s + s k
@@ -267,63 +348,67 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     ph[1] = mkphase(N, N, N, a.St + (long)(t + 1) * NN, N);
     ph[1].np = 1; ph[1].p[0] = mk(Sc, N, 0, Kc, N, 0, 1.0);
     ph[1].C1 = Sc; ph[1].ldc1 = N; ph[1].beta1 = 1.0;
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
     BARRIER_OR_RETURN();
   }
   {
     const double *KJ = a.Kt + (long)J * NN, *SJ = a.St + (long)J * NN;
     for (long e = gtid; e < NN; e += gstride) {
       int i = (int)(e / N), c = (int)(e % N);
-      a.Uocc[e] = KJ[e] + (i == c ? 1.0 : 0.0);
+      X::st(a.Uocc, e, X::add(X::ld(KJ, e), X::from(i == c ? 1.0 : 0.0)));
     }
     Phase ph = mkphase(V, N, N, a.Uocc + NN, N);  // -A^T s(P)
-    ph.np = 1; ph.p[0] = mk(a.A, V, 1, SJ, N, 0, -1.0);
-    run_phases(&ph, 1);
+    ph.np = 1; ph.p[0] = mk(Ar, V, 1, SJ, N, 0, -1.0);
+    run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
   {
     Phase ph = mkphase(M, N, M, a.O, N);  // O = C0 U_occ
     ph.np = 1; ph.p[0] = mk(a.C0, M, 0, a.Uocc, N, 0, 1.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
   if (a.Vacc) {  // mixed path: the density comes from O on the grid; T O for the kinetic energy and dE/dO
     Phase ph = mkphase(M, N, M, a.TO, N);
     ph.np = 1; ph.p[0] = mk(a.T, M, 0, a.O, N, 0, 1.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
   } else {
     Phase ph = mkphase(M, M, N, a.D, M);  // D = 2 O O^T (Eq. 12, f = 2)
     ph.np = 1; ph.p[0] = mk(a.O, N, 0, a.O, N, 1, 2.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
     const long MM = (long)M * M;
-    for (long e = gtid; e < MM; e += gstride) a.H[e] = a.T[e];
+    for (long e = gtid; e < MM; e += gstride) X::st(a.H, e, X::ld(a.T, e));
   }
 }
 
 // Reverse: E = Tr(D T) + grid terms; dE/dO = 4 H O; dE/dU = C0^T (4 H O);
 // (mixed path: Tr(D T) = 2 sum O o (T O), 4 H O = 4 T O + 4 V O);
 // back through U_occ, the doublings, the Taylor powers and P = A A^T.
+template <class R>
 __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want_grad) {
+  using X = Num<R>;
   const int M = a.M, N = a.N, V = a.V;
   const long NN = (long)N * N, MM = (long)M * M;
   const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long gstride = (long)gridDim.x * blockDim.x;
   const bool mixed = a.Vacc != nullptr;
   const long MN = (long)M * N;
+  const void *const Ar = X::kPair ? (const void *)a.Af : (const void *)a.A;  // set by the forward
   {
     double s = 0.0;
     if (mixed) {  // Tr(D T) = 2 sum O o (T O); H <- V (symmetric, from the upper triangle)
-      for (long e = gtid; e < MN; e += gstride) s += 2.0 * a.O[e] * a.TO[e];
+      for (long e = gtid; e < MN; e += gstride)
+        s += 2.0 * X::dbl(X::ld(a.O, e)) * X::dbl(X::ld(a.TO, e));
       for (long e = gtid; e < MM; e += gstride) {
         int i = (int)(e / M), c = (int)(e % M);
-        a.H[e] = i <= c ? a.Vacc[e] : a.Vacc[(long)c * M + i];
+        X::st(a.H, e, X::ld(a.Vacc, i <= c ? e : (long)c * M + i));
       }
     } else {
-      for (long e = gtid; e < MM; e += gstride) s += a.D[e] * a.T[e];
+      for (long e = gtid; e < MM; e += gstride) s += X::dbl(X::ld(a.D, e)) * X::dbl(X::ld(a.T, e));
       if (want_grad) {  // the grid pass accumulated the upper triangle of H
         for (long e = gtid; e < MM; e += gstride) {
           int i = (int)(e / M), c = (int)(e % M);
-          if (i > c) a.H[e] = a.H[(long)c * M + i];
+          if (i > c) X::st(a.H, e, X::ld(a.H, (long)c * M + i));
         }
       }
     }
@@ -333,18 +418,18 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   BARRIER_OR_RETURN();
   if (mixed) {
     // dE_pot/dO = 4 V O into Ubar (scratch until Ubar is formed); the kinetic
-    // energy is exact (FP64 O), only the grid energy saw Oq
+    // energy is exact (O as computed), only the grid energy saw Oq
     Phase ph = mkphase(M, N, M, a.Ubar, N);
     ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
     BARRIER_OR_RETURN();
     // Gbar = dE/dO = 4 T O + 4 V O; first-order correction of the density's O
     // quantization, sum (4 V O) o (O - Oq)
     double c = 0.0;
     for (long e = gtid; e < MN; e += gstride) {
-      const double u = a.Ubar[e];
-      a.Gbar[e] = 4.0 * a.TO[e] + u;
-      c += u * a.dO[e];
+      const R u = X::ld(a.Ubar, e);
+      X::st(a.Gbar, e, X::fma(4.0, X::ld(a.TO, e), u));
+      c += X::dbl(u) * a.dO[e];
     }
     c = block_sum(c);
     if (threadIdx.x == 0) a.red[gridDim.x + blockIdx.x] = c;
@@ -352,7 +437,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   } else if (want_grad) {
     Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
     ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
     BARRIER_OR_RETURN();
   }
   if (blockIdx.x == 0) {  // energy terms: tree sums over the block partials, all threads of block 0
@@ -377,7 +462,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   {
     Phase ph = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
     ph.np = 1; ph.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
   const int J = a.flags[FLAG_J];
@@ -386,10 +471,10 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   {
     Phase ph[2];
     ph[0] = mkphase(N, N, V, a.Sbar[0], N);  // Sbar_J = -A Ubar_v
-    ph[0].np = 1; ph[0].p[0] = mk(a.A, V, 0, Ubv, N, 0, -1.0);
+    ph[0].np = 1; ph[0].p[0] = mk(Ar, V, 0, Ubv, N, 0, -1.0);
     ph[1] = mkphase(N, V, N, a.Abar, V);     // Abar = -S_J Ubar_v^T
     ph[1].np = 1; ph[1].p[0] = mk(a.St + (long)J * NN, N, 0, Ubv, N, 1, -1.0);
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
   const double *kb = a.Ubar;  // Kbar_J = cotangent of cos sqrt(P) = Ubar_o
@@ -408,7 +493,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1].p[1] = mk(Kc, N, 0, kb, N, 0, 2.0);
     ph[1].p[2] = mk(Sc, N, 0, sb, N, 0, 1.0);
     ph[1].C1 = kb; ph[1].ldc1 = N; ph[1].beta1 = 4.0;
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
     BARRIER_OR_RETURN();
     kb = kbo; sb = sbo; pp = 1 - pp;
   }
@@ -427,7 +512,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, kb, N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kTsb), N);  // T_s bar = Q^4 sbar
     ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, sb, N, 0, 1.0);
-    run_phases(ph, 3);
+    run_phases<R>(ph, 3);
   }
   BARRIER_OR_RETURN();
   {  // back through T = B_1 + Q^4 B_2
@@ -441,22 +526,22 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, wr(kTcb), N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kBs2b), N);  // B_s2 bar = Q^4 T_s bar
     ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, wr(kTsb), N, 0, 1.0);
-    run_phases(ph, 3);
+    run_phases<R>(ph, 3);
   }
   BARRIER_OR_RETURN();
   // the blocks' cotangents to the powers: Q^r bar = sum_i c_{4i+r} B_ci bar + s_{4i+r} B_si bar
   for (long e = gtid; e < NN; e += gstride) {
-    const double bcb[3] = {kb[e], wr(kTcb)[e], wr(kBc2b)[e]};
-    const double bsb[3] = {sb[e], wr(kTsb)[e], wr(kBs2b)[e]};
-    double qb[4] = {0.0, 0.0, 0.0, 0.0};
+    const R bcb[3] = {X::ld(kb, e), X::ld(wr(kTcb), e), X::ld(wr(kBc2b), e)};
+    const R bsb[3] = {X::ld(sb, e), X::ld(wr(kTsb), e), X::ld(wr(kBs2b), e)};
+    R qb[4] = {X::zero(), X::zero(), X::zero(), X::zero()};
     for (int b = 0; b < 3; ++b)
       for (int r = 1; r < 4; ++r) {
         const int k = 4 * b + r;
-        if (k <= kTaylor) qb[r] += a.ck[k] * bcb[b] + a.sk[k] * bsb[b];
+        if (k <= kTaylor) qb[r] = X::fma(a.ck[k], bcb[b], X::fma(a.sk[k], bsb[b], qb[r]));
       }
-    wr(kQ1bB)[e] = qb[1];
-    wr(kQ2bB)[e] = qb[2];
-    wr(kQ3b)[e] = qb[3];
+    X::st(wr(kQ1bB), e, qb[1]);
+    X::st(wr(kQ2bB), e, qb[2]);
+    X::st(wr(kQ3b), e, qb[3]);
   }
   BARRIER_OR_RETURN();
   {  // back through Q^4 = Q^2 Q^2 and Q^3 = Q Q^2
@@ -470,7 +555,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1] = mkphase(N, N, N, wr(kQ1bt), N);  // Qbar_t = Q1bar_B + Q3bar Q^2
     ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 1.0);
     ph[1].C1 = wr(kQ1bB); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
-    run_phases(ph, 2);
+    run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // back through Q^2 = Q Q: Qbar = Qbar_t + Q2bar Q + Q Q2bar
@@ -479,27 +564,28 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
     ph.p[1] = mk(slot(kQ1), N, 0, wr(kQ2b), N, 0, 1.0);
     ph.C1 = wr(kQ1bt); ph.ldc1 = N; ph.beta1 = 1.0;
-    run_phases(&ph, 1);
+    run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
   {  // Q = sc P: Pbar + Pbar^T = sc (Qbar + Qbar^T)
     const double *Qb = wr(kQ1b);
     for (long e = gtid; e < NN; e += gstride) {
       int i = (int)(e / N), c = (int)(e % N);
-      a.Psym[e] = sc * (Qb[e] + Qb[(long)c * N + i]);
+      X::st(a.Psym, e, X::scale2(X::add(X::ld(Qb, e), X::ld(Qb, (long)c * N + i)), sc));
     }
   }
   BARRIER_OR_RETURN();
   {
-    Phase ph = mkphase(N, V, N, a.g, V);  // g = Abar + (Pbar + Pbar^T) A
-    ph.np = 1; ph.p[0] = mk(a.Psym, N, 0, a.A, V, 0, 1.0);
+    Phase ph = mkphase(N, V, N, a.g, V);  // g = Abar + (Pbar + Pbar^T) A, written as FP64
+    ph.np = 1; ph.p[0] = mk(a.Psym, N, 0, Ar, V, 0, 1.0);
     ph.C1 = a.Abar; ph.ldc1 = V; ph.beta1 = 1.0;
-    run_phases(&ph, 1);
+    ph.out64 = 1;
+    run_phases<R>(&ph, 1);
   }
 }
 
 // Plain (non-cooperative) product for set-up work.
-__global__ void __launch_bounds__(NT) gemm_kernel(Phase ph) { run_phases(&ph, 1); }
+__global__ void __launch_bounds__(NT) gemm_kernel(Phase ph) { run_phases<double>(&ph, 1); }
 
 // ---- L-BFGS two-loop (Sec. 3.1) with H0 = P^(k) (Eq. 33-34) ---------------
 __device__ __forceinline__ double precond_elem(const double *eps, int N, int V, long e,
@@ -509,22 +595,17 @@ __device__ __forceinline__ double precond_elem(const double *eps, int N, int V, 
   return 1.0 / (2.0 * (1.0 - gamma) * fabs(d) + gamma * beta);
 }
 
-// Dot product of the whole grid: every block gets the same value.
-__device__ double grid_dot_finish(LbfgsArgs &a, double part, bool *ok) {
+// Dot product of the whole grid: every block gets the same value.  The block
+// partials alternate between two halves of red[], so one barrier suffices: a
+// block can only write a half again after the next call's barrier, which every
+// block reaches after reading this call's sums.
+__device__ double grid_dot_finish(LbfgsArgs &a, double part, int *parity, bool *ok) {
+  double *red = a.red + (*parity) * gridDim.x;
+  *parity ^= 1;
   part = block_sum(part);
-  if (threadIdx.x == 0) a.red[blockIdx.x] = part;
+  if (threadIdx.x == 0) red[blockIdx.x] = part;
   if (!grid_barrier(a.bar, a.flags)) { *ok = false; return 0.0; }
-  __shared__ double tot;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += a.red[b];
-    tot = t;
-  }
-  __syncthreads();
-  double r = tot;
-  // a second barrier keeps red[] from being overwritten before all blocks read it
-  if (!grid_barrier(a.bar, a.flags)) { *ok = false; return 0.0; }
-  return r;
+  return block_sum_of(red, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
@@ -537,6 +618,7 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
   const bool have_prev = st[2] != 0.0;
   double beta = st[3];
   bool ok = true;
+  int par = 0;
   if (have_prev) {  // candidate pair into slot `head`
     double *sn = a.s + (long)head * n, *yn = a.y + (long)head * n;
     double p1 = 0.0, p2 = 0.0;
@@ -545,8 +627,8 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
       sn[e] = sv; yn[e] = yv;
       p1 += sv * yv; p2 += yv * yv;
     }
-    double sy = grid_dot_finish(a, p1, &ok); if (!ok) return;
-    double yy = grid_dot_finish(a, p2, &ok); if (!ok) return;
+    double sy = grid_dot_finish(a, p1, &par, &ok); if (!ok) return;
+    double yy = grid_dot_finish(a, p2, &par, &ok); if (!ok) return;
     if (sy > 1e-30) {
       beta = yy / sy;
       st[4 + head] = 1.0 / sy;  // rho of the slot (identical in every block)
@@ -566,7 +648,7 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
     const double *sv = a.s + (long)slot * n, *yv = a.y + (long)slot * n;
     double part = 0.0;
     for (long e = gtid; e < n; e += gstride) part += sv[e] * a.q[e];
-    double sq = grid_dot_finish(a, part, &ok); if (!ok) return;
+    double sq = grid_dot_finish(a, part, &par, &ok); if (!ok) return;
     double al = st[4 + slot] * sq;
     alph[c] = al;
     for (long e = gtid; e < n; e += gstride) a.q[e] -= al * yv[e];
@@ -580,7 +662,7 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
     const double *sv = a.s + (long)slot * n, *yv = a.y + (long)slot * n;
     double part = 0.0;
     for (long e = gtid; e < n; e += gstride) part += yv[e] * a.q[e];
-    double yr = grid_dot_finish(a, part, &ok); if (!ok) return;
+    double yr = grid_dot_finish(a, part, &par, &ok); if (!ok) return;
     double be = st[4 + slot] * yr;
     double coef = alph[c] - be;
     for (long e = gtid; e < n; e += gstride) a.q[e] += coef * sv[e];
@@ -694,13 +776,22 @@ __global__ void scale_copy_kernel(const double *src, double *dst, double c, long
 
 // ---- host wrappers ----------------------------------------------------------
 
+// The mixed path's evaluations run the chains on float pairs; the set-up
+// evaluation and the FP64 path on FP64.
+static bool dense_pairs(const etdm_handle *h) {
+  return h->precision == ETDM_PREC_MIXED && !h->in_setup;
+}
+
 static DenseArgs dense_args(etdm_handle *h, const double *a) {
   DenseArgs d{};
+  const bool pairs = dense_pairs(h);
   d.M = h->M; d.N = h->N; d.V = h->V;
   d.A = a;
+  d.Af = pairs ? reinterpret_cast<double *>(h->d_Af) : nullptr;
   d.P = h->d_P; d.Qk = h->d_Qk; d.Kt = h->d_Kt; d.St = h->d_St;
   d.Uocc = h->d_Uocc; d.O = h->d_O; d.D = h->d_D; d.H = h->d_H; d.TO = h->d_TO;
-  d.C0 = h->d_C0; d.T = h->d_T;
+  d.C0 = pairs ? (const void *)h->d_C0p : (const void *)h->d_C0;
+  d.T = pairs ? (const void *)h->d_Tp : (const void *)h->d_T;
   d.Gbar = h->d_Gbar; d.Ubar = h->d_Ubar;
   d.Kbar[0] = h->d_bar2[0]; d.Kbar[1] = h->d_bar2[1];
   d.Sbar[0] = h->d_bar2[2]; d.Sbar[1] = h->d_bar2[3];
@@ -708,7 +799,7 @@ static DenseArgs dense_args(etdm_handle *h, const double *a) {
   d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym; d.Wr = h->d_Wr;
   d.eterms = h->d_eterms;
   d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
-  if (h->precision == ETDM_PREC_MIXED && !h->in_setup) { d.Vacc = h->d_Vfin; d.dO = h->d_dO; }
+  if (pairs) { d.Vacc = h->d_Vfin; d.dO = h->d_dO; }
   d.red = h->d_red; d.flags = h->d_flags; d.bar = h->d_bar; d.scal = h->d_scal;
   // c_k = (-1)^k/(2k)!, s_k = (-1)^k/(2k+1)!
   double f = 1.0;
@@ -727,8 +818,10 @@ static DenseArgs dense_args(etdm_handle *h, const double *a) {
 cudaError_t launch_dense_forward(etdm_handle *h, const double *a, cudaStream_t s) {
   DenseArgs d = dense_args(h, a);
   void *args[] = {&d};
-  return cudaLaunchCooperativeKernel((void *)dense_forward_kernel, dim3(h->coop_blocks),
-                                     dim3(NT), args, 0, s);
+  const void *fn = dense_pairs(h) ? (const void *)dense_forward_kernel<float2>
+                                  : (const void *)dense_forward_kernel<double>;
+  h->pairs_last = dense_pairs(h);
+  return cudaLaunchCooperativeKernel(fn, dim3(h->coop_blocks), dim3(NT), args, 0, s);
 }
 
 cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, double *E,
@@ -737,8 +830,27 @@ cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, dou
   d.g = g; d.E = E;
   int want = g != nullptr;
   void *args[] = {&d, &want};
-  return cudaLaunchCooperativeKernel((void *)dense_reverse_kernel, dim3(h->coop_blocks),
-                                     dim3(NT), args, 0, s);
+  const void *fn = dense_pairs(h) ? (const void *)dense_reverse_kernel<float2>
+                                  : (const void *)dense_reverse_kernel<double>;
+  return cudaLaunchCooperativeKernel(fn, dim3(h->coop_blocks), dim3(NT), args, 0, s);
+}
+
+__global__ void to_pairs_kernel(const double *src, float2 *dst, long n) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    dst[e] = pair::split(src[e]);
+}
+__global__ void from_pairs_kernel(const float2 *src, double *dst, long n) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    dst[e] = pair::to_double(src[e]);
+}
+
+cudaError_t launch_to_pairs(const double *src, float2 *dst, long n, cudaStream_t s) {
+  to_pairs_kernel<<<(int)std::min<long>((n + 255) / 256, 1024), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_from_pairs(const float2 *src, double *dst, long n, cudaStream_t s) {
+  from_pairs_kernel<<<(int)std::min<long>((n + 255) / 256, 1024), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(const Phase &ph, cudaStream_t s) {
@@ -820,11 +932,15 @@ cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n,
 }
 
 int occupancy_dense(int *bps) {
-  int a = 0, b = 0;
-  cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, dense_forward_kernel, NT, 0);
-  cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dense_reverse_kernel, NT, 0);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) return -1;
-  *bps = a < b ? a : b;
+  const void *fns[4] = {(const void *)dense_forward_kernel<double>, (const void *)dense_reverse_kernel<double>,
+                        (const void *)dense_forward_kernel<float2>, (const void *)dense_reverse_kernel<float2>};
+  int best = 1 << 30;
+  for (const void *f : fns) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, NT, 0) != cudaSuccess) return -1;
+    best = std::min(best, b);
+  }
+  *bps = best;
   return 0;
 }
 

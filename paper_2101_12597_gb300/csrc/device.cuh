@@ -78,4 +78,11 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;
 }
 
+// Sum of red[0, n) by the whole block; every thread gets the total.
+__device__ __forceinline__ double block_sum_of(const double *red, int n) {
+  double t = 0.0;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) t += red[b];
+  return block_sum(t);
+}
+
 }  // namespace etdm

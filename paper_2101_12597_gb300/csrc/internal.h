@@ -43,49 +43,58 @@ struct Tables {
   const double *rc2;   // r_c * r_c
 };
 
-// One dense product term for the cooperative dense kernels.
+// One dense product term for the cooperative dense kernels.  The matrices hold
+// the kernel's element type (FP64, or float pairs in the mixed path's chains);
+// f64 marks operands held as FP64 whatever the element type (bit 0: A, bit 1: B).
 struct Prod {
-  const double *A;
-  const double *B;
+  const void *A;
+  const void *B;
   int lda, ldb;
   int ta, tb;   // op(A)[i][k] = ta ? A[k*lda+i] : A[i*lda+k]; same for B
   double alpha;
+  int f64;
 };
 
 // out[i][j] = sum_p alpha_p op(A_p) op(B_p) + beta1 C1 + beta2 C2 + diag * I
+// (out written as FP64 when out64 is set, else in the element type)
 struct Phase {
   int m, n, k;
   int np;
   Prod p[3];
-  const double *C1; int ldc1; double beta1;
-  const double *C2; int ldc2; double beta2;
+  const void *C1; int ldc1; double beta1;
+  const void *C2; int ldc2; double beta2;
   double diag;
-  double *out; int ldo;
+  void *out; int ldo;
+  int out64;
 };
 
+// Arguments of the dense chains.  In the mixed path's float-pair instantiation
+// the matrices marked (R) hold (hi, lo) float pairs in their 8-byte slots; A,
+// g, dO, the reductions and the energies are FP64 in both.
 struct DenseArgs {
   int M, N, V;
-  const double *A;       // a, N x V
-  double *P;             // N x N
-  double *Qk;            // [12][N*N] series workspace: Q^1..Q^4, blocks, Horner terms
-  double *Kt;            // [kJmax+1][N*N] cos sqrt(Q_t) - I
-  double *St;            // [kJmax+1][N*N] sin sqrt(Q_t)/sqrt(Q_t)
-  double *Uocc;          // M x N
-  double *O;             // M x N
-  double *D;             // M x M
-  double *H;             // M x M
-  double *TO;            // M x N, T O (mixed path)
-  const double *C0;      // M x M
-  const double *T;       // M x M
-  double *Gbar, *Ubar;   // M x N
-  double *Kbar[2], *Sbar[2], *Z[2];
-  double *Qbar, *Abar, *Psym;
-  double *Wr;            // [11][N*N] reverse workspace of the series
-  double *g;             // N x V output (may be null)
+  const double *A;       // a, N x V (FP64)
+  double *Af;            // (R) A as float pairs, N x V (mixed path only)
+  double *P;             // (R) N x N
+  double *Qk;            // (R) [12][N*N] series workspace: Q^1..Q^4, blocks, Horner terms
+  double *Kt;            // (R) [kJmax+1][N*N] cos sqrt(Q_t) - I
+  double *St;            // (R) [kJmax+1][N*N] sin sqrt(Q_t)/sqrt(Q_t)
+  double *Uocc;          // (R) M x N
+  double *O;             // (R) M x N
+  double *D;             // M x M (FP64 path)
+  double *H;             // (R) M x M
+  double *TO;            // (R) M x N, T O (mixed path)
+  const void *C0;        // (R) M x M
+  const void *T;         // (R) M x M
+  double *Gbar, *Ubar;   // (R) M x N
+  double *Kbar[2], *Sbar[2], *Z[2];  // (R)
+  double *Qbar, *Abar, *Psym;        // (R)
+  double *Wr;            // (R) [11][N*N] reverse workspace of the series
+  double *g;             // N x V output, FP64 (may be null)
   double *E;             // scalar output (may be null)
   double *eterms;        // [4] kinetic, external, hartree, exchange
   const double *gridpart;  // [n_gridpart][3] energy partials of the grid
-  const double *Vacc;    // mixed path: upper-triangle V from the grid pass, else null
+  const void *Vacc;      // (R) mixed path: upper-triangle V from the grid pass, else null
   const double *dO;      // mixed path: O - Oq for the first-order energy correction
   int n_gridpart;
   double *red;           // reduction scratch [gridDim][2]
@@ -167,7 +176,10 @@ struct etdm_handle {
   float2 *d_rhof = nullptr;   // [G] rho as float pairs
   float2 *d_vextf = nullptr;  // [G] v_ext as float pairs
   float2 *d_kpois = nullptr;  // [nx][ny][nz/2+1] Poisson kernel
-  double *d_Vfin = nullptr;   // [M][M] V (upper triangle), FP64
+  float2 *d_Vfin = nullptr;   // [M][M] V (upper triangle), float pairs
+  float2 *d_C0p = nullptr, *d_Tp = nullptr;  // C0 and T as float pairs
+  float2 *d_Af = nullptr;     // [N][V] A as float pairs
+  bool pairs_last = false;    // the last evaluation left float pairs in H, Uocc
   // matrices
   double *d_S = nullptr, *d_T = nullptr, *d_C0 = nullptr;
   double *d_D = nullptr, *d_H = nullptr, *d_Uocc = nullptr, *d_O = nullptr;
@@ -263,6 +275,8 @@ int tc_max_list();
 // message for etdm_last_error(NULL) from calls that take no handle
 void set_unbound_error(const std::string &msg);
 int occupancy_dense(int *blocks_per_sm);
+cudaError_t launch_to_pairs(const double *src, float2 *dst, long n, cudaStream_t s);
+cudaError_t launch_from_pairs(const float2 *src, double *dst, long n, cudaStream_t s);
 int occupancy_lbfgs(int *blocks_per_sm);
 
 }  // namespace etdm

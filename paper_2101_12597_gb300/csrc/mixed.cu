@@ -50,6 +50,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "pair.cuh"
 
 namespace etdm {
 
@@ -292,7 +293,6 @@ struct TcArgs {
   const double *v;              // [G]
   float2 *vt;                   // [n_tiles][128] v dV at the tile points (float pairs)
   unsigned long long *Vfix;     // [M][M] V (upper triangle) in fixed point, then [M*M] = max|v| bits
-  double *Vout;                 // [M][M] V, upper triangle
   double dV;
   int *flags;
 };
@@ -1070,13 +1070,13 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
 }
 
 // V (upper triangle) from its fixed-point sums
-__global__ void vfix_kernel(const unsigned long long *Vfix, int M, double *Vout) {
+__global__ void vfix_kernel(const unsigned long long *Vfix, int M, float2 *Vout) {
   const int F = vfix_exp((unsigned)Vfix[(long)M * M]);
   const long MM = (long)M * M;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
        e += (long)gridDim.x * blockDim.x) {
     if (e / M > e % M) continue;
-    Vout[e] = ldexp((double)(long long)Vfix[e], F);
+    Vout[e] = pair::split(ldexp((double)(long long)Vfix[e], F));
   }
 }
 
@@ -1095,14 +1095,15 @@ __global__ void tables_f32_kernel(const double *sq, const double *ex, const doub
   }
 }
 
-// Column slices of the occupied orbitals O (M x N): g_m = ilogb(max_mu |O_mu,m|)
-// + 2, K0 + K1 + K2 = O 2^(8 - g) to 24 bits (K_k on the 2^-8k grid); dO = O - Oq (FP64) for
-// the first-order energy correction sum (4 H O) o dO.
-__global__ void __launch_bounds__(256) oslice_kernel(const double *O, int M, int N, int NP,
+// Column slices of the occupied orbitals O (M x N, float pairs from the dense
+// chain): g_m = ilogb(max_mu |O_mu,m|) + 2, K0 + K1 + K2 = O 2^(8 - g) to 24 bits
+// (K_k on the 2^-8k grid); dO = O - Oq (FP64) for the first-order energy
+// correction sum (4 H O) o dO.
+__global__ void __launch_bounds__(256) oslice_kernel(const float2 *O, int M, int N, int NP,
                                                      uint2 *Osl, float *oscale, double *dO) {
   const int m = blockIdx.x;
   double mx = 0.0;
-  for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(O[(long)r * N + m]));
+  for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(pair::to_double(O[(long)r * N + m])));
   __shared__ double red[256];
   red[threadIdx.x] = mx;
   __syncthreads();
@@ -1114,7 +1115,7 @@ __global__ void __launch_bounds__(256) oslice_kernel(const double *O, int M, int
   const int g = mx > 0.0 ? ilogb(mx) + 2 : 0;
   if (threadIdx.x == 0) oscale[m] = ldexpf(1.f, g);
   for (int r = threadIdx.x; r < M; r += blockDim.x) {
-    const double o = O[(long)r * N + m];
+    const double o = pair::to_double(O[(long)r * N + m]);
     const double t0 = ldexp(o, 8 - g);
     const double r0 = rint(t0);
     const double t1 = (t0 - r0) * 256.0;
@@ -1153,7 +1154,6 @@ static TcArgs tc_args(etdm_handle *h) {
   a.v = h->d_vtot;
   a.vt = h->d_vt;
   a.Vfix = h->d_Vfix;
-  a.Vout = h->d_Vfin;
   a.dV = h->dV;
   a.flags = h->d_flags;
   return a;
@@ -1198,7 +1198,7 @@ void tc_tile_sizes(int nu, int *rho_steps, int *v_entries) {
 }
 
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
-  oslice_kernel<<<h->N, 256, 0, s>>>(h->d_O, h->M, h->N, h->N + (h->N & 1), h->d_Osl, h->d_oscale,
+  oslice_kernel<<<h->N, 256, 0, s>>>(reinterpret_cast<const float2 *>(h->d_O), h->M, h->N, h->N + (h->N & 1), h->d_Osl, h->d_oscale,
                                      h->d_dO);
   return cudaGetLastError();
 }
