@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <iterator>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -404,33 +405,77 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_rc2f = dalloc<float>(h, M);
     CUDA_TRY(cudaMemcpy(h->d_rc2f, rc2f.data(), M * sizeof(float), cudaMemcpyHostToDevice));
     h->d_rowexp = dalloc<signed char>(h, h->G);
-    // functions per tile, then the sizes and offsets of the resident X slices
+    // functions per tile (ascending: the image lists are sorted by key), the
+    // density's K steps per tile, and the V groups: greedy runs of consecutive
+    // tiles whose function lists have a union of at most tc_max_list() functions
     const int T = h->n_tiles_tc;
     h->d_nu_tc = dalloc<int>(h, std::max(T, 1));
     CUDA_TRY(launch_count_unique(h, h->d_nu_tc, s));
-    std::vector<int> nu(T), xr_off(T + 1, 0), xv_off(T + 1, 0);
-    CUDA_TRY(cudaMemcpy(nu.data(), h->d_nu_tc, T * sizeof(int), cudaMemcpyDeviceToHost));
-    long xr = 0, xv = 0;
+    std::vector<int> tptr(T + 1), keys(h->n_entries_tc);
+    CUDA_TRY(cudaMemcpy(tptr.data(), h->d_tile_ptr_tc, (T + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    if (h->n_entries_tc > 0)
+      CUDA_TRY(cudaMemcpy(keys.data(), h->d_keys_tc, h->n_entries_tc * sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> mu_off(T + 1, 0), tmu, xr_off(T + 1, 0);
+    long xr = 0;
     for (int t = 0; t < T; ++t) {
-      int ks = 0, ve = 0;
-      tc_tile_sizes(nu[t], &ks, &ve);
+      mu_off[t] = (int)tmu.size();
+      for (int e = tptr[t]; e < tptr[t + 1]; ++e) {
+        const int mu = keys[e] >> 9;
+        if (e == tptr[t] || mu != tmu.back()) tmu.push_back(mu);
+      }
       xr_off[t] = (int)xr;
-      xv_off[t] = (int)xv;
-      xr += ks;
-      xv += ve;
-      if (xr > INT32_MAX || xv > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
+      xr += tc_rho_steps((int)tmu.size() - mu_off[t]);
+      if (xr > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
     }
+    mu_off[T] = (int)tmu.size();
     xr_off[T] = (int)xr;
-    xv_off[T] = (int)xv;
+    std::vector<int> vg_t0, vg_nu, vg_eoff(1, 0), vg_xoff(1, 0), vg_mu;
+    {
+      std::vector<int> un, tmp;
+      long xkb = 0;
+      for (int t = 0; t < T;) {
+        un.assign(tmu.begin() + mu_off[t], tmu.begin() + mu_off[t + 1]);
+        int nt = 1;
+        while (nt < tc_group_max() && t + nt < T) {
+          tmp.clear();
+          std::set_union(un.begin(), un.end(), tmu.begin() + mu_off[t + nt],
+                         tmu.begin() + mu_off[t + nt + 1], std::back_inserter(tmp));
+          if ((int)tmp.size() > tc_max_list()) break;
+          un.swap(tmp);
+          ++nt;
+        }
+        const int np = tc_v_entries((int)un.size());
+        vg_t0.push_back(t);
+        vg_nu.push_back((int)un.size());
+        vg_mu.insert(vg_mu.end(), un.begin(), un.end());
+        vg_mu.resize(vg_mu.size() + (np - un.size()), 0);
+        vg_eoff.push_back((int)vg_mu.size());
+        xkb += (long)np * nt;
+        if (xkb > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
+        vg_xoff.push_back((int)xkb);
+        t += nt;
+      }
+      vg_t0.push_back(T);
+    }
+    h->n_vg = (int)vg_nu.size();
     h->xr_steps = xr;
-    h->xv_entries = xv;
-    h->d_xr_off = dalloc<int>(h, T + 1);
-    h->d_xv_off = dalloc<int>(h, T + 1);
-    CUDA_TRY(cudaMemcpy(h->d_xr_off, xr_off.data(), (T + 1) * sizeof(int), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(h->d_xv_off, xv_off.data(), (T + 1) * sizeof(int), cudaMemcpyHostToDevice));
-    h->d_xr = dalloc<uint8_t>(h, (size_t)xr * 16384);  // 4 slices x 4 KB per K step
-    h->d_xv = dalloc<uint8_t>(h, (size_t)xv * 1024);   // 8 K steps x 4 slices x 32 B per entry
-    h->d_vent = dalloc<float4>(h, (size_t)xv);
+    h->xv_entries = vg_eoff.back();
+    auto upload = [&](const std::vector<int> &v) {
+      int *d = dalloc<int>(h, std::max<size_t>(v.size(), 1));
+      if (!v.empty()) CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+      return d;
+    };
+    h->d_xr_off = upload(xr_off);
+    h->d_mu_off = upload(mu_off);
+    h->d_tmu = upload(tmu);
+    h->d_vg_t0 = upload(vg_t0);
+    h->d_vg_nu = upload(vg_nu);
+    h->d_vg_eoff = upload(vg_eoff);
+    h->d_vg_xoff = upload(vg_xoff);
+    h->d_vg_mu = upload(vg_mu);
+    h->d_xr = dalloc<uint8_t>(h, (size_t)xr * 16384);              // 4 slices x 4 KB per K step
+    h->d_xv = dalloc<uint8_t>(h, (size_t)vg_xoff.back() * 1024);   // per tile: 8 K steps x 4 slices x 32 B per entry
+    h->d_vent = dalloc<float4>(h, std::max<size_t>(vg_mu.size(), 1));
     h->d_vt = dalloc<float2>(h, (size_t)T * 128);
     CUDA_TRY(launch_operand_build(h, s));
     h->d_Osl = dalloc<uint2>(h, (long)M * (h->N + (h->N & 1)));  // rows padded to even length

@@ -160,9 +160,18 @@ struct etdm_handle {
   // function in one tile merged into one entry)
   int *d_nu_tc = nullptr;                // [n_tiles_tc] functions per tile
   int *d_xr_off = nullptr;               // [n_tiles_tc + 1] density K steps before a tile
-  int *d_xv_off = nullptr;               // [n_tiles_tc + 1] padded V entries before a tile
+  int *d_mu_off = nullptr;               // [n_tiles_tc + 1] functions of the tiles before a tile
+  int *d_tmu = nullptr;                  // functions of each tile (ascending)
+  // V groups: runs of consecutive 4x4x8 tiles whose function lists have a union
+  // of at most 128 functions; the V pass accumulates a group in one pass
+  int n_vg = 0;
+  int *d_vg_t0 = nullptr;                // [n_vg + 1] first tile of each group
+  int *d_vg_nu = nullptr;                // [n_vg] functions in the group's union
+  int *d_vg_eoff = nullptr;              // [n_vg + 1] padded union entries before a group
+  int *d_vg_xoff = nullptr;              // [n_vg + 1] KB of X^T slices before a group
+  int *d_vg_mu = nullptr;                // union function lists (ascending, padded)
   uint8_t *d_xr = nullptr, *d_xv = nullptr;
-  float4 *d_vent = nullptr;              // per padded V entry
+  float4 *d_vent = nullptr;              // per padded V group entry
   float2 *d_vt = nullptr;                // [n_tiles_tc][128] v dV in tile order
   long xr_steps = 0, xv_entries = 0;
   uint2 *d_Osl = nullptr;     // [M][N + N % 2] BF16 slices of O
@@ -267,7 +276,9 @@ cudaError_t launch_df_setup(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_df_potential(etdm_handle *h, cudaStream_t s);
 int df_pot_blocks(etdm_handle *h);
 cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);
-void tc_tile_sizes(int nu, int *rho_steps, int *v_entries);
+int tc_rho_steps(int nu);
+int tc_v_entries(int nu);
+int tc_group_max();
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);

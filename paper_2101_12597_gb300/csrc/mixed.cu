@@ -280,10 +280,17 @@ struct TcArgs {
   const float *rc2f;            // [M]
   const int *nu;                // [n_tiles] functions per tile (images merged)
   const int *xr_off;            // [n_tiles + 1] density K steps before each tile
-  const int *xv_off;            // [n_tiles + 1] padded V entries before each tile
+  const int *mu_off;            // [n_tiles + 1] functions of the tiles before each tile
+  const int *tmu;               // functions of each tile, ascending
+  int n_vg;                     // V groups: runs of consecutive tiles, union <= kNmax functions
+  const int *vg_t0;             // [n_vg + 1] first tile of each group
+  const int *vg_nu;             // [n_vg] functions of the group's union
+  const int *vg_eoff;           // [n_vg + 1] padded union entries before each group
+  const int *vg_xoff;           // [n_vg + 1] KB of X^T slices before each group
+  const int *vg_mu;             // union function lists, ascending, padded
   uint8_t *xr;                  // density X slices, 16 KB per K step
-  uint8_t *xv;                  // V X^T slices, 1 KB per padded entry
-  float4 *vent;                 // per padded entry: (mu bits, 2^(e_a - 8), bound, 0)
+  uint8_t *xv;                  // V X^T slices, 1 KB per padded union entry and tile
+  float4 *vent;                 // per padded union entry: (mu bits, 2^(e_a - 8), bound, 0)
   signed char *rowexp;          // [G] density row exponents e_p
   const uint2 *Osl;             // [M][NoccP] BF16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
   const float *oscale;          // [N] 2^g_m
@@ -441,59 +448,93 @@ __global__ void __launch_bounds__(256) xr_build_kernel(TcArgs A) {
 }
 
 // ---- set-up: V X^T slices (per-function exponents) -----------------------------
-// For tile t with padded length np, K step kk (points kk*16 .. kk*16+15), slice
-// k: block xv + xv_off[t] KB + kk * np * 128 + k * np * 32, element (a, c) at
-// kstep_off(a, c); rows a >= nu are zero.  vent[xv_off[t] + a] = (mu, 2^(e_a-8),
-// bound of |X_pa| over the tile, 0).
+// V group g (tiles t0 .. t0 + nt - 1, union of np padded entries): for K step kk
+// (points kk*16 .. kk*16+15 of the group, tile t0 + kk / 8), slice k: block
+// xv + vg_xoff[g] KB + kk * np * 128 + k * np * 32, element (a, c) at
+// kstep_off(a, c); rows a >= nu and functions absent from a tile's list are zero
+// there.  vent[vg_eoff[g] + a] = (mu, 2^(e_a-8), bound of |X_pa| over the group, 0).
+
+// row of function mu in the ascending union list umu[0, n) (mu is present)
+__device__ __forceinline__ int union_row(const int *umu, int n, int mu) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (umu[m] < mu) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(256) xv_build_kernel(TcArgs A) {
   extern __shared__ __align__(1024) uint8_t dsm[];
   float4 *xy = (float4 *)dsm, *zs = xy + kStageXY;
   __shared__ BuildShared S;
-  __shared__ float sa_s[kNmax];
-  for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
-    const int kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
-    stage_tile<true>(A, S, xy, zs, t, kb, n);
-    const int nu = S.nu, np = vpad(nu);
+  __shared__ float bnd_s[kNmax], sa_s[kNmax];
+  __shared__ int umu[kNmax], loc[kNmax];
+  for (int g = blockIdx.x; g < A.n_vg; g += gridDim.x) {
+    const int t0 = A.vg_t0[g], nt = A.vg_t0[g + 1] - t0, nu = A.vg_nu[g];
+    const int e0 = A.vg_eoff[g], np = A.vg_eoff[g + 1] - e0;
     for (int a = threadIdx.x; a < np; a += blockDim.x) {
-      float bnd = 0.f;
-      if (a < nu) {  // separable bound of |X_pa| over the tile, summed over images
-        for (int e = S.ustart[a]; e < S.ustart[a + 1]; ++e) {
+      umu[a] = A.vg_mu[e0 + a];
+      bnd_s[a] = 0.f;
+    }
+    __syncthreads();
+    for (int q = 0; q < nt; ++q) {  // separable bound of |X_pa| per tile, summed over images
+      const int t = t0 + q, kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
+      stage_tile<true>(A, S, xy, zs, t, kb, n);
+      for (int u = threadIdx.x; u < S.nu; u += blockDim.x) {
+        float bnd = 0.f;
+        for (int e = S.ustart[u]; e < S.ustart[u + 1]; ++e) {
           float mxy = 0.f, mz = 0.f;
           for (int s = 0; s < 16; ++s) mxy = fmaxf(mxy, xy[xy_idx<true>(e, s)].y);
           for (int s = 0; s < 8; ++s) mz = fmaxf(mz, zs[z_idx<true>(e, s)].y);
           bnd += mxy * mz * 1.0001f;
         }
-        bnd *= 1.0001f;
+        const int r = union_row(umu, nu, S.mu[S.ustart[u]]);
+        bnd_s[r] = fmaxf(bnd_s[r], bnd * 1.0001f);
       }
+      __syncthreads();
+    }
+    for (int a = threadIdx.x; a < np; a += blockDim.x) {
+      const float bnd = bnd_s[a];
       const int ea = slice_exp(bnd);
       sa_s[a] = pow2f(8 - ea);
-      A.vent[A.xv_off[t] + a] =
-          make_float4(__int_as_float(a < nu ? S.mu[S.ustart[a]] : 0), pow2f(ea - 8), bnd, 0.f);
+      A.vent[e0 + a] = make_float4(__int_as_float(a < nu ? umu[a] : 0), pow2f(ea - 8), bnd, 0.f);
     }
-    __syncthreads();
-    uint8_t *base = A.xv + (size_t)A.xv_off[t] * 1024;
-    for (int q = threadIdx.x; q < np * 16; q += blockDim.x) {
-      const int a = q % np, gq = q / np;  // points gq*8 .. gq*8+7
-      const float sa = sa_s[a];
-      uint32_t wd[4][4];
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        float r[2][4];
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          const int p = gq * 8 + u + v;
-          slice4(a < nu ? func_val<true>(S, xy, zs, a, p) : make_float2(0.f, 0.f), sa, r[v]);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) wd[k][u >> 1] = pack_bf16(r[0][k], r[1][k]);
+    uint8_t *base = A.xv + (size_t)A.vg_xoff[g] * 1024;
+    for (int q = 0; q < nt; ++q) {
+      const int t = t0 + q;
+      if (nt > 1) {  // (a one-tile group is still staged from the bound pass)
+        const int kb = A.tile_ptr[t], n = min(A.tile_ptr[t + 1] - kb, kNmax);
+        stage_tile<true>(A, S, xy, zs, t, kb, n);
       }
-      uint8_t *blk = base + (size_t)(gq >> 1) * np * 128;
-      const int off = kstep_off(a, (gq & 1) * 8);
+      for (int a = threadIdx.x; a < np; a += blockDim.x) loc[a] = -1;
+      __syncthreads();
+      for (int u = threadIdx.x; u < S.nu; u += blockDim.x) loc[union_row(umu, nu, S.mu[S.ustart[u]])] = u;
+      __syncthreads();
+      for (int qq = threadIdx.x; qq < np * 16; qq += blockDim.x) {
+        const int a = qq % np, gq = qq / np;  // points gq*8 .. gq*8+7 of the tile
+        const float sa = sa_s[a];
+        const int u = loc[a];
+        uint32_t wd[4][4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        *(uint4 *)(blk + k * np * 32 + off) = make_uint4(wd[k][0], wd[k][1], wd[k][2], wd[k][3]);
+        for (int uu = 0; uu < 8; uu += 2) {
+          float r[2][4];
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const int p = gq * 8 + uu + v;
+            slice4(u >= 0 ? func_val<true>(S, xy, zs, u, p) : make_float2(0.f, 0.f), sa, r[v]);
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) wd[k][uu >> 1] = pack_bf16(r[0][k], r[1][k]);
+        }
+        uint8_t *blk = base + (size_t)(q * 8 + (gq >> 1)) * np * 128;
+        const int off = kstep_off(a, (gq & 1) * 8);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          *(uint4 *)(blk + k * np * 32 + off) = make_uint4(wd[k][0], wd[k][1], wd[k][2], wd[k][3]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -580,7 +621,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int a = lane + 32 * r;
-        mu4[r] = a < nu ? __float_as_int(A.vent[A.xv_off[t] + a].x) : 0;
+        mu4[r] = a < nu ? A.tmu[A.mu_off[t] + a] : 0;
       }
       for (int kk = 0; kk < nk; ++kk, ++fill) {
         const int s = fill % kRhoStages, use = fill / kRhoStages;
@@ -773,48 +814,65 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
 }
 
 // ---- potential matrix ---------------------------------------------------------
-// V_loc = dV X^T diag(v) X per tile as D = W X^T on the tensor cores, W = (v X)^T
-// (rows = list functions i, the accumulator lanes) and X^T (columns j), both
-// in four exact integer slices, slice orders 0..3 in four FP32 accumulators.
-// Warp roles: 0-15 read the accumulators (lane quarter w % 4, every fourth
-// 8-column chunk by w / 4) into a staged triangle, hand them back, and add the
-// staged values into V by fixed-point reductions; 16-23
-// build W from the X^T slices and v; 24 streams the X^T slices and the tile
-// buffers (v at the points, list entries); 25 issues the MMAs.  Lane i takes the
-// columns j <= i and adds into V[mu_j][mu_i] (mu_j <= mu_i), so a warp's
-// reductions run along a row of V.
-constexpr int kVStages = 4;
+// V_loc = dV X^T diag(v) X per group of tiles as D = W X^T on the tensor cores,
+// W = (v X)^T (rows = union functions i, the accumulator lanes) and X^T
+// (columns j), both in four exact integer slices.  The slice products of order
+// 0 go into one FP32 accumulator (exact: integers below 2^24 on the 2^0 grid),
+// those of orders 1..3 into a second (about 2^-8 of the first, so its FP32
+// rounding is 2^-32 of V's scale).  Two accumulator pairs (4 x 128 TMEM
+// columns) alternate between groups, so the read-out of one group overlaps the
+// MMAs of the next.  Warp roles: 0-15 read the accumulators (lane quarter
+// w % 4, every fourth 8-column chunk by w / 4) and add into V by fixed-point
+// reductions; 16-23 build W from the X^T slices and v; 24 streams the X^T
+// slices and the group buffers (v at the points, union entries); 25 issues the
+// MMAs.  Lane i takes the columns j <= i and adds into V[mu_j][mu_i]
+// (mu_j <= mu_i), so a warp's reductions run along a row of V.
+constexpr int kVStages = 6;
 constexpr int kVA = 4 * kSlot;   // W slices (128 rows)
 constexpr int kVB = 4 * kSlot;   // X^T slices (np rows each, packed as stored)
 constexpr int kVStage = kVA + kVB;
 constexpr int kVEpiW = 16, kVBldW = 8;  // warps: 0-15 read-out, 16-23 build W
 constexpr int kVEpi = kVEpiW * 32, kVBld = kVBldW * 32;
 constexpr int kVThreads = kVEpi + kVBld + 64;
-constexpr int kVTileBuf = kTP * 8 + kNmax * 16;  // v pairs + list entries (3 KB)
-constexpr int kVTri = kNmax * (kNmax + 1) / 2;     // lower triangle of V_loc (float pairs)
-
-// start of column j of the column-major lower triangle of an n x n matrix
-__device__ __forceinline__ int tri_col(int j, int n) { return j * n - (j * (j - 1)) / 2; }
+constexpr int kVGmax = 2;                         // tiles per V group at most
+constexpr int kVTileBuf = kVGmax * kTP * 8 + kNmax * 16;  // v pairs + union entries
 
 struct VBars {
   uint64_t tma_full[kVStages], bld_full[kVStages], empty[kVStages];
-  uint64_t tile_full[2], tile_empty[2], acc_full, acc_empty, fin;
-  uint64_t stage_full, stage_free;  // read-out phases 1 -> 2 and 2 -> next 1
+  uint64_t tile_full[2], tile_empty[2], acc_full[2], acc_empty[2], fin;
   uint32_t tbase;
   int stop;
 };
 
-// max |v dV| over a tile's points (all lanes of the calling warp get it)
-__device__ __forceinline__ float tile_vmax(const float2 *vt) {
+// max |v dV| over a group's points (all lanes of the calling warp get it)
+__device__ __forceinline__ float tile_vmax(const float2 *vt, int n) {
   float m = 0.f;
-  for (int p = (threadIdx.x & 31); p < kTP; p += 32) m = fmaxf(m, fabsf(vt[p].x));
+  for (int p = (threadIdx.x & 31); p < n; p += 32) m = fmaxf(m, fabsf(vt[p].x));
   // non-negative floats order as their bit patterns
   return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
 }
 
+// 8 columns of the two accumulators of a lane quarter; the wait is a separate
+// statement that names the registers, so no use is scheduled before it
+__device__ __forceinline__ void tmem_ld2_issue(uint32_t t0, uint32_t t1, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(t0), "r"(t1));
+}
+__device__ __forceinline__ void tmem_ld2_wait(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
 __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   extern __shared__ __align__(1024) uint8_t dsm[];
-  uint8_t *tbuf = dsm + kVStages * kVStage;  // 2 tile buffers: vt[128] float2, vent[np] float4
+  uint8_t *tbuf = dsm + kVStages * kVStage;  // 2 group buffers: vt[nt * 128] float2, vent[np] float4
   __shared__ VBars R;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int M = A.g.M;
@@ -827,12 +885,10 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     for (int b = 0; b < 2; ++b) {
       mbar_init(&R.tile_full[b], 1);
       mbar_init(&R.tile_empty[b], (kVEpi + kVBld) / 32);
+      mbar_init(&R.acc_full[b], 1);
+      mbar_init(&R.acc_empty[b], kVEpiW);
     }
-    mbar_init(&R.acc_full, 1);
-    mbar_init(&R.acc_empty, kVEpi);
     mbar_init(&R.fin, 1);
-    mbar_init(&R.stage_full, kVEpi);
-    mbar_init(&R.stage_free, kVEpi);
     R.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -841,14 +897,12 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = R.tbase;
-  float2 *vst = (float2 *)(tbuf + 2 * kVTileBuf);  // staged V_loc, column-major lower triangle
-  float *ubs = (float *)(vst + kVTri);              // per-row scales of the tile
-  // a contiguous run of tiles per CTA: CTAs running at the same time work in
+  // a contiguous run of groups per CTA: CTAs running at the same time work in
   // different parts of the box and rarely add into the same entries of V
-  const int tbeg = (int)((long)A.n_tiles * blockIdx.x / gridDim.x);
-  const int ntl = (int)((long)A.n_tiles * (blockIdx.x + 1) / gridDim.x) - tbeg;
+  const int tbeg = (int)((long)A.n_vg * blockIdx.x / gridDim.x);
+  const int ntl = (int)((long)A.n_vg * (blockIdx.x + 1) / gridDim.x) - tbeg;
   volatile int *stop = &R.stop;
-  constexpr int kSteps = kTP / kKs;  // 8 K steps of 16 points per tile
+  constexpr int kSteps = kTP / kKs;  // 8 K steps of 16 points per tile of the group
 
   if (w == kVEpiW + kVBldW) {
     // ------------------------ bulk copies: tile buffers and X^T ------------------------
@@ -856,15 +910,16 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
       int fill = 0, it = 0;
       bool ok = true;
       for (; it < ntl && ok; ++it) {
-        const int t = tbeg + it, mb = it & 1;
-        const int x0 = A.xv_off[t], np = A.xv_off[t + 1] - x0;
+        const int g = tbeg + it, mb = it & 1;
+        const int t0 = A.vg_t0[g], nt = A.vg_t0[g + 1] - t0;
+        const int e0 = A.vg_eoff[g], np = A.vg_eoff[g + 1] - e0;
         if (it >= 2 && !mbar_wait(&R.tile_empty[mb], ((it >> 1) - 1) & 1, stop)) { ok = false; break; }
         uint8_t *tb = tbuf + mb * kVTileBuf;
-        mbar_expect_tx(&R.tile_full[mb], kTP * 8 + np * 16);
-        bulk_g2s(tb, A.vt + (size_t)t * kTP, kTP * 8, &R.tile_full[mb]);
-        bulk_g2s(tb + kTP * 8, A.vent + x0, np * 16, &R.tile_full[mb]);
-        const uint8_t *src = A.xv + (size_t)x0 * 1024;
-        for (int kk = 0; kk < kSteps; ++kk, ++fill) {
+        mbar_expect_tx(&R.tile_full[mb], nt * kTP * 8 + np * 16);
+        bulk_g2s(tb, A.vt + (size_t)t0 * kTP, nt * kTP * 8, &R.tile_full[mb]);
+        bulk_g2s(tb + kVGmax * kTP * 8, A.vent + e0, np * 16, &R.tile_full[mb]);
+        const uint8_t *src = A.xv + (size_t)A.vg_xoff[g] * 1024;
+        for (int kk = 0; kk < nt * kSteps; ++kk, ++fill) {
           const int s = fill % kVStages, use = fill / kVStages;
           if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
           mbar_expect_tx(&R.tma_full[s], np * 128);
@@ -884,12 +939,15 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
       int fill = 0;
       bool ok = true;
       for (int it = 0; it < ntl && ok; ++it) {
-        const int t = tbeg + it;
-        const int np = A.xv_off[t + 1] - A.xv_off[t];
-        if (it > 0 && !mbar_wait(&R.acc_empty, (it - 1) & 1, stop)) { ok = false; break; }
+        const int g = tbeg + it, buf = it & 1;
+        const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
+        const int np = A.vg_eoff[g + 1] - A.vg_eoff[g];
+        // the accumulator pair of group it - 2 has been read
+        if (it >= 2 && !mbar_wait(&R.acc_empty[buf], ((it >> 1) - 1) & 1, stop)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t idesc = idesc_bf16(np);
-        for (int kk = 0; kk < kSteps; ++kk, ++fill) {
+        const uint32_t d0 = tmem + buf * 2 * kNmax, d1 = d0 + kNmax;
+        for (int kk = 0; kk < nt * kSteps; ++kk, ++fill) {
           const int s = fill % kVStages, use = fill / kVStages;
           if (!mbar_wait(&R.tma_full[s], use & 1, stop) || !mbar_wait(&R.bld_full[s], use & 1, stop)) {
             ok = false;
@@ -904,19 +962,19 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
             X[k] = smem_desc(b0 + k * np * 32);
           }
           const uint32_t acc = kk > 0;
-          mma_bf16(tmem, W[0], X[0], idesc, acc);                 // order 0
-          mma_bf16(tmem + kNmax, W[0], X[1], idesc, acc);         // order 1
-          mma_bf16(tmem + kNmax, W[1], X[0], idesc, 1u);
-          mma_bf16(tmem + 2 * kNmax, W[0], X[2], idesc, acc);     // order 2
-          mma_bf16(tmem + 2 * kNmax, W[1], X[1], idesc, 1u);
-          mma_bf16(tmem + 2 * kNmax, W[2], X[0], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, W[0], X[3], idesc, acc);     // order 3
-          mma_bf16(tmem + 3 * kNmax, W[1], X[2], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, W[2], X[1], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, W[3], X[0], idesc, 1u);
+          mma_bf16(d0, W[0], X[0], idesc, acc);   // order 0
+          mma_bf16(d1, W[0], X[1], idesc, acc);   // orders 1..3
+          mma_bf16(d1, W[1], X[0], idesc, 1u);
+          mma_bf16(d1, W[0], X[2], idesc, 1u);
+          mma_bf16(d1, W[1], X[1], idesc, 1u);
+          mma_bf16(d1, W[2], X[0], idesc, 1u);
+          mma_bf16(d1, W[0], X[3], idesc, 1u);
+          mma_bf16(d1, W[1], X[2], idesc, 1u);
+          mma_bf16(d1, W[2], X[1], idesc, 1u);
+          mma_bf16(d1, W[3], X[0], idesc, 1u);
           mma_commit(&R.empty[s]);
         }
-        if (ok) mma_commit(&R.acc_full);
+        if (ok) mma_commit(&R.acc_full[buf]);
       }
       if (!ok) atomicExch((int *)stop, 1);
       mma_commit(&R.fin);
@@ -929,23 +987,24 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     int fill = 0;
     bool ok = true;
     for (int it = 0; it < ntl && ok; ++it) {
-      const int t = tbeg + it, mb = it & 1;
-      const int np = A.xv_off[t + 1] - A.xv_off[t];
-      const int nu = A.nu[t];
+      const int g = tbeg + it, mb = it & 1;
+      const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
+      const int np = A.vg_eoff[g + 1] - A.vg_eoff[g];
+      const int nu = A.vg_nu[g];
       ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop));
       if (!ok) break;
       const uint8_t *tb = tbuf + mb * kVTileBuf;
       const float2 *vt = (const float2 *)tb;
-      const float4 *ve = (const float4 *)(tb + kTP * 8);
-      const float vmax = tile_vmax(vt);
+      const float4 *ve = (const float4 *)(tb + kVGmax * kTP * 8);
+      const float vmax = tile_vmax(vt, nt * kTP);
       // row b: X^T slices of x 2^(8 - e_b); W row exponent from the bound of
-      // |v x| over the tile
+      // |v x| over the group
       float sb = 0.f;  // 2^(8 - e_w) 2^(e_b - 8): the X^T slices hold x 2^(8 - e_b)
       if (b < nu) {
         const float4 e = ve[b];
         sb = pow2f(8 - slice_exp(e.z * vmax * 1.0001f)) * e.y;
       }
-      for (int kk = 0; kk < kSteps; ++kk, ++fill) {
+      for (int kk = 0; kk < nt * kSteps; ++kk, ++fill) {
         const int s = fill % kVStages, use = fill / kVStages;
         if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
         if (!mbar_wait(&R.tma_full[s], use & 1, stop)) { ok = false; break; }
@@ -993,73 +1052,56 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     if (!ok) atomicExch((int *)stop, 1);
   } else {
     // ------------------------- accumulator read-out into V ----------------------------
-    // phase 1 (holds the accumulators): V_loc as float pairs (hi, lo) of y =
-    // acc0 + acc1 + acc2 + acc3 into the staged lower triangle, then the
-    // accumulators go back to the MMA thread; phase 2 (overlaps the next tile's
-    // MMAs): scale, convert to fixed point and add into V, a warp per column j,
-    // lanes along i, so the reductions into V[mu_j][mu_i] run along a row of V
+    // lane i of quarter w % 4 holds row i; columns j <= i of every fourth
+    // 8-column chunk (by w / 4): y = acc0 + acc1 as a float pair, scaled to the
+    // fixed-point unit, added into V[mu_j][mu_i]
     const int quad = w & 3, part = w >> 2;
     const int i = quad * 32 + lane;  // accumulator lane = W row
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
     const int fixe = vfix_exp((unsigned)A.Vfix[(long)M * M]);
     bool ok = true;
     for (int it = 0; it < ntl && ok; ++it) {
-      const int t = tbeg + it, mb = it & 1;
-      const int nu = A.nu[t];
+      const int g = tbeg + it, mb = it & 1, buf = it & 1;
+      const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
+      const int nu = A.vg_nu[g];
       ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop) &&
-                                       mbar_wait(&R.acc_full, it & 1, stop) &&
-                                       (it == 0 || mbar_wait(&R.stage_free, (it - 1) & 1, stop)));
+                                       mbar_wait(&R.acc_full[buf], (it >> 1) & 1, stop));
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint8_t *tb = tbuf + mb * kVTileBuf;
-      const float4 *ve = (const float4 *)(tb + kTP * 8);
-      if (part == 0) {  // 2^(e_i - 8 - F): W row scale over the fixed-point unit
-        const float vmax = tile_vmax((const float2 *)tb);
-        ubs[i] = i < nu ? pow2f(max(slice_exp(ve[i].z * vmax * 1.0001f) - 8 - fixe, -126)) : 0.f;
-      }
-      // phase 1: columns j <= i of this warp's lanes, every fourth 8-column chunk
+      const float4 *ve = (const float4 *)(tb + kVGmax * kTP * 8);
+      const float vmax = tile_vmax((const float2 *)tb, nt * kTP);
+      // 2^(e_i - 8 - F): W row scale over the fixed-point unit; mu of row i
+      const float ub = i < nu ? pow2f(max(slice_exp(ve[i].z * vmax * 1.0001f) - 8 - fixe, -126)) : 0.f;
+      const int mui = i < nu ? __float_as_int(ve[i].x) : 0;
+      unsigned long long *const vrow = A.Vfix + mui;
+      const uint32_t t0 = tmem + lanebits + buf * 2 * kNmax;
       const int jend = quad * 32 < nu ? min(quad * 32 + 32, nu) : 0;
       for (int c0 = part * 8; c0 < jend; c0 += 32) {
-        uint32_t ra[32];
-        tmem_ld_issue(tmem + lanebits + c0, ra);
-        tmem_ld_wait(ra);
-        if (i < nu) {
+        uint32_t ra[16];
+        tmem_ld2_issue(t0 + c0, t0 + kNmax + c0, ra);
+        tmem_ld2_wait(ra);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int j = c0 + c;
-            if (j <= i) {
-              const float y0 = __uint_as_float(ra[c]);
-              float lo = __uint_as_float(ra[8 + c]) +
-                         (__uint_as_float(ra[16 + c]) + __uint_as_float(ra[24 + c]));
-              const float hi = y0 + lo;
-              lo = lo - (hi - y0);
-              vst[tri_col(j, nu) + i - j] = make_float2(hi, lo);
+        for (int c = 0; c < 8; ++c) {
+          const int j = c0 + c;
+          if (i < nu && j <= i) {
+            const float4 ej = ve[j];
+            const float f = ub * ej.y;  // exact: a product of powers of two
+            const float2 y = pair::two_sum(__uint_as_float(ra[c]), __uint_as_float(ra[8 + c]));
+            // a contribution below the fixed-point unit truncates to zero: nothing to add
+            if (fabsf(y.x * f) >= 1.f) {
+              const long long val = f2ll_trunc(y.x * f) + f2ll_trunc(y.y * f);
+              atomicAdd(vrow + (long)__float_as_int(ej.x) * M, (unsigned long long)val);
             }
           }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&R.acc_empty);
-      mbar_arrive(&R.stage_full);
-      ok = __all_sync(0xffffffffu, mbar_wait(&R.stage_full, it & 1, stop));
-      if (!ok) break;
-      // phase 2: column j = w, w + 16, ..; rows i = j + lane, j + lane + 32, ..
-      for (int j = w; j < nu; j += kVEpiW) {
-        const float4 ej = ve[j];
-        const int muj = __float_as_int(ej.x);
-        const float2 *col = vst + tri_col(j, nu) - j;
-        for (int r = j + lane; r < nu; r += 32) {
-          const float2 y = col[r];
-          const float f = ubs[r] * ej.y;  // exact: a product of powers of two
-          // a contribution below the fixed-point unit truncates to zero: nothing to add
-          if (!(fabsf(y.x * f) >= 1.f)) continue;
-          const long long val = f2ll_trunc(y.x * f) + f2ll_trunc(y.y * f);
-          atomicAdd(A.Vfix + (long)muj * M + __float_as_int(ve[r].x), (unsigned long long)val);
-        }
-      }
-      mbar_arrive(&R.stage_free);
       __syncwarp();
-      if (lane == 0) mbar_arrive(&R.tile_empty[mb]);
+      if (lane == 0) {
+        mbar_arrive(&R.acc_empty[buf]);
+        mbar_arrive(&R.tile_empty[mb]);
+      }
     }
     if (!ok) atomicExch((int *)stop, 1);
   }
@@ -1140,7 +1182,14 @@ static TcArgs tc_args(etdm_handle *h) {
   a.rc2f = h->d_rc2f;
   a.nu = h->d_nu_tc;
   a.xr_off = h->d_xr_off;
-  a.xv_off = h->d_xv_off;
+  a.mu_off = h->d_mu_off;
+  a.tmu = h->d_tmu;
+  a.n_vg = h->n_vg;
+  a.vg_t0 = h->d_vg_t0;
+  a.vg_nu = h->d_vg_nu;
+  a.vg_eoff = h->d_vg_eoff;
+  a.vg_xoff = h->d_vg_xoff;
+  a.vg_mu = h->d_vg_mu;
   a.xr = h->d_xr;
   a.xv = h->d_xv;
   a.vent = h->d_vent;
@@ -1192,10 +1241,9 @@ cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-void tc_tile_sizes(int nu, int *rho_steps, int *v_entries) {
-  *rho_steps = rsteps(nu);
-  *v_entries = vpad(nu);
-}
+int tc_rho_steps(int nu) { return rsteps(nu); }
+int tc_v_entries(int nu) { return vpad(nu); }
+int tc_group_max() { return kVGmax; }
 
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
   oslice_kernel<<<h->N, 256, 0, s>>>(reinterpret_cast<const float2 *>(h->d_O), h->M, h->N, h->N + (h->N & 1), h->d_Osl, h->d_oscale,
@@ -1214,8 +1262,7 @@ cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
 }
 
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
-  const size_t sm = (size_t)kVStages * kVStage + 2 * (size_t)kVTileBuf +
-                    (size_t)kVTri * sizeof(float2) + kNmax * sizeof(float);
+  const size_t sm = (size_t)kVStages * kVStage + 2 * (size_t)kVTileBuf;
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -1223,7 +1270,7 @@ cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
   // order, by the potential pass
   const TcArgs a = tc_args(h);
   const size_t MM = (size_t)h->M * h->M;
-  vmat_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kVThreads, sm, s>>>(a);
+  vmat_tc_kernel<<<std::max(1, std::min(h->n_vg, h->num_sms)), kVThreads, sm, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   vfix_kernel<<<(int)std::min<size_t>((MM + 255) / 256, 1024), 256, 0, s>>>(h->d_Vfix, h->M, h->d_Vfin);
