@@ -450,7 +450,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
         vg_mu.insert(vg_mu.end(), un.begin(), un.end());
         vg_mu.resize(vg_mu.size() + (np - un.size()), 0);
         vg_eoff.push_back((int)vg_mu.size());
-        xkb += (long)np * nt;
+        xkb += (long)np * nt * tc_v_slices();  // 256-byte units: 8 K steps x 32 B per slice
         if (xkb > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
         vg_xoff.push_back((int)xkb);
         t += nt;
@@ -474,7 +474,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_vg_xoff = upload(vg_xoff);
     h->d_vg_mu = upload(vg_mu);
     h->d_xr = dalloc<uint8_t>(h, (size_t)xr * 16384);              // 4 slices x 4 KB per K step
-    h->d_xv = dalloc<uint8_t>(h, (size_t)vg_xoff.back() * 1024);   // per tile: 8 K steps x 4 slices x 32 B per entry
+    h->d_xv = dalloc<uint8_t>(h, (size_t)vg_xoff.back() * 256);
     h->d_vent = dalloc<float4>(h, std::max<size_t>(vg_mu.size(), 1));
     h->d_vt = dalloc<float2>(h, (size_t)T * 128);
     CUDA_TRY(launch_operand_build(h, s));

@@ -168,7 +168,7 @@ struct etdm_handle {
   int *d_vg_t0 = nullptr;                // [n_vg + 1] first tile of each group
   int *d_vg_nu = nullptr;                // [n_vg] functions in the group's union
   int *d_vg_eoff = nullptr;              // [n_vg + 1] padded union entries before a group
-  int *d_vg_xoff = nullptr;              // [n_vg + 1] KB of X^T slices before a group
+  int *d_vg_xoff = nullptr;              // [n_vg + 1] 256-byte units of X^T slices before a group
   int *d_vg_mu = nullptr;                // union function lists (ascending, padded)
   uint8_t *d_xr = nullptr, *d_xv = nullptr;
   float4 *d_vent = nullptr;              // per padded V group entry
@@ -279,6 +279,7 @@ cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);
 int tc_rho_steps(int nu);
 int tc_v_entries(int nu);
 int tc_group_max();
+int tc_v_slices();
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);

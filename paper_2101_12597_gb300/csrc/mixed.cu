@@ -56,6 +56,10 @@ namespace etdm {
 
 constexpr int kTP = 128;                 // points per tile (4 x 4 x 8)
 constexpr int kNmax = 128;               // max list length per tile
+// slices of the V operands, X^T (resident, per-function exponents over a
+// group) and W = (v X)^T (per-row exponents over the group), and the highest
+// order of slice products kept
+constexpr int kVSlX = 3, kVSlW = 3, kVOrd = 3;
 constexpr int kTmemCols = 512;
 constexpr long kMbarSpin = 4000000;
 constexpr int kKs = 16;                  // K of one MMA (a "K step")
@@ -253,16 +257,21 @@ __device__ __forceinline__ int vfix_exp(unsigned vmax_bits) {
 // 128 2^-8k.  Each r_k rounds the remainder to its grid by adding and removing
 // 1.5 2^(23-8k); the remainders are exact, only the step that adds the low part
 // rounds.
-__device__ __forceinline__ void slice4(float2 x, float sc, float *r) {
+template <int NS>
+__device__ __forceinline__ void slice_n(float2 x, float sc, float *r) {
+  static_assert(NS >= 2 && NS <= 4, "two to four slices");
   const float C0 = 12582912.f, C1 = 49152.f, C2 = 192.f, C3 = 0.75f;
   r[0] = __fadd_rn(__fmaf_rn(x.x, sc, C0), -C0);
   float u = __fmaf_rn(x.y, sc, __fmaf_rn(x.x, sc, -r[0]));
   r[1] = __fadd_rn(__fadd_rn(u, C1), -C1);
+  if (NS == 2) return;
   u = __fadd_rn(u, -r[1]);
   r[2] = __fadd_rn(__fadd_rn(u, C2), -C2);
+  if (NS == 3) return;
   u = __fadd_rn(u, -r[2]);
   r[3] = __fadd_rn(__fadd_rn(u, C3), -C3);
 }
+__device__ __forceinline__ void slice4(float2 x, float sc, float *r) { slice_n<4>(x, sc, r); }
 
 // BF16 pair (lo | hi << 16) of two floats with at most 8 significant bits (exact:
 // their low 16 bits are zero)
@@ -286,7 +295,7 @@ struct TcArgs {
   const int *vg_t0;             // [n_vg + 1] first tile of each group
   const int *vg_nu;             // [n_vg] functions of the group's union
   const int *vg_eoff;           // [n_vg + 1] padded union entries before each group
-  const int *vg_xoff;           // [n_vg + 1] KB of X^T slices before each group
+  const int *vg_xoff;           // [n_vg + 1] 256-byte units of X^T slices before each group
   const int *vg_mu;             // union function lists, ascending, padded
   uint8_t *xr;                  // density X slices, 16 KB per K step
   uint8_t *xv;                  // V X^T slices, 1 KB per padded union entry and tile
@@ -449,10 +458,10 @@ __global__ void __launch_bounds__(256) xr_build_kernel(TcArgs A) {
 
 // ---- set-up: V X^T slices (per-function exponents) -----------------------------
 // V group g (tiles t0 .. t0 + nt - 1, union of np padded entries): for K step kk
-// (points kk*16 .. kk*16+15 of the group, tile t0 + kk / 8), slice k: block
-// xv + vg_xoff[g] KB + kk * np * 128 + k * np * 32, element (a, c) at
-// kstep_off(a, c); rows a >= nu and functions absent from a tile's list are zero
-// there.  vent[vg_eoff[g] + a] = (mu, 2^(e_a-8), bound of |X_pa| over the group, 0).
+// (points kk*16 .. kk*16+15 of the group, tile t0 + kk / 8), slice k < kVSlX:
+// block xv + vg_xoff[g] * 256 + kk * np * 32 * kVSlX + k * np * 32, element (a, c)
+// at kstep_off(a, c); rows a >= nu and functions absent from a tile's list are
+// zero there.  vent[vg_eoff[g] + a] = (mu, 2^(e_a-8), bound of |X_pa| over the group, 0).
 
 // row of function mu in the ascending union list umu[0, n) (mu is present)
 __device__ __forceinline__ int union_row(const int *umu, int n, int mu) {
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(256) xv_build_kernel(TcArgs A) {
       sa_s[a] = pow2f(8 - ea);
       A.vent[e0 + a] = make_float4(__int_as_float(a < nu ? umu[a] : 0), pow2f(ea - 8), bnd, 0.f);
     }
-    uint8_t *base = A.xv + (size_t)A.vg_xoff[g] * 1024;
+    uint8_t *base = A.xv + (size_t)A.vg_xoff[g] * 256;
     for (int q = 0; q < nt; ++q) {
       const int t = t0 + q;
       if (nt > 1) {  // (a one-tile group is still staged from the bound pass)
@@ -515,22 +524,22 @@ __global__ void __launch_bounds__(256) xv_build_kernel(TcArgs A) {
         const int a = qq % np, gq = qq / np;  // points gq*8 .. gq*8+7 of the tile
         const float sa = sa_s[a];
         const int u = loc[a];
-        uint32_t wd[4][4];
+        uint32_t wd[kVSlX][4];
 #pragma unroll
         for (int uu = 0; uu < 8; uu += 2) {
           float r[2][4];
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
             const int p = gq * 8 + uu + v;
-            slice4(u >= 0 ? func_val<true>(S, xy, zs, u, p) : make_float2(0.f, 0.f), sa, r[v]);
+            slice_n<kVSlX>(u >= 0 ? func_val<true>(S, xy, zs, u, p) : make_float2(0.f, 0.f), sa, r[v]);
           }
 #pragma unroll
-          for (int k = 0; k < 4; ++k) wd[k][uu >> 1] = pack_bf16(r[0][k], r[1][k]);
+          for (int k = 0; k < kVSlX; ++k) wd[k][uu >> 1] = pack_bf16(r[0][k], r[1][k]);
         }
-        uint8_t *blk = base + (size_t)(q * 8 + (gq >> 1)) * np * 128;
+        uint8_t *blk = base + (size_t)(q * 8 + (gq >> 1)) * np * 32 * kVSlX;
         const int off = kstep_off(a, (gq & 1) * 8);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kVSlX; ++k)
           *(uint4 *)(blk + k * np * 32 + off) = make_uint4(wd[k][0], wd[k][1], wd[k][2], wd[k][3]);
       }
       __syncthreads();
@@ -816,10 +825,10 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
 // ---- potential matrix ---------------------------------------------------------
 // V_loc = dV X^T diag(v) X per group of tiles as D = W X^T on the tensor cores,
 // W = (v X)^T (rows = union functions i, the accumulator lanes) and X^T
-// (columns j), both in four exact integer slices.  The slice products of order
-// 0 go into one FP32 accumulator (exact: integers below 2^24 on the 2^0 grid),
-// those of orders 1..3 into a second (about 2^-8 of the first, so its FP32
-// rounding is 2^-32 of V's scale).  Two accumulator pairs (4 x 128 TMEM
+// (columns j), in kVSlW and kVSlX exact integer slices.  The slice products of
+// order 0 go into one FP32 accumulator (exact: integers below 2^24 on the 2^0
+// grid), those of orders 1 .. kVOrd into a second (about 2^-8 of the first, so
+// its FP32 rounding is 2^-32 of V's scale).  Two accumulator pairs (4 x 128 TMEM
 // columns) alternate between groups, so the read-out of one group overlaps the
 // MMAs of the next.  Warp roles: 0-15 read the accumulators (lane quarter
 // w % 4, every fourth 8-column chunk by w / 4) and add into V by fixed-point
@@ -827,10 +836,10 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
 // slices and the group buffers (v at the points, union entries); 25 issues the
 // MMAs.  Lane i takes the columns j <= i and adds into V[mu_j][mu_i]
 // (mu_j <= mu_i), so a warp's reductions run along a row of V.
-constexpr int kVStages = 6;
-constexpr int kVA = 4 * kSlot;   // W slices (128 rows)
-constexpr int kVB = 4 * kSlot;   // X^T slices (np rows each, packed as stored)
+constexpr int kVA = kVSlW * kSlot;  // W slices (128 rows)
+constexpr int kVB = kVSlX * kSlot;  // X^T slices (np rows each, packed as stored)
 constexpr int kVStage = kVA + kVB;
+constexpr int kVStages = (200 * 1024) / kVStage;  // operand ring in 200 KB of shared memory
 constexpr int kVEpiW = 16, kVBldW = 8;  // warps: 0-15 read-out, 16-23 build W
 constexpr int kVEpi = kVEpiW * 32, kVBld = kVBldW * 32;
 constexpr int kVThreads = kVEpi + kVBld + 64;
@@ -918,12 +927,12 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
         mbar_expect_tx(&R.tile_full[mb], nt * kTP * 8 + np * 16);
         bulk_g2s(tb, A.vt + (size_t)t0 * kTP, nt * kTP * 8, &R.tile_full[mb]);
         bulk_g2s(tb + kVGmax * kTP * 8, A.vent + e0, np * 16, &R.tile_full[mb]);
-        const uint8_t *src = A.xv + (size_t)A.vg_xoff[g] * 1024;
+        const uint8_t *src = A.xv + (size_t)A.vg_xoff[g] * 256;
         for (int kk = 0; kk < nt * kSteps; ++kk, ++fill) {
           const int s = fill % kVStages, use = fill / kVStages;
           if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
-          mbar_expect_tx(&R.tma_full[s], np * 128);
-          bulk_g2s_stream(dsm + s * kVStage + kVA, src + (size_t)kk * np * 128, np * 128,
+          mbar_expect_tx(&R.tma_full[s], np * 32 * kVSlX);
+          bulk_g2s_stream(dsm + s * kVStage + kVA, src + (size_t)kk * np * 32 * kVSlX, np * 32 * kVSlX,
                           &R.tma_full[s]);
         }
       }
@@ -955,23 +964,19 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = su32(dsm + s * kVStage), b0 = a0 + kVA;
-          uint64_t W[4], X[4];
+          uint64_t W[kVSlW], X[kVSlX];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            W[k] = smem_desc(a0 + k * kSlot);
-            X[k] = smem_desc(b0 + k * np * 32);
-          }
+          for (int k = 0; k < kVSlW; ++k) W[k] = smem_desc(a0 + k * kSlot);
+#pragma unroll
+          for (int k = 0; k < kVSlX; ++k) X[k] = smem_desc(b0 + k * np * 32);
           const uint32_t acc = kk > 0;
-          mma_bf16(d0, W[0], X[0], idesc, acc);   // order 0
-          mma_bf16(d1, W[0], X[1], idesc, acc);   // orders 1..3
-          mma_bf16(d1, W[1], X[0], idesc, 1u);
-          mma_bf16(d1, W[0], X[2], idesc, 1u);
-          mma_bf16(d1, W[1], X[1], idesc, 1u);
-          mma_bf16(d1, W[2], X[0], idesc, 1u);
-          mma_bf16(d1, W[0], X[3], idesc, 1u);
-          mma_bf16(d1, W[1], X[2], idesc, 1u);
-          mma_bf16(d1, W[2], X[1], idesc, 1u);
-          mma_bf16(d1, W[3], X[0], idesc, 1u);
+          mma_bf16(d0, W[0], X[0], idesc, acc);  // order 0
+#pragma unroll
+          for (int o = 1; o <= kVOrd; ++o)        // orders 1 .. kVOrd (W0 X1 first)
+#pragma unroll
+            for (int q = 0; q <= o; ++q)
+              if (q < kVSlW && o - q < kVSlX)
+                mma_bf16(d1, W[q], X[o - q], idesc, (o == 1 && q == 0) ? acc : 1u);
           mma_commit(&R.empty[s]);
         }
         if (ok) mma_commit(&R.acc_full[buf]);
@@ -1011,38 +1016,39 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
         uint8_t *Ast = dsm + s * kVStage;
         const uint8_t *Bst = Ast + kVA;
         const int off = kstep_off(b, h * 8);
-        uint4 o[4];
+        uint4 o[kVSlW];
         if (b < nu) {
-          uint4 xs[4];
+          uint4 xs[kVSlX];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) xs[k] = *(const uint4 *)(Bst + k * np * 32 + off);
-          uint32_t ww[4][4];
+          for (int k = 0; k < kVSlX; ++k) xs[k] = *(const uint4 *)(Bst + k * np * 32 + off);
+          uint32_t ww[kVSlW][4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {  // point pairs (2u, 2u + 1)
-            const uint32_t s0 = (&xs[0].x)[u], s1 = (&xs[1].x)[u], s2 = (&xs[2].x)[u],
-                           s3 = (&xs[3].x)[u];
             float r[2][4];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-              const float i0 = __uint_as_float(v ? (s0 & 0xFFFF0000u) : (s0 << 16));
-              const float i1 = __uint_as_float(v ? (s1 & 0xFFFF0000u) : (s1 << 16));
-              const float i2 = __uint_as_float(v ? (s2 & 0xFFFF0000u) : (s2 << 16));
-              const float i3 = __uint_as_float(v ? (s3 & 0xFFFF0000u) : (s3 << 16));
-              // the sliced x 2^(8 - e_b), exact: i0 + i1 + i2 on the 2^-16 grid below 2^8
-              const float2 x = make_float2((i0 + i1) + i2, i3);
-              slice4(df_mul_raw(x, vt[kk * kKs + h * 8 + 2 * u + v]), sb, r[v]);
+              // the sliced x 2^(8 - e_b), exact: the slices' sum on the 2^-16 grid
+              // below 2^8 (a fourth slice on the 2^-24 grid goes in the low part)
+              float i[4];
+#pragma unroll
+              for (int k = 0; k < kVSlX; ++k) {
+                const uint32_t sk = (&xs[k].x)[u];
+                i[k] = __uint_as_float(v ? (sk & 0xFFFF0000u) : (sk << 16));
+              }
+              const float2 x = make_float2((i[0] + i[1]) + (kVSlX > 2 ? i[2] : 0.f), kVSlX > 3 ? i[3] : 0.f);
+              slice_n<kVSlW>(df_mul_raw(x, vt[kk * kKs + h * 8 + 2 * u + v]), sb, r[v]);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) ww[k][u] = pack_bf16(r[0][k], r[1][k]);
+            for (int k = 0; k < kVSlW; ++k) ww[k][u] = pack_bf16(r[0][k], r[1][k]);
           }
 #pragma unroll
-          for (int k = 0; k < 4; ++k) o[k] = make_uint4(ww[k][0], ww[k][1], ww[k][2], ww[k][3]);
+          for (int k = 0; k < kVSlW; ++k) o[k] = make_uint4(ww[k][0], ww[k][1], ww[k][2], ww[k][3]);
         } else {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) o[k] = make_uint4(0u, 0u, 0u, 0u);
+          for (int k = 0; k < kVSlW; ++k) o[k] = make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) *(uint4 *)(Ast + k * kSlot + off) = o[k];
+        for (int k = 0; k < kVSlW; ++k) *(uint4 *)(Ast + k * kSlot + off) = o[k];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&R.bld_full[s]);
       }
@@ -1244,6 +1250,7 @@ cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s) {
 int tc_rho_steps(int nu) { return rsteps(nu); }
 int tc_v_entries(int nu) { return vpad(nu); }
 int tc_group_max() { return kVGmax; }
+int tc_v_slices() { return kVSlX; }
 
 cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
   oslice_kernel<<<h->N, 256, 0, s>>>(reinterpret_cast<const float2 *>(h->d_O), h->M, h->N, h->N + (h->N & 1), h->d_Osl, h->d_oscale,
