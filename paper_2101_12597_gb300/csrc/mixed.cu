@@ -165,14 +165,15 @@ __device__ __forceinline__ void bulk_g2s_stream(void *dst, const void *src, uint
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld_issue(uint32_t t, uint32_t (&r)[32]) {
+// 8 columns of four accumulators st columns apart, lane quarter of the warp
+__device__ __forceinline__ void tmem_ld_issue(uint32_t t, uint32_t (&r)[32], uint32_t st) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(t), "r"(t + kNmax), "r"(t + 2 * kNmax), "r"(t + 3 * kNmax));
+      : "r"(t), "r"(t + st), "r"(t + 2 * st), "r"(t + 3 * st));
 }
 // wait for the issued loads; the registers pass through the statement, so no
 // use of them can be scheduled before it
@@ -677,7 +678,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
         const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
         if (j > 0 && !mbar_wait(&R.acc_empty, (j - 1) & 1, stop)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t idesc = idesc_bf16(nmpad);
+        const uint32_t idesc = idesc_bf16(nmpad), idesc2 = idesc_bf16(2 * nmpad);
         for (int kk = 0; kk < nk; ++kk, ++fill) {
           const int s = fill % kRhoStages, use = fill / kRhoStages;
           if (!mbar_wait(&R.tma_full[s], use & 1, stop) || !mbar_wait(&R.bld_full[s], use & 1, stop)) {
@@ -690,17 +691,17 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) I[k] = smem_desc(a0 + k * kSlot);
 #pragma unroll
-          for (int k = 0; k < 3; ++k) K[k] = smem_desc(b0 + k * kSlot);
-          const uint32_t acc = kk > 0;
-          mma_bf16(tmem, I[0], K[0], idesc, acc);                  // order 0
-          mma_bf16(tmem + kNmax, I[0], K[1], idesc, acc);          // order 1
-          mma_bf16(tmem + kNmax, I[1], K[0], idesc, 1u);
-          mma_bf16(tmem + 2 * kNmax, I[0], K[2], idesc, acc);      // order 2
-          mma_bf16(tmem + 2 * kNmax, I[1], K[1], idesc, 1u);
-          mma_bf16(tmem + 2 * kNmax, I[2], K[0], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, I[1], K[2], idesc, acc);      // order 3
-          mma_bf16(tmem + 3 * kNmax, I[2], K[1], idesc, 1u);
-          mma_bf16(tmem + 3 * kNmax, I[3], K[0], idesc, 1u);
+          for (int k = 0; k < 3; ++k) K[k] = smem_desc(b0 + k * nmpad * 32);
+          // acc_o (order o) at column o * nmpad; I_i x [K_j; K_j+1] (N = 2 nmpad, the
+          // slices lie nmpad rows apart) adds I_i K_j to acc_(i+j) and I_i K_j+1 to
+          // acc_(i+j+1): the nine slice products of orders <= 3 in six MMAs
+          const uint32_t acc = kk > 0, ac = (uint32_t)nmpad;
+          mma_bf16(tmem, I[0], K[0], idesc2, acc);          // acc0 = I0 K0, acc1 = I0 K1
+          mma_bf16(tmem + 2 * ac, I[0], K[2], idesc, acc);  // acc2 = I0 K2
+          mma_bf16(tmem + ac, I[1], K[0], idesc2, 1u);      // acc1 += I1 K0, acc2 += I1 K1
+          mma_bf16(tmem + 3 * ac, I[1], K[2], idesc, acc);  // acc3 = I1 K2
+          mma_bf16(tmem + 2 * ac, I[2], K[0], idesc2, 1u);  // acc2 += I2 K0, acc3 += I2 K1
+          mma_bf16(tmem + 3 * ac, I[3], K[0], idesc, 1u);   // acc3 += I3 K0
           mma_commit(&R.empty[s]);  // the stage is free once these MMAs complete
         }
         if (ok) mma_commit(&R.acc_full);
@@ -746,8 +747,8 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
           v2.x = __byte_perm(w2[0], w2[1], 0x5410); v2.y = __byte_perm(w2[2], w2[3], 0x5410);
           v2.z = __byte_perm(w2[4], w2[5], 0x5410); v2.w = __byte_perm(w2[6], w2[7], 0x5410);
           *(uint4 *)(B + off) = v0;
-          *(uint4 *)(B + kSlot + off) = v1;
-          *(uint4 *)(B + 2 * kSlot + off) = v2;
+          *(uint4 *)(B + nmpad * 32 + off) = v1;
+          *(uint4 *)(B + 2 * nmpad * 32 + off) = v2;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&R.bld_full[s]);
@@ -778,14 +779,14 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       const int cb = part * (nmpad / kRhoParts), ce = cb + nmpad / kRhoParts;
       const float *f = fs + mc * kNmax;
       uint32_t ra[32], rb[32];
-      tmem_ld_issue(tmem + lanebits + cb, ra);
+      tmem_ld_issue(tmem + lanebits + cb, ra, nmpad);
       for (int c0 = cb; c0 < ce; c0 += 16) {
         tmem_ld_wait(ra);
-        if (c0 + 8 < ce) tmem_ld_issue(tmem + lanebits + c0 + 8, rb);
+        if (c0 + 8 < ce) tmem_ld_issue(tmem + lanebits + c0 + 8, rb, nmpad);
         rsum = rho_sum8(ra, f + c0, rsum);
         if (c0 + 8 >= ce) break;
         tmem_ld_wait(rb);
-        if (c0 + 16 < ce) tmem_ld_issue(tmem + lanebits + c0 + 16, ra);
+        if (c0 + 16 < ce) tmem_ld_issue(tmem + lanebits + c0 + 16, ra, nmpad);
         rsum = rho_sum8(rb, f + c0 + 8, rsum);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
