@@ -33,8 +33,9 @@
 
 namespace etdm {
 
-constexpr int BM = 8, BN = 16, BK = 32, NT = 256;
-constexpr int NG = 128;  // threads of one K group: a tile's K chunks alternate between two groups
+constexpr int BM = 8, BN = 16, BK = 16, NT = 512;
+constexpr int NG = 128;       // threads of one K group (one output each)
+constexpr int KG = NT / NG;   // K groups: a tile's K chunks go round-robin to the groups
 static_assert(kTaylor >= 8 && kTaylor <= 11, "Paterson-Stockmeyer blocks assume degree 8..11");
 // slots of the forward series workspace Qk
 enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc0, kBc1, kBc2, kBs0, kBs1, kBs2, kTc, kTs, kQslots };
@@ -104,25 +105,25 @@ __device__ __forceinline__ R opB(const Prod &P, int k, int j) {
   return (P.f64 & 2) ? Num<R>::ld_f64(P.B, e) : Num<R>::ld(P.B, e);
 }
 
-// One output tile (BM x BN) of a phase.  The block's two groups of 128 threads
-// (one output each) take alternate K chunks and add their partial sums at the
-// end, which doubles the work in flight per SM.  Each group double-buffers its
-// chunks in shared memory: the next chunk's global loads are in flight in
-// registers while the current one is multiplied.  Not inlined: every phase of
+// One output tile (BM x BN) of a phase.  The block's KG groups of 128 threads
+// (one output each) take the K chunks round-robin and add their partial sums
+// at the end, which divides the dependent multiply-add chain of a tile by KG.
+// Each group double-buffers its chunks in shared memory: the next chunk's
+// global loads are in flight in registers while the current one is multiplied.  Not inlined: every phase of
 // a chain runs the same copy of this code, which stays in the instruction
 // cache (inlined at each of the chain's call sites, the first chunk of every
 // phase waited on instruction fetch for several microseconds).
 constexpr int kLa = BM * BK / NG, kLb = BK * BN / NG;  // elements per thread per chunk
 template <class R>
 __device__ __noinline__ void phase_tile(const Phase &ph, int tile, R (*As)[2][BM][BK + 1],
-                           R (*Bs)[2][BK][BN + 1], R *part) {
+                           R (*Bs)[2][BK][BN + 1], R (*part)[NG]) {
   using X = Num<R>;
   const int tilesN = (ph.n + BN - 1) / BN;
   const int r0 = (tile / tilesN) * BM, c0 = (tile % tilesN) * BN;
   const int tid = threadIdx.x % NG, grp = threadIdx.x / NG;
   const int ty = tid / BN, tx = tid % BN;
   const int i = r0 + ty, j = c0 + tx;
-  const int nch = (ph.k + BK - 1) / BK, nit = (nch + 1) / 2;
+  const int nch = (ph.k + BK - 1) / BK, nit = nch > grp ? (nch - grp + KG - 1) / KG : 0;
   R acc = X::zero();
   for (int q = 0; q < ph.np; ++q) {
     const Prod P = ph.p[q];
@@ -159,28 +160,35 @@ __device__ __noinline__ void phase_tile(const Phase &ph, int tile, R (*As)[2][BM
 #pragma unroll
       for (int u = 0; u < kLb; ++u) Bs[grp][buf][bk[u]][bj[u]] = rb[u];
     };
-    load(grp);
-    store(0);
+    if (nit > 0) {
+      load(grp);
+      store(0);
+    }
     __syncthreads();
     Mac<R> mac;
-    for (int it = 0; it < nit; ++it) {  // this group's chunks grp, grp + 2, ...
+    const int nitm = (nch + KG - 1) / KG;  // iterations of the busiest group (block-uniform)
+    for (int it = 0; it < nitm; ++it) {  // this group's chunks grp, grp + KG, ...
       const int buf = it & 1;
       const bool more = it + 1 < nit;
-      if (more) load(2 * (it + 1) + grp);
+      if (more) load(KG * (it + 1) + grp);
+      if (it < nit) {
 #pragma unroll
-      for (int kk = 0; kk < BK; kk += 4) {
+        for (int kk = 0; kk < BK; kk += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) mac.step(u, As[grp][buf][ty][kk + u], Bs[grp][buf][kk + u][tx]);
+          for (int u = 0; u < 4; ++u) mac.step(u, As[grp][buf][ty][kk + u], Bs[grp][buf][kk + u][tx]);
+        }
       }
       if (more) store(buf ^ 1);
       __syncthreads();
     }
     acc = X::fma(P.alpha, mac.total(), acc);
   }
-  if (grp == 1) part[tid] = acc;
+  if (grp > 0) part[grp - 1][tid] = acc;
   __syncthreads();
   if (grp == 0 && i < ph.m && j < ph.n) {
-    R v = X::add(acc, part[tid]);
+    R v = acc;
+#pragma unroll
+    for (int q = 0; q < KG - 1; ++q) v = X::add(v, part[q][tid]);
     if (ph.C1) v = X::fma(ph.beta1, X::ld(ph.C1, (long)i * ph.ldc1 + j), v);
     if (ph.C2) v = X::fma(ph.beta2, X::ld(ph.C2, (long)i * ph.ldc2 + j), v);
     if (i == j) v = X::add(v, X::from(ph.diag));
@@ -199,9 +207,9 @@ __device__ __forceinline__ int phase_tiles(const Phase &ph) {
 // Run independent phases over one shared tile index space (no barrier).
 template <class R>
 __device__ void run_phases(const Phase *ph, int count) {
-  __shared__ R As[2][2][BM][BK + 1];
-  __shared__ R Bs[2][2][BK][BN + 1];
-  __shared__ R part[NG];
+  __shared__ R As[KG][2][BM][BK + 1];
+  __shared__ R Bs[KG][2][BK][BN + 1];
+  __shared__ R part[KG - 1][NG];
   int total = 0;
   for (int c = 0; c < count; ++c) total += phase_tiles(ph[c]);
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
