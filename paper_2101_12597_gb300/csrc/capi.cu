@@ -559,9 +559,11 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
     throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};
   const long nvar = (long)N * V;
+  // L-BFGS over every SM: its FP64 work per SM stays small (FP64 is the scarce
+  // pipe), at most two elements per thread up to water32
   h->lb_blocks = (int)std::min<long>((long)h->num_sms * std::min(bpl, 2),
-                                     std::max<long>(1, (nvar + 1023) / 1024));
-  h->d_red = dalloc<double>(h, 2 * std::max(h->coop_blocks, h->lb_blocks) + 8);
+                                     std::max<long>(h->num_sms, (nvar + 511) / 512));
+  h->d_red = dalloc<double>(h, 4 * std::max(h->coop_blocks, h->lb_blocks) + 8);
 
   // L-BFGS memory and line-search buffers
   h->d_s = dalloc<double>(h, (long)h->lbfgs_m * nvar);

@@ -604,11 +604,12 @@ __device__ __forceinline__ double precond_elem(const double *eps, int N, int V, 
 }
 
 // Dot product of the whole grid: every block gets the same value.  The block
-// partials alternate between two halves of red[], so one barrier suffices: a
-// block can only write a half again after the next call's barrier, which every
-// block reaches after reading this call's sums.
+// partials alternate between two halves of red[] (2 * gridDim entries each,
+// room for two sums), so one barrier suffices: a block can only write a half
+// again after the next call's barrier, which every block reaches after reading
+// this call's sums.
 __device__ double grid_dot_finish(LbfgsArgs &a, double part, int *parity, bool *ok) {
-  double *red = a.red + (*parity) * gridDim.x;
+  double *red = a.red + (*parity) * 2 * gridDim.x;
   *parity ^= 1;
   part = block_sum(part);
   if (threadIdx.x == 0) red[blockIdx.x] = part;
@@ -679,6 +680,137 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
   if (!grid_barrier(a.bar, a.flags)) return;
   if (gtid == 0) {
     st[0] = count; st[1] = head; st[2] = 1.0; st[3] = beta;
+  }
+}
+
+// The same two-loop when every thread of the grid owns at most kLbPer
+// elements (every system up to water32, spread over all SMs: the FP64 work
+// per SM stays small) and m <= kLbMaxM: the elements of a, g, the previous
+// point and the stored pairs are loaded once into registers, all loads in
+// flight together, so the loops wait on no global memory, and the two dot
+// products of a new pair share one grid barrier.
+constexpr int kLbPer = 2, kLbMaxM = 6;
+
+// Two dot products of the whole grid in one barrier (every block gets both).
+__device__ double2 grid_dot2_finish(LbfgsArgs &a, double p1, double p2, int *parity, bool *ok) {
+  double *red = a.red + (*parity) * 2 * gridDim.x;
+  *parity ^= 1;
+  p1 = block_sum(p1);
+  p2 = block_sum(p2);
+  if (threadIdx.x == 0) { red[blockIdx.x] = p1; red[gridDim.x + blockIdx.x] = p2; }
+  if (!grid_barrier(a.bar, a.flags)) { *ok = false; return make_double2(0.0, 0.0); }
+  const double r1 = block_sum_of(red, gridDim.x);
+  return make_double2(r1, block_sum_of(red + gridDim.x, gridDim.x));
+}
+
+__global__ void __launch_bounds__(256) lbfgs_reg_kernel(LbfgsArgs a) {
+  const long n = a.n;
+  const int m = a.m;
+  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long gstride = (long)gridDim.x * blockDim.x;
+  const double *st = a.state;
+  int count = (int)st[0], head = (int)st[1];
+  const bool have_prev = st[2] != 0.0;
+  double beta = st[3];
+  double rho[kLbMaxM], alph[kLbMaxM];
+  for (int k = 0; k < m; ++k) rho[k] = st[4 + k];
+  long e[kLbPer];
+  bool in[kLbPer];
+  double q[kLbPer], sv[kLbMaxM][kLbPer], yv[kLbMaxM][kLbPer];
+#pragma unroll
+  for (int u = 0; u < kLbPer; ++u) {
+    e[u] = gtid + u * gstride;
+    in[u] = e[u] < n;
+    q[u] = in[u] ? a.g[e[u]] : 0.0;
+#pragma unroll
+    for (int k = 0; k < kLbMaxM; ++k) {
+      const bool use = in[u] && k < m;
+      sv[k][u] = use ? a.s[(long)k * n + e[u]] : 0.0;
+      yv[k][u] = use ? a.y[(long)k * n + e[u]] : 0.0;
+    }
+  }
+  bool ok = true;
+  int par = 0, new_slot = -1;
+  if (have_prev) {  // candidate pair into slot `head`
+    double ns[kLbPer], ny[kLbPer], p1 = 0.0, p2 = 0.0;
+#pragma unroll
+    for (int u = 0; u < kLbPer; ++u) {
+      ns[u] = in[u] ? a.a[e[u]] - a.aprev[e[u]] : 0.0;
+      ny[u] = in[u] ? q[u] - a.gprev[e[u]] : 0.0;
+      p1 += ns[u] * ny[u];
+      p2 += ny[u] * ny[u];
+    }
+    const double2 d = grid_dot2_finish(a, p1, p2, &par, &ok);
+    if (!ok) return;
+    if (d.x > 1e-30) {
+#pragma unroll
+      for (int k = 0; k < kLbMaxM; ++k)
+        if (k == head) {
+#pragma unroll
+          for (int u = 0; u < kLbPer; ++u) {
+            sv[k][u] = ns[u];
+            yv[k][u] = ny[u];
+            if (in[u]) { a.s[(long)k * n + e[u]] = ns[u]; a.y[(long)k * n + e[u]] = ny[u]; }
+          }
+        }
+      beta = d.y / d.x;
+      rho[head] = 1.0 / d.x;
+      new_slot = head;
+      head = (head + 1) % m;
+      count = count < m ? count + 1 : m;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kLbPer; ++u)
+    if (in[u]) { a.aprev[e[u]] = a.a[e[u]]; a.gprev[e[u]] = q[u]; }
+  for (int c = 0; c < count; ++c) {  // first loop: newest to oldest
+    const int sl = (head - 1 - c + 2 * m) % m;
+    double part = 0.0;
+#pragma unroll
+    for (int k = 0; k < kLbMaxM; ++k)
+      if (k == sl) {
+#pragma unroll
+        for (int u = 0; u < kLbPer; ++u) part += sv[k][u] * q[u];
+      }
+    const double al = rho[sl] * grid_dot_finish(a, part, &par, &ok);
+    if (!ok) return;
+    alph[c] = al;
+#pragma unroll
+    for (int k = 0; k < kLbMaxM; ++k)
+      if (k == sl) {
+#pragma unroll
+        for (int u = 0; u < kLbPer; ++u) q[u] -= al * yv[k][u];
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < kLbPer; ++u)  // r = H0 q
+    if (in[u]) q[u] *= precond_elem(a.eps, a.N, a.V, e[u], a.gamma, beta);
+  for (int c = count - 1; c >= 0; --c) {  // second loop: oldest to newest
+    const int sl = (head - 1 - c + 2 * m) % m;
+    double part = 0.0;
+#pragma unroll
+    for (int k = 0; k < kLbMaxM; ++k)
+      if (k == sl) {
+#pragma unroll
+        for (int u = 0; u < kLbPer; ++u) part += yv[k][u] * q[u];
+      }
+    const double coef = alph[c] - rho[sl] * grid_dot_finish(a, part, &par, &ok);
+    if (!ok) return;
+#pragma unroll
+    for (int k = 0; k < kLbMaxM; ++k)
+      if (k == sl) {
+#pragma unroll
+        for (int u = 0; u < kLbPer; ++u) q[u] += coef * sv[k][u];
+      }
+  }
+#pragma unroll
+  for (int u = 0; u < kLbPer; ++u)
+    if (in[u]) a.p[e[u]] = -q[u];
+  if (!grid_barrier(a.bar, a.flags)) return;  // every block has read the state
+  if (gtid == 0) {
+    double *stw = a.state;
+    stw[0] = count; stw[1] = head; stw[2] = 1.0; stw[3] = beta;
+    if (new_slot >= 0) stw[4 + new_slot] = rho[new_slot];
   }
 }
 
@@ -877,6 +1009,9 @@ cudaError_t launch_lbfgs(etdm_handle *h, const double *a, const double *g, doubl
   d.state = h->d_lbstate; d.eps = h->d_eps; d.gamma = h->gamma;
   d.red = h->d_red; d.bar = h->d_bar; d.flags = h->d_flags;
   void *args[] = {&d};
+  if (d.n <= (long)h->lb_blocks * 256 * kLbPer && d.m <= kLbMaxM)  // registers hold every element
+    return cudaLaunchCooperativeKernel((void *)lbfgs_reg_kernel, dim3(h->lb_blocks), dim3(256), args,
+                                       0, s);
   return cudaLaunchCooperativeKernel((void *)lbfgs_kernel, dim3(h->lb_blocks), dim3(256), args,
                                      0, s);
 }

@@ -114,7 +114,7 @@ struct LbfgsArgs {
   double *state;         // [0]=count [1]=head [2]=have_prev [3]=beta [4..4+m)=rho [..+m)=alpha
   const double *eps;     // [M]
   double gamma;
-  double *red;           // [2*gridDim]
+  double *red;           // [4*gridDim]: two halves of two sums each
   unsigned *bar;
   int *flags;
 };
