@@ -924,13 +924,22 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_VTOT: src = h->d_vtot; break;
       case ETDM_ARR_H: case ETDM_ARR_UOCC:
         src = which == ETDM_ARR_H ? h->d_H : h->d_Uocc;
-        if (h->pairs_last) {  // the mixed path's dense chains left float pairs there
+        if (h->pairs_last) {  // the mixed path's dense chains hold float pairs
+          // (its H is V, kept as the upper triangle of the fixed-point read-out)
+          const bool hv = which == ETDM_ARR_H;
           double *tmp = nullptr;
           CUDA_TRY(cudaMalloc(&tmp, want));
-          cudaError_t e = launch_from_pairs(static_cast<const float2 *>(src), tmp, want / 8, 0);
+          cudaError_t e = launch_from_pairs(hv ? h->d_Vfin : static_cast<const float2 *>(src), tmp,
+                                            want / 8, 0);
           if (e == cudaSuccess) e = cudaMemcpy(dst, tmp, want, cudaMemcpyDeviceToHost);
           cudaFree(tmp);
           CUDA_TRY(e);
+          if (hv) {
+            double *d = static_cast<double *>(dst);
+            const int64_t M = h->M;
+            for (int64_t i = 1; i < M; ++i)
+              for (int64_t c = 0; c < i; ++c) d[i * M + c] = d[c * M + i];
+          }
           return ETDM_OK;
         }
         break;

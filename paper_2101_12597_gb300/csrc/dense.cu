@@ -38,7 +38,7 @@ constexpr int NG = 128;       // threads of one K group (one output each)
 constexpr int KG = NT / NG;   // K groups: a tile's K chunks go round-robin to the groups
 static_assert(kTaylor >= 8 && kTaylor <= 11, "Paterson-Stockmeyer blocks assume degree 8..11");
 // slots of the forward series workspace Qk
-enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc0, kBc1, kBc2, kBs0, kBs1, kBs2, kTc, kTs, kQslots };
+enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc2, kBs2, kTc, kTs, kQslots };
 // slots of the reverse workspace Wr
 enum { kQ4b = 0, kTcb, kTsb, kBc2b, kBs2b, kQ1bB, kQ2bB, kQ3b, kQ2b, kQ1bt, kQ1b, kWslots };
 
@@ -96,7 +96,8 @@ template <> struct Mac<float2> {
 
 template <class R>
 __device__ __forceinline__ R opA(const Prod &P, int i, int k) {
-  const long e = P.ta ? (long)k * P.lda + i : (long)i * P.lda + k;
+  long e = P.ta ? (long)k * P.lda + i : (long)i * P.lda + k;
+  if (P.f64 & 4) e = i <= k ? (long)i * P.lda + k : (long)k * P.lda + i;  // symmetric, upper stored
   return (P.f64 & 1) ? Num<R>::ld_f64(P.A, e) : Num<R>::ld(P.A, e);
 }
 template <class R>
@@ -116,7 +117,7 @@ __device__ __forceinline__ R opB(const Prod &P, int k, int j) {
 constexpr int kLa = BM * BK / NG, kLb = BK * BN / NG;  // elements per thread per chunk
 template <class R>
 __device__ __noinline__ void phase_tile(const Phase &ph, int tile, R (*As)[2][BM][BK + 1],
-                           R (*Bs)[2][BK][BN + 1], R (*part)[NG]) {
+                           R (*Bs)[2][BK][BN + 1], R (*part)[NG], double *sq) {
   using X = Num<R>;
   const int tilesN = (ph.n + BN - 1) / BN;
   const int r0 = (tile / tilesN) * BM, c0 = (tile % tilesN) * BN;
@@ -189,12 +190,15 @@ __device__ __noinline__ void phase_tile(const Phase &ph, int tile, R (*As)[2][BM
     R v = acc;
 #pragma unroll
     for (int q = 0; q < KG - 1; ++q) v = X::add(v, part[q][tid]);
-    if (ph.C1) v = X::fma(ph.beta1, X::ld(ph.C1, (long)i * ph.ldc1 + j), v);
-    if (ph.C2) v = X::fma(ph.beta2, X::ld(ph.C2, (long)i * ph.ldc2 + j), v);
+    for (int q = 0; q < ph.nc; ++q) v = X::fma(ph.beta[q], X::ld(ph.C[q], (long)i * ph.ldc[q] + j), v);
     if (i == j) v = X::add(v, X::from(ph.diag));
     const long o = (long)i * ph.ldo + j;
     if (ph.out64) static_cast<double *>(ph.out)[o] = X::dbl(v);
     else X::st(ph.out, o, v);
+    if (sq) {  // running sum of squares of this thread's outputs
+      const double d = X::dbl(v);
+      *sq += d * d;
+    }
   }
   __syncthreads();
 }
@@ -204,9 +208,10 @@ __device__ __forceinline__ int phase_tiles(const Phase &ph) {
   return ((ph.m + BM - 1) / BM) * ((ph.n + BN - 1) / BN);
 }
 
-// Run independent phases over one shared tile index space (no barrier).
+// Run independent phases over one shared tile index space (no barrier); with
+// sq, each thread adds the squares of the outputs it wrote to *sq.
 template <class R>
-__device__ void run_phases(const Phase *ph, int count) {
+__device__ void run_phases(const Phase *ph, int count, double *sq = nullptr) {
   __shared__ R As[KG][2][BM][BK + 1];
   __shared__ R Bs[KG][2][BK][BN + 1];
   __shared__ R part[KG - 1][NG];
@@ -215,7 +220,7 @@ __device__ void run_phases(const Phase *ph, int count) {
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int c = 0, base = 0;
     while (t - base >= phase_tiles(ph[c])) { base += phase_tiles(ph[c]); ++c; }
-    phase_tile<R>(ph[c], t - base, As, Bs, part);
+    phase_tile<R>(ph[c], t - base, As, Bs, part, sq);
   }
 }
 
@@ -229,10 +234,13 @@ __device__ __forceinline__ Prod mk(const void *A, int lda, int ta, const void *B
 __device__ __forceinline__ Phase mkphase(int m, int n, int k, void *out, int ldo) {
   Phase ph;
   ph.m = m; ph.n = n; ph.k = k; ph.np = 0;
-  ph.C1 = nullptr; ph.ldc1 = 0; ph.beta1 = 0.0;
-  ph.C2 = nullptr; ph.ldc2 = 0; ph.beta2 = 0.0;
+  ph.nc = 0;
   ph.diag = 0.0; ph.out = out; ph.ldo = ldo; ph.out64 = 0;
   return ph;
+}
+
+__device__ __forceinline__ void addc(Phase &ph, const void *c, int ld, double beta) {
+  ph.C[ph.nc] = c; ph.ldc[ph.nc] = ld; ph.beta[ph.nc] = beta; ++ph.nc;
 }
 
 #define BARRIER_OR_RETURN()                      \
@@ -254,25 +262,18 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
   // A_ov as R: the float-pair engine converts the FP64 input once, in the first phase
   const void *const Ar = X::kPair ? (const void *)a.Af : (const void *)a.A;
 
-  {  // P = A_ov A_ov^T (reads the FP64 A)
+  {  // P = A_ov A_ov^T (reads the FP64 A); each block sums the squares of its outputs
     if (X::kPair)
       for (long e = gtid; e < (long)N * V; e += gstride) X::st(a.Af, e, X::ld_f64(a.A, e));
     Phase ph = mkphase(N, N, V, a.P, N);
     ph.np = 1; ph.p[0] = mk(a.A, V, 0, a.A, V, 1, 1.0); ph.p[0].f64 = 3;
-    run_phases<R>(&ph, 1);
+    double sq = 0.0;
+    run_phases<R>(&ph, 1, &sq);
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) a.red[blockIdx.x] = sq;
   }
   BARRIER_OR_RETURN();
-  {
-    double s = 0.0;
-    for (long e = gtid; e < NN; e += gstride) {
-      const double p = X::dbl(X::ld(a.P, e));
-      s += p * p;
-    }
-    s = block_sum(s);
-    if (threadIdx.x == 0) a.red[blockIdx.x] = s;
-  }
-  BARRIER_OR_RETURN();
-  {
+  {  // j from |P|_F (every block sums the partials in the same order)
     const double t = block_sum_of(a.red, gridDim.x);
     double nrm = sqrt(t);
     int j = 0;
@@ -293,57 +294,73 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
   if (gtid == 0) { a.flags[FLAG_J] = J; a.scal[0] = sc; }
   double *const Qs = a.Qk;
   auto slot = [&](int k) { return Qs + (long)k * NN; };
+  // Q = sc P is kept for the reverse pass; the products below use P with the
+  // scale in their coefficients
   for (long e = gtid; e < NN; e += gstride) X::st(slot(kQ1), e, X::scale2(X::ld(a.P, e), sc));
-  BARRIER_OR_RETURN();
-  {  // Q^2
+  {  // Q^2 = sc^2 P P
     Phase ph = mkphase(N, N, N, slot(kQ2), N);
-    ph.np = 1; ph.p[0] = mk(slot(kQ1), N, 0, slot(kQ1), N, 0, 1.0);
+    ph.np = 1; ph.p[0] = mk(a.P, N, 0, a.P, N, 0, sc * sc);
     run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
-  {  // Q^3 = Q Q^2, Q^4 = Q^2 Q^2
+  {  // Q^3 = sc P Q^2, Q^4 = Q^2 Q^2
     Phase ph[2];
     ph[0] = mkphase(N, N, N, slot(kQ3), N);
-    ph[0].np = 1; ph[0].p[0] = mk(slot(kQ1), N, 0, slot(kQ2), N, 0, 1.0);
+    ph[0].np = 1; ph[0].p[0] = mk(a.P, N, 0, slot(kQ2), N, 0, sc);
     ph[1] = mkphase(N, N, N, slot(kQ4), N);
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
     run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
-  for (long e = gtid; e < NN; e += gstride) {  // blocks B_i = sum_r c_{4i+r} Q^r
+  // Paterson-Stockmeyer blocks B_i = sum_r c_{4i+r} Q^r (r < 4) enter the
+  // products below as epilogue terms; B_2 is also stored for the reverse pass
+  auto cf = [&](const double *c, int k) { return k <= kTaylor ? c[k] : 0.0; };
+  for (long e = gtid; e < NN; e += gstride) {
     const int i = (int)(e / N), c = (int)(e % N);
     const R q[4] = {X::from(i == c ? 1.0 : 0.0), X::ld(slot(kQ1), e), X::ld(slot(kQ2), e),
                     X::ld(slot(kQ3), e)};
-    for (int b = 0; b < 3; ++b) {
-      R bc = X::zero(), bs = X::zero();
-      for (int r = 0; r < 4; ++r) {
-        const int k = 4 * b + r;
-        if (k <= kTaylor) { bc = X::fma(a.ck[k], q[r], bc); bs = X::fma(a.sk[k], q[r], bs); }
-      }
-      X::st(slot(kBc0 + b), e, bc);
-      X::st(slot(kBs0 + b), e, bs);
+    R bc = X::zero(), bs = X::zero();
+    for (int r = 0; r < 4; ++r) {
+      bc = X::fma(cf(a.ck, 8 + r), q[r], bc);
+      bs = X::fma(cf(a.sk, 8 + r), q[r], bs);
     }
+    X::st(slot(kBc2), e, bc);
+    X::st(slot(kBs2), e, bs);
   }
-  BARRIER_OR_RETURN();
-  {  // T = B_1 + Q^4 B_2 for both series
+  {  // T = B_1 + Q^4 B_2 = B_1 + c_8 Q^4 + c_9 sc Q^4 P + c_10 Q^4 Q^2 (+ c_11 Q^4 Q^3)
     Phase ph[2];
-    ph[0] = mkphase(N, N, N, slot(kTc), N);
-    ph[0].np = 1; ph[0].p[0] = mk(slot(kQ4), N, 0, slot(kBc2), N, 0, 1.0);
-    ph[0].C1 = slot(kBc1); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
-    ph[1] = mkphase(N, N, N, slot(kTs), N);
-    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, slot(kBs2), N, 0, 1.0);
-    ph[1].C1 = slot(kBs1); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    const double *co[2] = {a.ck, a.sk};
+    double *const out[2] = {slot(kTc), slot(kTs)};
+    for (int w = 0; w < 2; ++w) {
+      const double *c = co[w];
+      ph[w] = mkphase(N, N, N, out[w], N);
+      ph[w].np = 0;
+      ph[w].p[ph[w].np++] = mk(slot(kQ4), N, 0, a.P, N, 0, cf(c, 9) * sc);
+      ph[w].p[ph[w].np++] = mk(slot(kQ4), N, 0, slot(kQ2), N, 0, cf(c, 10));
+      ph[w].p[ph[w].np++] = mk(slot(kQ4), N, 0, slot(kQ3), N, 0, cf(c, 11));
+      addc(ph[w], a.P, N, cf(c, 5) * sc);
+      addc(ph[w], slot(kQ2), N, cf(c, 6));
+      addc(ph[w], slot(kQ3), N, cf(c, 7));
+      addc(ph[w], slot(kQ4), N, cf(c, 8));
+      ph[w].diag = cf(c, 4);
+    }
     run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // k = cos sqrt(Q) - 1 = B_0 + Q^4 T_c, s = sin sqrt(Q) / sqrt(Q) = B_0 + Q^4 T_s
     Phase ph[2];
-    ph[0] = mkphase(N, N, N, a.Kt, N);
-    ph[0].np = 1; ph[0].p[0] = mk(slot(kQ4), N, 0, slot(kTc), N, 0, 1.0);
-    ph[0].C1 = slot(kBc0); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
-    ph[1] = mkphase(N, N, N, a.St, N);
-    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, slot(kTs), N, 0, 1.0);
-    ph[1].C1 = slot(kBs0); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    const double *co[2] = {a.ck, a.sk};
+    double *const out[2] = {a.Kt, a.St};
+    const double *tt[2] = {slot(kTc), slot(kTs)};
+    for (int w = 0; w < 2; ++w) {
+      const double *c = co[w];
+      ph[w] = mkphase(N, N, N, out[w], N);
+      ph[w].np = 1; ph[w].p[0] = mk(slot(kQ4), N, 0, tt[w], N, 0, 1.0);
+      addc(ph[w], a.P, N, cf(c, 1) * sc);
+      addc(ph[w], slot(kQ2), N, cf(c, 2));
+      addc(ph[w], slot(kQ3), N, cf(c, 3));
+      ph[w].diag = cf(c, 0);
+    }
     run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
@@ -352,10 +369,10 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     Phase ph[2];
     ph[0] = mkphase(N, N, N, a.Kt + (long)(t + 1) * NN, N);
     ph[0].np = 1; ph[0].p[0] = mk(Kc, N, 0, Kc, N, 0, 2.0);
-    ph[0].C1 = Kc; ph[0].ldc1 = N; ph[0].beta1 = 4.0;
+    addc(ph[0], Kc, N, 4.0);
     ph[1] = mkphase(N, N, N, a.St + (long)(t + 1) * NN, N);
     ph[1].np = 1; ph[1].p[0] = mk(Sc, N, 0, Kc, N, 0, 1.0);
-    ph[1].C1 = Sc; ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    addc(ph[1], Sc, N, 1.0);
     run_phases<R>(ph, 2);
     BARRIER_OR_RETURN();
   }
@@ -402,57 +419,63 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
   const bool mixed = a.Vacc != nullptr;
   const long MN = (long)M * N;
   const void *const Ar = X::kPair ? (const void *)a.Af : (const void *)a.A;  // set by the forward
-  {
+  if (mixed) {
+    // Tr(D T) = 2 sum O o (T O) (the kinetic energy is exact: O as computed,
+    // only the grid energy saw Oq); Gbar = dE/dO = 4 V O + 4 T O with V read
+    // from its upper triangle; the first-order correction of the density's O
+    // quantization, sum (4 V O) o (O - Oq) = sum Gbar o dO - 4 sum (T O) o dO
+    double s = 0.0, c = 0.0;
+    for (long e = gtid; e < MN; e += gstride) {
+      const double to = X::dbl(X::ld(a.TO, e));
+      s += 2.0 * X::dbl(X::ld(a.O, e)) * to;
+      c += to * a.dO[e];
+    }
+    s = block_sum(s);
+    c = block_sum(c);
+    if (threadIdx.x == 0) { a.red[blockIdx.x] = s; a.red[gridDim.x + blockIdx.x] = -4.0 * c; }
+    Phase ph = mkphase(M, N, M, a.Gbar, N);
+    ph.np = 1; ph.p[0] = mk(a.Vacc, M, 0, a.O, N, 0, 4.0); ph.p[0].f64 = 4;  // A symmetric (upper)
+    addc(ph, a.TO, N, 4.0);
+    run_phases<R>(&ph, 1);
+    BARRIER_OR_RETURN();
+    double c2 = 0.0;
+    for (long e = gtid; e < MN; e += gstride) c2 += X::dbl(X::ld(a.Gbar, e)) * a.dO[e];
+    c2 = block_sum(c2);
+    if (threadIdx.x == 0) a.red[2 * gridDim.x + blockIdx.x] = c2;
+    if (want_grad) {
+      Phase pu = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
+      pu.np = 1; pu.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
+      run_phases<R>(&pu, 1);
+    }
+    BARRIER_OR_RETURN();
+  } else {
     double s = 0.0;
-    if (mixed) {  // Tr(D T) = 2 sum O o (T O); H <- V (symmetric, from the upper triangle)
-      for (long e = gtid; e < MN; e += gstride)
-        s += 2.0 * X::dbl(X::ld(a.O, e)) * X::dbl(X::ld(a.TO, e));
+    for (long e = gtid; e < MM; e += gstride) s += X::dbl(X::ld(a.D, e)) * X::dbl(X::ld(a.T, e));
+    if (want_grad) {  // the grid pass accumulated the upper triangle of H
       for (long e = gtid; e < MM; e += gstride) {
         int i = (int)(e / M), c = (int)(e % M);
-        X::st(a.H, e, X::ld(a.Vacc, i <= c ? e : (long)c * M + i));
-      }
-    } else {
-      for (long e = gtid; e < MM; e += gstride) s += X::dbl(X::ld(a.D, e)) * X::dbl(X::ld(a.T, e));
-      if (want_grad) {  // the grid pass accumulated the upper triangle of H
-        for (long e = gtid; e < MM; e += gstride) {
-          int i = (int)(e / M), c = (int)(e % M);
-          if (i > c) X::st(a.H, e, X::ld(a.H, (long)c * M + i));
-        }
+        if (i > c) X::st(a.H, e, X::ld(a.H, (long)c * M + i));
       }
     }
     s = block_sum(s);
     if (threadIdx.x == 0) a.red[blockIdx.x] = s;
-  }
-  BARRIER_OR_RETURN();
-  if (mixed) {
-    // dE_pot/dO = 4 V O into Ubar (scratch until Ubar is formed); the kinetic
-    // energy is exact (O as computed), only the grid energy saw Oq
-    Phase ph = mkphase(M, N, M, a.Ubar, N);
-    ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    run_phases<R>(&ph, 1);
     BARRIER_OR_RETURN();
-    // Gbar = dE/dO = 4 T O + 4 V O; first-order correction of the density's O
-    // quantization, sum (4 V O) o (O - Oq)
-    double c = 0.0;
-    for (long e = gtid; e < MN; e += gstride) {
-      const R u = X::ld(a.Ubar, e);
-      X::st(a.Gbar, e, X::fma(4.0, X::ld(a.TO, e), u));
-      c += X::dbl(u) * a.dO[e];
+    if (want_grad) {
+      Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
+      ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
+      run_phases<R>(&ph, 1);
+      BARRIER_OR_RETURN();
+      Phase pu = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
+      pu.np = 1; pu.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
+      run_phases<R>(&pu, 1);
+      BARRIER_OR_RETURN();
     }
-    c = block_sum(c);
-    if (threadIdx.x == 0) a.red[gridDim.x + blockIdx.x] = c;
-    BARRIER_OR_RETURN();
-  } else if (want_grad) {
-    Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
-    ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-    run_phases<R>(&ph, 1);
-    BARRIER_OR_RETURN();
   }
   if (blockIdx.x == 0) {  // energy terms: tree sums over the block partials, all threads of block 0
     double kin = 0.0, corr = 0.0, t3[3] = {0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
       kin += a.red[b];
-      if (mixed) corr += a.red[gridDim.x + b];
+      if (mixed) corr += a.red[gridDim.x + b] + a.red[2 * gridDim.x + b];
     }
     for (int b = threadIdx.x; b < a.n_gridpart; b += blockDim.x)
       for (int q = 0; q < 3; ++q) t3[q] += a.gridpart[3 * b + q];
@@ -467,12 +490,6 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     }
   }
   if (!want_grad) return;
-  {
-    Phase ph = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
-    ph.np = 1; ph.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
-    run_phases<R>(&ph, 1);
-  }
-  BARRIER_OR_RETURN();
   const int J = a.flags[FLAG_J];
   const double sc = a.scal[0];
   const double *Ubv = a.Ubar + NN;  // rows N..M-1 (V x N)
@@ -494,13 +511,13 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     Phase ph[2];
     ph[0] = mkphase(N, N, N, sbo, N);
     ph[0].np = 1; ph[0].p[0] = mk(sb, N, 0, Kc, N, 0, 1.0);
-    ph[0].C1 = sb; ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    addc(ph[0], sb, N, 1.0);
     ph[1] = mkphase(N, N, N, kbo, N);
     ph[1].np = 3;
     ph[1].p[0] = mk(kb, N, 0, Kc, N, 0, 2.0);
     ph[1].p[1] = mk(Kc, N, 0, kb, N, 0, 2.0);
     ph[1].p[2] = mk(Sc, N, 0, sb, N, 0, 1.0);
-    ph[1].C1 = kb; ph[1].ldc1 = N; ph[1].beta1 = 4.0;
+    addc(ph[1], kb, N, 4.0);
     run_phases<R>(ph, 2);
     BARRIER_OR_RETURN();
     kb = kbo; sb = sbo; pp = 1 - pp;
@@ -529,7 +546,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[0].np = 2;
     ph[0].p[0] = mk(wr(kTcb), N, 0, slot(kBc2), N, 0, 1.0);
     ph[0].p[1] = mk(wr(kTsb), N, 0, slot(kBs2), N, 0, 1.0);
-    ph[0].C1 = wr(kQ4b); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    addc(ph[0], wr(kQ4b), N, 1.0);
     ph[1] = mkphase(N, N, N, wr(kBc2b), N);  // B_c2 bar = Q^4 T_c bar
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, wr(kTcb), N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kBs2b), N);  // B_s2 bar = Q^4 T_s bar
@@ -559,10 +576,10 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[0].p[0] = mk(wr(kQ4b), N, 0, slot(kQ2), N, 0, 1.0);
     ph[0].p[1] = mk(slot(kQ2), N, 0, wr(kQ4b), N, 0, 1.0);
     ph[0].p[2] = mk(slot(kQ1), N, 0, wr(kQ3b), N, 0, 1.0);
-    ph[0].C1 = wr(kQ2bB); ph[0].ldc1 = N; ph[0].beta1 = 1.0;
+    addc(ph[0], wr(kQ2bB), N, 1.0);
     ph[1] = mkphase(N, N, N, wr(kQ1bt), N);  // Qbar_t = Q1bar_B + Q3bar Q^2
     ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 1.0);
-    ph[1].C1 = wr(kQ1bB); ph[1].ldc1 = N; ph[1].beta1 = 1.0;
+    addc(ph[1], wr(kQ1bB), N, 1.0);
     run_phases<R>(ph, 2);
   }
   BARRIER_OR_RETURN();
@@ -571,22 +588,16 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph.np = 2;
     ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
     ph.p[1] = mk(slot(kQ1), N, 0, wr(kQ2b), N, 0, 1.0);
-    ph.C1 = wr(kQ1bt); ph.ldc1 = N; ph.beta1 = 1.0;
+    addc(ph, wr(kQ1bt), N, 1.0);
     run_phases<R>(&ph, 1);
   }
   BARRIER_OR_RETURN();
-  {  // Q = sc P: Pbar + Pbar^T = sc (Qbar + Qbar^T)
-    const double *Qb = wr(kQ1b);
-    for (long e = gtid; e < NN; e += gstride) {
-      int i = (int)(e / N), c = (int)(e % N);
-      X::st(a.Psym, e, X::scale2(X::add(X::ld(Qb, e), X::ld(Qb, (long)c * N + i)), sc));
-    }
-  }
-  BARRIER_OR_RETURN();
-  {
-    Phase ph = mkphase(N, V, N, a.g, V);  // g = Abar + (Pbar + Pbar^T) A, written as FP64
-    ph.np = 1; ph.p[0] = mk(a.Psym, N, 0, Ar, V, 0, 1.0);
-    ph.C1 = a.Abar; ph.ldc1 = V; ph.beta1 = 1.0;
+  {  // Q = sc P: g = Abar + (Pbar + Pbar^T) A = Abar + sc Qbar A + sc Qbar^T A, written as FP64
+    Phase ph = mkphase(N, V, N, a.g, V);
+    ph.np = 2;
+    ph.p[0] = mk(wr(kQ1b), N, 0, Ar, V, 0, sc);
+    ph.p[1] = mk(wr(kQ1b), N, 1, Ar, V, 0, sc);
+    addc(ph, a.Abar, V, 1.0);
     ph.out64 = 1;
     run_phases<R>(&ph, 1);
   }

@@ -45,7 +45,8 @@ struct Tables {
 
 // One dense product term for the cooperative dense kernels.  The matrices hold
 // the kernel's element type (FP64, or float pairs in the mixed path's chains);
-// f64 marks operands held as FP64 whatever the element type (bit 0: A, bit 1: B).
+// f64 marks operands held as FP64 whatever the element type (bit 0: A, bit 1: B)
+// and a symmetric A read from its upper triangle (bit 2).
 struct Prod {
   const void *A;
   const void *B;
@@ -55,14 +56,14 @@ struct Prod {
   int f64;
 };
 
-// out[i][j] = sum_p alpha_p op(A_p) op(B_p) + beta1 C1 + beta2 C2 + diag * I
+// out[i][j] = sum_p alpha_p op(A_p) op(B_p) + sum_q beta_q C_q + diag * I
 // (out written as FP64 when out64 is set, else in the element type)
 struct Phase {
   int m, n, k;
   int np;
   Prod p[3];
-  const void *C1; int ldc1; double beta1;
-  const void *C2; int ldc2; double beta2;
+  int nc;                  // terms C_q added in the epilogue (q < nc <= 4)
+  const void *C[4]; int ldc[4]; double beta[4];
   double diag;
   void *out; int ldo;
   int out64;

@@ -78,6 +78,15 @@ def test_mixed_energy_gradient_parity(which, cases):
         assert dg <= G_TOL
         rho = s.get_array("rho").reshape(tuple(o.n))
         assert np.abs(rho - ex["rho"]).max() < 1e-5 * ex["rho"].max()
+        # accessors of the float-pair dense chain: H is the grid part V (rebuilt
+        # symmetric from its upper triangle), U_occ has orthonormal columns
+        M, N = o.M, o.N
+        H = s.get_array("H").reshape(M, M)
+        Vref = ex["H"] - s.get_array("T").reshape(M, M)
+        assert np.array_equal(H, H.T)
+        assert np.abs(H - Vref).max() < 1e-5 * np.abs(Vref).max()
+        U = s.get_array("Uocc").reshape(M, N)
+        assert np.abs(U.T @ U - np.eye(N)).max() < 1e-11
 
 
 def test_mixed_energy_only_call(cases):
