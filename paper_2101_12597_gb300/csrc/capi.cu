@@ -559,10 +559,12 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
     throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};
   const long nvar = (long)N * V;
-  // L-BFGS over every SM: its FP64 work per SM stays small (FP64 is the scarce
+  // L-BFGS: one block for small n (the grid barrier is then a block barrier);
+  // else every SM, so the FP64 work per SM stays small (FP64 is the scarce
   // pipe), at most two elements per thread up to water32
-  h->lb_blocks = (int)std::min<long>((long)h->num_sms * std::min(bpl, 2),
-                                     std::max<long>(h->num_sms, (nvar + 511) / 512));
+  h->lb_blocks = nvar <= 512 ? 1
+                             : (int)std::min<long>((long)h->num_sms * std::min(bpl, 2),
+                                                   std::max<long>(h->num_sms, (nvar + 511) / 512));
   h->d_red = dalloc<double>(h, 4 * std::max(h->coop_blocks, h->lb_blocks) + 8);
 
   // L-BFGS memory and line-search buffers
@@ -901,6 +903,8 @@ int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
     case ETDM_ARR_TILE_PTR_TC: return h->d_tile_ptr_tc ? ((int64_t)h->n_tiles_tc + 1) * 4 : 0;
     case ETDM_ARR_TILE_KEYS_TC: return h->d_keys_tc ? (int64_t)h->n_entries_tc * 4 : 0;
     case ETDM_ARR_TILE_NU_TC: return h->d_nu_tc ? (int64_t)h->n_tiles_tc * 4 : 0;
+    case ETDM_ARR_VGROUP_T0: return h->d_vg_t0 ? ((int64_t)h->n_vg + 1) * 4 : 0;
+    case ETDM_ARR_VGROUP_NU: return h->d_vg_nu ? (int64_t)h->n_vg * 4 : 0;
     default: return -1;
   }
 }
@@ -952,6 +956,8 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_TILE_PTR_TC: src = h->d_tile_ptr_tc; break;
       case ETDM_ARR_TILE_KEYS_TC: src = h->d_keys_tc; break;
       case ETDM_ARR_TILE_NU_TC: src = h->d_nu_tc; break;
+      case ETDM_ARR_VGROUP_T0: src = h->d_vg_t0; break;
+      case ETDM_ARR_VGROUP_NU: src = h->d_vg_nu; break;
     }
     if (want > 0) CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
   } catch (const Fail &f) {

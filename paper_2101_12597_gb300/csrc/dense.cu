@@ -210,17 +210,25 @@ __device__ __forceinline__ int phase_tiles(const Phase &ph) {
 
 // Run independent phases over one shared tile index space (no barrier); with
 // sq, each thread adds the squares of the outputs it wrote to *sq.
+// The phase descriptors are copied once into shared memory: every thread holds
+// its own copy in its stack frame, and reading that local memory in each tile's
+// prologue and epilogue missed L1 (512 threads x 2 KB per SM).
 template <class R>
 __device__ void run_phases(const Phase *ph, int count, double *sq = nullptr) {
   __shared__ R As[KG][2][BM][BK + 1];
   __shared__ R Bs[KG][2][BK][BN + 1];
   __shared__ R part[KG - 1][NG];
+  __shared__ Phase sph[3];
+  __syncthreads();  // the previous user of sph is done
+  if (threadIdx.x == 0)
+    for (int c = 0; c < count; ++c) sph[c] = ph[c];
+  __syncthreads();
   int total = 0;
-  for (int c = 0; c < count; ++c) total += phase_tiles(ph[c]);
+  for (int c = 0; c < count; ++c) total += phase_tiles(sph[c]);
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int c = 0, base = 0;
-    while (t - base >= phase_tiles(ph[c])) { base += phase_tiles(ph[c]); ++c; }
-    phase_tile<R>(ph[c], t - base, As, Bs, part, sq);
+    while (t - base >= phase_tiles(sph[c])) { base += phase_tiles(sph[c]); ++c; }
+    phase_tile<R>(sph[c], t - base, As, Bs, part, sq);
   }
 }
 
