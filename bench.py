@@ -318,9 +318,12 @@ def run_ours(args):
         # the stage is timed inside a long step: the sustained BF16 figure
         pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
         nu = solver.get_array("tile_nu_tc").astype(np.int64)  # functions per 128-point tile
-        if dom == "vmat":  # 10 slice products per 16-point K step, N = list padded to 16
-            npad = np.maximum(16, ((nu + 15) // 16) * 16)
-            executed = float((10 * 2.0 * 128 * npad * 128).sum())
+        if dom == "vmat":  # 8 slice products per 16-point K step of a V group (runs of
+            # consecutive tiles), M = 128 rows, N = the group's union list padded to 16
+            t0 = solver.get_array("vgroup_t0").astype(np.int64)
+            gnu = solver.get_array("vgroup_nu").astype(np.int64)
+            npad = np.maximum(16, ((gnu + 15) // 16) * 16)
+            executed = float((8 * 2.0 * 128 * npad * 128 * np.diff(t0)).sum())
         else:  # 9 slice products per 16-function K step, N = occupied orbitals padded to 32
             nocc = dims["N"]
             nmpad = sum(min(128, nocc - m0) for m0 in range(0, nocc, 128))

@@ -166,7 +166,12 @@ enum {
   ETDM_ARR_TILE_KEYS_TC = 16, /* mixed precision: 4x4x8-tile list keys (i32) */
   ETDM_ARR_TILE_NU_TC = 17,   /* mixed precision: functions per 4x4x8 tile, periodic
                                  images merged (i32, n_tiles entries) */
-  ETDM_NARR = 17
+  ETDM_ARR_VGROUP_T0 = 18,    /* mixed precision: first 4x4x8 tile of each group of
+                                 consecutive tiles the V pass accumulates in one pass
+                                 (i32, groups + 1 entries, the last = n_tiles) */
+  ETDM_ARR_VGROUP_NU = 19,    /* mixed precision: functions in each V group's union
+                                 list (i32, one per group) */
+  ETDM_NARR = 20              /* number of array ids */
 };
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);
 int etdm_get_array(etdm_handle *h, int32_t which, void *host_dst,

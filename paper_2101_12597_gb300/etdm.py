@@ -26,7 +26,8 @@ ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "tile_keys": (11, np.int32), "eps": (12, np.float64),
           "eterms": (13, np.float64), "beta": (14, np.float64),
           "tile_ptr_tc": (15, np.int32), "tile_keys_tc": (16, np.int32),
-          "tile_nu_tc": (17, np.int32)}
+          "tile_nu_tc": (17, np.int32), "vgroup_t0": (18, np.int32),
+          "vgroup_nu": (19, np.int32)}
 DIM_NAMES = ["M", "N", "V", "G", "n_tiles", "entries", "max_list", "tx", "ty",
              "tz", "sum_npt2", "precision"]
 

@@ -55,11 +55,25 @@ def test_tc_truncation_lists_bit_exact(which, cases):
     tile = (4, 4, 8)
     nt = o.n_tiles(tile)
     assert len(ptr) == nt + 1 and len(nu) == nt
+    funcs = []
     for t in range(nt):
         ref = o.tile_list(tile, t)
         np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], ref)
         # functions per tile: periodic images of one function merged
-        assert nu[t] == len(np.unique(np.asarray(ref, dtype=np.int64) // 512))
+        funcs.append(np.unique(np.asarray(ref, dtype=np.int64) // 512))
+        assert nu[t] == len(funcs[t])
+    # V groups: greedy runs of at most two consecutive tiles whose union has at
+    # most 128 functions; a tile starts a new group only when joining it to the
+    # previous one-tile group would exceed 128
+    t0 = s.get_array("vgroup_t0")
+    gnu = s.get_array("vgroup_nu")
+    assert t0[0] == 0 and t0[-1] == nt and len(gnu) == len(t0) - 1
+    assert np.all(np.diff(t0) >= 1) and np.all(np.diff(t0) <= 2)
+    for g in range(len(gnu)):
+        un = np.unique(np.concatenate(funcs[t0[g]:t0[g + 1]]))
+        assert gnu[g] == len(un) <= 128
+        if t0[g + 1] - t0[g] == 1 and t0[g + 1] < nt:
+            assert len(np.union1d(funcs[t0[g]], funcs[t0[g + 1]])) > 128
 
 
 @pytest.mark.parametrize("which", ["tiny", "small", "ragged", "odd"])
