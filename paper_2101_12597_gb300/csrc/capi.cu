@@ -479,7 +479,10 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_vt = dalloc<float2>(h, (size_t)T * 128);
     CUDA_TRY(launch_operand_build(h, s));
     h->d_Osl = dalloc<uint2>(h, (long)M * (h->N + (h->N & 1)));  // rows padded to even length
-    h->d_oscale = dalloc<float>(h, h->N);
+    const long ch = tc_max_list();  // orbitals per chunk of the density pass
+    const long nsc = (h->N + ch - 1) / ch * ch;  // whole chunks, zero beyond N
+    h->d_oscale = dalloc<float>(h, nsc);
+    CUDA_TRY(cudaMemset(h->d_oscale, 0, nsc * sizeof(float)));
     h->d_dO = dalloc<double>(h, (long)M * h->N);
     h->d_TO = dalloc<double>(h, (long)M * h->N);
     h->d_Vfix = dalloc<unsigned long long>(h, (long)M * M + 1);

@@ -303,7 +303,7 @@ struct TcArgs {
   float4 *vent;                 // per padded union entry: (mu bits, 2^(e_a - 8), bound, 0)
   signed char *rowexp;          // [G] density row exponents e_p
   const uint2 *Osl;             // [M][NoccP] BF16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
-  const float *oscale;          // [N] 2^g_m
+  const float *oscale;          // [chunks * 128] 2^g_m, zero beyond N
   int Nocc, NoccP;              // occupied orbitals; O-slice row length (even)
   double *rho;                  // [G]
   float2 *rhof;                 // [G] rho as float pairs
@@ -571,24 +571,31 @@ struct RhoBars {
   uint64_t acc_full, acc_empty, part_full, part_empty, fin;
   uint32_t tbase;
   int stop;
-  float part[kRhoParts - 1][kTP];
+  float2 part[kRhoParts - 1][kTP];
 };
 
-// phi = (acc0 + acc1 + acc2 + acc3) 2^g for 8 columns; adds phi^2
-__device__ __forceinline__ float rho_sum8(const uint32_t (&r)[32], const float *f, float rsum) {
+// phi = (acc0 + acc1 + acc2 + acc3) 2^g for 8 columns; their squares summed in
+// FP32, the 8-term sum added to the float pair rs by TwoSum: the rounding of
+// the running sum (the error that grows with the number of orbitals) stays
+// at about 2^-44 of its value
+__device__ __forceinline__ float2 rho_sum8(const uint32_t (&r)[32], const float *f, float2 rs) {
+  float s8 = 0.f;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     float y = __uint_as_float(r[c]) +
               (__uint_as_float(r[8 + c]) + (__uint_as_float(r[16 + c]) + __uint_as_float(r[24 + c])));
     y *= f[c];
-    rsum = fmaf(y, y, rsum);
+    s8 = fmaf(y, y, s8);
   }
-  return rsum;
+  const float2 sm = pair::two_sum(rs.x, s8);
+  return make_float2(sm.x, __fadd_rn(rs.y, sm.y));
 }
 
 __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
   extern __shared__ __align__(1024) uint8_t dsm[];
-  float *fs = (float *)(dsm + kRhoStages * kRhoStage);  // column scales 2^g_m, zero-padded
+  // column scales 2^g_m, zero-padded: staged in shared memory for one chunk of
+  // orbitals, read from the (zero-padded) global array for several
+  float *fs = (float *)(dsm + kRhoStages * kRhoStage);
   __shared__ RhoBars R;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int nmc = (A.Nocc + kNmax - 1) / kNmax;
@@ -607,7 +614,9 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) tmem_alloc(&R.tbase);
-  for (int m = tid; m < nmc * kNmax; m += blockDim.x) fs[m] = m < A.Nocc ? A.oscale[m] : 0.f;
+  if (nmc == 1)
+    for (int m = tid; m < kNmax; m += blockDim.x) fs[m] = m < A.Nocc ? A.oscale[m] : 0.f;
+  const float *fsrc = nmc == 1 ? fs : A.oscale;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -762,7 +771,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     const int quad = w & 3, part = w >> 2;
     const int pe = quad * 32 + lane;
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
-    float rsum = 0.f;
+    float2 rsum = make_float2(0.f, 0.f);
     int ntile = 0;  // tiles finished (part buffer hand-overs)
     bool ok = true;
     for (int j = 0; j < njobs && ok; ++j) {
@@ -777,7 +786,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       // this warp's column part in chunks of 8, the next chunk's loads in
       // flight while the current one is summed
       const int cb = part * (nmpad / kRhoParts), ce = cb + nmpad / kRhoParts;
-      const float *f = fs + mc * kNmax;
+      const float *f = fsrc + mc * kNmax;
       uint32_t ra[32], rb[32];
       tmem_ld_issue(tmem + lanebits + cb, ra, nmpad);
       for (int c0 = cb; c0 < ce; c0 += 16) {
@@ -798,9 +807,9 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
           mbar_arrive(&R.part_full);
         } else {
           ok = mbar_wait(&R.part_full, ntile & 1, stop);
-          float2 r = make_float2(rsum, 0.f);
+          float2 r = rsum;
 #pragma unroll
-          for (int q = 0; q < kRhoParts - 1; ++q) r = df_add(r, make_float2(R.part[q][pe], 0.f));
+          for (int q = 0; q < kRhoParts - 1; ++q) r = df_add(r, R.part[q][pe]);
           mbar_arrive(&R.part_empty);
           if (ok && gp >= 0) {
             A.rho[gp] = ldexp((double)r.x + (double)r.y, 2 * ep - 31);
@@ -810,7 +819,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
             A.rhof[gp] = make_float2(r.x * sc, r.y * sc);
           }
         }
-        rsum = 0.f;
+        rsum = make_float2(0.f, 0.f);
         ++ntile;
         ok = __all_sync(0xffffffffu, ok);
       }
@@ -1261,7 +1270,7 @@ cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
 
 cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
   const int nmc = (h->N + kNmax - 1) / kNmax;
-  const size_t sm = (size_t)kRhoStages * kRhoStage + (size_t)nmc * kNmax * sizeof(float);
+  const size_t sm = (size_t)kRhoStages * kRhoStage + (nmc == 1 ? (size_t)kNmax * sizeof(float) : 0);
   cudaError_t e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;

@@ -146,3 +146,40 @@ def test_water32_mixed_full_size(cases):
     for t in list(range(0, nt, nt // 9)) + [nt - 1]:
         np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list((4, 4, 8), t))
     s.close()
+
+
+def test_water576_mixed_vs_fp64_path():
+    """The largest workload (1728 atoms, M=4608, N=2304, 192^3 grid): too big for
+    the CPU oracle's energy, so the mixed path is held to the FP64 GPU path (itself
+    pinned to the oracle on every smaller case) at the same bars, plus the
+    properties that hold at any size: unitary U, and sampled 4x4x8 truncation
+    lists bit-exact against the oracle's."""
+    torch = _torch()
+    d = synth.config_water576()
+    a = torch.tensor(d["a0"], device="cuda")
+    s = _solver(d)
+    E, g = s.energy_grad(a)
+    torch.cuda.synchronize()
+    s.check()
+    E, g = float(E.item()), g.cpu().numpy()
+    U = s.get_array("Uocc").reshape(s.M, s.N)
+    assert np.abs(U.T @ U - np.eye(s.N)).max() < 1e-11
+    o = Oracle(d)
+    ptr = s.get_array("tile_ptr_tc")
+    keys = s.get_array("tile_keys_tc")
+    nt = o.n_tiles((4, 4, 8))
+    assert len(ptr) == nt + 1
+    for t in (0, nt // 3, nt - 1):
+        np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list((4, 4, 8), t))
+    s.close()
+    from paper_2101_12597_gb300.etdm import ETDM
+    f = ETDM(d, precision="fp64")
+    E64, g64 = f.energy_grad(a)
+    torch.cuda.synchronize()
+    f.check()
+    dE = abs(E - float(E64.item()))
+    dg = _grad_err(g, g64.cpu().numpy())
+    print(f"water576 mixed vs FP64 path: |dE|={dE:.3e} Ha  grad err={dg:.3e}")
+    assert dE < E_TOL
+    assert dg <= G_TOL
+    f.close()
