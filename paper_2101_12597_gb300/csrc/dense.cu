@@ -208,27 +208,155 @@ __device__ __forceinline__ int phase_tiles(const Phase &ph) {
   return ((ph.m + BM - 1) / BM) * ((ph.n + BN - 1) / BN);
 }
 
+// ---- large output tiles for large matrices ------------------------------------
+// 64 x 64 outputs per block, K chunks of 16 double-buffered, each of the 512
+// threads 4 rows x 2 columns: six shared-memory loads per eight multiply-adds
+// (the 8 x 16 tiles above load two per one, and keep every SM busy only on
+// small matrices).  A phase takes them when it has at least four per block.
+constexpr int LBM = 64, LBN = 64, LBK = 16;
+static_assert(NT == 512 && (LBM / 4) * (LBN / 2) == NT, "16 x 32 threads, 4 x 2 outputs each");
+
+template <class R> struct Mac8;
+template <> struct Mac8<double> {
+  double c[8];
+  __device__ __forceinline__ Mac8() : c{0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0} {}
+  __device__ __forceinline__ void step(int u, double a, double b) { c[u] = fma(a, b, c[u]); }
+  __device__ __forceinline__ double get(int u) const { return c[u]; }
+};
+template <> struct Mac8<float2> {
+  float h[8], l[8];
+  __device__ __forceinline__ Mac8() : h{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, l{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f} {}
+  __device__ __forceinline__ void step(int u, float2 a, float2 b) { pair::mac(h[u], l[u], a, b); }
+  __device__ __forceinline__ float2 get(int u) const { return make_float2(h[u], l[u]); }
+};
+
+__device__ __forceinline__ int big_tiles(const Phase &ph) {
+  if (ph.m <= 0 || ph.n <= 0) return 0;
+  return ((ph.m + LBM - 1) / LBM) * ((ph.n + LBN - 1) / LBN);
+}
+__device__ __forceinline__ bool use_big(const Phase &ph) { return big_tiles(ph) >= 4 * (int)gridDim.x; }
+__device__ __forceinline__ int ntiles(const Phase &ph) { return use_big(ph) ? big_tiles(ph) : phase_tiles(ph); }
+
+template <class R>
+__device__ __noinline__ void phase_tile_big(const Phase &ph, int tile, R (*As)[LBK][LBM + 1],
+                                            R (*Bs)[LBK][LBN + 1], double *sq) {
+  using X = Num<R>;
+  const int tilesN = (ph.n + LBN - 1) / LBN;
+  const int r0 = (tile / tilesN) * LBM, c0 = (tile % tilesN) * LBN;
+  const int tid = threadIdx.x, ty = tid / 32, tx = tid % 32;  // rows ty*4 + r, columns tx + 32 c
+  const int nch = (ph.k + LBK - 1) / LBK;
+  R acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = X::zero();
+  for (int q = 0; q < ph.np; ++q) {
+    const Prod P = ph.p[q];
+    if (P.alpha == 0.0) continue;
+    // load slots (two elements of A's and of B's chunk per thread), along the
+    // stored rows of each operand
+    int ai[2], ak[2], bk[2], bj[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + u * NT;
+      if (P.ta) { ak[u] = e / LBM; ai[u] = e % LBM; } else { ai[u] = e / LBK; ak[u] = e % LBK; }
+      if (P.tb) { bj[u] = e / LBK; bk[u] = e % LBK; } else { bk[u] = e / LBN; bj[u] = e % LBN; }
+    }
+    R ra[2], rb[2];
+    auto load = [&](int c) {
+      const int k0 = c * LBK;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int gi = r0 + ai[u], gk = k0 + ak[u];
+        ra[u] = (gi < ph.m && gk < ph.k) ? opA<R>(P, gi, gk) : X::zero();
+        const int hk = k0 + bk[u], gj = c0 + bj[u];
+        rb[u] = (hk < ph.k && gj < ph.n) ? opB<R>(P, hk, gj) : X::zero();
+      }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        As[buf][ak[u]][ai[u]] = ra[u];
+        Bs[buf][bk[u]][bj[u]] = rb[u];
+      }
+    };
+    load(0);
+    store(0);
+    __syncthreads();
+    Mac8<R> mac;
+    for (int it = 0; it < nch; ++it) {
+      const int buf = it & 1;
+      const bool more = it + 1 < nch;
+      if (more) load(it + 1);
+#pragma unroll 4
+      for (int kk = 0; kk < LBK; ++kk) {
+        R a[4], b[2];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = As[buf][kk][ty * 4 + r];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) b[c] = Bs[buf][kk][tx + 32 * c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) mac.step(r * 2 + c, a[r], b[c]);
+      }
+      if (more) store(buf ^ 1);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = X::fma(P.alpha, mac.get(u), acc[u]);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = r0 + ty * 4 + r, j = c0 + tx + 32 * c;
+      if (i < ph.m && j < ph.n) {
+        R v = acc[r * 2 + c];
+        for (int q = 0; q < ph.nc; ++q) v = X::fma(ph.beta[q], X::ld(ph.C[q], (long)i * ph.ldc[q] + j), v);
+        if (i == j) v = X::add(v, X::from(ph.diag));
+        const long o = (long)i * ph.ldo + j;
+        if (ph.out64) static_cast<double *>(ph.out)[o] = X::dbl(v);
+        else X::st(ph.out, o, v);
+        if (sq) {
+          const double d = X::dbl(v);
+          *sq += d * d;
+        }
+      }
+    }
+  __syncthreads();
+}
+
 // Run independent phases over one shared tile index space (no barrier); with
 // sq, each thread adds the squares of the outputs it wrote to *sq.
 // The phase descriptors are copied once into shared memory: every thread holds
 // its own copy in its stack frame, and reading that local memory in each tile's
-// prologue and epilogue missed L1 (512 threads x 2 KB per SM).
+// prologue and epilogue missed L1 (512 threads x 2 KB per SM).  The small and
+// the large tiles share one shared-memory buffer.
+constexpr int kSmallTileBytes = (KG * 2 * BM * (BK + 1) + KG * 2 * BK * (BN + 1) + (KG - 1) * NG) * 8;
+constexpr int kBigTileBytes = (2 * LBK * (LBM + 1) + 2 * LBK * (LBN + 1)) * 8;
+constexpr int kTileBytes = kSmallTileBytes > kBigTileBytes ? kSmallTileBytes : kBigTileBytes;
+
 template <class R>
 __device__ void run_phases(const Phase *ph, int count, double *sq = nullptr) {
-  __shared__ R As[KG][2][BM][BK + 1];
-  __shared__ R Bs[KG][2][BK][BN + 1];
-  __shared__ R part[KG - 1][NG];
+  static_assert(sizeof(R) == 8, "8-byte elements");
+  __shared__ __align__(16) unsigned char tsm[kTileBytes];
   __shared__ Phase sph[3];
   __syncthreads();  // the previous user of sph is done
   if (threadIdx.x == 0)
     for (int c = 0; c < count; ++c) sph[c] = ph[c];
   __syncthreads();
+  R *const base = reinterpret_cast<R *>(tsm);
+  auto *As = reinterpret_cast<R (*)[2][BM][BK + 1]>(base);
+  auto *Bs = reinterpret_cast<R (*)[2][BK][BN + 1]>(base + KG * 2 * BM * (BK + 1));
+  auto *part = reinterpret_cast<R (*)[NG]>(base + KG * 2 * BM * (BK + 1) + KG * 2 * BK * (BN + 1));
+  auto *Al = reinterpret_cast<R (*)[LBK][LBM + 1]>(base);
+  auto *Bl = reinterpret_cast<R (*)[LBK][LBN + 1]>(base + 2 * LBK * (LBM + 1));
   int total = 0;
-  for (int c = 0; c < count; ++c) total += phase_tiles(sph[c]);
+  for (int c = 0; c < count; ++c) total += ntiles(sph[c]);
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    int c = 0, base = 0;
-    while (t - base >= phase_tiles(sph[c])) { base += phase_tiles(sph[c]); ++c; }
-    phase_tile<R>(sph[c], t - base, As, Bs, part, sq);
+    int c = 0, base_t = 0;
+    while (t - base_t >= ntiles(sph[c])) { base_t += ntiles(sph[c]); ++c; }
+    if (use_big(sph[c])) phase_tile_big<R>(sph[c], t - base_t, Al, Bl, sq);
+    else phase_tile<R>(sph[c], t - base_t, As, Bs, part, sq);
   }
 }
 
