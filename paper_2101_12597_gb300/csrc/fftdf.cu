@@ -27,7 +27,7 @@ namespace etdm {
 
 constexpr int kDfThreads = 256;
 constexpr int kZPairs = 8;    // line pairs per block of the z passes
-constexpr int kXYLines = 16;  // lines per block of the x and y passes
+constexpr int kXYLines = 8;   // lines per block of the x and y passes (4 blocks per SM)
 
 // ---- float-pair scalars (hi, lo) and complex numbers ---------------------------
 struct dcx {
@@ -202,7 +202,7 @@ struct DfArgs {
 
 // ---- pass 1: z lines, forward, real pairs -> half spectra ----------------------
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads) zfwd_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) zfwd_kernel(DfArgs a) {
   extern __shared__ __align__(16) float4 zsm[];
   const int nz = a.nz, nzh = a.nzh;
   float4 *tw = zsm, *b0 = zsm + nz, *b1 = b0 + kZPairs * nz;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kDfThreads) zfwd_kernel(DfArgs a) {
 
 // ---- passes 2 and 4: y lines (fixed x, kz) --------------------------------------
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads) yfft_kernel(DfArgs a, int sign) {
+__global__ void __launch_bounds__(kDfThreads, 4) yfft_kernel(DfArgs a, int sign) {
   extern __shared__ __align__(16) float4 ysm[];
   const int ny = a.ny, nzh = a.nzh;
   float4 *tw = ysm, *b0 = ysm + ny, *b1 = b0 + kXYLines * ny;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kDfThreads) yfft_kernel(DfArgs a, int sign) {
 
 // ---- pass 3: x lines, forward, Poisson kernel, inverse ---------------------------
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads) xpois_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) xpois_kernel(DfArgs a) {
   extern __shared__ __align__(16) float4 xsm[];
   const int nx = a.nx, ny = a.ny, nzh = a.nzh;
   float4 *tw = xsm, *b0 = xsm + nx, *b1 = b0 + kXYLines * nx;
@@ -314,7 +314,7 @@ __device__ __forceinline__ float2 warp_fdf_sum(float2 v) {
 
 // ---- pass 5: z lines, inverse, half spectra pairs -> real potentials; potential --
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads) zinv_pot_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) zinv_pot_kernel(DfArgs a) {
   extern __shared__ __align__(16) float4 zsm[];
   const int nz = a.nz, nzh = a.nzh;
   float4 *tw = zsm, *b0 = zsm + nz, *b1 = b0 + kZPairs * nz;
