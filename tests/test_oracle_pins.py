@@ -386,6 +386,21 @@ def test_minimization_decreases_energy(small):
     assert np.abs(g).max() < 0.2 * np.abs(g0).max()
 
 
+def test_stationarity_eq15_at_convergence():
+    """At the minimum the occupied-virtual block of C^T H C vanishes (Eq. 15:
+    the gradient of the unitary-invariant functional is zero) -- the whole
+    chain (exp, density, potential, H, adjoint, preconditioned L-BFGS, line
+    search) has to be right for the minimization to land there."""
+    for d in (synth.tiny(), synth.config_small_molecule()):
+        o = Oracle(d)
+        hist, a = minimize(o, d["a0"], n_steps=300)
+        E, g, ex = o.energy_grad(a, want=True)
+        Hmo, N = ex["Hmo"], o.N
+        assert np.abs(Hmo[:N, N:]).max() < 1e-8 * np.abs(Hmo).max()
+        assert np.abs(g).max() < 1e-8
+        assert E <= hist[0][0]
+
+
 # ---- truncation lists (index work) --------------------------------------------------
 
 @pytest.mark.parametrize("tile", [(4, 4, 4), (8, 4, 4)])
