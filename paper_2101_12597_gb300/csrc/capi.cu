@@ -228,17 +228,17 @@ void inverse_sqrt(etdm_handle *h, cudaStream_t s) {
   for (int it = 0; it < 200; ++it) {
     Phase ph{};
     ph.m = M; ph.n = M; ph.k = M; ph.np = 1;
-    ph.p[0] = Prod{Zm, Y, M, M, 0, 0, -0.5};
+    ph.p[0] = Prod{Zm, Y, M, M, 0, 0, -0.5, 0};
     ph.diag = 1.5; ph.out = Tm; ph.ldo = M;
     CUDA_TRY(launch_gemm(ph, s));
     CUDA_TRY(launch_resid(Tm, sc + 1, M, s));
     Phase py{};
     py.m = M; py.n = M; py.k = M; py.np = 1;
-    py.p[0] = Prod{Y, Tm, M, M, 0, 0, 1.0};
+    py.p[0] = Prod{Y, Tm, M, M, 0, 0, 1.0, 0};
     py.out = Y2; py.ldo = M;
     CUDA_TRY(launch_gemm(py, s));
     Phase pz = py;
-    pz.p[0] = Prod{Tm, Zm, M, M, 0, 0, 1.0};
+    pz.p[0] = Prod{Tm, Zm, M, M, 0, 0, 1.0, 0};
     pz.out = Z2;
     CUDA_TRY(launch_gemm(pz, s));
     std::swap(Y, Y2);
@@ -537,10 +537,8 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   h->d_St = dalloc<double>(h, NN * (kJmax + 1));
   h->d_Gbar = dalloc<double>(h, (long)M * N);
   h->d_Ubar = dalloc<double>(h, (long)M * N);
-  for (int i = 0; i < 6; ++i) h->d_bar2[i] = dalloc<double>(h, NN);
-  h->d_Qbar = dalloc<double>(h, NN);
+  for (int i = 0; i < 4; ++i) h->d_bar2[i] = dalloc<double>(h, NN);
   h->d_Abar = dalloc<double>(h, (long)N * V);
-  h->d_Psym = dalloc<double>(h, NN);
   h->d_E = dalloc<double>(h, 2);
   h->d_eterms = dalloc<double>(h, 4);
   h->d_scal = dalloc<double>(h, 4);

@@ -1082,8 +1082,7 @@ static DenseArgs dense_args(etdm_handle *h, const double *a) {
   d.Gbar = h->d_Gbar; d.Ubar = h->d_Ubar;
   d.Kbar[0] = h->d_bar2[0]; d.Kbar[1] = h->d_bar2[1];
   d.Sbar[0] = h->d_bar2[2]; d.Sbar[1] = h->d_bar2[3];
-  d.Z[0] = h->d_bar2[4]; d.Z[1] = h->d_bar2[5];
-  d.Qbar = h->d_Qbar; d.Abar = h->d_Abar; d.Psym = h->d_Psym; d.Wr = h->d_Wr;
+  d.Abar = h->d_Abar; d.Wr = h->d_Wr;
   d.eterms = h->d_eterms;
   d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
   if (pairs) { d.Vacc = h->d_Vfin; d.dO = h->d_dO; }

@@ -88,8 +88,8 @@ struct DenseArgs {
   const void *C0;        // (R) M x M
   const void *T;         // (R) M x M
   double *Gbar, *Ubar;   // (R) M x N
-  double *Kbar[2], *Sbar[2], *Z[2];  // (R)
-  double *Qbar, *Abar, *Psym;        // (R)
+  double *Kbar[2], *Sbar[2];         // (R) cotangents of the doubling steps, ping-pong
+  double *Abar;                      // (R) N x V
   double *Wr;            // (R) [11][N*N] reverse workspace of the series
   double *g;             // N x V output, FP64 (may be null)
   double *E;             // scalar output (may be null)
@@ -195,9 +195,9 @@ struct etdm_handle {
   double *d_D = nullptr, *d_H = nullptr, *d_Uocc = nullptr, *d_O = nullptr;
   double *d_P = nullptr, *d_Qk = nullptr, *d_Kt = nullptr, *d_St = nullptr;
   double *d_Gbar = nullptr, *d_Ubar = nullptr;
-  double *d_bar2[6] = {nullptr};
+  double *d_bar2[4] = {nullptr};
   double *d_Wr = nullptr;
-  double *d_Qbar = nullptr, *d_Abar = nullptr, *d_Psym = nullptr;
+  double *d_Abar = nullptr;
   // grid
   double *d_vext = nullptr, *d_rho = nullptr, *d_vtot = nullptr;
   double2 *d_fft = nullptr;
