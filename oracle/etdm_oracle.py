@@ -34,6 +34,15 @@ setting.  Readings of passages that are garbled or silent:
 * The orbital energies in Eq. 33 are the diagonal of C0^T H C0 at A = 0 and
   the orbital-energy term enters with its absolute value so that the
   preconditioner stays positive for a non-aufbau reference.
+
+Conventions the paper does not fix, whose parity is unpinned (both sides
+implement the same choice; tests pin only the properties they must keep):
+
+* beta^(0) = 1 Ha, and the curvature threshold s.y > 1e-30 below which a pair
+  is not stored (the skip itself is pinned: the direction equals dense BFGS
+  over the stored pairs and stays a descent direction).
+* The line search's bracketing, interpolation safeguards and trial limit
+  beyond the Eq. 25-29 conditions (pinned: the accepted point satisfies them).
 """
 from __future__ import annotations
 

@@ -360,6 +360,50 @@ def test_lbfgs_two_loop_equals_dense_bfgs():
         x = x + 0.5 * p
 
 
+def test_lbfgs_skips_negative_curvature_pairs():
+    """On an indefinite quadratic, steps along negative-curvature directions give
+    s.y < 0.  BFGS keeps its inverse Hessian positive definite only with pairs of
+    positive curvature, so such a pair is not stored and beta (Eq. 34) keeps the
+    value of the last stored pair; the direction is then the dense BFGS update
+    over the stored pairs alone and remains a descent direction."""
+    rng = np.random.default_rng(3)
+    n = 8
+    Qm, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    lam = np.array([3.0, 2.0, 1.5, 1.0, 0.5, -0.5, -1.0, -2.0])
+    Amat = Qm @ np.diag(lam) @ Qm.T
+    b = rng.normal(size=n)
+    diagP = lambda beta: 1.0 / (np.linspace(1, 3, n) + 0.25 * beta)
+    lb = LBFGS(diagP, m=3, beta0=1.0)
+    x = rng.normal(size=n)
+    kept, beta, skipped = [], 1.0, 0
+    for k in range(10):
+        gr = Amat @ x - b
+        if k:
+            s, y = x - x_prev, gr - g_prev
+            assert (s @ y > 0) == (k % 3 != 0)     # the steps below set the sign
+            if s @ y > 0:
+                kept = (kept + [(s, y)])[-3:]
+                beta = (y @ y) / (s @ y)
+            else:
+                skipped += 1
+        p = lb.step(x, gr)
+        assert len(lb.s) == len(kept) and lb.beta == pytest.approx(beta, rel=1e-14)
+        H = np.diag(diagP(beta))
+        for s, y in kept:
+            r = 1.0 / (y @ s)
+            I = np.eye(n)
+            H = (I - r * np.outer(s, y)) @ H @ (I - r * np.outer(y, s)) + r * np.outer(s, s)
+        assert np.linalg.eigvalsh(0.5 * (H + H.T)).min() > 0
+        assert np.abs(p - (-H @ gr)).max() < 1e-12 * max(1, np.abs(p).max())
+        assert p @ gr < 0
+        x_prev, g_prev = x, gr
+        # every third step lies in the negative-curvature subspace, the rest in
+        # the positive one
+        sub = Qm[:, 5:] if (k + 1) % 3 == 0 else Qm[:, :5]
+        x = x + sub @ rng.normal(size=sub.shape[1]) * 0.3
+    assert skipped == 3
+
+
 def test_cubic_min_exact_on_cubic():
     f = lambda t: (t - 0.3) ** 2 * (t + 2.0)
     df = lambda t: 2 * (t - 0.3) * (t + 2.0) + (t - 0.3) ** 2
