@@ -420,6 +420,27 @@ def test_line_search_returns_wolfe_point():
     assert trials <= 20
 
 
+@pytest.mark.parametrize("E0,kappa,accept", [
+    (-1000.0, 1e-12, True),     # derivative conditions hold, Eq. 28 tolerates the noise
+    (0.0, 1e-12, False),        # eps |E0| = 0: Eq. 28 cannot absorb the noise
+    (-1000.0, 0.05e-12, False),  # phi'(1) below sigma phi'(0): Eq. 27 fails
+])
+def test_approximate_wolfe_accepts_noisy_flat_step(E0, kappa, accept):
+    """Eq. 27-28: near a minimum the energy change of a step is below the noise
+    of E while the directional derivative still says where the minimum is.  A
+    quadratic along p with a constant offset eta on every trial energy (noise)
+    fails Eq. 25 at alpha = 1; the step is accepted on the first trial exactly
+    when phi'(1) lies in [sigma phi'(0), (2 delta - 1) phi'(0)] and the offset
+    is within eps |E0|."""
+    d0, eta = -1e-12, 1e-10
+    phi = lambda t: (E0 + d0 * t + 0.5 * kappa * t * t + eta, d0 + kappa * t, t)
+    E1, d1, _ = phi(1.0)
+    assert not (E1 <= E0 + orc.C1 * d0)              # Eq. 25 fails at alpha = 1
+    assert wolfe_ok(1.0, E1, d1, E0, d0) == accept
+    alpha, _, _, _, trials = line_search(phi, E0, d0)
+    assert (alpha == 1.0 and trials == 1) == accept
+
+
 def test_minimization_decreases_energy(small):
     d, o = small
     hist, a = minimize(o, d["a0"], n_steps=8)
