@@ -253,7 +253,8 @@ void inverse_sqrt(etdm_handle *h, cudaStream_t s) {
   if (!done)
     throw Fail{ETDM_ERR_NOT_CONVERGED,
                "S^(-1/2) Newton-Schulz iteration did not converge (S ill-conditioned?)"};
-  // S^(-1/2) = Z / sqrt(c), into d_S scratch? keep S: write into Tm then permute later
+  // Z converged to (S / c)^(-1/2), so S^(-1/2) = Z / sqrt(c); the columns are
+  // put in reference order later (S stays in d_S, readable through etdm_get_array)
   CUDA_TRY(launch_scale_copy(Zm, h->d_C0, 1.0 / sqrt(c), MM, s));
 }
 
