@@ -45,9 +45,31 @@ def workload_system(name):
     import etdm_synth as synth
     return {"water32": synth.config_water32, "small": synth.config_small_molecule,
             "water576": synth.config_water576}[name]()
+
+
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 rate of a GB300 (no measured figure)
 HBM_FALLBACK_GBS = 6800.0
 BF16_FALLBACK_TFLOPS = 1900.0
+
+
+def oracle_threads():
+    """Threads the oracle's BLAS calls run on: threadpoolctl's count where it is
+    installed, else OpenBLAS's environment variables in its own order of
+    precedence, else the CPUs this process may run on (torchrun sets
+    OMP_NUM_THREADS=1 for its workers)."""
+    ncpu = len(os.sched_getaffinity(0))
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i["num_threads"] for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except ImportError:
+        pass
+    for k in ("OPENBLAS_NUM_THREADS", "GOTO_NUM_THREADS", "OMP_NUM_THREADS"):
+        v = os.environ.get(k, "")
+        if v.isdigit() and int(v) > 0:
+            return min(int(v), ncpu)
+    return ncpu
 
 
 def measured_peaks():
@@ -162,16 +184,16 @@ def cpu_baseline(d, budget_s=20.0, max_evals=6, workload=None):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": n / dt, "unit": "evals/s", "cores": oracle_threads(), "kind": "oracle",
             "sample": f"{n} oracle energy+gradient evaluations of {workload} at A_ov = a0 "
                       "(numpy FP64; basis matrix and reference set up before timing)"}
 
 
 def run_reference(args):
-    world, rank, local = dist_setup(args.gpus)
-    if rank != 0:
+    # the oracle arm uses neither a GPU nor a collective: under torchrun rank 0
+    # alone runs it and the other ranks exit without work
+    if int(os.environ.get("RANK", "0")) != 0:
         return
-    import etdm_synth as synth
     from oracle.etdm_oracle import Oracle
     d = workload_system(args.workload)
     o = Oracle(d)
@@ -190,7 +212,7 @@ def run_reference(args):
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "parallelism": "replicas"},
-        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(),
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": oracle_threads(),
                          "kind": "oracle",
                          "sample": "each step: 1 oracle energy+gradient evaluation of "
                                    f"{WORKLOADS[args.workload]}"},

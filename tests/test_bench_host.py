@@ -1,0 +1,86 @@
+"""Host-side logic of bench.py that runs without a GPU: the replica aggregation
+over ranks (gloo, world size 2), the oracle arm launched under torchrun, and
+the count of threads the oracle's timing reports."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _aggregate_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # each replica times its own steps; value = all evaluations / slowest rank
+        ms = [120.0, 180.0][rank]
+        evals = [13, 11][rank]
+        bench.barrier(world)
+        t_max = bench.reduce_max(ms, world, "cpu")
+        n_all = bench.reduce_sum(evals, world, "cpu")
+        with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+            json.dump({"t_max": t_max, "n_all": n_all,
+                       "value": n_all / (t_max / 1e3)}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_aggregation_max_time_sum_of_evaluations(tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_aggregate_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    res = [json.load(open(tmp_path / f"r{r}.json")) for r in range(2)]
+    for r in res:
+        assert r["t_max"] == 180.0
+        assert r["n_all"] == 24.0
+        assert r["value"] == pytest.approx(24 / 0.18)
+
+
+def test_single_rank_helpers_need_no_process_group():
+    assert bench.reduce_max(2.5, 1, "cpu") == 2.5
+    assert bench.reduce_sum(7, 1, "cpu") == 7
+    bench.barrier(1)
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """Two ranks of the oracle arm: rank 0 alone runs and prints; both exit 0."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+           "--workload", "small", "--steps", "2", "--warmup", "1"]
+    p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [json.loads(x) for x in p.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    ln = lines[0]
+    assert ln["impl"] == "reference" and ln["n_gpus"] == 2 and ln["steps"] == 2
+    assert ln["value"] > 0 and ln["e2e"]["value"] == ln["value"]
+    assert ln["cpu_baseline"]["value"] == ln["value"]
+    # torchrun sets OMP_NUM_THREADS=1 for its workers unless it is already set
+    if "OMP_NUM_THREADS" not in os.environ and "OPENBLAS_NUM_THREADS" not in os.environ:
+        assert ln["cpu_baseline"]["cores"] == 1
+
+
+def test_oracle_threads_without_threadpoolctl(monkeypatch):
+    monkeypatch.setitem(sys.modules, "threadpoolctl", None)  # import raises ImportError
+    ncpu = len(os.sched_getaffinity(0))
+    for k in ("OPENBLAS_NUM_THREADS", "GOTO_NUM_THREADS", "OMP_NUM_THREADS"):
+        monkeypatch.delenv(k, raising=False)
+    assert bench.oracle_threads() == ncpu
+    monkeypatch.setenv("OMP_NUM_THREADS", "1")
+    assert bench.oracle_threads() == 1
+    monkeypatch.setenv("OPENBLAS_NUM_THREADS", str(ncpu + 5))  # takes precedence, capped
+    assert bench.oracle_threads() == ncpu
