@@ -328,6 +328,41 @@ def test_preconditioner_formula():
     assert P.shape == (o.N, o.V) and np.all(P > 0)
 
 
+def test_preconditioner_gamma0_is_inverse_fd_hessian():
+    """Eq. 31-33: with gamma = 0 the preconditioner is the inverse of the diagonal
+    Hessian, which for a fixed potential in its eigenbasis is exact: compare
+    1 / P_ij with the second difference of E along a_ij (and check that gamma
+    mixes the inverse Hessian linearly with beta)."""
+    d = synth.config_small_molecule()
+    o = Oracle(d, hartree=False, exchange=False)
+    ref = o.reference()
+    from scipy.linalg import eigh
+    eps, C = eigh(ref["hcore"], ref["S"])
+    P0 = o.precond(eps, beta=7.0, gamma=0.0)
+    Pg = o.precond(eps, beta=7.0, gamma=0.3)
+    h = 1e-4
+    for (i, j) in [(0, 0), (3, 2), (1, 9), (2, 11)]:
+        e = np.zeros((o.N, o.V)); e[i, j] = h
+        fd2 = (o.energy(e, C0=C) - 2 * o.energy(0 * e, C0=C) + o.energy(-e, C0=C)) / h**2
+        assert abs(1.0 / P0[i, j] - fd2) < 1e-5 * fd2, (i, j, 1.0 / P0[i, j], fd2)
+        assert abs(1.0 / Pg[i, j] - (0.7 * fd2 + 0.3 * 7.0)) < 1e-5 * fd2
+
+
+def test_orbital_energies_sum_is_trace_of_S_inverse_H():
+    """Sum_j eps_j = Tr(C0^T H C0) = Tr(S^-1 H) for any C0 with C0 C0^T = S^-1,
+    whatever the column order: pins that the Eq. 33 orbital energies contract
+    H[rho(A = 0)] with the reference orbitals of Eq. 3-4."""
+    d = synth.config_small_molecule()
+    o = Oracle(d)
+    eps = o.orbital_energies()
+    _, _, ex = o.energy_grad(np.zeros((o.N, o.V)), want=True)
+    S = o.reference()["S"]
+    want = float(np.trace(np.linalg.solve(S, ex["H"])))
+    assert abs(eps.sum() - want) < 1e-10 * max(1.0, abs(want))
+    from scipy.linalg import eigh
+    assert abs(want - eigh(ex["H"], S, eigvals_only=True).sum()) < 1e-10 * max(1.0, abs(want))
+
+
 def test_paper_parameters_golden():
     with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
         g = json.load(f)
