@@ -50,9 +50,10 @@ enum {
 
 enum {
   ETDM_PREC_FP64 = 0,  /* every step in FP64 */
-  ETDM_PREC_MIXED = 1  /* grid contractions on tensor cores with split
-                          operands and FP32 accumulation; exp(A), energy
-                          sums and L-BFGS in FP64 */
+  ETDM_PREC_MIXED = 1  /* density and V on tensor cores (exact BF16 slices
+                          of split operands); potential, exp(A), O and the
+                          adjoint on float pairs (about 47 bits); kinetic
+                          energy, energy total, gradient and L-BFGS in FP64 */
 };
 
 /* One periodic system (Eq. 3-5 at the Gamma point).  All host pointers,
