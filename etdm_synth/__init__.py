@@ -17,8 +17,17 @@ Every system is a plain dict of numpy arrays in atomic units:
     n_electrons int                   even; N = n_electrons / 2 doubly occupied
     a0         (N, M-N)     float64   starting occupied-virtual block A_ov
 
+Crystals (k-point sampling, full A(k)) add:
+
+    kpts       (n_k, 3)     float64   k-points, fractional reciprocal coordinates
+    kw         (n_k,)       float64   k-point weights (sum 1)
+    kT         float                  Fermi-Dirac temperature of the reference
+                                      occupations, hartree
+    a0         (n_k*M*M,)   float64   real variables of every A(k) (gradient checks)
+
 The recipes (positions, exponents, grid, truncation, A_ov distribution) follow
-the workloads the paper studies (small molecules, liquid-water boxes), shrunk
+the workloads the paper studies (small molecules, liquid-water boxes, insulating
+crystals with k-point sampling), shrunk
 to a model Hamiltonian of s-type Gaussians; the water-like boxes stand in for
 the paper's liquid-water snapshots, which are not reproduced here.
 """
@@ -163,6 +172,66 @@ def ragged_water(grid=(36, 28, 44), seed=11):
     """2 water-like units on a grid whose sizes are not tile multiples."""
     return water_box(lattice=(2, 1, 1), box_ang=6.0, grid=grid, rcut_ang=3.0,
                      a_sigma=0.05, seed=seed)
+
+
+HA_PER_EV = 1.0 / 27.211386245988  # CODATA 2018
+
+
+def monkhorst_pack(q):
+    """q x q x q Monkhorst-Pack k-points in fractional reciprocal coordinates,
+    k_a = (2 r - q - 1) / (2 q) for r = 1 .. q, and their equal weights."""
+    ks = [(2.0 * r - q - 1.0) / (2.0 * q) for r in range(1, q + 1)]
+    kpts = np.array([[a, b, c] for a in ks for b in ks for c in ks], dtype=np.float64)
+    return kpts, np.full(len(kpts), 1.0 / len(kpts))
+
+
+def crystal(cells=(4, 4, 4), spacing_ang=2.8, jitter_ang=0.05, n_exp=8, Z=4.0,
+            grid=(56, 56, 56), rcut_ang=4.0, kmesh=2, kT_ev=0.1, sigma=0.5,
+            a_sigma=0.01, seed=4, exps=None):
+    """Simple-cubic crystal, one atom per lattice site with a seeded jitter, n_exp
+    s-Gaussians per atom (exponents geometric in 0.3 .. 3.0 bohr^-2), a
+    Monkhorst-Pack k-mesh and a Fermi-Dirac temperature for the reference
+    occupations.  a0 holds the seeded real variables of the full A(k) of every
+    k-point (M*M per k-point) for gradient checks; minimizations start at A = 0."""
+    cells = np.asarray(cells)
+    box = cells * spacing_ang * ANGSTROM
+    rng = np.random.default_rng(seed + 1000)
+    pos = []
+    for i in range(cells[0]):
+        for j in range(cells[1]):
+            for k in range(cells[2]):
+                site = (np.array([i, j, k]) + 0.5) * spacing_ang * ANGSTROM
+                pos.append(site + rng.uniform(-jitter_ang, jitter_ang, 3) * ANGSTROM)
+    if exps is None:
+        exps = [0.3 * 10.0 ** (e / (n_exp - 1)) for e in range(n_exp)]
+    n_at = len(pos)
+    rcut = None if rcut_ang is None else rcut_ang * ANGSTROM
+    d = _finish(np.array(pos), [Z] * n_at, [list(exps)] * n_at, box, grid,
+                rcut, sigma, a_sigma, seed)
+    kpts, kw = monkhorst_pack(kmesh)
+    M = len(d["bf_exp"])
+    d.update(kpts=kpts, kw=kw, kT=kT_ev * HA_PER_EV,
+             a0=np.random.default_rng(seed).normal(0.0, a_sigma, size=len(kw) * M * M))
+    return d
+
+
+def config_crystal64():
+    """64 atoms on a 4x4x4 simple-cubic lattice (2.8 A, 0.05 A jitter, seed 4),
+    8 Gaussians per atom (M = 512), Z = 4 (256 electrons), 56^3 grid over the
+    11.2 A cell, r_c = 4 A, 2x2x2 Monkhorst-Pack k-points, kT = 0.1 eV;
+    gradient-check variables ~ N(0, 0.01)."""
+    return crystal()
+
+
+def tiny_crystal(kT_ev=0.5, kmesh=2, grid=(24, 12, 12), seed=6):
+    """Two atoms per cell (a 2x1x1 supercell of a 2.2 A simple-cubic lattice),
+    2 Gaussians each (exponents 0.4 and 1.2, M = 4), Z = 1, with a k-mesh and a
+    temperature at which the occupations are fractional; the 1e-16 truncation
+    rule and an isotropic grid keep the analytic S and T within quadrature
+    error of the grid.  Brute-force sized."""
+    return crystal(cells=(2, 1, 1), spacing_ang=2.2, jitter_ang=0.1, Z=1.0,
+                   exps=(0.4, 1.2), grid=grid, rcut_ang=None, kmesh=kmesh,
+                   kT_ev=kT_ev, a_sigma=0.05, seed=seed)
 
 
 def direction(shape, seed, scale=1.0):

@@ -81,3 +81,31 @@ def test_distinct_seeds_differ():
     assert x.shape == (3, 4) and np.array_equal(x, synth.direction((3, 4), seed=5, scale=0.1))
     y = synth.direction((400, 50), seed=1, scale=2.0)
     assert abs(y.std() - 2.0) < 0.05 and abs(y.mean()) < 0.05
+
+
+def test_crystal64_recipe():
+    d = synth.config_crystal64()
+    assert d["pos"].shape == (64, 3) and len(d["bf_exp"]) == 512 and d["n_electrons"] == 256
+    assert tuple(d["grid"]) == (56, 56, 56) and np.allclose(d["box"], 11.2 * A)
+    assert np.allclose(d["bf_rcut"], 4.0 * A) and np.all(d["Z"] == 4.0)
+    exps = d["bf_exp"][:8]
+    assert np.allclose(exps[[0, -1]], [0.3, 3.0]) and np.allclose(exps[1:] / exps[:-1], 10 ** (1 / 7))
+    # simple-cubic sites at (n + 1/2) 2.8 A with a jitter of at most 0.05 A per axis
+    site = (np.floor(d["pos"] / (2.8 * A)) + 0.5) * 2.8 * A
+    assert np.abs(d["pos"] - site).max() <= 0.05 * A + 1e-12
+    kp, kw = d["kpts"], d["kw"]
+    assert kp.shape == (8, 3) and np.all(np.abs(kp) == 0.25) and np.allclose(kw, 1 / 8)
+    assert len({tuple(k) for k in kp}) == 8
+    assert abs(d["kT"] - 0.1 / 27.211386245988) < 1e-18
+    assert d["a0"].shape == (8 * 512 * 512,) and abs(d["a0"].std() - 0.01) < 1e-4
+
+
+def test_monkhorst_pack():
+    for q in (1, 2, 3, 4):
+        kp, kw = synth.monkhorst_pack(q)
+        assert kp.shape == (q ** 3, 3) and abs(kw.sum() - 1) < 1e-15
+        # symmetric under k -> -k, inside the first zone, Gamma only for odd q
+        s = {tuple(np.round(k, 12)) for k in kp}
+        assert s == {tuple(np.round(-k, 12)) for k in kp}
+        assert np.all(np.abs(kp) < 0.5)
+        assert ((0.0, 0.0, 0.0) in s) == (q % 2 == 1)
