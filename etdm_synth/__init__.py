@@ -234,6 +234,43 @@ def tiny_crystal(kT_ev=0.5, kmesh=2, grid=(24, 12, 12), seed=6):
                    kT_ev=kT_ev, a_sigma=0.05, seed=seed)
 
 
+def molecule_batch(n_mol=148, atoms=(2, 20), p_heavy=1.0 / 3.0, cube_ang=4.8,
+                   box_ang=9.6, grid=(48, 48, 48), rcut_ang=4.0, min_sep_ang=1.0,
+                   sigma=0.5, a_sigma=0.05, seed=3):
+    """Molecules of uneven size, each in its own cell: n_atoms uniform in
+    [atoms[0], atoms[1]], each site heavy (Z = 6, 4 Gaussians 0.3 .. 3.0) with
+    probability p_heavy, else light (Z = 1, exponents 0.5 and 1.5); when the
+    electron count is odd the last light site becomes heavy.  Positions are
+    uniform in a cube of edge cube_ang centred in the box, at least min_sep_ang
+    apart.  Molecule i draws its A_ov from seed 1000 * seed + i."""
+    rng = np.random.default_rng(seed + 1000)
+    box = np.full(3, box_ang * ANGSTROM)
+    half = 0.5 * cube_ang * ANGSTROM
+    out = []
+    for i in range(n_mol):
+        n_at = int(rng.integers(atoms[0], atoms[1] + 1))
+        heavy = rng.random(n_at) < p_heavy
+        light = np.flatnonzero(~heavy)
+        if len(light) % 2 == 1:
+            heavy[light[-1]] = True
+        pos = []
+        while len(pos) < n_at:
+            p = 0.5 * box + rng.uniform(-half, half, 3)
+            if all(np.linalg.norm(p - q) >= min_sep_ang * ANGSTROM for q in pos):
+                pos.append(p)
+        Z = [6.0 if h else 1.0 for h in heavy]
+        exps = [HEAVY_EXPS if h else LIGHT_EXPS for h in heavy]
+        out.append(_finish(np.array(pos), Z, exps, box, grid, rcut_ang * ANGSTROM,
+                           sigma, a_sigma, 1000 * seed + i))
+    return out
+
+
+def config_molecules148():
+    """148 molecules of 2 to 20 atoms (M from 4 to 80), each on a 48^3 grid over
+    a 9.6 A box (0.2 A spacing), r_c = 4 A, A_ov ~ N(0, 0.05) (seed 3)."""
+    return molecule_batch()
+
+
 def direction(shape, seed, scale=1.0):
     """A seeded random array (search directions, FD probes, test vectors)."""
     return np.random.default_rng(seed).normal(0.0, scale, size=shape)

@@ -109,3 +109,35 @@ def test_monkhorst_pack():
         assert s == {tuple(np.round(-k, 12)) for k in kp}
         assert np.all(np.abs(kp) < 0.5)
         assert ((0.0, 0.0, 0.0) in s) == (q % 2 == 1)
+
+
+def test_molecules148_recipe():
+    ms = synth.config_molecules148()
+    assert len(ms) == 148
+    box = 9.6 * A
+    for m in ms:
+        n = len(m["Z"])
+        assert 2 <= n <= 20 and m["n_electrons"] % 2 == 0
+        assert tuple(m["grid"]) == (48, 48, 48) and np.allclose(m["box"], box)
+        assert np.allclose(m["bf_rcut"], 4.0 * A)
+        heavy = m["Z"] == 6.0
+        assert np.all(heavy | (m["Z"] == 1.0))
+        assert len(m["bf_exp"]) == 4 * heavy.sum() + 2 * (~heavy).sum()
+        assert m["a0"].shape == (m["n_electrons"] // 2, len(m["bf_exp"]) - m["n_electrons"] // 2)
+        # inside the centred 4.8 A cube, at least 1 A apart
+        assert np.all(np.abs(m["pos"] - 0.5 * box) <= 2.4 * A)
+        dd = np.linalg.norm(m["pos"][:, None] - m["pos"][None, :], axis=-1)
+        assert dd[np.triu_indices(n, 1)].min() >= 1.0 * A
+    M = [len(m["bf_exp"]) for m in ms]
+    assert min(M) == 4 and max(M) <= 80
+    na = [len(m["Z"]) for m in ms]
+    assert set(na) == set(range(2, 21))  # every size occurs
+
+
+def test_batch_molecule_through_the_oracle():
+    from oracle.etdm_oracle import Oracle
+    m = min(synth.config_molecules148(), key=lambda x: len(x["bf_exp"]))
+    o = Oracle(m)
+    D = o.density_matrix(o.orbitals(m["a0"]))
+    assert abs(float(np.sum(D * o.reference()["S"])) - m["n_electrons"]) < 1e-12
+    assert abs(o.dV * o.density(D).sum() - m["n_electrons"]) < 1e-8 * m["n_electrons"]
