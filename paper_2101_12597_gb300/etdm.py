@@ -114,6 +114,41 @@ class EtdmError(RuntimeError):
         self.code = code
 
 
+def _require(t, dev, name, shape=None, numel=None):
+    """ValueError unless t is a contiguous float64 tensor on the device dev, of
+    the given shape (or element count): the library receives raw pointers and
+    sizes, so nothing past this point can check them."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_contiguous()
+          and t.device == dev and (shape is None or tuple(t.shape) == tuple(shape))
+          and (numel is None or t.numel() == numel))
+    if not ok:
+        want = f"shape {tuple(shape)}" if shape is not None else f"{numel} elements"
+        got = (f"{tuple(t.shape)} {t.dtype} on {t.device}, contiguous={t.is_contiguous()}"
+               if isinstance(t, torch.Tensor) else type(t).__name__)
+        raise ValueError(f"{name}: expected a contiguous float64 tensor of {want} on {dev}; "
+                         f"got {got}")
+
+
+def _noalloc_shapes(g, S, Y, h0, out):
+    """(m, n) of an allocation-free direction call after checking that every
+    tensor sits on g's device with consistent sizes: S and Y of shape (m, n)
+    (both None for m = 0), g, h0 and out of n elements."""
+    n = g.numel()
+    dev = g.device
+    _require(g, dev, "g", numel=n)
+    _require(h0, dev, "h0", numel=n)
+    _require(out, dev, "out", numel=n)
+    if (S is None) != (Y is None):
+        raise ValueError("S and Y: give both or neither")
+    if S is None:
+        return 0, n
+    m = S.shape[0] if S.dim() == 2 else -1
+    _require(S, dev, "S", shape=(m, n))
+    _require(Y, dev, "Y", shape=(m, n))
+    return m, n
+
+
 def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
@@ -178,11 +213,8 @@ class ETDM:
         if rc != ETDM_OK:
             raise EtdmError(rc, self.lib.etdm_last_error(self.h).decode())
 
-    def _check_tensor(self, t, shape):
-        import torch
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-                and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
-            raise ValueError(f"expected a contiguous cuda float64 tensor of shape {shape}")
+    def _check_tensor(self, t, shape, name="a"):
+        _require(t, self.dev, name, shape=shape)
 
     # -- entry points -------------------------------------------------------------
     def energy_grad(self, a, want_grad=True, E=None, g=None, stream=None):
@@ -191,8 +223,11 @@ class ETDM:
         self._check_tensor(a, (self.N, self.V))
         if E is None:
             E = torch.empty(1, dtype=torch.float64, device=self.dev)
+        _require(E, self.dev, "E", numel=1)
         if want_grad and g is None:
             g = torch.empty((self.N, self.V), dtype=torch.float64, device=self.dev)
+        if want_grad:
+            self._check_tensor(g, (self.N, self.V), "g")
         rc = self.lib.etdm_energy_grad(self.h, ctypes.c_void_p(a.data_ptr()),
                                        ctypes.c_void_p(E.data_ptr()),
                                        ctypes.c_void_p(g.data_ptr()) if want_grad else None,
@@ -202,7 +237,8 @@ class ETDM:
 
     def energy_grad_host(self, a, want_grad=True):
         a = np.ascontiguousarray(a, dtype=np.float64)
-        assert a.shape == (self.N, self.V)
+        if a.shape != (self.N, self.V):
+            raise ValueError(f"a: expected shape {(self.N, self.V)}, got {a.shape}")
         E = np.zeros(1)
         g = np.zeros((self.N, self.V)) if want_grad else None
         rc = self.lib.etdm_energy_grad_host(self.h, _dptr(a), _dptr(E),
@@ -212,8 +248,9 @@ class ETDM:
 
     def precondition(self, g, out=None, stream=None):
         import torch
-        self._check_tensor(g, (self.N, self.V))
+        self._check_tensor(g, (self.N, self.V), "g")
         out = torch.empty_like(g) if out is None else out
+        self._check_tensor(out, (self.N, self.V), "out")
         self._raise(self.lib.etdm_precondition(self.h, ctypes.c_void_p(g.data_ptr()),
                                                ctypes.c_void_p(out.data_ptr()),
                                                _stream_ptr(stream)))
@@ -222,8 +259,9 @@ class ETDM:
     def lbfgs_step(self, a, g, out=None, stream=None):
         import torch
         self._check_tensor(a, (self.N, self.V))
-        self._check_tensor(g, (self.N, self.V))
+        self._check_tensor(g, (self.N, self.V), "g")
         out = torch.empty_like(g) if out is None else out
+        self._check_tensor(out, (self.N, self.V), "out")
         self._raise(self.lib.etdm_lbfgs_step(self.h, ctypes.c_void_p(a.data_ptr()),
                                              ctypes.c_void_p(g.data_ptr()),
                                              ctypes.c_void_p(out.data_ptr()),
@@ -289,12 +327,10 @@ def lbfgs_direction_noalloc(g, S, Y, h0, out=None, stream=None):
     callers (here it is created when None)."""
     import torch
     lib = load_library()
-    n = g.numel()
-    m = 0 if S is None else S.shape[0]
-    for t in [g, h0] + ([S, Y] if m else []):
-        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-            raise ValueError("contiguous cuda float64 tensors expected")
+    if not (isinstance(g, torch.Tensor) and g.is_cuda):
+        raise ValueError("g: expected a CUDA tensor")
     out = torch.empty_like(g) if out is None else out
+    m, n = _noalloc_shapes(g, S, Y, h0, out)
     rc = lib.etdm_lbfgs_direction_noalloc(
         ctypes.c_void_p(g.data_ptr()),
         ctypes.c_void_p(S.data_ptr()) if m else None,
