@@ -68,3 +68,61 @@ def test_no_cpu_fallback():
     build.build()
     with pytest.raises(ValueError, match="CUDA tensor"):
         etdm.lbfgs_direction_noalloc(_t(4), None, None, _t(4))
+
+
+class _StubLib:
+    """Records the arguments of each entry point and returns ETDM_OK."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        if not name.startswith("etdm_"):
+            raise AttributeError(name)
+
+        def f(*args):
+            self.calls.append((name, args))
+            return 0
+        return f
+
+
+def _stub_solver(N=3, V=5):
+    s = object.__new__(etdm.ETDM)
+    s.lib, s.h, s.dev, s.N, s.V, s.M = _StubLib(), None, CPU, N, V, N + V
+    return s
+
+
+def test_marshalling_with_a_stub_library():
+    class Stream:  # a caller-owned stream: only its handle is passed on
+        cuda_stream = 0
+
+    st = Stream()
+    s = _stub_solver()
+    a = _t(3, 5)
+    E, g = s.energy_grad(a, stream=st)
+    name, args = s.lib.calls[-1]
+    assert name == "etdm_energy_grad"
+    assert [x.value for x in args[1:4]] == [a.data_ptr(), E.data_ptr(), g.data_ptr()]
+    E2, g2 = s.energy_grad(a, want_grad=False, stream=st)
+    assert g2 is None and s.lib.calls[-1][1][3] is None
+    out = _t(3, 5)
+    assert s.precondition(g, out=out, stream=st) is out
+    assert s.lbfgs_step(a, g, out=out, stream=st) is out
+    assert s.lib.calls[-1][0] == "etdm_lbfgs_step"
+    assert [x.value for x in s.lib.calls[-1][1][1:4]] == [a.data_ptr(), g.data_ptr(),
+                                                          out.data_ptr()]
+    n_calls = len(s.lib.calls)
+    for bad in [dict(E=_t(2)), dict(g=_t(5, 3)), dict(g=_t(3, 5, dtype=torch.float32))]:
+        with pytest.raises(ValueError):
+            s.energy_grad(a, stream=st, **bad)
+    with pytest.raises(ValueError, match="out:"):
+        s.precondition(g, out=_t(15), stream=st)
+    with pytest.raises(ValueError, match="a:"):
+        s.lbfgs_step(_t(5, 3), g, stream=st)
+    with pytest.raises(ValueError):
+        s.energy_grad(a.t().contiguous().t(), stream=st)  # a non-contiguous view
+    assert len(s.lib.calls) == n_calls  # none of these reached the library
+    with pytest.raises(ValueError, match="a: expected shape"):
+        s.energy_grad_host(np.zeros((5, 3)))
+    E, gh = s.energy_grad_host(np.zeros((3, 5)))
+    assert gh.shape == (3, 5) and s.lib.calls[-1][0] == "etdm_energy_grad_host"
