@@ -130,10 +130,24 @@ class BlochOracle(Oracle):
 
     def Xk(self, k):
         """Dense Bloch basis matrix X_k[r, mu] = chi_mu,k(r), grid in C order."""
-        if k not in self._Xk:
-            self._Xk[k] = np.concatenate([self.basis_plane_k(i, k)
-                                          for i in range(int(self.n[0]))])
-        return self._Xk[k]
+        if k in self._Xk:
+            return self._Xk[k]
+        X = np.concatenate([self.basis_plane_k(i, k) for i in range(int(self.n[0]))])
+        if self._cache_x:
+            self._Xk[k] = X
+        return X
+
+    def _planes_k(self, k):
+        """(x-plane index, basis rows of that plane): from the cached X_k, or
+        built one plane at a time when caching is off (large systems)."""
+        per = int(self.n[1] * self.n[2])
+        if self._cache_x or k in self._Xk:
+            X = self.Xk(k)
+            for i in range(int(self.n[0])):
+                yield i, X[i * per:(i + 1) * per]
+        else:
+            for i in range(int(self.n[0])):
+                yield i, self.basis_plane_k(i, k)
 
     # ---- S(k), T(k) ------------------------------------------------------------
     def overlap_kinetic_k(self, k):
@@ -163,13 +177,20 @@ class BlochOracle(Oracle):
     # ---- density and Hamiltonian per k-point (Eq. 2, Eq. 11-12) ---------------
     def density_k(self, D, k):
         """sum_mu,nu chi_mu,k(r) D_mu,nu conj(chi_nu,k(r)) (real up to rounding)."""
-        X = self.Xk(k)
-        return np.einsum("pa,pa->p", X @ D, X.conj()).real.reshape(tuple(self.n))
+        out = np.empty(self.G)
+        per = int(self.n[1] * self.n[2])
+        for i, Xp in self._planes_k(k):
+            out[i * per:(i + 1) * per] = np.einsum("pa,pa->p", Xp @ D, Xp.conj()).real
+        return out.reshape(tuple(self.n))
 
     def potential_matrix_k(self, v, k):
         """V_mu,nu(k) = dV sum_r conj(chi_mu,k(r)) v(r) chi_nu,k(r)."""
-        X = self.Xk(k)
-        return self.dV * (X.conj().T @ (v.reshape(-1, 1) * X))
+        Vm = np.zeros((self.M, self.M), dtype=np.complex128)
+        per = int(self.n[1] * self.n[2])
+        vf = v.reshape(-1)
+        for i, Xp in self._planes_k(k):
+            Vm += Xp.conj().T @ (vf[i * per:(i + 1) * per, None] * Xp)
+        return self.dV * Vm
 
     # ---- reference orbitals and occupations ---------------------------------------
     def reference_k(self):

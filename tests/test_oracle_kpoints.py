@@ -268,3 +268,30 @@ def test_minimization_reaches_stationarity(tiny):
     assert np.abs(g).max() < 1e-8
     # Eq. 15 with fractional occupation: [F, H_mo] = 0 at the minimum
     assert max(np.abs(x["L"]).max() for x in ex["k"]) < 1e-8
+
+
+def test_streamed_planes_equal_the_cached_basis(tiny):
+    """Large systems build the Bloch basis one x-plane at a time; the sums are
+    the same, in a different association order."""
+    d, bo = tiny
+    bs = BlochOracle(d, cache_x=False)
+    E1, g1 = bo.energy_grad(d["a0"])
+    E2, g2 = bs.energy_grad(d["a0"])
+    assert not bs._Xk and abs(E1 - E2) < 1e-13 and np.abs(g1 - g2).max() < 1e-13
+
+
+def test_oracle_matches_stored_tiny_crystal_values(tiny):
+    # stored values come from tests/golden/make_golden.py (oracle only); this
+    # guards the k-point oracle against unreviewed arithmetic changes
+    import json
+    import os
+    d, bo = tiny
+    with open(os.path.join(os.path.dirname(__file__), "golden", "tiny_crystal_oracle.json")) as f:
+        gold = json.load(f)
+    E, g = bo.energy_grad(d["a0"])
+    ref = bo.reference_k()
+    assert abs(E - gold["E_a0"]) < 1e-11
+    assert np.abs(g - np.array(gold["g_a0"])).max() < 1e-10
+    assert abs(ref["mu"] - gold["mu"]) < 1e-11
+    assert np.abs(np.array(ref["f"]) - np.array(gold["f"])).max() < 1e-11
+    assert np.abs(np.array(ref["eps_core"]) - np.array(gold["eps_core"])).max() < 1e-11
