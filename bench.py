@@ -100,8 +100,9 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except OSError:
-            self.proc = None
+        except OSError:  # no nvidia-smi: no clock record, and no file left behind
+            os.unlink(self.path)
+            self.proc, self.path = None, None
 
     def stop(self):
         if self.proc is None:

@@ -84,3 +84,44 @@ def test_oracle_threads_without_threadpoolctl(monkeypatch):
     assert bench.oracle_threads() == 1
     monkeypatch.setenv("OPENBLAS_NUM_THREADS", str(ncpu + 5))  # takes precedence, capped
     assert bench.oracle_threads() == ncpu
+
+
+def test_clock_record_parsing(tmp_path):
+    """The sampler's CSV (nvidia-smi, no header, no units): median SM clock under
+    load, the maximum, and every throttle reason seen active."""
+    p = tmp_path / "clocks.csv"
+    p.write_text(
+        "0, 1965, 2070, 950.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2070, 2070, 900.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, [N/A], 2070, [N/A], 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1995, 2070, 1000.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "garbled line\n")
+
+    class Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+        def kill(self):
+            pass
+
+    c = bench.Clocks(0)
+    c.proc, c.path = Proc(), str(p)
+    r = c.stop()
+    assert r == {"sm_mhz": 1995.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 4}
+    assert not p.exists()
+    p.write_text("0, 1410, 2070, 700.0, 0x0000000000000048, Active, Not Active, Active, Not Active\n")
+    c.proc, c.path = Proc(), str(p)
+    assert c.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
+    monkeypatch.setenv("PATH", str(tmp_path))  # no nvidia-smi on the path
+    monkeypatch.setattr(bench.tempfile, "tempdir", str(tmp_path))
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop() is None
+    assert list(tmp_path.iterdir()) == []  # the temporary file is gone
