@@ -295,3 +295,17 @@ def test_oracle_matches_stored_tiny_crystal_values(tiny):
     assert abs(ref["mu"] - gold["mu"]) < 1e-11
     assert np.abs(np.array(ref["f"]) - np.array(gold["f"])).max() < 1e-11
     assert np.abs(np.array(ref["eps_core"]) - np.array(gold["eps_core"])).max() < 1e-11
+
+
+def test_imaginary_diagonal_force_vanishes_only_at_zero(tiny):
+    """Im a_ii: zero gradient at A = 0 (L_ii = 0), generally non-zero elsewhere
+    (a diagonal step commutes with A only in special cases), so these variables
+    stay in the parametrization."""
+    d, bo = tiny
+    nre = bo.M * (bo.M - 1) // 2
+    diag = [nre + p for p, (i, j) in enumerate(zip(*bo._iud)) if i == j]
+    idx = [k * bo.nvar + p for k in range(bo.nk) for p in diag]
+    _, g0 = bo.energy_grad(np.zeros_like(d["a0"]))
+    _, g = bo.energy_grad(d["a0"])
+    assert np.abs(g0[idx]).max() == 0.0
+    assert np.abs(g[idx]).max() > 1e-5
