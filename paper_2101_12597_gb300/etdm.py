@@ -247,6 +247,8 @@ class ETDM:
         return float(E[0]), g
 
     def precondition(self, g, out=None, stream=None):
+        """P^(k) o g (Eq. 33) with the current beta^(k) (Eq. 34): g (N x V) on the
+        device; returns `out` (created when None)."""
         import torch
         self._check_tensor(g, (self.N, self.V), "g")
         out = torch.empty_like(g) if out is None else out
@@ -257,6 +259,9 @@ class ETDM:
         return out
 
     def lbfgs_step(self, a, g, out=None, stream=None):
+        """L-BFGS direction p = -H g at the point a (Sec. 3.1): stores the pair
+        (a - a_prev, g - g_prev) when its curvature is positive, updates beta
+        (Eq. 34) and runs the two-loop recursion with H0 = P^(k).  Returns `out`."""
         import torch
         self._check_tensor(a, (self.N, self.V))
         self._check_tensor(g, (self.N, self.V), "g")
@@ -269,6 +274,7 @@ class ETDM:
         return out
 
     def lbfgs_reset(self):
+        """Erase the L-BFGS memory (no pairs, no previous point, beta = beta0)."""
         self._raise(self.lib.etdm_lbfgs_reset(self.h))
 
     def minimize(self, a, n_steps, stream=None):
@@ -284,9 +290,11 @@ class ETDM:
         return E, al, tr
 
     def check(self, stream=None):
+        """Wait for `stream` and raise EtdmError on a deferred device-side error."""
         self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream)))
 
     def get_array(self, name):
+        """A copy of an internal array (names in ARRAYS: S, T, C0, rho, H, ...)."""
         which, dt = ARRAYS[name]
         nb = self.lib.etdm_array_bytes(self.h, which)
         out = np.zeros(nb // np.dtype(dt).itemsize, dtype=dt)
@@ -295,6 +303,7 @@ class ETDM:
         return out
 
     def set_profiling(self, on=True):
+        """Record CUDA events around each stage (read with stage_times)."""
         self._raise(self.lib.etdm_set_profiling(self.h, 1 if on else 0))
 
     def stage_times(self):
@@ -307,6 +316,7 @@ class ETDM:
                 dict(zip(STAGES, cnt[:len(STAGES)].tolist())), int(cnt[-1]))
 
     def close(self):
+        """Release the handle's device memory (the object is unusable afterwards)."""
         if getattr(self, "h", None):
             self.lib.etdm_free(self.h)
             self.h = None
