@@ -1,0 +1,229 @@
+"""CPU check of the arithmetic the mixed-precision path is built on: float-pair
+numbers (hi + lo in two FP32), their split from FP64, the error-free multiply-add,
+and the cut of a float pair into BF16 slices whose products the tensor cores
+accumulate exactly per slice order.
+
+Each FP32 operation is written out as the exact rational result rounded once to
+FP32 (round to nearest, ties to even), which is what the GPU's __fadd_rn,
+__fmul_rn and __fmaf_rn do, so the error bounds checked here are the kernels'
+and not those of a different evaluation order.  Nothing here is shared with the
+CUDA sources or the oracle."""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+F = Fraction
+
+
+def r32(q):
+    """Round a rational to the nearest FP32 value (ties to even), as a Fraction."""
+    q = F(q)
+    if q == 0:
+        return F(0)
+    s = -1 if q < 0 else 1
+    a = abs(q)
+    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
+    while F(2) ** e > a:
+        e -= 1
+    while F(2) ** (e + 1) <= a:
+        e += 1
+    e = max(e, -126)                  # subnormal range shares the last exponent
+    ulp = F(2) ** (e - 23)
+    n, rem = divmod(a, ulp)
+    if rem > ulp / 2 or (rem == ulp / 2 and n % 2 == 1):
+        n += 1
+    return s * n * ulp
+
+
+def fadd(a, b):
+    return r32(F(a) + F(b))
+
+
+def fmul(a, b):
+    return r32(F(a) * F(b))
+
+
+def fma(a, b, c):
+    return r32(F(a) * F(b) + F(c))
+
+
+def is_f32(q):
+    return r32(q) == q
+
+
+def sig_bits(q):
+    """Number of significant bits of a dyadic rational."""
+    q = abs(F(q))
+    if q == 0:
+        return 0
+    n, d = q.numerator, q.denominator
+    while n % 2 == 0:
+        n //= 2
+    return n.bit_length()
+
+
+# ---- float pairs ----------------------------------------------------------------------
+
+def split(x):
+    """FP64 -> (hi, lo): hi = leading 24 significand bits (truncated), lo = the
+    next 23, both exact (the integer construction of the split)."""
+    x = F(x)
+    if x == 0:
+        return F(0), F(0)
+    s = -1 if x < 0 else 1
+    a = abs(x)
+    e = math.floor(math.log2(a))
+    while F(2) ** e > a:
+        e -= 1
+    while F(2) ** (e + 1) <= a:
+        e += 1
+    hi = (a / F(2) ** (e - 23)).__floor__() * F(2) ** (e - 23)
+    lo = ((a - hi) / F(2) ** (e - 46)).__floor__() * F(2) ** (e - 46)
+    return s * hi, s * lo
+
+
+def two_sum(a, b):
+    s = fadd(a, b)
+    bb = fadd(s, -a)
+    return s, fadd(fadd(a, -fadd(s, -bb)), fadd(b, -bb))
+
+
+def mac(h, l, a, b):
+    """(h, l) += a b as the error-free multiply-add of the float-pair kernels."""
+    p = fmul(a[0], b[0])
+    e = fma(a[0], b[0], -p)
+    e = fma(a[0], b[1], e)
+    e = fma(a[1], b[0], e)
+    s, t = two_sum(h, p)
+    return s, fadd(l, fadd(t, e))
+
+
+def test_split_bounds():
+    rng = np.random.default_rng(1)
+    xs = list(rng.normal(size=300) * 10.0 ** rng.integers(-20, 20, size=300)) + [1.0, -3.0]
+    for x in xs:
+        hi, lo = split(float(x))
+        assert is_f32(hi) and is_f32(lo)
+        assert sig_bits(hi) <= 24 and sig_bits(lo) <= 23
+        assert abs(F(float(x)) - hi - lo) < F(2) ** -46 * abs(F(float(x)))
+        assert abs(lo) < F(2) ** -23 * abs(hi)
+
+
+def test_two_sum_is_error_free():
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        a = r32(F(float(rng.normal() * 10.0 ** rng.integers(-6, 6))))
+        b = r32(F(float(rng.normal() * 10.0 ** rng.integers(-6, 6))))
+        s, t = two_sum(a, b)
+        assert s + t == a + b and s == fadd(a, b)
+
+
+def test_float_pair_dot_product():
+    """K float-pair multiply-adds carry the dot product to about K ulp of the
+    high part's 2^-47 relative precision: far below the 1e-9 relative the
+    energy needs."""
+    rng = np.random.default_rng(3)
+    for K in (16, 128):
+        xs = [split(float(v)) for v in rng.normal(size=K)]
+        ys = [split(float(v)) for v in rng.normal(size=K)]
+        h = l = F(0)
+        for x, y in zip(xs, ys):
+            h, l = mac(h, l, x, y)
+        exact = sum((x[0] + x[1]) * (y[0] + y[1]) for x, y in zip(xs, ys))
+        scale = sum(abs((x[0] + x[1]) * (y[0] + y[1])) for x, y in zip(xs, ys))
+        assert abs(h + l - exact) <= 2 * K * F(2) ** -47 * scale
+
+
+# ---- BF16 slices --------------------------------------------------------------------------
+
+C = [F(12582912), F(49152), F(192), F(3, 4)]  # 1.5 * 2^(23 - 8k)
+
+
+def slices(x, sc, ns=4):
+    """The slicing of the tensor-core passes: x sc = r0 + ... + r_{ns-1} + small."""
+    r = [fadd(fma(x[0], sc, C[0]), -C[0])]
+    u = fma(x[1], sc, fma(x[0], sc, -r[0]))
+    for k in range(1, ns):
+        if k > 1:
+            u = fadd(u, -r[k - 1])
+        r.append(fadd(fadd(u, C[k]), -C[k]))
+    return r
+
+
+def _random_pairs(rng, n):
+    out = []
+    for _ in range(n):
+        v = float(rng.uniform(-1, 1) * 2.0 ** rng.integers(-3, 4))
+        out.append(split(v))
+    return out
+
+
+def _scale_for(x):
+    """Power of two with |x sc| <= 128 (the per-row / per-function exponent)."""
+    a = abs(x[0] + x[1])
+    if a == 0:
+        return F(1)
+    e = math.floor(math.log2(a)) + 1
+    return F(2) ** (7 - e)
+
+
+def test_slices_are_bf16_bounded_and_reconstruct():
+    rng = np.random.default_rng(4)
+    for x in _random_pairs(rng, 400):
+        sc = _scale_for(x)
+        r = slices(x, sc)
+        for k, rk in enumerate(r):
+            assert sig_bits(rk) <= 8                              # exact in BF16
+            assert (rk / F(2) ** (-8 * k)).denominator == 1       # multiple of 2^-8k
+            assert abs(rk) <= 128 * F(2) ** (-8 * k)
+        err = abs((x[0] + x[1]) * sc - sum(r))
+        assert err <= F(2) ** -24                                 # of a value up to 128
+
+
+def test_per_order_accumulation_is_exact_in_fp32():
+    """Products of slices of orders i and j are integers times 2^-8(i+j) below
+    2^14 of that unit, so an FP32 accumulator of one order over 128 K steps of
+    up to four products never rounds."""
+    rng = np.random.default_rng(5)
+    K = 128
+    X = [slices(x, _scale_for(x)) for x in _random_pairs(rng, K)]
+    W = [slices(w, _scale_for(w)) for w in _random_pairs(rng, K)]
+    for order in range(4):
+        acc = F(0)
+        exact = F(0)
+        for xs, ws in zip(X, W):
+            for i in range(order + 1):
+                p = fmul(ws[i], xs[order - i])
+                assert p == ws[i] * xs[order - i]                 # the product is exact
+                acc = fadd(acc, p)
+                exact += ws[i] * xs[order - i]
+        assert acc == exact
+        assert abs(exact) < F(2) ** 24 * F(2) ** (-8 * order)
+
+
+def test_three_slices_and_orders_up_to_three():
+    """The V pass keeps three slices of each operand and the slice products of
+    orders 0..3 (eight per K step).  Per term, the operands' cut at three slices
+    costs up to 2^-24 of each (the remainder below 2^-16 of values up to 128),
+    while the one dropped product (order 4, W2 X2) is below 2^-32 of the term's
+    scale: the pass is as accurate as its three-slice operands."""
+    rng = np.random.default_rng(6)
+    K = 64
+    xs, ws = _random_pairs(rng, K), _random_pairs(rng, K)
+    sx = [_scale_for(x) for x in xs]
+    sw = [_scale_for(w) for w in ws]
+    X = [slices(x, s, 3) for x, s in zip(xs, sx)]
+    W = [slices(w, s, 3) for w, s in zip(ws, sw)]
+    for t in range(K):
+        wv, xv = (ws[t][0] + ws[t][1]) * sw[t], (xs[t][0] + xs[t][1]) * sx[t]
+        assert abs(sum(W[t]) - wv) <= F(2) ** -17 and abs(sum(X[t]) - xv) <= F(2) ** -17
+        dropped = W[t][2] * X[t][2]
+        assert abs(dropped) <= F(2) ** -18                       # 2^-32 of 128 * 128
+    kept = sum(W[t][i] * X[t][j] for t in range(K) for i in range(3) for j in range(3)
+               if i + j <= 3)
+    full3 = sum(sum(W[t]) * sum(X[t]) for t in range(K))
+    assert abs(kept - full3) <= K * F(2) ** -18
+    exact = sum(((w[0] + w[1]) * a) * ((x[0] + x[1]) * b)
+                for w, x, a, b in zip(ws, xs, sw, sx))
+    assert abs(kept - exact) <= K * (2 * 128 * F(2) ** -17 + F(2) ** -18)
