@@ -227,3 +227,29 @@ def test_three_slices_and_orders_up_to_three():
     exact = sum(((w[0] + w[1]) * a) * ((x[0] + x[1]) * b)
                 for w, x, a, b in zip(ws, xs, sw, sx))
     assert abs(kept - exact) <= K * (2 * 128 * F(2) ** -17 + F(2) ** -18)
+
+
+def dot_sub(a, b, c, d):
+    """a b - c d with one renormalization, as the FFT passes' butterflies form
+    their complex products: TwoSum of the two rounded products, their exact
+    errors and the cross terms gathered in the low part."""
+    p, q = fmul(a[0], b[0]), fmul(c[0], d[0])
+    ep, eq = fma(a[0], b[0], -p), fma(c[0], d[0], -q)
+    s, t = two_sum(p, -q)
+    e = fadd(t, fadd(ep, -eq))
+    e = fma(a[0], b[1], fma(a[1], b[0], e))
+    e = fma(-c[0], d[1], fma(-c[1], d[0], e))
+    h = fadd(s, e)
+    return h, fadd(e, -fadd(h, -s))
+
+
+def test_float_pair_dot_sub():
+    """The butterfly product a b - c d keeps about 2^-44 of |a b| + |c d| when the
+    TwoSum sees the two rounded products (the float-pair FFT's accuracy rests on
+    this step)."""
+    rng = np.random.default_rng(7)
+    for _ in range(500):
+        a, b, c, d = [split(float(rng.normal() * 2.0 ** rng.integers(-4, 4))) for _ in range(4)]
+        A, B, Cc, D = [x[0] + x[1] for x in (a, b, c, d)]
+        h, l = dot_sub(a, b, c, d)
+        assert abs(h + l - (A * B - Cc * D)) <= F(2) ** -43 * (abs(A * B) + abs(Cc * D))
