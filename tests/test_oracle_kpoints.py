@@ -309,3 +309,15 @@ def test_imaginary_diagonal_force_vanishes_only_at_zero(tiny):
     _, g = bo.energy_grad(d["a0"])
     assert np.abs(g0[idx]).max() == 0.0
     assert np.abs(g[idx]).max() > 1e-5
+
+
+def test_orbital_energies_sum_is_trace_per_k(tiny):
+    """Eq. 33 at k-points: sum_m eps_m(k) = Tr(C0^dag H C0) = Tr(S(k)^-1 H(k)) at
+    A = 0, for any reference with C0 C0^dag = S^-1."""
+    d, bo = tiny
+    eps = bo.orbital_energies()
+    _, _, ex = bo.energy_grad(np.zeros(bo.nk * bo.nvar), want=True)
+    ref = bo.reference_k()
+    for k in range(bo.nk):
+        tr = np.trace(np.linalg.solve(ref["S"][k], ex["k"][k]["H"]))
+        assert abs(tr.imag) < 1e-12 and abs(eps[k].sum() - tr.real) < 1e-11
