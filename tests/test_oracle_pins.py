@@ -62,6 +62,22 @@ def test_expm_rotation_special_case():
     assert np.abs(o.expm_eig(o.full_A(np.array([[th]]))).real - R).max() < 1e-15
 
 
+def test_expm_series_branch_is_seamless():
+    """Eq. 37 switches s(p), c(p) from their closed forms to series below
+    p = 1e-2: eigenvalues of P placed on both sides of the switch (and at 0)
+    give the same exp(A) as the eigendecomposition route of Eq. 35."""
+    o = Oracle(synth.tiny())
+    o.N, o.M, o.V = 4, 10, 6
+    rng = np.random.default_rng(12)
+    Ql, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    Qr, _ = np.linalg.qr(rng.normal(size=(6, 6)))
+    for sv in ([0.1 - 1e-9, 0.1 + 1e-9, 0.05, 0.0], [0.3, 0.1, 1e-4, 1e-8]):
+        Aov = Ql @ np.diag(sv) @ Qr[:4]                 # P = Aov Aov^T has eigenvalues sv^2
+        U37 = o.expm_occvirt(Aov)
+        U35 = o.expm_eig(o.full_A(Aov)).real
+        assert np.abs(U37 - U35).max() < 2e-15
+
+
 def test_expm_small_A_matches_short_taylor():
     o = Oracle(synth.tiny())
     o.N, o.M, o.V = 3, 8, 5
