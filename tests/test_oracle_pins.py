@@ -287,6 +287,29 @@ def test_gradient_central_differences(which, small, ragged):
         assert abs(fd - g[i, j]) <= max(1e-6, 1e-5 * abs(g[i, j])), (i, j, fd, g[i, j])
 
 
+def test_eq39_equals_the_eq14_integral():
+    """Eq. 39's eigenbasis form of the gradient against Eq. 14 itself,
+    (2 - d_ij)/2 (int_0^1 e^{tA} L e^{-tA} dt)_ji, by 40-point Gauss-Legendre
+    quadrature, for a complex skew-Hermitian A whose spectrum has an exact
+    degeneracy and gaps on both sides of the divided difference's series switch
+    (|Omega_a - Omega_b| = 1e-3).  Pins the sign reading of Eq. 40 and both
+    branches of the divided difference."""
+    rng = np.random.default_rng(21)
+    M = 7
+    W, _ = np.linalg.qr(rng.normal(size=(M, M)) + 1j * rng.normal(size=(M, M)))
+    Om = np.array([0.0, 0.0, 1e-3 * (1 - 1e-6), 1e-3 * (2 + 1e-6), 0.4, -1.1, 2.3])
+    A = -1j * (W * Om) @ W.conj().T                   # iA = W Omega W^dag
+    Lr = rng.normal(size=(M, M)) + 1j * rng.normal(size=(M, M))
+    L = Lr - Lr.conj().T
+    x, w = np.polynomial.legendre.leggauss(40)
+    K = np.zeros((M, M), dtype=complex)
+    for xi, wi in zip(0.5 * (x + 1), 0.5 * w):
+        E = (W * np.exp(-1j * Om * xi)) @ W.conj().T   # e^{tA}
+        K += wi * E @ L @ E.conj().T
+    fac = np.where(np.eye(M, dtype=bool), 0.5, 1.0)
+    assert np.abs(Oracle.grad_eq39(A, L) - fac * K.T).max() < 1e-13
+
+
 def test_gradient_at_zero_is_eq42(small):
     d, o = small
     a = np.zeros_like(d["a0"])
