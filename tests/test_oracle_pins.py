@@ -515,6 +515,21 @@ def test_approximate_wolfe_accepts_noisy_flat_step(E0, kappa, accept):
     assert (alpha == 1.0 and trials == 1) == accept
 
 
+@pytest.mark.parametrize("amin,alpha,trials", [
+    (0.2, 0.2, 2),    # alpha = 1 overshoots: bracket [0, 1], the cubic lands on the minimum
+    (30.0, 4.0, 3),   # too short: the cubic's minimum (30) lies beyond 4 alpha, so 1 -> 2 -> 4
+    (1.5, 1.0, 1),    # alpha = 1 already satisfies strong Wolfe
+])
+def test_line_search_steps_on_a_quadratic(amin, alpha, trials):
+    """The bracketing and zoom rules on phi(t) = (t - amin)^2, where the cubic
+    through two points with their slopes is exact, so each trial is predictable:
+    the accepted step and the number of trials are pinned."""
+    phi = lambda t: ((t - amin) ** 2, 2 * (t - amin), t)
+    a, E, d, _, n = line_search(phi, amin ** 2, -2 * amin)
+    assert abs(a - alpha) < 1e-12 and n == trials
+    assert wolfe_ok(a, E, d, amin ** 2, -2 * amin)
+
+
 def test_minimization_decreases_energy(small):
     d, o = small
     hist, a = minimize(o, d["a0"], n_steps=8)
