@@ -206,3 +206,26 @@ def test_water576_mixed_vs_fp64_path():
     assert dE < E_TOL
     assert dg <= G_TOL
     f.close()
+
+
+@pytest.mark.xfail(strict=False, reason="open question: whether the float-pair FFT butterflies "
+                   "keep float-pair accuracy under the compiler's FMA contraction")
+@pytest.mark.parametrize("which", ["small", "odd"])
+def test_mixed_potential_at_float_pair_accuracy(which, cases):
+    """The potential of the mixed path (float-pair half-spectrum transforms,
+    Slater exchange, v_ext) against the oracle's potential of the same density:
+    the GPU's own rho is read back exactly, so the difference is the potential
+    arithmetic alone.  Float-pair accuracy leaves about 1e-13 of max|v|;
+    butterflies at FP32 accuracy would leave about 1e-8."""
+    torch = _torch()
+    d, o, s = cases[which]
+    s.energy_grad(torch.tensor(d["a0"], device="cuda"))
+    torch.cuda.synchronize()
+    s.check()
+    rho = s.get_array("rho").reshape(tuple(o.n))
+    v = s.get_array("vtot").reshape(tuple(o.n))
+    _, vx = o.lda_x(rho)
+    vref = o.reference()["vext"] + o.hartree_potential(rho) + vx
+    err = float(np.abs(v - vref).max() / np.abs(vref).max())
+    print(f"{which}: potential error {err:.2e} of max|v|")
+    assert err < 1e-11, f"potential error {err:.2e} of max|v|"
