@@ -162,6 +162,15 @@ def config_water576():
                      rcut_ang=3.5, a_sigma=0.01, seed=2)
 
 
+def config_water75():
+    """75 water-like units (225 atoms), M=600, N=300, 64^3 grid over a 13.13 A
+    box (the water32 density), r_c = 3.5 A, A_ov ~ N(0, 0.02) (seed 5): the
+    largest case the CPU oracle evaluates in seconds that still spans several
+    orbital chunks of 128 and large dense products."""
+    return water_box(lattice=(5, 5, 3), box_ang=13.13, grid=(64, 64, 64),
+                     rcut_ang=3.5, a_sigma=0.02, seed=5)
+
+
 def tiny(grid=(16, 16, 16), seed=7):
     """2 atoms with 2 functions each in a 4 A box: brute-force sized."""
     return random_atoms(n_atoms=2, box_ang=4.0, grid=grid, a_sigma=0.1,

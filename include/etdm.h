@@ -78,9 +78,15 @@ typedef struct {
   double gamma;      /* Eq. 33 mixing (0.25) */
   double beta0;      /* beta before any step exists (1.0) */
   int32_t device;    /* CUDA device ordinal */
+  int32_t dense_blocks; /* grid of the cooperative dense kernels: 0 picks it
+                           from the largest product (every SM for large
+                           systems); n > 0 fixes it (at most the co-resident
+                           limit), which moves products onto 64 x 64 output
+                           tiles once they have four per block */
 } etdm_options;
 
-/* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1). */
+/* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1,
+ * automatic dense grid). */
 void etdm_default_options(etdm_options *opt);
 
 /* Build everything that does not depend on A (Sec. 2, Eq. 4-6): grid basis
@@ -172,7 +178,9 @@ enum {
                                  (i32, groups + 1 entries, the last = n_tiles) */
   ETDM_ARR_VGROUP_NU = 19,    /* mixed precision: functions in each V group's union
                                  list (i32, one per group) */
-  ETDM_NARR = 20              /* number of array ids */
+  ETDM_ARR_DOUBLINGS = 20,    /* [1] i32 doubling steps j of the last evaluation's
+                                 exp (|A_ov A_ov^T|_F / 4^j <= 1) */
+  ETDM_NARR = 21              /* number of array ids */
 };
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);
 int etdm_get_array(etdm_handle *h, int32_t which, void *host_dst,
@@ -210,19 +218,29 @@ const char *etdm_last_error(const etdm_handle *h);
  *   g_dev  [n]      gradient
  *   s_dev  [m*n]    steps s_i = a_(i+1) - a_i, oldest (i = 0) to newest
  *   y_dev  [m*n]    gradient changes y_i; every pair needs y_i . s_i > 0
- *   h0_dev [n]      diagonal initial inverse Hessian (e.g. the Eq. 33
- *                   preconditioner, etdm_precondition applied to ones)
+ *   h0_dev [n]      diagonal initial inverse Hessian (any positive diagonal)
  *   p_dev  [n]      output direction (may not alias the inputs)
  * Limits: 0 <= m <= 16 and 0 <= n <= 2^40; larger m returns
  * ETDM_ERR_INVALID_ARG with a message for etdm_last_error(NULL).  The first
  * call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call clears the array's barrier words and
- * shares the array, so calls that overlap on the GPU (two streams or host
- * threads at once) race.  Asynchronous on `stream`. */
+ * before any stream capture.  Every call clears the array's barrier and
+ * status words and shares the array, so calls that overlap on the GPU (two
+ * streams or host threads at once) race.  Asynchronous on `stream`: a failure
+ * on the device (a grid barrier that gave up, a pair with y . s <= 0) leaves
+ * p_dev incomplete and is reported by etdm_lbfgs_direction_noalloc_status. */
 int etdm_lbfgs_direction_noalloc(const double *g_dev, const double *s_dev,
                                  const double *y_dev, int32_t m, int64_t n,
                                  const double *h0_dev, double *p_dev, void *stream);
+
+/* Status of the last etdm_lbfgs_direction_noalloc call on the current device:
+ * waits for `stream` (the stream that call ran on), reads the scratch array's
+ * status word into host memory without allocating, and returns ETDM_OK,
+ * ETDM_ERR_TIMEOUT (a bounded grid barrier gave up) or ETDM_ERR_NUMERIC (a
+ * pair without positive finite curvature), with a message for
+ * etdm_last_error(NULL).  The word keeps its value until the next direction
+ * call clears it. */
+int etdm_lbfgs_direction_noalloc_status(void *stream);
 
 /* Release all device memory of h (NULL is a no-op). */
 void etdm_free(etdm_handle *h);

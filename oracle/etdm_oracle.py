@@ -270,12 +270,22 @@ class Oracle:
         return -0.75 * cx * r * r13, -cx * r13
 
     # ---- density and Hamiltonian matrix (Eq. 2, Eq. 11-12) ------------------
+    @staticmethod
+    def density_plane(Xp, D):
+        """rho at the points of one x-plane: sum_{mu,nu} chi_mu D_mu,nu chi_nu."""
+        return np.einsum("pa,pa->p", Xp @ D, Xp)
+
+    @staticmethod
+    def potential_plane(Xp, vp):
+        """One x-plane's part of sum_r chi_mu(r) v(r) chi_nu(r) (without dV)."""
+        return Xp.T @ (vp[:, None] * Xp)
+
     def density(self, D):
         """rho(r) = sum_{mu,nu} chi_mu(r) D_mu,nu chi_nu(r)."""
         out = np.empty(self.G)
         per = int(self.n[1] * self.n[2])
         for i, Xp in self._planes():
-            out[i * per:(i + 1) * per] = np.einsum("pa,pa->p", Xp @ D, Xp)
+            out[i * per:(i + 1) * per] = self.density_plane(Xp, D)
         return out.reshape(tuple(self.n))
 
     def potential_matrix(self, v):
@@ -284,7 +294,7 @@ class Oracle:
         per = int(self.n[1] * self.n[2])
         vf = v.reshape(-1)
         for i, Xp in self._planes():
-            Vm += Xp.T @ (vf[i * per:(i + 1) * per, None] * Xp)
+            Vm += self.potential_plane(Xp, vf[i * per:(i + 1) * per])
         return Vm * self.dV
 
     # ---- reference orbitals -------------------------------------------------

@@ -208,6 +208,7 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
     if (opt->lbfgs_m < 1 || opt->lbfgs_m > 16) bad("lbfgs_m must be in [1, 16]");
     if (!(opt->gamma >= 0.0 && opt->gamma <= 1.0)) bad("gamma must be in [0, 1]");
     if (!(opt->beta0 > 0.0)) bad("beta0 must be positive");
+    if (opt->dense_blocks < 0) bad("dense_blocks must be >= 0");
   }
 }
 
@@ -556,6 +557,12 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     auto tiles = [](long m, long n) { return ((m + 7) / 8) * ((n + 15) / 16); };
     const long mt = std::max({tiles(N, N), tiles(N, V), tiles(V, N), tiles(M, N), tiles(M, M)});
     h->coop_blocks = mt <= 8 ? 1 : (int)std::min<long>(h->num_sms, mt);
+    if (o.dense_blocks > 0) {
+      if (o.dense_blocks > bps * h->num_sms)
+        throw Fail{ETDM_ERR_INVALID_ARG, "dense_blocks exceeds the co-resident limit (" +
+                                             std::to_string(bps * h->num_sms) + ")"};
+      h->coop_blocks = o.dense_blocks;
+    }
   }
   int bpl = 0;
   if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
@@ -666,6 +673,7 @@ void etdm_default_options(etdm_options *opt) {
   opt->gamma = 0.25;
   opt->beta0 = 1.0;
   opt->device = 0;
+  opt->dense_blocks = 0;
 }
 
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {
@@ -907,6 +915,7 @@ int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
     case ETDM_ARR_TILE_NU_TC: return h->d_nu_tc ? (int64_t)h->n_tiles_tc * 4 : 0;
     case ETDM_ARR_VGROUP_T0: return h->d_vg_t0 ? ((int64_t)h->n_vg + 1) * 4 : 0;
     case ETDM_ARR_VGROUP_NU: return h->d_vg_nu ? (int64_t)h->n_vg * 4 : 0;
+    case ETDM_ARR_DOUBLINGS: return 4;
     default: return -1;
   }
 }
@@ -960,6 +969,7 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_TILE_NU_TC: src = h->d_nu_tc; break;
       case ETDM_ARR_VGROUP_T0: src = h->d_vg_t0; break;
       case ETDM_ARR_VGROUP_NU: src = h->d_vg_nu; break;
+      case ETDM_ARR_DOUBLINGS: src = h->d_flags + FLAG_J; break;
     }
     if (want > 0) CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
   } catch (const Fail &f) {

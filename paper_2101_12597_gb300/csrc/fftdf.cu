@@ -34,42 +34,46 @@ struct dcx {
   float2 re, im;
 };
 
+// Every operation below is an explicit round-to-nearest intrinsic: the
+// compiler may not contract a product and a sum into one fused operation,
+// which would break the error-free transformations (for a b - c d, fusing the
+// TwoSum's p - q into fma(a, b, -q) would leave the product at FP32 accuracy).
 __device__ __forceinline__ float2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return make_float2(s, (a - (s - bb)) + (b - bb));
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
 __device__ __forceinline__ float2 fdf_add(float2 a, float2 b) {
   const float2 s = two_sum(a.x, b.x);
-  const float e = s.y + (a.y + b.y);
-  const float h = s.x + e;
-  return make_float2(h, e - (h - s.x));
+  const float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s.x, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s.x)));
 }
 __device__ __forceinline__ float2 fdf_neg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 fdf_mul(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  float e = fmaf(a.x, b.x, -p);
-  e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
-  const float h = p + e;
-  return make_float2(h, e - (h - p));
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
 }
 // a b - c d, one renormalization
 __device__ __forceinline__ float2 fdf_dot_sub(float2 a, float2 b, float2 c, float2 d) {
-  const float p = a.x * b.x, q = c.x * d.x;
-  const float ep = fmaf(a.x, b.x, -p), eq = fmaf(c.x, d.x, -q);
+  const float p = __fmul_rn(a.x, b.x), q = __fmul_rn(c.x, d.x);
+  const float ep = __fmaf_rn(a.x, b.x, -p), eq = __fmaf_rn(c.x, d.x, -q);
   const float2 s = two_sum(p, -q);
-  float e = s.y + (ep - eq);
-  e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
-  e = fmaf(-c.x, d.y, fmaf(-c.y, d.x, e));
-  const float h = s.x + e;
-  return make_float2(h, e - (h - s.x));
+  float e = __fadd_rn(s.y, __fsub_rn(ep, eq));
+  e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e));
+  e = __fmaf_rn(-c.x, d.y, __fmaf_rn(-c.y, d.x, e));
+  const float h = __fadd_rn(s.x, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s.x)));
 }
 // a b + c d, one renormalization
 __device__ __forceinline__ float2 fdf_dot_add(float2 a, float2 b, float2 c, float2 d) {
   return fdf_dot_sub(a, b, fdf_neg(c), d);
 }
 __device__ __forceinline__ float2 fdf_scale2(float2 a, float s) {  // s a power of two
-  return make_float2(a.x * s, a.y * s);
+  return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s));
 }
 
 __device__ __forceinline__ dcx cx_ld(float4 v) {
@@ -297,7 +301,8 @@ __global__ void __launch_bounds__(kDfThreads, 4) xpois_kernel(DfArgs a) {
 __device__ __forceinline__ float2 fdf_cbrt(float2 r) {
   if (!(r.x > 0.f)) return make_float2(0.f, 0.f);
   const float y = cbrtf(r.x);
-  const float2 yy = make_float2(y * y, fmaf(y, y, -y * y));  // y^2 exactly
+  const float y2 = __fmul_rn(y, y);
+  const float2 yy = make_float2(y2, __fmaf_rn(y, y, -y2));  // y^2 exactly
   const float2 y3 = fdf_mul(yy, make_float2(y, 0.f));
   const float2 res = fdf_add(y3, fdf_neg(r));       // y^3 - r
   const float corr = res.x / (3.f * y * y);          // Newton: y - (y^3 - r) / (3 y^2)

@@ -200,30 +200,32 @@ __device__ __forceinline__ uint16_t bf16_bits(float x) {
 }
 
 // ---- float-pair arithmetic and exact slicing -----------------------------------
+// (explicit round-to-nearest intrinsics throughout: a product contracted with
+// the following sum would break the error-free transformations)
 // product of two float pairs (hi + lo): exact product by FMA, then renormalization
 __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  const float e = fmaf(a.x, b.x, -p);
-  const float t = e + fmaf(a.x, b.y, a.y * b.x);
-  const float s = p + t;
-  return make_float2(s, t - (s - p));
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.x, -p);
+  const float t = __fadd_rn(e, __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+  const float s = __fadd_rn(p, t);
+  return make_float2(s, __fsub_rn(t, __fsub_rn(s, p)));
 }
 
 // the same product left unnormalized (hi = fl(a.x b.x), |lo| <= 2 ulp(hi)), as
 // slice4 takes it
 __device__ __forceinline__ float2 df_mul_raw(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  return make_float2(p, fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x));
+  const float p = __fmul_rn(a.x, b.x);
+  return make_float2(p, __fadd_rn(__fmaf_rn(a.x, b.x, -p), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x))));
 }
 
 // sum of two float pairs with an exact TwoSum of the high parts
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  const float s = a.x + b.x;
-  const float bb = s - a.x;
-  const float e = (a.x - (s - bb)) + (b.x - bb);
-  const float t = e + a.y + b.y;
-  const float h = s + t;
-  return make_float2(h, t - (h - s));
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  const float t = __fadd_rn(__fadd_rn(e, a.y), b.y);
+  const float h = __fadd_rn(s, t);
+  return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
 }
 
 // 2^k for -126 <= k <= 127, built from its bits (exact)

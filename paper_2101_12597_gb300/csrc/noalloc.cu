@@ -11,8 +11,11 @@
 //
 // The scratch array lives in every GPU that loads the library until the
 // process exits.  All calls share it and it keeps the last call's contents:
-// the barrier words are cleared at the start of each call, and calls that
-// overlap on the GPU (two streams, or two host threads) race on it.
+// the barrier words and the status word are cleared at the start of each
+// call, and calls that overlap on the GPU (two streams, or two host threads)
+// race on it.  The status word records a device-side failure of the last call
+// (a grid barrier that gave up, or a pair without positive curvature);
+// etdm_lbfgs_direction_noalloc_status reads it without allocating.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <stdint.h>
@@ -64,6 +67,9 @@ __device__ double na_dot(const NaArgs &a, double part, bool *ok) {
 
 // p = -H g by the two-loop recursion over pairs oldest (0) .. newest (m-1),
 // with the diagonal initial inverse Hessian h0; p doubles as the work vector.
+// A pair whose curvature y.s is not positive and finite makes the direction
+// meaningless: the kernel records ETDM_ERR_NUMERIC in the status word and
+// returns (every block sees the same sum, so all of them stop together).
 __global__ void __launch_bounds__(kNaThreads) lbfgs_noalloc_kernel(NaArgs a) {
   const long n = a.n;
   const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,6 +82,10 @@ __global__ void __launch_bounds__(kNaThreads) lbfgs_noalloc_kernel(NaArgs a) {
     for (long e = gtid; e < n; e += gstride) part += yi[e] * si[e];
     double ys = na_dot(a, part, &ok);
     if (!ok) return;
+    if (!(ys > 0.0) || isinf(ys)) {
+      if (gtid == 0) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+      return;
+    }
     rho[i] = 1.0 / ys;
   }
   for (long e = gtid; e < n; e += gstride) a.p[e] = a.g[e];
@@ -123,6 +133,40 @@ int na_fail(int code, const std::string &msg) {
 
 using namespace etdm;
 
+namespace etdm {
+namespace {
+
+// The device's scratch address and launch size, looked up once per device with
+// that device current (the array's host-side name is not a device address).
+int na_device(NaDevice **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaDevices)
+    return na_fail(ETDM_ERR_CUDA, "no current CUDA device");
+  NaDevice *d = &g_na[dev];
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!d->ready) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return na_fail(ETDM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    int sms = 0, bps = 0, coop = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, lbfgs_noalloc_kernel, kNaThreads,
+                                                      0) != cudaSuccess ||
+        !coop || bps < 1)
+      return na_fail(ETDM_ERR_CUDA, "cannot size the cooperative two-loop kernel");
+    d->scratch = (unsigned char *)ptr;
+    d->blocks_max = std::min(kNaMaxBlocks, sms * bps);
+    d->ready = true;
+  }
+  *out = d;
+  return ETDM_OK;
+}
+
+}  // namespace
+}  // namespace etdm
+
 extern "C" int etdm_lbfgs_direction_noalloc(const double *g_dev, const double *s_dev,
                                             const double *y_dev, int32_t m, int64_t n,
                                             const double *h0_dev, double *p_dev,
@@ -134,34 +178,11 @@ extern "C" int etdm_lbfgs_direction_noalloc(const double *g_dev, const double *s
   if (n == 0) return ETDM_OK;
   if (!g_dev || !h0_dev || !p_dev || (m > 0 && (!s_dev || !y_dev)))
     return na_fail(ETDM_ERR_INVALID_ARG, "g, h0, p (and s, y when m > 0) are required");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaDevices)
-    return na_fail(ETDM_ERR_CUDA, "no current CUDA device");
-  NaDevice *d = &g_na[dev];
-  {
-    // once per device, with that device current: the device address of the
-    // file-scope scratch array (its host-side name is not a device address)
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!d->ready) {
-      void *ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess)
-        return na_fail(ETDM_ERR_CUDA,
-                       std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      int sms = 0, bps = 0, coop = 0;
-      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, lbfgs_noalloc_kernel, kNaThreads,
-                                                        0) != cudaSuccess ||
-          !coop || bps < 1)
-        return na_fail(ETDM_ERR_CUDA, "cannot size the cooperative two-loop kernel");
-      d->scratch = (unsigned char *)ptr;
-      d->blocks_max = std::min(kNaMaxBlocks, sms * bps);
-      d->ready = true;
-    }
-  }
+  NaDevice *d = nullptr;
+  int rc = na_device(&d);
+  if (rc != ETDM_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  // barrier words and error flag must start at zero
+  // barrier words and the status word must start at zero
   cudaError_t e = cudaMemsetAsync(d->scratch, 0, 256, s);
   if (e != cudaSuccess)
     return na_fail(ETDM_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
@@ -178,5 +199,28 @@ extern "C" int etdm_lbfgs_direction_noalloc(const double *g_dev, const double *s
                                   args, 0, s);
   if (e != cudaSuccess)
     return na_fail(ETDM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return ETDM_OK;
+}
+
+extern "C" int etdm_lbfgs_direction_noalloc_status(void *stream) {
+  NaDevice *d = nullptr;
+  int rc = na_device(&d);
+  if (rc != ETDM_OK) return rc;
+  // wait for the calls queued on `stream`, then copy the status word into a
+  // local (a pageable copy: no pinned staging buffer, nothing allocated)
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  int word = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&word, d->scratch + 64, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess)
+    return na_fail(ETDM_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+  if (word == ETDM_ERR_TIMEOUT)
+    return na_fail(ETDM_ERR_TIMEOUT,
+                   "the last allocation-free direction gave up at a grid barrier "
+                   "(blocks not co-resident?); its output is incomplete");
+  if (word == ETDM_ERR_NUMERIC)
+    return na_fail(ETDM_ERR_NUMERIC,
+                   "the last allocation-free direction met a pair with y.s <= 0 (or not "
+                   "finite); its output is incomplete");
+  if (word != 0) return na_fail(word, "the last allocation-free direction failed on the device");
   return ETDM_OK;
 }

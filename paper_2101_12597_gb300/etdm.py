@@ -27,7 +27,7 @@ ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "eterms": (13, np.float64), "beta": (14, np.float64),
           "tile_ptr_tc": (15, np.int32), "tile_keys_tc": (16, np.int32),
           "tile_nu_tc": (17, np.int32), "vgroup_t0": (18, np.int32),
-          "vgroup_nu": (19, np.int32)}
+          "vgroup_nu": (19, np.int32), "doublings": (20, np.int32)}
 DIM_NAMES = ["M", "N", "V", "G", "n_tiles", "entries", "max_list", "tx", "ty",
              "tz", "sum_npt2", "precision"]
 
@@ -36,7 +36,7 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_lbfgs_reset", "etdm_minimize", "etdm_check", "etdm_layout",
            "etdm_array_bytes", "etdm_get_array", "etdm_set_profiling",
            "etdm_stage_times", "etdm_last_error", "etdm_free",
-           "etdm_lbfgs_direction_noalloc"]
+           "etdm_lbfgs_direction_noalloc", "etdm_lbfgs_direction_noalloc_status"]
 STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
 
 
@@ -59,7 +59,8 @@ class EtdmOptions(ctypes.Structure):
                 ("lbfgs_m", ctypes.c_int32),
                 ("gamma", ctypes.c_double),
                 ("beta0", ctypes.c_double),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32),
+                ("dense_blocks", ctypes.c_int32)]
 
 
 _lib = None
@@ -96,6 +97,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.etdm_stage_times.argtypes = [P, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.etdm_lbfgs_direction_noalloc.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int64,
                                                  P, P, P]
+    lib.etdm_lbfgs_direction_noalloc_status.argtypes = [P]
     lib.etdm_last_error.argtypes = [P]
     lib.etdm_last_error.restype = ctypes.c_char_p
     lib.etdm_free.argtypes = [P]
@@ -163,7 +165,7 @@ class ETDM:
     """One system on one GPU: the handle of etdm_init_basis."""
 
     def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
-                 device=0):
+                 device=0, dense_blocks=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
@@ -196,6 +198,7 @@ class ETDM:
         o.gamma = gamma
         o.beta0 = beta0
         o.device = device
+        o.dense_blocks = dense_blocks
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -328,28 +331,75 @@ class ETDM:
             pass
 
 
+def _storage_span(t):
+    """Byte range [lo, hi) of the storage a tensor's elements occupy."""
+    lo = t.data_ptr()
+    return lo, lo + t.numel() * t.element_size()
+
+
+def _overlaps(x, y):
+    (a0, a1), (b0, b1) = _storage_span(x), _storage_span(y)
+    return a0 < b1 and b0 < a1
+
+
+def _noalloc_checks(g, S, Y, h0, out, stream):
+    """(m, n) after every check an allocation-free direction call needs before
+    its pointers reach the library: shapes and device (_noalloc_shapes), an
+    output that overlaps no input, and a stream on the tensors' device."""
+    m, n = _noalloc_shapes(g, S, Y, h0, out)
+    for name, t in (("g", g), ("h0", h0), ("S", S), ("Y", Y)):
+        if t is not None and t.numel() and out.numel() and _overlaps(out, t):
+            raise ValueError(f"out may not overlap {name}")
+    if stream is not None and stream.device != g.device:
+        raise ValueError(f"stream is on {stream.device}, the tensors on {g.device}")
+    return m, n
+
+
 def lbfgs_direction_noalloc(g, S, Y, h0, out=None, stream=None):
     """p = -H g by the L-BFGS two-loop recursion over the pairs S[i], Y[i]
     (oldest first) with the diagonal initial inverse Hessian h0, through the
     allocation-free entry point: for callers that cannot allocate device
-    memory where they need a direction.  All tensors are contiguous CUDA FP64;
-    S and Y have shape (m, n) with m <= 16.  `out` must be preallocated by such
-    callers (here it is created when None)."""
+    memory where they need a direction.  All tensors are contiguous CUDA FP64
+    on one device; S and Y have shape (m, n) with m <= 16; `out` may not
+    overlap the inputs.  `out` must be preallocated by such callers (here it
+    is created when None).  The call runs with g's device current, on
+    `stream` (default: that device's current stream); a device-side failure
+    is reported by lbfgs_direction_noalloc_status(stream)."""
     import torch
     lib = load_library()
     if not (isinstance(g, torch.Tensor) and g.is_cuda):
         raise ValueError("g: expected a CUDA tensor")
     out = torch.empty_like(g) if out is None else out
-    m, n = _noalloc_shapes(g, S, Y, h0, out)
-    rc = lib.etdm_lbfgs_direction_noalloc(
-        ctypes.c_void_p(g.data_ptr()),
-        ctypes.c_void_p(S.data_ptr()) if m else None,
-        ctypes.c_void_p(Y.data_ptr()) if m else None,
-        m, n, ctypes.c_void_p(h0.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-        _stream_ptr(stream))
+    m, n = _noalloc_checks(g, S, Y, h0, out, stream)
+    with torch.cuda.device(g.device):
+        st = stream if stream is not None else torch.cuda.current_stream(g.device)
+        rc = lib.etdm_lbfgs_direction_noalloc(
+            ctypes.c_void_p(g.data_ptr()),
+            ctypes.c_void_p(S.data_ptr()) if m else None,
+            ctypes.c_void_p(Y.data_ptr()) if m else None,
+            m, n, ctypes.c_void_p(h0.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(st.cuda_stream))
     if rc != ETDM_OK:
         raise EtdmError(rc, lib.etdm_last_error(None).decode())
     return out
+
+
+def lbfgs_direction_noalloc_status(device=None, stream=None):
+    """Waits for `stream` (default: the device's current stream) and raises
+    EtdmError when the last allocation-free direction on `device` failed on
+    the GPU (a grid barrier that gave up, a pair with y.s <= 0); its output is
+    then incomplete."""
+    import torch
+    lib = load_library()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None \
+        else torch.device(device)
+    if stream is not None and stream.device != dev:
+        raise ValueError(f"stream is on {stream.device}, not {dev}")
+    with torch.cuda.device(dev):
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        rc = lib.etdm_lbfgs_direction_noalloc_status(ctypes.c_void_p(st.cuda_stream))
+    if rc != ETDM_OK:
+        raise EtdmError(rc, lib.etdm_last_error(None).decode())
 
 
 def energy_function():

@@ -125,3 +125,20 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
     c.start()
     assert c.stop() is None
     assert list(tmp_path.iterdir()) == []  # the temporary file is gone
+
+
+def test_oracle_plane_sample_is_the_oracles_grid_work():
+    """The bounded sample the CPU baseline takes of the 192^3 water box: one
+    x-plane of the oracle's own density and potential-matrix code.  On a small
+    system the per-plane pieces add up to the oracle's whole-grid results."""
+    import numpy as np
+    import etdm_synth as synth
+    d = synth.config_small_molecule()
+    o, D, v = bench._plane_sample_setup(d)
+    assert bench._plane_sample(o, D, v, 3) > 0.0
+    per = int(o.n[1] * o.n[2])
+    rho = np.concatenate([o.density_plane(o.basis_plane(i), D) for i in range(int(o.n[0]))])
+    np.testing.assert_allclose(rho, o.density(D).reshape(-1), rtol=1e-13, atol=1e-15)
+    Vm = sum(o.potential_plane(o.basis_plane(i), v[i * per:(i + 1) * per])
+             for i in range(int(o.n[0]))) * o.dV
+    np.testing.assert_allclose(Vm, o.potential_matrix(v), rtol=1e-12, atol=1e-14)

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 from paper_2101_12597_gb300 import etdm
-from paper_2101_12597_gb300.etdm import _noalloc_shapes, _require
+from paper_2101_12597_gb300.etdm import _noalloc_checks, _noalloc_shapes, _require
 
 CPU = torch.device("cpu")
 
@@ -57,6 +57,33 @@ def test_noalloc_shapes():
         _noalloc_shapes(g, None, None, _t(n - 1), out)
     with pytest.raises(ValueError, match="out:"):
         _noalloc_shapes(g, None, None, h0, _t(n, dtype=torch.float32))
+
+
+def test_noalloc_output_may_not_overlap_an_input():
+    n = 12
+    buf = _t(3 * n)
+    g, h0 = buf[:n], buf[n:2 * n]
+    S = Y = _t(2, n)
+    assert _noalloc_checks(g, S, Y, h0, buf[2 * n:], None) == (2, n)
+    with pytest.raises(ValueError, match="overlap g"):
+        _noalloc_checks(g, S, Y, h0, g, None)
+    with pytest.raises(ValueError, match="overlap h0"):
+        _noalloc_checks(g, S, Y, h0, buf[n + 1:2 * n + 1], None)
+    with pytest.raises(ValueError, match="overlap S"):
+        _noalloc_checks(g, S, Y, h0, S[1], None)
+
+
+def test_noalloc_stream_must_be_on_the_tensors_device():
+    class Stream:
+        def __init__(self, dev):
+            self.device = torch.device(dev)
+            self.cuda_stream = 0
+
+    n = 6
+    g, h0, out = _t(n), _t(n), _t(n)
+    assert _noalloc_checks(g, None, None, h0, out, Stream("cpu")) == (0, n)
+    with pytest.raises(ValueError, match="stream is on meta"):
+        _noalloc_checks(g, None, None, h0, out, Stream("meta"))
 
 
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU behaviour")

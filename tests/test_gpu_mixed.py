@@ -208,15 +208,14 @@ def test_water576_mixed_vs_fp64_path():
     f.close()
 
 
-@pytest.mark.xfail(strict=False, reason="open question: whether the float-pair FFT butterflies "
-                   "keep float-pair accuracy under the compiler's FMA contraction")
 @pytest.mark.parametrize("which", ["small", "odd"])
 def test_mixed_potential_at_float_pair_accuracy(which, cases):
     """The potential of the mixed path (float-pair half-spectrum transforms,
     Slater exchange, v_ext) against the oracle's potential of the same density:
     the GPU's own rho is read back exactly, so the difference is the potential
     arithmetic alone.  Float-pair accuracy leaves about 1e-13 of max|v|;
-    butterflies at FP32 accuracy would leave about 1e-8."""
+    butterflies at FP32 accuracy would leave about 1e-8 (the helpers use
+    explicit-rounding intrinsics, so the compiler cannot fuse them into that)."""
     torch = _torch()
     d, o, s = cases[which]
     s.energy_grad(torch.tensor(d["a0"], device="cuda"))
@@ -229,3 +228,78 @@ def test_mixed_potential_at_float_pair_accuracy(which, cases):
     err = float(np.abs(v - vref).max() / np.abs(vref).max())
     print(f"{which}: potential error {err:.2e} of max|v|")
     assert err < 1e-11, f"potential error {err:.2e} of max|v|"
+
+
+@pytest.fixture(scope="module")
+def water75():
+    """The oracle's evaluation of the 75-unit water box (M = 600, N = 300,
+    64^3 grid), shared by the cases below."""
+    d = synth.config_water75()
+    o = Oracle(d)
+    E, g, ex = o.energy_grad(d["a0"], want=True)
+    return d, o, E, g, ex
+
+
+@pytest.mark.parametrize("precision,dense_blocks", [("fp64", 0), ("fp64", 4),
+                                                    ("mixed", 0), ("mixed", 4)])
+def test_water75_against_oracle(water75, precision, dense_blocks):
+    """Both GPU paths at a size that runs the density pass over three orbital
+    chunks (N = 300 > 128) and, with the dense grid fixed at 4 blocks, puts
+    every product of the dense chains on the 64 x 64 output tiles (the
+    automatic grid keeps them on 8 x 16 tiles): energy, gradient, density and
+    the Hamiltonian (its grid part V on the mixed path) element by element
+    against the oracle."""
+    torch = _torch()
+    from paper_2101_12597_gb300.etdm import ETDM
+    d, o, E_ref, g_ref, ex = water75
+    s = ETDM(d, precision=precision, dense_blocks=dense_blocks)
+    E, g = s.energy_grad(torch.tensor(d["a0"], device="cuda"))
+    torch.cuda.synchronize()
+    s.check()
+    dE = abs(float(E.item()) - E_ref)
+    dg = _grad_err(g.cpu().numpy(), g_ref)
+    rho = s.get_array("rho").reshape(tuple(o.n))
+    drho = float(np.abs(rho - ex["rho"]).max() / ex["rho"].max())
+    M = o.M
+    H = s.get_array("H").reshape(M, M)
+    Href = ex["H"] - (s.get_array("T").reshape(M, M) if precision == "mixed" else 0.0)
+    dH = float(np.abs(H - Href).max() / np.abs(Href).max())
+    print(f"water75 {precision} dense_blocks={dense_blocks}: |dE|={dE:.3e} Ha "
+          f"grad err={dg:.3e} rho err={drho:.2e} H err={dH:.2e}")
+    assert dE < E_TOL
+    assert dg <= G_TOL
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    assert drho < tol and dH < tol
+    U = s.get_array("Uocc").reshape(M, o.N)
+    assert np.abs(U.T @ U - np.eye(o.N)).max() < 1e-11
+    s.close()
+
+
+def test_autograd_backward_water32_against_oracle_differences():
+    """The autograd Function on the mixed path (water32: M = 256, N = 128):
+    its backward against central differences (h = 1e-5) of the oracle's
+    energy on 32 seeded entries of A_ov, within the gradient bar."""
+    torch = _torch()
+    from paper_2101_12597_gb300.etdm import energy_function
+    d = synth.config_water32()
+    o = Oracle(d)
+    s = _solver(d)
+    a = torch.tensor(d["a0"], device="cuda", requires_grad=True)
+    E = energy_function().apply(a, s)
+    E.backward()
+    g = a.grad.cpu().numpy()
+    rng = np.random.default_rng(32)
+    N, V = d["a0"].shape
+    idx = rng.choice(N * V, size=32, replace=False)
+    h = 1e-5
+    fd = []
+    for k in idx:
+        ap, am = d["a0"].copy(), d["a0"].copy()
+        ap.flat[k] += h
+        am.flat[k] -= h
+        fd.append((o.energy(ap) - o.energy(am)) / (2 * h))
+    fd = np.array(fd)
+    err = float(np.abs(g.flat[idx] - fd).max() / np.abs(g).max())
+    print(f"water32 autograd vs oracle central differences: {err:.2e} of max|g|")
+    assert err <= G_TOL
+    s.close()

@@ -575,6 +575,66 @@ def test_tile_lists_cover_nonzero_basis_values(ragged, tile):
         assert set((keys // 512).tolist()) == nonzero
 
 
+def _brute_force_images(d, tile, t):
+    """Per (mu, image n) of a tile, written without the oracle: the squared
+    distance from every tile point to the image centre d_mu + n L, over all
+    n in [-3, 3]^3 (with r_c < 2 min L no farther image can reach a point of
+    the cell), as (r2 [mu, image, point], rc2 [mu], image list)."""
+    L = np.asarray(d["box"], dtype=np.float64)
+    n = np.asarray(d["grid"])
+    c = np.asarray(d["pos"], dtype=np.float64)[np.asarray(d["bf_atom"])]
+    rc = np.asarray(d["bf_rcut"], dtype=np.float64)
+    nb = [-(-int(n[a]) // tile[a]) for a in range(3)]
+    bx, rem = divmod(t, nb[1] * nb[2])
+    by, bz = divmod(rem, nb[2])
+    idx = [np.arange(b * tile[a], min((b + 1) * tile[a], int(n[a])))
+           for a, b in enumerate((bx, by, bz))]
+    pts = np.stack(np.meshgrid(*[idx[a] * (L[a] / n[a]) for a in range(3)],
+                               indexing="ij"), -1).reshape(-1, 3)
+    imgs = np.array([(i, j, k) for i in range(-3, 4) for j in range(-3, 4)
+                     for k in range(-3, 4)])
+    centres = c[:, None, :] + (imgs * L)[None, :, :]          # [M, 343, 3]
+    diff = pts[None, None, :, :] - centres[:, :, None, :]      # [M, 343, P, 3]
+    r2 = np.einsum("mipa,mipa->mip", diff, diff)
+    return r2, rc * rc, imgs
+
+
+@pytest.mark.parametrize("name,tile", [("tiny", (4, 4, 8)), ("tiny", (4, 4, 4)),
+                                       ("small", (4, 4, 8)), ("ragged", (4, 4, 8))])
+def test_tile_lists_per_image_against_brute_force(name, tile):
+    """Every key (mu, image) of a tile list has a point of the tile strictly
+    inside that image's truncation sphere, and every (mu, image) with such a
+    point is listed: the image part of the lists, which the function-level
+    check above cannot see (a dropped image of a function with another image
+    in the tile, or an extra image whose sphere misses the tile).  Points
+    within 1e-9 relative of a sphere's surface are left out of the decision
+    (rounding order may differ from the oracle's there); they must be rare."""
+    d = {"tiny": synth.tiny, "small": synth.config_small_molecule,
+         "ragged": synth.ragged_water}[name]()
+    o = Oracle(d)
+    nt = o.n_tiles(tile)
+    ties = 0
+    checked = 0
+    for t in range(0, nt, max(1, nt // 40)):
+        keys = set(o.tile_list(tile, t).tolist())
+        r2, rc2, imgs = _brute_force_images(d, tile, t)
+        inside = (r2 < rc2[:, None, None] * (1 - 1e-9)).any(-1)
+        near = (np.abs(r2 - rc2[:, None, None]) <= 1e-9 * rc2[:, None, None]).any(-1)
+        for mu in range(o.M):
+            for k, nimg in enumerate(imgs):
+                key = o.pack_key(mu, tuple(int(x) for x in nimg))
+                if near[mu, k] and not inside[mu, k]:
+                    ties += 1
+                    continue
+                assert (key in keys) == bool(inside[mu, k]), (t, mu, tuple(nimg))
+                checked += 1
+        # nothing listed outside the functions and images enumerated here
+        every = {o.pack_key(mu, tuple(int(x) for x in nimg))
+                 for mu in range(o.M) for nimg in imgs}
+        assert keys <= every
+    assert checked > 0 and ties <= 1e-4 * checked
+
+
 def test_oracle_matches_stored_small_molecule_values(small):
     # stored values come from tests/golden/make_golden.py (oracle only); this
     # guards the oracle against unreviewed arithmetic changes
