@@ -38,6 +38,8 @@ WORKLOADS = {
     "water576": "water576: 1728 atoms, M=4608, N=2304, 192^3 grid, 25 A box, r_c=3.5 A",
     "water32": "water32: 96 atoms, M=256, N=128, 96^3 grid, 9.9 A box, r_c=4 A",
     "small": "small molecule: 8 atoms, M=16, N=4, 32^3 grid, 6.4 A box",
+    "molecules148": "molecules148: 148 molecules of 2-20 atoms (M 4-60), each on its own "
+                    "48^3 grid over a 9.6 A box, r_c=4 A, evaluated as one batch",
 }
 # workloads whose resident operands (basis slices, grids) exceed the 129 MB L2:
 # the timed steps run back to back; the small molecule fits in L2 and flushes it
@@ -48,7 +50,8 @@ LARGE = {"water576", "water32"}
 def workload_system(name):
     import etdm_synth as synth
     return {"water32": synth.config_water32, "small": synth.config_small_molecule,
-            "water576": synth.config_water576}[name]()
+            "water576": synth.config_water576,
+            "molecules148": synth.config_molecules148}[name]()
 
 
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 rate of a GB300 (no measured figure)
@@ -253,6 +256,22 @@ def run_reference(args):
         t = sum(_plane_sample(o, D, v, (args.warmup + k) % n) for k in range(args.steps))
         dt = t * n  # seconds of the K whole evaluations the samples stand for
         sample = PLANE_SAMPLE.format(k=1, n=n, w=w) + " (one x-plane per step)"
+    elif args.workload == "molecules148":
+        # each step: one molecule's oracle evaluation, the molecules in turn
+        # (set-up not timed); the unit is molecule evaluations per second
+        from oracle.etdm_oracle import Oracle
+        n = args.warmup + args.steps
+        os_ = [Oracle(d[k % len(d)]) for k in range(n)]
+        for o in os_:
+            o.reference()
+        for k in range(args.warmup):
+            os_[k].energy_grad(d[k % len(d)]["a0"])
+        t0 = time.perf_counter()
+        for k in range(args.warmup, n):
+            os_[k].energy_grad(d[k % len(d)]["a0"])
+        dt = time.perf_counter() - t0
+        sample = (f"each step: 1 oracle energy+gradient evaluation of one molecule of {w}, "
+                  "molecules in turn")
     else:
         from oracle.etdm_oracle import Oracle
         o = Oracle(d)
@@ -517,6 +536,198 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+def run_batch(args):
+    """The batched workload: K L-BFGS steps of one batched minimization of all
+    molecules (each with its own line search), timed back to back; value =
+    molecule energy+gradient evaluations per second.  The plain FP64 path runs
+    each molecule's own launch sequence."""
+    import torch
+
+    from paper_2101_12597_gb300 import build as b
+    from paper_2101_12597_gb300.etdm import ETDMBatch
+
+    world, rank, local = dist_setup(args.gpus)
+    b.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    mols = workload_system(args.workload)
+    n = len(mols)
+    t_setup = time.perf_counter()
+    bt = ETDMBatch(mols, precision="mixed", device=local)
+    t_setup = time.perf_counter() - t_setup
+    a0 = torch.tensor(bt.pack([d["a0"] for d in mols]), device=dev)
+    dims_M = [m.M for m in bt.systems]
+    if args.profile_once:
+        bt.energy_grad(a0)
+        torch.cuda.synchronize()
+        bt.check()
+        print(json.dumps({"profile_once": True, "workload": args.workload}))
+        return
+    # warm-up, then the timed minimization from the start point
+    a = a0.clone()
+    if args.warmup:
+        bt.minimize(a, args.warmup)
+    torch.cuda.synchronize()
+    bt.lbfgs_reset()
+    a = a0.clone()
+    bt.launches()
+    clocks = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    torch.cuda.nvtx.range_push("timed")
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record()
+    E_h, al_h, tr_h = bt.minimize(a, args.steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    clk = clocks.stop()
+    launches = bt.launches()
+    total_ms = ev0.elapsed_time(ev1)
+    evals = int(tr_h.sum())
+    t_max = reduce_max(total_ms, world, dev)
+    all_evals = reduce_sum(evals, world, dev)
+    value = all_evals / (t_max / 1e3)
+
+    # one batched evaluation (graph) at the start point, and its stages timed
+    # one by one (the same kernels launched outside the graph)
+    Eb, _ = bt.energy_grad(a0)
+    torch.cuda.synchronize()
+    reps = 10
+    ev0.record()
+    for _ in range(reps):
+        bt.energy_grad(a0)
+    ev1.record()
+    torch.cuda.synchronize()
+    graph_ms = ev0.elapsed_time(ev1) / reps
+    bt.lib.etdm_set_profiling(bt.h, 1)
+    bt.launches()
+    for _ in range(3):
+        bt.energy_grad(a0)
+    torch.cuda.synchronize()
+    ms = np.zeros(8)
+    cnt = np.zeros(8, dtype=np.int64)
+    import ctypes
+    bt.lib.etdm_stage_times(bt.h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    bt.lib.etdm_set_profiling(bt.h, 0)
+    names = ["dense_fwd", "rho", "potential", "vmat", "dense_rev"]
+    stage = {k: float(ms[i] / max(1, cnt[i])) for i, k in enumerate(names)}
+
+    # end to end through the host-buffer entry point
+    a_host = bt.pack([d["a0"] for d in mols])
+    bt.energy_grad_host(a_host)
+    n_e2e = 10
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        E_run, _ = bt.energy_grad_host(a_host)
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": world * n * n_e2e / e2e_dt, "unit": "evals/s",
+           "h2d_bytes_per_step": 8 * bt.nvar, "d2h_bytes_per_step": 8 * (bt.nvar + n),
+           "evals": n * n_e2e}
+
+    # the plain FP64 path: every molecule on its own launch sequence
+    fp64 = None
+    if not args.no_fp64_compare:
+        ref = ETDMBatch(mols, precision="fp64", device=local)
+        E64, _ = ref.energy_grad_host(a_host)
+        torch.cuda.synchronize()
+        k64 = 3
+        ev0.record()
+        for _ in range(k64):
+            ref.energy_grad(a0)
+        ev1.record()
+        torch.cuda.synchronize()
+        fp64 = {"value": n * k64 / (ev0.elapsed_time(ev1) / 1e3), "unit": "evals/s",
+                "evals_timed": n * k64, "dE_Ha_max": float(np.abs(E_run - E64).max()),
+                "launches_per_batch_eval": None}
+        ref.launches()
+        ref.energy_grad(a0)
+        torch.cuda.synchronize()
+        fp64["launches_per_batch_eval"] = ref.launches()
+        ref.close()
+
+    # roofline of the dominant stage of the batched evaluation
+    peaks, src = measured_peaks()
+    layout = (ctypes.c_int64 * 12)()
+    bt.lib.etdm_layout(bt.h, layout)
+    sum_npt2 = int(layout[10])
+    dom = max(stage, key=lambda k: stage[k])
+    pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
+    if dom in ("rho", "vmat"):
+        ach = 2.0 * sum_npt2 / (stage[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": captured_traffic(f"{dom}_tc_kernel", args.workload),
+                "kernel": f"{dom}_tc_kernel (all molecules in one launch)",
+                "peak_source": f"{src} dense bf16 (sustained)"}
+    elif dom == "potential":
+        # the five half-spectrum passes: each reads and writes the half spectrum
+        # (float-pair complex, 16 B) once; the first reads rho, the last v_ext and
+        # rho and writes v (FP64), v dV (pairs): bytes per grid point
+        G = int(layout[3])
+        nbytes = G * (2 * 5 * 16 * 0.5 + 8 + 3 * 8 + 8 + 8)
+        ach = nbytes / (stage[dom] * 1e-3) / 1e9
+        hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None,
+                "kernel": "potential passes (zfwd, yfft x2, xpois, zinv_pot) over all molecules",
+                "peak_source": f"{src} copy bandwidth"}
+    else:
+        macs = 0.0
+        for m in bt.systems:
+            J = int(m.get_array("doublings")[0])
+            f_, r_ = dense_macs(m.M, m.N, m.V, J)
+            macs += f_ if dom == "dense_fwd" else r_
+        ach = 2.0 * macs / (stage[dom] * 1e-3) / 1e12
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        pair_peak = 152 * 128 * sm_mhz * 1e6 * 2.0 / 12.0 / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": pair_peak, "unit": "TFLOP/s",
+                "frac": ach / pair_peak, "traffic": None,
+                "kernel": f"{dom} batched float-pair chains (one block per molecule)",
+                "peak_source": "derived float-pair multiply-add rate of the FP32 pipes"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32+bf16", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "precision": "mixed",
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (resident basis slices and grids of 148 "
+                         "molecules), steps back to back in one batched minimization",
+                   "molecules": n, "M_range": [min(dims_M), max(dims_M)],
+                   "evals_timed": int(all_evals),
+                   "batched_eval_graph_ms": graph_ms,
+                   "molecule_evals_per_s_graph": n / (graph_ms * 1e-3),
+                   "stage_ms_per_batched_eval": stage, "setup_s": t_setup,
+                   "fp64_path": fp64, "E_sum_Ha": float(np.sum(E_run))},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle.etdm_oracle import Oracle
+        pick = list(range(0, n, 15))
+        t = 0.0
+        for i in pick:
+            o = Oracle(mols[i])
+            o.reference()
+            t0 = time.perf_counter()
+            o.energy_grad(mols[i]["a0"])
+            t += time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": len(pick) / t, "unit": "evals/s", "cores": oracle_threads(),
+            "kind": "oracle",
+            "sample": f"oracle energy+gradient evaluations of {len(pick)} of the {n} molecules "
+                      "(every 15th; set-up not timed)"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,7 +737,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="water576",
                     help="water576 (the largest workload on one GPU: the default), "
-                         "water32, or the 8-atom molecule")
+                         "water32, the 8-atom molecule, or the batch of 148 molecules")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--profile-once", action="store_true",
                     help="set up, run one energy+gradient evaluation, exit (for ncu)")
@@ -534,6 +745,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "molecules148":
+        run_batch(args)
     else:
         run_ours(args)
 

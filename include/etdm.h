@@ -100,8 +100,41 @@ void etdm_default_options(etdm_options *opt);
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt,
                     etdm_handle **out);
 
+/* A batch of n_sys independent systems in one handle (molecules of uneven
+ * size, each in its own cell; Sec. 4.1 evaluates such a set one molecule at a
+ * time).  Every system is set up as by etdm_init_basis (same options); their
+ * variables are packed one after another (etdm_system_layout gives each
+ * system's offset and length), E_dev has n_sys entries, and the entry points
+ * below take the packed vectors.  In mixed precision one evaluation of all
+ * systems is one captured CUDA graph (batched dense chains, density, potential
+ * and V passes), and etdm_minimize advances every system with its own line
+ * search, one trial point per system per round; with ETDM_PREC_FP64 every
+ * system runs its own launch sequence (the plain path).  Errors: those of
+ * etdm_init_basis, with the failing system's index in the message. */
+int etdm_init_batch(const etdm_system *sys, int32_t n_sys, const etdm_options *opt,
+                    etdm_handle **out);
+
+/* Systems in a handle (1 for etdm_init_basis handles, 0 for NULL). */
+int32_t etdm_num_systems(const etdm_handle *h);
+
+/* Offset and length (N_i V_i) of system `sys`'s variables in the packed a, g
+ * and p vectors of a batch (system 0 of a single handle: 0 and N V). */
+int etdm_system_layout(const etdm_handle *h, int32_t sys, int64_t *offset, int64_t *len);
+
+/* The handle of system `sys` of a batch (the handle itself for system 0 of a
+ * single handle), for etdm_layout and etdm_get_array; borrowed: it lives until
+ * the batch is freed and must not be passed to etdm_free.  NULL if out of
+ * range.  Its arrays reflect the batch's last evaluation. */
+etdm_handle *etdm_system_handle(etdm_handle *h, int32_t sys);
+
+/* Systems that the next etdm_energy_grad on a batch evaluates: active_host
+ * [n_sys], nonzero = evaluate (all are active after set-up).  The inactive
+ * systems' E and g entries are left as they are.  Synchronizes the device. */
+int etdm_set_active(etdm_handle *h, const int32_t *active_host);
+
 /* One energy + gradient evaluation (Eq. 1, 7, 12, 11, 14 / 39-41):
  * a_dev [N*V] (A_ov) -> E_dev [1] and g_dev [N*V] = dE/dA_ov (Eq. 20).
+ * On a batch: a_dev, g_dev packed per etdm_system_layout, E_dev [n_sys].
  * g_dev may be NULL (energy only).  Asynchronous on `stream`; numerical
  * failures (NaN/Inf, |P| beyond the exp range) are reported by the next
  * synchronizing call (etdm_check or a *_host call) as ETDM_ERR_NUMERIC. */
@@ -113,7 +146,8 @@ int etdm_energy_grad(etdm_handle *h, const double *a_dev, double *E_dev,
 int etdm_energy_grad_host(etdm_handle *h, const double *a_host,
                           double *E_host, double *g_host);
 
-/* pg = P^(k) o g (Eq. 33) with the current beta^(k) (Eq. 34). */
+/* pg = P^(k) o g (Eq. 33) with the current beta^(k) (Eq. 34).  On a batch:
+ * per system on the packed vectors (as is etdm_lbfgs_step). */
 int etdm_precondition(etdm_handle *h, const double *g_dev, double *pg_dev,
                       void *stream);
 
@@ -133,7 +167,11 @@ int etdm_lbfgs_reset(etdm_handle *h);
  * or approximate Wolfe Eq. 27 with Eq. 28; cubic interpolation; at most 20
  * trials).  Per step i (0 = the start point) the host arrays, each of
  * n_steps+1 entries and each optional, receive E, the accepted alpha and the
- * number of evaluations.  Synchronizes `stream` once per trial. */
+ * number of evaluations.  Synchronizes `stream` once per trial.  On a batch
+ * every system takes n_steps steps with its own line search and L-BFGS
+ * memory (the same rules, so each system's trajectory is the one it would
+ * take alone); the arrays are [n_sys][n_steps+1]; a mixed-precision batch
+ * synchronizes once per round of trials. */
 int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps,
                   double *E_hist, double *alpha_hist, int32_t *trials_hist,
                   void *stream);

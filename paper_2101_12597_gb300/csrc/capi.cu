@@ -10,7 +10,9 @@
 #include <string>
 #include <vector>
 
+#include "host.h"
 #include "internal.h"
+#include "linesearch.h"
 
 using namespace etdm;
 
@@ -18,36 +20,10 @@ namespace {
 
 std::string g_init_err;
 
-struct Fail {
-  int code;
-  std::string msg;
-};
-
-#define CUDA_TRY(expr)                                                            \
-  do {                                                                            \
-    cudaError_t _e = (expr);                                                      \
-    if (_e != cudaSuccess)                                                        \
-      throw Fail{ETDM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)}; \
-  } while (0)
-
-template <typename T>
-T *dalloc(etdm_handle *h, size_t count) {
-  void *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    throw Fail{ETDM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
-                                 " bytes failed: " + cudaGetErrorString(e)};
-  }
-  h->allocs.push_back(p);
-  CUDA_TRY(cudaMemset(p, 0, count * sizeof(T)));
-  return (T *)p;
-}
-
 void release(etdm_handle *h) {
   if (!h) return;
   cudaSetDevice(h->device);
+  batch_release(h);
   for (auto &pe : h->prof_events) {
     cudaEventDestroy(pe.second.first);
     cudaEventDestroy(pe.second.second);
@@ -115,8 +91,7 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
   {
     StageTimer t(h, s, ETDM_STAGE_RHO);
     if (mixed) {
-      CUDA_TRY(launch_oslice(h, s));
-      CUDA_TRY(launch_rho_tc(h, s));
+      CUDA_TRY(launch_mixed_rho(h->plan, s));
     } else {
       CUDA_TRY(launch_rho_fp64(h, h->d_D, h->d_rho, s));
     }
@@ -125,8 +100,7 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
   {
     StageTimer t(h, s, ETDM_STAGE_POTENTIAL);
     if (mixed) {  // float-pair half-spectrum pipeline; also resets V's fixed-point sums
-      CUDA_TRY(cudaMemsetAsync(h->d_Vfix, 0, ((size_t)h->M * h->M + 1) * sizeof(unsigned long long), s));
-      CUDA_TRY(launch_df_potential(h, s));
+      CUDA_TRY(launch_mixed_potential(h->plan, s));
       h->n_gridpart = df_pot_blocks(h);
     } else {
       CUDA_TRY(launch_pack_real(h, h->d_rho, h->d_fft, s));
@@ -144,7 +118,7 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
   h->launches += mixed ? 11 : 12;
   if (mixed) {  // also needed for the energy: first-order correction of D's quantization
     StageTimer t(h, s, ETDM_STAGE_VMAT);
-    CUDA_TRY(launch_vmat_tc(h, s));
+    CUDA_TRY(launch_mixed_vmat(h->plan, s));
     t.done();
   } else if (g) {
     StageTimer t(h, s, ETDM_STAGE_VMAT);
@@ -467,6 +441,11 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
       if (!v.empty()) CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
       return d;
     };
+    h->h_xr_off = xr_off;
+    h->h_vg_t0 = vg_t0;
+    h->h_vg_eoff = vg_eoff;
+    h->h_mu_off = mu_off;
+    h->h_vg_nu = vg_nu;
     h->d_xr_off = upload(xr_off);
     h->d_mu_off = upload(mu_off);
     h->d_tmu = upload(tmu);
@@ -620,6 +599,13 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     CUDA_TRY(launch_to_pairs(h->d_T, h->d_Tp, MM, s));
   }
 
+  if (h->precision == ETDM_PREC_MIXED) {  // device tables of the grid stages
+    const int one = 1;
+    h->d_active1 = dupload(h, &one, 1);
+    build_mixed_plan(h, {h}, h->d_active1, h->d_flags, false, h->d_Vfix,
+                     ((size_t)M * M + 1) * sizeof(unsigned long long), &h->plan);
+  }
+
   // orbital energies of Eq. 33 at A = 0
   CUDA_TRY(cudaMemsetAsync(h->d_a, 0, nvar * 8, s));
   h->in_setup = true;
@@ -633,33 +619,15 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   CUDA_TRY(cudaDeviceSynchronize());
 }
 
-// ---- line search (Eq. 25-29), same rules as the paper's description ----------
-constexpr double C1 = 1e-4, C2 = 0.9, DEL = 0.1, SIG = 0.9, EPSE = 1e-6;
-constexpr int MAX_TRIALS = 20;
-
-bool cubic_min(double a, double fa, double da, double b, double fb, double db, double *out) {
-  if (a == b) return false;
-  double d1 = da + db - 3.0 * (fa - fb) / (a - b);
-  double disc = d1 * d1 - da * db;
-  if (disc < 0.0) return false;
-  double d2 = copysign(sqrt(disc), b - a);
-  double den = db - da + 2.0 * d2;
-  if (den == 0.0) return false;
-  *out = b - (b - a) * (db + d2 - d1) / den;
-  return true;
-}
-
-bool wolfe_ok(double alpha, double E, double d, double E0, double d0) {
-  bool strong = (E <= E0 + C1 * alpha * d0) && (fabs(d) <= C2 * fabs(d0));
-  bool approx = ((2.0 * DEL - 1.0) * d0 >= d) && (d >= SIG * d0) && (E <= E0 + EPSE * fabs(E0));
-  return strong || approx;
-}
-
-struct Pt {
-  double a, E, d;
-};
-
 }  // namespace
+
+void etdm::init_system(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) {
+  init_impl(h, sys, opt);
+}
+void etdm::eval_system(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s) {
+  evaluate(h, a, E, g, s);
+}
+void etdm::release_handle(etdm_handle *h) { release(h); }
 
 void etdm::set_unbound_error(const std::string &msg) { g_init_err = msg; }
 
@@ -697,7 +665,8 @@ int etdm_energy_grad(etdm_handle *h, const double *a_dev, double *E_dev, double 
   if (!a_dev || !E_dev) return set_err(h, ETDM_ERR_INVALID_ARG, "a_dev and E_dev are required");
   try {
     CUDA_TRY(cudaSetDevice(h->device));
-    evaluate(h, a_dev, E_dev, g_dev, (cudaStream_t)stream);
+    if (!h->members.empty()) batch_energy_grad(h, a_dev, E_dev, g_dev, (cudaStream_t)stream);
+    else evaluate(h, a_dev, E_dev, g_dev, (cudaStream_t)stream);
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
   }
@@ -710,6 +679,10 @@ int etdm_energy_grad_host(etdm_handle *h, const double *a_host, double *E_host,
   if (!a_host || !E_host) return set_err(h, ETDM_ERR_INVALID_ARG, "a_host and E_host are required");
   try {
     CUDA_TRY(cudaSetDevice(h->device));
+    if (!h->members.empty()) {
+      batch_energy_grad_host(h, a_host, E_host, g_host);
+      return ETDM_OK;
+    }
     cudaStream_t s = 0;
     const long nvar = (long)h->N * h->V;
     CUDA_TRY(cudaMemcpyAsync(h->d_a, a_host, nvar * 8, cudaMemcpyHostToDevice, s));
@@ -728,6 +701,12 @@ int etdm_precondition(etdm_handle *h, const double *g_dev, double *pg_dev, void 
   if (!g_dev || !pg_dev) return set_err(h, ETDM_ERR_INVALID_ARG, "g_dev and pg_dev are required");
   try {
     CUDA_TRY(cudaSetDevice(h->device));
+    if (!h->members.empty()) {  // per system, at its slice of the packed vectors
+      for (size_t i = 0; i < h->members.size(); ++i)
+        CUDA_TRY(launch_precond(h->members[i], g_dev + h->var_off[i], pg_dev + h->var_off[i],
+                                (cudaStream_t)stream));
+      return ETDM_OK;
+    }
     CUDA_TRY(launch_precond(h, g_dev, pg_dev, (cudaStream_t)stream));
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
@@ -742,6 +721,12 @@ int etdm_lbfgs_step(etdm_handle *h, const double *a_dev, const double *g_dev, do
     return set_err(h, ETDM_ERR_INVALID_ARG, "a_dev, g_dev and p_dev are required");
   try {
     CUDA_TRY(cudaSetDevice(h->device));
+    if (!h->members.empty()) {  // per system, at its slice of the packed vectors
+      for (size_t i = 0; i < h->members.size(); ++i)
+        lbfgs(h->members[i], a_dev + h->var_off[i], g_dev + h->var_off[i], p_dev + h->var_off[i],
+              (cudaStream_t)stream);
+      return ETDM_OK;
+    }
     lbfgs(h, a_dev, g_dev, p_dev, (cudaStream_t)stream);
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
@@ -751,6 +736,11 @@ int etdm_lbfgs_step(etdm_handle *h, const double *a_dev, const double *g_dev, do
 
 int etdm_lbfgs_reset(etdm_handle *h) {
   if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  for (etdm_handle *m : h->members) {
+    const int rc = etdm_lbfgs_reset(m);
+    if (rc != ETDM_OK) return set_err(h, rc, m->err);
+  }
+  if (!h->members.empty()) return ETDM_OK;
   try {
     CUDA_TRY(cudaSetDevice(h->device));
     CUDA_TRY(cudaDeviceSynchronize());
@@ -768,7 +758,8 @@ int etdm_check(etdm_handle *h, void *stream) {
   if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
   try {
     CUDA_TRY(cudaSetDevice(h->device));
-    check_flags(h, (cudaStream_t)stream);
+    if (!h->members.empty()) batch_check(h, (cudaStream_t)stream);
+    else check_flags(h, (cudaStream_t)stream);
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
   }
@@ -782,6 +773,15 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
   cudaStream_t s = (cudaStream_t)stream;
   const long nvar = (long)h->N * h->V;
   double *hp = h->h_pinned;
+  if (!h->members.empty()) {
+    try {
+      CUDA_TRY(cudaSetDevice(h->device));
+      batch_minimize(h, a_dev, n_steps, E_hist, alpha_hist, trials_hist, s);
+    } catch (const Fail &f) {
+      return set_err(h, f.code, f.msg);
+    }
+    return ETDM_OK;
+  }
   try {
     CUDA_TRY(cudaSetDevice(h->device));
     // E and g at the start point
@@ -793,6 +793,7 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
     if (alpha_hist) alpha_hist[0] = 0.0;
     if (trials_hist) trials_hist[0] = 1;
     // phi(alpha): E(a + alpha p) and grad . p, into hp[0], hp[1]
+    struct Pt { double a, E, d; };
     auto phi = [&](double alpha) -> Pt {
       CUDA_TRY(launch_axpy(a_dev, alpha, h->d_p, h->d_at, nvar, s));
       evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
@@ -802,6 +803,7 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
       check_flags(h, s);
       return Pt{alpha, hp[0], hp[1]};
     };
+    LineSearch ls;
     for (int it = 1; it <= n_steps; ++it) {
       lbfgs(h, a_dev, h->d_g, h->d_p, s);
       CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
@@ -828,57 +830,20 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
         check_flags(h, s);
         d0 = hp[2];
       }
-      const double E0 = E;
-      int trials = 0;
-      bool accepted = false, have_bracket = false;
-      Pt prev{0.0, E0, d0}, lo{}, hi{}, cur{};
-      double alpha = 1.0;
-      while (trials < MAX_TRIALS) {
-        cur = (trials == 0 && have_first) ? first : phi(alpha);
-        ++trials;
-        if (wolfe_ok(cur.a, cur.E, cur.d, E0, d0)) { accepted = true; break; }
-        if (cur.E > E0 + C1 * cur.a * d0 || (trials > 1 && cur.E >= prev.E)) {
-          lo = prev; hi = cur; have_bracket = true; break;
-        }
-        if (cur.d >= 0.0) { lo = cur; hi = prev; have_bracket = true; break; }
-        double nxt;
-        if (!cubic_min(prev.a, prev.E, prev.d, cur.a, cur.E, cur.d, &nxt) ||
-            !(1.1 * cur.a <= nxt && nxt <= 4.0 * cur.a))
-          nxt = 2.0 * cur.a;
-        prev = cur;
-        alpha = nxt;
+      ls.start(E, d0);
+      if (have_first) ls.feed(first.E, first.d);
+      while (!ls.done()) {  // each trial leaves its point and gradient in d_at, d_gt
+        const Pt cur = phi(ls.alpha());
+        ls.feed(cur.E, cur.d);
       }
-      while (!accepted && have_bracket && trials < MAX_TRIALS) {
-        double w = fabs(hi.a - lo.a), left = std::min(lo.a, hi.a), right = std::max(lo.a, hi.a);
-        double aj;
-        if (!cubic_min(lo.a, lo.E, lo.d, hi.a, hi.E, hi.d, &aj) ||
-            !(left + 0.1 * w <= aj && aj <= right - 0.1 * w))
-          aj = 0.5 * (lo.a + hi.a);
-        cur = phi(aj);
-        ++trials;
-        if (wolfe_ok(cur.a, cur.E, cur.d, E0, d0)) { accepted = true; break; }
-        if (cur.E > E0 + C1 * cur.a * d0 || cur.E >= lo.E) {
-          hi = cur;
-        } else {
-          if (cur.d * (hi.a - lo.a) >= 0.0) hi = lo;
-          lo = cur;
-        }
-      }
-      if (!accepted) {  // best point seen (the bracket's low end), re-evaluated
-        Pt best = have_bracket ? lo : prev;
-        if (best.a != 0.0) {
-          cur = phi(best.a);
-          accepted = true;
-        }
-      }
-      if (accepted) {
+      if (ls.accepted()) {
         CUDA_TRY(cudaMemcpyAsync(a_dev, h->d_at, nvar * 8, cudaMemcpyDeviceToDevice, s));
         std::swap(h->d_g, h->d_gt);
-        E = cur.E;
+        E = ls.result().E;
       }
       if (E_hist) E_hist[it] = E;
-      if (alpha_hist) alpha_hist[it] = accepted ? cur.a : 0.0;
-      if (trials_hist) trials_hist[it] = trials;
+      if (alpha_hist) alpha_hist[it] = ls.accepted() ? ls.result().a : 0.0;
+      if (trials_hist) trials_hist[it] = ls.trials();
     }
     CUDA_TRY(cudaStreamSynchronize(s));
   } catch (const Fail &f) {
@@ -889,6 +854,18 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
 
 int etdm_layout(const etdm_handle *h, int64_t *dims) {
   if (!h || !dims) return ETDM_ERR_INVALID_ARG;
+  if (!h->members.empty()) {  // a batch: totals over the systems (maxima for M, N, V, lists)
+    for (int k = 0; k < ETDM_NDIMS; ++k) dims[k] = 0;
+    for (const etdm_handle *m : h->members) {
+      int64_t d[ETDM_NDIMS];
+      etdm_layout(m, d);
+      for (int k : {0, 1, 2, 6}) dims[k] = std::max(dims[k], d[k]);
+      for (int k : {3, 4, 5, 10}) dims[k] += d[k];
+      for (int k : {7, 8, 9}) dims[k] = d[k];
+    }
+    dims[11] = h->precision;
+    return ETDM_OK;
+  }
   dims[0] = h->M; dims[1] = h->N; dims[2] = h->V; dims[3] = h->G;
   dims[4] = h->n_tiles; dims[5] = h->n_entries; dims[6] = h->max_list;
   dims[7] = h->geom.tx; dims[8] = h->geom.ty; dims[9] = h->geom.tz;
@@ -897,7 +874,7 @@ int etdm_layout(const etdm_handle *h, int64_t *dims) {
 }
 
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
-  if (!h) return -1;
+  if (!h || !h->members.empty()) return -1;  // a batch: ask its systems (etdm_system_handle)
   const int64_t M = h->M, N = h->N;
   switch (which) {
     case ETDM_ARR_S: case ETDM_ARR_T: case ETDM_ARR_C0: case ETDM_ARR_H: case ETDM_ARR_D:
@@ -1006,6 +983,65 @@ int etdm_stage_times(etdm_handle *h, double *ms, int64_t *counts) {
     }
     if (counts) counts[ETDM_NSTAGES - 1] = h->launches;
     h->launches = 0;
+  } catch (const Fail &f) {
+    return set_err(h, f.code, f.msg);
+  }
+  return ETDM_OK;
+}
+
+int etdm_init_batch(const etdm_system *sys, int32_t n_sys, const etdm_options *opt,
+                    etdm_handle **out) {
+  if (!out) return set_err(nullptr, ETDM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  etdm_handle *h = new etdm_handle();
+  try {
+    if (opt) validate(sys, opt);
+    init_batch(h, sys, n_sys, opt);
+  } catch (const Fail &f) {
+    release(h);
+    delete h;
+    return set_err(nullptr, f.code, f.msg);
+  }
+  *out = h;
+  return ETDM_OK;
+}
+
+int32_t etdm_num_systems(const etdm_handle *h) {
+  if (!h) return 0;
+  return h->members.empty() ? 1 : (int32_t)h->members.size();
+}
+
+int etdm_system_layout(const etdm_handle *h, int32_t sys, int64_t *offset, int64_t *len) {
+  if (!h || !offset || !len) return ETDM_ERR_INVALID_ARG;
+  if (h->members.empty()) {
+    if (sys != 0) return ETDM_ERR_INVALID_ARG;
+    *offset = 0;
+    *len = (int64_t)h->N * h->V;
+    return ETDM_OK;
+  }
+  if (sys < 0 || sys >= (int32_t)h->members.size()) return ETDM_ERR_INVALID_ARG;
+  *offset = h->var_off[sys];
+  *len = h->var_off[sys + 1] - h->var_off[sys];
+  return ETDM_OK;
+}
+
+etdm_handle *etdm_system_handle(etdm_handle *h, int32_t sys) {
+  if (!h) return nullptr;
+  if (h->members.empty()) return sys == 0 ? h : nullptr;
+  if (sys < 0 || sys >= (int32_t)h->members.size()) return nullptr;
+  return h->members[sys];
+}
+
+int etdm_set_active(etdm_handle *h, const int32_t *active_host) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (h->members.empty() || !active_host)
+    return set_err(h, ETDM_ERR_INVALID_ARG, "a batch handle and a mask are required");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<int> m(h->members.size());
+    for (size_t i = 0; i < m.size(); ++i) m[i] = active_host[i] != 0;
+    CUDA_TRY(cudaMemcpy(h->d_act, m.data(), m.size() * sizeof(int), cudaMemcpyHostToDevice));
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
   }

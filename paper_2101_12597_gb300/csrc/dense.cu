@@ -37,6 +37,27 @@ constexpr int BM = 8, BN = 16, BK = 16, NT = 512;
 constexpr int NG = 128;       // threads of one K group (one output each)
 constexpr int KG = NT / NG;   // K groups: a tile's K chunks go round-robin to the groups
 static_assert(kTaylor >= 8 && kTaylor <= 11, "Paterson-Stockmeyer blocks assume degree 8..11");
+// The blocks that run one chain together: either a cooperative grid (one
+// system per launch, a bounded grid barrier between dependent products) or a
+// single block of a batched launch (one system per block, where the block
+// barrier is all the chain needs).
+struct Coop {
+  int rank, size;
+  unsigned *bar;
+  int *flags;
+  __device__ __forceinline__ bool sync() const {
+    if (size == 1) {
+      __syncthreads();
+      return true;
+    }
+    return grid_barrier(bar, flags);
+  }
+};
+__device__ __forceinline__ Coop grid_coop(unsigned *bar, int *flags) {
+  return Coop{(int)blockIdx.x, (int)gridDim.x, bar, flags};
+}
+__device__ __forceinline__ Coop block_coop() { return Coop{0, 1, nullptr, nullptr}; }
+
 // slots of the forward series workspace Qk
 enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc2, kBs2, kTc, kTs, kQslots };
 // slots of the reverse workspace Wr
@@ -234,8 +255,10 @@ __device__ __forceinline__ int big_tiles(const Phase &ph) {
   if (ph.m <= 0 || ph.n <= 0) return 0;
   return ((ph.m + LBM - 1) / LBM) * ((ph.n + LBN - 1) / LBN);
 }
-__device__ __forceinline__ bool use_big(const Phase &ph) { return big_tiles(ph) >= 4 * (int)gridDim.x; }
-__device__ __forceinline__ int ntiles(const Phase &ph) { return use_big(ph) ? big_tiles(ph) : phase_tiles(ph); }
+__device__ __forceinline__ bool use_big(const Phase &ph, int nb) { return big_tiles(ph) >= 4 * nb; }
+__device__ __forceinline__ int ntiles(const Phase &ph, int nb) {
+  return use_big(ph, nb) ? big_tiles(ph) : phase_tiles(ph);
+}
 
 template <class R>
 __device__ __noinline__ void phase_tile_big(const Phase &ph, int tile, R (*As)[LBK][LBM + 1],
@@ -336,7 +359,7 @@ constexpr int kBigTileBytes = (2 * LBK * (LBM + 1) + 2 * LBK * (LBN + 1)) * 8;
 constexpr int kTileBytes = kSmallTileBytes > kBigTileBytes ? kSmallTileBytes : kBigTileBytes;
 
 template <class R>
-__device__ void run_phases(const Phase *ph, int count, double *sq = nullptr) {
+__device__ void run_phases(const Coop &cp, const Phase *ph, int count, double *sq = nullptr) {
   static_assert(sizeof(R) == 8, "8-byte elements");
   __shared__ __align__(16) unsigned char tsm[kTileBytes];
   __shared__ Phase sph[3];
@@ -351,11 +374,11 @@ __device__ void run_phases(const Phase *ph, int count, double *sq = nullptr) {
   auto *Al = reinterpret_cast<R (*)[LBK][LBM + 1]>(base);
   auto *Bl = reinterpret_cast<R (*)[LBK][LBN + 1]>(base + 2 * LBK * (LBM + 1));
   int total = 0;
-  for (int c = 0; c < count; ++c) total += ntiles(sph[c]);
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+  for (int c = 0; c < count; ++c) total += ntiles(sph[c], cp.size);
+  for (int t = cp.rank; t < total; t += cp.size) {
     int c = 0, base_t = 0;
-    while (t - base_t >= ntiles(sph[c])) { base_t += ntiles(sph[c]); ++c; }
-    if (use_big(sph[c])) phase_tile_big<R>(sph[c], t - base_t, Al, Bl, sq);
+    while (t - base_t >= ntiles(sph[c], cp.size)) { base_t += ntiles(sph[c], cp.size); ++c; }
+    if (use_big(sph[c], cp.size)) phase_tile_big<R>(sph[c], t - base_t, Al, Bl, sq);
     else phase_tile<R>(sph[c], t - base_t, As, Bs, part, sq);
   }
 }
@@ -379,20 +402,20 @@ __device__ __forceinline__ void addc(Phase &ph, const void *c, int ld, double be
   ph.C[ph.nc] = c; ph.ldc[ph.nc] = ld; ph.beta[ph.nc] = beta; ++ph.nc;
 }
 
-#define BARRIER_OR_RETURN()                      \
-  do {                                           \
-    if (!grid_barrier(a.bar, a.flags)) return;   \
+#define BARRIER_OR_RETURN()   \
+  do {                        \
+    if (!cp.sync()) return;   \
   } while (0)
 
 // Forward: P, j, Q^k, Taylor series, doublings, U_occ = [cos sqrt P; -A^T s(P)],
 // O = C0 U_occ, then D = 2 O O^T and H <- T (FP64 grid passes) or T O (mixed).
 template <class R>
-__global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
+__device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
   using X = Num<R>;
   const int M = a.M, N = a.N, V = a.V;
   const long NN = (long)N * N;
-  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long gstride = (long)gridDim.x * blockDim.x;
+  const long gtid = (long)cp.rank * blockDim.x + threadIdx.x;
+  const long gstride = (long)cp.size * blockDim.x;
   __shared__ int sh_j;
   __shared__ double sh_sc;
   // A_ov as R: the float-pair engine converts the FP64 input once, in the first phase
@@ -404,13 +427,13 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     Phase ph = mkphase(N, N, V, a.P, N);
     ph.np = 1; ph.p[0] = mk(a.A, V, 0, a.A, V, 1, 1.0); ph.p[0].f64 = 3;
     double sq = 0.0;
-    run_phases<R>(&ph, 1, &sq);
+    run_phases<R>(cp, &ph, 1, &sq);
     sq = block_sum(sq);
-    if (threadIdx.x == 0) a.red[blockIdx.x] = sq;
+    if (threadIdx.x == 0) a.red[cp.rank] = sq;
   }
   BARRIER_OR_RETURN();
   {  // j from |P|_F (every block sums the partials in the same order)
-    const double t = block_sum_of(a.red, gridDim.x);
+    const double t = block_sum_of(a.red, cp.size);
     double nrm = sqrt(t);
     int j = 0;
     while (nrm > 1.0 && j <= kJmax) { nrm *= 0.25; ++j; }
@@ -436,7 +459,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
   {  // Q^2 = sc^2 P P
     Phase ph = mkphase(N, N, N, slot(kQ2), N);
     ph.np = 1; ph.p[0] = mk(a.P, N, 0, a.P, N, 0, sc * sc);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {  // Q^3 = sc P Q^2, Q^4 = Q^2 Q^2
@@ -445,7 +468,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     ph[0].np = 1; ph[0].p[0] = mk(a.P, N, 0, slot(kQ2), N, 0, sc);
     ph[1] = mkphase(N, N, N, slot(kQ4), N);
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   // Paterson-Stockmeyer blocks B_i = sum_r c_{4i+r} Q^r (r < 4) enter the
@@ -480,7 +503,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
       addc(ph[w], slot(kQ4), N, cf(c, 8));
       ph[w].diag = cf(c, 4);
     }
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // k = cos sqrt(Q) - 1 = B_0 + Q^4 T_c, s = sin sqrt(Q) / sqrt(Q) = B_0 + Q^4 T_s
@@ -497,7 +520,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
       addc(ph[w], slot(kQ3), N, cf(c, 3));
       ph[w].diag = cf(c, 0);
     }
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   for (int t = 0; t < J; ++t) {  // doubling: k' = 4k + 2k^2, s' = s + s k
@@ -509,7 +532,7 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     ph[1] = mkphase(N, N, N, a.St + (long)(t + 1) * NN, N);
     ph[1].np = 1; ph[1].p[0] = mk(Sc, N, 0, Kc, N, 0, 1.0);
     addc(ph[1], Sc, N, 1.0);
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
     BARRIER_OR_RETURN();
   }
   {
@@ -520,25 +543,42 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
     }
     Phase ph = mkphase(V, N, N, a.Uocc + NN, N);  // -A^T s(P)
     ph.np = 1; ph.p[0] = mk(Ar, V, 1, SJ, N, 0, -1.0);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {
     Phase ph = mkphase(M, N, M, a.O, N);  // O = C0 U_occ
     ph.np = 1; ph.p[0] = mk(a.C0, M, 0, a.Uocc, N, 0, 1.0);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   if (a.Vacc) {  // mixed path: the density comes from O on the grid; T O for the kinetic energy and dE/dO
     Phase ph = mkphase(M, N, M, a.TO, N);
     ph.np = 1; ph.p[0] = mk(a.T, M, 0, a.O, N, 0, 1.0);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
   } else {
     Phase ph = mkphase(M, M, N, a.D, M);  // D = 2 O O^T (Eq. 12, f = 2)
     ph.np = 1; ph.p[0] = mk(a.O, N, 0, a.O, N, 1, 2.0);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
     const long MM = (long)M * M;
     for (long e = gtid; e < MM; e += gstride) X::st(a.H, e, X::ld(a.T, e));
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
+  dense_forward<R>(a, grid_coop(a.bar, a.flags));
+}
+
+// Batched: block b runs the chains of systems order[b], order[b + gridDim], ...
+// (largest first) one after another, each system on this block alone; systems
+// whose active flag is 0 are skipped.
+template <class R>
+__global__ void __launch_bounds__(NT) dense_forward_batch_kernel(const DenseArgs *av, const int *order,
+                                                                 int n, const int *active) {
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    const int i = order[q];
+    if (active[i]) dense_forward<R>(av[i], block_coop());
   }
 }
 
@@ -546,12 +586,12 @@ __global__ void __launch_bounds__(NT) dense_forward_kernel(DenseArgs a) {
 // (mixed path: Tr(D T) = 2 sum O o (T O), 4 H O = 4 T O + 4 V O);
 // back through U_occ, the doublings, the Taylor powers and P = A A^T.
 template <class R>
-__global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want_grad) {
+__device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp) {
   using X = Num<R>;
   const int M = a.M, N = a.N, V = a.V;
   const long NN = (long)N * N, MM = (long)M * M;
-  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long gstride = (long)gridDim.x * blockDim.x;
+  const long gtid = (long)cp.rank * blockDim.x + threadIdx.x;
+  const long gstride = (long)cp.size * blockDim.x;
   const bool mixed = a.Vacc != nullptr;
   const long MN = (long)M * N;
   const void *const Ar = X::kPair ? (const void *)a.Af : (const void *)a.A;  // set by the forward
@@ -568,20 +608,20 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     }
     s = block_sum(s);
     c = block_sum(c);
-    if (threadIdx.x == 0) { a.red[blockIdx.x] = s; a.red[gridDim.x + blockIdx.x] = -4.0 * c; }
+    if (threadIdx.x == 0) { a.red[cp.rank] = s; a.red[cp.size + cp.rank] = -4.0 * c; }
     Phase ph = mkphase(M, N, M, a.Gbar, N);
     ph.np = 1; ph.p[0] = mk(a.Vacc, M, 0, a.O, N, 0, 4.0); ph.p[0].f64 = 4;  // A symmetric (upper)
     addc(ph, a.TO, N, 4.0);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
     BARRIER_OR_RETURN();
     double c2 = 0.0;
     for (long e = gtid; e < MN; e += gstride) c2 += X::dbl(X::ld(a.Gbar, e)) * a.dO[e];
     c2 = block_sum(c2);
-    if (threadIdx.x == 0) a.red[2 * gridDim.x + blockIdx.x] = c2;
+    if (threadIdx.x == 0) a.red[2 * cp.size + cp.rank] = c2;
     if (want_grad) {
       Phase pu = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
       pu.np = 1; pu.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
-      run_phases<R>(&pu, 1);
+      run_phases<R>(cp, &pu, 1);
     }
     BARRIER_OR_RETURN();
   } else {
@@ -594,24 +634,24 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
       }
     }
     s = block_sum(s);
-    if (threadIdx.x == 0) a.red[blockIdx.x] = s;
+    if (threadIdx.x == 0) a.red[cp.rank] = s;
     BARRIER_OR_RETURN();
     if (want_grad) {
       Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
       ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-      run_phases<R>(&ph, 1);
+      run_phases<R>(cp, &ph, 1);
       BARRIER_OR_RETURN();
       Phase pu = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
       pu.np = 1; pu.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
-      run_phases<R>(&pu, 1);
+      run_phases<R>(cp, &pu, 1);
       BARRIER_OR_RETURN();
     }
   }
-  if (blockIdx.x == 0) {  // energy terms: tree sums over the block partials, all threads of block 0
+  if (cp.rank == 0) {  // energy terms: tree sums over the block partials, all threads of block 0
     double kin = 0.0, corr = 0.0, t3[3] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < cp.size; b += blockDim.x) {
       kin += a.red[b];
-      if (mixed) corr += a.red[gridDim.x + b] + a.red[2 * gridDim.x + b];
+      if (mixed) corr += a.red[cp.size + b] + a.red[2 * cp.size + b];
     }
     for (int b = threadIdx.x; b < a.n_gridpart; b += blockDim.x)
       for (int q = 0; q < 3; ++q) t3[q] += a.gridpart[3 * b + q];
@@ -635,7 +675,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[0].np = 1; ph[0].p[0] = mk(Ar, V, 0, Ubv, N, 0, -1.0);
     ph[1] = mkphase(N, V, N, a.Abar, V);     // Abar = -S_J Ubar_v^T
     ph[1].np = 1; ph[1].p[0] = mk(a.St + (long)J * NN, N, 0, Ubv, N, 1, -1.0);
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   const double *kb = a.Ubar;  // Kbar_J = cotangent of cos sqrt(P) = Ubar_o
@@ -654,7 +694,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1].p[1] = mk(Kc, N, 0, kb, N, 0, 2.0);
     ph[1].p[2] = mk(Sc, N, 0, sb, N, 0, 1.0);
     addc(ph[1], kb, N, 4.0);
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
     BARRIER_OR_RETURN();
     kb = kbo; sb = sbo; pp = 1 - pp;
   }
@@ -673,7 +713,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, kb, N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kTsb), N);  // T_s bar = Q^4 sbar
     ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, sb, N, 0, 1.0);
-    run_phases<R>(ph, 3);
+    run_phases<R>(cp, ph, 3);
   }
   BARRIER_OR_RETURN();
   {  // back through T = B_1 + Q^4 B_2
@@ -687,7 +727,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, wr(kTcb), N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kBs2b), N);  // B_s2 bar = Q^4 T_s bar
     ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, wr(kTsb), N, 0, 1.0);
-    run_phases<R>(ph, 3);
+    run_phases<R>(cp, ph, 3);
   }
   BARRIER_OR_RETURN();
   // the blocks' cotangents to the powers: Q^r bar = sum_i c_{4i+r} B_ci bar + s_{4i+r} B_si bar
@@ -716,7 +756,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph[1] = mkphase(N, N, N, wr(kQ1bt), N);  // Qbar_t = Q1bar_B + Q3bar Q^2
     ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 1.0);
     addc(ph[1], wr(kQ1bB), N, 1.0);
-    run_phases<R>(ph, 2);
+    run_phases<R>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // back through Q^2 = Q Q: Qbar = Qbar_t + Q2bar Q + Q Q2bar
@@ -725,7 +765,7 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
     ph.p[1] = mk(slot(kQ1), N, 0, wr(kQ2b), N, 0, 1.0);
     addc(ph, wr(kQ1bt), N, 1.0);
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {  // Q = sc P: g = Abar + (Pbar + Pbar^T) A = Abar + sc Qbar A + sc Qbar^T A, written as FP64
@@ -735,12 +775,28 @@ __global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want
     ph.p[1] = mk(wr(kQ1b), N, 1, Ar, V, 0, sc);
     addc(ph, a.Abar, V, 1.0);
     ph.out64 = 1;
-    run_phases<R>(&ph, 1);
+    run_phases<R>(cp, &ph, 1);
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) dense_reverse_kernel(DenseArgs a, int want_grad) {
+  dense_reverse<R>(a, want_grad, grid_coop(a.bar, a.flags));
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) dense_reverse_batch_kernel(const DenseArgs *av, const int *order,
+                                                                 int n, const int *active) {
+  for (int q = blockIdx.x; q < n; q += gridDim.x) {
+    const int i = order[q];
+    if (active[i]) dense_reverse<R>(av[i], 1, block_coop());
   }
 }
 
 // Plain (non-cooperative) product for set-up work.
-__global__ void __launch_bounds__(NT) gemm_kernel(Phase ph) { run_phases<double>(&ph, 1); }
+__global__ void __launch_bounds__(NT) gemm_kernel(Phase ph) {
+  run_phases<double>(grid_coop(nullptr, nullptr), &ph, 1);
+}
 
 // ---- L-BFGS two-loop (Sec. 3.1) with H0 = P^(k) (Eq. 33-34) ---------------
 __device__ __forceinline__ double precond_elem(const double *eps, int N, int V, long e,
@@ -755,20 +811,21 @@ __device__ __forceinline__ double precond_elem(const double *eps, int N, int V, 
 // room for two sums), so one barrier suffices: a block can only write a half
 // again after the next call's barrier, which every block reaches after reading
 // this call's sums.
-__device__ double grid_dot_finish(LbfgsArgs &a, double part, int *parity, bool *ok) {
-  double *red = a.red + (*parity) * 2 * gridDim.x;
+__device__ double grid_dot_finish(const LbfgsArgs &a, const Coop &cp, double part, int *parity,
+                                  bool *ok) {
+  double *red = a.red + (*parity) * 2 * cp.size;
   *parity ^= 1;
   part = block_sum(part);
-  if (threadIdx.x == 0) red[blockIdx.x] = part;
-  if (!grid_barrier(a.bar, a.flags)) { *ok = false; return 0.0; }
-  return block_sum_of(red, gridDim.x);
+  if (threadIdx.x == 0) red[cp.rank] = part;
+  if (!cp.sync()) { *ok = false; return 0.0; }
+  return block_sum_of(red, cp.size);
 }
 
-__global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
+__device__ void lbfgs_two_loop(const LbfgsArgs &a, const Coop &cp) {
   const long n = a.n;
   const int m = a.m;
-  const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long gstride = (long)gridDim.x * blockDim.x;
+  const long gtid = (long)cp.rank * blockDim.x + threadIdx.x;
+  const long gstride = (long)cp.size * blockDim.x;
   double *st = a.state;
   int count = (int)st[0], head = (int)st[1];
   const bool have_prev = st[2] != 0.0;
@@ -783,8 +840,8 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
       sn[e] = sv; yn[e] = yv;
       p1 += sv * yv; p2 += yv * yv;
     }
-    double sy = grid_dot_finish(a, p1, &par, &ok); if (!ok) return;
-    double yy = grid_dot_finish(a, p2, &par, &ok); if (!ok) return;
+    double sy = grid_dot_finish(a, cp, p1, &par, &ok); if (!ok) return;
+    double yy = grid_dot_finish(a, cp, p2, &par, &ok); if (!ok) return;
     if (sy > 1e-30) {
       beta = yy / sy;
       st[4 + head] = 1.0 / sy;  // rho of the slot (identical in every block)
@@ -804,7 +861,7 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
     const double *sv = a.s + (long)slot * n, *yv = a.y + (long)slot * n;
     double part = 0.0;
     for (long e = gtid; e < n; e += gstride) part += sv[e] * a.q[e];
-    double sq = grid_dot_finish(a, part, &par, &ok); if (!ok) return;
+    double sq = grid_dot_finish(a, cp, part, &par, &ok); if (!ok) return;
     double al = st[4 + slot] * sq;
     alph[c] = al;
     for (long e = gtid; e < n; e += gstride) a.q[e] -= al * yv[e];
@@ -818,15 +875,39 @@ __global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
     const double *sv = a.s + (long)slot * n, *yv = a.y + (long)slot * n;
     double part = 0.0;
     for (long e = gtid; e < n; e += gstride) part += yv[e] * a.q[e];
-    double yr = grid_dot_finish(a, part, &par, &ok); if (!ok) return;
+    double yr = grid_dot_finish(a, cp, part, &par, &ok); if (!ok) return;
     double be = st[4 + slot] * yr;
     double coef = alph[c] - be;
     for (long e = gtid; e < n; e += gstride) a.q[e] += coef * sv[e];
   }
   for (long e = gtid; e < n; e += gstride) a.p[e] = -a.q[e];
-  if (!grid_barrier(a.bar, a.flags)) return;
+  if (!cp.sync()) return;
   if (gtid == 0) {
     st[0] = count; st[1] = head; st[2] = 1.0; st[3] = beta;
+  }
+}
+
+__global__ void __launch_bounds__(256) lbfgs_kernel(LbfgsArgs a) {
+  lbfgs_two_loop(a, grid_coop(a.bar, a.flags));
+}
+
+// Batched: block b runs the two-loop of systems b, b + gridDim, ... whose dir
+// flag is set, each on this block alone; reset[i] first erases the system's
+// memory (no pairs, no previous point; beta kept), as after a direction that
+// was not a descent direction.
+__global__ void __launch_bounds__(256) lbfgs_batch_kernel(const LbfgsArgs *av, const int *dir,
+                                                          const int *reset, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    if (!dir[i]) continue;
+    const LbfgsArgs &a = av[i];
+    __syncthreads();  // the previous system's reads of its state are done
+    if (reset[i] && threadIdx.x == 0) {
+      a.state[0] = 0.0;
+      a.state[1] = 0.0;
+      a.state[2] = 0.0;
+    }
+    __syncthreads();
+    lbfgs_two_loop(a, block_coop());
   }
 }
 
@@ -919,7 +1000,7 @@ __global__ void __launch_bounds__(256) lbfgs_reg_kernel(LbfgsArgs a) {
 #pragma unroll
         for (int u = 0; u < kLbPer; ++u) part += sv[k][u] * q[u];
       }
-    const double al = rho[sl] * grid_dot_finish(a, part, &par, &ok);
+    const double al = rho[sl] * grid_dot_finish(a, grid_coop(a.bar, a.flags), part, &par, &ok);
     if (!ok) return;
     alph[c] = al;
 #pragma unroll
@@ -941,7 +1022,7 @@ __global__ void __launch_bounds__(256) lbfgs_reg_kernel(LbfgsArgs a) {
 #pragma unroll
         for (int u = 0; u < kLbPer; ++u) part += yv[k][u] * q[u];
       }
-    const double coef = alph[c] - rho[sl] * grid_dot_finish(a, part, &par, &ok);
+    const double coef = alph[c] - rho[sl] * grid_dot_finish(a, grid_coop(a.bar, a.flags), part, &par, &ok);
     if (!ok) return;
 #pragma unroll
     for (int k = 0; k < kLbMaxM; ++k)
@@ -1069,7 +1150,7 @@ static bool dense_pairs(const etdm_handle *h) {
   return h->precision == ETDM_PREC_MIXED && !h->in_setup;
 }
 
-static DenseArgs dense_args(etdm_handle *h, const double *a) {
+DenseArgs dense_args(etdm_handle *h, const double *a) {
   DenseArgs d{};
   const bool pairs = dense_pairs(h);
   d.M = h->M; d.N = h->N; d.V = h->V;
@@ -1217,6 +1298,36 @@ cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t 
 cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n,
                               cudaStream_t s) {
   scale_copy_kernel<<<256, 256, 0, s>>>(src, dst, c, n);
+  return cudaGetLastError();
+}
+
+LbfgsArgs lbfgs_args(etdm_handle *h, const double *a, const double *g, double *p) {
+  LbfgsArgs d{};
+  d.n = (long)h->N * h->V; d.N = h->N; d.V = h->V; d.m = h->lbfgs_m;
+  d.a = a; d.g = g; d.p = p;
+  d.s = h->d_s; d.y = h->d_y; d.aprev = h->d_aprev; d.gprev = h->d_gprev; d.q = h->d_q;
+  d.state = h->d_lbstate; d.eps = h->d_eps; d.gamma = h->gamma;
+  d.red = h->d_red; d.bar = h->d_bar; d.flags = h->d_flags;
+  return d;
+}
+
+cudaError_t launch_dense_batch(const DenseArgs *av, const int *order, int n, const int *active,
+                               int grid, bool pairs, bool reverse, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (reverse) {
+    if (pairs) dense_reverse_batch_kernel<float2><<<grid, NT, 0, s>>>(av, order, n, active);
+    else dense_reverse_batch_kernel<double><<<grid, NT, 0, s>>>(av, order, n, active);
+  } else {
+    if (pairs) dense_forward_batch_kernel<float2><<<grid, NT, 0, s>>>(av, order, n, active);
+    else dense_forward_batch_kernel<double><<<grid, NT, 0, s>>>(av, order, n, active);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_batch(const LbfgsArgs *av, const int *dir, const int *reset, int n,
+                               int grid, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  lbfgs_batch_kernel<<<grid, 256, 0, s>>>(av, dir, reset, n);
   return cudaGetLastError();
 }
 

@@ -146,11 +146,6 @@ __device__ void df_stage(const float4 *in, float4 *out, int n, int Ns, int lines
   }
 }
 
-struct DfPlan {
-  int n, nst;
-  int radix[12];
-};
-
 // In-place (ping-pong) transform of `lines` lines held in b0; returns the buffer
 // holding the result.  Ends with a block barrier.  BIG: radices 7, 11, 13 are
 // compiled in (only grids with those factors need them; they cost registers).
@@ -187,32 +182,21 @@ __device__ void load_tw(float4 *dst, const float4 *src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-struct DfArgs {
-  int nx, ny, nz, nzh;
-  DfPlan px, py, pz;
-  const float4 *twx, *twy, *twz;
-  float4 *H;               // [nx][ny][nzh] half spectrum
-  const float2 *rhof;      // [G] rho as float pairs
-  const float2 *vextf;     // [G] v_ext as float pairs
-  const float2 *kpois;     // [nx][ny][nzh] 4 pi / (|G|^2 Ng), 0 at G = 0
-  double *vtot;            // [G] (FP64 copy of v for the array interface)
-  float2 *vt;              // [n_tiles][128] v dV in tile order
-  unsigned *vmax_bits;     // max |v| as float bits
-  double *part;            // [3 * blocks] energy partial sums
-  float2 dV;
-  float2 cx;               // (3 / pi)^(1/3)
-  GridGeom gtc;            // 4 x 4 x 8 tiles of the potential-matrix pass
-};
-
 // ---- pass 1: z lines, forward, real pairs -> half spectra ----------------------
+// Every pass runs over one or several systems: blockIdx.y picks the system
+// (its arguments in av[], skipped when its active flag is 0), blockIdx.x the
+// lines; blocks beyond the system's lines return at once.
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads, 4) zfwd_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) zfwd_kernel(const DfArgs *av, const int *active) {
   extern __shared__ __align__(16) float4 zsm[];
+  if (!active[blockIdx.y]) return;
+  const DfArgs &a = av[blockIdx.y];
+  const long NL = (long)a.nx * a.ny;
+  const long L0 = (long)blockIdx.x * kZPairs * 2;
+  if (L0 >= NL) return;
   const int nz = a.nz, nzh = a.nzh;
   float4 *tw = zsm, *b0 = zsm + nz, *b1 = b0 + kZPairs * nz;
   load_tw(tw, a.twz, nz);
-  const long NL = (long)a.nx * a.ny;
-  const long L0 = (long)blockIdx.x * kZPairs * 2;
   for (int q = threadIdx.x; q < kZPairs * nz; q += blockDim.x) {
     const int p = q / nz, z = q % nz;
     const long La = L0 + 2 * p, Lb = La + 1;
@@ -237,13 +221,17 @@ __global__ void __launch_bounds__(kDfThreads, 4) zfwd_kernel(DfArgs a) {
 
 // ---- passes 2 and 4: y lines (fixed x, kz) --------------------------------------
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads, 4) yfft_kernel(DfArgs a, int sign) {
+__global__ void __launch_bounds__(kDfThreads, 4) yfft_kernel(const DfArgs *av, const int *active,
+                                                             int sign) {
   extern __shared__ __align__(16) float4 ysm[];
+  if (!active[blockIdx.y]) return;
+  const DfArgs &a = av[blockIdx.y];
   const int ny = a.ny, nzh = a.nzh;
-  float4 *tw = ysm, *b0 = ysm + ny, *b1 = b0 + kXYLines * ny;
-  load_tw(tw, a.twy, ny);
   const long nlines = (long)a.nx * nzh;
   const long q0 = (long)blockIdx.x * kXYLines;
+  if (q0 >= nlines) return;
+  float4 *tw = ysm, *b0 = ysm + ny, *b1 = b0 + kXYLines * ny;
+  load_tw(tw, a.twy, ny);
   const int lines = (int)min((long)kXYLines, nlines - q0);
   for (int q = threadIdx.x; q < kXYLines * ny; q += blockDim.x) {
     const int y = q / kXYLines, l = q % kXYLines;
@@ -265,13 +253,16 @@ __global__ void __launch_bounds__(kDfThreads, 4) yfft_kernel(DfArgs a, int sign)
 
 // ---- pass 3: x lines, forward, Poisson kernel, inverse ---------------------------
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads, 4) xpois_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) xpois_kernel(const DfArgs *av, const int *active) {
   extern __shared__ __align__(16) float4 xsm[];
+  if (!active[blockIdx.y]) return;
+  const DfArgs &a = av[blockIdx.y];
   const int nx = a.nx, ny = a.ny, nzh = a.nzh;
-  float4 *tw = xsm, *b0 = xsm + nx, *b1 = b0 + kXYLines * nx;
-  load_tw(tw, a.twx, nx);
   const long nlines = (long)ny * nzh;
   const long q0 = (long)blockIdx.x * kXYLines;
+  if (q0 >= nlines) return;
+  float4 *tw = xsm, *b0 = xsm + nx, *b1 = b0 + kXYLines * nx;
+  load_tw(tw, a.twx, nx);
   const int lines = (int)min((long)kXYLines, nlines - q0);
   const long stride = (long)ny * nzh;
   for (int q = threadIdx.x; q < kXYLines * nx; q += blockDim.x) {
@@ -319,13 +310,16 @@ __device__ __forceinline__ float2 warp_fdf_sum(float2 v) {
 
 // ---- pass 5: z lines, inverse, half spectra pairs -> real potentials; potential --
 template <bool BIG>
-__global__ void __launch_bounds__(kDfThreads, 4) zinv_pot_kernel(DfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 4) zinv_pot_kernel(const DfArgs *av, const int *active) {
   extern __shared__ __align__(16) float4 zsm[];
+  if (!active[blockIdx.y]) return;
+  const DfArgs &a = av[blockIdx.y];
+  const long NL = (long)a.nx * a.ny;
+  const long L0 = (long)blockIdx.x * kZPairs * 2;
+  if (L0 >= NL) return;
   const int nz = a.nz, nzh = a.nzh;
   float4 *tw = zsm, *b0 = zsm + nz, *b1 = b0 + kZPairs * nz;
   load_tw(tw, a.twz, nz);
-  const long NL = (long)a.nx * a.ny;
-  const long L0 = (long)blockIdx.x * kZPairs * 2;
   // Z(k) = Va(k) + i Vb(k), with V(k) = conj V(nz - k) for k > nz/2
   for (int q = threadIdx.x; q < kZPairs * nz; q += blockDim.x) {
     const int p = q / nz, k = q % nz;
@@ -439,7 +433,7 @@ static DfPlan df_plan(int n) {
   return p;
 }
 
-static DfArgs df_args(etdm_handle *h) {
+DfArgs df_args(etdm_handle *h) {
   DfArgs a{};
   a.nx = h->n[0]; a.ny = h->n[1]; a.nz = h->n[2];
   a.nzh = h->n[2] / 2 + 1;
@@ -480,33 +474,43 @@ cudaError_t launch_df_setup(etdm_handle *h, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Sizes of a batched launch of the five passes over the systems' arguments
+// (host copies): blocks per system (the largest), shared memory, radices.
+DfLaunch df_launch_plan(const std::vector<DfArgs> &args) {
+  DfLaunch L{};
+  for (const DfArgs &a : args) {
+    L.zb = std::max(L.zb, (int)(((long)a.nx * a.ny + 2 * kZPairs - 1) / (2 * kZPairs)));
+    L.yb = std::max(L.yb, (int)(((long)a.nx * a.nzh + kXYLines - 1) / kXYLines));
+    L.xb = std::max(L.xb, (int)(((long)a.ny * a.nzh + kXYLines - 1) / kXYLines));
+    L.smz = std::max(L.smz, (size_t)(a.nz + 2 * kZPairs * a.nz) * sizeof(float4));
+    L.smy = std::max(L.smy, (size_t)(a.ny + 2 * kXYLines * a.ny) * sizeof(float4));
+    L.smx = std::max(L.smx, (size_t)(a.nx + 2 * kXYLines * a.nx) * sizeof(float4));
+    for (const DfPlan *p : {&a.px, &a.py, &a.pz})
+      for (int i = 0; i < p->nst; ++i) L.big = L.big || p->radix[i] > 5;
+  }
+  L.n_sys = (int)args.size();
+  return L;
+}
+
 template <bool BIG>
-static cudaError_t df_potential(const DfArgs &a, int zb, cudaStream_t s) {
-  const size_t smz = (size_t)(a.nz + 2 * kZPairs * a.nz) * sizeof(float4);
-  const size_t smy = (size_t)(a.ny + 2 * kXYLines * a.ny) * sizeof(float4);
-  const size_t smx = (size_t)(a.nx + 2 * kXYLines * a.nx) * sizeof(float4);
+static cudaError_t df_potential(const DfLaunch &L, const DfArgs *av, const int *active,
+                                cudaStream_t s) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(zfwd_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(zinv_pot_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smz)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(yfft_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(xpois_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx)) != cudaSuccess) return e;
-  const int yb = (int)(((long)a.nx * a.nzh + kXYLines - 1) / kXYLines);
-  const int xb = (int)(((long)a.ny * a.nzh + kXYLines - 1) / kXYLines);
-  zfwd_kernel<BIG><<<zb, kDfThreads, smz, s>>>(a);
-  yfft_kernel<BIG><<<yb, kDfThreads, smy, s>>>(a, -1);
-  xpois_kernel<BIG><<<xb, kDfThreads, smx, s>>>(a);
-  yfft_kernel<BIG><<<yb, kDfThreads, smy, s>>>(a, +1);
-  zinv_pot_kernel<BIG><<<zb, kDfThreads, smz, s>>>(a);
+  if ((e = cudaFuncSetAttribute(zfwd_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smz)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(zinv_pot_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smz)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(yfft_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smy)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(xpois_kernel<BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smx)) != cudaSuccess) return e;
+  zfwd_kernel<BIG><<<dim3(L.zb, L.n_sys), kDfThreads, L.smz, s>>>(av, active);
+  yfft_kernel<BIG><<<dim3(L.yb, L.n_sys), kDfThreads, L.smy, s>>>(av, active, -1);
+  xpois_kernel<BIG><<<dim3(L.xb, L.n_sys), kDfThreads, L.smx, s>>>(av, active);
+  yfft_kernel<BIG><<<dim3(L.yb, L.n_sys), kDfThreads, L.smy, s>>>(av, active, +1);
+  zinv_pot_kernel<BIG><<<dim3(L.zb, L.n_sys), kDfThreads, L.smz, s>>>(av, active);
   return cudaGetLastError();
 }
 
-cudaError_t launch_df_potential(etdm_handle *h, cudaStream_t s) {
-  const DfArgs a = df_args(h);
-  bool big = false;
-  for (const DfPlan *p : {&a.px, &a.py, &a.pz})
-    for (int i = 0; i < p->nst; ++i) big = big || p->radix[i] > 5;
-  const int zb = df_pot_blocks(h);
-  return big ? df_potential<true>(a, zb, s) : df_potential<false>(a, zb, s);
+cudaError_t launch_df_potential(const DfLaunch &L, const DfArgs *av, const int *active,
+                                cudaStream_t s) {
+  return L.big ? df_potential<true>(L, av, active, s) : df_potential<false>(L, av, active, s);
 }
 
 }  // namespace etdm

@@ -105,6 +105,120 @@ struct DenseArgs {
   double ck[kTaylor + 1], sk[kTaylor + 1];
 };
 
+// Arguments of the tensor-core grid passes for one system (mixed path):
+// 4 x 4 x 8 tiles, their lists and the resident operand slices.
+struct TcArgs {
+  GridGeom g;  // 4 x 4 x 8 tiles
+  int n_tiles;
+  const int *tile_ptr, *keys;   // image lists (set-up only)
+  const float4 *tab[3];         // per axis [mu][img][i]: (sq, c hi, c lo, 0),
+                                // c = norm^(1/3) exp(-alpha sq) as a float pair
+  const float *rc2f;            // [M]
+  const int *nu;                // [n_tiles] functions per tile (images merged)
+  const int *xr_off;            // [n_tiles + 1] density K steps before each tile
+  const int *mu_off;            // [n_tiles + 1] functions of the tiles before each tile
+  const int *tmu;               // functions of each tile, ascending
+  int n_vg;                     // V groups: runs of consecutive tiles, union <= kNmax functions
+  const int *vg_t0;             // [n_vg + 1] first tile of each group
+  const int *vg_nu;             // [n_vg] functions of the group's union
+  const int *vg_eoff;           // [n_vg + 1] padded union entries before each group
+  const int *vg_xoff;           // [n_vg + 1] 256-byte units of X^T slices before each group
+  const int *vg_mu;             // union function lists, ascending, padded
+  uint8_t *xr;                  // density X slices, 16 KB per K step
+  uint8_t *xv;                  // V X^T slices, 1 KB per padded union entry and tile
+  float4 *vent;                 // per padded union entry: (mu bits, 2^(e_a - 8), bound, 0)
+  signed char *rowexp;          // [G] density row exponents e_p
+  const uint2 *Osl;             // [M][NoccP] BF16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
+  const float *oscale;          // [chunks * 128] 2^g_m, zero beyond N
+  int Nocc, NoccP;              // occupied orbitals; O-slice row length (even)
+  double *rho;                  // [G]
+  float2 *rhof;                 // [G] rho as float pairs
+  const double *v;              // [G]
+  float2 *vt;                   // [n_tiles][128] v dV at the tile points (float pairs)
+  unsigned long long *Vfix;     // [M][M] V (upper triangle) in fixed point, then [M*M] = max|v| bits
+  double dV;
+  int *flags;
+};
+
+// One launch of a grid pass over one or several systems: the systems'
+// arguments and, per CTA, a list of jobs in the order the CTA runs them.
+// Density jobs are (system, tile, orbital chunk, chunks of that tile), the
+// chunks of a tile consecutive in one CTA's list; V jobs are (system, group,
+// 0, 0).  A system whose active flag is 0 is skipped by every role.
+struct TcBatch {
+  const TcArgs *sys;   // [n_sys] (device)
+  const int4 *jobs;    // (device)
+  const int *cta_ptr;  // [grid + 1] (device): CTA b runs jobs[cta_ptr[b] .. cta_ptr[b + 1])
+  const int *active;   // [n_sys] (device)
+  int *flags;          // status words: a bounded wait that gave up sets the timeout
+  int grid;            // CTAs of the launch
+  int max_nmc;         // largest number of orbital chunks of a job (density)
+};
+
+// Float-pair potential pipeline of the mixed path (fftdf.cu): per system, the
+// radix plans of the three axes and the buffers of the half-spectrum
+// transforms.
+struct DfPlan {
+  int n, nst;
+  int radix[12];
+};
+
+struct DfArgs {
+  int nx, ny, nz, nzh;
+  DfPlan px, py, pz;
+  const float4 *twx, *twy, *twz;
+  float4 *H;               // [nx][ny][nzh] half spectrum
+  const float2 *rhof;      // [G] rho as float pairs
+  const float2 *vextf;     // [G] v_ext as float pairs
+  const float2 *kpois;     // [nx][ny][nzh] 4 pi / (|G|^2 Ng), 0 at G = 0
+  double *vtot;            // [G] (FP64 copy of v for the array interface)
+  float2 *vt;              // [n_tiles][128] v dV in tile order
+  unsigned *vmax_bits;     // max |v| as float bits
+  double *part;            // [3 * blocks] energy partial sums
+  float2 dV;
+  float2 cx;               // (3 / pi)^(1/3)
+  GridGeom gtc;            // 4 x 4 x 8 tiles of the potential-matrix pass
+};
+
+// Sizes of one launch of the potential passes over one or several systems.
+struct DfLaunch {
+  int n_sys, zb, yb, xb;     // systems; z, y and x blocks of the largest
+  size_t smz, smy, smx;      // dynamic shared memory of the passes
+  bool big;                  // some axis has a radix 7, 11 or 13
+};
+
+// Column slices of one system's occupied orbitals (mixed path).
+struct OsArgs {
+  const float2 *O;  // [M][N] float pairs from the dense chain
+  int M, N, NP;     // NP = N rounded up to even: the O-slice row length
+  uint2 *Osl;       // [M][NP]
+  float *oscale;    // [whole chunks of 128] 2^g_m
+  double *dO;       // [M][N] O - Oq
+};
+
+// V of one system from its fixed-point sums (mixed path).
+struct VfArgs {
+  const unsigned long long *Vfix;  // [M*M + 1]
+  int M;
+  float2 *Vout;                    // [M][M], upper triangle written
+};
+
+// Device tables of the mixed path's grid stages (O slices, density,
+// potential, V) for one system or a batch of systems.
+struct MixedPlan {
+  int n_sys = 0;
+  const int *active = nullptr;  // [n_sys] (device)
+  TcBatch rho{}, v{};
+  const DfArgs *df = nullptr;   // [n_sys] (device)
+  DfLaunch dfl{};
+  const OsArgs *os = nullptr;   // [n_sys] (device)
+  int os_maxN = 0;
+  const VfArgs *vf = nullptr;   // [n_sys] (device)
+  int vf_blocks = 1;
+  unsigned long long *vfix = nullptr;  // every system's fixed-point V sums, one array
+  size_t vfix_bytes = 0;               // zeroed before each evaluation's potential pass
+};
+
 struct LbfgsArgs {
   long n;
   int N, V, m;
@@ -175,6 +289,11 @@ struct etdm_handle {
   float4 *d_vent = nullptr;              // per padded V group entry
   float2 *d_vt = nullptr;                // [n_tiles_tc][128] v dV in tile order
   long xr_steps = 0, xv_entries = 0;
+  // host copies of the per-tile K steps and the V groups (job tables)
+  std::vector<int> h_xr_off, h_vg_t0, h_vg_eoff, h_mu_off, h_vg_nu;
+  // device tables of the grid stages of this handle's evaluations
+  etdm::MixedPlan plan{};
+  int *d_active1 = nullptr;              // [1] = 1
   uint2 *d_Osl = nullptr;     // [M][N + N % 2] BF16 slices of O
   float *d_oscale = nullptr;  // [N]
   double *d_dO = nullptr;     // [M][N] O - Oq
@@ -218,6 +337,29 @@ struct etdm_handle {
          *d_p = nullptr, *d_dot = nullptr;
   double *h_pinned = nullptr;
   std::vector<void *> allocs;
+  // a batch of systems (etdm_init_batch): the members own every per-system
+  // array; the batch owns the packed variable vectors, the batched launch
+  // tables and the captured graphs
+  std::vector<etdm_handle *> members;
+  std::vector<long> var_off;          // [n_sys + 1] offsets of the systems' variables
+  long nvar_tot = 0;
+  double *d_ae = nullptr, *d_ge = nullptr;  // evaluation point and its gradient (packed)
+  double *d_res = nullptr;            // [3 n_sys]: E | g.p at the trial | g.p at the start
+  unsigned char *d_ctlbuf = nullptr;  // round control: [4 n_sys] int flags, then [n_sys] alpha
+  int *d_act = nullptr;               // [n_sys] the active mask of etdm_energy_grad
+  int *d_bflags = nullptr;            // [FLAG_NFLAGS (n_sys + 1)]: members', then the batch's
+  long long *d_off = nullptr;         // [n_sys + 1] var_off on the device
+  etdm::DenseArgs *d_dargs = nullptr;
+  etdm::LbfgsArgs *d_largs = nullptr;
+  int *d_order = nullptr;             // systems by decreasing dense work
+  int dense_grid = 0, lb_grid = 0;
+  etdm::MixedPlan bplan_act{}, bplan_eval{};  // grid stages masked by d_act / by the eval flags
+  cudaStream_t cap = nullptr;         // stream the graphs are captured on
+  cudaGraphExec_t g_eval = nullptr, g_round = nullptr;
+  long long graph_kernels_eval = 0, graph_kernels_round = 0;
+  unsigned char *h_ctl = nullptr;     // pinned mirror of d_ctlbuf
+  double *h_res = nullptr;            // pinned: [3 n_sys] results, then the status words
+  int tune_choice = 0;                // work partition the autotuner picked
   // optional per-stage CUDA-event timing (etdm_set_profiling)
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
@@ -274,20 +416,35 @@ cudaError_t launch_max_rowsum(const double *S, double *out, int M, cudaStream_t 
 cudaError_t launch_tables_f32(etdm_handle *h, cudaStream_t s);
 cudaError_t launch_count_unique(etdm_handle *h, int *d_nu, cudaStream_t s);
 cudaError_t launch_df_setup(etdm_handle *h, cudaStream_t s);
-cudaError_t launch_df_potential(etdm_handle *h, cudaStream_t s);
+DfArgs df_args(etdm_handle *h);
+DfLaunch df_launch_plan(const std::vector<DfArgs> &args);
+cudaError_t launch_df_potential(const DfLaunch &L, const DfArgs *av, const int *active,
+                                cudaStream_t s);
 int df_pot_blocks(etdm_handle *h);
 cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);
 int tc_rho_steps(int nu);
 int tc_v_entries(int nu);
 int tc_group_max();
 int tc_v_slices();
-cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s);
-cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s);
-cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s);
+TcArgs tc_args(etdm_handle *h);
+OsArgs os_args(etdm_handle *h);
+VfArgs vf_args(etdm_handle *h);
+// the grid stages of one evaluation over the systems of a plan
+cudaError_t launch_mixed_rho(const MixedPlan &P, cudaStream_t s);        // O slices, density
+cudaError_t launch_mixed_potential(const MixedPlan &P, cudaStream_t s);  // V sums reset, potential
+cudaError_t launch_mixed_vmat(const MixedPlan &P, cudaStream_t s);       // V pass, fixed point -> pairs
 int tc_max_list();
 // message for etdm_last_error(NULL) from calls that take no handle
 void set_unbound_error(const std::string &msg);
 int occupancy_dense(int *blocks_per_sm);
+// arguments of one system's dense chains at the point a (g, E: set by the caller)
+DenseArgs dense_args(etdm_handle *h, const double *a);
+LbfgsArgs lbfgs_args(etdm_handle *h, const double *a, const double *g, double *p);
+// batched dense chains: block b runs systems order[b], order[b + grid], ...
+cudaError_t launch_dense_batch(const DenseArgs *av, const int *order, int n, const int *active,
+                               int grid, bool pairs, bool reverse, cudaStream_t s);
+cudaError_t launch_lbfgs_batch(const LbfgsArgs *av, const int *dir, const int *reset, int n,
+                               int grid, cudaStream_t s);
 cudaError_t launch_to_pairs(const double *src, float2 *dst, long n, cudaStream_t s);
 cudaError_t launch_from_pairs(const float2 *src, double *dst, long n, cudaStream_t s);
 int occupancy_lbfgs(int *blocks_per_sm);

@@ -283,39 +283,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // ---- tiles, lists and staged basis factors ------------------------------------
-struct TcArgs {
-  GridGeom g;  // 4 x 4 x 8 tiles
-  int n_tiles;
-  const int *tile_ptr, *keys;   // image lists (set-up only)
-  const float4 *tab[3];         // per axis [mu][img][i]: (sq, c hi, c lo, 0),
-                                // c = norm^(1/3) exp(-alpha sq) as a float pair
-  const float *rc2f;            // [M]
-  const int *nu;                // [n_tiles] functions per tile (images merged)
-  const int *xr_off;            // [n_tiles + 1] density K steps before each tile
-  const int *mu_off;            // [n_tiles + 1] functions of the tiles before each tile
-  const int *tmu;               // functions of each tile, ascending
-  int n_vg;                     // V groups: runs of consecutive tiles, union <= kNmax functions
-  const int *vg_t0;             // [n_vg + 1] first tile of each group
-  const int *vg_nu;             // [n_vg] functions of the group's union
-  const int *vg_eoff;           // [n_vg + 1] padded union entries before each group
-  const int *vg_xoff;           // [n_vg + 1] 256-byte units of X^T slices before each group
-  const int *vg_mu;             // union function lists, ascending, padded
-  uint8_t *xr;                  // density X slices, 16 KB per K step
-  uint8_t *xv;                  // V X^T slices, 1 KB per padded union entry and tile
-  float4 *vent;                 // per padded union entry: (mu bits, 2^(e_a - 8), bound, 0)
-  signed char *rowexp;          // [G] density row exponents e_p
-  const uint2 *Osl;             // [M][NoccP] BF16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
-  const float *oscale;          // [chunks * 128] 2^g_m, zero beyond N
-  int Nocc, NoccP;              // occupied orbitals; O-slice row length (even)
-  double *rho;                  // [G]
-  float2 *rhof;                 // [G] rho as float pairs
-  const double *v;              // [G]
-  float2 *vt;                   // [n_tiles][128] v dV at the tile points (float pairs)
-  unsigned long long *Vfix;     // [M][M] V (upper triangle) in fixed point, then [M*M] = max|v| bits
-  double dV;
-  int *flags;
-};
-
 __device__ __forceinline__ int tile_point(const GridGeom &g, int t, int p) {
   const int bz = t % g.nbz, by = (t / g.nbz) % g.nby, bx = t / (g.nbz * g.nby);
   const int i = bx * 4 + (p >> 5), j = by * 4 + ((p >> 3) & 3), k = bz * 8 + (p & 7);
@@ -593,14 +560,22 @@ __device__ __forceinline__ float2 rho_sum8(const uint32_t (&r)[32], const float 
   return make_float2(sm.x, __fadd_rn(rs.y, sm.y));
 }
 
-__global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
+// job j of this CTA (density): its system's arguments, tile, orbital chunk and
+// the tile's number of chunks
+struct RhoJob {
+  const TcArgs *A;
+  int t, mc, nmc;
+  bool on;
+};
+__device__ __forceinline__ RhoJob rho_job(const TcBatch &B, int j) {
+  const int4 q = B.jobs[B.cta_ptr[blockIdx.x] + j];
+  return RhoJob{B.sys + q.x, q.y, q.z, q.w, B.active[q.x] != 0};
+}
+
+__global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
   extern __shared__ __align__(1024) uint8_t dsm[];
-  // column scales 2^g_m, zero-padded: staged in shared memory for one chunk of
-  // orbitals, read from the (zero-padded) global array for several
-  float *fs = (float *)(dsm + kRhoStages * kRhoStage);
   __shared__ RhoBars R;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int nmc = (A.Nocc + kNmax - 1) / kNmax;
   if (tid == 0) {
     for (int s = 0; s < kRhoStages; ++s) {
       mbar_init(&R.tma_full[s], 1);
@@ -616,17 +591,11 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) tmem_alloc(&R.tbase);
-  if (nmc == 1)
-    for (int m = tid; m < kNmax; m += blockDim.x) fs[m] = m < A.Nocc ? A.oscale[m] : 0.f;
-  const float *fsrc = nmc == 1 ? fs : A.oscale;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = R.tbase;
-  const int ntl = A.n_tiles > (int)blockIdx.x
-                      ? (A.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
-                      : 0;
-  const int njobs = ntl * nmc;
+  const int njobs = B.cta_ptr[blockIdx.x + 1] - B.cta_ptr[blockIdx.x];
   volatile int *stop = &R.stop;
 
   if (w == kRhoEpiW + kRhoBldW) {
@@ -634,7 +603,10 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     int fill = 0;
     bool ok = true;
     for (int j = 0; j < njobs && ok; ++j) {
-      const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+      const RhoJob J = rho_job(B, j);
+      if (!J.on) continue;
+      const TcArgs &A = *J.A;
+      const int t = J.t, mc = J.mc;
       const int k0 = A.xr_off[t], nk = A.xr_off[t + 1] - k0, nu = A.nu[t];
       const int m0 = mc * kNmax, nme = min(kNmax, A.NoccP - m0);  // even
       // functions of the tile: lane l holds entries l, l + 32, l + 64, l + 96
@@ -661,7 +633,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
         const int mu = __shfl_sync(0xffffffffu, mv, a & 31);
         // row c of the staging area (rows nme * 8 bytes apart) <- O-slice row mu_c
         const int mup = __shfl_up_sync(0xffffffffu, mu, 1);
-        const bool cont = nmc == 1 && lane > 0 && lane < nrow && mu == mup + 1;
+        const bool cont = J.nmc == 1 && lane > 0 && lane < nrow && mu == mup + 1;
         const unsigned cb = __ballot_sync(0xffffffffu, cont);
         if (lane < nrow && !cont) {  // a run starts here: rows lane .. lane + len - 1
           const unsigned after = ~(cb >> (lane + 1));
@@ -680,14 +652,17 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
   } else if (w == kRhoEpiW + kRhoBldW + 1) {
     // ---------------------------------- MMA issue ----------------------------------
     if (lane == 0) {
-      int fill = 0;
+      int fill = 0, jp = 0;  // jp: jobs run (the accumulator hand-overs)
       bool ok = true;
       for (int j = 0; j < njobs && ok; ++j) {
-        const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+        const RhoJob J = rho_job(B, j);
+        if (!J.on) continue;
+        const TcArgs &A = *J.A;
+        const int t = J.t, mc = J.mc;
         const int nk = A.xr_off[t + 1] - A.xr_off[t];
         const int nm = min(kNmax, A.Nocc - mc * kNmax);
         const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
-        if (j > 0 && !mbar_wait(&R.acc_empty, (j - 1) & 1, stop)) { ok = false; break; }
+        if (jp > 0 && !mbar_wait(&R.acc_empty, (jp - 1) & 1, stop)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t idesc = idesc_bf16(nmpad), idesc2 = idesc_bf16(2 * nmpad);
         for (int kk = 0; kk < nk; ++kk, ++fill) {
@@ -716,6 +691,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
           mma_commit(&R.empty[s]);  // the stage is free once these MMAs complete
         }
         if (ok) mma_commit(&R.acc_full);
+        ++jp;
       }
       if (!ok) atomicExch((int *)stop, 1);
       mma_commit(&R.fin);  // every MMA issued has completed before the TMEM is released
@@ -727,7 +703,10 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     int fill = 0;
     bool ok = true;
     for (int j = 0; j < njobs && ok; ++j) {
-      const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+      const RhoJob J = rho_job(B, j);
+      if (!J.on) continue;
+      const TcArgs &A = *J.A;
+      const int t = J.t, mc = J.mc;
       const int nk = A.xr_off[t + 1] - A.xr_off[t], nu = A.nu[t];
       const int nm = min(kNmax, A.Nocc - mc * kNmax);
       const int nme = min(kNmax, A.NoccP - mc * kNmax);  // staged row length (even)
@@ -735,8 +714,8 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       for (int kk = 0; kk < nk; ++kk, ++fill) {
         const int s = fill % kRhoStages, use = fill / kRhoStages;
         if (!mbar_wait(&R.tma_full[s], use & 1, stop)) { ok = false; break; }
-        uint8_t *B = dsm + s * kRhoStage + kRhoA;
-        const uint8_t *G = B + kRhoB;
+        uint8_t *Bs = dsm + s * kRhoStage + kRhoA;
+        const uint8_t *G = Bs + kRhoB;
         const int nrow = max(0, min(kKs, nu - kk * kKs));
         for (int q = bt; q < nmpad * 2; q += kRhoBld) {  // items (orbital, 8 functions)
           const int m = q % nmpad, h = q / nmpad;
@@ -757,9 +736,9 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
           v1.z = __byte_perm(w01[4], w01[5], 0x7632); v1.w = __byte_perm(w01[6], w01[7], 0x7632);
           v2.x = __byte_perm(w2[0], w2[1], 0x5410); v2.y = __byte_perm(w2[2], w2[3], 0x5410);
           v2.z = __byte_perm(w2[4], w2[5], 0x5410); v2.w = __byte_perm(w2[6], w2[7], 0x5410);
-          *(uint4 *)(B + off) = v0;
-          *(uint4 *)(B + nmpad * 32 + off) = v1;
-          *(uint4 *)(B + 2 * nmpad * 32 + off) = v2;
+          *(uint4 *)(Bs + off) = v0;
+          *(uint4 *)(Bs + nmpad * 32 + off) = v1;
+          *(uint4 *)(Bs + 2 * nmpad * 32 + off) = v2;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&R.bld_full[s]);
@@ -774,21 +753,26 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
     const int pe = quad * 32 + lane;
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
     float2 rsum = make_float2(0.f, 0.f);
-    int ntile = 0;  // tiles finished (part buffer hand-overs)
+    int ntile = 0, jp = 0;  // tiles finished (part buffer hand-overs), jobs run
     bool ok = true;
     for (int j = 0; j < njobs && ok; ++j) {
-      const int t = blockIdx.x + (j / nmc) * gridDim.x, mc = j % nmc;
+      const RhoJob J = rho_job(B, j);
+      if (!J.on) continue;
+      const TcArgs &A = *J.A;
+      const int t = J.t, mc = J.mc;
       const int nm = min(kNmax, A.Nocc - mc * kNmax);
       const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
       const int gp = tile_point(A.g, t, pe);
       const int ep = gp >= 0 ? (int)A.rowexp[gp] : 0;
-      ok = __all_sync(0xffffffffu, mbar_wait(&R.acc_full, j & 1, stop));
+      ok = __all_sync(0xffffffffu, mbar_wait(&R.acc_full, jp & 1, stop));
+      ++jp;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // this warp's column part in chunks of 8, the next chunk's loads in
-      // flight while the current one is summed
+      // flight while the current one is summed; the column scales 2^g_m come
+      // from the (zero-padded) global array of the job's system
       const int cb = part * (nmpad / kRhoParts), ce = cb + nmpad / kRhoParts;
-      const float *f = fsrc + mc * kNmax;
+      const float *f = A.oscale + mc * kNmax;
       uint32_t ra[32], rb[32];
       tmem_ld_issue(tmem + lanebits + cb, ra, nmpad);
       for (int c0 = cb; c0 < ce; c0 += 16) {
@@ -802,7 +786,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&R.acc_empty);
-      if (mc == nmc - 1) {  // the tile is done: add the column parts
+      if (mc == J.nmc - 1) {  // the tile is done: add the column parts
         if (part > 0) {
           if (ntile > 0) ok = mbar_wait(&R.part_empty, (ntile - 1) & 1, stop);
           R.part[part - 1][pe] = rsum;
@@ -831,7 +815,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcArgs A) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (w == 0) tmem_dealloc(tmem);
-  if (tid == 0 && R.stop) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
+  if (tid == 0 && R.stop) atomicExch(B.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
 }
 
 // ---- potential matrix ---------------------------------------------------------
@@ -891,12 +875,22 @@ __device__ __forceinline__ void tmem_ld2_wait(uint32_t (&r)[16]) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
+// job `it` of this CTA (V pass): its system's arguments and group
+struct VJob {
+  const TcArgs *A;
+  int g;
+  bool on;
+};
+__device__ __forceinline__ VJob v_job(const TcBatch &B, int it) {
+  const int4 q = B.jobs[B.cta_ptr[blockIdx.x] + it];
+  return VJob{B.sys + q.x, q.y, B.active[q.x] != 0};
+}
+
+__global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
   extern __shared__ __align__(1024) uint8_t dsm[];
   uint8_t *tbuf = dsm + kVStages * kVStage;  // 2 group buffers: vt[nt * 128] float2, vent[np] float4
   __shared__ VBars R;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int M = A.g.M;
   if (tid == 0) {
     for (int s = 0; s < kVStages; ++s) {
       mbar_init(&R.tma_full[s], 1);
@@ -918,20 +912,23 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = R.tbase;
-  // a contiguous run of groups per CTA: CTAs running at the same time work in
-  // different parts of the box and rarely add into the same entries of V
-  const int tbeg = (int)((long)A.n_vg * blockIdx.x / gridDim.x);
-  const int ntl = (int)((long)A.n_vg * (blockIdx.x + 1) / gridDim.x) - tbeg;
+  // each CTA's jobs are a contiguous run of groups (of one system or a few):
+  // CTAs running at the same time work in different parts of a box and rarely
+  // add into the same entries of V
+  const int ntl = B.cta_ptr[blockIdx.x + 1] - B.cta_ptr[blockIdx.x];
   volatile int *stop = &R.stop;
   constexpr int kSteps = kTP / kKs;  // 8 K steps of 16 points per tile of the group
 
   if (w == kVEpiW + kVBldW) {
     // ------------------------ bulk copies: tile buffers and X^T ------------------------
     if (lane == 0) {
-      int fill = 0, it = 0;
+      int fill = 0, it = 0;  // it: jobs run (the group buffer hand-overs)
       bool ok = true;
-      for (; it < ntl && ok; ++it) {
-        const int g = tbeg + it, mb = it & 1;
+      for (int jj = 0; jj < ntl && ok; ++jj) {
+        const VJob J = v_job(B, jj);
+        if (!J.on) continue;
+        const TcArgs &A = *J.A;
+        const int g = J.g, mb = it & 1;
         const int t0 = A.vg_t0[g], nt = A.vg_t0[g + 1] - t0;
         const int e0 = A.vg_eoff[g], np = A.vg_eoff[g + 1] - e0;
         if (it >= 2 && !mbar_wait(&R.tile_empty[mb], ((it >> 1) - 1) & 1, stop)) { ok = false; break; }
@@ -947,6 +944,7 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
           bulk_g2s_stream(dsm + s * kVStage + kVA, src + (size_t)kk * np * 32 * kVSlX, np * 32 * kVSlX,
                           &R.tma_full[s]);
         }
+        ++it;
       }
       if (!ok) atomicExch((int *)stop, 1);
       // the copies still in flight land before the CTA exits
@@ -957,10 +955,13 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   } else if (w == kVEpiW + kVBldW + 1) {
     // ---------------------------------- MMA issue ----------------------------------
     if (lane == 0) {
-      int fill = 0;
+      int fill = 0, it = 0;
       bool ok = true;
-      for (int it = 0; it < ntl && ok; ++it) {
-        const int g = tbeg + it, buf = it & 1;
+      for (int jj = 0; jj < ntl && ok; ++jj, ++it) {
+        const VJob J = v_job(B, jj);
+        if (!J.on) { --it; continue; }
+        const TcArgs &A = *J.A;
+        const int g = J.g, buf = it & 1;
         const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
         const int np = A.vg_eoff[g + 1] - A.vg_eoff[g];
         // the accumulator pair of group it - 2 has been read
@@ -1001,10 +1002,13 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     // -------------------- W = (v X)^T: rows b, 8 points of each K step ----------------------
     const int bt = tid - kVEpi;
     const int b = bt & 127, h = bt >> 7;
-    int fill = 0;
+    int fill = 0, it = 0;
     bool ok = true;
-    for (int it = 0; it < ntl && ok; ++it) {
-      const int g = tbeg + it, mb = it & 1;
+    for (int jj = 0; jj < ntl && ok; ++jj, ++it) {
+      const VJob J = v_job(B, jj);
+      if (!J.on) { --it; continue; }
+      const TcArgs &A = *J.A;
+      const int g = J.g, mb = it & 1;
       const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
       const int np = A.vg_eoff[g + 1] - A.vg_eoff[g];
       const int nu = A.vg_nu[g];
@@ -1076,10 +1080,16 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
     const int quad = w & 3, part = w >> 2;
     const int i = quad * 32 + lane;  // accumulator lane = W row
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
-    const int fixe = vfix_exp((unsigned)A.Vfix[(long)M * M]);
+    int it = 0;
     bool ok = true;
-    for (int it = 0; it < ntl && ok; ++it) {
-      const int g = tbeg + it, mb = it & 1, buf = it & 1;
+    for (int jj = 0; jj < ntl && ok; ++jj, ++it) {
+      const VJob J = v_job(B, jj);
+      if (!J.on) { --it; continue; }
+      const TcArgs &A = *J.A;
+      const int M = A.g.M;
+      // fixed-point unit of the job's system (its max |v| from the potential pass)
+      const int fixe = vfix_exp((unsigned)A.Vfix[(long)M * M]);
+      const int g = J.g, mb = it & 1, buf = it & 1;
       const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
       const int nu = A.vg_nu[g];
       ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop) &&
@@ -1126,17 +1136,20 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcArgs A) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (w == 0) tmem_dealloc(tmem);
-  if (tid == 0 && R.stop) atomicExch(A.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
+  if (tid == 0 && R.stop) atomicExch(B.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
 }
 
-// V (upper triangle) from its fixed-point sums
-__global__ void vfix_kernel(const unsigned long long *Vfix, int M, float2 *Vout) {
-  const int F = vfix_exp((unsigned)Vfix[(long)M * M]);
+// V (upper triangle) from its fixed-point sums; blockIdx.y picks the system
+__global__ void vfix_kernel(const VfArgs *av, const int *active) {
+  if (!active[blockIdx.y]) return;
+  const VfArgs &a = av[blockIdx.y];
+  const int M = a.M;
+  const int F = vfix_exp((unsigned)a.Vfix[(long)M * M]);
   const long MM = (long)M * M;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MM;
        e += (long)gridDim.x * blockDim.x) {
     if (e / M > e % M) continue;
-    Vout[e] = pair::split(ldexp((double)(long long)Vfix[e], F));
+    a.Vout[e] = pair::split(ldexp((double)(long long)a.Vfix[e], F));
   }
 }
 
@@ -1159,11 +1172,14 @@ __global__ void tables_f32_kernel(const double *sq, const double *ex, const doub
 // chain): g_m = ilogb(max_mu |O_mu,m|) + 2, K0 + K1 + K2 = O 2^(8 - g) to 24 bits
 // (K_k on the 2^-8k grid); dO = O - Oq (FP64) for the first-order energy
 // correction sum (4 H O) o dO.
-__global__ void __launch_bounds__(256) oslice_kernel(const float2 *O, int M, int N, int NP,
-                                                     uint2 *Osl, float *oscale, double *dO) {
-  const int m = blockIdx.x;
+__global__ void __launch_bounds__(256) oslice_kernel(const OsArgs *av, const int *active) {
+  if (!active[blockIdx.y]) return;
+  const OsArgs &a = av[blockIdx.y];
+  const int m = blockIdx.x;  // orbital (blockIdx.y: the system)
+  if (m >= a.N) return;
+  const int M = a.M, N = a.N;
   double mx = 0.0;
-  for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(pair::to_double(O[(long)r * N + m])));
+  for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(pair::to_double(a.O[(long)r * N + m])));
   __shared__ double red[256];
   red[threadIdx.x] = mx;
   __syncthreads();
@@ -1173,9 +1189,9 @@ __global__ void __launch_bounds__(256) oslice_kernel(const float2 *O, int M, int
   }
   mx = red[0];
   const int g = mx > 0.0 ? ilogb(mx) + 2 : 0;
-  if (threadIdx.x == 0) oscale[m] = ldexpf(1.f, g);
+  if (threadIdx.x == 0) a.oscale[m] = ldexpf(1.f, g);
   for (int r = threadIdx.x; r < M; r += blockDim.x) {
-    const double o = pair::to_double(O[(long)r * N + m]);
+    const double o = pair::to_double(a.O[(long)r * N + m]);
     const double t0 = ldexp(o, 8 - g);
     const double r0 = rint(t0);
     const double t1 = (t0 - r0) * 256.0;
@@ -1183,14 +1199,14 @@ __global__ void __launch_bounds__(256) oslice_kernel(const float2 *O, int M, int
     const double t2 = (t1 - r1) * 256.0;
     const double r2 = rint(t2);
     const double q = ldexp(r0 + (r1 + r2 * (1.0 / 256.0)) * (1.0 / 256.0), g - 8);
-    dO[(long)r * N + m] = o - q;
-    Osl[(long)r * NP + m] = make_uint2(
+    a.dO[(long)r * N + m] = o - q;
+    a.Osl[(long)r * a.NP + m] = make_uint2(
         (uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)(r1 * (1.0 / 256.0))) << 16),
         (uint32_t)bf16_bits((float)(r2 * (1.0 / 65536.0))));
   }
 }
 
-static TcArgs tc_args(etdm_handle *h) {
+TcArgs tc_args(etdm_handle *h) {
   TcArgs a{};
   a.g = h->geom_tc;
   a.n_tiles = h->n_tiles_tc;
@@ -1264,35 +1280,47 @@ int tc_v_entries(int nu) { return vpad(nu); }
 int tc_group_max() { return kVGmax; }
 int tc_v_slices() { return kVSlX; }
 
-cudaError_t launch_oslice(etdm_handle *h, cudaStream_t s) {
-  oslice_kernel<<<h->N, 256, 0, s>>>(reinterpret_cast<const float2 *>(h->d_O), h->M, h->N, h->N + (h->N & 1), h->d_Osl, h->d_oscale,
-                                     h->d_dO);
-  return cudaGetLastError();
+OsArgs os_args(etdm_handle *h) {
+  OsArgs a{};
+  a.O = reinterpret_cast<const float2 *>(h->d_O);
+  a.M = h->M; a.N = h->N; a.NP = h->N + (h->N & 1);
+  a.Osl = h->d_Osl; a.oscale = h->d_oscale; a.dO = h->d_dO;
+  return a;
 }
 
-cudaError_t launch_rho_tc(etdm_handle *h, cudaStream_t s) {
-  const int nmc = (h->N + kNmax - 1) / kNmax;
-  const size_t sm = (size_t)kRhoStages * kRhoStage + (nmc == 1 ? (size_t)kNmax * sizeof(float) : 0);
-  cudaError_t e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+VfArgs vf_args(etdm_handle *h) {
+  VfArgs a{};
+  a.Vfix = h->d_Vfix; a.M = h->M; a.Vout = h->d_Vfin;
+  return a;
+}
+
+cudaError_t launch_mixed_rho(const MixedPlan &P, cudaStream_t s) {
+  oslice_kernel<<<dim3(std::max(P.os_maxN, 1), P.n_sys), 256, 0, s>>>(P.os, P.active);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  rho_tc_kernel<<<std::min(h->n_tiles_tc, h->num_sms), kRhoThreads, sm, s>>>(tc_args(h));
+  const size_t sm = (size_t)kRhoStages * kRhoStage;
+  e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  rho_tc_kernel<<<P.rho.grid, kRhoThreads, sm, s>>>(P.rho);
   return cudaGetLastError();
 }
 
-cudaError_t launch_vmat_tc(etdm_handle *h, cudaStream_t s) {
+cudaError_t launch_mixed_potential(const MixedPlan &P, cudaStream_t s) {
+  // the V pass adds into zeroed fixed-point sums; the potential pass records max |v|
+  cudaError_t e = cudaMemsetAsync(P.vfix, 0, P.vfix_bytes, s);
+  if (e != cudaSuccess) return e;
+  return launch_df_potential(P.dfl, P.df, P.active, s);
+}
+
+cudaError_t launch_mixed_vmat(const MixedPlan &P, cudaStream_t s) {
   const size_t sm = (size_t)kVStages * kVStage + 2 * (size_t)kVTileBuf;
   cudaError_t e = cudaFuncSetAttribute(vmat_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  // the fixed-point sums and max|v| were reset, and v dV laid out in tile
-  // order, by the potential pass
-  const TcArgs a = tc_args(h);
-  const size_t MM = (size_t)h->M * h->M;
-  vmat_tc_kernel<<<std::max(1, std::min(h->n_vg, h->num_sms)), kVThreads, sm, s>>>(a);
+  vmat_tc_kernel<<<P.v.grid, kVThreads, sm, s>>>(P.v);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  vfix_kernel<<<(int)std::min<size_t>((MM + 255) / 256, 1024), 256, 0, s>>>(h->d_Vfix, h->M, h->d_Vfin);
+  vfix_kernel<<<dim3(P.vf_blocks, P.n_sys), 256, 0, s>>>(P.vf, P.active);
   return cudaGetLastError();
 }
 

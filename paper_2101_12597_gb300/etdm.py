@@ -36,7 +36,9 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_lbfgs_reset", "etdm_minimize", "etdm_check", "etdm_layout",
            "etdm_array_bytes", "etdm_get_array", "etdm_set_profiling",
            "etdm_stage_times", "etdm_last_error", "etdm_free",
-           "etdm_lbfgs_direction_noalloc", "etdm_lbfgs_direction_noalloc_status"]
+           "etdm_lbfgs_direction_noalloc", "etdm_lbfgs_direction_noalloc_status",
+           "etdm_init_batch", "etdm_num_systems", "etdm_system_layout", "etdm_system_handle",
+           "etdm_set_active"]
 STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
 
 
@@ -98,13 +100,22 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.etdm_lbfgs_direction_noalloc.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int64,
                                                  P, P, P]
     lib.etdm_lbfgs_direction_noalloc_status.argtypes = [P]
+    lib.etdm_init_batch.argtypes = [ctypes.POINTER(EtdmSystem), ctypes.c_int32,
+                                    ctypes.POINTER(EtdmOptions), ctypes.POINTER(P)]
+    lib.etdm_num_systems.argtypes = [P]
+    lib.etdm_num_systems.restype = ctypes.c_int32
+    lib.etdm_system_layout.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]
+    lib.etdm_system_handle.argtypes = [P, ctypes.c_int32]
+    lib.etdm_system_handle.restype = P
+    lib.etdm_set_active.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.etdm_last_error.argtypes = [P]
     lib.etdm_last_error.restype = ctypes.c_char_p
     lib.etdm_free.argtypes = [P]
     lib.etdm_free.restype = None
     for name in EXPORTS:
         if name not in ("etdm_default_options", "etdm_last_error", "etdm_free",
-                        "etdm_array_bytes"):
+                        "etdm_array_bytes", "etdm_num_systems", "etdm_system_handle"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -161,6 +172,43 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _system_struct(sysd, s=None):
+    """An EtdmSystem for the system dict sysd (etdm_synth's layout) and the
+    arrays it points into (keep them alive while the struct is used)."""
+    keep = dict(
+        pos=np.ascontiguousarray(sysd["pos"], dtype=np.float64),
+        Z=np.ascontiguousarray(sysd["Z"], dtype=np.float64),
+        bf_atom=np.ascontiguousarray(sysd["bf_atom"], dtype=np.int32),
+        bf_exp=np.ascontiguousarray(sysd["bf_exp"], dtype=np.float64),
+        bf_rcut=np.ascontiguousarray(sysd["bf_rcut"], dtype=np.float64))
+    s = EtdmSystem() if s is None else s
+    s.n_atoms = len(keep["Z"])
+    s.pos = _dptr(keep["pos"])
+    s.Z = _dptr(keep["Z"])
+    s.n_basis = len(keep["bf_exp"])
+    s.bf_atom = keep["bf_atom"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    s.bf_exp = _dptr(keep["bf_exp"])
+    s.bf_rcut = _dptr(keep["bf_rcut"])
+    for a in range(3):
+        s.box[a] = float(sysd["box"][a])
+        s.grid[a] = int(sysd["grid"][a])
+    s.ion_sigma = float(sysd["ion_sigma"])
+    s.n_electrons = int(sysd["n_electrons"])
+    return s, keep
+
+
+def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks):
+    o = EtdmOptions()
+    lib.etdm_default_options(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    o.lbfgs_m = lbfgs_m
+    o.gamma = gamma
+    o.beta0 = beta0
+    o.device = device
+    o.dense_blocks = dense_blocks
+    return o
+
+
 class ETDM:
     """One system on one GPU: the handle of etdm_init_basis."""
 
@@ -171,45 +219,31 @@ class ETDM:
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
         self.lib = load_library()
         self.device = device
-        self._keep = dict(
-            pos=np.ascontiguousarray(sysd["pos"], dtype=np.float64),
-            Z=np.ascontiguousarray(sysd["Z"], dtype=np.float64),
-            bf_atom=np.ascontiguousarray(sysd["bf_atom"], dtype=np.int32),
-            bf_exp=np.ascontiguousarray(sysd["bf_exp"], dtype=np.float64),
-            bf_rcut=np.ascontiguousarray(sysd["bf_rcut"], dtype=np.float64))
-        k = self._keep
-        s = EtdmSystem()
-        s.n_atoms = len(k["Z"])
-        s.pos = _dptr(k["pos"])
-        s.Z = _dptr(k["Z"])
-        s.n_basis = len(k["bf_exp"])
-        s.bf_atom = k["bf_atom"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        s.bf_exp = _dptr(k["bf_exp"])
-        s.bf_rcut = _dptr(k["bf_rcut"])
-        for a in range(3):
-            s.box[a] = float(sysd["box"][a])
-            s.grid[a] = int(sysd["grid"][a])
-        s.ion_sigma = float(sysd["ion_sigma"])
-        s.n_electrons = int(sysd["n_electrons"])
-        o = EtdmOptions()
-        self.lib.etdm_default_options(ctypes.byref(o))
-        o.precision = PRECISION[precision]
-        o.lbfgs_m = lbfgs_m
-        o.gamma = gamma
-        o.beta0 = beta0
-        o.device = device
-        o.dense_blocks = dense_blocks
+        s, self._keep = _system_struct(sysd)
+        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
         if rc != ETDM_OK:
             raise EtdmError(rc, self.lib.etdm_last_error(None).decode())
         self.h = h
+        self._borrowed = False
+        self._read_dims()
+        self.dev = torch.device("cuda", device)
+
+    @classmethod
+    def _view(cls, lib, h, dev):
+        """A system of a batch: inspection through its borrowed handle."""
+        v = object.__new__(cls)
+        v.lib, v.h, v.dev, v.device, v._borrowed = lib, h, dev, dev.index, True
+        v._read_dims()
+        return v
+
+    def _read_dims(self):
         dims = (ctypes.c_int64 * 12)()
         self.lib.etdm_layout(self.h, dims)
         self.dims = dict(zip(DIM_NAMES, [int(x) for x in dims]))
         self.M, self.N, self.V = self.dims["M"], self.dims["N"], self.dims["V"]
-        self.dev = torch.device("cuda", device)
 
     # -- helpers ----------------------------------------------------------------
     def _raise(self, rc):
@@ -319,8 +353,126 @@ class ETDM:
                 dict(zip(STAGES, cnt[:len(STAGES)].tolist())), int(cnt[-1]))
 
     def close(self):
-        """Release the handle's device memory (the object is unusable afterwards)."""
+        """Release the handle's device memory (the object is unusable afterwards);
+        a system of a batch is released with its batch."""
         if getattr(self, "h", None):
+            if not getattr(self, "_borrowed", False):
+                self.lib.etdm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ETDMBatch:
+    """Many systems in one handle (etdm_init_batch): packed variable vectors,
+    one energy per system, one graph per evaluation on the mixed path."""
+
+    def __init__(self, systems, precision="mixed", lbfgs_m=3, gamma=0.25, beta0=1.0,
+                 device=0, dense_blocks=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ETDMBatch needs a CUDA GPU; there is no CPU fallback")
+        self.lib = load_library()
+        n = len(systems)
+        if n < 1:
+            raise ValueError("need at least one system")
+        arr = (EtdmSystem * n)()
+        self._keep = [_system_struct(d, arr[i])[1] for i, d in enumerate(systems)]
+        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks)
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        rc = self.lib.etdm_init_batch(arr, n, ctypes.byref(o), ctypes.byref(h))
+        if rc != ETDM_OK:
+            raise EtdmError(rc, self.lib.etdm_last_error(None).decode())
+        self.h = h
+        self.n = n
+        self.dev = torch.device("cuda", device)
+        off, ln = ctypes.c_int64(), ctypes.c_int64()
+        self.offsets = []
+        for i in range(n):
+            self._raise(self.lib.etdm_system_layout(self.h, i, ctypes.byref(off), ctypes.byref(ln)))
+            self.offsets.append((int(off.value), int(ln.value)))
+        self.nvar = self.offsets[-1][0] + self.offsets[-1][1]
+        self.systems = [ETDM._view(self.lib, self.lib.etdm_system_handle(self.h, i), self.dev)
+                        for i in range(n)]
+        self.shapes = [(m.N, m.V) for m in self.systems]
+
+    def _raise(self, rc):
+        if rc != ETDM_OK:
+            raise EtdmError(rc, self.lib.etdm_last_error(self.h).decode())
+
+    def pack(self, arrays):
+        """One packed float64 vector from the per-system (N_i, V_i) arrays."""
+        return np.concatenate([np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+                               for x in arrays])
+
+    def split(self, x):
+        """Per-system (N_i, V_i) views of a packed vector (numpy or torch)."""
+        return [x[o:o + ln].reshape(shp) for (o, ln), shp in zip(self.offsets, self.shapes)]
+
+    def energy_grad(self, a, E=None, g=None, stream=None):
+        """E [n] and the packed gradient for the packed point a (on the device)."""
+        import torch
+        _require(a, self.dev, "a", numel=self.nvar)
+        E = torch.empty(self.n, dtype=torch.float64, device=self.dev) if E is None else E
+        g = torch.empty_like(a) if g is None else g
+        _require(E, self.dev, "E", numel=self.n)
+        _require(g, self.dev, "g", numel=self.nvar)
+        self._raise(self.lib.etdm_energy_grad(self.h, ctypes.c_void_p(a.data_ptr()),
+                                              ctypes.c_void_p(E.data_ptr()),
+                                              ctypes.c_void_p(g.data_ptr()), _stream_ptr(stream)))
+        return E, g
+
+    def energy_grad_host(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if a.size != self.nvar:
+            raise ValueError(f"a: expected {self.nvar} packed variables, got {a.size}")
+        E = np.zeros(self.n)
+        g = np.zeros(self.nvar)
+        self._raise(self.lib.etdm_energy_grad_host(self.h, _dptr(a), _dptr(E), _dptr(g)))
+        return E, g
+
+    def set_active(self, mask):
+        m = np.ascontiguousarray(mask, dtype=np.int32).reshape(-1)
+        if m.size != self.n:
+            raise ValueError(f"mask: expected {self.n} entries")
+        self._raise(self.lib.etdm_set_active(self.h, m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+    def minimize(self, a, n_steps, stream=None):
+        """n_steps ETDM iterations of every system, in place on the packed a;
+        returns (E, alpha, trials), each [n, n_steps + 1]."""
+        _require(a, self.dev, "a", numel=self.nvar)
+        E = np.zeros((self.n, n_steps + 1))
+        al = np.zeros((self.n, n_steps + 1))
+        tr = np.zeros((self.n, n_steps + 1), dtype=np.int32)
+        self._raise(self.lib.etdm_minimize(self.h, ctypes.c_void_p(a.data_ptr()), n_steps,
+                                           _dptr(E), _dptr(al),
+                                           tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           _stream_ptr(stream)))
+        return E, al, tr
+
+    def lbfgs_reset(self):
+        self._raise(self.lib.etdm_lbfgs_reset(self.h))
+
+    def check(self, stream=None):
+        self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream)))
+
+    def launches(self):
+        """Kernel launches (graph kernel nodes included) since the last call."""
+        ms = np.zeros(8)
+        cnt = np.zeros(8, dtype=np.int64)
+        self._raise(self.lib.etdm_stage_times(self.h, _dptr(ms),
+                                              cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return int(cnt[-1])
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in getattr(self, "systems", []):
+                m.h = None
             self.lib.etdm_free(self.h)
             self.h = None
 

@@ -1,0 +1,210 @@
+"""The batched path (148 molecules of uneven size, each in its own 48^3 cell,
+one handle, one graph per evaluation) against the FP64 oracle, molecule by
+molecule.
+
+Bars as for one system: energy within 1e-6 Ha for every molecule; gradient
+within 1e-5 of max|g| (max-abs) for the largest, the smallest and ten seeded
+molecules, compared element by element; a batched 20-step minimization whose
+per-molecule trajectories match the oracle's accepted steps (trial counts
+equal, energies within 1e-6 Ha, step lengths within 1e-9).  The oracle runs in
+a pool of processes started with spawn (16 cores on the GPU machine)."""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import etdm_synth as synth
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-6
+G_TOL = 1e-5
+STEPS = 20
+
+
+def _oracle_energy_grad(i):
+    from oracle.etdm_oracle import Oracle
+    d = synth.config_molecules148()[i]
+    return Oracle(d).energy_grad(d["a0"])
+
+
+def _oracle_trajectory(i):
+    from oracle.etdm_oracle import Oracle, minimize
+    d = synth.config_molecules148()[i]
+    hist, _ = minimize(Oracle(d), d["a0"], n_steps=STEPS)
+    return hist
+
+
+def _pool_map(fn, items):
+    """fn over items in spawned processes, one BLAS thread each."""
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    try:
+        with mp.get_context("spawn").Pool(min(len(items), os.cpu_count() or 4)) as pool:
+            return pool.map(fn, items)
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.fixture(scope="module")
+def mols():
+    return synth.config_molecules148()
+
+
+@pytest.fixture(scope="module")
+def sample(mols):
+    """The largest and the smallest molecule (by M) and ten seeded others."""
+    M = np.array([len(d["bf_exp"]) for d in mols])
+    big, small = int(np.argmax(M)), int(np.argmin(M))
+    rest = [i for i in range(len(mols)) if i not in (big, small)]
+    pick = np.random.default_rng(148).choice(rest, size=10, replace=False)
+    return [big, small] + sorted(int(i) for i in pick)
+
+
+@pytest.fixture(scope="module")
+def oracle_eg(mols):
+    return _pool_map(_oracle_energy_grad, list(range(len(mols))))
+
+
+@pytest.fixture(scope="module")
+def batch(mols):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2101_12597_gb300.etdm import ETDMBatch
+    b = ETDMBatch(mols, precision="mixed")
+    yield b
+    b.close()
+
+
+def test_batch_layout(batch, mols):
+    assert batch.n == len(mols)
+    off = 0
+    for (o, ln), d in zip(batch.offsets, mols):
+        N, V = d["a0"].shape
+        assert o == off and ln == N * V
+        off += ln
+    assert batch.nvar == off
+
+
+def test_batch_energy_gradient_against_oracle(batch, mols, sample, oracle_eg):
+    import torch
+    a = torch.tensor(batch.pack([d["a0"] for d in mols]), device=batch.dev)
+    E, g = batch.energy_grad(a)
+    torch.cuda.synchronize()
+    batch.check()
+    E = E.cpu().numpy()
+    g = batch.split(g.cpu().numpy())
+    dE = np.abs(E - np.array([e for e, _ in oracle_eg]))
+    print(f"batch of {len(mols)}: max |dE| = {dE.max():.3e} Ha (molecule {int(dE.argmax())})")
+    assert dE.max() < E_TOL
+    worst = 0.0
+    for i in sample:
+        gref = oracle_eg[i][1]
+        err = float(np.abs(g[i] - gref).max() / np.abs(gref).max())
+        worst = max(worst, err)
+        assert err <= G_TOL, (i, err)
+    print(f"sampled gradients: worst {worst:.3e} of max|g|")
+
+
+def test_batch_active_mask_leaves_inactive_systems_alone(batch, mols):
+    """A masked evaluation computes the active molecules exactly as the full
+    one (the same kernels run on the same jobs) and writes nothing for the
+    others."""
+    import torch
+    a = torch.tensor(batch.pack([d["a0"] for d in mols]), device=batch.dev)
+    E_all, g_all = batch.energy_grad(a)
+    E_all, g_all = E_all.clone(), g_all.clone()
+    mask = np.zeros(batch.n, dtype=np.int32)
+    mask[::3] = 1
+    batch.set_active(mask)
+    try:
+        E = torch.full((batch.n,), float("nan"), dtype=torch.float64, device=batch.dev)
+        g = torch.full_like(a, float("nan"))
+        batch.energy_grad(a, E=E, g=g)
+        torch.cuda.synchronize()
+        batch.check()
+    finally:
+        batch.set_active(np.ones(batch.n, dtype=np.int32))
+    E, g = E.cpu().numpy(), batch.split(g.cpu().numpy())
+    Ea, ga = E_all.cpu().numpy(), batch.split(g_all.cpu().numpy())
+    for i in range(batch.n):
+        if mask[i]:
+            assert E[i] == Ea[i] and np.array_equal(g[i], ga[i]), i
+        else:
+            assert np.isnan(E[i]) and np.all(np.isnan(g[i])), i
+
+
+def test_batch_minimization_trajectories_match_oracle(batch, mols, sample):
+    """STEPS L-BFGS steps of all 148 molecules in one batched minimization
+    (each with its own line search, the rounds synchronized across the batch);
+    the sampled molecules' accepted steps against the oracle's."""
+    import torch
+    ref = _pool_map(_oracle_trajectory, sample)
+    batch.lbfgs_reset()
+    a = torch.tensor(batch.pack([d["a0"] for d in mols]), device=batch.dev)
+    E, al, tr = batch.minimize(a, STEPS)
+    batch.check()
+    assert np.all(np.isfinite(E)) and np.all(tr[:, 1:] >= 1)
+    assert np.all(np.diff(E, axis=1) <= 1e-6 * np.abs(E[:, :1]))  # no step raises E
+    worst = 0.0
+    for i, hist in zip(sample, ref):
+        for k in range(STEPS + 1):
+            worst = max(worst, abs(E[i, k] - hist[k][0]))
+            assert abs(E[i, k] - hist[k][0]) < E_TOL, (i, k, E[i, k], hist[k][0])
+            assert tr[i, k] == hist[k][2], (i, k, tr[i, k], hist[k][2])
+            assert al[i, k] == pytest.approx(hist[k][1], abs=1e-9), (i, k)
+    print(f"trajectories of {len(sample)} molecules: worst |dE| {worst:.3e} Ha; "
+          f"evaluations per molecule {tr.sum(1).min()}..{tr.sum(1).max()}")
+    # the final point of every molecule: the energy the batch reports is the
+    # energy of the point it returns
+    E2, _ = batch.energy_grad(a)
+    torch.cuda.synchronize()
+    assert np.abs(E2.cpu().numpy() - E[:, -1]).max() < 1e-9 * np.abs(E[:, -1]).max()
+    batch.lbfgs_reset()
+
+
+def test_batch_of_one_equals_the_single_system_path(mols):
+    """A batch of one molecule against the same molecule's own handle (mixed
+    path): the batched kernels compute what the single-system kernels do."""
+    import torch
+    from paper_2101_12597_gb300.etdm import ETDM, ETDMBatch
+    i = 7
+    d = mols[i]
+    b = ETDMBatch([d], precision="mixed")
+    s = ETDM(d, precision="mixed")
+    a = torch.tensor(d["a0"], device="cuda")
+    Eb, gb = b.energy_grad(a.reshape(-1).clone())
+    Es, gs = s.energy_grad(a)
+    torch.cuda.synchronize()
+    b.check()
+    s.check()
+    assert abs(float(Eb[0]) - float(Es[0])) < 1e-11 * abs(float(Es[0]))
+    gs = gs.cpu().numpy().reshape(-1)
+    assert np.abs(gb.cpu().numpy() - gs).max() < 1e-9 * np.abs(gs).max()
+    b.close()
+    s.close()
+
+
+def test_fp64_batch_runs_each_system_on_the_plain_path(mols, sample, oracle_eg):
+    """The plain FP64 baseline of the batched workload (one launch sequence
+    per molecule) on a few molecules, against the oracle."""
+    import torch
+    from paper_2101_12597_gb300.etdm import ETDMBatch
+    idx = sample[:4]
+    b = ETDMBatch([mols[i] for i in idx], precision="fp64")
+    a = torch.tensor(b.pack([mols[i]["a0"] for i in idx]), device=b.dev)
+    E, g = b.energy_grad(a)
+    torch.cuda.synchronize()
+    b.check()
+    g = b.split(g.cpu().numpy())
+    for k, i in enumerate(idx):
+        assert abs(float(E[k]) - oracle_eg[i][0]) < 1e-9
+        gref = oracle_eg[i][1]
+        assert np.abs(g[k] - gref).max() < 1e-9 * np.abs(gref).max()
+    b.close()
