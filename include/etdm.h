@@ -176,6 +176,21 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps,
                   double *E_hist, double *alpha_hist, int32_t *trials_hist,
                   void *stream);
 
+/* Minimize to convergence (Sec. 3.5): the iterations of etdm_minimize until
+ * the Eq. 45 residual of the current point, (1/N_e) sum_i f_i |H psi_i -
+ * sum_j lambda_ij psi_j|^2 with H psi_i represented in the span of the basis
+ * (lambda = O^T H O), is at most tol (Hartree^2; the paper's 1e-10 eV^2 is
+ * 1.3505e-13), or max_steps iterations (the paper stops at 333).  The
+ * residual is computed with every evaluation of the call, in the orthonormal
+ * basis of C0: R = Ubar - U_occ U_occ^T Ubar with Ubar = C0^T (4 H O), value
+ * |R|^2 / (16 N).  History arrays as etdm_minimize (max_steps + 1 entries,
+ * optional), resid_hist receives the residual per step; *steps_done the
+ * iterations taken (0 when the start point already meets tol).  One system
+ * only: a batch returns ETDM_ERR_INVALID_ARG. */
+int etdm_minimize_converge(etdm_handle *h, double *a_dev, int32_t max_steps, double tol,
+                           double *E_hist, double *alpha_hist, int32_t *trials_hist,
+                           double *resid_hist, int32_t *steps_done, void *stream);
+
 /* Wait for `stream` and report any deferred device-side error. */
 int etdm_check(etdm_handle *h, void *stream);
 

@@ -20,6 +20,8 @@ in FP64 / complex128, with numpy's matmul, eigh and FFT as library steps:
   exponential (used here only as a cross-check of Eq. 35).
 * Eq. 33-34: the diagonal preconditioner; Sec. 3.1: L-BFGS (m = 3);
   Eq. 25-29: line search conditions and parameter values.
+* Eq. 45: the convergence criterion (residual of the Kohn-Sham equations of
+  the occupied orbitals), with H psi represented in the span of the basis.
 
 The model Hamiltonian (s-type normalized Gaussians, Gaussian ion charges,
 spectral Poisson solve, Slater exchange) stands in for the paper's PAW/PBE
@@ -438,6 +440,24 @@ class Oracle:
             return E, g, dict(terms=terms, rho=rho, v=v, H=H, D=D, O=O, L=L,
                               Hmo=Hmo, dEda=dEda)
         return E, g
+
+    # ---- convergence criterion (Eq. 45) ----------------------------------------
+    def residual_eq45(self, Aov, C0=None):
+        """Eq. 45: (1/N_e) sum_i f_i int |H psi_i - sum_j lambda_ij psi_j|^2 dr,
+        lambda = O^T H O over the occupied orbitals, with H psi_i represented in
+        the span of the basis (what an LCAO calculation holds of it): its
+        coefficients are S^-1 (H O)_i, so the residual of orbital i has the
+        coefficients r_i = S^-1 (H O)_i - sum_j O_j lambda_ji and the integral
+        is r_i^T S r_i.  Hartree^2."""
+        ref = self.reference()
+        _, _, ex = self.energy_grad(Aov, C0, want=True)
+        N = self.N
+        O = ex["O"][:, :N]
+        HO = ex["H"] @ O
+        lam = O.T @ HO
+        R = np.linalg.solve(ref["S"], HO) - O @ lam
+        per = np.einsum("mi,mn,ni->i", R, ref["S"], R)
+        return float(np.sum(self.f[:N] * per) / self.n_e)
 
     # ---- preconditioner (Eq. 33-34) ------------------------------------------
     def orbital_energies(self):

@@ -73,6 +73,18 @@ __global__ void __launch_bounds__(1024) dot_batch_kernel(const long long *off, c
   }
 }
 
+// dst <- src (packed variables and energies) for the active systems only
+__global__ void copy_active_kernel(const long long *off, const int *active, const double *g_src,
+                                   double *g_dst, const double *E_src, double *E_dst) {
+  const int i = blockIdx.y;
+  if (!active[i]) return;
+  if (g_dst)
+    for (long long e = off[i] + (long long)blockIdx.x * blockDim.x + threadIdx.x; e < off[i + 1];
+         e += (long long)gridDim.x * blockDim.x)
+      g_dst[e] = g_src[e];
+  if (E_dst && blockIdx.x == 0 && threadIdx.x == 0) E_dst[i] = E_src[i];
+}
+
 int *ctl_flags(etdm_handle *h, int k) { return (int *)h->d_ctlbuf + (long)k * h->members.size(); }
 double *ctl_alpha(etdm_handle *h) {
   return (double *)(h->d_ctlbuf + (long)kCtlFlags * h->members.size() * sizeof(int));
@@ -232,6 +244,7 @@ void init_batch(etdm_handle *h, const etdm_system *sys, int n_sys, const etdm_op
   h->d_ctlbuf = dalloc<unsigned char>(h, ctl_bytes(h));
   std::vector<int> ones(n, 1);
   h->d_act = dupload(h, ones.data(), n);
+  h->act_host = ones;
   h->d_bflags = dalloc<int>(h, stat_count(h));
   std::vector<long long> off(h->var_off.begin(), h->var_off.end());
   h->d_off = dupload(h, off.data(), off.size());
@@ -338,17 +351,22 @@ void batch_energy_grad(etdm_handle *h, const double *a, double *E, double *g, cu
   } else if (h->precision == ETDM_PREC_MIXED) {
     CUDA_TRY(cudaGraphLaunch(h->g_eval, s));
     h->launches += h->graph_kernels_eval;
-  } else {  // the plain path: one launch sequence per system
+  } else {  // the plain path: one launch sequence per (active) system
     for (int i = 0; i < n; ++i) {
+      if (!h->act_host[i]) continue;
       eval_system(h->members[i], h->d_ae + h->var_off[i], h->d_res + i, h->d_ge + h->var_off[i], s);
       h->launches += h->members[i]->launches;
       h->members[i]->launches = 0;
     }
   }
-  if (g && g != h->d_ge)
-    CUDA_TRY(cudaMemcpyAsync(g, h->d_ge, h->nvar_tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  if (E && E != h->d_res)
-    CUDA_TRY(cudaMemcpyAsync(E, h->d_res, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // the results of the active systems (inactive entries of E and g untouched)
+  const bool gout = g && g != h->d_ge, Eout = E && E != h->d_res;
+  if (gout || Eout) {
+    const int vb = (int)std::min<long>(64, (h->nvar_tot / n + 255) / 256 + 1);
+    copy_active_kernel<<<dim3(vb, n), 256, 0, s>>>(h->d_off, h->d_act, h->d_ge, gout ? g : nullptr,
+                                                   h->d_res, Eout ? E : nullptr);
+    CUDA_TRY(cudaGetLastError());
+  }
 }
 
 void batch_check(etdm_handle *h, cudaStream_t s) {
@@ -370,9 +388,23 @@ void batch_energy_grad_host(etdm_handle *h, const double *a, double *E, double *
   const int n = (int)h->members.size();
   CUDA_TRY(cudaMemcpyAsync(h->d_ae, a, h->nvar_tot * sizeof(double), cudaMemcpyHostToDevice, s));
   batch_energy_grad(h, h->d_ae, h->d_res, h->d_ge, s);
-  CUDA_TRY(cudaMemcpyAsync(E, h->d_res, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (g) CUDA_TRY(cudaMemcpyAsync(g, h->d_ge, h->nvar_tot * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const bool all = std::all_of(h->act_host.begin(), h->act_host.end(), [](int v) { return v != 0; });
+  if (all) {
+    CUDA_TRY(cudaMemcpyAsync(E, h->d_res, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (g) CUDA_TRY(cudaMemcpyAsync(g, h->d_ge, h->nvar_tot * sizeof(double), cudaMemcpyDeviceToHost, s));
+    batch_check(h, s);
+    return;
+  }
+  // a mask is set: copy back the active systems' entries only
+  std::vector<double> Et(n), gt(g ? h->nvar_tot : 0);
+  CUDA_TRY(cudaMemcpyAsync(Et.data(), h->d_res, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (g) CUDA_TRY(cudaMemcpyAsync(gt.data(), h->d_ge, h->nvar_tot * sizeof(double), cudaMemcpyDeviceToHost, s));
   batch_check(h, s);
+  for (int i = 0; i < n; ++i) {
+    if (!h->act_host[i]) continue;
+    E[i] = Et[i];
+    if (g) std::copy(gt.begin() + h->var_off[i], gt.begin() + h->var_off[i + 1], g + h->var_off[i]);
+  }
 }
 
 void batch_minimize(etdm_handle *h, double *a_dev, int n_steps, double *E_hist, double *alpha_hist,

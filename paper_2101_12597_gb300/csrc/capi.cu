@@ -446,6 +446,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->h_vg_eoff = vg_eoff;
     h->h_mu_off = mu_off;
     h->h_vg_nu = vg_nu;
+    h->h_vg_xoff = vg_xoff;
     h->d_xr_off = upload(xr_off);
     h->d_mu_off = upload(mu_off);
     h->d_tmu = upload(tmu);
@@ -766,14 +767,20 @@ int etdm_check(etdm_handle *h, void *stream) {
   return ETDM_OK;
 }
 
-int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist,
-                  double *alpha_hist, int32_t *trials_hist, void *stream) {
+// n_steps ETDM iterations (tol < 0), or iterations until the Eq. 45 residual
+// of the current point is at most tol (at most n_steps of them); resid_hist
+// and *steps_done are then filled too.
+static int minimize_impl(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist,
+                         double *alpha_hist, int32_t *trials_hist, double tol,
+                         double *resid_hist, int32_t *steps_done, void *stream) {
   if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
   if (!a_dev || n_steps < 0) return set_err(h, ETDM_ERR_INVALID_ARG, "bad a_dev or n_steps");
   cudaStream_t s = (cudaStream_t)stream;
+  const bool conv = tol >= 0.0;
   const long nvar = (long)h->N * h->V;
   double *hp = h->h_pinned;
   if (!h->members.empty()) {
+    if (conv) return set_err(h, ETDM_ERR_INVALID_ARG, "the convergence test runs on one system");
     try {
       CUDA_TRY(cudaSetDevice(h->device));
       batch_minimize(h, a_dev, n_steps, E_hist, alpha_hist, trials_hist, s);
@@ -782,29 +789,39 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
     }
     return ETDM_OK;
   }
+  struct WantResid {  // the evaluations of this call compute Eq. 45 (reset on exit)
+    etdm_handle *h;
+    WantResid(etdm_handle *hh, bool on) : h(hh) { h->want_resid = on; }
+    ~WantResid() { h->want_resid = false; }
+  } want(h, conv);
   try {
     CUDA_TRY(cudaSetDevice(h->device));
-    // E and g at the start point
+    // E and g at the start point (values read back: E, g.p, g0.p, residual)
     evaluate(h, a_dev, h->d_dot, h->d_g, s);
-    CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 4 * 8, cudaMemcpyDeviceToHost, s));
     check_flags(h, s);
-    double E = hp[0];
+    double E = hp[0], resid = hp[3];
     if (E_hist) E_hist[0] = E;
     if (alpha_hist) alpha_hist[0] = 0.0;
     if (trials_hist) trials_hist[0] = 1;
+    if (resid_hist) resid_hist[0] = resid;
+    int done_steps = 0;
     // phi(alpha): E(a + alpha p) and grad . p, into hp[0], hp[1]
     struct Pt { double a, E, d; };
+    double last_resid = resid;  // Eq. 45 at the last point evaluated
     auto phi = [&](double alpha) -> Pt {
       CUDA_TRY(launch_axpy(a_dev, alpha, h->d_p, h->d_at, nvar, s));
       evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
       CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, nullptr, s));
       h->launches += 2;
-      CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 2 * 8, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 4 * 8, cudaMemcpyDeviceToHost, s));
       check_flags(h, s);
+      last_resid = hp[3];
       return Pt{alpha, hp[0], hp[1]};
     };
     LineSearch ls;
     for (int it = 1; it <= n_steps; ++it) {
+      if (conv && resid <= tol) break;
       lbfgs(h, a_dev, h->d_g, h->d_p, s);
       CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
       h->launches += 1;
@@ -814,8 +831,9 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
       evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
       CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, nullptr, s));
       h->launches += 2;
-      CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 3 * 8, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 4 * 8, cudaMemcpyDeviceToHost, s));
       check_flags(h, s);
+      last_resid = hp[3];
       double d0 = hp[2];
       const Pt first{1.0, hp[0], hp[1]};
       const bool have_first = d0 < 0.0;
@@ -836,20 +854,38 @@ int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist
         const Pt cur = phi(ls.alpha());
         ls.feed(cur.E, cur.d);
       }
-      if (ls.accepted()) {
+      if (ls.accepted()) {  // the accepted point is the last one evaluated
         CUDA_TRY(cudaMemcpyAsync(a_dev, h->d_at, nvar * 8, cudaMemcpyDeviceToDevice, s));
         std::swap(h->d_g, h->d_gt);
         E = ls.result().E;
+        resid = last_resid;
       }
       if (E_hist) E_hist[it] = E;
       if (alpha_hist) alpha_hist[it] = ls.accepted() ? ls.result().a : 0.0;
       if (trials_hist) trials_hist[it] = ls.trials();
+      if (resid_hist) resid_hist[it] = resid;
+      done_steps = it;
     }
+    if (steps_done) *steps_done = done_steps;
     CUDA_TRY(cudaStreamSynchronize(s));
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
   }
   return ETDM_OK;
+}
+
+int etdm_minimize(etdm_handle *h, double *a_dev, int32_t n_steps, double *E_hist,
+                  double *alpha_hist, int32_t *trials_hist, void *stream) {
+  return minimize_impl(h, a_dev, n_steps, E_hist, alpha_hist, trials_hist, -1.0, nullptr, nullptr,
+                       stream);
+}
+
+int etdm_minimize_converge(etdm_handle *h, double *a_dev, int32_t max_steps, double tol,
+                           double *E_hist, double *alpha_hist, int32_t *trials_hist,
+                           double *resid_hist, int32_t *steps_done, void *stream) {
+  if (!(tol >= 0.0)) return set_err(h, ETDM_ERR_INVALID_ARG, "tol must be >= 0");
+  return minimize_impl(h, a_dev, max_steps, E_hist, alpha_hist, trials_hist, tol, resid_hist,
+                       steps_done, stream);
 }
 
 int etdm_layout(const etdm_handle *h, int64_t *dims) {
@@ -1042,6 +1078,7 @@ int etdm_set_active(etdm_handle *h, const int32_t *active_host) {
     std::vector<int> m(h->members.size());
     for (size_t i = 0; i < m.size(); ++i) m[i] = active_host[i] != 0;
     CUDA_TRY(cudaMemcpy(h->d_act, m.data(), m.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->act_host = m;
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
   }

@@ -777,6 +777,34 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph.out64 = 1;
     run_phases<R>(cp, &ph, 1);
   }
+  if (!a.resid) return;
+  // Eq. 45 in the orthonormal basis of C0 (C0^T S C0 = I): the occupied
+  // orbitals are U_occ, H psi_i has the coefficients (C0^T H C0 U)_i =
+  // Ubar_i / 4 and lambda = U^T (Ubar / 4), so the residual is
+  // R / 4 with R = Ubar - U_occ (U_occ^T Ubar), and Eq. 45 = (1/N_e) sum f_i
+  // |R_i / 4|^2 = |R|^2 / (8 N_e) with f = 2, N_e = 2 N.  X in the first
+  // reverse workspace slot and R in Gbar (both free by now).
+  BARRIER_OR_RETURN();
+  {
+    Phase ph = mkphase(N, N, M, wr(kQ4b), N);  // X = U_occ^T Ubar
+    ph.np = 1; ph.p[0] = mk(a.Uocc, N, 1, a.Ubar, N, 0, 1.0);
+    run_phases<R>(cp, &ph, 1);
+  }
+  BARRIER_OR_RETURN();
+  {
+    Phase ph = mkphase(M, N, N, a.Gbar, N);  // R = Ubar - U_occ X
+    ph.np = 1; ph.p[0] = mk(a.Uocc, N, 0, wr(kQ4b), N, 0, -1.0);
+    addc(ph, a.Ubar, N, 1.0);
+    double sq = 0.0;
+    run_phases<R>(cp, &ph, 1, &sq);
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) a.red[3 * cp.size + cp.rank] = sq;
+  }
+  BARRIER_OR_RETURN();
+  if (cp.rank == 0) {
+    const double t = block_sum_of(a.red + 3 * cp.size, cp.size);
+    if (threadIdx.x == 0) *a.resid = t / (16.0 * N);
+  }
 }
 
 template <class R>
@@ -1195,6 +1223,7 @@ cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, dou
                                  cudaStream_t s) {
   DenseArgs d = dense_args(h, a);
   d.g = g; d.E = E;
+  d.resid = (h->want_resid && g) ? h->d_dot + 3 : nullptr;  // Eq. 45 with the energy
   int want = g != nullptr;
   void *args[] = {&d, &want};
   const void *fn = dense_pairs(h) ? (const void *)dense_reverse_kernel<float2>

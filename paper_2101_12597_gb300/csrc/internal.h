@@ -93,6 +93,7 @@ struct DenseArgs {
   double *Wr;            // (R) [11][N*N] reverse workspace of the series
   double *g;             // N x V output, FP64 (may be null)
   double *E;             // scalar output (may be null)
+  double *resid;         // Eq. 45 residual output, Hartree^2 (null: not computed; needs g)
   double *eterms;        // [4] kinetic, external, hartree, exchange
   const double *gridpart;  // [n_gridpart][3] energy partials of the grid
   const void *Vacc;      // (R) mixed path: upper-triangle V from the grid pass, else null
@@ -140,14 +141,22 @@ struct TcArgs {
   int *flags;
 };
 
+// One job of a grid pass, with the table entries it needs (one 32-byte load):
+//   density: a = (system, tile, orbital chunk, chunks of the tile),
+//            b = (first K step, K steps, functions, first function entry);
+//   V:       a = (system, group, first tile, tiles),
+//            b = (first union entry, padded entries, functions, X^T offset).
+struct TcJob {
+  int4 a, b;
+};
+
 // One launch of a grid pass over one or several systems: the systems'
-// arguments and, per CTA, a list of jobs in the order the CTA runs them.
-// Density jobs are (system, tile, orbital chunk, chunks of that tile), the
-// chunks of a tile consecutive in one CTA's list; V jobs are (system, group,
-// 0, 0).  A system whose active flag is 0 is skipped by every role.
+// arguments and, per CTA, a list of jobs in the order the CTA runs them (the
+// chunks of a density tile consecutive in one CTA's list).  A system whose
+// active flag is 0 is skipped by every role.
 struct TcBatch {
   const TcArgs *sys;   // [n_sys] (device)
-  const int4 *jobs;    // (device)
+  const TcJob *jobs;   // (device)
   const int *cta_ptr;  // [grid + 1] (device): CTA b runs jobs[cta_ptr[b] .. cta_ptr[b + 1])
   const int *active;   // [n_sys] (device)
   int *flags;          // status words: a bounded wait that gave up sets the timeout
@@ -290,10 +299,11 @@ struct etdm_handle {
   float2 *d_vt = nullptr;                // [n_tiles_tc][128] v dV in tile order
   long xr_steps = 0, xv_entries = 0;
   // host copies of the per-tile K steps and the V groups (job tables)
-  std::vector<int> h_xr_off, h_vg_t0, h_vg_eoff, h_mu_off, h_vg_nu;
+  std::vector<int> h_xr_off, h_vg_t0, h_vg_eoff, h_mu_off, h_vg_nu, h_vg_xoff;
   // device tables of the grid stages of this handle's evaluations
   etdm::MixedPlan plan{};
   int *d_active1 = nullptr;              // [1] = 1
+  bool want_resid = false;               // evaluations also compute the Eq. 45 residual
   uint2 *d_Osl = nullptr;     // [M][N + N % 2] BF16 slices of O
   float *d_oscale = nullptr;  // [N]
   double *d_dO = nullptr;     // [M][N] O - Oq
@@ -347,6 +357,7 @@ struct etdm_handle {
   double *d_res = nullptr;            // [3 n_sys]: E | g.p at the trial | g.p at the start
   unsigned char *d_ctlbuf = nullptr;  // round control: [4 n_sys] int flags, then [n_sys] alpha
   int *d_act = nullptr;               // [n_sys] the active mask of etdm_energy_grad
+  std::vector<int> act_host;          // its host copy
   int *d_bflags = nullptr;            // [FLAG_NFLAGS (n_sys + 1)]: members', then the batch's
   long long *d_off = nullptr;         // [n_sys + 1] var_off on the device
   etdm::DenseArgs *d_dargs = nullptr;

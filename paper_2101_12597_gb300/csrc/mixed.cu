@@ -560,17 +560,24 @@ __device__ __forceinline__ float2 rho_sum8(const uint32_t (&r)[32], const float 
   return make_float2(sm.x, __fadd_rn(rs.y, sm.y));
 }
 
-// job j of this CTA (density): its system's arguments, tile, orbital chunk and
-// the tile's number of chunks
-struct RhoJob {
-  const TcArgs *A;
-  int t, mc, nmc;
-  bool on;
+// The jobs of this CTA in order, each record read one job ahead (the next
+// job's tables are in registers when the current one ends).
+struct JobStream {
+  const TcJob *p;
+  int n, j;
+  TcJob next;
+  __device__ __forceinline__ explicit JobStream(const TcBatch &B)
+      : p(B.jobs + B.cta_ptr[blockIdx.x]),
+        n(B.cta_ptr[blockIdx.x + 1] - B.cta_ptr[blockIdx.x]), j(0) {
+    if (n > 0) next = p[0];
+  }
+  __device__ __forceinline__ bool get(TcJob &J) {
+    if (j >= n) return false;
+    J = next;
+    if (++j < n) next = p[j];
+    return true;
+  }
 };
-__device__ __forceinline__ RhoJob rho_job(const TcBatch &B, int j) {
-  const int4 q = B.jobs[B.cta_ptr[blockIdx.x] + j];
-  return RhoJob{B.sys + q.x, q.y, q.z, q.w, B.active[q.x] != 0};
-}
 
 __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
   extern __shared__ __align__(1024) uint8_t dsm[];
@@ -595,26 +602,26 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = R.tbase;
-  const int njobs = B.cta_ptr[blockIdx.x + 1] - B.cta_ptr[blockIdx.x];
   volatile int *stop = &R.stop;
 
   if (w == kRhoEpiW + kRhoBldW) {
     // ------------- bulk copies: X slices and the O-slice rows of each K step -------------
     int fill = 0;
     bool ok = true;
-    for (int j = 0; j < njobs && ok; ++j) {
-      const RhoJob J = rho_job(B, j);
-      if (!J.on) continue;
-      const TcArgs &A = *J.A;
-      const int t = J.t, mc = J.mc;
-      const int k0 = A.xr_off[t], nk = A.xr_off[t + 1] - k0, nu = A.nu[t];
+    JobStream js(B);
+    TcJob J;
+    while (ok && js.get(J)) {
+      if (!B.active[J.a.x]) continue;
+      const TcArgs &A = B.sys[J.a.x];
+      const int mc = J.a.z, nmc = J.a.w;
+      const int k0 = J.b.x, nk = J.b.y, nu = J.b.z;
       const int m0 = mc * kNmax, nme = min(kNmax, A.NoccP - m0);  // even
       // functions of the tile: lane l holds entries l, l + 32, l + 64, l + 96
       int mu4[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int a = lane + 32 * r;
-        mu4[r] = a < nu ? A.tmu[A.mu_off[t] + a] : 0;
+        mu4[r] = a < nu ? A.tmu[J.b.w + a] : 0;
       }
       for (int kk = 0; kk < nk; ++kk, ++fill) {
         const int s = fill % kRhoStages, use = fill / kRhoStages;
@@ -633,7 +640,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
         const int mu = __shfl_sync(0xffffffffu, mv, a & 31);
         // row c of the staging area (rows nme * 8 bytes apart) <- O-slice row mu_c
         const int mup = __shfl_up_sync(0xffffffffu, mu, 1);
-        const bool cont = J.nmc == 1 && lane > 0 && lane < nrow && mu == mup + 1;
+        const bool cont = nmc == 1 && lane > 0 && lane < nrow && mu == mup + 1;
         const unsigned cb = __ballot_sync(0xffffffffu, cont);
         if (lane < nrow && !cont) {  // a run starts here: rows lane .. lane + len - 1
           const unsigned after = ~(cb >> (lane + 1));
@@ -654,12 +661,12 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
     if (lane == 0) {
       int fill = 0, jp = 0;  // jp: jobs run (the accumulator hand-overs)
       bool ok = true;
-      for (int j = 0; j < njobs && ok; ++j) {
-        const RhoJob J = rho_job(B, j);
-        if (!J.on) continue;
-        const TcArgs &A = *J.A;
-        const int t = J.t, mc = J.mc;
-        const int nk = A.xr_off[t + 1] - A.xr_off[t];
+      JobStream js(B);
+      TcJob J;
+      while (ok && js.get(J)) {
+        if (!B.active[J.a.x]) continue;
+        const TcArgs &A = B.sys[J.a.x];
+        const int mc = J.a.z, nk = J.b.y;
         const int nm = min(kNmax, A.Nocc - mc * kNmax);
         const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
         if (jp > 0 && !mbar_wait(&R.acc_empty, (jp - 1) & 1, stop)) { ok = false; break; }
@@ -702,12 +709,12 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
     const int bt = tid - kRhoEpi;
     int fill = 0;
     bool ok = true;
-    for (int j = 0; j < njobs && ok; ++j) {
-      const RhoJob J = rho_job(B, j);
-      if (!J.on) continue;
-      const TcArgs &A = *J.A;
-      const int t = J.t, mc = J.mc;
-      const int nk = A.xr_off[t + 1] - A.xr_off[t], nu = A.nu[t];
+    JobStream js(B);
+    TcJob J;
+    while (ok && js.get(J)) {
+      if (!B.active[J.a.x]) continue;
+      const TcArgs &A = B.sys[J.a.x];
+      const int mc = J.a.z, nk = J.b.y, nu = J.b.z;
       const int nm = min(kNmax, A.Nocc - mc * kNmax);
       const int nme = min(kNmax, A.NoccP - mc * kNmax);  // staged row length (even)
       const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
@@ -755,11 +762,12 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
     float2 rsum = make_float2(0.f, 0.f);
     int ntile = 0, jp = 0;  // tiles finished (part buffer hand-overs), jobs run
     bool ok = true;
-    for (int j = 0; j < njobs && ok; ++j) {
-      const RhoJob J = rho_job(B, j);
-      if (!J.on) continue;
-      const TcArgs &A = *J.A;
-      const int t = J.t, mc = J.mc;
+    JobStream js(B);
+    TcJob J;
+    while (ok && js.get(J)) {
+      if (!B.active[J.a.x]) continue;
+      const TcArgs &A = B.sys[J.a.x];
+      const int t = J.a.y, mc = J.a.z;
       const int nm = min(kNmax, A.Nocc - mc * kNmax);
       const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
       const int gp = tile_point(A.g, t, pe);
@@ -786,7 +794,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&R.acc_empty);
-      if (mc == J.nmc - 1) {  // the tile is done: add the column parts
+      if (mc == J.a.w - 1) {  // the tile is done: add the column parts
         if (part > 0) {
           if (ntile > 0) ok = mbar_wait(&R.part_empty, (ntile - 1) & 1, stop);
           R.part[part - 1][pe] = rsum;
@@ -875,17 +883,6 @@ __device__ __forceinline__ void tmem_ld2_wait(uint32_t (&r)[16]) {
                : "memory");
 }
 
-// job `it` of this CTA (V pass): its system's arguments and group
-struct VJob {
-  const TcArgs *A;
-  int g;
-  bool on;
-};
-__device__ __forceinline__ VJob v_job(const TcBatch &B, int it) {
-  const int4 q = B.jobs[B.cta_ptr[blockIdx.x] + it];
-  return VJob{B.sys + q.x, q.y, B.active[q.x] != 0};
-}
-
 __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
   extern __shared__ __align__(1024) uint8_t dsm[];
   uint8_t *tbuf = dsm + kVStages * kVStage;  // 2 group buffers: vt[nt * 128] float2, vent[np] float4
@@ -915,7 +912,6 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
   // each CTA's jobs are a contiguous run of groups (of one system or a few):
   // CTAs running at the same time work in different parts of a box and rarely
   // add into the same entries of V
-  const int ntl = B.cta_ptr[blockIdx.x + 1] - B.cta_ptr[blockIdx.x];
   volatile int *stop = &R.stop;
   constexpr int kSteps = kTP / kKs;  // 8 K steps of 16 points per tile of the group
 
@@ -924,19 +920,19 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
     if (lane == 0) {
       int fill = 0, it = 0;  // it: jobs run (the group buffer hand-overs)
       bool ok = true;
-      for (int jj = 0; jj < ntl && ok; ++jj) {
-        const VJob J = v_job(B, jj);
-        if (!J.on) continue;
-        const TcArgs &A = *J.A;
-        const int g = J.g, mb = it & 1;
-        const int t0 = A.vg_t0[g], nt = A.vg_t0[g + 1] - t0;
-        const int e0 = A.vg_eoff[g], np = A.vg_eoff[g + 1] - e0;
+      JobStream js(B);
+      TcJob J;
+      while (ok && js.get(J)) {
+        if (!B.active[J.a.x]) continue;
+        const TcArgs &A = B.sys[J.a.x];
+        const int mb = it & 1;
+        const int t0 = J.a.z, nt = J.a.w, e0 = J.b.x, np = J.b.y;
         if (it >= 2 && !mbar_wait(&R.tile_empty[mb], ((it >> 1) - 1) & 1, stop)) { ok = false; break; }
         uint8_t *tb = tbuf + mb * kVTileBuf;
         mbar_expect_tx(&R.tile_full[mb], nt * kTP * 8 + np * 16);
         bulk_g2s(tb, A.vt + (size_t)t0 * kTP, nt * kTP * 8, &R.tile_full[mb]);
         bulk_g2s(tb + kVGmax * kTP * 8, A.vent + e0, np * 16, &R.tile_full[mb]);
-        const uint8_t *src = A.xv + (size_t)A.vg_xoff[g] * 256;
+        const uint8_t *src = A.xv + (size_t)J.b.w * 256;
         for (int kk = 0; kk < nt * kSteps; ++kk, ++fill) {
           const int s = fill % kVStages, use = fill / kVStages;
           if (use > 0 && !mbar_wait(&R.empty[s], (use - 1) & 1, stop)) { ok = false; break; }
@@ -957,13 +953,12 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
     if (lane == 0) {
       int fill = 0, it = 0;
       bool ok = true;
-      for (int jj = 0; jj < ntl && ok; ++jj, ++it) {
-        const VJob J = v_job(B, jj);
-        if (!J.on) { --it; continue; }
-        const TcArgs &A = *J.A;
-        const int g = J.g, buf = it & 1;
-        const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
-        const int np = A.vg_eoff[g + 1] - A.vg_eoff[g];
+      JobStream js(B);
+      TcJob J;
+      for (; ok && js.get(J); ++it) {
+        if (!B.active[J.a.x]) { --it; continue; }
+        const int buf = it & 1;
+        const int nt = J.a.w, np = J.b.y;
         // the accumulator pair of group it - 2 has been read
         if (it >= 2 && !mbar_wait(&R.acc_empty[buf], ((it >> 1) - 1) & 1, stop)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1004,14 +999,12 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
     const int b = bt & 127, h = bt >> 7;
     int fill = 0, it = 0;
     bool ok = true;
-    for (int jj = 0; jj < ntl && ok; ++jj, ++it) {
-      const VJob J = v_job(B, jj);
-      if (!J.on) { --it; continue; }
-      const TcArgs &A = *J.A;
-      const int g = J.g, mb = it & 1;
-      const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
-      const int np = A.vg_eoff[g + 1] - A.vg_eoff[g];
-      const int nu = A.vg_nu[g];
+    JobStream js(B);
+    TcJob J;
+    for (; ok && js.get(J); ++it) {
+      if (!B.active[J.a.x]) { --it; continue; }
+      const int mb = it & 1;
+      const int nt = J.a.w, np = J.b.y, nu = J.b.z;
       ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop));
       if (!ok) break;
       const uint8_t *tb = tbuf + mb * kVTileBuf;
@@ -1082,16 +1075,16 @@ __global__ void __launch_bounds__(kVThreads, 1) vmat_tc_kernel(TcBatch B) {
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
     int it = 0;
     bool ok = true;
-    for (int jj = 0; jj < ntl && ok; ++jj, ++it) {
-      const VJob J = v_job(B, jj);
-      if (!J.on) { --it; continue; }
-      const TcArgs &A = *J.A;
+    JobStream js(B);
+    TcJob J;
+    for (; ok && js.get(J); ++it) {
+      if (!B.active[J.a.x]) { --it; continue; }
+      const TcArgs &A = B.sys[J.a.x];
       const int M = A.g.M;
       // fixed-point unit of the job's system (its max |v| from the potential pass)
       const int fixe = vfix_exp((unsigned)A.Vfix[(long)M * M]);
-      const int g = J.g, mb = it & 1, buf = it & 1;
-      const int nt = A.vg_t0[g + 1] - A.vg_t0[g];
-      const int nu = A.vg_nu[g];
+      const int mb = it & 1, buf = it & 1;
+      const int nt = J.a.w, nu = J.b.z;
       ok = __all_sync(0xffffffffu, mbar_wait(&R.tile_full[mb], (it >> 1) & 1, stop) &&
                                        mbar_wait(&R.acc_full[buf], (it >> 1) & 1, stop));
       if (!ok) break;

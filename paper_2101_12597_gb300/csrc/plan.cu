@@ -13,8 +13,11 @@ namespace etdm {
 namespace {
 
 // density jobs of one tile: its orbital chunks of 128, consecutive
-void push_tile(std::vector<int4> &out, int s, int t, int nmc) {
-  for (int mc = 0; mc < nmc; ++mc) out.push_back(make_int4(s, t, mc, nmc));
+void push_tile(std::vector<TcJob> &out, const etdm_handle *h, int s, int t, int nmc) {
+  const int k0 = h->h_xr_off[t], nk = h->h_xr_off[t + 1] - k0;
+  const int muo = h->h_mu_off[t], nu = h->h_mu_off[t + 1] - muo;
+  for (int mc = 0; mc < nmc; ++mc)
+    out.push_back(TcJob{make_int4(s, t, mc, nmc), make_int4(k0, nk, nu, muo)});
 }
 
 int chunks(const etdm_handle *h) { return (h->N + tc_max_list() - 1) / tc_max_list(); }
@@ -54,12 +57,12 @@ void build_mixed_plan(etdm_handle *owner, const std::vector<etdm_handle *> &subs
     long total_tiles = 0;
     for (auto *h : subs) total_tiles += h->n_tiles_tc;
     const int grid = (int)std::max<long>(1, std::min<long>(total_tiles, sms));
-    std::vector<std::vector<int4>> per(grid);
+    std::vector<std::vector<TcJob>> per(grid);
     int max_nmc = 1;
     if (!batch) {  // tile t on CTA t mod grid, in order
       const etdm_handle *h = subs[0];
       const int nmc = chunks(h);
-      for (int t = 0; t < h->n_tiles_tc; ++t) push_tile(per[t % grid], 0, t, nmc);
+      for (int t = 0; t < h->n_tiles_tc; ++t) push_tile(per[t % grid], h, 0, t, nmc);
       max_nmc = nmc;
     } else {
       // longest processing time first: a job's cost is its K steps (plus the
@@ -86,11 +89,11 @@ void build_mixed_plan(etdm_handle *owner, const std::vector<etdm_handle *> &subs
       for (const Item &it : items) {
         Load l = q.top();
         q.pop();
-        push_tile(per[l.second], it.s, it.t, chunks(subs[it.s]));
+        push_tile(per[l.second], subs[it.s], it.s, it.t, chunks(subs[it.s]));
         q.push(Load{l.first + it.cost, l.second});
       }
     }
-    std::vector<int4> jobs;
+    std::vector<TcJob> jobs;
     std::vector<int> ptr(grid + 1, 0);
     for (int b = 0; b < grid; ++b) {
       jobs.insert(jobs.end(), per[b].begin(), per[b].end());
@@ -102,16 +105,17 @@ void build_mixed_plan(etdm_handle *owner, const std::vector<etdm_handle *> &subs
 
   // V: per CTA a contiguous run of (system, group)
   {
-    std::vector<int4> jobs;
+    std::vector<TcJob> jobs;
     std::vector<long> cost;
     for (int s = 0; s < ns; ++s) {
       const etdm_handle *h = subs[s];
       for (int g = 0; g < h->n_vg; ++g) {
-        if (batch && h->h_vg_nu[g] == 0) continue;  // adds nothing to V
-        jobs.push_back(make_int4(s, g, 0, 0));
-        const long nt = h->h_vg_t0[g + 1] - h->h_vg_t0[g];
-        const long np = h->h_vg_eoff[g + 1] - h->h_vg_eoff[g];
-        cost.push_back(nt * (np + 32));
+        const int t0 = h->h_vg_t0[g], nt = h->h_vg_t0[g + 1] - t0;
+        const int e0 = h->h_vg_eoff[g], np = h->h_vg_eoff[g + 1] - e0;
+        if (batch && h->h_vg_nu[g] == 0) continue;  // an empty group adds nothing to V
+        jobs.push_back(TcJob{make_int4(s, g, t0, nt),
+                             make_int4(e0, np, h->h_vg_nu[g], h->h_vg_xoff[g])});
+        cost.push_back((long)nt * (np + 32));
       }
     }
     const long nj = (long)jobs.size();

@@ -38,7 +38,7 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_stage_times", "etdm_last_error", "etdm_free",
            "etdm_lbfgs_direction_noalloc", "etdm_lbfgs_direction_noalloc_status",
            "etdm_init_batch", "etdm_num_systems", "etdm_system_layout", "etdm_system_handle",
-           "etdm_set_active"]
+           "etdm_set_active", "etdm_minimize_converge"]
 STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
 
 
@@ -90,6 +90,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.etdm_lbfgs_reset.argtypes = [P]
     lib.etdm_minimize.argtypes = [P, P, ctypes.c_int32, dp, dp,
                                   ctypes.POINTER(ctypes.c_int32), P]
+    lib.etdm_minimize_converge.argtypes = [P, P, ctypes.c_int32, ctypes.c_double, dp, dp,
+                                           ctypes.POINTER(ctypes.c_int32), dp,
+                                           ctypes.POINTER(ctypes.c_int32), P]
     lib.etdm_check.argtypes = [P, P]
     lib.etdm_layout.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.etdm_array_bytes.argtypes = [P, ctypes.c_int32]
@@ -325,6 +328,23 @@ class ETDM:
                                            tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                            _stream_ptr(stream)))
         return E, al, tr
+
+    def minimize_converge(self, a, max_steps=333, tol=1e-10 / 27.211386245988 ** 2,
+                          stream=None):
+        """ETDM iterations in place on a until the Eq. 45 residual is at most tol
+        (Hartree^2; default the paper's 1e-10 eV^2) or max_steps; returns
+        (steps, E, alpha, trials, residual), the histories cut to steps + 1."""
+        self._check_tensor(a, (self.N, self.V))
+        K = max_steps + 1
+        E, al, res = np.zeros(K), np.zeros(K), np.zeros(K)
+        tr = np.zeros(K, dtype=np.int32)
+        done = ctypes.c_int32(0)
+        self._raise(self.lib.etdm_minimize_converge(
+            self.h, ctypes.c_void_p(a.data_ptr()), max_steps, tol, _dptr(E), _dptr(al),
+            tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(res), ctypes.byref(done),
+            _stream_ptr(stream)))
+        k = int(done.value)
+        return k, E[:k + 1], al[:k + 1], tr[:k + 1], res[:k + 1]
 
     def check(self, stream=None):
         """Wait for `stream` and raise EtdmError on a deferred device-side error."""

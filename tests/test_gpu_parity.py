@@ -246,3 +246,34 @@ def test_water32_full_size_parity(water32):
     nt = o.n_tiles(tile)
     for t in list(range(0, nt, nt // 11)) + [nt - 1]:
         np.testing.assert_array_equal(keys[ptr[t]:ptr[t + 1]], o.tile_list(tile, t))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_minimize_to_the_eq45_criterion(precision):
+    """Sec. 3.5: iterations until the Eq. 45 residual is at most the paper's
+    1e-10 eV^2 (at most 333): the residual the GPU computes in C0's
+    orthonormal basis against the oracle's S^-1 route at the start and at the
+    final point; the final point meets the bar on the oracle's side too, and
+    the iterations taken equal the oracle's count of steps to reach it."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from oracle.etdm_oracle import Oracle, minimize
+    from paper_2101_12597_gb300.etdm import ETDM
+    tol = 1e-10 / 27.211386245988 ** 2
+    d = synth.config_small_molecule()
+    o = Oracle(d)
+    s = ETDM(d, precision=precision)
+    a = torch.tensor(d["a0"], device="cuda")
+    k, E, al, tr, res = s.minimize_converge(a, 333, tol)
+    s.check()
+    r0 = o.residual_eq45(d["a0"])
+    print(f"{precision}: {k} steps, residual {res[0]:.3e} -> {res[-1]:.3e} Ha^2 "
+          f"(oracle at start {r0:.3e})")
+    assert res[0] == pytest.approx(r0, rel=1e-5 if precision == "mixed" else 1e-10)
+    assert 0 < k < 333 and res[-1] <= tol and np.all(res[:-1] > tol)
+    r_end = o.residual_eq45(a.cpu().numpy())
+    assert r_end <= 2 * tol
+    hist, a_ref = minimize(o, d["a0"], n_steps=k)
+    assert abs(hist[-1][0] - E[-1]) < 1e-6
+    s.close()

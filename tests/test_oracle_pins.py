@@ -555,6 +555,42 @@ def test_stationarity_eq15_at_convergence():
         assert E <= hist[0][0]
 
 
+# ---- convergence criterion (Eq. 45) ----------------------------------------------------
+
+def test_residual_eq45_at_reference_equals_gradient_norm(small):
+    """At A = 0 the occupied orbitals are C0's first N columns, and in that
+    orthonormal basis the residual of orbital i is the virtual column of
+    C0^T H C0, whose entries the exact gradient gives by Eq. 42:
+    g_ij = 2 (f_j - f_i) (C0^T H C0)_ji = -4 (C0^T H C0)_ji.  So Eq. 45 equals
+    (1/N_e) sum_i f_i sum_j (g_ij / 4)^2 -- the S^-1 route of residual_eq45
+    against the Eq. 39 gradient route."""
+    d, o = small
+    A0 = np.zeros((o.N, o.V))
+    _, g = o.energy_grad(A0)
+    via_grad = 2.0 * float(np.sum((g / 4.0) ** 2)) / o.n_e
+    assert o.residual_eq45(A0) == pytest.approx(via_grad, rel=1e-10)
+
+
+def test_residual_eq45_vanishes_at_the_minimum_and_is_rotation_invariant():
+    """Eq. 45 is zero where the energy is stationary (Eq. 15), positive
+    elsewhere, and unchanged by a rotation among the occupied orbitals (the
+    lambda_ij term makes it independent of the occupied basis)."""
+    d = synth.tiny()
+    o = Oracle(d)
+    r0 = o.residual_eq45(d["a0"])
+    assert r0 > 1e-6
+    hist, a = minimize(o, d["a0"], n_steps=300)
+    assert o.residual_eq45(a) < 1e-14 * r0 + 1e-22
+    d2 = synth.config_small_molecule()
+    o2 = Oracle(d2)
+    ref = o2.reference()
+    Q, _ = np.linalg.qr(np.random.default_rng(45).normal(size=(o2.N, o2.N)))
+    C1 = ref["C0"].copy()
+    C1[:, : o2.N] = C1[:, : o2.N] @ Q  # a rotation of the occupied reference orbitals
+    A0 = np.zeros((o2.N, o2.V))
+    assert o2.residual_eq45(A0, C1) == pytest.approx(o2.residual_eq45(A0), rel=1e-10)
+
+
 # ---- truncation lists (index work) --------------------------------------------------
 
 @pytest.mark.parametrize("tile", [(4, 4, 4), (8, 4, 4)])
