@@ -345,7 +345,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     d = workload_system(args.workload)
-    solver = ETDM(d, precision=args.precision, device=local)
+    solver = ETDM(d, precision=args.precision, device=local, dense_tc=args.dense_tc)
     dims = solver.dims
     a0 = torch.tensor(d["a0"], dtype=torch.float64, device=dev)
     if args.profile_once:  # one evaluation after set-up, for profiler captures
@@ -455,7 +455,30 @@ def run_ours(args):
             flops = 2.0 * (fwd if dom == "dense_fwd" else rev)
             achieved = flops / (per_eval[dom] * 1e-3) / 1e12
             kern = "dense_forward_kernel" if dom == "dense_fwd" else "dense_reverse_kernel"
-            if mixed:
+            # the float-pair products go to the tensor cores from 2^26 multiply-adds
+            # on (every product of the chains at this size when the smallest does)
+            on_tc = mixed and (args.dense_tc == 1 or
+                               (args.dense_tc == 0 and N * N * min(N, V) >= 1 << 26))
+            if on_tc:
+                kern = kern.replace("_kernel", "_tc_kernel")
+                pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
+                # executed: 15 BF16 slice products per multiply-add, the outputs
+                # padded to 128 x 64 tiles and K to 16
+                pad = (lambda x, q: -(-x // q) * q)
+                ex_fwd, ex_rev = dense_macs(pad(M, 128), pad(N, 64), pad(V, 64), J)
+                executed = 15 * 2.0 * (ex_fwd if dom == "dense_fwd" else ex_rev)
+                ex_t = executed / (per_eval[dom] * 1e-3) / 1e12
+                roof = {"bound": "tensor", "achieved": achieved, "peak": pk / 15.0,
+                        "unit": "TFLOP/s", "frac": achieved / (pk / 15.0),
+                        "traffic": captured_traffic(kern, args.workload),
+                        "kernel": kern + " (float-pair products as exact BF16 slice "
+                                         "products on tcgen05)",
+                        "peak_source": f"derived: {src} dense bf16"
+                                       + (" (sustained)" if "bf16_tflops_sustained" in peaks else "")
+                                       + " / 15 BF16 slice products per float-pair multiply-add",
+                        "algorithmic_flops_per_launch": flops, "doublings": J,
+                        "executed_bf16_tflops": ex_t, "executed_frac": ex_t / pk}
+            elif mixed:
                 roof = {"bound": "alu", "achieved": achieved, "peak": pair_peak,
                         "unit": "TFLOP/s", "frac": achieved / pair_peak,
                         "traffic": captured_traffic(kern + "<float2>", args.workload),
@@ -742,6 +765,9 @@ def main():
     ap.add_argument("--profile-once", action="store_true",
                     help="set up, run one energy+gradient evaluation, exit (for ncu)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dense-tc", type=int, choices=[-1, 0, 1], default=0,
+                    help="float-pair dense products on the tensor cores: 0 the large ones "
+                         "(default), 1 all, -1 none")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -83,10 +83,15 @@ typedef struct {
                            systems); n > 0 fixes it (at most the co-resident
                            limit), which moves products onto 64 x 64 output
                            tiles once they have four per block */
+  int32_t dense_tc;     /* mixed precision: 0 puts the products of the dense
+                           chains with at least 2^26 multiply-adds on the tensor
+                           cores (exact BF16 slices, about 2^-39 relative per
+                           product), 1 every product, -1 none (float pairs on
+                           the FP32 pipes) */
 } etdm_options;
 
 /* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1,
- * automatic dense grid). */
+ * automatic dense grid, automatic tensor-core products). */
 void etdm_default_options(etdm_options *opt);
 
 /* Build everything that does not depend on A (Sec. 2, Eq. 4-6): grid basis
@@ -233,7 +238,10 @@ enum {
                                  list (i32, one per group) */
   ETDM_ARR_DOUBLINGS = 20,    /* [1] i32 doubling steps j of the last evaluation's
                                  exp (|A_ov A_ov^T|_F / 4^j <= 1) */
-  ETDM_NARR = 21              /* number of array ids */
+  ETDM_ARR_STATUS = 21,       /* [4] i32 device status words: error code, doublings,
+                                 then where a bounded wait of the tensor-core
+                                 products gave up and at which count (0: none) */
+  ETDM_NARR = 22              /* number of array ids */
 };
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);
 int etdm_get_array(etdm_handle *h, int32_t which, void *host_dst,
@@ -294,6 +302,18 @@ int etdm_lbfgs_direction_noalloc(const double *g_dev, const double *s_dev,
  * etdm_last_error(NULL).  The word keeps its value until the next direction
  * call clears it. */
 int etdm_lbfgs_direction_noalloc_status(void *stream);
+
+/* C = op(A) op(B) for FP64 device matrices (row-major; op(X) = X, or X^T
+ * when ta / tb is nonzero; A is m x k after op, B k x n, C m x n) on the
+ * tensor-core path of the mixed-precision dense chains (Eq. 7, 37 and their
+ * reverse pass): rows of op(A) and columns of op(B) cut into five exact BF16
+ * slices each after a power-of-two scaling, the slice products of orders <= 4
+ * accumulated exactly in tensor memory (orders 0-3 over 240-element K chunks,
+ * order 4 in FP32), the chunks summed in float pairs.  Relative error about
+ * 2^-39 of |A||B| per entry.  Allocates its workspace, synchronizes `stream`;
+ * a bounded wait that gave up returns ETDM_ERR_TIMEOUT.  1 <= m, n, k <= 65536. */
+int etdm_pair_gemm(const double *A_dev, const double *B_dev, double *C_dev, int32_t m,
+                   int32_t n, int32_t k, int32_t ta, int32_t tb, void *stream);
 
 /* Release all device memory of h (NULL is a no-op). */
 void etdm_free(etdm_handle *h);

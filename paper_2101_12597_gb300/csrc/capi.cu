@@ -183,6 +183,7 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
     if (!(opt->gamma >= 0.0 && opt->gamma <= 1.0)) bad("gamma must be in [0, 1]");
     if (!(opt->beta0 > 0.0)) bad("beta0 must be positive");
     if (opt->dense_blocks < 0) bad("dense_blocks must be >= 0");
+    if (opt->dense_tc < -1 || opt->dense_tc > 1) bad("dense_tc must be -1, 0 or 1");
   }
 }
 
@@ -544,6 +545,24 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
       h->coop_blocks = o.dense_blocks;
     }
   }
+  // tensor-core products of the float-pair chains: every product (dense_tc 1),
+  // or those of at least 2^26 multiply-adds (0) when the system has one
+  if (h->precision == ETDM_PREC_MIXED && o.dense_tc >= 0) {
+    const long long big = std::max<long long>((long long)M * M * N, (long long)N * N * std::max(N, V));
+    const long long min_work = o.dense_tc == 1 ? 1 : (1LL << 26);
+    if (big >= min_work) {
+      int bt = 0;
+      if (occupancy_dense_tc(&bt) != 0 || bt < 1)
+        throw Fail{ETDM_ERR_CUDA, "cannot size the tensor-core dense kernels"};
+      h->dense_tc = true;
+      h->tc_min_work = min_work;
+      h->coop_blocks = std::min(h->coop_blocks, bt * h->num_sms);
+      h->d_tc_asl = dalloc<uint8_t>(h, dense_tc_asl_bytes(M));
+      h->d_tc_bsl = dalloc<uint8_t>(h, dense_tc_bsl_bytes(M));
+      h->d_tc_rexp = dalloc<int>(h, (size_t)M + 128);
+      h->d_tc_cexp = dalloc<int>(h, (size_t)M + 128);
+    }
+  }
   int bpl = 0;
   if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
     throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};
@@ -643,6 +662,7 @@ void etdm_default_options(etdm_options *opt) {
   opt->beta0 = 1.0;
   opt->device = 0;
   opt->dense_blocks = 0;
+  opt->dense_tc = 0;
 }
 
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {
@@ -929,6 +949,7 @@ int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
     case ETDM_ARR_VGROUP_T0: return h->d_vg_t0 ? ((int64_t)h->n_vg + 1) * 4 : 0;
     case ETDM_ARR_VGROUP_NU: return h->d_vg_nu ? (int64_t)h->n_vg * 4 : 0;
     case ETDM_ARR_DOUBLINGS: return 4;
+    case ETDM_ARR_STATUS: return 4 * FLAG_NFLAGS;
     default: return -1;
   }
 }
@@ -983,6 +1004,7 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
       case ETDM_ARR_VGROUP_T0: src = h->d_vg_t0; break;
       case ETDM_ARR_VGROUP_NU: src = h->d_vg_nu; break;
       case ETDM_ARR_DOUBLINGS: src = h->d_flags + FLAG_J; break;
+      case ETDM_ARR_STATUS: src = h->d_flags; break;
     }
     if (want > 0) CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
   } catch (const Fail &f) {
@@ -1022,6 +1044,44 @@ int etdm_stage_times(etdm_handle *h, double *ms, int64_t *counts) {
   } catch (const Fail &f) {
     return set_err(h, f.code, f.msg);
   }
+  return ETDM_OK;
+}
+
+int etdm_pair_gemm(const double *A_dev, const double *B_dev, double *C_dev, int32_t m,
+                   int32_t n, int32_t k, int32_t ta, int32_t tb, void *stream) {
+  if (!A_dev || !B_dev || !C_dev || m < 1 || n < 1 || k < 1 || m > (1 << 16) || n > (1 << 16) ||
+      k > (1 << 16))
+    return set_err(nullptr, ETDM_ERR_INVALID_ARG, "need A, B, C and 1 <= m, n, k <= 65536");
+  cudaStream_t s = (cudaStream_t)stream;
+  etdm_handle scratch;  // owns the workspace of this call
+  try {
+    int dev = 0, sms = 0, bps = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (occupancy_dense_tc(&bps) != 0 || bps < 1)
+      throw Fail{ETDM_ERR_CUDA, "cannot size the tensor-core product kernel"};
+    const long big = std::max({(long)m, (long)n, (long)k});
+    uint8_t *asl = dalloc<uint8_t>(&scratch, dense_tc_asl_bytes(big));
+    uint8_t *bsl = dalloc<uint8_t>(&scratch, dense_tc_bsl_bytes(big));
+    int *rexp = dalloc<int>(&scratch, big + 128), *cexp = dalloc<int>(&scratch, big + 128);
+    unsigned *bar = dalloc<unsigned>(&scratch, 4);
+    int *flags = dalloc<int>(&scratch, FLAG_NFLAGS);
+    const long tiles = ((m + 127) / 128) * (long)((n + 63) / 64);
+    const int blocks = (int)std::max<long>(1, std::min<long>(tiles, (long)sms * bps));
+    CUDA_TRY(launch_pair_gemm(A_dev, B_dev, C_dev, m, n, k, ta, tb, asl, bsl, rexp, cexp, bar, flags,
+                              blocks, s));
+    int w[FLAG_NFLAGS];
+    CUDA_TRY(cudaMemcpyAsync(w, flags, sizeof(w), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (w[FLAG_ERR] != 0)
+      throw Fail{w[FLAG_ERR], "tensor-core product: device status " + std::to_string(w[FLAG_ERR]) +
+                                  ", wait " + std::to_string(w[2]) + " gave up at count " +
+                                  std::to_string(w[3])};
+  } catch (const Fail &f) {
+    release(&scratch);
+    return set_err(nullptr, f.code, f.msg);
+  }
+  release(&scratch);
   return ETDM_OK;
 }
 

@@ -30,6 +30,7 @@
 #include "device.cuh"
 #include "internal.h"
 #include "pair.cuh"
+#include "tcgemm.cuh"
 
 namespace etdm {
 
@@ -45,6 +46,7 @@ struct Coop {
   int rank, size;
   unsigned *bar;
   int *flags;
+  const struct TcRun *tc = nullptr;  // tensor-core products of large phases (mixed path)
   __device__ __forceinline__ bool sync() const {
     if (size == 1) {
       __syncthreads();
@@ -54,9 +56,15 @@ struct Coop {
   }
 };
 __device__ __forceinline__ Coop grid_coop(unsigned *bar, int *flags) {
-  return Coop{(int)blockIdx.x, (int)gridDim.x, bar, flags};
+  return Coop{(int)blockIdx.x, (int)gridDim.x, bar, flags, nullptr};
 }
-__device__ __forceinline__ Coop block_coop() { return Coop{0, 1, nullptr, nullptr}; }
+__device__ __forceinline__ Coop block_coop() { return Coop{0, 1, nullptr, nullptr, nullptr}; }
+
+// the tensor-core context and the size from which a phase's products use it
+struct TcRun {
+  TcCtx ctx;
+  long long min_work;  // m n k of the largest product of a call
+};
 
 // slots of the forward series workspace Qk
 enum { kQ1 = 0, kQ2, kQ3, kQ4, kBc2, kBs2, kTc, kTs, kQslots };
@@ -359,7 +367,11 @@ constexpr int kBigTileBytes = (2 * LBK * (LBM + 1) + 2 * LBK * (LBN + 1)) * 8;
 constexpr int kTileBytes = kSmallTileBytes > kBigTileBytes ? kSmallTileBytes : kBigTileBytes;
 
 template <class R>
-__device__ void run_phases(const Coop &cp, const Phase *ph, int count, double *sq = nullptr) {
+__device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *sph, int count, double *sq);
+
+template <class R, bool TCK = false>
+__device__ __forceinline__ void run_phases(const Coop &cp, const Phase *ph, int count,
+                                           double *sq = nullptr) {
   static_assert(sizeof(R) == 8, "8-byte elements");
   __shared__ __align__(16) unsigned char tsm[kTileBytes];
   __shared__ Phase sph[3];
@@ -367,6 +379,15 @@ __device__ void run_phases(const Coop &cp, const Phase *ph, int count, double *s
   if (threadIdx.x == 0)
     for (int c = 0; c < count; ++c) sph[c] = ph[c];
   __syncthreads();
+  if constexpr (TCK) {  // large products on the tensor cores
+    long long work = 0;
+    for (int c = 0; c < count; ++c)
+      work = max(work, (long long)sph[c].m * sph[c].n * sph[c].k);
+    if (cp.tc && work >= cp.tc->min_work) {
+      run_phases_tc<R>(cp, sph, count, sq);
+      return;
+    }
+  }
   R *const base = reinterpret_cast<R *>(tsm);
   auto *As = reinterpret_cast<R (*)[2][BM][BK + 1]>(base);
   auto *Bs = reinterpret_cast<R (*)[2][BK][BN + 1]>(base + KG * 2 * BM * (BK + 1));
@@ -380,6 +401,264 @@ __device__ void run_phases(const Coop &cp, const Phase *ph, int count, double *s
     while (t - base_t >= ntiles(sph[c], cp.size)) { base_t += ntiles(sph[c], cp.size); ++c; }
     if (use_big(sph[c], cp.size)) phase_tile_big<R>(sph[c], t - base_t, Al, Bl, sq);
     else phase_tile<R>(sph[c], t - base_t, As, Bs, part, sq);
+  }
+}
+
+// ---- tensor-core products of large phases (float pairs; tcgemm.cuh) ----------
+// one 8-column load of a single accumulator (lane quarter of the warp)
+__device__ __forceinline__ void tmem_ld8(uint32_t t, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(t)
+      : "memory");
+}
+
+// where a bounded wait of the tensor-core products gave up: the first one is
+// recorded in the status words 2 (1: stage free, 2: read-out done, 3: stage
+// filled, 4: accumulators ready) and 3 (the stage fill or chunk count)
+__device__ __forceinline__ void tc_gave_up(const Coop &cp, int where, int count) {
+  if (atomicCAS(cp.flags + 2, 0, where) == 0) cp.flags[3] = count;
+}
+
+// out (m x n) of product q of phase P, on this CTA's tiles (see tcgemm.cuh);
+// `first`: the phase's first product (writes alpha AB + epilogue terms), else
+// adds alpha AB to out; `last`: accumulates the squares of the outputs in *sq
+__device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod &pr, bool first,
+                                      bool last, double *sq) {
+  const TcCtx &C = cp.tc->ctx;
+  GemmSmem &S = *C.S;
+  const int m = P.m, n = P.n, K = P.k;
+  const int ncb = (n + kGN - 1) / kGN, nks = (K + 15) / 16;
+  const int ntiles = ((m + 127) / 128) * ncb;
+  const int nch = (nks + kGChunk - 1) / kGChunk;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  // the barriers live for the whole kernel; the counts of the previous
+  // products give each wait its phase
+  const int fill0_copy = S.fill_copy, fill0_mma = S.fill_mma;
+  const int ch0_mma = S.chunk_mma, ch0_epi = S.chunk_epi, fins = S.fins;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  volatile int *stop = &S.stop;
+
+  if (w == 0) {
+    // --------------------- bulk copies of the slices of each K step ---------------------
+    if (lane == 0) {
+      // the slices were written by generic stores (before the grid barrier)
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      int fill = fill0_copy;
+      bool ok = true;
+      for (int t = cp.rank; t < ntiles && ok; t += cp.size) {
+        const int rb = t / ncb, cb = t % ncb;
+        const uint8_t *ab = C.ws.asl + (size_t)rb * nks * kGA;
+        const uint8_t *bb = C.ws.bsl + (size_t)cb * nks * kGB;
+        for (int ks = 0; ks < nks; ++ks, ++fill) {
+          const int s = fill % kGStages, use = fill / kGStages;
+          if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, stop)) {
+            tc_gave_up(cp, 1, fill);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&S.full[s], kGStage);
+          bulk_g2s(C.dyn + s * kGStage, ab + (size_t)ks * kGA, kGA, &S.full[s]);
+          bulk_g2s(C.dyn + s * kGStage + kGA, bb + (size_t)ks * kGB, kGB, &S.full[s]);
+        }
+      }
+      if (!ok) atomicExch((int *)stop, 1);
+      // the copies still in flight land before the call ends
+      for (int q = 0; q < kGStages && q < fill - fill0_copy; ++q) {
+        const int f = fill - 1 - q;
+        mbar_wait(&S.full[f % kGStages], (f / kGStages) & 1);
+      }
+      S.fill_copy = fill;
+    }
+  } else if (w == 1) {
+    // ------------------------------------ MMA issue ------------------------------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kGN);
+      int fill = fill0_mma, ch = ch0_mma;
+      bool ok = true;
+      for (int t = cp.rank; t < ntiles && ok; t += cp.size) {
+        for (int ks = 0; ks < nks; ++ks, ++fill) {
+          const int kc = ks % kGChunk;
+          if (kc == 0 && ch > 0) {  // the read-out of the previous chunk is done
+            if (!mbar_wait(&S.acc_empty, (ch - 1) & 1, stop)) {
+              tc_gave_up(cp, 2, ch);
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          const int s = fill % kGStages, use = fill / kGStages;
+          if (!mbar_wait(&S.full[s], use & 1, stop)) {
+            tc_gave_up(cp, 3, fill);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = su32(C.dyn + s * kGStage), b0 = a0 + kGA;
+          uint64_t Ad[kGS], Bd[kGS];
+#pragma unroll
+          for (int q = 0; q < kGS; ++q) {
+            Ad[q] = smem_desc(a0 + q * 4096);
+            Bd[q] = smem_desc(b0 + q * 2048);
+          }
+          // order o = t + u into the accumulator at column o * 64; orders 0-3
+          // restart every chunk, order 4 every tile
+#pragma unroll
+          for (int o = 0; o < kGS; ++o) {
+#pragma unroll
+            for (int q = 0; q <= o; ++q) {
+              const bool restart = q == 0 && (o < kGS - 1 ? kc == 0 : ks == 0);
+              mma_bf16(C.tmem + o * kGN, Ad[q], Bd[o - q], idesc, restart ? 0u : 1u);
+            }
+          }
+          mma_commit(&S.empty[s]);
+          if (kc == kGChunk - 1 || ks == nks - 1) {
+            mma_commit(&S.acc_full);
+            ++ch;
+          }
+        }
+      }
+      if (!ok) atomicExch((int *)stop, 1);
+      mma_commit(&S.fin);  // every MMA issued has completed when the call ends
+      mbar_wait(&S.fin, fins & 1);
+      S.fill_mma = fill;
+      S.chunk_mma = ch;
+      S.fins = fins + 1;
+    }
+  } else if (w >= kGEpiW0) {
+    // ---------------------------- read-out and outputs ----------------------------
+    const int e = w - kGEpiW0, quad = w & 3, half = e >> 2;
+    const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
+    const int row = quad * 32 + lane;
+    int ch = ch0_epi;
+    bool ok = true;
+    double sql = 0.0;
+    for (int t = cp.rank; t < ntiles && ok; t += cp.size) {
+      const int rb = t / ncb, cb = t % ncb;
+      float2 acc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = make_float2(0.f, 0.f);
+      for (int c = 0; c < nch; ++c, ++ch) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&S.acc_full, ch & 1, stop));
+        if (!ok) {
+          if (lane == 0) tc_gave_up(cp, 4, ch);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {  // 8 columns of the four exact orders
+          uint32_t r[32];
+          tmem_ld_issue(C.tmem + lanebits + half * 32 + cg * 8, r, kGN);
+          tmem_ld_wait(r);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            // the exact integers of orders 0 .. 3 (each on its own 2^-8o grid)
+            const float2 y = pair::two_sum(__uint_as_float(r[j]), __uint_as_float(r[8 + j]));
+            const float lo = __fadd_rn(y.y, __fadd_rn(__uint_as_float(r[16 + j]), __uint_as_float(r[24 + j])));
+            acc[cg * 8 + j] = pair::add(acc[cg * 8 + j], make_float2(y.x, lo));
+          }
+        }
+        if (c == nch - 1) {  // the FP32 order-4 sums of the whole K range
+#pragma unroll
+          for (int cg = 0; cg < 4; ++cg) {
+            uint32_t r[8];
+            tmem_ld8(C.tmem + lanebits + 4 * kGN + half * 32 + cg * 8, r);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              acc[cg * 8 + j] = pair::add(acc[cg * 8 + j], make_float2(__uint_as_float(r[j]), 0.f));
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.acc_empty);
+      }
+      if (!ok) break;
+      // out = alpha 2^(e_i - 8) 2^(f_j - 8) acc (+ epilogue terms on the first product)
+      const int i = rb * 128 + row;
+      if (i < m) {
+        const float si = pow2f(slice_exp(__int_as_float(C.ws.rexp[i])) - 8);
+        const float2 al = pair::split(pr.alpha);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int j = cb * kGN + half * 32 + c;
+          if (j >= n) continue;
+          const float sj = pow2f(slice_exp(__int_as_float(C.ws.cexp[j])) - 8);
+          float2 v = pair::scale2(pair::scale2(acc[c], si), sj);
+          v = pair::mul(al, v);
+          const long o = (long)i * P.ldo + j;
+          if (first) {
+            for (int q = 0; q < P.nc; ++q)
+              v = pair::add(pair::mul(pair::split(P.beta[q]),
+                                      static_cast<const float2 *>(P.C[q])[(long)i * P.ldc[q] + j]),
+                            v);
+            if (i == j) v = pair::add(v, pair::split(P.diag));
+          } else {
+            v = pair::add(v, P.out64 ? pair::split(static_cast<const double *>(P.out)[o])
+                                     : static_cast<const float2 *>(P.out)[o]);
+          }
+          if (P.out64) static_cast<double *>(P.out)[o] = pair::to_double(v);
+          else static_cast<float2 *>(P.out)[o] = v;
+          if (last && sq) {
+            const double d = pair::to_double(v);
+            sql += d * d;
+          }
+        }
+      }
+    }
+    if (!ok) atomicExch((int *)stop, 1);
+    if (sq) *sq += sql;
+    if (e == 0 && lane == 0) S.chunk_epi = ch;  // (every read-out warp counts the same)
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && S.stop) atomicExch(cp.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
+}
+
+// A call of run_phases on the tensor cores: the phases one after another,
+// each product sliced (exponents, then slices, into the workspace) and
+// multiplied; grid barriers between the steps.  Only the float-pair chains
+// take this path.
+template <class R>
+__device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *tph, int count, double *sq) {
+  if constexpr (!Num<R>::kPair) {
+    return;
+  } else {
+    const GemmWs &W = cp.tc->ctx.ws;
+    const long gtid = (long)cp.rank * blockDim.x + threadIdx.x;
+    const long gstride = (long)cp.size * blockDim.x;
+    for (int c = 0; c < count; ++c) {
+      const Phase &P = tph[c];
+      int first = -1, last = -1;
+      for (int q = 0; q < P.np; ++q)
+        if (P.p[q].alpha != 0.0) {
+          if (first < 0) first = q;
+          last = q;
+        }
+      if (first < 0) continue;  // (every phase of the chains has a product)
+      for (int q = first; q <= last; ++q) {
+        const Prod &pr = P.p[q];  // (shared memory)
+        if (pr.alpha == 0.0) continue;
+        for (long e = gtid; e < P.m; e += gstride) W.rexp[e] = 0;
+        for (long e = gtid; e < P.n; e += gstride) W.cexp[e] = 0;
+        if (!cp.sync()) return;
+        auto fa = [&](int i, int k) { return opA<float2>(pr, i, k); };
+        auto fb = [&](int j, int k) { return opB<float2>(pr, k, j); };  // rows of op(B)^T
+        tc_maxima(fa, P.m, P.k, !pr.ta, W.rexp, gtid, gstride);
+        tc_maxima(fb, P.n, P.k, pr.tb != 0, W.cexp, gtid, gstride);
+        if (!cp.sync()) return;
+        tc_slice(fa, P.m, P.k, 128, !pr.ta, W.rexp, W.asl, gtid, gstride);
+        tc_slice(fb, P.n, P.k, kGN, pr.tb != 0, W.cexp, W.bsl, gtid, gstride);
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk copies
+        if (!cp.sync()) return;
+        tc_tiles(cp, P, pr, q == first, q == last, sq);
+        // the next product rewrites the workspace (and adds to these outputs)
+        if ((q < last || c + 1 < count) && !cp.sync()) return;
+      }
+    }
   }
 }
 
@@ -409,7 +688,7 @@ __device__ __forceinline__ void addc(Phase &ph, const void *c, int ld, double be
 
 // Forward: P, j, Q^k, Taylor series, doublings, U_occ = [cos sqrt P; -A^T s(P)],
 // O = C0 U_occ, then D = 2 O O^T and H <- T (FP64 grid passes) or T O (mixed).
-template <class R>
+template <class R, bool TCK = false>
 __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
   using X = Num<R>;
   const int M = a.M, N = a.N, V = a.V;
@@ -427,7 +706,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     Phase ph = mkphase(N, N, V, a.P, N);
     ph.np = 1; ph.p[0] = mk(a.A, V, 0, a.A, V, 1, 1.0); ph.p[0].f64 = 3;
     double sq = 0.0;
-    run_phases<R>(cp, &ph, 1, &sq);
+    run_phases<R, TCK>(cp, &ph, 1, &sq);
     sq = block_sum(sq);
     if (threadIdx.x == 0) a.red[cp.rank] = sq;
   }
@@ -459,7 +738,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
   {  // Q^2 = sc^2 P P
     Phase ph = mkphase(N, N, N, slot(kQ2), N);
     ph.np = 1; ph.p[0] = mk(a.P, N, 0, a.P, N, 0, sc * sc);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {  // Q^3 = sc P Q^2, Q^4 = Q^2 Q^2
@@ -468,7 +747,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     ph[0].np = 1; ph[0].p[0] = mk(a.P, N, 0, slot(kQ2), N, 0, sc);
     ph[1] = mkphase(N, N, N, slot(kQ4), N);
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   // Paterson-Stockmeyer blocks B_i = sum_r c_{4i+r} Q^r (r < 4) enter the
@@ -503,7 +782,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
       addc(ph[w], slot(kQ4), N, cf(c, 8));
       ph[w].diag = cf(c, 4);
     }
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // k = cos sqrt(Q) - 1 = B_0 + Q^4 T_c, s = sin sqrt(Q) / sqrt(Q) = B_0 + Q^4 T_s
@@ -520,7 +799,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
       addc(ph[w], slot(kQ3), N, cf(c, 3));
       ph[w].diag = cf(c, 0);
     }
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   for (int t = 0; t < J; ++t) {  // doubling: k' = 4k + 2k^2, s' = s + s k
@@ -532,7 +811,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     ph[1] = mkphase(N, N, N, a.St + (long)(t + 1) * NN, N);
     ph[1].np = 1; ph[1].p[0] = mk(Sc, N, 0, Kc, N, 0, 1.0);
     addc(ph[1], Sc, N, 1.0);
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
     BARRIER_OR_RETURN();
   }
   {
@@ -543,23 +822,23 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     }
     Phase ph = mkphase(V, N, N, a.Uocc + NN, N);  // -A^T s(P)
     ph.np = 1; ph.p[0] = mk(Ar, V, 1, SJ, N, 0, -1.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {
     Phase ph = mkphase(M, N, M, a.O, N);  // O = C0 U_occ
     ph.np = 1; ph.p[0] = mk(a.C0, M, 0, a.Uocc, N, 0, 1.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   if (a.Vacc) {  // mixed path: the density comes from O on the grid; T O for the kinetic energy and dE/dO
     Phase ph = mkphase(M, N, M, a.TO, N);
     ph.np = 1; ph.p[0] = mk(a.T, M, 0, a.O, N, 0, 1.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   } else {
     Phase ph = mkphase(M, M, N, a.D, M);  // D = 2 O O^T (Eq. 12, f = 2)
     ph.np = 1; ph.p[0] = mk(a.O, N, 0, a.O, N, 1, 2.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
     const long MM = (long)M * M;
     for (long e = gtid; e < MM; e += gstride) X::st(a.H, e, X::ld(a.T, e));
   }
@@ -585,7 +864,7 @@ __global__ void __launch_bounds__(NT) dense_forward_batch_kernel(const DenseArgs
 // Reverse: E = Tr(D T) + grid terms; dE/dO = 4 H O; dE/dU = C0^T (4 H O);
 // (mixed path: Tr(D T) = 2 sum O o (T O), 4 H O = 4 T O + 4 V O);
 // back through U_occ, the doublings, the Taylor powers and P = A A^T.
-template <class R>
+template <class R, bool TCK = false>
 __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp) {
   using X = Num<R>;
   const int M = a.M, N = a.N, V = a.V;
@@ -612,7 +891,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     Phase ph = mkphase(M, N, M, a.Gbar, N);
     ph.np = 1; ph.p[0] = mk(a.Vacc, M, 0, a.O, N, 0, 4.0); ph.p[0].f64 = 4;  // A symmetric (upper)
     addc(ph, a.TO, N, 4.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
     BARRIER_OR_RETURN();
     double c2 = 0.0;
     for (long e = gtid; e < MN; e += gstride) c2 += X::dbl(X::ld(a.Gbar, e)) * a.dO[e];
@@ -621,7 +900,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     if (want_grad) {
       Phase pu = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
       pu.np = 1; pu.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
-      run_phases<R>(cp, &pu, 1);
+      run_phases<R, TCK>(cp, &pu, 1);
     }
     BARRIER_OR_RETURN();
   } else {
@@ -639,11 +918,11 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     if (want_grad) {
       Phase ph = mkphase(M, N, M, a.Gbar, N);  // Gbar = dE/dO = 4 H O
       ph.np = 1; ph.p[0] = mk(a.H, M, 0, a.O, N, 0, 4.0);
-      run_phases<R>(cp, &ph, 1);
+      run_phases<R, TCK>(cp, &ph, 1);
       BARRIER_OR_RETURN();
       Phase pu = mkphase(M, N, M, a.Ubar, N);  // Ubar = C0^T Gbar
       pu.np = 1; pu.p[0] = mk(a.C0, M, 1, a.Gbar, N, 0, 1.0);
-      run_phases<R>(cp, &pu, 1);
+      run_phases<R, TCK>(cp, &pu, 1);
       BARRIER_OR_RETURN();
     }
   }
@@ -675,7 +954,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph[0].np = 1; ph[0].p[0] = mk(Ar, V, 0, Ubv, N, 0, -1.0);
     ph[1] = mkphase(N, V, N, a.Abar, V);     // Abar = -S_J Ubar_v^T
     ph[1].np = 1; ph[1].p[0] = mk(a.St + (long)J * NN, N, 0, Ubv, N, 1, -1.0);
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   const double *kb = a.Ubar;  // Kbar_J = cotangent of cos sqrt(P) = Ubar_o
@@ -694,7 +973,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph[1].p[1] = mk(Kc, N, 0, kb, N, 0, 2.0);
     ph[1].p[2] = mk(Sc, N, 0, sb, N, 0, 1.0);
     addc(ph[1], kb, N, 4.0);
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
     BARRIER_OR_RETURN();
     kb = kbo; sb = sbo; pp = 1 - pp;
   }
@@ -713,7 +992,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, kb, N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kTsb), N);  // T_s bar = Q^4 sbar
     ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, sb, N, 0, 1.0);
-    run_phases<R>(cp, ph, 3);
+    run_phases<R, TCK>(cp, ph, 3);
   }
   BARRIER_OR_RETURN();
   {  // back through T = B_1 + Q^4 B_2
@@ -727,7 +1006,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph[1].np = 1; ph[1].p[0] = mk(slot(kQ4), N, 0, wr(kTcb), N, 0, 1.0);
     ph[2] = mkphase(N, N, N, wr(kBs2b), N);  // B_s2 bar = Q^4 T_s bar
     ph[2].np = 1; ph[2].p[0] = mk(slot(kQ4), N, 0, wr(kTsb), N, 0, 1.0);
-    run_phases<R>(cp, ph, 3);
+    run_phases<R, TCK>(cp, ph, 3);
   }
   BARRIER_OR_RETURN();
   // the blocks' cotangents to the powers: Q^r bar = sum_i c_{4i+r} B_ci bar + s_{4i+r} B_si bar
@@ -756,7 +1035,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph[1] = mkphase(N, N, N, wr(kQ1bt), N);  // Qbar_t = Q1bar_B + Q3bar Q^2
     ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 1.0);
     addc(ph[1], wr(kQ1bB), N, 1.0);
-    run_phases<R>(cp, ph, 2);
+    run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
   {  // back through Q^2 = Q Q: Qbar = Qbar_t + Q2bar Q + Q Q2bar
@@ -765,7 +1044,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
     ph.p[1] = mk(slot(kQ1), N, 0, wr(kQ2b), N, 0, 1.0);
     addc(ph, wr(kQ1bt), N, 1.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {  // Q = sc P: g = Abar + (Pbar + Pbar^T) A = Abar + sc Qbar A + sc Qbar^T A, written as FP64
@@ -775,7 +1054,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph.p[1] = mk(wr(kQ1b), N, 1, Ar, V, 0, sc);
     addc(ph, a.Abar, V, 1.0);
     ph.out64 = 1;
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   }
   if (!a.resid) return;
   // Eq. 45 in the orthonormal basis of C0 (C0^T S C0 = I): the occupied
@@ -788,7 +1067,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
   {
     Phase ph = mkphase(N, N, M, wr(kQ4b), N);  // X = U_occ^T Ubar
     ph.np = 1; ph.p[0] = mk(a.Uocc, N, 1, a.Ubar, N, 0, 1.0);
-    run_phases<R>(cp, &ph, 1);
+    run_phases<R, TCK>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
   {
@@ -796,7 +1075,7 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     ph.np = 1; ph.p[0] = mk(a.Uocc, N, 0, wr(kQ4b), N, 0, -1.0);
     addc(ph, a.Ubar, N, 1.0);
     double sq = 0.0;
-    run_phases<R>(cp, &ph, 1, &sq);
+    run_phases<R, TCK>(cp, &ph, 1, &sq);
     sq = block_sum(sq);
     if (threadIdx.x == 0) a.red[3 * cp.size + cp.rank] = sq;
   }
@@ -819,6 +1098,79 @@ __global__ void __launch_bounds__(NT) dense_reverse_batch_kernel(const DenseArgs
     const int i = order[q];
     if (active[i]) dense_reverse<R>(av[i], 1, block_coop());
   }
+}
+
+// The float-pair chains with their large products on the tensor cores: one
+// block per SM (the stage ring's dynamic shared memory leaves room for no
+// second block), 512 tensor-memory columns held for the kernel's lifetime.
+__device__ __forceinline__ void tc_setup(const DenseArgs &a, TcRun &run, GemmSmem &gS,
+                                         uint8_t *dyn, uint32_t *slot) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGStages; ++s) {
+      mbar_init(&gS.full[s], 1);
+      mbar_init(&gS.empty[s], 1);
+    }
+    mbar_init(&gS.acc_full, 1);
+    mbar_init(&gS.acc_empty, 8);  // one arrival per read-out warp
+    mbar_init(&gS.fin, 1);
+    gS.stop = 0;
+    gS.fill_copy = gS.fill_mma = gS.chunk_mma = gS.chunk_epi = gS.fins = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  run.ctx.ws = GemmWs{a.tc_asl, a.tc_bsl, a.tc_rexp, a.tc_cexp};
+  run.ctx.dyn = dyn;
+  run.ctx.S = &gS;
+  run.ctx.tmem = *slot;
+  run.min_work = a.tc_min_work;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem);
+}
+
+__global__ void __launch_bounds__(NT) dense_forward_tc_kernel(DenseArgs a) {
+  extern __shared__ __align__(1024) uint8_t gdyn[];
+  __shared__ GemmSmem gS;
+  __shared__ uint32_t slot;
+  TcRun run;
+  tc_setup(a, run, gS, gdyn, &slot);
+  Coop cp = grid_coop(a.bar, a.flags);
+  cp.tc = &run;
+  dense_forward<float2, true>(a, cp);
+  tc_teardown(run.ctx.tmem);
+}
+
+__global__ void __launch_bounds__(NT) dense_reverse_tc_kernel(DenseArgs a, int want_grad) {
+  extern __shared__ __align__(1024) uint8_t gdyn[];
+  __shared__ GemmSmem gS;
+  __shared__ uint32_t slot;
+  TcRun run;
+  tc_setup(a, run, gS, gdyn, &slot);
+  Coop cp = grid_coop(a.bar, a.flags);
+  cp.tc = &run;
+  dense_reverse<float2, true>(a, want_grad, cp);
+  tc_teardown(run.ctx.tmem);
+}
+
+// One product C = op(A) op(B) of FP64 matrices on the tensor-core path (the
+// building block of the chains' large products), as a cooperative launch.
+__global__ void __launch_bounds__(NT) pair_gemm_kernel(Phase ph, DenseArgs a) {
+  extern __shared__ __align__(1024) uint8_t gdyn[];
+  __shared__ GemmSmem gS;
+  __shared__ uint32_t slot;
+  TcRun run;
+  tc_setup(a, run, gS, gdyn, &slot);
+  Coop cp = grid_coop(a.bar, a.flags);
+  cp.tc = &run;
+  run.min_work = 0;
+  run_phases<float2, true>(cp, &ph, 1);
+  tc_teardown(run.ctx.tmem);
 }
 
 // Plain (non-cooperative) product for set-up work.
@@ -1195,6 +1547,9 @@ DenseArgs dense_args(etdm_handle *h, const double *a) {
   d.eterms = h->d_eterms;
   d.gridpart = h->d_gridpart; d.n_gridpart = h->n_gridpart;
   if (pairs) { d.Vacc = h->d_Vfin; d.dO = h->d_dO; }
+  d.tc_asl = h->d_tc_asl; d.tc_bsl = h->d_tc_bsl;
+  d.tc_rexp = h->d_tc_rexp; d.tc_cexp = h->d_tc_cexp;
+  d.tc_min_work = h->tc_min_work;
   d.red = h->d_red; d.flags = h->d_flags; d.bar = h->d_bar; d.scal = h->d_scal;
   // c_k = (-1)^k/(2k)!, s_k = (-1)^k/(2k+1)!
   double f = 1.0;
@@ -1213,9 +1568,12 @@ DenseArgs dense_args(etdm_handle *h, const double *a) {
 cudaError_t launch_dense_forward(etdm_handle *h, const double *a, cudaStream_t s) {
   DenseArgs d = dense_args(h, a);
   void *args[] = {&d};
+  h->pairs_last = dense_pairs(h);
+  if (dense_pairs(h) && h->dense_tc)
+    return cudaLaunchCooperativeKernel((const void *)dense_forward_tc_kernel, dim3(h->coop_blocks),
+                                       dim3(NT), args, kGDyn, s);
   const void *fn = dense_pairs(h) ? (const void *)dense_forward_kernel<float2>
                                   : (const void *)dense_forward_kernel<double>;
-  h->pairs_last = dense_pairs(h);
   return cudaLaunchCooperativeKernel(fn, dim3(h->coop_blocks), dim3(NT), args, 0, s);
 }
 
@@ -1226,6 +1584,9 @@ cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, dou
   d.resid = (h->want_resid && g) ? h->d_dot + 3 : nullptr;  // Eq. 45 with the energy
   int want = g != nullptr;
   void *args[] = {&d, &want};
+  if (dense_pairs(h) && h->dense_tc)
+    return cudaLaunchCooperativeKernel((const void *)dense_reverse_tc_kernel, dim3(h->coop_blocks),
+                                       dim3(NT), args, kGDyn, s);
   const void *fn = dense_pairs(h) ? (const void *)dense_reverse_kernel<float2>
                                   : (const void *)dense_reverse_kernel<double>;
   return cudaLaunchCooperativeKernel(fn, dim3(h->coop_blocks), dim3(NT), args, 0, s);
@@ -1372,6 +1733,41 @@ int occupancy_dense(int *bps) {
   *bps = best;
   return 0;
 }
+
+int occupancy_dense_tc(int *bps) {
+  const void *fns[2] = {(const void *)dense_forward_tc_kernel, (const void *)dense_reverse_tc_kernel};
+  int best = 1 << 30;
+  for (const void *f : fns) {
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kGDyn) != cudaSuccess)
+      return -1;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, NT, kGDyn) != cudaSuccess) return -1;
+    best = std::min(best, b);
+  }
+  *bps = best;
+  return 0;
+}
+
+cudaError_t launch_pair_gemm(const double *A, const double *B, double *C, int m, int n, int k,
+                             int ta, int tb, uint8_t *asl, uint8_t *bsl, int *rexp, int *cexp,
+                             unsigned *bar, int *flags, int blocks, cudaStream_t s) {
+  Phase ph{};
+  ph.m = m; ph.n = n; ph.k = k; ph.np = 1;
+  ph.p[0] = Prod{A, B, ta ? m : k, tb ? k : n, ta, tb, 1.0, 3};
+  ph.out = C; ph.ldo = n; ph.out64 = 1;
+  DenseArgs d{};
+  d.tc_asl = asl; d.tc_bsl = bsl; d.tc_rexp = rexp; d.tc_cexp = cexp;
+  d.bar = bar; d.flags = flags;
+  void *args[] = {&ph, &d};
+  cudaError_t e = cudaFuncSetAttribute((const void *)pair_gemm_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kGDyn);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((const void *)pair_gemm_kernel, dim3(blocks), dim3(NT), args,
+                                     kGDyn, s);
+}
+
+size_t dense_tc_asl_bytes(long M) { return (size_t)kGS * gpad(M, 128) * gpad(M, 16) * 2; }
+size_t dense_tc_bsl_bytes(long M) { return (size_t)kGS * gpad(M, kGN) * gpad(M, 16) * 2; }
 
 int occupancy_lbfgs(int *bps) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, lbfgs_kernel, 256, 0) != cudaSuccess)

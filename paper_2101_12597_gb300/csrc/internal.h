@@ -94,6 +94,11 @@ struct DenseArgs {
   double *g;             // N x V output, FP64 (may be null)
   double *E;             // scalar output (may be null)
   double *resid;         // Eq. 45 residual output, Hartree^2 (null: not computed; needs g)
+  // tensor-core products of the float-pair chains: slice workspace and the
+  // size (m n k) from which a phase uses them
+  uint8_t *tc_asl, *tc_bsl;
+  int *tc_rexp, *tc_cexp;
+  long long tc_min_work;
   double *eterms;        // [4] kinetic, external, hartree, exchange
   const double *gridpart;  // [n_gridpart][3] energy partials of the grid
   const void *Vacc;      // (R) mixed path: upper-triangle V from the grid pass, else null
@@ -304,6 +309,10 @@ struct etdm_handle {
   etdm::MixedPlan plan{};
   int *d_active1 = nullptr;              // [1] = 1
   bool want_resid = false;               // evaluations also compute the Eq. 45 residual
+  bool dense_tc = false;                 // the float-pair chains use the tensor cores
+  long long tc_min_work = 0;
+  uint8_t *d_tc_asl = nullptr, *d_tc_bsl = nullptr;
+  int *d_tc_rexp = nullptr, *d_tc_cexp = nullptr;
   uint2 *d_Osl = nullptr;     // [M][N + N % 2] BF16 slices of O
   float *d_oscale = nullptr;  // [N]
   double *d_dO = nullptr;     // [M][N] O - Oq
@@ -448,6 +457,12 @@ int tc_max_list();
 // message for etdm_last_error(NULL) from calls that take no handle
 void set_unbound_error(const std::string &msg);
 int occupancy_dense(int *blocks_per_sm);
+int occupancy_dense_tc(int *blocks_per_sm);  // the tensor-core variants (with their shared memory)
+cudaError_t launch_pair_gemm(const double *A, const double *B, double *C, int m, int n, int k,
+                             int ta, int tb, uint8_t *asl, uint8_t *bsl, int *rexp, int *cexp,
+                             unsigned *bar, int *flags, int blocks, cudaStream_t s);
+size_t dense_tc_asl_bytes(long M);
+size_t dense_tc_bsl_bytes(long M);
 // arguments of one system's dense chains at the point a (g, E: set by the caller)
 DenseArgs dense_args(etdm_handle *h, const double *a);
 LbfgsArgs lbfgs_args(etdm_handle *h, const double *a, const double *g, double *p);

@@ -1,0 +1,142 @@
+// Tensor-core products of the mixed path's dense chains (Eq. 7 O = C0 U, the
+// exp(A) series, T O, V O, C0^T Gbar and the reverse pass), run inside the
+// cooperative dense kernels on float-pair matrices.
+//
+// A product out = alpha op(A) op(B) (+ epilogue terms) of float pairs (about
+// 47 bits) is evaluated exactly in BF16 slices:
+//   row i of op(A) and column j of op(B) are scaled by powers of two
+//   2^(8-e_i), 2^(8-f_j) (|scaled| < 128) and cut into five slices each, r_t
+//   a multiple of 2^-8t with an integer numerator of at most 129 (exact in
+//   BF16, slice5);
+//   the slice products of orders t + u <= 4 (15 MMAs per K step of 16) go
+//   into five FP32 accumulators in tensor memory, one per order;
+//   every product of slices is an integer of at most 2^14 in units of its
+//   order, so an accumulator of order <= 3 (at most four products per K
+//   element) is exact over 15 K steps (240 elements: 4 x 240 x 129^2 <
+//   2^24) whatever rounding the accumulator applies; the epilogue reads these
+//   four every 15 K steps and adds them into float-pair sums; the order-4
+//   accumulator runs over all of K in FP32 (its rounding is about 2^-41 of
+//   the result);
+//   the dropped orders >= 5 are about 2^-40 of |A||B| per term.
+// Roles (warps of the 512-thread block): warp 0 streams the slices of a K
+// step (one 20 KB and one 10 KB bulk copy) into a five-stage ring, warp 1
+// issues the MMAs, warps 8-15 read the accumulators (lane quarter w % 4,
+// 32-column half (w - 8) / 4) and write the outputs with the phase's epilogue
+// terms.  Every wait is bounded.
+#pragma once
+
+#include "pair.cuh"
+#include "tc.cuh"
+
+namespace etdm {
+
+constexpr int kGS = 5;                   // BF16 slices per operand
+constexpr int kGN = 64;                  // output tile columns (MMA N); rows: 128
+constexpr int kGA = kGS * 4096;          // A slices of one K step (128 rows x 16): 20 KB
+constexpr int kGB = kGS * 2048;          // B slices of one K step (64 rows x 16): 10 KB
+constexpr int kGStage = kGA + kGB;
+constexpr int kGStages = 5;
+constexpr int kGChunk = 15;              // K steps per exact chunk of the order 0-3 sums
+constexpr int kGDyn = kGStages * kGStage;  // dynamic shared memory, 150 KB
+constexpr int kGEpiW0 = 8;               // first read-out warp
+
+__host__ __device__ __forceinline__ long gpad(long x, long q) { return (x + q - 1) / q * q; }
+
+// Workspace of the tensor-core products (device memory, one product at a time)
+struct GemmWs {
+  uint8_t *asl;  // A slices: [row block][K step][slice][4 KB], canonical K-major layout
+  uint8_t *bsl;  // B slices: [column block][K step][slice][2 KB]
+  int *rexp;     // per row of op(A): bits of max |value| (then the slice exponent)
+  int *cexp;     // per column of op(B)
+};
+
+// mbarriers of the tensor-core products, initialized once per kernel, and the
+// roles' running counts (stage fills, exact chunks, final waits), carried
+// from one product to the next so that every wait names its phase exactly
+struct GemmSmem {
+  uint64_t full[kGStages], empty[kGStages];
+  uint64_t acc_full, acc_empty, fin;
+  int stop;
+  int fill_copy, fill_mma, chunk_mma, chunk_epi, fins;
+};
+
+// tensor-core context of one block of a cooperative dense kernel
+struct TcCtx {
+  GemmWs ws;
+  uint8_t *dyn;     // dynamic shared memory (the stage ring)
+  GemmSmem *S;
+  uint32_t tmem;    // 512 columns, allocated for the kernel's lifetime
+};
+
+// row (column) maxima of |op(X)| as float bits, atomicMax over 32-element
+// segments; `rowmajor` when the rows of op(X) are contiguous in memory
+template <class F>
+__device__ void tc_maxima(F fetch, int rows, int K, bool rowmajor, int *out, long gtid,
+                          long gstride) {
+  const long segs = (K + 31) / 32;
+  // 32 lanes per (row, segment) when rows are contiguous, else per (group of
+  // 32 rows, segment)
+  const long items = (rowmajor ? (long)rows : (long)((rows + 31) / 32)) * segs * 32;
+  for (long e = gtid; e < items; e += gstride) {
+    const int lane = (int)(e & 31);
+    const long w = e >> 5;
+    float m = 0.f;
+    if (rowmajor) {  // the warp reads 32 consecutive k of one row
+      const int i = (int)(w / segs), k = (int)(w % segs) * 32 + lane;
+      if (i < rows && k < K) m = fabsf(fetch(i, k).x);
+      m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+      if (lane == 0 && i < rows) atomicMax(out + i, __float_as_int(m));
+    } else {  // the lanes read 32 consecutive rows at each k of the segment
+      const int i = (int)(w / segs) * 32 + lane, k0 = (int)(w % segs) * 32;
+      if (i < rows) {
+        for (int k = k0; k < min(K, k0 + 32); ++k) m = fmaxf(m, fabsf(fetch(i, k).x));
+        atomicMax(out + i, __float_as_int(m));
+      }
+    }
+  }
+}
+
+// slices of op(X) (rows x K) into the canonical layout: blocks of `br` rows x
+// 16 K, one block per slice, kGS blocks of br*32 bytes per (row block, K step);
+// padding rows and K are zero
+template <class F>
+__device__ void tc_slice(F fetch, int rows, int K, int br, bool rowmajor, const int *exps,
+                         uint8_t *dst, long gtid, long gstride) {
+  const int nrb = (rows + br - 1) / br, nks = (K + 15) / 16;
+  const long items = (long)nrb * br * nks * 2;  // (row, 8-element K group)
+  const int bb = br * 32;                        // bytes of one slice block
+  for (long e = gtid; e < items; e += gstride) {
+    int i, g;
+    if (rowmajor) {  // consecutive threads: consecutive K groups of one row
+      i = (int)(e / (nks * 2));
+      g = (int)(e % (nks * 2));
+    } else {  // consecutive threads: consecutive rows at one K group
+      g = (int)(e / ((long)nrb * br));
+      i = (int)(e % ((long)nrb * br));
+    }
+    const int k0 = g * 8;
+    float sc = 0.f;
+    if (i < rows) sc = pow2f(8 - slice_exp(__int_as_float(exps[i])));
+    uint32_t wd[kGS][4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      float r[2][kGS];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int k = k0 + u + v;
+        const float2 x = (i < rows && k < K) ? fetch(i, k) : make_float2(0.f, 0.f);
+        slice5(x, sc, r[v]);
+      }
+#pragma unroll
+      for (int t = 0; t < kGS; ++t) wd[t][u >> 1] = pack_bf16(r[0][t], r[1][t]);
+    }
+    const int rb = i / br, rr = i % br, ks = g >> 1;
+    uint8_t *blk = dst + ((long)rb * nks + ks) * kGS * bb;
+    const int off = kstep_off(rr, (g & 1) * 8);
+#pragma unroll
+    for (int t = 0; t < kGS; ++t)
+      *(uint4 *)(blk + t * bb + off) = make_uint4(wd[t][0], wd[t][1], wd[t][2], wd[t][3]);
+  }
+}
+
+}  // namespace etdm

@@ -27,7 +27,8 @@ ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "eterms": (13, np.float64), "beta": (14, np.float64),
           "tile_ptr_tc": (15, np.int32), "tile_keys_tc": (16, np.int32),
           "tile_nu_tc": (17, np.int32), "vgroup_t0": (18, np.int32),
-          "vgroup_nu": (19, np.int32), "doublings": (20, np.int32)}
+          "vgroup_nu": (19, np.int32), "doublings": (20, np.int32),
+          "status": (21, np.int32)}
 DIM_NAMES = ["M", "N", "V", "G", "n_tiles", "entries", "max_list", "tx", "ty",
              "tz", "sum_npt2", "precision"]
 
@@ -38,7 +39,7 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_stage_times", "etdm_last_error", "etdm_free",
            "etdm_lbfgs_direction_noalloc", "etdm_lbfgs_direction_noalloc_status",
            "etdm_init_batch", "etdm_num_systems", "etdm_system_layout", "etdm_system_handle",
-           "etdm_set_active", "etdm_minimize_converge"]
+           "etdm_set_active", "etdm_minimize_converge", "etdm_pair_gemm"]
 STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
 
 
@@ -62,7 +63,8 @@ class EtdmOptions(ctypes.Structure):
                 ("gamma", ctypes.c_double),
                 ("beta0", ctypes.c_double),
                 ("device", ctypes.c_int32),
-                ("dense_blocks", ctypes.c_int32)]
+                ("dense_blocks", ctypes.c_int32),
+                ("dense_tc", ctypes.c_int32)]
 
 
 _lib = None
@@ -93,6 +95,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.etdm_minimize_converge.argtypes = [P, P, ctypes.c_int32, ctypes.c_double, dp, dp,
                                            ctypes.POINTER(ctypes.c_int32), dp,
                                            ctypes.POINTER(ctypes.c_int32), P]
+    lib.etdm_pair_gemm.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_int32, P]
     lib.etdm_check.argtypes = [P, P]
     lib.etdm_layout.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.etdm_array_bytes.argtypes = [P, ctypes.c_int32]
@@ -200,7 +204,7 @@ def _system_struct(sysd, s=None):
     return s, keep
 
 
-def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks):
+def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc=0):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision]
@@ -209,6 +213,7 @@ def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks):
     o.beta0 = beta0
     o.device = device
     o.dense_blocks = dense_blocks
+    o.dense_tc = dense_tc
     return o
 
 
@@ -216,14 +221,14 @@ class ETDM:
     """One system on one GPU: the handle of etdm_init_basis."""
 
     def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
-                 device=0, dense_blocks=0):
+                 device=0, dense_blocks=0, dense_tc=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
         self.lib = load_library()
         self.device = device
         s, self._keep = _system_struct(sysd)
-        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks)
+        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -501,6 +506,32 @@ class ETDMBatch:
             self.close()
         except Exception:
             pass
+
+
+def pair_gemm(A, B, ta=False, tb=False, stream=None):
+    """C = op(A) op(B) of FP64 CUDA matrices through the tensor-core product of
+    the mixed-precision dense chains (exact BF16 slices, about 2^-39 relative)."""
+    import torch
+    lib = load_library()
+    if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dim() == 2):
+        raise ValueError("A: expected a 2-D CUDA tensor")
+    if not (isinstance(B, torch.Tensor) and B.dim() == 2):
+        raise ValueError("B: expected a 2-D CUDA tensor")
+    m, k = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
+    k2, n = (B.shape[1], B.shape[0]) if tb else (B.shape[0], B.shape[1])
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {k} and {k2}")
+    _require(A, A.device, "A", shape=tuple(A.shape))
+    _require(B, A.device, "B", shape=tuple(B.shape))
+    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    with torch.cuda.device(A.device):
+        st = stream if stream is not None else torch.cuda.current_stream(A.device)
+        rc = lib.etdm_pair_gemm(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                ctypes.c_void_p(C.data_ptr()), m, n, k, int(bool(ta)),
+                                int(bool(tb)), ctypes.c_void_p(st.cuda_stream))
+    if rc != ETDM_OK:
+        raise EtdmError(rc, lib.etdm_last_error(None).decode())
+    return C
 
 
 def _storage_span(t):

@@ -76,6 +76,28 @@ def test_tc_truncation_lists_bit_exact(which, cases):
             assert len(np.union1d(funcs[t0[g]], funcs[t0[g + 1]])) > 128
 
 
+@pytest.mark.parametrize("which", ["tiny", "small", "ragged"])
+def test_mixed_tensor_core_chains_on_small_systems(which, cases):
+    """Every product of the float-pair chains on the tensor cores for systems
+    whose matrices are far smaller than one 128 x 64 tile (padding, one K
+    step): energy and gradient against the oracle."""
+    torch = _torch()
+    from paper_2101_12597_gb300.etdm import ETDM
+    d, o, _ = cases[which]
+    s = ETDM(d, precision="mixed", dense_tc=1)
+    E_ref, g_ref = o.energy_grad(d["a0"])
+    E, g = s.energy_grad(torch.tensor(d["a0"], device="cuda"))
+    torch.cuda.synchronize()
+    print(f"{which} status words: {s.get_array('status').tolist()}")
+    s.check()
+    dE = abs(float(E.item()) - E_ref)
+    dg = _grad_err(g.cpu().numpy(), g_ref)
+    print(f"{which} tensor-core chains: |dE|={dE:.3e} Ha  grad err={dg:.3e}")
+    assert dE < E_TOL
+    assert dg <= G_TOL
+    s.close()
+
+
 @pytest.mark.parametrize("which", ["tiny", "small", "ragged", "odd"])
 def test_mixed_energy_gradient_parity(which, cases):
     torch = _torch()
@@ -178,13 +200,21 @@ def test_water576_mixed_vs_fp64_path():
     properties that hold at any size: unitary U, and sampled 4x4x8 truncation
     lists bit-exact against the oracle's."""
     torch = _torch()
+    from paper_2101_12597_gb300.etdm import ETDM
     d = synth.config_water576()
     a = torch.tensor(d["a0"], device="cuda")
-    s = _solver(d)
+    s = _solver(d)  # the large products of the chains on the tensor cores
     E, g = s.energy_grad(a)
     torch.cuda.synchronize()
     s.check()
     E, g = float(E.item()), g.cpu().numpy()
+    s2 = ETDM(d, precision="mixed", dense_tc=-1)  # every product on float pairs
+    E2, g2 = s2.energy_grad(a)
+    torch.cuda.synchronize()
+    s2.check()
+    print(f"water576 tensor-core vs float-pair chains: |dE|={abs(E - float(E2.item())):.3e} Ha "
+          f"grad err={_grad_err(g, g2.cpu().numpy()):.3e}")
+    s2.close()
     U = s.get_array("Uocc").reshape(s.M, s.N)
     assert np.abs(U.T @ U - np.eye(s.N)).max() < 1e-11
     o = Oracle(d)
@@ -240,21 +270,23 @@ def water75():
     return d, o, E, g, ex
 
 
-@pytest.mark.parametrize("precision,dense_blocks", [("fp64", 0), ("fp64", 4),
-                                                    ("mixed", 0), ("mixed", 4)])
-def test_water75_against_oracle(water75, precision, dense_blocks):
+@pytest.mark.parametrize("precision,dense_blocks,dense_tc", [
+    ("fp64", 0, 0), ("fp64", 4, 0), ("mixed", 0, -1), ("mixed", 4, -1), ("mixed", 0, 1)])
+def test_water75_against_oracle(water75, precision, dense_blocks, dense_tc):
     """Both GPU paths at a size that runs the density pass over three orbital
     chunks (N = 300 > 128) and, with the dense grid fixed at 4 blocks, puts
     every product of the dense chains on the 64 x 64 output tiles (the
     automatic grid keeps them on 8 x 16 tiles): energy, gradient, density and
     the Hamiltonian (its grid part V on the mixed path) element by element
-    against the oracle."""
+    against the oracle.  dense_tc = 1 runs every product of the float-pair
+    chains on the tensor cores (exact BF16 slices)."""
     torch = _torch()
     from paper_2101_12597_gb300.etdm import ETDM
     d, o, E_ref, g_ref, ex = water75
-    s = ETDM(d, precision=precision, dense_blocks=dense_blocks)
+    s = ETDM(d, precision=precision, dense_blocks=dense_blocks, dense_tc=dense_tc)
     E, g = s.energy_grad(torch.tensor(d["a0"], device="cuda"))
     torch.cuda.synchronize()
+    print(f"water75 status words: {s.get_array('status').tolist()}")
     s.check()
     dE = abs(float(E.item()) - E_ref)
     dg = _grad_err(g.cpu().numpy(), g_ref)
@@ -264,7 +296,7 @@ def test_water75_against_oracle(water75, precision, dense_blocks):
     H = s.get_array("H").reshape(M, M)
     Href = ex["H"] - (s.get_array("T").reshape(M, M) if precision == "mixed" else 0.0)
     dH = float(np.abs(H - Href).max() / np.abs(Href).max())
-    print(f"water75 {precision} dense_blocks={dense_blocks}: |dE|={dE:.3e} Ha "
+    print(f"water75 {precision} dense_blocks={dense_blocks} dense_tc={dense_tc}: |dE|={dE:.3e} Ha "
           f"grad err={dg:.3e} rho err={drho:.2e} H err={dH:.2e}")
     assert dE < E_TOL
     assert dg <= G_TOL

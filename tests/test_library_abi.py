@@ -40,8 +40,8 @@ def test_default_options(lib):
     from paper_2101_12597_gb300.etdm import EtdmOptions
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
-    assert (o.precision, o.lbfgs_m, o.gamma, o.beta0, o.device, o.dense_blocks) == \
-        (0, 3, 0.25, 1.0, 0, 0)
+    assert (o.precision, o.lbfgs_m, o.gamma, o.beta0, o.device, o.dense_blocks,
+            o.dense_tc) == (0, 3, 0.25, 1.0, 0, 0, 0)
 
 
 def _system(lib, d, **over):
