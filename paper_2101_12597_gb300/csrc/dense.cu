@@ -430,6 +430,13 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
   const TcCtx &C = cp.tc->ctx;
   GemmSmem &S = *C.S;
   const int m = P.m, n = P.n, K = P.k;
+  // scalars in registers: the MMA and copy loops read no memory between their
+  // asm statements (which clobber memory)
+  const uint32_t tmem = C.tmem;
+  uint8_t *const dyn = C.dyn;
+  const uint8_t *const asl = C.ws.asl, *const bsl = C.ws.bsl;
+  const int *const rexp = C.ws.rexp, *const cexp = C.ws.cexp;
+  const int rank = cp.rank, size = cp.size;
   const int ncb = (n + kGN - 1) / kGN, nks = (K + 15) / 16;
   const int ntiles = ((m + 127) / 128) * ncb;
   const int nch = (nks + kGChunk - 1) / kGChunk;
@@ -450,10 +457,10 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
       asm volatile("fence.proxy.async.global;" ::: "memory");
       int fill = fill0_copy;
       bool ok = true;
-      for (int t = cp.rank; t < ntiles && ok; t += cp.size) {
+      for (int t = rank; t < ntiles && ok; t += size) {
         const int rb = t / ncb, cb = t % ncb;
-        const uint8_t *ab = C.ws.asl + (size_t)rb * nks * kGA;
-        const uint8_t *bb = C.ws.bsl + (size_t)cb * nks * kGB;
+        const uint8_t *ab = asl + (size_t)rb * nks * kGA;
+        const uint8_t *bb = bsl + (size_t)cb * nks * kGB;
         for (int ks = 0; ks < nks; ++ks, ++fill) {
           const int s = fill % kGStages, use = fill / kGStages;
           if (use > 0 && !mbar_wait(&S.empty[s], (use - 1) & 1, stop)) {
@@ -462,8 +469,8 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
             break;
           }
           mbar_expect_tx(&S.full[s], kGStage);
-          bulk_g2s(C.dyn + s * kGStage, ab + (size_t)ks * kGA, kGA, &S.full[s]);
-          bulk_g2s(C.dyn + s * kGStage + kGA, bb + (size_t)ks * kGB, kGB, &S.full[s]);
+          bulk_g2s(dyn + s * kGStage, ab + (size_t)ks * kGA, kGA, &S.full[s]);
+          bulk_g2s(dyn + s * kGStage + kGA, bb + (size_t)ks * kGB, kGB, &S.full[s]);
         }
       }
       if (!ok) atomicExch((int *)stop, 1);
@@ -477,19 +484,20 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
   } else if (w == 1) {
     // ------------------------------------ MMA issue ------------------------------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kGN);
+      // instruction descriptors of N = 256, 192, 128, 64 (index 4 - N / 64)
+      const uint32_t id256 = idesc_bf16(256), id192 = idesc_bf16(192), id128 = idesc_bf16(128),
+                     id64 = idesc_bf16(64);
       int fill = fill0_mma, ch = ch0_mma;
       bool ok = true;
-      for (int t = cp.rank; t < ntiles && ok; t += cp.size) {
+      for (int t = rank; t < ntiles && ok; t += size) {
         for (int ks = 0; ks < nks; ++ks, ++fill) {
-          const int kc = ks % kGChunk;
-          if (kc == 0 && ch > 0) {  // the read-out of the previous chunk is done
-            if (!mbar_wait(&S.acc_empty, (ch - 1) & 1, stop)) {
+          const int kc = ks % kGChunk, b = ch & 1;
+          if (kc == 0 && ch >= 2) {  // the read-out of this buffer's previous chunk is done
+            if (!mbar_wait(&S.acc_empty[b], ((ch >> 1) - 1) & 1, stop)) {
               tc_gave_up(cp, 2, ch);
               ok = false;
               break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           }
           const int s = fill % kGStages, use = fill / kGStages;
           if (!mbar_wait(&S.full[s], use & 1, stop)) {
@@ -498,26 +506,23 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = su32(C.dyn + s * kGStage), b0 = a0 + kGA;
-          uint64_t Ad[kGS], Bd[kGS];
+          const uint32_t a0 = su32(dyn + s * kGStage), b0 = a0 + kGA;
+          const uint32_t d = tmem + b * kGSet;
+          const uint64_t B0 = smem_desc(b0);
+          // A_q against B_0 .. B_(3-q) (consecutive in shared memory) lands the
+          // orders q .. 3 at columns 64 q .. 192: one MMA per q; the first of a
+          // chunk starts the four sums afresh
+          mma_bf16(d, smem_desc(a0), B0, id256, kc == 0 ? 0u : 1u);
+          mma_bf16(d + 64, smem_desc(a0 + 4096), B0, id192, 1u);
+          mma_bf16(d + 128, smem_desc(a0 + 8192), B0, id128, 1u);
+          mma_bf16(d + 192, smem_desc(a0 + 12288), B0, id64, 1u);
+          // the order-4 products A_q B_(4-q) into the order-3 sum (FP32)
 #pragma unroll
-          for (int q = 0; q < kGS; ++q) {
-            Ad[q] = smem_desc(a0 + q * 4096);
-            Bd[q] = smem_desc(b0 + q * 2048);
-          }
-          // order o = t + u into the accumulator at column o * 64; orders 0-3
-          // restart every chunk, order 4 every tile
-#pragma unroll
-          for (int o = 0; o < kGS; ++o) {
-#pragma unroll
-            for (int q = 0; q <= o; ++q) {
-              const bool restart = q == 0 && (o < kGS - 1 ? kc == 0 : ks == 0);
-              mma_bf16(C.tmem + o * kGN, Ad[q], Bd[o - q], idesc, restart ? 0u : 1u);
-            }
-          }
+          for (int q = 0; q < kGS; ++q)
+            mma_bf16(d + 192, smem_desc(a0 + q * 4096), smem_desc(b0 + (4 - q) * 2048), id64, 1u);
           mma_commit(&S.empty[s]);
           if (kc == kGChunk - 1 || ks == nks - 1) {
-            mma_commit(&S.acc_full);
+            mma_commit(&S.acc_full[b]);
             ++ch;
           }
         }
@@ -537,56 +542,48 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
     int ch = ch0_epi;
     bool ok = true;
     double sql = 0.0;
-    for (int t = cp.rank; t < ntiles && ok; t += cp.size) {
+    for (int t = rank; t < ntiles && ok; t += size) {
       const int rb = t / ncb, cb = t % ncb;
       float2 acc[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) acc[c] = make_float2(0.f, 0.f);
       for (int c = 0; c < nch; ++c, ++ch) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&S.acc_full, ch & 1, stop));
+        const int b = ch & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&S.acc_full[b], (ch >> 1) & 1, stop));
         if (!ok) {
           if (lane == 0) tc_gave_up(cp, 4, ch);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int cg = 0; cg < 4; ++cg) {  // 8 columns of the four exact orders
+        for (int cg = 0; cg < 4; ++cg) {  // 8 columns of the four sums
           uint32_t r[32];
-          tmem_ld_issue(C.tmem + lanebits + half * 32 + cg * 8, r, kGN);
+          tmem_ld_issue(tmem + b * kGSet + lanebits + half * 32 + cg * 8, r, kGN);
           tmem_ld_wait(r);
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            // the exact integers of orders 0 .. 3 (each on its own 2^-8o grid)
+            // the exact integers of orders 0 .. 2 (each on its own 2^-8o grid)
+            // and the FP32 sum of orders 3 and 4
             const float2 y = pair::two_sum(__uint_as_float(r[j]), __uint_as_float(r[8 + j]));
             const float lo = __fadd_rn(y.y, __fadd_rn(__uint_as_float(r[16 + j]), __uint_as_float(r[24 + j])));
             acc[cg * 8 + j] = pair::add(acc[cg * 8 + j], make_float2(y.x, lo));
           }
         }
-        if (c == nch - 1) {  // the FP32 order-4 sums of the whole K range
-#pragma unroll
-          for (int cg = 0; cg < 4; ++cg) {
-            uint32_t r[8];
-            tmem_ld8(C.tmem + lanebits + 4 * kGN + half * 32 + cg * 8, r);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              acc[cg * 8 + j] = pair::add(acc[cg * 8 + j], make_float2(__uint_as_float(r[j]), 0.f));
-          }
-        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.acc_empty);
+        if (lane == 0) mbar_arrive(&S.acc_empty[b]);
       }
       if (!ok) break;
       // out = alpha 2^(e_i - 8) 2^(f_j - 8) acc (+ epilogue terms on the first product)
       const int i = rb * 128 + row;
       if (i < m) {
-        const float si = pow2f(slice_exp(__int_as_float(C.ws.rexp[i])) - 8);
+        const float si = pow2f(slice_exp(__int_as_float(rexp[i])) - 8);
         const float2 al = pair::split(pr.alpha);
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int j = cb * kGN + half * 32 + c;
           if (j >= n) continue;
-          const float sj = pow2f(slice_exp(__int_as_float(C.ws.cexp[j])) - 8);
+          const float sj = pow2f(slice_exp(__int_as_float(cexp[j])) - 8);
           float2 v = pair::scale2(pair::scale2(acc[c], si), sj);
           v = pair::mul(al, v);
           const long o = (long)i * P.ldo + j;
@@ -1110,8 +1107,10 @@ __device__ __forceinline__ void tc_setup(const DenseArgs &a, TcRun &run, GemmSme
       mbar_init(&gS.full[s], 1);
       mbar_init(&gS.empty[s], 1);
     }
-    mbar_init(&gS.acc_full, 1);
-    mbar_init(&gS.acc_empty, 8);  // one arrival per read-out warp
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&gS.acc_full[b], 1);
+      mbar_init(&gS.acc_empty[b], 8);  // one arrival per read-out warp
+    }
     mbar_init(&gS.fin, 1);
     gS.stop = 0;
     gS.fill_copy = gS.fill_mma = gS.chunk_mma = gS.chunk_epi = gS.fins = 0;

@@ -3,26 +3,32 @@
 // cooperative dense kernels on float-pair matrices.
 //
 // A product out = alpha op(A) op(B) (+ epilogue terms) of float pairs (about
-// 47 bits) is evaluated exactly in BF16 slices:
+// 47 bits) is evaluated in BF16 slices:
 //   row i of op(A) and column j of op(B) are scaled by powers of two
 //   2^(8-e_i), 2^(8-f_j) (|scaled| < 128) and cut into five slices each, r_t
 //   a multiple of 2^-8t with an integer numerator of at most 129 (exact in
 //   BF16, slice5);
-//   the slice products of orders t + u <= 4 (15 MMAs per K step of 16) go
-//   into five FP32 accumulators in tensor memory, one per order;
-//   every product of slices is an integer of at most 2^14 in units of its
-//   order, so an accumulator of order <= 3 (at most four products per K
-//   element) is exact over 15 K steps (240 elements: 4 x 240 x 129^2 <
-//   2^24) whatever rounding the accumulator applies; the epilogue reads these
-//   four every 15 K steps and adds them into float-pair sums; the order-4
-//   accumulator runs over all of K in FP32 (its rounding is about 2^-41 of
-//   the result);
+//   the 15 slice products of orders t + u <= 4 go into four FP32 sums in
+//   tensor memory: one each for the orders 0, 1 and 2, and one for the orders
+//   3 and 4 together;
+//   the B slices of a K step lie one after another in shared memory, so
+//   A_q times [B_0 .. B_(3-q)] (one MMA of N = 64 (4 - q)) puts the orders
+//   q .. 3 at columns 64 q .. 192 at once; the five order-4 products A_q
+//   B_(4-q) add into the order-3 sum: 9 MMAs per K step of 16;
+//   every product of slices is an integer of at most 129^2 in units of its
+//   order, so the sums of orders 0 .. 2 (at most three products per K
+//   element) are exact over 21 K steps (336 elements: 3 x 336 x 129^2 <
+//   2^24) whatever rounding the accumulator applies; the epilogue reads the
+//   four sums every 21 K steps and adds them into float-pair sums; the FP32
+//   rounding of the order 3-4 sum is about 2^-48 of |A||B| per element;
 //   the dropped orders >= 5 are about 2^-40 of |A||B| per term.
+// Tensor memory holds two buffers of the four sums (256 columns each): the
+// MMAs of one chunk run while the epilogue reads the previous one.
 // Roles (warps of the 512-thread block): warp 0 streams the slices of a K
 // step (one 20 KB and one 10 KB bulk copy) into a five-stage ring, warp 1
-// issues the MMAs, warps 8-15 read the accumulators (lane quarter w % 4,
-// 32-column half (w - 8) / 4) and write the outputs with the phase's epilogue
-// terms.  Every wait is bounded.
+// issues the MMAs, warps 8-15 read the sums (lane quarter w % 4, 32-column
+// half (w - 8) / 4) and write the outputs with the phase's epilogue terms.
+// Every wait is bounded.
 #pragma once
 
 #include "pair.cuh"
@@ -36,7 +42,8 @@ constexpr int kGA = kGS * 4096;          // A slices of one K step (128 rows x 1
 constexpr int kGB = kGS * 2048;          // B slices of one K step (64 rows x 16): 10 KB
 constexpr int kGStage = kGA + kGB;
 constexpr int kGStages = 5;
-constexpr int kGChunk = 15;              // K steps per exact chunk of the order 0-3 sums
+constexpr int kGChunk = 21;              // K steps per chunk (exact order 0-2 sums)
+constexpr int kGSet = 256;               // tensor-memory columns of one buffer of the four sums
 constexpr int kGDyn = kGStages * kGStage;  // dynamic shared memory, 150 KB
 constexpr int kGEpiW0 = 8;               // first read-out warp
 
@@ -55,7 +62,7 @@ struct GemmWs {
 // from one product to the next so that every wait names its phase exactly
 struct GemmSmem {
   uint64_t full[kGStages], empty[kGStages];
-  uint64_t acc_full, acc_empty, fin;
+  uint64_t acc_full[2], acc_empty[2], fin;  // per tensor-memory buffer
   int stop;
   int fill_copy, fill_mma, chunk_mma, chunk_epi, fins;
 };
