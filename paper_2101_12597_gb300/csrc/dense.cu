@@ -365,9 +365,11 @@ __device__ __noinline__ void phase_tile_big(const Phase &ph, int tile, R (*As)[L
 constexpr int kSmallTileBytes = (KG * 2 * BM * (BK + 1) + KG * 2 * BK * (BN + 1) + (KG - 1) * NG) * 8;
 constexpr int kBigTileBytes = (2 * LBK * (LBM + 1) + 2 * LBK * (LBN + 1)) * 8;
 constexpr int kTileBytes = kSmallTileBytes > kBigTileBytes ? kSmallTileBytes : kBigTileBytes;
+static_assert(kTileBytes >= 8 * 32 * 16 * 8, "the tensor-core epilogue stages 8 warps x 32 x 16 float pairs here");
 
 template <class R>
-__device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *sph, int count, double *sq);
+__device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *sph, int count, double *sq,
+                                           float2 *stage);
 
 template <class R, bool TCK = false>
 __device__ __forceinline__ void run_phases(const Coop &cp, const Phase *ph, int count,
@@ -384,7 +386,7 @@ __device__ __forceinline__ void run_phases(const Coop &cp, const Phase *ph, int 
     for (int c = 0; c < count; ++c)
       work = max(work, (long long)sph[c].m * sph[c].n * sph[c].k);
     if (cp.tc && work >= cp.tc->min_work) {
-      run_phases_tc<R>(cp, sph, count, sq);
+      run_phases_tc<R>(cp, sph, count, sq, reinterpret_cast<float2 *>(tsm));  // tsm: 32 KB staging
       return;
     }
   }
@@ -426,7 +428,7 @@ __device__ __forceinline__ void tc_gave_up(const Coop &cp, int where, int count)
 // `first`: the phase's first product (writes alpha AB + epilogue terms), else
 // adds alpha AB to out; `last`: accumulates the squares of the outputs in *sq
 __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod &pr, bool first,
-                                      bool last, double *sq) {
+                                      bool last, double *sq, float2 *stage) {
   const TcCtx &C = cp.tc->ctx;
   GemmSmem &S = *C.S;
   const int m = P.m, n = P.n, K = P.k;
@@ -538,7 +540,10 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
     // ---------------------------- read-out and outputs ----------------------------
     const int e = w - kGEpiW0, quad = w & 3, half = e >> 2;
     const uint32_t lanebits = (uint32_t)(quad * 32) << 16;
-    const int row = quad * 32 + lane;
+    const float2 al = pair::split(pr.alpha), diag = pair::split(P.diag);
+    const long ldo = P.ldo;
+    void *const out = P.out;
+    const int out64 = P.out64, nc = P.nc;
     int ch = ch0_epi;
     bool ok = true;
     double sql = 0.0;
@@ -574,31 +579,45 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
         if (lane == 0) mbar_arrive(&S.acc_empty[b]);
       }
       if (!ok) break;
-      // out = alpha 2^(e_i - 8) 2^(f_j - 8) acc (+ epilogue terms on the first product)
-      const int i = rb * 128 + row;
-      if (i < m) {
-        const float si = pow2f(slice_exp(__int_as_float(rexp[i])) - 8);
-        const float2 al = pair::split(pr.alpha);
+      // out = alpha 2^(e_i - 8) 2^(f_j - 8) acc (+ epilogue terms on the first
+      // product); the warp's 32 x 32 block goes out through shared memory in two
+      // passes of 16 columns, so that each load and store of the outputs and the
+      // epilogue terms covers two 128-byte row pieces
+      const int i0 = rb * 128 + quad * 32;
+      {
+        const float si = i0 + lane < m ? pow2f(slice_exp(__int_as_float(rexp[i0 + lane])) - 8) : 0.f;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int j = cb * kGN + half * 32 + c;
-          if (j >= n) continue;
-          const float sj = pow2f(slice_exp(__int_as_float(cexp[j])) - 8);
-          float2 v = pair::scale2(pair::scale2(acc[c], si), sj);
-          v = pair::mul(al, v);
-          const long o = (long)i * P.ldo + j;
+        for (int c = 0; c < 32; ++c) acc[c] = pair::scale2(acc[c], si);
+      }
+      float2 *stg = stage + e * 512;  // this warp's 32 x 16 buffer (XOR-swizzled columns)
+      const int jc = lane & 15;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) stg[lane * 16 + (c ^ (lane & 15))] = acc[16 * p + c];
+        __syncwarp();
+        const int j = cb * kGN + half * 32 + 16 * p + jc;
+        if (j >= n) continue;
+        const float sj = pow2f(slice_exp(__int_as_float(cexp[j])) - 8);
+#pragma unroll 4
+        for (int rr = 0; rr < 16; ++rr) {
+          const int r = 2 * rr + (lane >> 4), i = i0 + r;
+          if (i >= m) continue;
+          float2 v = pair::mul(al, pair::scale2(stg[r * 16 + (jc ^ (r & 15))], sj));
+          const long o = (long)i * ldo + j;
           if (first) {
-            for (int q = 0; q < P.nc; ++q)
+            for (int q = 0; q < nc; ++q)
               v = pair::add(pair::mul(pair::split(P.beta[q]),
                                       static_cast<const float2 *>(P.C[q])[(long)i * P.ldc[q] + j]),
                             v);
-            if (i == j) v = pair::add(v, pair::split(P.diag));
+            if (i == j) v = pair::add(v, diag);
           } else {
-            v = pair::add(v, P.out64 ? pair::split(static_cast<const double *>(P.out)[o])
-                                     : static_cast<const float2 *>(P.out)[o]);
+            v = pair::add(v, out64 ? pair::split(static_cast<const double *>(out)[o])
+                                   : static_cast<const float2 *>(out)[o]);
           }
-          if (P.out64) static_cast<double *>(P.out)[o] = pair::to_double(v);
-          else static_cast<float2 *>(P.out)[o] = v;
+          if (out64) static_cast<double *>(out)[o] = pair::to_double(v);
+          else static_cast<float2 *>(out)[o] = v;
           if (last && sq) {
             const double d = pair::to_double(v);
             sql += d * d;
@@ -615,12 +634,45 @@ __device__ __noinline__ void tc_tiles(const Coop &cp, const Phase &P, const Prod
   if (tid == 0 && S.stop) atomicExch(cp.flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
 }
 
+// Element (i, k) of op(X) as a float pair, the storage fixed at compile time
+// (the slicing passes then issue their loads back to back): FMT bit 0 FP64
+// (else float pairs), bit 1 symmetric with the upper triangle stored;
+// T: op(X) = X^T.
+template <int FMT, int T>
+struct OpX {
+  const void *p;
+  long ld;
+  __device__ __forceinline__ float2 operator()(int i, int k) const {
+    long e;
+    if constexpr ((FMT & 2) != 0) e = i <= k ? (long)i * ld + k : (long)k * ld + i;
+    else e = T ? (long)k * ld + i : (long)i * ld + k;
+    if constexpr ((FMT & 1) == 0) return static_cast<const float2 *>(p)[e];
+    else return pair::split(static_cast<const double *>(p)[e]);
+  }
+};
+
+// calls g(accessor, rowmajor) with the accessor of op(A) (rows i, columns k)
+// or of op(B)^T (rows j, columns k)
+template <class G>
+__device__ __forceinline__ void with_op(const void *p, long ld, int trans, int fmt, G g) {
+  if (fmt == 3) g(OpX<3, 0>{p, ld}, true);
+  else if (fmt == 2) g(OpX<2, 0>{p, ld}, true);
+  else if (fmt == 1) {
+    if (trans) g(OpX<1, 1>{p, ld}, false);
+    else g(OpX<1, 0>{p, ld}, true);
+  } else {
+    if (trans) g(OpX<0, 1>{p, ld}, false);
+    else g(OpX<0, 0>{p, ld}, true);
+  }
+}
+
 // A call of run_phases on the tensor cores: the phases one after another,
 // each product sliced (exponents, then slices, into the workspace) and
 // multiplied; grid barriers between the steps.  Only the float-pair chains
 // take this path.
 template <class R>
-__device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *tph, int count, double *sq) {
+__device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *tph, int count, double *sq,
+                                           float2 *stage) {
   if constexpr (!Num<R>::kPair) {
     return;
   } else {
@@ -642,16 +694,25 @@ __device__ __noinline__ void run_phases_tc(const Coop &cp, const Phase *tph, int
         for (long e = gtid; e < P.m; e += gstride) W.rexp[e] = 0;
         for (long e = gtid; e < P.n; e += gstride) W.cexp[e] = 0;
         if (!cp.sync()) return;
-        auto fa = [&](int i, int k) { return opA<float2>(pr, i, k); };
-        auto fb = [&](int j, int k) { return opB<float2>(pr, k, j); };  // rows of op(B)^T
-        tc_maxima(fa, P.m, P.k, !pr.ta, W.rexp, gtid, gstride);
-        tc_maxima(fb, P.n, P.k, pr.tb != 0, W.cexp, gtid, gstride);
+        // op(A): rows i; op(B)^T: rows j (op(B)^T = B when tb, else B^T)
+        const int fa = (pr.f64 & 1) | ((pr.f64 & 4) ? 2 : 0), fb = (pr.f64 & 2) ? 1 : 0;
+        const int m = P.m, n = P.n, K = P.k;
+        with_op(pr.A, pr.lda, pr.ta, fa, [&](auto x, bool rm) {
+          tc_maxima(x, m, K, rm, W.rexp, gtid, gstride);
+        });
+        with_op(pr.B, pr.ldb, !pr.tb, fb, [&](auto x, bool rm) {
+          tc_maxima(x, n, K, rm, W.cexp, gtid, gstride);
+        });
         if (!cp.sync()) return;
-        tc_slice(fa, P.m, P.k, 128, !pr.ta, W.rexp, W.asl, gtid, gstride);
-        tc_slice(fb, P.n, P.k, kGN, pr.tb != 0, W.cexp, W.bsl, gtid, gstride);
+        with_op(pr.A, pr.lda, pr.ta, fa, [&](auto x, bool rm) {
+          tc_slice(x, m, K, 128, rm, W.rexp, W.asl, gtid, gstride);
+        });
+        with_op(pr.B, pr.ldb, !pr.tb, fb, [&](auto x, bool rm) {
+          tc_slice(x, n, K, kGN, rm, W.cexp, W.bsl, gtid, gstride);
+        });
         asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk copies
         if (!cp.sync()) return;
-        tc_tiles(cp, P, pr, q == first, q == last, sq);
+        tc_tiles(cp, P, pr, q == first, q == last, sq, stage);
         // the next product rewrites the workspace (and adds to these outputs)
         if ((q < last || c + 1 < count) && !cp.sync()) return;
       }

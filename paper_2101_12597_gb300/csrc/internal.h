@@ -45,7 +45,8 @@ struct Tables {
 
 // One dense product term for the cooperative dense kernels.  The matrices hold
 // the kernel's element type (FP64, or float pairs in the mixed path's chains);
-// f64 marks operands held as FP64 whatever the element type (bit 0: A, bit 1: B)
+// f64 marks operands held as FP64 whatever the element type (bit 0: A, bit 1: B);
+// bit 2: A symmetric with its upper triangle stored
 // and a symmetric A read from its upper triangle (bit 2).
 struct Prod {
   const void *A;

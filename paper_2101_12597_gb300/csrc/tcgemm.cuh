@@ -75,65 +75,101 @@ struct TcCtx {
   uint32_t tmem;    // 512 columns, allocated for the kernel's lifetime
 };
 
-// row (column) maxima of |op(X)| as float bits, atomicMax over 32-element
-// segments; `rowmajor` when the rows of op(X) are contiguous in memory
+// row (column) maxima of |op(X)| as float bits, atomicMax per segment of K;
+// `rowmajor` when the rows of op(X) are contiguous in memory.  Each thread has
+// eight loads in flight.
 template <class F>
 __device__ void tc_maxima(F fetch, int rows, int K, bool rowmajor, int *out, long gtid,
                           long gstride) {
-  const long segs = (K + 31) / 32;
-  // 32 lanes per (row, segment) when rows are contiguous, else per (group of
-  // 32 rows, segment)
-  const long items = (rowmajor ? (long)rows : (long)((rows + 31) / 32)) * segs * 32;
-  for (long e = gtid; e < items; e += gstride) {
-    const int lane = (int)(e & 31);
-    const long w = e >> 5;
-    float m = 0.f;
-    if (rowmajor) {  // the warp reads 32 consecutive k of one row
-      const int i = (int)(w / segs), k = (int)(w % segs) * 32 + lane;
-      if (i < rows && k < K) m = fabsf(fetch(i, k).x);
-      m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-      if (lane == 0 && i < rows) atomicMax(out + i, __float_as_int(m));
-    } else {  // the lanes read 32 consecutive rows at each k of the segment
-      const int i = (int)(w / segs) * 32 + lane, k0 = (int)(w % segs) * 32;
-      if (i < rows) {
-        for (int k = k0; k < min(K, k0 + 32); ++k) m = fmaxf(m, fabsf(fetch(i, k).x));
-        atomicMax(out + i, __float_as_int(m));
+  if (rowmajor) {  // a warp per (row, 256 consecutive k)
+    const long segs = (K + 255) / 256;
+    const long items = (long)rows * segs * 32;
+    for (long e = gtid; e < items; e += gstride) {
+      const int lane = (int)(e & 31);
+      const long w = e >> 5;
+      const int i = (int)(w / segs), k0 = (int)(w % segs) * 256 + lane;
+      float m = 0.f;
+      if (k0 + 224 < K) {  // the eight loads unconditional, all issued before the first use
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = fetch(i, k0 + 32 * u).x;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m = fmaxf(m, fabsf(x[u]));
+      } else {
+        for (int k = k0; k < K; k += 32) m = fmaxf(m, fabsf(fetch(i, k).x));
       }
+      m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+      if (lane == 0) atomicMax(out + i, __float_as_int(m));
+    }
+  } else {  // the lanes of a warp: 32 consecutive rows, 32 consecutive k each
+    const long segs = (K + 31) / 32;
+    const long items = (long)((rows + 31) / 32) * segs * 32;
+    for (long e = gtid; e < items; e += gstride) {
+      const long w = e >> 5;
+      const int i = (int)(w / segs) * 32 + (int)(e & 31), k0 = (int)(w % segs) * 32;
+      if (i >= rows) continue;
+      float m = 0.f;
+      if (k0 + 32 <= K) {
+#pragma unroll
+        for (int u0 = 0; u0 < 32; u0 += 8) {
+          float x[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) x[u] = fetch(i, k0 + u0 + u).x;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) m = fmaxf(m, fabsf(x[u]));
+        }
+      } else {
+        for (int k = k0; k < K; ++k) m = fmaxf(m, fabsf(fetch(i, k).x));
+      }
+      atomicMax(out + i, __float_as_int(m));
     }
   }
 }
 
 // slices of op(X) (rows x K) into the canonical layout: blocks of `br` rows x
 // 16 K, one block per slice, kGS blocks of br*32 bytes per (row block, K step);
-// padding rows and K are zero
+// padding rows and K are zero.  A thread slices 8 consecutive K of one row
+// (a K group); the warp's stores fill whole 128-byte core matrices: 8 rows x
+// 4 K groups per warp when rows are contiguous in memory, else 32 consecutive
+// rows at one K group.
 template <class F>
 __device__ void tc_slice(F fetch, int rows, int K, int br, bool rowmajor, const int *exps,
                          uint8_t *dst, long gtid, long gstride) {
-  const int nrb = (rows + br - 1) / br, nks = (K + 15) / 16;
-  const long items = (long)nrb * br * nks * 2;  // (row, 8-element K group)
-  const int bb = br * 32;                        // bytes of one slice block
+  const int nrb = (rows + br - 1) / br, nks = (K + 15) / 16, ng = nks * 2;
+  const long nrows = (long)nrb * br;  // a multiple of 8
+  const int ngq = (ng + 3) / 4;
+  const long items = rowmajor ? nrows / 8 * ngq * 32 : nrows * ng;
+  const int bb = br * 32;  // bytes of one slice block
   for (long e = gtid; e < items; e += gstride) {
     int i, g;
-    if (rowmajor) {  // consecutive threads: consecutive K groups of one row
-      i = (int)(e / (nks * 2));
-      g = (int)(e % (nks * 2));
-    } else {  // consecutive threads: consecutive rows at one K group
-      g = (int)(e / ((long)nrb * br));
-      i = (int)(e % ((long)nrb * br));
+    if (rowmajor) {
+      const int lane = (int)(e & 31);
+      const long w = e >> 5;
+      i = (int)(w / ngq) * 8 + (lane & 7);
+      g = (int)(w % ngq) * 4 + (lane >> 3);
+      if (g >= ng) continue;
+    } else {
+      g = (int)(e / nrows);
+      i = (int)(e % nrows);
     }
     const int k0 = g * 8;
     float sc = 0.f;
     if (i < rows) sc = pow2f(8 - slice_exp(__int_as_float(exps[i])));
+    float2 x[8];
+    if (i < rows && k0 + 8 <= K) {  // the eight loads issued before the first use
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = fetch(i, k0 + u);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = (i < rows && k0 + u < K) ? fetch(i, k0 + u) : make_float2(0.f, 0.f);
+    }
     uint32_t wd[kGS][4];
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
       float r[2][kGS];
-#pragma unroll
-      for (int v = 0; v < 2; ++v) {
-        const int k = k0 + u + v;
-        const float2 x = (i < rows && k < K) ? fetch(i, k) : make_float2(0.f, 0.f);
-        slice5(x, sc, r[v]);
-      }
+      slice5(x[u], sc, r[0]);
+      slice5(x[u + 1], sc, r[1]);
 #pragma unroll
       for (int t = 0; t < kGS; ++t) wd[t][u >> 1] = pack_bf16(r[0][t], r[1][t]);
     }
