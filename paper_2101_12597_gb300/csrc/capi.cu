@@ -461,7 +461,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->d_vent = dalloc<float4>(h, std::max<size_t>(vg_mu.size(), 1));
     h->d_vt = dalloc<float2>(h, (size_t)T * 128);
     CUDA_TRY(launch_operand_build(h, s));
-    h->d_Osl = dalloc<uint2>(h, (long)M * (h->N + (h->N & 1)));  // rows padded to even length
+    h->d_Osl = dalloc<uint2>(h, osl_elems(M, h->N));  // [chunk][M][osl_width(N)]
     const long ch = tc_max_list();  // orbitals per chunk of the density pass
     const long nsc = (h->N + ch - 1) / ch * ch;  // whole chunks, zero beyond N
     h->d_oscale = dalloc<float>(h, nsc);

@@ -112,6 +112,19 @@ struct DenseArgs {
   double ck[kTaylor + 1], sk[kTaylor + 1];
 };
 
+// Orbitals per chunk row of the O slices: all of them (N rounded up to even)
+// up to 128, else 128.  The slices are stored chunk by chunk, [chunk][M][ocw],
+// so that the rows of consecutive functions of one chunk are consecutive in
+// memory (the density pass gathers a run of them with one bulk copy).
+__host__ __device__ inline int osl_width(int N) {
+  const int np = N + (N & 1);
+  return np <= 128 ? np : 128;
+}
+__host__ __device__ inline long osl_elems(int M, int N) {
+  const int np = N + (N & 1), w = osl_width(N);
+  return (long)((np + w - 1) / w) * w * M;
+}
+
 // Arguments of the tensor-core grid passes for one system (mixed path):
 // 4 x 4 x 8 tiles, their lists and the resident operand slices.
 struct TcArgs {
@@ -135,9 +148,11 @@ struct TcArgs {
   uint8_t *xv;                  // V X^T slices, 1 KB per padded union entry and tile
   float4 *vent;                 // per padded union entry: (mu bits, 2^(e_a - 8), bound, 0)
   signed char *rowexp;          // [G] density row exponents e_p
-  const uint2 *Osl;             // [M][NoccP] BF16 slices of column-scaled O: x = K0 | K1 << 16, y = K2
+  const uint2 *Osl;             // BF16 slices of column-scaled O (x = K0 | K1 << 16, y = K2) in
+                                // chunks of ocw orbitals: [chunk][M][ocw] (see osl_width)
   const float *oscale;          // [chunks * 128] 2^g_m, zero beyond N
-  int Nocc, NoccP;              // occupied orbitals; O-slice row length (even)
+  int Nocc, NoccP;              // occupied orbitals; N rounded up to even
+  int ocw;                      // orbitals per O-slice chunk row
   double *rho;                  // [G]
   float2 *rhof;                 // [G] rho as float pairs
   const double *v;              // [G]
@@ -205,8 +220,9 @@ struct DfLaunch {
 // Column slices of one system's occupied orbitals (mixed path).
 struct OsArgs {
   const float2 *O;  // [M][N] float pairs from the dense chain
-  int M, N, NP;     // NP = N rounded up to even: the O-slice row length
-  uint2 *Osl;       // [M][NP]
+  int M, N, NP;     // NP = N rounded up to even
+  int ocw;          // orbitals per O-slice chunk row (osl_width)
+  uint2 *Osl;       // [chunk][M][ocw]
   float *oscale;    // [whole chunks of 128] 2^g_m
   double *dO;       // [M][N] O - Oq
 };

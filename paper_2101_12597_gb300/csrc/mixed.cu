@@ -446,9 +446,10 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
     while (ok && js.get(J)) {
       if (!B.active[J.a.x]) continue;
       const TcArgs &A = B.sys[J.a.x];
-      const int mc = J.a.z, nmc = J.a.w;
+      const int mc = J.a.z;
       const int k0 = J.b.x, nk = J.b.y, nu = J.b.z;
-      const int m0 = mc * kNmax, nme = min(kNmax, A.NoccP - m0);  // even
+      const int ocw = A.ocw;  // staged row length (even); the chunk's rows, ocw apart
+      const uint2 *osl = A.Osl + (size_t)mc * A.g.M * ocw;
       // functions of the tile: lane l holds entries l, l + 32, l + 64, l + 96
       int mu4[4];
 #pragma unroll
@@ -464,22 +465,23 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
         const int nrow = max(0, min(kKs, nu - kk * kKs));
         uint8_t *st = dsm + s * kRhoStage;
         if (lane == 0) {
-          mbar_expect_tx(&R.tma_full[s], kRhoA + nrow * nme * 8);
+          mbar_expect_tx(&R.tma_full[s], kRhoA + nrow * ocw * 8);
           bulk_g2s_stream(st, A.xr + (size_t)(k0 + kk) * kRhoA, kRhoA, &R.tma_full[s]);
         }
         __syncwarp();
         const int a = kk * kKs + (lane & 15), r = a >> 5;  // r is the same for the warp
         const int mv = r == 0 ? mu4[0] : r == 1 ? mu4[1] : r == 2 ? mu4[2] : mu4[3];
         const int mu = __shfl_sync(0xffffffffu, mv, a & 31);
-        // row c of the staging area (rows nme * 8 bytes apart) <- O-slice row mu_c
+        // row c of the staging area (rows ocw * 8 bytes apart) <- O-slice row mu_c
+        // of the chunk; a run of consecutive functions is one copy
         const int mup = __shfl_up_sync(0xffffffffu, mu, 1);
-        const bool cont = nmc == 1 && lane > 0 && lane < nrow && mu == mup + 1;
+        const bool cont = lane > 0 && lane < nrow && mu == mup + 1;
         const unsigned cb = __ballot_sync(0xffffffffu, cont);
         if (lane < nrow && !cont) {  // a run starts here: rows lane .. lane + len - 1
           const unsigned after = ~(cb >> (lane + 1));
           const int len = __ffs(after);  // 1 + the run's continued rows
-          bulk_g2s(st + kRhoA + kRhoB + lane * nme * 8, A.Osl + (size_t)mu * A.NoccP + m0,
-                   len * nme * 8, &R.tma_full[s]);
+          bulk_g2s(st + kRhoA + kRhoB + lane * ocw * 8, osl + (size_t)mu * ocw, len * ocw * 8,
+                   &R.tma_full[s]);
         }
       }
     }
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
       const TcArgs &A = B.sys[J.a.x];
       const int mc = J.a.z, nk = J.b.y, nu = J.b.z;
       const int nm = min(kNmax, A.Nocc - mc * kNmax);
-      const int nme = min(kNmax, A.NoccP - mc * kNmax);  // staged row length (even)
+      const int ocw = A.ocw;  // staged row length (even)
       const int nmpad = nm <= 32 ? 32 : ((nm + 31) / 32) * 32;
       for (int kk = 0; kk < nk; ++kk, ++fill) {
         const int s = fill % kRhoStages, use = fill / kRhoStages;
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
           for (int u = 0; u < 8; ++u) {
             const int c = h * 8 + u;
             uint2 o = make_uint2(0u, 0u);
-            if (c < nrow && m < nm) o = *(const uint2 *)(G + (c * nme + m) * 8);
+            if (c < nrow && m < nm) o = *(const uint2 *)(G + (c * ocw + m) * 8);
             w01[u] = o.x;
             w2[u] = o.y;
           }
@@ -1026,7 +1028,7 @@ __global__ void __launch_bounds__(256) oslice_kernel(const OsArgs *av, const int
     const double r2 = rint(t2);
     const double q = ldexp(r0 + (r1 + r2 * (1.0 / 256.0)) * (1.0 / 256.0), g - 8);
     a.dO[(long)r * N + m] = o - q;
-    a.Osl[(long)r * a.NP + m] = make_uint2(
+    a.Osl[((long)(m / a.ocw) * M + r) * a.ocw + m % a.ocw] = make_uint2(
         (uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)(r1 * (1.0 / 256.0))) << 16),
         (uint32_t)bf16_bits((float)(r2 * (1.0 / 65536.0))));
   }
@@ -1058,6 +1060,7 @@ TcArgs tc_args(etdm_handle *h) {
   a.oscale = h->d_oscale;
   a.Nocc = h->N;
   a.NoccP = h->N + (h->N & 1);
+  a.ocw = osl_width(h->N);
   a.rho = h->d_rho;
   a.rhof = h->d_rhof;
   a.v = h->d_vtot;
@@ -1109,7 +1112,7 @@ int tc_v_slices() { return kVSlX; }
 OsArgs os_args(etdm_handle *h) {
   OsArgs a{};
   a.O = reinterpret_cast<const float2 *>(h->d_O);
-  a.M = h->M; a.N = h->N; a.NP = h->N + (h->N & 1);
+  a.M = h->M; a.N = h->N; a.NP = h->N + (h->N & 1); a.ocw = osl_width(h->N);
   a.Osl = h->d_Osl; a.oscale = h->d_oscale; a.dO = h->d_dO;
   return a;
 }
