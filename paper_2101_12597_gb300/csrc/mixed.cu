@@ -351,19 +351,19 @@ __global__ void __launch_bounds__(256) xv_build_kernel(TcArgs A) {
 }
 
 // ---- density ---------------------------------------------------------------
-// Warp roles: 0-7 read the accumulators (lane quarter w % 4, column half w / 4),
-// 8-11 lay out the O-slice operand of each K step, 12 streams the X slices and
-// gathers the O-slice rows of the K step's 16 functions (one bulk copy per run
-// of consecutive function indices when all orbitals fit one chunk: the copy
-// engine's cost is per request), 13 issues the MMAs.  A job is (tile, chunk of
-// <= 128 occupied orbitals).
+// Warp roles: 0-15 read the accumulators (lane quarter w % 4, column quarter
+// w / 4), 16-19 lay out the O-slice operand of each K step, 20 streams the X
+// slices and gathers the O-slice rows of the K step's 16 functions (one bulk
+// copy per run of consecutive functions: the O slices are stored chunk by
+// chunk, and the copy engine takes about one request per 90 cycles per SM),
+// 21 issues the MMAs.  A job is (tile, chunk of <= 128 occupied orbitals).
 constexpr int kRhoStages = 5;
 constexpr int kRhoA = 4 * kSlot;        // X slices I0..I3 of a K step (16 KB, as stored)
 constexpr int kRhoB = 3 * kSlot;        // O slices K0..K2 of a K step (12 KB)
 constexpr int kRhoRow = kNmax * 8;      // room for one gathered O-slice row (<= 128 orbitals)
 constexpr int kRhoG = kKs * kRhoRow;    // the K step's 16 rows (16 KB)
 constexpr int kRhoStage = kRhoA + kRhoB + kRhoG;
-constexpr int kRhoEpiW = 8, kRhoBldW = 4;
+constexpr int kRhoEpiW = 16, kRhoBldW = 4;
 constexpr int kRhoParts = kRhoEpiW / 4;  // column parts per lane quarter
 constexpr int kRhoEpi = kRhoEpiW * 32, kRhoBld = kRhoBldW * 32;
 constexpr int kRhoThreads = kRhoEpi + kRhoBld + 64;
@@ -559,28 +559,43 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
         uint8_t *Bs = dsm + s * kRhoStage + kRhoA;
         const uint8_t *G = Bs + kRhoB;
         const int nrow = max(0, min(kKs, nu - kk * kKs));
-        for (int q = bt; q < nmpad * 2; q += kRhoBld) {  // items (orbital, 8 functions)
-          const int m = q % nmpad, h = q / nmpad;
-          uint32_t w01[8], w2[8];
+        // a thread per orbital m: its 16 gathered entries (all loads issued
+        // before the first use), laid out as the two 8-function halves of the
+        // K step in each of the three slices
+        const bool full = nrow == kKs;
+        for (int m = bt; m < nmpad; m += kRhoBld) {
+          uint32_t w01[kKs], w2[kKs];
+          if (full && m < nm) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int c = h * 8 + u;
-            uint2 o = make_uint2(0u, 0u);
-            if (c < nrow && m < nm) o = *(const uint2 *)(G + (c * ocw + m) * 8);
-            w01[u] = o.x;
-            w2[u] = o.y;
+            for (int c = 0; c < kKs; ++c) {
+              const uint2 o = *(const uint2 *)(G + (c * ocw + m) * 8);
+              w01[c] = o.x;
+              w2[c] = o.y;
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < kKs; ++c) {
+              uint2 o = make_uint2(0u, 0u);
+              if (c < nrow && m < nm) o = *(const uint2 *)(G + (c * ocw + m) * 8);
+              w01[c] = o.x;
+              w2[c] = o.y;
+            }
           }
-          const int off = kstep_off(m, h * 8);
-          uint4 v0, v1, v2;
-          v0.x = __byte_perm(w01[0], w01[1], 0x5410); v0.y = __byte_perm(w01[2], w01[3], 0x5410);
-          v0.z = __byte_perm(w01[4], w01[5], 0x5410); v0.w = __byte_perm(w01[6], w01[7], 0x5410);
-          v1.x = __byte_perm(w01[0], w01[1], 0x7632); v1.y = __byte_perm(w01[2], w01[3], 0x7632);
-          v1.z = __byte_perm(w01[4], w01[5], 0x7632); v1.w = __byte_perm(w01[6], w01[7], 0x7632);
-          v2.x = __byte_perm(w2[0], w2[1], 0x5410); v2.y = __byte_perm(w2[2], w2[3], 0x5410);
-          v2.z = __byte_perm(w2[4], w2[5], 0x5410); v2.w = __byte_perm(w2[6], w2[7], 0x5410);
-          *(uint4 *)(Bs + off) = v0;
-          *(uint4 *)(Bs + nmpad * 32 + off) = v1;
-          *(uint4 *)(Bs + 2 * nmpad * 32 + off) = v2;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t *x = w01 + 8 * h, *y = w2 + 8 * h;
+            const int off = kstep_off(m, h * 8);
+            uint4 v0, v1, v2;
+            v0.x = __byte_perm(x[0], x[1], 0x5410); v0.y = __byte_perm(x[2], x[3], 0x5410);
+            v0.z = __byte_perm(x[4], x[5], 0x5410); v0.w = __byte_perm(x[6], x[7], 0x5410);
+            v1.x = __byte_perm(x[0], x[1], 0x7632); v1.y = __byte_perm(x[2], x[3], 0x7632);
+            v1.z = __byte_perm(x[4], x[5], 0x7632); v1.w = __byte_perm(x[6], x[7], 0x7632);
+            v2.x = __byte_perm(y[0], y[1], 0x5410); v2.y = __byte_perm(y[2], y[3], 0x5410);
+            v2.z = __byte_perm(y[4], y[5], 0x5410); v2.w = __byte_perm(y[6], y[7], 0x5410);
+            *(uint4 *)(Bs + off) = v0;
+            *(uint4 *)(Bs + nmpad * 32 + off) = v1;
+            *(uint4 *)(Bs + 2 * nmpad * 32 + off) = v2;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&R.bld_full[s]);
@@ -611,21 +626,16 @@ __global__ void __launch_bounds__(kRhoThreads, 1) rho_tc_kernel(TcBatch B) {
       ++jp;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // this warp's column part in chunks of 8, the next chunk's loads in
-      // flight while the current one is summed; the column scales 2^g_m come
-      // from the (zero-padded) global array of the job's system
+      // this warp's column part (a quarter of the chunk) in pieces of 8; the
+      // column scales 2^g_m come from the (zero-padded) global array of the
+      // job's system
       const int cb = part * (nmpad / kRhoParts), ce = cb + nmpad / kRhoParts;
       const float *f = A.oscale + mc * kNmax;
-      uint32_t ra[32], rb[32];
-      tmem_ld_issue(tmem + lanebits + cb, ra, nmpad);
-      for (int c0 = cb; c0 < ce; c0 += 16) {
-        tmem_ld_wait(ra);
-        if (c0 + 8 < ce) tmem_ld_issue(tmem + lanebits + c0 + 8, rb, nmpad);
-        rsum = rho_sum8(ra, f + c0, rsum);
-        if (c0 + 8 >= ce) break;
-        tmem_ld_wait(rb);
-        if (c0 + 16 < ce) tmem_ld_issue(tmem + lanebits + c0 + 16, ra, nmpad);
-        rsum = rho_sum8(rb, f + c0 + 8, rsum);
+      for (int c0 = cb; c0 < ce; c0 += 8) {
+        uint32_t r[32];
+        tmem_ld_issue(tmem + lanebits + c0, r, nmpad);
+        tmem_ld_wait(r);
+        rsum = rho_sum8(r, f + c0, rsum);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&R.acc_empty);
