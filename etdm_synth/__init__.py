@@ -232,15 +232,27 @@ def config_crystal64():
     return crystal()
 
 
-def tiny_crystal(kT_ev=0.5, kmesh=2, grid=(24, 12, 12), seed=6):
+def tiny_crystal(kT_ev=0.5, kmesh=2, grid=(24, 12, 12), seed=6, rcut_ang=None):
     """Two atoms per cell (a 2x1x1 supercell of a 2.2 A simple-cubic lattice),
     2 Gaussians each (exponents 0.4 and 1.2, M = 4), Z = 1, with a k-mesh and a
     temperature at which the occupations are fractional; the 1e-16 truncation
     rule and an isotropic grid keep the analytic S and T within quadrature
-    error of the grid.  Brute-force sized."""
+    error of the grid.  Brute-force sized.  rcut_ang (a hard radius, below
+    twice the shortest cell edge) makes it a system the GPU path accepts."""
     return crystal(cells=(2, 1, 1), spacing_ang=2.2, jitter_ang=0.1, Z=1.0,
-                   exps=(0.4, 1.2), grid=grid, rcut_ang=None, kmesh=kmesh,
+                   exps=(0.4, 1.2), grid=grid, rcut_ang=rcut_ang, kmesh=kmesh,
                    kT_ev=kT_ev, a_sigma=0.05, seed=seed)
+
+
+def small_crystal(seed=8):
+    """Eight atoms (a 2x2x2 simple-cubic cell of 2.6 A, 0.1 A jitter), 3
+    Gaussians each (M = 24), Z = 1.5 (12 electrons, the Fermi level inside a
+    band: occupations from 1 to 0.02 of full), 2x2x2 k-points, kT = 0.5 eV,
+    r_c = 3 A, a ragged 26 x 24 x 22 grid (tiles of 4^3 with partial tiles on
+    every axis): the full-A path at a size that spans several tiles."""
+    return crystal(cells=(2, 2, 2), spacing_ang=2.6, jitter_ang=0.1, n_exp=3, Z=1.5,
+                   grid=(26, 24, 22), rcut_ang=3.0, kmesh=2, kT_ev=0.5, a_sigma=0.05,
+                   seed=seed)
 
 
 def molecule_batch(n_mol=148, atoms=(2, 20), p_heavy=1.0 / 3.0, cube_ang=4.8,

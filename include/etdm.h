@@ -56,8 +56,22 @@ enum {
                           energy, energy total, gradient and L-BFGS in FP64 */
 };
 
-/* One periodic system (Eq. 3-5 at the Gamma point).  All host pointers,
- * read during etdm_init_basis only. */
+enum {
+  ETDM_PARAM_OCCVIRT = 0, /* A = [[0, A_ov], [-A_ov^T, 0]] (Eq. 36) at the Gamma
+                             point, N = n_electrons / 2 doubly occupied orbitals;
+                             variables: A_ov, N x V row-major */
+  ETDM_PARAM_FULL = 1     /* the full skew-Hermitian A(k) of every k-point
+                             (Eq. 8, 22-24), occupations fixed at the reference
+                             (Fermi-Dirac at kT, or integer at kT = 0); variables
+                             per k-point: Re a_ij (i < j), then Im a_ij (i <= j),
+                             row-major over the upper triangle, M^2 per k-point,
+                             the k-points one after another */
+};
+
+/* One periodic system (Eq. 3-5).  All host pointers, read during
+ * etdm_init_basis only.  n_k = 0 is the Gamma point alone; n_k >= 1 selects
+ * the full-A path over the given k-points (Bloch functions of Eq. 5 without
+ * the 1/sqrt(N) factor, so that S(k) is the overlap over one cell). */
 typedef struct {
   int32_t n_atoms;
   const double *pos;      /* [n_atoms*3] positions, bohr, inside [0, box) */
@@ -70,6 +84,11 @@ typedef struct {
   int32_t grid[3];        /* grid points per axis; prime factors <= 13 */
   double ion_sigma;       /* Gaussian ion-charge width, bohr */
   int32_t n_electrons;    /* even, 2 <= n_electrons <= 2M; N = n_electrons/2 */
+  int32_t n_k;            /* k-points (0: Gamma point, occupied-virtual A) */
+  const double *k_frac;   /* [n_k*3] k-points in fractional reciprocal coordinates */
+  const double *k_w;      /* [n_k] positive weights summing to 1 */
+  double kT;              /* Fermi-Dirac temperature of the reference occupations,
+                             Hartree; 0: integer occupation (n_k <= 1 only) */
 } etdm_system;
 
 typedef struct {
@@ -88,6 +107,10 @@ typedef struct {
                            cores (exact BF16 slices, about 2^-39 relative per
                            product), 1 every product, -1 none (float pairs on
                            the FP32 pipes) */
+  int32_t param;        /* ETDM_PARAM_OCCVIRT (default; needs n_k = 0) or
+                           ETDM_PARAM_FULL (needs ETDM_PREC_FP64; n_k = 0 then
+                           means the Gamma point with weight 1); n_k >= 1
+                           implies ETDM_PARAM_FULL */
 } etdm_options;
 
 /* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1,
@@ -98,10 +121,18 @@ void etdm_default_options(etdm_options *opt);
  * tables, truncation lists per grid tile, analytic S and T, v_ext, the
  * reference C0 = S^(-1/2) (columns ordered by ascending diagonal of
  * C0^T (T + V_ext) C0, the first N occupied) and the orbital energies of
- * Eq. 33 (diagonal of C0^T H C0 at A = 0).  On success *out owns device
+ * Eq. 33 (diagonal of C0^T H C0 at A = 0).  The full-A path (n_k >= 1 or
+ * ETDM_PARAM_FULL) instead builds S(k), T(k), h_core(k) = T(k) + V_ext(k),
+ * takes C0(k) as the generalized eigenvectors of h_core(k) with S(k)
+ * (ascending eigenvalues; FP64 Householder + QL eigensolver on the device),
+ * sets the occupations f_m(k) = 2 w_k / (1 + exp((e_m(k) - mu) / kT)) with mu
+ * by bisection to sum f = n_electrons (or f = 2 on the N lowest at kT = 0) and
+ * keeps them fixed, and takes the Eq. 33 orbital energies as the diagonal of
+ * C0(k)^dagger H(k) C0(k) at A = 0.  On success *out owns device
  * memory until etdm_free().  Errors: INVALID_ARG (sizes, radii, grid
- * factors, list lengths over the tile limit), OOM, CUDA, NUMERIC (S not
- * positive definite), NOT_CONVERGED (S^(-1/2) iteration). */
+ * factors, list lengths over the tile limit, k-point arrays, M > 1024 or mixed
+ * precision on the full-A path), OOM, CUDA, NUMERIC (S not positive
+ * definite), NOT_CONVERGED (S^(-1/2) iteration, or the eigensolver). */
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt,
                     etdm_handle **out);
 
@@ -241,8 +272,17 @@ enum {
   ETDM_ARR_STATUS = 21,       /* [4] i32 device status words: error code, doublings,
                                  then where a bounded wait of the tensor-core
                                  products gave up and at which count (0: none) */
-  ETDM_NARR = 22              /* number of array ids */
+  ETDM_ARR_OCC = 22,          /* full A: [n_k*M] f64 occupations f_m(k) (k-point
+                                 weight and spin included) */
+  ETDM_ARR_EPS_REF = 23,      /* full A: [n_k*M] f64 eigenvalues of h_core(k) with
+                                 S(k) (ascending; the reference's) */
+  ETDM_ARR_OMEGA = 24,        /* full A: [n_k*M] f64 eigenvalues of iA(k) at the
+                                 last evaluation (Eq. 35) */
+  ETDM_NARR = 25              /* number of array ids */
 };
+/* On the full-A path S, T, C0, H and D are complex128 (re, im interleaved)
+ * [n_k][M][M] row-major per k-point, EPS is [n_k*M]; ORDER, UOCC and
+ * DOUBLINGS do not exist there (etdm_array_bytes returns -1). */
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which);
 int etdm_get_array(etdm_handle *h, int32_t which, void *host_dst,
                    int64_t n_bytes);
@@ -314,6 +354,23 @@ int etdm_lbfgs_direction_noalloc_status(void *stream);
  * a bounded wait that gave up returns ETDM_ERR_TIMEOUT.  1 <= m, n, k <= 65536. */
 int etdm_pair_gemm(const double *A_dev, const double *B_dev, double *C_dev, int32_t m,
                    int32_t n, int32_t k, int32_t ta, int32_t tb, void *stream);
+
+/* Replace the reference orbitals C0 of system `sys` (0 for a single-system
+ * handle) that O = C0 exp(A) rotates (Eq. 6-7), for example with C0 exp(A) of
+ * an accepted point (the reference update of Sec. 3.5).  Then re-evaluates
+ * at A = 0 for the Eq. 33 orbital energies (diagonal of C0^dagger H C0) and
+ * erases the L-BFGS memory (beta back to beta0).
+ *   C0_host   occupied-virtual path: [M*M] f64 row-major, columns are the
+ *             orbitals, the first N occupied; full-A path: [n_k*M*M]
+ *             complex128 (re, im interleaved), row-major per k-point.
+ *   occ_host  full-A path only: [n_k*M] occupations f_m(k) (weight and spin
+ *             included, finite, >= 0, summing to n_electrons), or NULL to keep
+ *             the current ones; must be NULL on the occupied-virtual path.
+ * The columns must be orthonormal in the S (S(k)) metric; that is not
+ * checked.  Host pointers, read during the call; synchronizes the device.
+ * Errors: INVALID_ARG, CUDA, NUMERIC. */
+int etdm_set_reference(etdm_handle *h, int32_t sys, const double *C0_host,
+                       const double *occ_host);
 
 /* Release all device memory of h (NULL is a no-op). */
 void etdm_free(etdm_handle *h);

@@ -14,8 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libetdm.so")
 SOURCES = ["capi.cu", "dense.cu", "grid.cu", "potential.cu", "mixed.cu", "fftdf.cu", "noalloc.cu",
-           "plan.cu", "batch.cu"]
-HEADERS = ["internal.h", "device.cuh", "host.h", "pair.cuh", "linesearch.h", "tc.cuh"]
+           "plan.cu", "batch.cu", "kpoint.cu", "kpath.cu"]
+HEADERS = ["internal.h", "device.cuh", "host.h", "pair.cuh", "linesearch.h", "tc.cuh", "kpoint.h"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
          "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC"]

@@ -12,6 +12,7 @@
 
 #include "host.h"
 #include "internal.h"
+#include "kpoint.h"
 #include "linesearch.h"
 
 using namespace etdm;
@@ -82,6 +83,10 @@ struct StageTimer {
 
 // One energy (+ gradient) evaluation, all on `s`.
 void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s) {
+  if (h->kpath) {
+    evaluate_k(h, a, E, g, s);
+    return;
+  }
   {
     StageTimer t(h, s, ETDM_STAGE_DENSE_FWD);
     CUDA_TRY(launch_dense_forward(h, a, s));
@@ -176,6 +181,29 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
       bad("bf_rcut must be in (0, 2 * min(box))");
   }
   if (!(sys->ion_sigma > 0.0)) bad("ion_sigma must be positive");
+  const bool full = sys->n_k >= 1 || (opt && opt->param == ETDM_PARAM_FULL);
+  if (sys->n_k < 0) bad("n_k must be >= 0");
+  if (sys->n_k >= 1) {
+    if (!sys->k_frac || !sys->k_w) bad("n_k >= 1 needs k_frac and k_w");
+    double wsum = 0.0;
+    for (int k = 0; k < sys->n_k; ++k) {
+      if (!(sys->k_w[k] > 0.0)) bad("k-point weights must be positive");
+      wsum += sys->k_w[k];
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(sys->k_frac[3 * k + a])) bad("k-points must be finite");
+    }
+    if (fabs(wsum - 1.0) > 1e-12) bad("k-point weights must sum to 1");
+  }
+  if (full) {
+    if (!(sys->kT >= 0.0) || !std::isfinite(sys->kT)) bad("kT must be finite and >= 0");
+    if (sys->kT == 0.0 && sys->n_k > 1) bad("kT = 0 (integer occupation) needs n_k <= 1");
+    if (sys->n_basis > 1024) bad("the full-A path takes n_basis <= 1024");
+    if (opt && opt->precision != ETDM_PREC_FP64) bad("the full-A path runs in FP64 only");
+    if (opt && opt->param != ETDM_PARAM_FULL && opt->param != ETDM_PARAM_OCCVIRT)
+      bad("unknown param");
+  } else if (opt && opt->param != ETDM_PARAM_OCCVIRT) {
+    bad("unknown param");
+  }
   if (opt) {
     if (opt->precision != ETDM_PREC_FP64 && opt->precision != ETDM_PREC_MIXED)
       bad("unknown precision");
@@ -297,6 +325,39 @@ void build_lists(etdm_handle *h, const GridGeom &g, int n_tiles, int **d_ptr, in
                    "): use a finer grid or shorter truncation radii"};
 }
 
+}  // namespace
+
+// L-BFGS memory, line-search buffers and reduction scratch for h->nvar
+// variables (both parametrizations).
+void etdm::alloc_opt_buffers(etdm_handle *h) {
+  int bpl = 0;
+  if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
+    throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};
+  const long nvar = h->nvar;
+  // L-BFGS: one block for small n (the grid barrier is then a block barrier);
+  // else every SM, so the FP64 work per SM stays small (FP64 is the scarce
+  // pipe), at most two elements per thread up to water32
+  h->lb_blocks = nvar <= 512 ? 1
+                             : (int)std::min<long>((long)h->num_sms * std::min(bpl, 2),
+                                                   std::max<long>(h->num_sms, (nvar + 511) / 512));
+  h->d_red = dalloc<double>(h, 4 * std::max(h->coop_blocks, h->lb_blocks) + 8);
+  h->d_s = dalloc<double>(h, (long)h->lbfgs_m * nvar);
+  h->d_y = dalloc<double>(h, (long)h->lbfgs_m * nvar);
+  h->d_aprev = dalloc<double>(h, nvar);
+  h->d_gprev = dalloc<double>(h, nvar);
+  h->d_q = dalloc<double>(h, nvar);
+  h->d_lbstate = dalloc<double>(h, 4 + 2 * 16);
+  h->d_a = dalloc<double>(h, nvar);
+  h->d_g = dalloc<double>(h, nvar);
+  h->d_at = dalloc<double>(h, nvar);
+  h->d_gt = dalloc<double>(h, nvar);
+  h->d_p = dalloc<double>(h, nvar);
+  h->d_dot = dalloc<double>(h, 4);
+  CUDA_TRY(cudaMallocHost(&h->h_pinned, 16 * sizeof(double)));  // [0, 8) values, [8, 16) status words
+}
+
+namespace {
+
 void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) {
   validate(sys, opt);
   etdm_options o;
@@ -307,6 +368,18 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   h->lbfgs_m = o.lbfgs_m;
   h->gamma = o.gamma;
   h->beta0 = o.beta0;
+  h->kpath = sys->n_k >= 1 || o.param == ETDM_PARAM_FULL;
+  if (h->kpath) {
+    h->nk = sys->n_k >= 1 ? sys->n_k : 1;
+    h->h_kfrac.assign(3 * h->nk, 0.0);
+    h->h_kw.assign(h->nk, 1.0);
+    if (sys->n_k >= 1) {
+      h->h_kfrac.assign(sys->k_frac, sys->k_frac + 3 * h->nk);
+      h->h_kw.assign(sys->k_w, sys->k_w + h->nk);
+    }
+    h->kT = sys->kT;
+    h->n_elec = sys->n_electrons;
+  }
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
   if (o.device < 0 || o.device >= ndev) throw Fail{ETDM_ERR_INVALID_ARG, "no such CUDA device"};
@@ -505,6 +578,15 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   CUDA_TRY(fft3d(h, h->d_fft, +1, s));
   CUDA_TRY(launch_real_part(h, h->d_fft, h->d_vext, s));
   if (h->precision == ETDM_PREC_MIXED) CUDA_TRY(launch_df_setup(h, s));  // twiddles, v_ext, Poisson kernel
+  if (h->kpath) {  // full A over k-points: its own matrices and reference
+    h->d_E = dalloc<double>(h, 2);
+    h->d_eterms = dalloc<double>(h, 4);
+    h->d_flags = dalloc<int>(h, FLAG_NFLAGS);
+    h->d_bar = dalloc<unsigned>(h, 4);
+    h->coop_blocks = 1;
+    init_kpoints(h, sys);
+    return;
+  }
 
   // dense workspaces
   const int N = h->N, V = h->V;
@@ -563,32 +645,8 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
       h->d_tc_cexp = dalloc<int>(h, (size_t)M + 128);
     }
   }
-  int bpl = 0;
-  if (occupancy_lbfgs(&bpl) != 0 || bpl < 1)
-    throw Fail{ETDM_ERR_CUDA, "cannot size the cooperative L-BFGS kernel"};
-  const long nvar = (long)N * V;
-  // L-BFGS: one block for small n (the grid barrier is then a block barrier);
-  // else every SM, so the FP64 work per SM stays small (FP64 is the scarce
-  // pipe), at most two elements per thread up to water32
-  h->lb_blocks = nvar <= 512 ? 1
-                             : (int)std::min<long>((long)h->num_sms * std::min(bpl, 2),
-                                                   std::max<long>(h->num_sms, (nvar + 511) / 512));
-  h->d_red = dalloc<double>(h, 4 * std::max(h->coop_blocks, h->lb_blocks) + 8);
-
-  // L-BFGS memory and line-search buffers
-  h->d_s = dalloc<double>(h, (long)h->lbfgs_m * nvar);
-  h->d_y = dalloc<double>(h, (long)h->lbfgs_m * nvar);
-  h->d_aprev = dalloc<double>(h, nvar);
-  h->d_gprev = dalloc<double>(h, nvar);
-  h->d_q = dalloc<double>(h, nvar);
-  h->d_lbstate = dalloc<double>(h, 4 + 2 * 16);
-  h->d_a = dalloc<double>(h, nvar);
-  h->d_g = dalloc<double>(h, nvar);
-  h->d_at = dalloc<double>(h, nvar);
-  h->d_gt = dalloc<double>(h, nvar);
-  h->d_p = dalloc<double>(h, nvar);
-  h->d_dot = dalloc<double>(h, 4);
-  CUDA_TRY(cudaMallocHost(&h->h_pinned, 16 * sizeof(double)));  // [0, 8) values, [8, 16) status words
+  h->nvar = (long)N * V;
+  etdm::alloc_opt_buffers(h);
 
   // reference orbitals: Loewdin S^(-1/2), columns by ascending diag of C0^T h_core C0
   inverse_sqrt(h, s);
@@ -614,7 +672,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   if (h->precision == ETDM_PREC_MIXED) {  // the mixed path's dense chains run on float pairs
     h->d_C0p = dalloc<float2>(h, MM);
     h->d_Tp = dalloc<float2>(h, MM);
-    h->d_Af = dalloc<float2>(h, nvar);
+    h->d_Af = dalloc<float2>(h, h->nvar);
     CUDA_TRY(launch_to_pairs(h->d_C0, h->d_C0p, MM, s));
     CUDA_TRY(launch_to_pairs(h->d_T, h->d_Tp, MM, s));
   }
@@ -627,7 +685,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
   }
 
   // orbital energies of Eq. 33 at A = 0
-  CUDA_TRY(cudaMemsetAsync(h->d_a, 0, nvar * 8, s));
+  CUDA_TRY(cudaMemsetAsync(h->d_a, 0, h->nvar * 8, s));
   h->in_setup = true;
   evaluate(h, h->d_a, h->d_E, h->d_g, s);
   h->in_setup = false;
@@ -663,6 +721,7 @@ void etdm_default_options(etdm_options *opt) {
   opt->device = 0;
   opt->dense_blocks = 0;
   opt->dense_tc = 0;
+  opt->param = ETDM_PARAM_OCCVIRT;
 }
 
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {
@@ -705,7 +764,7 @@ int etdm_energy_grad_host(etdm_handle *h, const double *a_host, double *E_host,
       return ETDM_OK;
     }
     cudaStream_t s = 0;
-    const long nvar = (long)h->N * h->V;
+    const long nvar = h->nvar;
     CUDA_TRY(cudaMemcpyAsync(h->d_a, a_host, nvar * 8, cudaMemcpyHostToDevice, s));
     evaluate(h, h->d_a, h->d_E, g_host ? h->d_g : nullptr, s);
     CUDA_TRY(cudaMemcpyAsync(E_host, h->d_E, 8, cudaMemcpyDeviceToHost, s));
@@ -775,6 +834,64 @@ int etdm_lbfgs_reset(etdm_handle *h) {
   return ETDM_OK;
 }
 
+int etdm_set_reference(etdm_handle *h, int32_t sys, const double *C0_host, const double *occ_host) {
+  if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
+  if (!h->members.empty()) {
+    if (sys < 0 || sys >= (int32_t)h->members.size())
+      return set_err(h, ETDM_ERR_INVALID_ARG, "no such system");
+    const int rc = etdm_set_reference(h->members[sys], 0, C0_host, occ_host);
+    return rc == ETDM_OK ? rc : set_err(h, rc, h->members[sys]->err);
+  }
+  if (sys != 0) return set_err(h, ETDM_ERR_INVALID_ARG, "a single-system handle has system 0 only");
+  if (!C0_host) return set_err(h, ETDM_ERR_INVALID_ARG, "C0 is NULL");
+  if (occ_host && !h->kpath)
+    return set_err(h, ETDM_ERR_INVALID_ARG, "occupations are fixed (f = 2 / 0) on the occupied-virtual path");
+  try {
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    cudaStream_t s = 0;
+    const long MM = (long)h->M * h->M;
+    if (h->kpath) {
+      const long nf = (long)h->nk * h->M;
+      if (occ_host) {
+        double tot = 0.0;
+        for (long q = 0; q < nf; ++q) {
+          if (!std::isfinite(occ_host[q]) || occ_host[q] < 0.0)
+            throw Fail{ETDM_ERR_INVALID_ARG, "occupations must be finite and >= 0"};
+          tot += occ_host[q];
+        }
+        if (fabs(tot - h->n_elec) > 1e-9 * std::max(1.0, h->n_elec))
+          throw Fail{ETDM_ERR_INVALID_ARG, "occupations must sum to n_electrons"};
+        CUDA_TRY(cudaMemcpy(h->d_kf, occ_host, nf * 8, cudaMemcpyHostToDevice));
+      }
+      CUDA_TRY(cudaMemcpy(h->d_kC0, C0_host, (size_t)h->nk * MM * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemsetAsync(h->d_a, 0, h->nvar * 8, s));
+      evaluate_k(h, h->d_a, h->d_E, h->d_g, s);
+      check_flags(h, s);
+      CUDA_TRY(zgemm_sq(h->d_kH, 0, h->d_kC0, 0, h->d_kX1, h->M, h->nk, s));
+      CUDA_TRY(k_diag(h->d_kC0, h->d_kX1, h->d_eps, h->nk, h->M, s));
+      CUDA_TRY(k_precond_parts(h->d_eps, h->d_kf, h->d_kw, h->nk, h->M, h->gamma, h->d_kpden,
+                               h->d_kpw, s));
+    } else {
+      for (long q = 0; q < MM; ++q)
+        if (!std::isfinite(C0_host[q])) throw Fail{ETDM_ERR_INVALID_ARG, "C0 must be finite"};
+      CUDA_TRY(cudaMemcpy(h->d_C0, C0_host, MM * 8, cudaMemcpyHostToDevice));
+      if (h->d_C0p) CUDA_TRY(launch_to_pairs(h->d_C0, h->d_C0p, MM, s));
+      CUDA_TRY(cudaMemsetAsync(h->d_a, 0, h->nvar * 8, s));
+      h->in_setup = true;
+      evaluate(h, h->d_a, h->d_E, h->d_g, s);
+      h->in_setup = false;
+      check_flags(h, s);
+      CUDA_TRY(launch_diag_quad(h->d_C0, h->d_H, h->d_eps, h->M, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+  } catch (const Fail &f) {
+    h->in_setup = false;
+    return set_err(h, f.code, f.msg);
+  }
+  return etdm_lbfgs_reset(h);
+}
+
 int etdm_check(etdm_handle *h, void *stream) {
   if (!h) return set_err(nullptr, ETDM_ERR_STATE, "handle is NULL");
   try {
@@ -797,7 +914,7 @@ static int minimize_impl(etdm_handle *h, double *a_dev, int32_t n_steps, double 
   if (!a_dev || n_steps < 0) return set_err(h, ETDM_ERR_INVALID_ARG, "bad a_dev or n_steps");
   cudaStream_t s = (cudaStream_t)stream;
   const bool conv = tol >= 0.0;
-  const long nvar = (long)h->N * h->V;
+  const long nvar = h->nvar;
   double *hp = h->h_pinned;
   if (!h->members.empty()) {
     if (conv) return set_err(h, ETDM_ERR_INVALID_ARG, "the convergence test runs on one system");
@@ -904,6 +1021,8 @@ int etdm_minimize_converge(etdm_handle *h, double *a_dev, int32_t max_steps, dou
                            double *E_hist, double *alpha_hist, int32_t *trials_hist,
                            double *resid_hist, int32_t *steps_done, void *stream) {
   if (!(tol >= 0.0)) return set_err(h, ETDM_ERR_INVALID_ARG, "tol must be >= 0");
+  if (h && h->kpath)
+    return set_err(h, ETDM_ERR_INVALID_ARG, "the Eq. 45 residual is built for the occupied-virtual path");
   return minimize_impl(h, a_dev, max_steps, E_hist, alpha_hist, trials_hist, tol, resid_hist,
                        steps_done, stream);
 }
@@ -932,6 +1051,20 @@ int etdm_layout(const etdm_handle *h, int64_t *dims) {
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
   if (!h || !h->members.empty()) return -1;  // a batch: ask its systems (etdm_system_handle)
   const int64_t M = h->M, N = h->N;
+  if (h->kpath) {  // complex [n_k][M][M] matrices, [n_k][M] vectors
+    const int64_t KM = (int64_t)h->nk * M * M, KV = (int64_t)h->nk * M;
+    switch (which) {
+      case ETDM_ARR_S: case ETDM_ARR_T: case ETDM_ARR_C0: case ETDM_ARR_H: case ETDM_ARR_D:
+        return KM * 16;
+      case ETDM_ARR_EPS: case ETDM_ARR_OCC: case ETDM_ARR_EPS_REF: case ETDM_ARR_OMEGA:
+        return KV * 8;
+      case ETDM_ARR_ORDER: case ETDM_ARR_UOCC: case ETDM_ARR_DOUBLINGS:
+        return -1;
+      default: break;
+    }
+  } else if (which == ETDM_ARR_OCC || which == ETDM_ARR_EPS_REF || which == ETDM_ARR_OMEGA) {
+    return -1;
+  }
   switch (which) {
     case ETDM_ARR_S: case ETDM_ARR_T: case ETDM_ARR_C0: case ETDM_ARR_H: case ETDM_ARR_D:
       return M * M * 8;
@@ -963,6 +1096,24 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
     CUDA_TRY(cudaSetDevice(h->device));
     CUDA_TRY(cudaDeviceSynchronize());
     const void *src = nullptr;
+    if (h->kpath) {
+      switch (which) {
+        case ETDM_ARR_S: src = h->d_kS; break;
+        case ETDM_ARR_T: src = h->d_kT; break;
+        case ETDM_ARR_C0: src = h->d_kC0; break;
+        case ETDM_ARR_H: src = h->d_kH; break;
+        case ETDM_ARR_D: src = h->d_kD; break;
+        case ETDM_ARR_EPS: src = h->d_eps; break;
+        case ETDM_ARR_OCC: src = h->d_kf; break;
+        case ETDM_ARR_EPS_REF: src = h->d_keps0; break;
+        case ETDM_ARR_OMEGA: src = h->d_komega; break;
+        default: break;
+      }
+      if (src) {
+        CUDA_TRY(cudaMemcpy(dst, src, want, cudaMemcpyDeviceToHost));
+        return ETDM_OK;
+      }
+    }
     switch (which) {
       case ETDM_ARR_S: src = h->d_S; break;
       case ETDM_ARR_T: src = h->d_T; break;
@@ -1092,6 +1243,11 @@ int etdm_init_batch(const etdm_system *sys, int32_t n_sys, const etdm_options *o
   etdm_handle *h = new etdm_handle();
   try {
     if (opt) validate(sys, opt);
+    if (opt && opt->param != ETDM_PARAM_OCCVIRT)
+      throw Fail{ETDM_ERR_INVALID_ARG, "batches take occupied-virtual Gamma-point systems"};
+    for (int i = 0; sys && i < n_sys; ++i)
+      if (sys[i].n_k != 0)
+        throw Fail{ETDM_ERR_INVALID_ARG, "batches take Gamma-point systems (n_k = 0)"};
     init_batch(h, sys, n_sys, opt);
   } catch (const Fail &f) {
     release(h);
@@ -1112,7 +1268,7 @@ int etdm_system_layout(const etdm_handle *h, int32_t sys, int64_t *offset, int64
   if (h->members.empty()) {
     if (sys != 0) return ETDM_ERR_INVALID_ARG;
     *offset = 0;
-    *len = (int64_t)h->N * h->V;
+    *len = (int64_t)h->nvar;
     return ETDM_OK;
   }
   if (sys < 0 || sys >= (int32_t)h->members.size()) return ETDM_ERR_INVALID_ARG;

@@ -1246,6 +1246,14 @@ __device__ __forceinline__ double precond_elem(const double *eps, int N, int V, 
   return 1.0 / (2.0 * (1.0 - gamma) * fabs(d) + gamma * beta);
 }
 
+// P^(k) of variable e: the occupied-virtual form above, or (full A over
+// k-points) from the per-variable parts 2 (1 - gamma) |(e_i - e_j)(f_i - f_j)|
+// and w_k (Eq. 33 with the k-point weight on beta, Sec. 3.3).
+__device__ __forceinline__ double precond_of(const LbfgsArgs &a, long e, double beta) {
+  if (a.pden) return 1.0 / (a.pden[e] + a.gamma * beta * a.pw[e]);
+  return precond_elem(a.eps, a.N, a.V, e, a.gamma, beta);
+}
+
 // Dot product of the whole grid: every block gets the same value.  The block
 // partials alternate between two halves of red[] (2 * gridDim entries each,
 // room for two sums), so one barrier suffices: a block can only write a half
@@ -1308,7 +1316,7 @@ __device__ void lbfgs_two_loop(const LbfgsArgs &a, const Coop &cp) {
   }
   // r = H0 q
   for (long e = gtid; e < n; e += gstride)
-    a.q[e] *= precond_elem(a.eps, a.N, a.V, e, a.gamma, beta);
+    a.q[e] *= precond_of(a, e, beta);
   // second loop: oldest to newest
   for (int c = count - 1; c >= 0; --c) {
     int slot = (head - 1 - c + 2 * m) % m;
@@ -1452,7 +1460,7 @@ __global__ void __launch_bounds__(256) lbfgs_reg_kernel(LbfgsArgs a) {
   }
 #pragma unroll
   for (int u = 0; u < kLbPer; ++u)  // r = H0 q
-    if (in[u]) q[u] *= precond_elem(a.eps, a.N, a.V, e[u], a.gamma, beta);
+    if (in[u]) q[u] *= precond_of(a, e[u], beta);
   for (int c = count - 1; c >= 0; --c) {  // second loop: oldest to newest
     const int sl = (head - 1 - c + 2 * m) % m;
     double part = 0.0;
@@ -1482,13 +1490,11 @@ __global__ void __launch_bounds__(256) lbfgs_reg_kernel(LbfgsArgs a) {
   }
 }
 
-__global__ void precond_kernel(const double *eps, int N, int V, double gamma,
-                               const double *state, const double *g, double *pg) {
-  long n = (long)N * V;
-  double beta = state[3];
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+__global__ void precond_kernel(LbfgsArgs a, const double *g, double *pg) {
+  const double beta = a.state[3];
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < a.n;
        e += (long)gridDim.x * blockDim.x)
-    pg[e] = precond_elem(eps, N, V, e, gamma, beta) * g[e];
+    pg[e] = precond_of(a, e, beta) * g[e];
 }
 
 // Deterministic single-block dot product (line-search scalars).
@@ -1679,12 +1685,7 @@ cudaError_t launch_gemm(const Phase &ph, cudaStream_t s) {
 
 cudaError_t launch_lbfgs(etdm_handle *h, const double *a, const double *g, double *p,
                          cudaStream_t s) {
-  LbfgsArgs d{};
-  d.n = (long)h->N * h->V; d.N = h->N; d.V = h->V; d.m = h->lbfgs_m;
-  d.a = a; d.g = g; d.p = p;
-  d.s = h->d_s; d.y = h->d_y; d.aprev = h->d_aprev; d.gprev = h->d_gprev; d.q = h->d_q;
-  d.state = h->d_lbstate; d.eps = h->d_eps; d.gamma = h->gamma;
-  d.red = h->d_red; d.bar = h->d_bar; d.flags = h->d_flags;
+  LbfgsArgs d = lbfgs_args(h, a, g, p);
   void *args[] = {&d};
   if (d.n <= (long)h->lb_blocks * 256 * kLbPer && d.m <= kLbMaxM)  // registers hold every element
     return cudaLaunchCooperativeKernel((void *)lbfgs_reg_kernel, dim3(h->lb_blocks), dim3(256), args,
@@ -1694,11 +1695,11 @@ cudaError_t launch_lbfgs(etdm_handle *h, const double *a, const double *g, doubl
 }
 
 cudaError_t launch_precond(etdm_handle *h, const double *g, double *pg, cudaStream_t s) {
-  long n = (long)h->N * h->V;
-  int blocks = (int)((n + 255) / 256);
+  const LbfgsArgs d = lbfgs_args(h, nullptr, g, pg);
+  int blocks = (int)((d.n + 255) / 256);
   if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
   if (blocks < 1) blocks = 1;
-  precond_kernel<<<blocks, 256, 0, s>>>(h->d_eps, h->N, h->V, h->gamma, h->d_lbstate, g, pg);
+  precond_kernel<<<blocks, 256, 0, s>>>(d, g, pg);
   return cudaGetLastError();
 }
 
@@ -1753,8 +1754,9 @@ cudaError_t launch_scale_copy(const double *src, double *dst, double c, long n,
 
 LbfgsArgs lbfgs_args(etdm_handle *h, const double *a, const double *g, double *p) {
   LbfgsArgs d{};
-  d.n = (long)h->N * h->V; d.N = h->N; d.V = h->V; d.m = h->lbfgs_m;
+  d.n = h->nvar; d.N = h->N; d.V = h->V; d.m = h->lbfgs_m;
   d.a = a; d.g = g; d.p = p;
+  d.pden = h->d_kpden; d.pw = h->d_kpw;
   d.s = h->d_s; d.y = h->d_y; d.aprev = h->d_aprev; d.gprev = h->d_gprev; d.q = h->d_q;
   d.state = h->d_lbstate; d.eps = h->d_eps; d.gamma = h->gamma;
   d.red = h->d_red; d.bar = h->d_bar; d.flags = h->d_flags;

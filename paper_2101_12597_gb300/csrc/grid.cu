@@ -11,6 +11,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "kpoint.h"
 
 namespace etdm {
 
@@ -454,6 +455,155 @@ cudaError_t launch_vmat_fp64(etdm_handle *h, const double *v, double *Hacc, cuda
   if (e != cudaSuccess) return e;
   vmat_fp64_kernel<<<h->n_tiles, kRhoThreads, sm, s>>>(h->geom, tables_of(h), h->d_tile_ptr,
                                                        h->d_keys, v, Hacc);
+  return cudaGetLastError();
+}
+
+
+// ---- full A over k-points: the grid passes resolved by lattice offset --------
+// With Bloch functions (Eq. 5) the density of Eq. 2 summed over k is
+//   rho(r) = sum_(a, b) eta_a(r) eta_b(r) DR[n_a - n_b][mu_a][mu_b],
+// a, b the (function, image) entries of the tile's list and
+// DR[R] = Re sum_k exp(2 pi i k.R) D_k; the potential matrix of Eq. 11 is
+//   V_k = sum_R exp(-2 pi i k.R) VR[R],  VR[R][mu][nu] = dV sum over the
+// entries of mu and nu with n_a - n_b = R of sum_r eta_a v eta_b.  Both passes
+// stay real; the phases are applied to the small dense matrices.  A pair whose
+// offset lies outside the table has no grid point within r_c of both images
+// (the table covers |R_x| < 2 r_c / L_x + 1), so it contributes nothing.
+__device__ inline int k_ridx(const KGeom &G, int ka, int kb) {
+  const int rx = ((ka >> 6) & 7) - ((kb >> 6) & 7);
+  const int ry = ((ka >> 3) & 7) - ((kb >> 3) & 7);
+  const int rz = (ka & 7) - (kb & 7);
+  if (abs(rx) > G.Rm[0] || abs(ry) > G.Rm[1] || abs(rz) > G.Rm[2]) return -1;
+  return ((rx + G.Rm[0]) * (2 * G.Rm[1] + 1) + ry + G.Rm[1]) * (2 * G.Rm[2] + 1) + rz + G.Rm[2];
+}
+
+__global__ void __launch_bounds__(kRhoThreads) rho_k_kernel(GridGeom g, Tables tb,
+                                                            const int *tile_ptr,
+                                                            const int *keys, KGeom G,
+                                                            const double *DR, double *rho) {
+  extern __shared__ double smem[];
+  const int t = blockIdx.x;
+  const int kb = tile_ptr[t], n = tile_ptr[t + 1] - kb;
+  double *X = smem;                       // [n][64]
+  double *Dc = X + (long)n * kTP;         // [kChunk][n]
+  int *mu_s = (int *)(Dc + (long)kChunk * n);
+  int *key_s = mu_s + n;
+  __shared__ double part[kRhoThreads];
+  TileRange r = tile_range(g, t);
+  build_tile_basis(g, tb, keys + kb, n, r, mu_s, X);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) key_s[e] = keys[kb + e];
+  __syncthreads();
+  const long MM = (long)g.M * g.M;
+  const int p = threadIdx.x % kTP, grp = threadIdx.x / kTP, ngrp = kRhoThreads / kTP;
+  double acc = 0.0;
+  for (int a0 = 0; a0 < n; a0 += kChunk) {
+    int rows = min(kChunk, n - a0);
+    for (int q = threadIdx.x; q < rows * n; q += blockDim.x) {
+      int rr = q / n, b = q % n;
+      const int ri = k_ridx(G, key_s[a0 + rr], key_s[b]);
+      Dc[rr * n + b] = ri < 0 ? 0.0 : DR[ri * MM + (long)mu_s[a0 + rr] * g.M + mu_s[b]];
+    }
+    __syncthreads();
+    for (int rr = grp; rr < rows; rr += ngrp) {
+      const double *drow = Dc + rr * n;
+      double y = 0.0;
+      for (int b = 0; b < n; ++b) y = fma(drow[b], X[b * kTP + p], y);
+      acc = fma(X[(a0 + rr) * kTP + p], y, acc);
+    }
+    __syncthreads();
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < kTP) {
+    double s = 0.0;
+    for (int q = 0; q < ngrp; ++q) s += part[q * kTP + threadIdx.x];
+    int pk = p % g.tz, pj = (p / g.tz) % g.ty, pi = p / (g.tz * g.ty);
+    int i = r.i0 + pi, j = r.j0 + pj, k = r.k0 + pk;
+    if (i < r.i1 && j < r.j1 && k < r.k1) rho[((long)i * g.ny + j) * g.nz + k] = s;
+  }
+}
+
+cudaError_t launch_rho_k(etdm_handle *h, const double *DR, double *rho, cudaStream_t s) {
+  size_t sm = rho_smem(h->max_list) + (size_t)h->max_list * 4;
+  cudaError_t e = cudaFuncSetAttribute(rho_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  rho_k_kernel<<<h->n_tiles, kRhoThreads, sm, s>>>(h->geom, tables_of(h), h->d_tile_ptr,
+                                                   h->d_keys, h->kg, DR, rho);
+  return cudaGetLastError();
+}
+
+// VR[R][mu_a][mu_b] += dV sum_p X_ap v_p X_bp for every ordered pair of list
+// entries (computed once per unordered pair).
+__global__ void __launch_bounds__(kRhoThreads) vmat_k_kernel(GridGeom g, Tables tb,
+                                                             const int *tile_ptr,
+                                                             const int *keys, KGeom G,
+                                                             const double *v, double *VR) {
+  extern __shared__ double smem[];
+  const int t = blockIdx.x;
+  const int kb = tile_ptr[t], n = tile_ptr[t + 1] - kb;
+  double *X = smem;                          // [n][65] padded
+  double *Xv = X + (long)n * (kTP + 1);      // [n][65]
+  int *mu_s = (int *)(Xv + (long)n * (kTP + 1));
+  int *key_s = mu_s + n;
+  __shared__ double vp[kTP];
+  TileRange r = tile_range(g, t);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    key_s[e] = keys[kb + e];
+    mu_s[e] = keys[kb + e] >> 9;
+  }
+  if (threadIdx.x < kTP) {
+    int p = threadIdx.x;
+    int pk = p % g.tz, pj = (p / g.tz) % g.ty, pi = p / (g.tz * g.ty);
+    int i = r.i0 + pi, j = r.j0 + pj, k = r.k0 + pk;
+    vp[p] = (i < r.i1 && j < r.j1 && k < r.k1) ? v[((long)i * g.ny + j) * g.nz + k] * g.dV
+                                                 : 0.0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n * kTP; q += blockDim.x) {
+    int e = q / kTP, p = q % kTP;
+    int pk = p % g.tz, pj = (p / g.tz) % g.ty, pi = p / (g.tz * g.ty);
+    int i = r.i0 + pi, j = r.j0 + pj, k = r.k0 + pk;
+    double val = 0.0;
+    if (i < r.i1 && j < r.j1 && k < r.k1) {
+      int mu, ix, iy, iz;
+      decode_key(key_s[e], mu, ix, iy, iz);
+      long bx = ((long)mu * kImgN + ix) * g.nx + i;
+      long by = ((long)mu * kImgN + iy) * g.ny + j;
+      long bz = ((long)mu * kImgN + iz) * g.nz + k;
+      double r2 = __dadd_rn(__dadd_rn(tb.sq[0][bx], tb.sq[1][by]), tb.sq[2][bz]);
+      if (r2 < tb.rc2[mu]) val = tb.norm[mu] * tb.ex[0][bx] * tb.ex[1][by] * tb.ex[2][bz];
+    }
+    X[e * (kTP + 1) + p] = val;
+    Xv[e * (kTP + 1) + p] = val * vp[p];
+  }
+  __syncthreads();
+  const long MM = (long)g.M * g.M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = warp; a < n; a += nw) {
+    const double *xa = Xv + a * (kTP + 1);
+    for (int b = a + lane; b < n; b += 32) {
+      const int rab = k_ridx(G, key_s[a], key_s[b]);
+      if (rab < 0) continue;
+      const double *xb = X + b * (kTP + 1);
+      double s = 0.0;
+#pragma unroll 8
+      for (int p = 0; p < kTP; ++p) s = fma(xa[p], xb[p], s);
+      if (s == 0.0) continue;
+      const int ma = mu_s[a], mb = mu_s[b];
+      atomicAdd(VR + rab * MM + (long)ma * g.M + mb, s);
+      if (a != b) atomicAdd(VR + k_ridx(G, key_s[b], key_s[a]) * MM + (long)mb * g.M + ma, s);
+    }
+  }
+}
+
+cudaError_t launch_vmat_k(etdm_handle *h, const double *v, double *VR, cudaStream_t s) {
+  size_t sm = (size_t)h->max_list * (kTP + 1) * 16 + (size_t)h->max_list * 8 + 16;
+  cudaError_t e = cudaFuncSetAttribute(vmat_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  vmat_k_kernel<<<h->n_tiles, kRhoThreads, sm, s>>>(h->geom, tables_of(h), h->d_tile_ptr,
+                                                    h->d_keys, h->kg, v, VR);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,10 @@ void build_mixed_plan(etdm_handle *owner, const std::vector<etdm_handle *> &subs
                       const int *d_active, int *d_flags, bool batch,
                       unsigned long long *vfix, size_t vfix_bytes, MixedPlan *P);
 
+// L-BFGS memory, line-search buffers and reduction scratch for h->nvar
+// variables (capi.cu).
+void alloc_opt_buffers(etdm_handle *h);
+
 // Single-system pieces of the C ABI (capi.cu) that the batch reuses.
 void init_system(etdm_handle *h, const etdm_system *sys, const etdm_options *opt);
 void eval_system(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s);

@@ -259,10 +259,22 @@ struct LbfgsArgs {
   double *aprev, *gprev, *q;
   double *state;         // [0]=count [1]=head [2]=have_prev [3]=beta [4..4+m)=rho [..+m)=alpha
   const double *eps;     // [M]
+  const double *pden;    // full A: [n] 2 (1 - gamma) |(e_i - e_j)(f_i - f_j)| (null: occupied-virtual)
+  const double *pw;      // full A: [n] k-point weight of each variable
   double gamma;
   double *red;           // [4*gridDim]: two halves of two sums each
   unsigned *bar;
   int *flags;
+};
+
+// Lattice offsets R = n_a - n_b between two images that meet in a tile (the
+// full-A path's real-space density and potential matrices): |R_x| <= Rm[0]
+// etc., index ((Rx + Rm0)(2 Rm1 + 1) + Ry + Rm1)(2 Rm2 + 1) + Rz + Rm2.
+struct KGeom {
+  int nk, M;
+  int Rm[3];
+  int nR;
+  const double *kfrac;  // [nk][3] k-points in fractional reciprocal coordinates (device)
 };
 
 }  // namespace etdm
@@ -274,6 +286,26 @@ struct etdm_handle {
   int lbfgs_m = 3;
   double gamma = 0.25, beta0 = 1.0;
   int M = 0, N = 0, V = 0, n_atoms = 0;
+  long nvar = 0;          // variables: N V (occupied-virtual) or n_k M^2 (full A)
+  // full A over k-points (etdm_system.n_k >= 1 or ETDM_PARAM_FULL): complex
+  // FP64 matrices [n_k][M][M], row-major
+  bool kpath = false;
+  int nk = 0;
+  double kT = 0.0, mu = 0.0, n_elec = 0.0;
+  etdm::KGeom kg{};
+  std::vector<double> h_kfrac, h_kw;
+  double *d_kfrac = nullptr, *d_kw = nullptr;
+  double *d_kf = nullptr;       // [n_k][M] occupations (weight and spin included)
+  double *d_keps0 = nullptr;    // [n_k][M] eigenvalues of h_core(k) (reference)
+  double *d_komega = nullptr;   // [n_k][M] eigenvalues of iA(k), last evaluation
+  double *d_kpden = nullptr, *d_kpw = nullptr;  // [nvar] preconditioner parts
+  double *d_kpart = nullptr;    // kinetic-energy block partials
+  double2 *d_kS = nullptr, *d_kT = nullptr, *d_kC0 = nullptr;
+  double2 *d_kW = nullptr, *d_kO = nullptr, *d_kD = nullptr, *d_kH = nullptr;
+  double2 *d_kX1 = nullptr, *d_kX2 = nullptr;
+  double *d_kDR = nullptr, *d_kVR = nullptr;  // [nR][M][M]
+  void *d_kwork = nullptr;      // eigensolver workspace
+  bool kref_set = false;        // reference given by etdm_set_reference
   int n[3] = {0, 0, 0};
   long G = 0;
   double L[3], h[3], dV = 0, omega = 0, sigma = 0;

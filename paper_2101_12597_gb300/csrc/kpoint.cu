@@ -1,0 +1,836 @@
+// The full-A path with k-point sampling (Sec. 2-3 with fractional occupation):
+// complex FP64 dense kernels (batched over the k-points), the Hermitian
+// eigensolver behind Eq. 35 and Eq. 39, and the element-wise steps between
+// them.  The grid passes of this path are in grid.cu (density and V resolved
+// by lattice offset), the sequencing in capi.cu.
+//
+// Layout: every complex matrix is row-major M x M (double2 = re, im), the
+// k-points' matrices one after another.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
+#include "host.h"
+#include "kpoint.h"
+
+namespace etdm {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc += a * b
+__device__ __forceinline__ void cfma(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+
+// ---- batched complex GEMM ----------------------------------------------------
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b], op(X) = X (0) or X^dagger (1).
+// 64 x 64 output tiles, K steps of 16, 4 x 4 outputs per thread; FP64 FMA.
+constexpr int kZB = 64, kZK = 16;
+
+__global__ void __launch_bounds__(256) zgemm_kernel(ZgemmArgs g) {
+  __shared__ double2 As[kZK][kZB];
+  __shared__ double2 Bs[kZK][kZB];
+  const int b = blockIdx.z;
+  const double2 *A = g.A + (long)b * g.sA;
+  const double2 *B = g.B + (long)b * g.sB;
+  double2 *C = g.C + (long)b * g.sC;
+  const int row0 = blockIdx.y * kZB, col0 = blockIdx.x * kZB;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < g.k; k0 += kZK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      if (g.opa == 0) {  // op(A)[i][kk] = A[i][kk]: kk fastest
+        const int i = e / kZK, kk = e % kZK;
+        const int gi = row0 + i, gk = k0 + kk;
+        As[kk][i] = (gi < g.m && gk < g.k) ? A[(long)gi * g.lda + gk] : make_double2(0.0, 0.0);
+      } else {           // op(A)[i][kk] = conj(A[kk][i]): i fastest
+        const int kk = e / kZB, i = e % kZB;
+        const int gi = row0 + i, gk = k0 + kk;
+        As[kk][i] = (gi < g.m && gk < g.k) ? cconj(A[(long)gk * g.lda + gi]) : make_double2(0.0, 0.0);
+      }
+      if (g.opb == 0) {  // op(B)[kk][j] = B[kk][j]: j fastest
+        const int kk = e / kZB, j = e % kZB;
+        const int gj = col0 + j, gk = k0 + kk;
+        Bs[kk][j] = (gj < g.n && gk < g.k) ? B[(long)gk * g.ldb + gj] : make_double2(0.0, 0.0);
+      } else {           // op(B)[kk][j] = conj(B[j][kk]): kk fastest
+        const int j = e / kZK, kk = e % kZK;
+        const int gj = col0 + j, gk = k0 + kk;
+        Bs[kk][j] = (gj < g.n && gk < g.k) ? cconj(B[(long)gj * g.ldb + gk]) : make_double2(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kZK; ++kk) {
+      double2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = row0 + ty * 4 + i;
+    if (gi >= g.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = col0 + tx * 4 + j;
+      if (gj >= g.n) continue;
+      double2 v = cmul(g.alpha, acc[i][j]);
+      double2 *c = C + (long)gi * g.ldc + gj;
+      if (g.beta.x != 0.0 || g.beta.y != 0.0) v = cadd(v, cmul(g.beta, *c));
+      *c = v;
+    }
+  }
+}
+
+cudaError_t launch_zgemm(const ZgemmArgs &g, int batch, cudaStream_t s) {
+  if (g.m <= 0 || g.n <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((g.n + kZB - 1) / kZB, (g.m + kZB - 1) / kZB, batch);
+  zgemm_kernel<<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// Square n x n batch: C = alpha op(A) op(B) + beta C with the k-point stride n^2.
+cudaError_t zgemm_sq(const double2 *A, int opa, const double2 *B, int opb, double2 *C, int n,
+                     int batch, cudaStream_t s, double alpha, double beta) {
+  ZgemmArgs g;
+  g.A = A; g.B = B; g.C = C;
+  g.m = g.n = g.k = n;
+  g.lda = g.ldb = g.ldc = n;
+  g.sA = g.sB = g.sC = (long)n * n;
+  g.opa = opa; g.opb = opb;
+  g.alpha = make_double2(alpha, 0.0);
+  g.beta = make_double2(beta, 0.0);
+  return launch_zgemm(g, batch, s);
+}
+
+// ---- Hermitian eigensolver (FP64) ------------------------------------------------
+// A = V diag(w) V^dagger for a batch of n x n Hermitian matrices, in three
+// kernels: Householder reduction to a tridiagonal T = Q^dagger A Q (one block
+// per matrix, the matrix held in L2), implicit QL iterations with Wilkinson
+// shifts on the real tridiagonal Phi^dagger T Phi (Phi a diagonal of phases;
+// one block per matrix, rotations applied by all threads to the rows of Z),
+// and the back-transformation V = Q Phi Z (blocks over slabs of columns).
+// Eigenvalues ascending.
+
+// Reflector j maps x = A[j+1 .., j] to alpha e_1: H_j = I - 2 u u^dagger with
+// u = (x - alpha e_1) / |x - alpha e_1|, alpha = -(x_0/|x_0|) |x|; u is stored
+// in hv[j][j+1 ..] (zero when the column is already reduced).  The trailing
+// block becomes H A H = A - 2 u w^dagger - 2 w u^dagger, w = p - (u^dagger p) u,
+// p = A u.  d[j] = Re A[j][j], e[j] = T[j+1][j].
+__global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb, double *db,
+                                                       double2 *eb, int n) {
+  extern __shared__ double2 zsm[];
+  double2 *u = zsm;       // [n]
+  double2 *p = zsm + n;   // [n]
+  __shared__ double2 alpha_s;
+  __shared__ int skip_s;
+  const int b = blockIdx.x;
+  double2 *A = Ab + (long)b * n * n;
+  double2 *hv = hvb + (long)b * n * n;
+  double *d = db + (long)b * n;
+  double2 *e = eb + (long)b * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = n - j - 1, o = j + 1;
+    for (int i = tid; i < m; i += nt) u[i] = A[(long)(o + i) * n + j];
+    __syncthreads();
+    double tail = 0.0;
+    for (int i = 1 + tid; i < m; i += nt) tail += u[i].x * u[i].x + u[i].y * u[i].y;
+    tail = block_sum(tail);
+    if (tid == 0) {
+      const double2 x0 = u[0];
+      const double ax0 = hypot(x0.x, x0.y);
+      if (tail == 0.0) {  // already reduced: no reflection
+        skip_s = 1;
+        alpha_s = x0;
+      } else {
+        const double xn = sqrt(ax0 * ax0 + tail);
+        const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+        alpha_s = make_double2(-ph.x * xn, -ph.y * xn);
+        const double v0 = ax0 + xn;                   // v_0 = ph (|x_0| + |x|)
+        const double inv = 1.0 / sqrt(v0 * v0 + tail);  // 1 / |v|
+        u[0] = make_double2(ph.x * v0 * inv, ph.y * v0 * inv);
+        p[0] = make_double2(inv, 0.0);                // scale of the other entries
+        skip_s = 0;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) e[j] = alpha_s;
+    double2 *hrow = hv + (long)j * n;
+    if (skip_s) {
+      for (int i = tid; i < n; i += nt) hrow[i] = make_double2(0.0, 0.0);
+      __syncthreads();
+      continue;
+    }
+    const double inv = p[0].x;
+    __syncthreads();
+    for (int i = 1 + tid; i < m; i += nt) u[i] = cscale(u[i], inv);
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) hrow[i] = i >= o ? u[i - o] : make_double2(0.0, 0.0);
+    // p = A_t u: a warp per row
+    for (int i = warp; i < m; i += nw) {
+      const double2 *row = A + (long)(o + i) * n + o;
+      double2 s = make_double2(0.0, 0.0);
+      for (int l = lane; l < m; l += 32) cfma(s, row[l], u[l]);
+      for (int q = 16; q > 0; q >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, q);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, q);
+      }
+      if (lane == 0) p[i] = s;
+    }
+    __syncthreads();
+    double kr = 0.0;  // K = u^dagger p (real for Hermitian A)
+    for (int i = tid; i < m; i += nt) kr += u[i].x * p[i].x + u[i].y * p[i].y;
+    kr = block_sum(kr);
+    for (int i = tid; i < m; i += nt) p[i] = csub(p[i], cscale(u[i], kr));
+    __syncthreads();
+    // A_t -= 2 (u w^dagger + w u^dagger)
+    for (long q = tid; q < (long)m * m; q += nt) {
+      const int i = (int)(q / m), l = (int)(q % m);
+      double2 t = cmul(u[i], cconj(p[l]));
+      cfma(t, p[i], cconj(u[l]));
+      double2 *a = A + (long)(o + i) * n + o + l;
+      *a = csub(*a, cscale(t, 2.0));
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) d[i] = A[(long)i * n + i].x;
+  if (tid == 0) {
+    e[n - 1] = make_double2(0.0, 0.0);
+    if (n >= 1) for (int i = 0; i < n; ++i) hv[(long)(n - 1) * n + i] = make_double2(0.0, 0.0);
+  }
+}
+
+// Implicit QL with Wilkinson shifts on the real tridiagonal (d, |e|); thread 0
+// computes each sweep's rotations, every thread applies them to its rows of Z
+// (stored by columns, Zt[c][r]).  Then the eigenvalues are ranked ascending.
+// More than 60 sweeps for one eigenvalue sets ETDM_ERR_NOT_CONVERGED.
+__global__ void __launch_bounds__(512) ztql_kernel(const double *db, const double2 *eb, double *wb,
+                                                    double2 *phib, double *Ztb, int *permb,
+                                                    int *flags, int n) {
+  extern __shared__ double qsm[];
+  double *d = qsm, *e = qsm + n, *cs = qsm + 2 * n, *sn = qsm + 3 * n;
+  __shared__ int hi_s, stop_s, done_s;
+  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  double *Zt = Ztb + (long)b * n * n;
+  for (long q = tid; q < (long)n * n; q += nt) Zt[q] = (q / n == q % n) ? 1.0 : 0.0;
+  for (int i = tid; i < n; i += nt) {
+    d[i] = db[(long)b * n + i];
+    const double2 ei = eb[(long)b * n + i];
+    e[i] = hypot(ei.x, ei.y);
+  }
+  __syncthreads();
+  double anorm = 0.0;
+  if (tid == 0) {  // phases: T[j+1][j] = phi_(j+1) conj(phi_j) |e_j|
+    double2 ph = make_double2(1.0, 0.0);
+    phib[(long)b * n] = ph;
+    for (int j = 0; j + 1 < n; ++j) {
+      const double2 ej = eb[(long)b * n + j];
+      const double a = e[j];
+      if (a > 0.0) ph = cmul(ph, make_double2(ej.x / a, ej.y / a));
+      phib[(long)b * n + j + 1] = ph;
+    }
+    for (int j = 0; j < n; ++j) anorm = fmax(anorm, fabs(d[j]) + e[j] + (j ? e[j - 1] : 0.0));
+  }
+  const double eps = 2.220446049250313e-16;
+  int dn = 0;  // the block's copy of done_s (read between two barriers)
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      if (tid == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          const double dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= eps * dd || fabs(e[m]) <= eps * eps * anorm) break;
+        }
+        done_s = (m == l);
+        if (!done_s) {
+          if (++iter > 60) {
+            atomicExch(flags + FLAG_ERR, ETDM_ERR_NOT_CONVERGED);
+            done_s = 2;
+          } else {
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+            double s = 1.0, c = 1.0, pp = 0.0;
+            int i = m - 1;
+            for (; i >= l; --i) {
+              const double f = s * e[i], bb = c * e[i];
+              r = hypot(f, g);
+              e[i + 1] = r;
+              if (r == 0.0) {  // underflow: deflate here
+                d[i + 1] -= pp;
+                e[m] = 0.0;
+                break;
+              }
+              s = f / r;
+              c = g / r;
+              g = d[i + 1] - pp;
+              r = (d[i] - g) * s + 2.0 * c * bb;
+              pp = s * r;
+              d[i + 1] = g + pp;
+              g = c * r - bb;
+              cs[i] = c;
+              sn[i] = s;
+            }
+            stop_s = i + 1;  // rotations i = m-1 .. stop_s were made
+            if (i < l) {
+              d[l] -= pp;
+              e[l] = g;
+              e[m] = 0.0;
+            }
+            hi_s = m;
+          }
+        }
+      }
+      __syncthreads();
+      dn = done_s;
+      const int hi = hi_s, st = stop_s;
+      __syncthreads();  // every thread has read the sweep's words before thread 0 writes again
+      if (dn) break;
+      for (int r = tid; r < n; r += nt) {  // rotate columns (i, i+1) of row r, i = hi-1 .. st
+        double carry = Zt[(long)hi * n + r];
+        for (int i = hi - 1; i >= st; --i) {
+          const double zi = Zt[(long)i * n + r];
+          Zt[(long)(i + 1) * n + r] = sn[i] * zi + cs[i] * carry;
+          carry = cs[i] * zi - sn[i] * carry;
+        }
+        Zt[(long)st * n + r] = carry;
+      }
+      __syncthreads();
+    }
+    if (dn == 2) break;
+  }
+  __syncthreads();
+  // rank the eigenvalues (ties by index)
+  for (int i = tid; i < n; i += nt) {
+    int rk = 0;
+    const double di = d[i];
+    for (int j = 0; j < n; ++j) rk += (d[j] < di) || (d[j] == di && j < i);
+    wb[(long)b * n + rk] = di;
+    permb[(long)b * n + rk] = i;
+  }
+}
+
+// V[:, c] = H_0 ... H_(n-3) Phi Z[:, perm[c]] for a slab of kBackW columns.
+constexpr int kBackW = 8;
+__global__ void __launch_bounds__(256) zback_kernel(const double2 *hvb, const double2 *phib,
+                                                     const double *Ztb, const int *permb,
+                                                     double2 *Vb, int n) {
+  extern __shared__ double2 W[];  // [n][kBackW]
+  __shared__ double2 sc[kBackW];
+  const int b = blockIdx.y, c0 = blockIdx.x * kBackW;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const double2 *hv = hvb + (long)b * n * n;
+  const double *Zt = Ztb + (long)b * n * n;
+  const int nc = min(kBackW, n - c0);
+  for (int q = tid; q < n * kBackW; q += nt) {
+    const int c = q / n, r = q % n;
+    double2 v = make_double2(0.0, 0.0);
+    if (c < nc) v = cscale(phib[(long)b * n + r], Zt[(long)permb[(long)b * n + c0 + c] * n + r]);
+    W[r * kBackW + c] = v;
+  }
+  __syncthreads();
+  for (int j = n - 3; j >= 0; --j) {
+    const int o = j + 1, m = n - o;
+    const double2 *u = hv + (long)j * n + o;
+    if (warp < kBackW) {  // s_c = u^dagger W[o.., c], a warp per column
+      double2 s = make_double2(0.0, 0.0);
+      for (int i = lane; i < m; i += 32) cfma(s, cconj(u[i]), W[(o + i) * kBackW + warp]);
+      for (int q = 16; q > 0; q >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, q);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, q);
+      }
+      if (lane == 0) sc[warp] = cscale(s, 2.0);
+    }
+    __syncthreads();
+    for (int q = tid; q < m * kBackW; q += nt) {
+      const int i = q / kBackW, c = q % kBackW;
+      W[(o + i) * kBackW + c] = csub(W[(o + i) * kBackW + c], cmul(u[i], sc[c]));
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < n * kBackW; q += nt) {
+    const int r = q / kBackW, c = q % kBackW;
+    if (c < nc) Vb[(long)b * n * n + (long)r * n + c0 + c] = W[r * kBackW + c];
+  }
+}
+
+size_t heev_work_bytes(int n, int batch) {
+  const size_t nn = (size_t)n * n * batch;
+  return nn * 16 /* hv */ + nn * 8 /* Z */ + (size_t)n * batch * (8 + 16 + 16 + 4) + 256 * 6;
+}
+
+// A (destroyed) -> w ascending, V (columns); work from heev_work_bytes.
+cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, void *work,
+                        int *flags, cudaStream_t s) {
+  if (n < 1 || n > kEigMax || batch < 1) return cudaErrorInvalidValue;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char *p = (char *)work;
+  const size_t nn = (size_t)n * n * batch;
+  double2 *hv = (double2 *)p; p += al(nn * 16);
+  double *Z = (double *)p; p += al(nn * 8);
+  double *d = (double *)p; p += al((size_t)n * batch * 8);
+  double2 *e = (double2 *)p; p += al((size_t)n * batch * 16);
+  double2 *phi = (double2 *)p; p += al((size_t)n * batch * 16);
+  int *perm = (int *)p;
+  cudaError_t err;
+  const int smt = 2 * n * (int)sizeof(double2);
+  err = cudaFuncSetAttribute(zhetrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smt);
+  if (err != cudaSuccess) return err;
+  zhetrd_kernel<<<batch, 1024, smt, s>>>(A, hv, d, e, n);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const int smq = 4 * n * (int)sizeof(double);
+  err = cudaFuncSetAttribute(ztql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
+  if (err != cudaSuccess) return err;
+  ztql_kernel<<<batch, 512, smq, s>>>(d, e, w, phi, Z, perm, flags, n);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  const int smb = n * kBackW * (int)sizeof(double2);
+  err = cudaFuncSetAttribute(zback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+  if (err != cudaSuccess) return err;
+  zback_kernel<<<dim3((n + kBackW - 1) / kBackW, batch), 256, smb, s>>>(hv, phi, Z, perm, V, n);
+  return cudaGetLastError();
+}
+
+// ---- element-wise steps of the k-point path ----------------------------------------
+// Variables of one k-point (Eq. 22-24): Re a_ij for i < j, then Im a_ij for
+// i <= j, both row-major over the upper triangle.
+__host__ __device__ inline long k_re_idx(long i, long j, long M) { return i * M - i * (i + 1) / 2 + (j - i - 1); }
+__host__ __device__ inline long k_im_idx(long i, long j, long M) { return i * M - i * (i - 1) / 2 + (j - i); }
+
+// iA(k) from the variables: A_ij = a_ij (i < j), A_ji = -conj(a_ij),
+// A_ii = i Im a_ii (skew-Hermitian, Eq. 8), times i.
+__global__ void k_build_iA_kernel(const double *a, int nk, int M, double2 *iA) {
+  const long MM = (long)M * M, nre = (long)M * (M - 1) / 2;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int i = (int)(r / M), j = (int)(r % M);
+    const double *v = a + k * MM;
+    double2 z;
+    if (i < j) z = make_double2(-v[nre + k_im_idx(i, j, M)], v[k_re_idx(i, j, M)]);
+    else if (i > j) z = make_double2(-v[nre + k_im_idx(j, i, M)], -v[k_re_idx(j, i, M)]);
+    else z = make_double2(-v[nre + k_im_idx(i, i, M)], 0.0);
+    iA[q] = z;
+  }
+}
+
+// X[k][r][c] = Y[k][r][c] s[k][c]: mode 0 s = x (real), mode 1 s = x^(-1/2)
+// (x <= 0 sets ETDM_ERR_NUMERIC), mode 2 s = exp(-i x) (Eq. 35).
+__global__ void k_colscale_kernel(const double2 *Y, const double *x, double2 *X, int nk, int M,
+                                  int mode, int *flags) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM;
+    const int c = (int)(q % M);
+    const double xv = x[k * M + c];
+    double2 s;
+    if (mode == 0) {
+      s = make_double2(xv, 0.0);
+    } else if (mode == 1) {
+      if (!(xv > 0.0)) atomicExch(flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+      s = make_double2(xv > 0.0 ? 1.0 / sqrt(xv) : 0.0, 0.0);
+    } else {
+      double sn, cs;
+      sincos(xv, &sn, &cs);
+      s = make_double2(cs, -sn);
+    }
+    X[q] = cmul(Y[q], s);
+  }
+}
+
+// X = (X + X^dagger) / 2, per k-point.
+__global__ void k_hermitize_kernel(double2 *X, int nk, int M) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int i = (int)(r / M), j = (int)(r % M);
+    if (i > j) continue;
+    double2 *x = X + k * MM;
+    const double2 a = x[(long)i * M + j], b = x[(long)j * M + i];
+    const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    x[(long)i * M + j] = h;
+    x[(long)j * M + i] = cconj(h);
+  }
+}
+
+__device__ inline void k_offset(const KGeom &G, int ridx, int *R) {
+  const int ny = 2 * G.Rm[1] + 1, nz = 2 * G.Rm[2] + 1;
+  R[2] = ridx % nz - G.Rm[2];
+  R[1] = (ridx / nz) % ny - G.Rm[1];
+  R[0] = ridx / (nz * ny) - G.Rm[0];
+}
+
+// exp(2 pi i k.R) for fractional k
+__device__ inline double2 k_phase(const double *kf, const int *R) {
+  const double x = 2.0 * (kf[0] * R[0] + kf[1] * R[1] + kf[2] * R[2]);
+  double sn, cs;
+  sincospi(x, &sn, &cs);
+  return make_double2(cs, sn);
+}
+
+// Real-space density matrix per lattice offset (Eq. 2 summed over k):
+// DR[R][mu][nu] = Re sum_k exp(2 pi i k.R) D_k[mu][nu].
+__global__ void k_dr_kernel(KGeom G, const double2 *D, double *DR) {
+  const long MM = (long)G.M * G.M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < G.nR * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const int ridx = (int)(q / MM);
+    const long r = q % MM;
+    int R[3];
+    k_offset(G, ridx, R);
+    double s = 0.0;
+    for (int k = 0; k < G.nk; ++k) {
+      const double2 ph = k_phase(G.kfrac + 3 * k, R);
+      const double2 d = D[k * MM + r];
+      s += ph.x * d.x - ph.y * d.y;
+    }
+    DR[q] = s;
+  }
+}
+
+// H_k = T_k + sum_R exp(-2 pi i k.R) VR[R] (Eq. 11 with Bloch functions).
+__global__ void k_hamiltonian_kernel(KGeom G, const double2 *T, const double *VR, double2 *H) {
+  const long MM = (long)G.M * G.M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < G.nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(q / MM);
+    const long r = q % MM;
+    double2 h = T ? T[q] : make_double2(0.0, 0.0);
+    for (int ridx = 0; ridx < G.nR; ++ridx) {
+      int R[3];
+      k_offset(G, ridx, R);
+      const double2 ph = k_phase(G.kfrac + 3 * k, R);
+      const double v = VR[ridx * MM + r];
+      h.x += ph.x * v;
+      h.y -= ph.y * v;
+    }
+    H[q] = h;
+  }
+}
+
+// L_ij = (f_i - f_j) Hmo_ij (Eq. 13), in place.
+__global__ void k_commutator_kernel(double2 *X, const double *f, int nk, int M) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int i = (int)(r / M), j = (int)(r % M);
+    X[q] = cscale(X[q], f[k * M + i] - f[k * M + j]);
+  }
+}
+
+// Lt_ab *= Dt_ab = int_0^1 exp(-i t (w_a - w_b)) dt = (1 - e^(-i d)) / (i d)
+// (Eq. 40, sign as fixed by Eq. 42), series for |d| < 1e-3.
+__global__ void k_dtilde_kernel(double2 *X, const double *w, int nk, int M) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int a = (int)(r / M), b = (int)(r % M);
+    const double d = w[k * M + a] - w[k * M + b];
+    double2 t;
+    if (fabs(d) < 1e-3) {
+      t = make_double2(1.0 - d * d / 6.0, -0.5 * d + d * d * d / 24.0);
+    } else {
+      double sn, cs;
+      sincos(d, &sn, &cs);
+      t = make_double2(sn / d, (cs - 1.0) / d);  // (1 - cos d + i sin d) / (i d)
+    }
+    X[q] = cmul(X[q], t);
+  }
+}
+
+// Real-variable gradient from G^T (Eq. 39, 41, 20): dE/da_ij = (2 - d_ij)/2 G_ij,
+// dE/dRe a_ij = 2 Re, dE/dIm a_ij = -2 Im.
+__global__ void k_grad_vars_kernel(const double2 *GT, double *g, int nk, int M) {
+  const long MM = (long)M * M, nre = (long)M * (M - 1) / 2;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int i = (int)(r / M), j = (int)(r % M);
+    if (i > j) continue;
+    const double2 G = GT[k * MM + (long)j * M + i];  // G_ij
+    double *gk = g + k * MM;
+    if (i < j) {
+      gk[k_re_idx(i, j, M)] = 2.0 * G.x;
+      gk[nre + k_im_idx(i, j, M)] = -2.0 * G.y;
+    } else {
+      gk[nre + k_im_idx(i, i, M)] = -G.y;
+    }
+  }
+}
+
+// Kinetic energy sum_k Re Tr(D_k T_k) = sum Re(D_mn conj(T_mn)) (T Hermitian):
+// one partial per block.
+__global__ void __launch_bounds__(256) k_kinetic_kernel(const double2 *D, const double2 *T, long n,
+                                                        double *part) {
+  double s = 0.0;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    s += D[q].x * T[q].x + D[q].y * T[q].y;
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// E = kinetic + external + Hartree + exchange (Eq. 1) from the partials.
+__global__ void __launch_bounds__(1024) k_energy_kernel(const double *kpart, int nkp,
+                                                        const double *gridpart, int ngp,
+                                                        double *eterms, double *E, int *flags) {
+  double kin = 0.0, t3[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nkp; b += blockDim.x) kin += kpart[b];
+  for (int b = threadIdx.x; b < ngp; b += blockDim.x)
+    for (int q = 0; q < 3; ++q) t3[q] += gridpart[3 * b + q];
+  kin = block_sum(kin);
+  for (int q = 0; q < 3; ++q) t3[q] = block_sum(t3[q]);
+  if (threadIdx.x == 0) {
+    const double e = kin + t3[0] + t3[1] + t3[2];
+    eterms[0] = kin; eterms[1] = t3[0]; eterms[2] = t3[1]; eterms[3] = t3[2];
+    if (E) *E = e;
+    if (!(e == e) || isinf(e)) atomicExch(flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+  }
+}
+
+// 1 / (1 + exp(x)) without overflow
+__device__ inline double k_fd(double x) {
+  const double e = exp(-fabs(x));
+  return x > 0.0 ? e / (1.0 + e) : 1.0 / (1.0 + e);
+}
+
+// Occupations of the reference (fixed afterwards): kT > 0: f_m(k) = 2 w_k
+// FD((eps_m(k) - mu) / kT) with mu by bisection to sum f = n_e; kT = 0 (one
+// k-point): f = 2 on the n_e / 2 lowest eigenvalues (eps ascending per k).
+__global__ void __launch_bounds__(1024) k_occupation_kernel(const double *eps, const double *kw,
+                                                            int nk, int M, double ne, double kT,
+                                                            double *f, double *mu_out) {
+  __shared__ double lo_s, hi_s;
+  const long n = (long)nk * M;
+  if (kT == 0.0) {
+    const int N = (int)(ne / 2.0 + 0.5);
+    for (long q = threadIdx.x; q < n; q += blockDim.x) f[q] = (q % M) < N ? 2.0 * kw[q / M] : 0.0;
+    if (threadIdx.x == 0) *mu_out = 0.0;
+    return;
+  }
+  {  // bracket: [min eps - 50 kT - 1, max eps + 50 kT + 1]
+    __shared__ double red[2][32];
+    double a = 1e300, b = -1e300;
+    for (long q = threadIdx.x; q < n; q += blockDim.x) {
+      a = fmin(a, eps[q]);
+      b = fmax(b, eps[q]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    if (l == 0) { red[0][w] = a; red[1][w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double A = 1e300, B = -1e300;
+      for (int i = 0; i < nw; ++i) { A = fmin(A, red[0][i]); B = fmax(B, red[1][i]); }
+      lo_s = A - 50.0 * kT - 1.0;
+      hi_s = B + 50.0 * kT + 1.0;
+    }
+    __syncthreads();
+  }
+  for (int it = 0; it < 400; ++it) {
+    const double mid = 0.5 * (lo_s + hi_s);
+    double c = 0.0;
+    for (long q = threadIdx.x; q < n; q += blockDim.x) c += 2.0 * kw[q / M] * k_fd((eps[q] - mid) / kT);
+    c = block_sum(c);
+    if (threadIdx.x == 0) {
+      if (c < ne) lo_s = mid; else hi_s = mid;
+    }
+    __syncthreads();
+    const double lo = lo_s, hi = hi_s;
+    __syncthreads();
+    if (hi - lo <= 1e-13 * fmax(1.0, fabs(0.5 * (lo + hi)))) break;
+  }
+  const double mu = 0.5 * (lo_s + hi_s);
+  for (long q = threadIdx.x; q < n; q += blockDim.x) f[q] = 2.0 * kw[q / M] * k_fd((eps[q] - mu) / kT);
+  if (threadIdx.x == 0) *mu_out = mu;
+}
+
+// eps_m(k) = Re (C^dagger X)_mm with X = H C (Eq. 33's orbital energies).
+__global__ void k_diag_kernel(const double2 *C, const double2 *X, double *out, int nk, int M) {
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < (long)nk * M;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / M;
+    const int m = (int)(q % M);
+    const double2 *c = C + k * M * M, *x = X + k * M * M;
+    double s = 0.0;
+    for (int mu = 0; mu < M; ++mu) {
+      const double2 a = c[(long)mu * M + m], b = x[(long)mu * M + m];
+      s += a.x * b.x + a.y * b.y;
+    }
+    out[q] = s;
+  }
+}
+
+// Preconditioner parts per variable (Eq. 33-34 with the k-point weight on
+// beta): den = 2 (1 - gamma) |(e_i - e_j)(f_i - f_j)|, wk = w_k; the same for
+// Re a_ij and Im a_ij.
+__global__ void k_precond_parts_kernel(const double *eps, const double *f, const double *kw,
+                                       int nk, int M, double gamma, double *den, double *wk) {
+  const long MM = (long)M * M, nre = (long)M * (M - 1) / 2;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int i = (int)(r / M), j = (int)(r % M);
+    if (i > j) continue;
+    const double *e = eps + k * M, *fk = f + k * M;
+    const double dv = 2.0 * (1.0 - gamma) * fabs((e[i] - e[j]) * (fk[i] - fk[j]));
+    const long base = k * MM;
+    if (i < j) {
+      den[base + k_re_idx(i, j, M)] = dv;
+      wk[base + k_re_idx(i, j, M)] = kw[k];
+    }
+    den[base + nre + k_im_idx(i, j, M)] = dv;
+    wk[base + nre + k_im_idx(i, j, M)] = kw[k];
+  }
+}
+
+// S(k), T(k) of normalized s-Gaussians (analytic; Eq. 4, 11 with Bloch
+// functions): sum over images n with |d_mu - d_nu - n L| < r_c,mu + r_c,nu of
+// exp(2 pi i k.n) s(R), the inclusion test in a fixed operation order.
+__global__ void k_overlap_kinetic_kernel(const double *center, const double *alpha,
+                                         const double *rcut, int M, double L0, double L1,
+                                         double L2, int n0, int n1, int n2, const double *kfrac,
+                                         int nk, double2 *S, double2 *T) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(q / MM);
+    const long e = q % MM;
+    const int mu = (int)(e / M), nu = (int)(e % M);
+    const double a = alpha[mu], b = alpha[nu];
+    const double xi = a * b / (a + b);
+    const double pre = pow(2.0 * sqrt(a * b) / (a + b), 1.5);
+    const double cut = __dadd_rn(rcut[mu], rcut[nu]);
+    const double cut2 = __dmul_rn(cut, cut);
+    const double d0 = __dsub_rn(center[mu * 3], center[nu * 3]);
+    const double d1 = __dsub_rn(center[mu * 3 + 1], center[nu * 3 + 1]);
+    const double d2 = __dsub_rn(center[mu * 3 + 2], center[nu * 3 + 2]);
+    const double *kf = kfrac + 3 * k;
+    double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+    for (int ix = -n0; ix <= n0; ++ix)
+      for (int iy = -n1; iy <= n1; ++iy)
+        for (int iz = -n2; iz <= n2; ++iz) {
+          const double r0 = __dsub_rn(d0, __dmul_rn((double)ix, L0));
+          const double r1 = __dsub_rn(d1, __dmul_rn((double)iy, L1));
+          const double r2 = __dsub_rn(d2, __dmul_rn((double)iz, L2));
+          const double R2 = __dadd_rn(__dadd_rn(__dmul_rn(r0, r0), __dmul_rn(r1, r1)),
+                                      __dmul_rn(r2, r2));
+          if (R2 < cut2) {
+            const int n[3] = {ix, iy, iz};
+            const double2 ph = k_phase(kf, n);
+            const double v = pre * exp(-xi * R2);
+            const double tv = xi * (3.0 - 2.0 * xi * R2) * v;
+            s.x += ph.x * v; s.y += ph.y * v;
+            t.x += ph.x * tv; t.y += ph.y * tv;
+          }
+        }
+    S[q] = s;
+    T[q] = t;
+  }
+}
+
+// ---- launchers ------------------------------------------------------------------------
+static int k_blocks(long n) {
+  long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+cudaError_t k_build_iA(const double *a, int nk, int M, double2 *iA, cudaStream_t s) {
+  k_build_iA_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(a, nk, M, iA);
+  return cudaGetLastError();
+}
+cudaError_t k_colscale(const double2 *Y, const double *x, double2 *X, int nk, int M, int mode,
+                       int *flags, cudaStream_t s) {
+  k_colscale_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(Y, x, X, nk, M, mode, flags);
+  return cudaGetLastError();
+}
+cudaError_t k_hermitize(double2 *X, int nk, int M, cudaStream_t s) {
+  k_hermitize_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(X, nk, M);
+  return cudaGetLastError();
+}
+cudaError_t k_dr(const KGeom &G, const double2 *D, double *DR, cudaStream_t s) {
+  k_dr_kernel<<<k_blocks((long)G.nR * G.M * G.M), 256, 0, s>>>(G, D, DR);
+  return cudaGetLastError();
+}
+cudaError_t k_hamiltonian(const KGeom &G, const double2 *T, const double *VR, double2 *H,
+                          cudaStream_t s) {
+  k_hamiltonian_kernel<<<k_blocks((long)G.nk * G.M * G.M), 256, 0, s>>>(G, T, VR, H);
+  return cudaGetLastError();
+}
+cudaError_t k_commutator(double2 *X, const double *f, int nk, int M, cudaStream_t s) {
+  k_commutator_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(X, f, nk, M);
+  return cudaGetLastError();
+}
+cudaError_t k_dtilde(double2 *X, const double *w, int nk, int M, cudaStream_t s) {
+  k_dtilde_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(X, w, nk, M);
+  return cudaGetLastError();
+}
+cudaError_t k_grad_vars(const double2 *GT, double *g, int nk, int M, cudaStream_t s) {
+  k_grad_vars_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(GT, g, nk, M);
+  return cudaGetLastError();
+}
+int k_kinetic_parts() { return 512; }
+cudaError_t k_energy(const double2 *D, const double2 *T, long n, double *part,
+                     const double *gridpart, int ngp, double *eterms, double *E, int *flags,
+                     cudaStream_t s) {
+  k_kinetic_kernel<<<k_kinetic_parts(), 256, 0, s>>>(D, T, n, part);
+  k_energy_kernel<<<1, 1024, 0, s>>>(part, k_kinetic_parts(), gridpart, ngp, eterms, E, flags);
+  return cudaGetLastError();
+}
+cudaError_t k_occupation(const double *eps, const double *kw, int nk, int M, double ne, double kT,
+                         double *f, double *mu, cudaStream_t s) {
+  k_occupation_kernel<<<1, 1024, 0, s>>>(eps, kw, nk, M, ne, kT, f, mu);
+  return cudaGetLastError();
+}
+cudaError_t k_diag(const double2 *C, const double2 *X, double *out, int nk, int M, cudaStream_t s) {
+  k_diag_kernel<<<k_blocks((long)nk * M), 256, 0, s>>>(C, X, out, nk, M);
+  return cudaGetLastError();
+}
+cudaError_t k_precond_parts(const double *eps, const double *f, const double *kw, int nk, int M,
+                            double gamma, double *den, double *wk, cudaStream_t s) {
+  k_precond_parts_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(eps, f, kw, nk, M, gamma, den, wk);
+  return cudaGetLastError();
+}
+cudaError_t k_overlap_kinetic(etdm_handle *h, cudaStream_t s) {
+  double rmax = 0.0;
+  std::vector<double> rc(h->M);
+  CUDA_TRY(cudaMemcpy(rc.data(), h->d_rcut, h->M * sizeof(double), cudaMemcpyDeviceToHost));
+  for (double r : rc) rmax = std::max(rmax, r);
+  int nimg[3];
+  for (int a = 0; a < 3; ++a) nimg[a] = (int)floor(2.0 * rmax / h->L[a]) + 1;
+  k_overlap_kinetic_kernel<<<k_blocks((long)h->nk * h->M * h->M), 256, 0, s>>>(
+      h->d_center, h->d_alpha, h->d_rcut, h->M, h->L[0], h->L[1], h->L[2], nimg[0], nimg[1],
+      nimg[2], h->d_kfrac, h->nk, h->d_kS, h->d_kT);
+  return cudaGetLastError();
+}
+
+}  // namespace etdm

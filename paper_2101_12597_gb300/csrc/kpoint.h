@@ -1,0 +1,63 @@
+// Internal declarations of the full-A / k-point path (kpoint.cu, grid.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace etdm {
+
+constexpr int kEigMax = 1024;  // largest matrix of the Hermitian eigensolver
+
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b] over a batch (strides sA, sB, sC
+// elements); op 0: X, op 1: X^dagger; row-major.
+struct ZgemmArgs {
+  const double2 *A, *B;
+  double2 *C;
+  int m, n, k;
+  int lda, ldb, ldc;
+  long sA, sB, sC;
+  int opa, opb;
+  double2 alpha, beta;
+};
+cudaError_t launch_zgemm(const ZgemmArgs &g, int batch, cudaStream_t s);
+cudaError_t zgemm_sq(const double2 *A, int opa, const double2 *B, int opb, double2 *C, int n,
+                     int batch, cudaStream_t s, double alpha = 1.0, double beta = 0.0);
+
+// Hermitian eigensolver: A (destroyed) = V diag(w) V^dagger, w ascending.
+size_t heev_work_bytes(int n, int batch);
+cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, void *work,
+                        int *flags, cudaStream_t s);
+
+
+}  // namespace etdm
+namespace etdm {
+// element-wise steps (kpoint.cu)
+cudaError_t k_build_iA(const double *a, int nk, int M, double2 *iA, cudaStream_t s);
+// X = Y diag(s): mode 0 s = x, mode 1 s = x^(-1/2), mode 2 s = exp(-i x)
+cudaError_t k_colscale(const double2 *Y, const double *x, double2 *X, int nk, int M, int mode,
+                       int *flags, cudaStream_t s);
+cudaError_t k_hermitize(double2 *X, int nk, int M, cudaStream_t s);
+cudaError_t k_dr(const KGeom &G, const double2 *D, double *DR, cudaStream_t s);
+cudaError_t k_hamiltonian(const KGeom &G, const double2 *T, const double *VR, double2 *H,
+                          cudaStream_t s);
+cudaError_t k_commutator(double2 *X, const double *f, int nk, int M, cudaStream_t s);
+cudaError_t k_dtilde(double2 *X, const double *w, int nk, int M, cudaStream_t s);
+cudaError_t k_grad_vars(const double2 *GT, double *g, int nk, int M, cudaStream_t s);
+int k_kinetic_parts();
+cudaError_t k_energy(const double2 *D, const double2 *T, long n, double *part,
+                     const double *gridpart, int ngp, double *eterms, double *E, int *flags,
+                     cudaStream_t s);
+cudaError_t k_occupation(const double *eps, const double *kw, int nk, int M, double ne, double kT,
+                         double *f, double *mu, cudaStream_t s);
+cudaError_t k_diag(const double2 *C, const double2 *X, double *out, int nk, int M, cudaStream_t s);
+cudaError_t k_precond_parts(const double *eps, const double *f, const double *kw, int nk, int M,
+                            double gamma, double *den, double *wk, cudaStream_t s);
+cudaError_t k_overlap_kinetic(etdm_handle *h, cudaStream_t s);
+// grid passes resolved by lattice offset (grid.cu)
+cudaError_t launch_rho_k(etdm_handle *h, const double *DR, double *rho, cudaStream_t s);
+cudaError_t launch_vmat_k(etdm_handle *h, const double *v, double *VR, cudaStream_t s);
+// set-up and one evaluation of the full-A path (kpath.cu)
+void init_kpoints(etdm_handle *h, const etdm_system *sys);
+void evaluate_k(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s);
+}  // namespace etdm

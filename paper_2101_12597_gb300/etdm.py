@@ -19,6 +19,7 @@ ETDM_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED",
           -5: "TIMEOUT", -6: "STATE", -7: "NUMERIC"}
 PRECISION = {"fp64": 0, "mixed": 1}
+PARAM = {"occvirt": 0, "full": 1}
 ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "order": (3, np.int32), "vext": (4, np.float64), "rho": (5, np.float64),
           "vtot": (6, np.float64), "H": (7, np.float64), "D": (8, np.float64),
@@ -28,7 +29,11 @@ ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "tile_ptr_tc": (15, np.int32), "tile_keys_tc": (16, np.int32),
           "tile_nu_tc": (17, np.int32), "vgroup_t0": (18, np.int32),
           "vgroup_nu": (19, np.int32), "doublings": (20, np.int32),
-          "status": (21, np.int32)}
+          "status": (21, np.int32),
+          # full-A path: complex [n_k][M][M] matrices and [n_k][M] vectors
+          "S_k": (0, np.complex128), "T_k": (1, np.complex128), "C0_k": (2, np.complex128),
+          "H_k": (7, np.complex128), "D_k": (8, np.complex128), "occ": (22, np.float64),
+          "eps_ref": (23, np.float64), "omega": (24, np.float64)}
 DIM_NAMES = ["M", "N", "V", "G", "n_tiles", "entries", "max_list", "tx", "ty",
              "tz", "sum_npt2", "precision"]
 
@@ -39,7 +44,8 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_stage_times", "etdm_last_error", "etdm_free",
            "etdm_lbfgs_direction_noalloc", "etdm_lbfgs_direction_noalloc_status",
            "etdm_init_batch", "etdm_num_systems", "etdm_system_layout", "etdm_system_handle",
-           "etdm_set_active", "etdm_minimize_converge", "etdm_pair_gemm"]
+           "etdm_set_active", "etdm_minimize_converge", "etdm_pair_gemm",
+           "etdm_set_reference"]
 STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
 
 
@@ -54,7 +60,11 @@ class EtdmSystem(ctypes.Structure):
                 ("box", ctypes.c_double * 3),
                 ("grid", ctypes.c_int32 * 3),
                 ("ion_sigma", ctypes.c_double),
-                ("n_electrons", ctypes.c_int32)]
+                ("n_electrons", ctypes.c_int32),
+                ("n_k", ctypes.c_int32),
+                ("k_frac", ctypes.POINTER(ctypes.c_double)),
+                ("k_w", ctypes.POINTER(ctypes.c_double)),
+                ("kT", ctypes.c_double)]
 
 
 class EtdmOptions(ctypes.Structure):
@@ -64,7 +74,8 @@ class EtdmOptions(ctypes.Structure):
                 ("beta0", ctypes.c_double),
                 ("device", ctypes.c_int32),
                 ("dense_blocks", ctypes.c_int32),
-                ("dense_tc", ctypes.c_int32)]
+                ("dense_tc", ctypes.c_int32),
+                ("param", ctypes.c_int32)]
 
 
 _lib = None
@@ -116,6 +127,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.etdm_system_handle.argtypes = [P, ctypes.c_int32]
     lib.etdm_system_handle.restype = P
     lib.etdm_set_active.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.etdm_set_reference.argtypes = [P, ctypes.c_int32, dp, dp]
     lib.etdm_last_error.argtypes = [P]
     lib.etdm_last_error.restype = ctypes.c_char_p
     lib.etdm_free.argtypes = [P]
@@ -201,10 +213,21 @@ def _system_struct(sysd, s=None):
         s.grid[a] = int(sysd["grid"][a])
     s.ion_sigma = float(sysd["ion_sigma"])
     s.n_electrons = int(sysd["n_electrons"])
+    if sysd.get("kpts") is not None:  # k-points: the full-A path
+        keep["k_frac"] = np.ascontiguousarray(np.atleast_2d(sysd["kpts"]), dtype=np.float64)
+        keep["k_w"] = np.ascontiguousarray(sysd["kw"], dtype=np.float64)
+        s.n_k = len(keep["k_w"])
+        s.k_frac = _dptr(keep["k_frac"])
+        s.k_w = _dptr(keep["k_w"])
+        s.kT = float(sysd["kT"])
+    else:
+        s.n_k = 0
+        s.kT = float(sysd.get("kT", 0.0))
     return s, keep
 
 
-def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc=0):
+def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc=0,
+             param="occvirt"):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision]
@@ -214,21 +237,29 @@ def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_
     o.device = device
     o.dense_blocks = dense_blocks
     o.dense_tc = dense_tc
+    o.param = PARAM[param]
     return o
 
 
 class ETDM:
-    """One system on one GPU: the handle of etdm_init_basis."""
+    """One system on one GPU: the handle of etdm_init_basis.  A system dict
+    with "kpts" (with "kw" and "kT"), or param="full", selects the full-A path:
+    the variables are then a flat vector of n_k M^2 reals (Re a_ij for i < j,
+    then Im a_ij for i <= j, per k-point)."""
 
     def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
-                 device=0, dense_blocks=0, dense_tc=0):
+                 device=0, dense_blocks=0, dense_tc=0, param=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
         self.lib = load_library()
         self.device = device
         s, self._keep = _system_struct(sysd)
-        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc)
+        if param is None:
+            param = "full" if sysd.get("kpts") is not None else "occvirt"
+        self.full = param == "full"
+        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc,
+                     param)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
@@ -252,6 +283,14 @@ class ETDM:
         self.lib.etdm_layout(self.h, dims)
         self.dims = dict(zip(DIM_NAMES, [int(x) for x in dims]))
         self.M, self.N, self.V = self.dims["M"], self.dims["N"], self.dims["V"]
+        off, ln = ctypes.c_int64(), ctypes.c_int64()
+        self.lib.etdm_system_layout(self.h, 0, ctypes.byref(off), ctypes.byref(ln))
+        self.nvar = int(ln.value)
+
+    @property
+    def var_shape(self):
+        """Shape of a and g: N x V (occupied-virtual) or a flat n_k M^2 vector (full A)."""
+        return (self.nvar,) if getattr(self, "full", False) else (self.N, self.V)
 
     # -- helpers ----------------------------------------------------------------
     def _raise(self, rc):
@@ -265,14 +304,14 @@ class ETDM:
     def energy_grad(self, a, want_grad=True, E=None, g=None, stream=None):
         """E and dE/dA_ov for a (N x V) on the device; returns (E[1], g or None)."""
         import torch
-        self._check_tensor(a, (self.N, self.V))
+        self._check_tensor(a, self.var_shape)
         if E is None:
             E = torch.empty(1, dtype=torch.float64, device=self.dev)
         _require(E, self.dev, "E", numel=1)
         if want_grad and g is None:
-            g = torch.empty((self.N, self.V), dtype=torch.float64, device=self.dev)
+            g = torch.empty(self.var_shape, dtype=torch.float64, device=self.dev)
         if want_grad:
-            self._check_tensor(g, (self.N, self.V), "g")
+            self._check_tensor(g, self.var_shape, "g")
         rc = self.lib.etdm_energy_grad(self.h, ctypes.c_void_p(a.data_ptr()),
                                        ctypes.c_void_p(E.data_ptr()),
                                        ctypes.c_void_p(g.data_ptr()) if want_grad else None,
@@ -282,10 +321,10 @@ class ETDM:
 
     def energy_grad_host(self, a, want_grad=True):
         a = np.ascontiguousarray(a, dtype=np.float64)
-        if a.shape != (self.N, self.V):
-            raise ValueError(f"a: expected shape {(self.N, self.V)}, got {a.shape}")
+        if a.shape != self.var_shape:
+            raise ValueError(f"a: expected shape {self.var_shape}, got {a.shape}")
         E = np.zeros(1)
-        g = np.zeros((self.N, self.V)) if want_grad else None
+        g = np.zeros(self.var_shape) if want_grad else None
         rc = self.lib.etdm_energy_grad_host(self.h, _dptr(a), _dptr(E),
                                             _dptr(g) if want_grad else None)
         self._raise(rc)
@@ -295,9 +334,9 @@ class ETDM:
         """P^(k) o g (Eq. 33) with the current beta^(k) (Eq. 34): g (N x V) on the
         device; returns `out` (created when None)."""
         import torch
-        self._check_tensor(g, (self.N, self.V), "g")
+        self._check_tensor(g, self.var_shape, "g")
         out = torch.empty_like(g) if out is None else out
-        self._check_tensor(out, (self.N, self.V), "out")
+        self._check_tensor(out, self.var_shape, "out")
         self._raise(self.lib.etdm_precondition(self.h, ctypes.c_void_p(g.data_ptr()),
                                                ctypes.c_void_p(out.data_ptr()),
                                                _stream_ptr(stream)))
@@ -308,10 +347,10 @@ class ETDM:
         (a - a_prev, g - g_prev) when its curvature is positive, updates beta
         (Eq. 34) and runs the two-loop recursion with H0 = P^(k).  Returns `out`."""
         import torch
-        self._check_tensor(a, (self.N, self.V))
-        self._check_tensor(g, (self.N, self.V), "g")
+        self._check_tensor(a, self.var_shape)
+        self._check_tensor(g, self.var_shape, "g")
         out = torch.empty_like(g) if out is None else out
-        self._check_tensor(out, (self.N, self.V), "out")
+        self._check_tensor(out, self.var_shape, "out")
         self._raise(self.lib.etdm_lbfgs_step(self.h, ctypes.c_void_p(a.data_ptr()),
                                              ctypes.c_void_p(g.data_ptr()),
                                              ctypes.c_void_p(out.data_ptr()),
@@ -322,9 +361,31 @@ class ETDM:
         """Erase the L-BFGS memory (no pairs, no previous point, beta = beta0)."""
         self._raise(self.lib.etdm_lbfgs_reset(self.h))
 
+    def set_reference(self, C0, occ=None):
+        """Replace the reference orbitals (Eq. 6-7) and, on the full-A path,
+        optionally the occupations; re-derives the Eq. 33 orbital energies and
+        erases the L-BFGS memory.  C0: (M, M) real (occupied-virtual) or
+        (n_k, M, M) complex (full A), columns are orbitals; occ: (n_k, M)."""
+        if self.full:
+            C0 = np.ascontiguousarray(C0, dtype=np.complex128)
+            want = (self.nvar // (self.M * self.M), self.M, self.M)
+        else:
+            C0 = np.ascontiguousarray(C0, dtype=np.float64)
+            want = (self.M, self.M)
+        if C0.shape != want:
+            raise ValueError(f"C0: expected shape {want}, got {C0.shape}")
+        ov = None
+        if occ is not None:
+            ov = np.ascontiguousarray(occ, dtype=np.float64)
+            if not self.full or ov.shape != want[:2]:
+                raise ValueError("occ: only on the full-A path, shape (n_k, M)")
+        self._raise(self.lib.etdm_set_reference(
+            self.h, 0, C0.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            _dptr(ov) if ov is not None else None))
+
     def minimize(self, a, n_steps, stream=None):
         """Runs n_steps ETDM iterations in place on a; returns (E, alpha, trials)."""
-        self._check_tensor(a, (self.N, self.V))
+        self._check_tensor(a, self.var_shape)
         E = np.zeros(n_steps + 1)
         al = np.zeros(n_steps + 1)
         tr = np.zeros(n_steps + 1, dtype=np.int32)
@@ -339,7 +400,7 @@ class ETDM:
         """ETDM iterations in place on a until the Eq. 45 residual is at most tol
         (Hartree^2; default the paper's 1e-10 eV^2) or max_steps; returns
         (steps, E, alpha, trials, residual), the histories cut to steps + 1."""
-        self._check_tensor(a, (self.N, self.V))
+        self._check_tensor(a, self.var_shape)
         K = max_steps + 1
         E, al, res = np.zeros(K), np.zeros(K), np.zeros(K)
         tr = np.zeros(K, dtype=np.int32)

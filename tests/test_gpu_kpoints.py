@@ -1,0 +1,141 @@
+"""GPU parity of the full-A path over k-points (Bloch basis of Eq. 5, the full
+skew-Hermitian A(k) of Eq. 8 and 22-24, exp(A) by Eq. 35, the Eq. 39-41
+adjoint, fractional occupations fixed at the reference, the Sec. 3.3
+preconditioner) against the k-point oracle, element by element.
+
+The GPU builds its own reference (generalized eigenvectors of h_core(k) with
+S(k), Fermi-Dirac occupations); eigenvector phases are arbitrary, so what the
+two sides share there is what is phase-free: eigenvalues, occupations, D at
+A = 0, E(0) and |g(0)|.  For E(A) and g(A) at A != 0 the test hands the
+oracle's C0(k) and occupations to the GPU (etdm_set_reference)."""
+import numpy as np
+import pytest
+
+import etdm_synth as synth
+from oracle.etdm_kpoints import BlochOracle
+from oracle.etdm_oracle import minimize
+
+pytestmark = pytest.mark.gpu
+
+CASES = {"tiny": lambda: synth.tiny_crystal(rcut_ang=3.0), "small": synth.small_crystal}
+
+
+@pytest.fixture(scope="module")
+def cases():
+    from paper_2101_12597_gb300.etdm import ETDM
+    out = {}
+    for name, make in CASES.items():
+        d = make()
+        out[name] = (d, BlochOracle(d), ETDM(d))
+    yield out
+    for _, _, s in out.values():
+        s.close()
+
+
+def _k_blocks(x, nk, M):
+    return np.asarray(x).reshape(nk, M, M)
+
+
+@pytest.mark.parametrize("which", list(CASES))
+def test_kpoint_setup_against_oracle(which, cases):
+    """S(k), T(k), the reference eigenvalues, the occupations, D(A = 0) and E(0)."""
+    import torch
+    d, bo, s = cases[which]
+    ref = bo.reference_k()
+    nk, M = bo.nk, bo.M
+    Sk = _k_blocks(s.get_array("S_k"), nk, M)
+    Tk = _k_blocks(s.get_array("T_k"), nk, M)
+    for k in range(nk):
+        S, T = bo.overlap_kinetic_k(k)
+        assert np.abs(Sk[k] - S).max() <= 1e-13 * np.abs(S).max()
+        assert np.abs(Tk[k] - T).max() <= 1e-13 * np.abs(T).max()
+    eps = s.get_array("eps_ref").reshape(nk, M)
+    occ = s.get_array("occ").reshape(nk, M)
+    for k in range(nk):
+        assert np.abs(eps[k] - ref["eps_core"][k]).max() < 1e-10
+        assert np.abs(occ[k] - ref["f"][k]).max() < 1e-10
+    assert abs(occ.sum() - d["n_electrons"]) < 1e-10
+    # D(A = 0) = C0 f C0^dagger is free of the eigenvector phases
+    a0 = torch.zeros(s.var_shape, dtype=torch.float64, device="cuda")
+    E, g = s.energy_grad(a0)
+    Dk = _k_blocks(s.get_array("D_k"), nk, M)
+    for k in range(nk):
+        Dref = (ref["C0"][k] * ref["f"][k][None, :]) @ ref["C0"][k].conj().T
+        assert np.abs(Dk[k] - Dref).max() <= 1e-11 * np.abs(Dref).max()
+    E_ref, g_ref = bo.energy_grad(np.zeros(bo.nk * bo.nvar))
+    print(f"{which}: E(0) GPU {float(E.item()):.12f} oracle {E_ref:.12f}")
+    assert abs(float(E.item()) - E_ref) < 1e-9
+    # |g(0)| per k-point (2 |L|_F^2 at A = 0: unitary-invariant)
+    gg = g.cpu().numpy().reshape(nk, -1)
+    gr = g_ref.reshape(nk, -1)
+    for k in range(nk):
+        n1, n2 = np.linalg.norm(gg[k]), np.linalg.norm(gr[k])
+        assert abs(n1 - n2) <= 1e-9 * max(1.0, n2)
+
+
+@pytest.mark.parametrize("which", list(CASES))
+def test_kpoint_energy_gradient_parity(which, cases):
+    """With the oracle's reference: E, every gradient entry of every k-point,
+    rho, v, H(k) and the eigenvalues of iA(k) at the seeded A."""
+    import torch
+    d, bo, s = cases[which]
+    ref = bo.reference_k()
+    nk, M = bo.nk, bo.M
+    s.set_reference(np.array(ref["C0"]), np.array(ref["f"]))
+    a = torch.tensor(d["a0"], dtype=torch.float64, device="cuda")
+    E, g = s.energy_grad(a)
+    torch.cuda.synchronize()
+    s.check()
+    E_ref, g_ref, ex = bo.energy_grad(d["a0"], want=True)
+    g = g.cpu().numpy()
+    dE = abs(float(E.item()) - E_ref)
+    gmax = np.abs(g_ref).max()
+    per_k = [np.abs(g[k * bo.nvar:(k + 1) * bo.nvar] - g_ref[k * bo.nvar:(k + 1) * bo.nvar]).max()
+             / gmax for k in range(nk)]
+    print(f"{which}: |dE|={dE:.3e} Ha  grad err per k={max(per_k):.3e} (max|g|={gmax:.3e})")
+    assert dE < 1e-9
+    assert max(per_k) <= 1e-9
+    rho = s.get_array("rho").reshape(tuple(bo.n))
+    assert np.abs(rho - ex["rho"]).max() <= 1e-11 * np.abs(ex["rho"]).max()
+    v = s.get_array("vtot").reshape(tuple(bo.n))
+    assert np.abs(v - ex["v"]).max() <= 1e-11 * np.abs(ex["v"]).max()
+    Hk = _k_blocks(s.get_array("H_k"), nk, M)
+    om = s.get_array("omega").reshape(nk, M)
+    for k in range(nk):
+        Href = ex["k"][k]["H"]
+        assert np.abs(Hk[k] - Href).max() <= 1e-11 * np.abs(Href).max()
+        A = bo.A_of(d["a0"][k * bo.nvar:(k + 1) * bo.nvar])
+        assert np.abs(om[k] - np.linalg.eigvalsh(1j * A)).max() < 1e-12
+
+
+@pytest.mark.parametrize("which", list(CASES))
+def test_kpoint_precondition(which, cases):
+    """P^(k) o g with beta^(0) and the k-point weight on beta (Eq. 33-34, Sec. 3.3)."""
+    import torch
+    d, bo, s = cases[which]
+    ref = bo.reference_k()
+    s.set_reference(np.array(ref["C0"]), np.array(ref["f"]))
+    eps = bo.orbital_energies()
+    assert np.abs(s.get_array("eps").reshape(bo.nk, bo.M) - np.array(eps)).max() < 1e-10
+    g = torch.tensor(synth.direction(bo.nk * bo.nvar, 5), dtype=torch.float64, device="cuda")
+    pg = s.precondition(g).cpu().numpy()
+    want = bo.precond(eps, 1.0) * g.cpu().numpy()
+    assert np.abs(pg - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_kpoint_minimization_trajectory(cases):
+    """Eight L-BFGS steps from A = 0 on the tiny crystal: energies, step
+    lengths and trial counts of the accepted steps equal the oracle's."""
+    import torch
+    d, bo, s = cases["tiny"]
+    ref = bo.reference_k()
+    s.set_reference(np.array(ref["C0"]), np.array(ref["f"]))
+    a = torch.zeros(s.var_shape, dtype=torch.float64, device="cuda")
+    E, al, tr = s.minimize(a, 8)
+    hist, a_ref = minimize(bo, np.zeros(bo.nk * bo.nvar), 8)
+    E_ref = np.array([h[0] for h in hist])
+    print("tiny crystal trajectory:", np.abs(E - E_ref).max(), E_ref[0] - E_ref[-1])
+    assert np.abs(E - E_ref).max() < 1e-9
+    assert np.abs(al - np.array([h[1] for h in hist])).max() < 1e-6
+    assert list(tr) == [h[2] for h in hist]
+    assert np.abs(a.cpu().numpy() - a_ref).max() < 1e-6
