@@ -11,7 +11,7 @@ preconditioner and the line search, whose trials are energy+gradient
 evaluations); `value` counts every energy+gradient evaluation in it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload water576|water32|small]
+                    [--workload water576|water32|small|molecules148|crystal64]
 
 Under torchrun each rank runs an independent replica (the path has no
 exchange step); value = all evaluations / max time over ranks.
@@ -40,6 +40,9 @@ WORKLOADS = {
     "small": "small molecule: 8 atoms, M=16, N=4, 32^3 grid, 6.4 A box",
     "molecules148": "molecules148: 148 molecules of 2-20 atoms (M 4-60), each on its own "
                     "48^3 grid over a 9.6 A box, r_c=4 A, evaluated as one batch",
+    "crystal64": "crystal64: 64 atoms, M=512, 8 k-points (2x2x2 Monkhorst-Pack), 256 "
+                 "electrons, kT=0.1 eV, 56^3 grid over an 11.2 A cell, r_c=4 A, full "
+                 "complex A(k) per k-point",
 }
 # workloads whose resident operands (basis slices, grids) exceed the 129 MB L2:
 # the timed steps run back to back; the small molecule fits in L2 and flushes it
@@ -51,7 +54,8 @@ def workload_system(name):
     import etdm_synth as synth
     return {"water32": synth.config_water32, "small": synth.config_small_molecule,
             "water576": synth.config_water576,
-            "molecules148": synth.config_molecules148}[name]()
+            "molecules148": synth.config_molecules148,
+            "crystal64": synth.config_crystal64}[name]()
 
 
 FP64_PEAK_TFLOPS = 1.25      # nominal FP64 rate of a GB300 (no measured figure)
@@ -256,6 +260,21 @@ def run_reference(args):
         t = sum(_plane_sample(o, D, v, (args.warmup + k) % n) for k in range(args.steps))
         dt = t * n  # seconds of the K whole evaluations the samples stand for
         sample = PLANE_SAMPLE.format(k=1, n=n, w=w) + " (one x-plane per step)"
+    elif args.workload == "crystal64":
+        # each step: one x-plane of one k-point's oracle grid work, scaled to a
+        # whole evaluation (8 k-points; an oracle evaluation takes minutes)
+        from oracle.etdm_kpoints import BlochOracle
+        o = BlochOracle(d, cache_x=False)
+        rng = np.random.default_rng(0)
+        C = rng.normal(size=(o.M, o.M)) + 1j * rng.normal(size=(o.M, o.M))
+        D = (C @ C.conj().T) / o.M
+        vv = rng.normal(size=o.G)
+        n = int(o.n[0])
+        for k in range(args.warmup):
+            _kplane_sample(o, D, vv, k % n)
+        t = sum(_kplane_sample(o, D, vv, (args.warmup + k) % n) for k in range(args.steps))
+        dt = t * n * o.nk
+        sample = KPLANE_SAMPLE.format(k=1, n=n, nk=o.nk, w=w) + " (one x-plane per step)"
     elif args.workload == "molecules148":
         # each step: one molecule's oracle evaluation, the molecules in turn
         # (set-up not timed); the unit is molecule evaluations per second
@@ -751,6 +770,129 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def _kplane_sample(o, D, v, i):
+    """Seconds the k-point oracle takes for one x-plane of one k-point's grid
+    work: the Bloch basis on the plane (Eq. 5), the density there (Eq. 2) and
+    the plane's part of the potential matrix (Eq. 11)."""
+    per = int(o.n[1] * o.n[2])
+    t0 = time.perf_counter()
+    Xp = o.basis_plane_k(i, 0)
+    np.einsum("pa,pa->p", Xp @ D, Xp.conj()).real
+    Xp.conj().T @ (v[i * per:(i + 1) * per, None] * Xp)
+    return time.perf_counter() - t0
+
+
+KPLANE_SAMPLE = ("the k-point oracle's grid work (Bloch basis values, density, potential-"
+                 "matrix part) on {k} of the {n} x-planes of one k-point of {w}, scaled by "
+                 "{n}/{k} x {nk} k-points to one evaluation; the dense steps (eigendecomposition "
+                 "of iA(k), M x M complex products) and the FFTs are left out")
+
+
+def run_kpoints(args):
+    """The full-A path over k-points (FP64): K L-BFGS steps of one minimization
+    from A = 0, the reference built on the device (generalized eigenvectors of
+    h_core(k), Fermi-Dirac occupations)."""
+    import torch
+    from paper_2101_12597_gb300 import build as b
+    from paper_2101_12597_gb300.etdm import ETDM
+
+    world, rank, local = dist_setup(args.gpus)
+    b.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    d = workload_system(args.workload)
+    solver = ETDM(d, precision="fp64", device=local)
+    a0 = torch.zeros(solver.var_shape, dtype=torch.float64, device=dev)
+    if args.profile_once:
+        solver.energy_grad(torch.tensor(d["a0"], dtype=torch.float64, device=dev))
+        torch.cuda.synchronize()
+        solver.check()
+        print(json.dumps({"profile_once": True, "workload": args.workload}))
+        return
+    a = a0.clone()
+    if args.warmup:
+        solver.minimize(a, args.warmup)
+    torch.cuda.synchronize()
+    solver.lbfgs_reset()
+    a = a0.clone()
+    solver.set_profiling(True)
+    solver.stage_times()
+    clocks = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record()
+    E_h, al_h, tr_h = solver.minimize(a, args.steps)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_n, launches = solver.stage_times()
+    solver.set_profiling(False)
+    evals = int(tr_h.sum())
+    t_max = reduce_max(total_ms, world, dev)
+    all_evals = reduce_sum(evals, world, dev)
+    value = all_evals / (t_max / 1e3)
+    # end to end through the host-buffer entry point
+    a_host = np.ascontiguousarray(d["a0"])
+    solver.energy_grad_host(a_host)
+    torch.cuda.synchronize()
+    n_e2e = min(args.steps, 5)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        solver.energy_grad_host(a_host)
+    e2e_dt = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * n_e2e / e2e_dt, "unit": "evals/s",
+           "h2d_bytes_per_step": 8 * solver.nvar, "d2h_bytes_per_step": 8 * solver.nvar + 8,
+           "evals": n_e2e}
+    per_eval = {k: v / max(evals, 1) for k, v in stage_ms.items()}
+    # dominant stage: FP64 ALU bound (complex products, the eigensolver)
+    M, nk = solver.M, solver.nvar // (solver.M * solver.M)
+    zflop = 8.0 * M ** 3 * nk  # one batched complex product
+    roof = {"bound": "alu", "kernel": "zgemm_kernel (dense forward + reverse: 9 batched "
+            "complex products per evaluation)",
+            "achieved": 9 * zflop / ((per_eval["dense_fwd"] + per_eval["dense_rev"]) * 1e-3) / 1e12,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+            "peak_source": "nominal FP64 rate of a GB300 (no measured FP64 figure)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "precision": "fp64",
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (complex matrices of 8 k-points, grids), "
+                         "steps back to back in one minimization",
+                   "evals_timed": int(all_evals), "E_first": float(E_h[0]),
+                   "E_last": float(E_h[-1]), "stage_ms_per_eval": per_eval,
+                   "M": M, "n_k": nk},
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle.etdm_kpoints import BlochOracle
+        o = BlochOracle(d, cache_x=False)
+        rng = np.random.default_rng(0)
+        C = rng.normal(size=(o.M, o.M)) + 1j * rng.normal(size=(o.M, o.M))
+        D = (C @ C.conj().T) / o.M
+        v = rng.normal(size=o.G)
+        t, k = 0.0, 0
+        while k < int(o.n[0]) and (k == 0 or t < 10.0):
+            t += _kplane_sample(o, D, v, k)
+            k += 1
+        n = int(o.n[0])
+        line["cpu_baseline"] = {"value": 1.0 / (t / k * n * o.nk), "unit": "evals/s",
+                                "cores": oracle_threads(), "kind": "oracle",
+                                "sample": KPLANE_SAMPLE.format(k=k, n=n, nk=o.nk,
+                                                               w=WORKLOADS[args.workload])}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -773,6 +915,8 @@ def main():
         run_reference(args)
     elif args.workload == "molecules148":
         run_batch(args)
+    elif args.workload == "crystal64":
+        run_kpoints(args)
     else:
         run_ours(args)
 

@@ -68,6 +68,16 @@ enum {
                              the k-points one after another */
 };
 
+enum {
+  ETDM_EXPM_EIG = 0, /* full A: exp(A(k)) = W exp(-i Omega) W^dagger from the FP64
+                        eigendecomposition iA(k) = W Omega W^dagger (Eq. 35) and
+                        the exact gradient of Eq. 39-41 */
+  ETDM_EXPM_SS = 1   /* full A: exp(A(k)) by scaling and squaring (Eq. 38), with
+                        the approximate gradient G ~ L^T (Eq. 42; exact at A = 0)
+                        and, in etdm_minimize, the reference updates of Sec. 3.5
+                        chosen by etdm_options.ref_update */
+};
+
 /* One periodic system (Eq. 3-5).  All host pointers, read during
  * etdm_init_basis only.  n_k = 0 is the Gamma point alone; n_k >= 1 selects
  * the full-A path over the given k-points (Bloch functions of Eq. 5 without
@@ -111,6 +121,14 @@ typedef struct {
                            ETDM_PARAM_FULL (needs ETDM_PREC_FP64; n_k = 0 then
                            means the Gamma point with weight 1); n_k >= 1
                            implies ETDM_PARAM_FULL */
+  int32_t expm;         /* full A: ETDM_EXPM_EIG (default) or ETDM_EXPM_SS */
+  int32_t ref_update;   /* ETDM_EXPM_SS: reference updates C0 <- C0 exp(A), A <- 0
+                           in etdm_minimize (Sec. 3.5), each followed by erasing
+                           the L-BFGS pairs and taking the Eq. 33 orbital
+                           energies afresh at A = 0: 0 never (default), n > 0
+                           after every n steps, -1 when |L| < 3 |[A, L]|
+                           (Frobenius norms over all k-points, checked before
+                           each step) */
 } etdm_options;
 
 /* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1,
@@ -300,6 +318,10 @@ enum {
   ETDM_STAGE_VMAT = 3,      /* grid -> basis Hamiltonian */
   ETDM_STAGE_DENSE_REV = 4, /* energy sum and analytic gradient */
   ETDM_STAGE_LBFGS = 5,     /* two-loop update */
+  ETDM_STAGE_EIG = 6,       /* full A: exp(A(k)) itself, by the eigendecomposition
+                               of iA(k) (Eq. 35) or by scaling and squaring
+                               (Eq. 38); the rest of the dense forward work is
+                               DENSE_FWD */
   ETDM_NSTAGES = 8
 };
 int etdm_set_profiling(etdm_handle *h, int on);

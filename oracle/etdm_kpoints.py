@@ -46,7 +46,7 @@ import math
 
 import numpy as np
 
-from .etdm_oracle import GAMMA, Oracle, _fsum
+from .etdm_oracle import GAMMA, LBFGS, Oracle, _fsum, line_search
 
 
 def fermi_dirac(x):
@@ -217,6 +217,27 @@ class BlochOracle(Oracle):
         self._kref = dict(S=S, T=T, hcore=H0, C0=C0, eps_core=eps, mu=mu, f=f, vext=vext)
         return self._kref
 
+    def set_reference(self, C0, f=None):
+        """Replace the reference orbitals C0(k) that O(k) = C0(k) exp(A(k))
+        rotates (Eq. 6-7) and, optionally, the occupations; the rest of the
+        reference (S, T, v_ext) stays."""
+        ref = dict(self.reference_k())
+        ref["C0"] = [np.asarray(c, dtype=np.complex128) for c in C0]
+        if f is not None:
+            ref["f"] = [np.asarray(x, dtype=np.float64) for x in f]
+        self._kref = ref
+
+    def lowdin_reference(self):
+        """S(k)^(-1/2) per k-point (a matrix function, free of the eigenvector
+        phases): the Loewdin orthonormal orbitals of the Bloch basis."""
+        out = []
+        for k in range(self.nk):
+            S, _ = self.overlap_kinetic_k(k)
+            S = 0.5 * (S + S.conj().T)
+            w, Q = np.linalg.eigh(S)
+            out.append((Q / np.sqrt(w)) @ Q.conj().T)
+        return out
+
     # ---- variables <-> A(k) (Eq. 22-24) ----------------------------------------
     def A_of(self, v):
         """Skew-Hermitian A from the M^2 real variables of one k-point."""
@@ -282,6 +303,100 @@ class BlochOracle(Oracle):
         if want:
             return E, g, dict(terms=terms, rho=rho, v=v, k=extra)
         return E, g
+
+    # ---- scaling and squaring with the approximate gradient (Eq. 38, 42-44) -----
+    @staticmethod
+    def expm_ss(A):
+        """Eq. 38: exp(A) = exp(A / 2^m)^(2^m) with a [q, q] Pade approximant of
+        exp(A / 2^m), m and q chosen by the algorithm of Al-Mohy and Higham
+        (SciPy's expm, the implementation the paper names)."""
+        from scipy.linalg import expm
+        return expm(A)
+
+    def energy_grad_approx(self, a, want=False):
+        """E with exp(A(k)) by Eq. 38 and the approximate gradient of Eq. 42,
+        G ~ L^T (the first term of the Eq. 19 expansion; exact at A = 0), in
+        the real variables of Eq. 20-24."""
+        ref = self.reference_k()
+        orbs = []
+        for k in range(self.nk):
+            A = self.A_of(a[k * self.nvar:(k + 1) * self.nvar])
+            orbs.append((A, ref["C0"][k] @ self.expm_ss(A)))
+        Ds = self.density_matrices(orbs)
+        E, terms, rho, v = self.energy_terms_k(Ds)
+        g = np.empty(self.nk * self.nvar)
+        Ls = []
+        for k, (A, O) in enumerate(orbs):
+            H = ref["T"][k] + self.potential_matrix_k(v, k)
+            Hmo = O.conj().T @ H @ O
+            f = ref["f"][k]
+            L = f[:, None] * Hmo - Hmo * f[None, :]
+            fac = np.where(np.eye(self.M, dtype=bool), 0.5, 1.0)
+            g[k * self.nvar:(k + 1) * self.nvar] = self.vars_of_grad(fac * L.T)
+            Ls.append((A, L, H))
+        if want:
+            return E, g, dict(terms=terms, rho=rho, v=v, L=Ls)
+        return E, g
+
+    @staticmethod
+    def commutator_test(Ls, eps=3.0):
+        """The reference-update test of Sec. 3.5 as read here: update when
+        |L| < eps |[A, L]| (Frobenius norms over all k-points), eps = 3."""
+        nL = math.sqrt(sum(float(np.vdot(L, L).real) for _, L, _ in Ls))
+        nC = math.sqrt(sum(float(np.vdot(A @ L - L @ A, A @ L - L @ A).real)
+                           for A, L, _ in Ls))
+        return nL < eps * nC, nL, nC
+
+    def minimize_ss(self, a0, n_steps, ref_update=-1):
+        """ETDM with exp by Eq. 38 and the approximate gradient of Eq. 42 (the
+        paper's "ss" route), with reference updates C <- C exp(A), A <- 0:
+        ref_update = n > 0 after every n steps, -1 by the Sec. 3.5 test, 0
+        never.  After an update the L-BFGS memory is erased (Sec. 3.5) and the
+        Eq. 33 orbital energies are taken afresh at the new reference.
+        Returns the (E, alpha, trials) history, the final variables and the
+        number of updates."""
+        eps = self.orbital_energies()
+        lb = LBFGS(lambda beta: self.precond(eps, beta))
+        a = np.array(a0, dtype=np.float64)
+        E, g, ex = self.energy_grad_approx(a, want=True)
+        hist = [(E, 0.0, 1)]
+        since, updates = 0, 0
+        for _ in range(n_steps):
+            if ref_update > 0:
+                upd = since >= ref_update
+            elif ref_update < 0:
+                upd = self.commutator_test(ex["L"])[0]
+            else:
+                upd = False
+            if upd:
+                ref = self.reference_k()
+                self.set_reference([ref["C0"][k] @ self.expm_ss(
+                    self.A_of(a[k * self.nvar:(k + 1) * self.nvar])) for k in range(self.nk)])
+                a = np.zeros_like(a)
+                lb.reset()
+                eps = self.orbital_energies()
+                lb.pfn = lambda beta, eps=eps: self.precond(eps, beta)
+                E, g, ex = self.energy_grad_approx(a, want=True)
+                since, updates = 0, updates + 1
+            p = lb.step(a, g)
+            d0 = float(np.vdot(g, p))
+            if not d0 < 0.0:
+                lb.reset()
+                p = -self.precond(eps, lb.beta) * g
+                lb.a_prev, lb.g_prev = a.copy(), g.copy()
+                d0 = float(np.vdot(g, p))
+
+            def phi(alpha, a=a, p=p):
+                Et, gt, ext = self.energy_grad_approx(a + alpha * p, want=True)
+                return Et, float(np.vdot(gt, p)), (gt, ext)
+
+            alpha, Et, _, pay, trials = line_search(phi, E, d0)
+            if pay is not None:
+                E, (g, ex) = Et, pay
+                a = a + alpha * p
+            hist.append((E, alpha, trials))
+            since += 1
+        return hist, a, updates
 
     # ---- preconditioner (Eq. 33-34, k-point weight on beta) -----------------------
     def orbital_energies(self):

@@ -60,27 +60,6 @@ int check_flags(etdm_handle *h, cudaStream_t s) {
   return ETDM_OK;
 }
 
-// Optional stage timing: events around a stage on the calling stream.
-struct StageTimer {
-  etdm_handle *h;
-  cudaStream_t s;
-  int stage;
-  cudaEvent_t e0 = nullptr;
-  StageTimer(etdm_handle *hh, cudaStream_t ss, int st) : h(hh), s(ss), stage(st) {
-    if (h->profiling) {
-      CUDA_TRY(cudaEventCreate(&e0));
-      CUDA_TRY(cudaEventRecord(e0, s));
-    }
-  }
-  void done() {
-    if (!h->profiling) return;
-    cudaEvent_t e1;
-    CUDA_TRY(cudaEventCreate(&e1));
-    CUDA_TRY(cudaEventRecord(e1, s));
-    h->prof_events.push_back({stage, {e0, e1}});
-  }
-};
-
 // One energy (+ gradient) evaluation, all on `s`.
 void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s) {
   if (h->kpath) {
@@ -203,6 +182,13 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
       bad("unknown param");
   } else if (opt && opt->param != ETDM_PARAM_OCCVIRT) {
     bad("unknown param");
+  }
+  if (opt) {
+    if (opt->expm != ETDM_EXPM_EIG && opt->expm != ETDM_EXPM_SS) bad("unknown expm");
+    if (opt->expm == ETDM_EXPM_SS && !full) bad("expm = ETDM_EXPM_SS needs the full-A path");
+    if (opt->ref_update < -1) bad("ref_update must be >= -1");
+    if (opt->ref_update != 0 && opt->expm != ETDM_EXPM_SS)
+      bad("ref_update needs expm = ETDM_EXPM_SS");
   }
   if (opt) {
     if (opt->precision != ETDM_PREC_FP64 && opt->precision != ETDM_PREC_MIXED)
@@ -379,6 +365,8 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     }
     h->kT = sys->kT;
     h->n_elec = sys->n_electrons;
+    h->kexpm = o.expm;
+    h->ref_every = o.ref_update;
   }
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
@@ -722,6 +710,8 @@ void etdm_default_options(etdm_options *opt) {
   opt->dense_blocks = 0;
   opt->dense_tc = 0;
   opt->param = ETDM_PARAM_OCCVIRT;
+  opt->expm = ETDM_EXPM_EIG;
+  opt->ref_update = 0;
 }
 
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {
@@ -865,13 +855,8 @@ int etdm_set_reference(etdm_handle *h, int32_t sys, const double *C0_host, const
         CUDA_TRY(cudaMemcpy(h->d_kf, occ_host, nf * 8, cudaMemcpyHostToDevice));
       }
       CUDA_TRY(cudaMemcpy(h->d_kC0, C0_host, (size_t)h->nk * MM * 16, cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemsetAsync(h->d_a, 0, h->nvar * 8, s));
-      evaluate_k(h, h->d_a, h->d_E, h->d_g, s);
+      refresh_reference_k(h, s);
       check_flags(h, s);
-      CUDA_TRY(zgemm_sq(h->d_kH, 0, h->d_kC0, 0, h->d_kX1, h->M, h->nk, s));
-      CUDA_TRY(k_diag(h->d_kC0, h->d_kX1, h->d_eps, h->nk, h->M, s));
-      CUDA_TRY(k_precond_parts(h->d_eps, h->d_kf, h->d_kw, h->nk, h->M, h->gamma, h->d_kpden,
-                               h->d_kpw, s));
     } else {
       for (long q = 0; q < MM; ++q)
         if (!std::isfinite(C0_host[q])) throw Fail{ETDM_ERR_INVALID_ARG, "C0 must be finite"};
@@ -957,8 +942,32 @@ static int minimize_impl(etdm_handle *h, double *a_dev, int32_t n_steps, double 
       return Pt{alpha, hp[0], hp[1]};
     };
     LineSearch ls;
+    int since_update = 0;
     for (int it = 1; it <= n_steps; ++it) {
       if (conv && resid <= tol) break;
+      if (h->kpath && h->kexpm == ETDM_EXPM_SS && h->ref_every != 0) {
+        // reference update of Sec. 3.5 before the step: C0 <- C0 exp(A), A <- 0,
+        // the L-BFGS pairs erased (beta kept), orbital energies afresh
+        bool upd = false;
+        if (h->ref_every > 0) {
+          upd = since_update >= h->ref_every;
+        } else {
+          double nL = 0.0, nC = 0.0;
+          commutator_norms_k(h, a_dev, h->d_g, &nL, &nC, s);
+          upd = nL < 3.0 * nC;
+        }
+        if (upd) {
+          reference_update_k(h, a_dev, s);
+          CUDA_TRY(cudaMemcpyAsync(hp, h->d_E, 8, cudaMemcpyDeviceToHost, s));
+          check_flags(h, s);
+          E = hp[0];
+          double st[3] = {0.0, 0.0, 0.0};
+          CUDA_TRY(cudaMemcpy(h->d_lbstate, st, sizeof(st), cudaMemcpyHostToDevice));
+          since_update = 0;
+          ++h->ref_updates;
+        }
+      }
+      ++since_update;
       lbfgs(h, a_dev, h->d_g, h->d_p, s);
       CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
       h->launches += 1;

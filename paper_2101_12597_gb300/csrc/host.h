@@ -59,6 +59,27 @@ void build_mixed_plan(etdm_handle *owner, const std::vector<etdm_handle *> &subs
                       const int *d_active, int *d_flags, bool batch,
                       unsigned long long *vfix, size_t vfix_bytes, MixedPlan *P);
 
+// Optional stage timing: events around a stage on the calling stream.
+struct StageTimer {
+  etdm_handle *h;
+  cudaStream_t s;
+  int stage;
+  cudaEvent_t e0 = nullptr;
+  StageTimer(etdm_handle *hh, cudaStream_t ss, int st) : h(hh), s(ss), stage(st) {
+    if (h->profiling) {
+      CUDA_TRY(cudaEventCreate(&e0));
+      CUDA_TRY(cudaEventRecord(e0, s));
+    }
+  }
+  void done() {
+    if (!h->profiling) return;
+    cudaEvent_t e1;
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e1, s));
+    h->prof_events.push_back({stage, {e0, e1}});
+  }
+};
+
 // L-BFGS memory, line-search buffers and reduction scratch for h->nvar
 // variables (capi.cu).
 void alloc_opt_buffers(etdm_handle *h);

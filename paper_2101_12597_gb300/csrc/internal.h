@@ -306,6 +306,12 @@ struct etdm_handle {
   double *d_kDR = nullptr, *d_kVR = nullptr;  // [nR][M][M]
   void *d_kwork = nullptr;      // eigensolver workspace
   bool kref_set = false;        // reference given by etdm_set_reference
+  int kexpm = 0;                // ETDM_EXPM_EIG (Eq. 35, Eq. 39) or ETDM_EXPM_SS (Eq. 38, Eq. 42)
+  int ref_every = 0;            // reference updates in etdm_minimize (ETDM_EXPM_SS)
+  long long ref_updates = 0;    // reference updates made so far
+  double2 *d_kB = nullptr, *d_kB2 = nullptr, *d_kB3 = nullptr;  // scaling and squaring
+  unsigned long long *d_knorm = nullptr;  // 1-norm of A (double bits)
+  double *d_kfro = nullptr;     // Frobenius partials
   int n[3] = {0, 0, 0};
   long G = 0;
   double L[3], h[3], dV = 0, omega = 0, sigma = 0;

@@ -420,9 +420,10 @@ cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, voi
 __host__ __device__ inline long k_re_idx(long i, long j, long M) { return i * M - i * (i + 1) / 2 + (j - i - 1); }
 __host__ __device__ inline long k_im_idx(long i, long j, long M) { return i * M - i * (i - 1) / 2 + (j - i); }
 
-// iA(k) from the variables: A_ij = a_ij (i < j), A_ji = -conj(a_ij),
-// A_ii = i Im a_ii (skew-Hermitian, Eq. 8), times i.
-__global__ void k_build_iA_kernel(const double *a, int nk, int M, double2 *iA) {
+// scale * iA(k) (times_i) or scale * A(k) from the variables: A_ij = a_ij
+// (i < j), A_ji = -conj(a_ij), A_ii = i Im a_ii (skew-Hermitian, Eq. 8).
+__global__ void k_build_iA_kernel(const double *a, int nk, int M, double2 *iA, int times_i,
+                                  double scale) {
   const long MM = (long)M * M, nre = (long)M * (M - 1) / 2;
   for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
        q += (long)gridDim.x * blockDim.x) {
@@ -433,7 +434,8 @@ __global__ void k_build_iA_kernel(const double *a, int nk, int M, double2 *iA) {
     if (i < j) z = make_double2(-v[nre + k_im_idx(i, j, M)], v[k_re_idx(i, j, M)]);
     else if (i > j) z = make_double2(-v[nre + k_im_idx(j, i, M)], -v[k_re_idx(j, i, M)]);
     else z = make_double2(-v[nre + k_im_idx(i, i, M)], 0.0);
-    iA[q] = z;
+    if (!times_i) z = make_double2(z.y, -z.x);  // A = -i (iA)
+    iA[q] = cscale(z, scale);
   }
 }
 
@@ -764,8 +766,88 @@ static int k_blocks(long n) {
   return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
-cudaError_t k_build_iA(const double *a, int nk, int M, double2 *iA, cudaStream_t s) {
-  k_build_iA_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(a, nk, M, iA);
+cudaError_t k_build_iA(const double *a, int nk, int M, double2 *iA, cudaStream_t s,
+                       int times_i, double scale) {
+  k_build_iA_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(a, nk, M, iA, times_i, scale);
+  return cudaGetLastError();
+}
+
+// ---- scaling and squaring (Eq. 38) and the approximate gradient (Eq. 42) ------
+// max over k-points of the largest column sum of |X| (the 1-norm), as the
+// bits of a non-negative double (their integer order is the value order)
+__global__ void k_norm1_kernel(const double2 *X, int nk, int M, unsigned long long *out) {
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < (long)nk * M;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / M;
+    const int c = (int)(q % M);
+    const double2 *x = X + k * M * M;
+    double sum = 0.0;
+    for (int r = 0; r < M; ++r) sum += hypot(x[(long)r * M + c].x, x[(long)r * M + c].y);
+    atomicMax(out, (unsigned long long)__double_as_longlong(sum));
+  }
+}
+
+// Q = c0 I + c1 B + c2 B2 (a Horner coefficient of the Taylor polynomial in B^3)
+__global__ void k_poly_kernel(double2 *Q, const double2 *B, const double2 *B2, double c0,
+                              double c1, double c2, int nk, int M) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long r = q % MM;
+    double2 v = make_double2(c1 * B[q].x + c2 * B2[q].x, c1 * B[q].y + c2 * B2[q].y);
+    if (r / M == r % M) v.x += c0;
+    Q[q] = v;
+  }
+}
+
+// L(k) from approximate-gradient variables (Eq. 42: dE/da_ij = (2 - d_ij)/2 L_ji):
+// L_ji = (g_re - i g_im) / 2 for i < j, L_ii = -i g_im, L_ij = -conj(L_ji).
+__global__ void k_from_grad_kernel(const double *g, double2 *L, int nk, int M) {
+  const long MM = (long)M * M, nre = (long)M * (M - 1) / 2;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nk * MM;
+       q += (long)gridDim.x * blockDim.x) {
+    const long k = q / MM, r = q % MM;
+    const int row = (int)(r / M), col = (int)(r % M);
+    const double *gk = g + k * MM;
+    double2 v;
+    if (row == col) {
+      v = make_double2(0.0, -gk[nre + k_im_idx(row, row, M)]);
+    } else if (row > col) {  // L_ji with j = row > i = col
+      v = make_double2(0.5 * gk[k_re_idx(col, row, M)], -0.5 * gk[nre + k_im_idx(col, row, M)]);
+    } else {                 // L_ij = -conj(L_ji)
+      v = make_double2(-0.5 * gk[k_re_idx(row, col, M)], -0.5 * gk[nre + k_im_idx(row, col, M)]);
+    }
+    L[q] = v;
+  }
+}
+
+// sum |X|^2 (Frobenius norm squared over all k-points): block partials
+__global__ void __launch_bounds__(256) k_fro2_kernel(const double2 *X, long n, double *part) {
+  double s = 0.0;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+    s += X[q].x * X[q].x + X[q].y * X[q].y;
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+cudaError_t k_norm1(const double2 *X, int nk, int M, unsigned long long *out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_norm1_kernel<<<k_blocks((long)nk * M), 256, 0, s>>>(X, nk, M, out);
+  return cudaGetLastError();
+}
+cudaError_t k_poly(double2 *Q, const double2 *B, const double2 *B2, double c0, double c1,
+                   double c2, int nk, int M, cudaStream_t s) {
+  k_poly_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(Q, B, B2, c0, c1, c2, nk, M);
+  return cudaGetLastError();
+}
+cudaError_t k_from_grad(const double *g, double2 *L, int nk, int M, cudaStream_t s) {
+  k_from_grad_kernel<<<k_blocks((long)nk * M * M), 256, 0, s>>>(g, L, nk, M);
+  return cudaGetLastError();
+}
+int k_fro2_parts() { return 256; }
+cudaError_t k_fro2(const double2 *X, long n, double *part, cudaStream_t s) {
+  k_fro2_kernel<<<k_fro2_parts(), 256, 0, s>>>(X, n, part);
   return cudaGetLastError();
 }
 cudaError_t k_colscale(const double2 *Y, const double *x, double2 *X, int nk, int M, int mode,

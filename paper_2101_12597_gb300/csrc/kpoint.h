@@ -33,7 +33,16 @@ cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, voi
 }  // namespace etdm
 namespace etdm {
 // element-wise steps (kpoint.cu)
-cudaError_t k_build_iA(const double *a, int nk, int M, double2 *iA, cudaStream_t s);
+// scale * iA(k) (times_i = 1) or scale * A(k) (times_i = 0) from the variables
+cudaError_t k_build_iA(const double *a, int nk, int M, double2 *iA, cudaStream_t s,
+                       int times_i = 1, double scale = 1.0);
+// scaling and squaring / approximate gradient helpers
+cudaError_t k_norm1(const double2 *X, int nk, int M, unsigned long long *out, cudaStream_t s);
+cudaError_t k_poly(double2 *Q, const double2 *B, const double2 *B2, double c0, double c1,
+                   double c2, int nk, int M, cudaStream_t s);
+cudaError_t k_from_grad(const double *g, double2 *L, int nk, int M, cudaStream_t s);
+int k_fro2_parts();
+cudaError_t k_fro2(const double2 *X, long n, double *part, cudaStream_t s);
 // X = Y diag(s): mode 0 s = x, mode 1 s = x^(-1/2), mode 2 s = exp(-i x)
 cudaError_t k_colscale(const double2 *Y, const double *x, double2 *X, int nk, int M, int mode,
                        int *flags, cudaStream_t s);
@@ -60,4 +69,13 @@ cudaError_t launch_vmat_k(etdm_handle *h, const double *v, double *VR, cudaStrea
 // set-up and one evaluation of the full-A path (kpath.cu)
 void init_kpoints(etdm_handle *h, const etdm_system *sys);
 void evaluate_k(etdm_handle *h, const double *a, double *E, double *g, cudaStream_t s);
+// Eq. 33 orbital energies and preconditioner parts at the current reference
+// (one evaluation at A = 0, E into h->d_E and the gradient into h->d_g)
+void refresh_reference_k(etdm_handle *h, cudaStream_t s);
+// reference update of Sec. 3.5: C0 <- C0 exp(A(a)), a <- 0, then the refresh
+void reference_update_k(etdm_handle *h, double *a, cudaStream_t s);
+// |L| and |[A, L]| (Frobenius, all k-points) with L rebuilt from an
+// approximate gradient g (Eq. 42) and A from a; synchronizes s
+void commutator_norms_k(etdm_handle *h, const double *a, const double *g, double *nL,
+                        double *nC, cudaStream_t s);
 }  // namespace etdm

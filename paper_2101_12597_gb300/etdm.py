@@ -20,6 +20,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED"
           -5: "TIMEOUT", -6: "STATE", -7: "NUMERIC"}
 PRECISION = {"fp64": 0, "mixed": 1}
 PARAM = {"occvirt": 0, "full": 1}
+EXPM = {"eig": 0, "ss": 1}
 ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "order": (3, np.int32), "vext": (4, np.float64), "rho": (5, np.float64),
           "vtot": (6, np.float64), "H": (7, np.float64), "D": (8, np.float64),
@@ -46,7 +47,7 @@ EXPORTS = ["etdm_default_options", "etdm_init_basis", "etdm_energy_grad",
            "etdm_init_batch", "etdm_num_systems", "etdm_system_layout", "etdm_system_handle",
            "etdm_set_active", "etdm_minimize_converge", "etdm_pair_gemm",
            "etdm_set_reference"]
-STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs"]
+STAGES = ["dense_fwd", "rho", "potential", "vmat", "dense_rev", "lbfgs", "eig"]
 
 
 class EtdmSystem(ctypes.Structure):
@@ -75,7 +76,9 @@ class EtdmOptions(ctypes.Structure):
                 ("device", ctypes.c_int32),
                 ("dense_blocks", ctypes.c_int32),
                 ("dense_tc", ctypes.c_int32),
-                ("param", ctypes.c_int32)]
+                ("param", ctypes.c_int32),
+                ("expm", ctypes.c_int32),
+                ("ref_update", ctypes.c_int32)]
 
 
 _lib = None
@@ -227,7 +230,7 @@ def _system_struct(sysd, s=None):
 
 
 def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc=0,
-             param="occvirt"):
+             param="occvirt", expm="eig", ref_update=0):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision]
@@ -238,6 +241,8 @@ def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_
     o.dense_blocks = dense_blocks
     o.dense_tc = dense_tc
     o.param = PARAM[param]
+    o.expm = EXPM[expm]
+    o.ref_update = ref_update
     return o
 
 
@@ -245,10 +250,13 @@ class ETDM:
     """One system on one GPU: the handle of etdm_init_basis.  A system dict
     with "kpts" (with "kw" and "kT"), or param="full", selects the full-A path:
     the variables are then a flat vector of n_k M^2 reals (Re a_ij for i < j,
-    then Im a_ij for i <= j, per k-point)."""
+    then Im a_ij for i <= j, per k-point).  On that path expm="ss" evaluates
+    exp(A) by scaling and squaring with the approximate gradient G ~ L^T, and
+    ref_update (n > 0: every n steps, -1: the |L| < 3 |[A, L]| test) makes
+    minimize() move the reference, C0 <- C0 exp(A), A <- 0."""
 
     def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
-                 device=0, dense_blocks=0, dense_tc=0, param=None):
+                 device=0, dense_blocks=0, dense_tc=0, param=None, expm="eig", ref_update=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
@@ -259,7 +267,7 @@ class ETDM:
             param = "full" if sysd.get("kpts") is not None else "occvirt"
         self.full = param == "full"
         o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc,
-                     param)
+                     param, expm, ref_update)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))

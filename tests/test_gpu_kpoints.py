@@ -139,3 +139,102 @@ def test_kpoint_minimization_trajectory(cases):
     assert np.abs(al - np.array([h[1] for h in hist])).max() < 1e-6
     assert list(tr) == [h[2] for h in hist]
     assert np.abs(a.cpu().numpy() - a_ref).max() < 1e-6
+
+
+def test_crystal64_against_stored_oracle_values():
+    """The 64-atom crystal at full size (M = 512, 8 k-points, 56^3 grid),
+    against values the oracle stored (tests/golden/make_golden.py crystal64):
+    the reference's eigenvalues and occupations, E and the gradient norm per
+    k-point at A = 0 with the GPU's own reference, then E and 256 seeded
+    gradient entries at the seeded A with the Loewdin reference S(k)^(-1/2)
+    (from the oracle's analytic S(k)) and the stored occupations."""
+    import json
+    import os
+
+    import torch
+    from paper_2101_12597_gb300.etdm import ETDM
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "crystal64_oracle.json")))
+    d = synth.config_crystal64()
+    s = ETDM(d)
+    try:
+        bo = BlochOracle(d, cache_x=False)
+        nk, M = bo.nk, bo.M
+        assert np.abs(s.get_array("eps_ref").reshape(nk, M) - np.array(gold["eps_core"])).max() < 1e-9
+        assert np.abs(s.get_array("occ").reshape(nk, M) - np.array(gold["f"])).max() < 1e-9
+        z = torch.zeros(s.var_shape, dtype=torch.float64, device="cuda")
+        E0, g0 = s.energy_grad(z)
+        g0 = g0.cpu().numpy().reshape(nk, -1)
+        print(f"crystal64: E(0) GPU {float(E0.item()):.10f} oracle {gold['E_0']:.10f}")
+        assert abs(float(E0.item()) - gold["E_0"]) < 1e-8
+        assert np.abs(np.linalg.norm(g0, axis=1) - np.array(gold["gnorm_0"])).max() \
+            <= 1e-8 * max(gold["gnorm_0"])
+        s.set_reference(np.array(bo.lowdin_reference()), np.array(gold["f"]))
+        a = torch.tensor(d["a0"], dtype=torch.float64, device="cuda")
+        E1, g1 = s.energy_grad(a)
+        g1 = g1.cpu().numpy()
+        s.check()
+        gs = np.array(gold["g_a0_lowdin"])
+        err = np.abs(g1[np.array(gold["g_idx"])] - gs).max() / max(gold["gnorm_a0_lowdin"])
+        print(f"crystal64: |dE| at a0 = {abs(float(E1.item()) - gold['E_a0_lowdin']):.3e} Ha, "
+              f"sampled gradient err {err:.3e} of the largest per-k norm")
+        assert abs(float(E1.item()) - gold["E_a0_lowdin"]) < 1e-8
+        assert err < 1e-10
+        gn = np.linalg.norm(g1.reshape(nk, -1), axis=1)
+        assert np.abs(gn - np.array(gold["gnorm_a0_lowdin"])).max() <= 1e-9 * gn.max()
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("which", list(CASES))
+def test_ss_energy_and_approximate_gradient(which, cases):
+    """expm="ss": exp(A) by scaling and squaring (Eq. 38) gives the energy of
+    the eigendecomposition route, and the gradient is the approximate one of
+    Eq. 42 (G ~ L^T), element by element against the oracle's."""
+    import torch
+    from paper_2101_12597_gb300.etdm import ETDM
+    d, bo, s_eig = cases[which]
+    ref = bo.reference_k()
+    s = ETDM(d, expm="ss")
+    try:
+        s.set_reference(np.array(ref["C0"]), np.array(ref["f"]))
+        for t in (1.0, 30.0):  # 30 x: several squarings
+            a = torch.tensor(t * d["a0"], dtype=torch.float64, device="cuda")
+            E, g = s.energy_grad(a)
+            s.check()
+            E_ref, g_ref = bo.energy_grad_approx(t * d["a0"])
+            g = g.cpu().numpy()
+            dE = abs(float(E.item()) - E_ref)
+            dg = np.abs(g - g_ref).max() / np.abs(g_ref).max()
+            print(f"{which} ss x{t:g}: |dE|={dE:.3e} Ha  approx-grad err={dg:.3e}")
+            assert dE < 1e-9
+            assert dg <= 1e-9
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("ref_update", [4, -1])
+def test_ss_minimization_with_reference_updates(ref_update):
+    """The paper's "ss" route: twelve steps from the seeded A with reference
+    updates (every 4 steps, or by the |L| < 3 |[A, L]| test of Sec. 3.5),
+    against the oracle's minimization with the same rules."""
+    import torch
+    from paper_2101_12597_gb300.etdm import ETDM
+    d = synth.tiny_crystal(rcut_ang=3.0)
+    bo = BlochOracle(d)
+    ref = bo.reference_k()
+    s = ETDM(d, expm="ss", ref_update=ref_update)
+    try:
+        s.set_reference(np.array(ref["C0"]), np.array(ref["f"]))
+        a = torch.tensor(d["a0"], dtype=torch.float64, device="cuda")
+        E, al, tr = s.minimize(a, 12)
+        hist, a_ref, nu = bo.minimize_ss(d["a0"], 12, ref_update)
+        E_ref = np.array([h[0] for h in hist])
+        print(f"ss ref_update={ref_update}: {nu} updates, |dE| max {np.abs(E - E_ref).max():.3e}")
+        assert np.abs(E - E_ref).max() < 1e-9
+        assert list(tr) == [h[2] for h in hist]
+        assert np.abs(a.cpu().numpy() - a_ref).max() < 1e-6
+        if ref_update == 4:
+            assert nu == 2
+    finally:
+        s.close()

@@ -41,7 +41,7 @@ def test_default_options(lib):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     assert (o.precision, o.lbfgs_m, o.gamma, o.beta0, o.device, o.dense_blocks,
-            o.dense_tc) == (0, 3, 0.25, 1.0, 0, 0, 0)
+            o.dense_tc, o.param, o.expm, o.ref_update) == (0, 3, 0.25, 1.0, 0, 0, 0, 0, 0, 0)
 
 
 def _system(lib, d, **over):
@@ -86,3 +86,78 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.etdm_lbfgs_reset(None) == -6
     assert lib.etdm_check(None, None) == -6
     lib.etdm_free(None)
+
+
+def _kpoint_system(lib, d, nk=None, kfrac=None, kw=None, kT=None):
+    s, keep = _system(lib, d)
+    kf = np.ascontiguousarray(d["kpts"] if kfrac is None else kfrac, dtype=np.float64)
+    w = np.ascontiguousarray(d["kw"] if kw is None else kw, dtype=np.float64)
+    keep.update(kf=kf, w=w)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    s.n_k = len(w) if nk is None else nk
+    s.k_frac, s.k_w = dp(kf), dp(w)
+    s.kT = float(d["kT"] if kT is None else kT)
+    return s, keep
+
+
+@pytest.mark.parametrize("over,frag", [
+    (dict(nk=-1), "n_k"),
+    (dict(kw=np.full(8, 0.2)), "sum to 1"),
+    (dict(kw=np.r_[-0.125, np.full(7, 1.125 / 7)]), "positive"),
+    (dict(kfrac=np.full((8, 3), np.nan)), "finite"),
+    (dict(kT=-1.0), "kT"),
+    (dict(kT=0.0), "integer occupation"),
+])
+def test_kpoint_arguments_rejected_before_device_work(lib, over, frag):
+    """The full-A path's k-point arrays and temperature are checked on the host."""
+    d = synth.tiny_crystal(rcut_ang=3.0)
+    s, keep = _kpoint_system(lib, d, **over)
+    h = ctypes.c_void_p()
+    rc = lib.etdm_init_basis(ctypes.byref(s), None, ctypes.byref(h))
+    assert rc == -1
+    assert frag in lib.etdm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("param,precision,nk,frag", [
+    (1, 1, 8, "FP64 only"),   # full A in mixed precision
+    (3, 0, 8, "unknown param"),
+    (2, 0, 0, "unknown param"),
+])
+def test_full_a_options_checked(lib, param, precision, nk, frag):
+    from paper_2101_12597_gb300.etdm import EtdmOptions
+    d = synth.tiny_crystal(rcut_ang=3.0)
+    if nk:
+        s, keep = _kpoint_system(lib, d)
+    else:
+        s, keep = _system(lib, d)
+    o = EtdmOptions()
+    lib.etdm_default_options(ctypes.byref(o))
+    o.param, o.precision = param, precision
+    h = ctypes.c_void_p()
+    rc = lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
+    assert rc == -1
+    assert frag in lib.etdm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("expm,ref,full,frag", [
+    (1, 0, False, "needs the full-A path"),
+    (2, 0, True, "unknown expm"),
+    (1, -2, True, "ref_update"),
+    (0, 5, True, "needs expm"),
+])
+def test_ss_options_checked(lib, expm, ref, full, frag):
+    from paper_2101_12597_gb300.etdm import EtdmOptions
+    d = synth.tiny_crystal(rcut_ang=3.0)
+    s, keep = _kpoint_system(lib, d) if full else _system(lib, d)
+    o = EtdmOptions()
+    lib.etdm_default_options(ctypes.byref(o))
+    o.expm, o.ref_update = expm, ref
+    h = ctypes.c_void_p()
+    rc = lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
+    assert rc == -1
+    assert frag in lib.etdm_last_error(None).decode()
+
+
+def test_set_reference_rejects_null_handle(lib):
+    rc = lib.etdm_set_reference(None, 0, None, None)
+    assert rc == -6

@@ -321,3 +321,90 @@ def test_orbital_energies_sum_is_trace_per_k(tiny):
     for k in range(bo.nk):
         tr = np.trace(np.linalg.solve(ref["S"][k], ex["k"][k]["H"]))
         assert abs(tr.imag) < 1e-12 and abs(eps[k].sum() - tr.real) < 1e-11
+
+
+def test_lowdin_reference_is_s_orthonormal(tiny):
+    """S(k)^(-1/2): Hermitian and C0^dagger S C0 = I for every k-point."""
+    d, bo = tiny
+    for k, C in enumerate(bo.lowdin_reference()):
+        S, _ = bo.overlap_kinetic_k(k)
+        assert np.abs(C - C.conj().T).max() < 1e-13
+        assert np.abs(C.conj().T @ S @ C - np.eye(bo.M)).max() < 1e-12
+
+
+def test_reference_update_identity(tiny):
+    """E with reference C0 at A equals E with reference C0 exp(A) at A = 0:
+    the identity behind the reference update C <- C exp(A) of Sec. 3.5."""
+    d, _ = tiny
+    bo = BlochOracle(d)
+    a = d["a0"]
+    E_a = bo.energy(a)
+    ref = bo.reference_k()
+    moved = [ref["C0"][k] @ bo.expm_eig(bo.A_of(a[k * bo.nvar:(k + 1) * bo.nvar]))
+             for k in range(bo.nk)]
+    bo2 = BlochOracle(d)
+    bo2.set_reference(moved)
+    assert abs(bo2.energy(np.zeros_like(a)) - E_a) < 1e-12
+    # and the energy does not depend on which S-orthonormal basis of the same
+    # occupied space is the reference when A = 0 and occupations are equal
+    # within it: here a phase on every column
+    ph = [np.exp(1j * np.arange(bo.M)) for _ in range(bo.nk)]
+    bo3 = BlochOracle(d)
+    bo3.set_reference([ref["C0"][k] * ph[k][None, :] for k in range(bo.nk)])
+    assert abs(bo3.energy(np.zeros_like(a)) - bo.energy(np.zeros_like(a))) < 1e-12
+
+
+def test_scaling_and_squaring_equals_the_eigendecomposition_route(tiny):
+    """Eq. 38 (Pade scaling and squaring) and Eq. 35 give the same exp(A),
+    also for a rotation large enough to need several squarings."""
+    d, bo = tiny
+    for k in (0, 5):
+        A = bo.A_of(d["a0"][k * bo.nvar:(k + 1) * bo.nvar])
+        for t in (1.0, 40.0):
+            U = bo.expm_ss(t * A)
+            assert np.abs(U - bo.expm_eig(t * A)).max() < 1e-13
+            assert np.abs(U.conj().T @ U - np.eye(bo.M)).max() < 1e-13
+
+
+def test_approximate_gradient_is_the_first_term_of_eq19(tiny):
+    """Eq. 42 is the first term of the Eq. 19 series: with the L of the
+    approximate evaluation, L + [A, L]/2! + [A, [A, L]]/3! + ... summed to
+    convergence gives the exact Eq. 39 gradient; at A = 0 the two are equal."""
+    d, bo = tiny
+    z = np.zeros_like(d["a0"])
+    E0, g0 = bo.energy_grad(z)
+    E1, g1 = bo.energy_grad_approx(z)
+    assert E0 == E1 and np.array_equal(g0, g1)
+    a = d["a0"]
+    Ee, ge = bo.energy_grad(a)
+    Ea, ga, ex = bo.energy_grad_approx(a, want=True)
+    assert abs(Ee - Ea) < 1e-14
+    fac = np.where(np.eye(bo.M, dtype=bool), 0.5, 1.0)
+    gs = np.empty_like(ge)
+    for k, (A, L, _) in enumerate(ex["L"]):
+        term, S = L.copy(), L.copy()
+        for n in range(1, 40):
+            term = (A @ term - term @ A) / (n + 1)
+            S = S + term
+        gs[k * bo.nvar:(k + 1) * bo.nvar] = bo.vars_of_grad(fac * S.T)
+    assert np.abs(gs - ge).max() <= 1e-12 * np.abs(ge).max()
+    assert np.abs(ga - ge).max() > 1e-6 * np.abs(ge).max()  # the approximation is visible
+
+
+def test_ss_minimization_with_reference_updates(tiny):
+    """The "ss" route with reference updates (every 5 steps, and by the
+    Sec. 3.5 test) lowers E monotonically and ends where the exact-gradient
+    minimization ends; after an update the new reference at A = 0 reproduces
+    the energy of the point it was taken at (C <- C exp(A))."""
+    d, _ = tiny
+    z = np.zeros_like(d["a0"])
+    h_ex, _ = minimize(BlochOracle(d), z, 20)
+    for ru in (5, -1):
+        bo = BlochOracle(d)
+        h, a, nu = bo.minimize_ss(d["a0"], 20, ru)
+        E = np.array([x[0] for x in h])
+        assert np.all(np.diff(E) <= 1e-12)
+        assert abs(E[-1] - h_ex[-1][0]) < 1e-9
+        if ru == 5:
+            assert nu == 3
+        assert abs(bo.energy_grad_approx(a)[0] - E[-1]) < 1e-12
