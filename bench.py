@@ -746,6 +746,8 @@ def run_batch(args):
                    "batched_eval_graph_ms": graph_ms,
                    "molecule_evals_per_s_graph": n / (graph_ms * 1e-3),
                    "stage_ms_per_batched_eval": stage, "setup_s": t_setup,
+                   "autotuner": {"tiles_per_v_group": bt.tune()[0],
+                                 "ms_per_batched_eval_by_tiles": bt.tune()[1]},
                    "fp64_path": fp64, "E_sum_Ha": float(np.sum(E_run))},
         "roofline": roof,
         "e2e": e2e,
@@ -801,7 +803,7 @@ def run_kpoints(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     d = workload_system(args.workload)
-    solver = ETDM(d, precision="fp64", device=local)
+    solver = ETDM(d, precision="fp64", device=local, expm=args.expm, ref_update=args.ref_update)
     a0 = torch.zeros(solver.var_shape, dtype=torch.float64, device=dev)
     if args.profile_once:
         solver.energy_grad(torch.tensor(d["a0"], dtype=torch.float64, device=dev))
@@ -866,6 +868,10 @@ def run_kpoints(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "precision": "fp64",
+                   "expm": ("eigendecomposition of iA(k) (Eq. 35), exact gradient (Eq. 39)"
+                            if args.expm == "eig" else
+                            "scaling and squaring (Eq. 38), approximate gradient (Eq. 42), "
+                            f"reference updates {args.ref_update}"),
                    "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (complex matrices of 8 k-points, grids), "
                          "steps back to back in one minimization",
@@ -904,6 +910,12 @@ def main():
                     help="water576 (the largest workload on one GPU: the default), "
                          "water32, the 8-atom molecule, or the batch of 148 molecules")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--expm", choices=["eig", "ss"], default="eig",
+                    help="crystal64: exp(A(k)) by the eigendecomposition of iA (Eq. 35, exact "
+                         "gradient) or by scaling and squaring (Eq. 38, approximate gradient)")
+    ap.add_argument("--ref-update", type=int, default=0,
+                    help="crystal64 with --expm ss: reference update every n steps, -1 by "
+                         "the |L| < 3 |[A, L]| test, 0 never")
     ap.add_argument("--profile-once", action="store_true",
                     help="set up, run one energy+gradient evaluation, exit (for ncu)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

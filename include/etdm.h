@@ -129,6 +129,11 @@ typedef struct {
                            after every n steps, -1 when |L| < 3 |[A, L]|
                            (Frobenius norms over all k-points, checked before
                            each step) */
+  int32_t vgroup;       /* mixed precision: tiles (4 x 4 x 8) whose V the tensor
+                           memory accumulates between two read-outs, 1..8; 0
+                           (default) picks it: 2 for one system, and for a batch
+                           the fastest of 2, 4 and 8 in timed evaluations at
+                           set-up (the choice: ETDM_ARR_TUNE) */
 } etdm_options;
 
 /* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1,
@@ -296,7 +301,10 @@ enum {
                                  S(k) (ascending; the reference's) */
   ETDM_ARR_OMEGA = 24,        /* full A: [n_k*M] f64 eigenvalues of iA(k) at the
                                  last evaluation (Eq. 35) */
-  ETDM_NARR = 25              /* number of array ids */
+  ETDM_ARR_TUNE = 25,         /* [8] f64: tiles per V group in use, then up to three
+                                 (tiles per group, ms per evaluation) pairs the
+                                 set-up timed (zeros where none); batches too */
+  ETDM_NARR = 26              /* number of array ids */
 };
 /* On the full-A path S, T, C0, H and D are complex128 (re, im interleaved)
  * [n_k][M][M] row-major per k-point, EPS is [n_k*M]; ORDER, UOCC and

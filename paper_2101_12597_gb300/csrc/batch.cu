@@ -202,6 +202,60 @@ void check_words(etdm_handle *h, const int *words) {
 
 }  // namespace
 
+// Autotuner of the batch's V pass: the number of 4x4x8 tiles whose V the
+// tensor memory accumulates between two read-outs (a V group; the union of
+// the group's functions stays within 128).  Small molecules have few
+// functions, so long groups cut the read-outs and hand-overs per point; the
+// exact order-0 accumulator allows up to 8 tiles.  Each candidate rebuilds the
+// members' group tables and X^T slices and the batch's job lists, and the
+// evaluation (dense chains, density, potential, V) is timed with CUDA events
+// (two warm-up evaluations, then the mean of three); the fastest is kept and
+// the members' own plans are rebuilt for it.
+template <class F>
+void autotune_vgroups(etdm_handle *h, F make_plan) {
+  const int n = (int)h->members.size();
+  const int cand[3] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  double best_ms = 1e300;
+  int best = cand[0], built = h->members[0]->vg_max;
+  h->tune_ms.clear();
+  for (int c : cand) {
+    if (c != built) {
+      for (etdm_handle *m : h->members) build_vgroups(m, c, h->cap);
+      make_plan(&h->bplan_act);
+      built = c;
+    }
+    for (int r = 0; r < 2; ++r) eval_body(h, h->bplan_act, h->d_act, h->cap);
+    CUDA_TRY(cudaEventRecord(e0, h->cap));
+    for (int r = 0; r < 3; ++r) eval_body(h, h->bplan_act, h->d_act, h->cap);
+    CUDA_TRY(cudaEventRecord(e1, h->cap));
+    CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    h->tune_ms.push_back(c);
+    h->tune_ms.push_back(ms / 3.0);
+    if (ms / 3.0 < best_ms) {
+      best_ms = ms / 3.0;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best != built) {
+    for (etdm_handle *m : h->members) build_vgroups(m, best, h->cap);
+    make_plan(&h->bplan_act);
+  }
+  for (etdm_handle *m : h->members)  // the members' own evaluations use the new groups
+    build_mixed_plan(m, {m}, m->d_active1, m->d_flags, false, m->d_Vfix,
+                     ((size_t)m->M * m->M + 1) * sizeof(unsigned long long), &m->plan);
+  CUDA_TRY(cudaMemset(h->d_bflags, 0, stat_count(h) * sizeof(int)));
+  CUDA_TRY(cudaStreamSynchronize(h->cap));
+  h->tune_choice = best;
+  (void)n;
+}
+
 void init_batch(etdm_handle *h, const etdm_system *sys, int n_sys, const etdm_options *opt) {
   if (!sys || n_sys < 1) throw Fail{ETDM_ERR_INVALID_ARG, "need n_sys >= 1 systems"};
   etdm_options o;
@@ -300,21 +354,26 @@ void init_batch(etdm_handle *h, const etdm_system *sys, int n_sys, const etdm_op
     own[i] = h->members[i]->d_Vfix;
     h->members[i]->d_Vfix = arena + vo[i];
   }
-  try {
-    build_mixed_plan(h, h->members, h->d_act, bflag, true, arena, vo[n] * sizeof(unsigned long long),
-                     &h->bplan_act);
-  } catch (...) {
+  auto make_plan = [&](MixedPlan *P) {
+    for (int i = 0; i < n; ++i) h->members[i]->d_Vfix = arena + vo[i];
+    try {
+      build_mixed_plan(h, h->members, h->d_act, bflag, true, arena,
+                       vo[n] * sizeof(unsigned long long), P);
+    } catch (...) {
+      for (int i = 0; i < n; ++i) h->members[i]->d_Vfix = own[i];
+      throw;
+    }
     for (int i = 0; i < n; ++i) h->members[i]->d_Vfix = own[i];
-    throw;
-  }
-  for (int i = 0; i < n; ++i) h->members[i]->d_Vfix = own[i];
+  };
+  CUDA_TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  make_plan(&h->bplan_act);
+  if (o.vgroup == 0 && n > 1) autotune_vgroups(h, make_plan);
   // the same tables masked by the round's eval flags instead
   h->bplan_eval = h->bplan_act;
   const int *ev = ctl_flags(h, CTL_EVAL);
   h->bplan_eval.active = h->bplan_eval.rho.active = h->bplan_eval.v.active = ev;
 
   // graphs (the launches once outside a capture first: kernel attributes are set)
-  CUDA_TRY(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   eval_body(h, h->bplan_act, h->d_act, h->cap);
   CUDA_TRY(cudaStreamSynchronize(h->cap));
   h->graph_kernels_eval =

@@ -198,6 +198,7 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
     if (!(opt->beta0 > 0.0)) bad("beta0 must be positive");
     if (opt->dense_blocks < 0) bad("dense_blocks must be >= 0");
     if (opt->dense_tc < -1 || opt->dense_tc > 1) bad("dense_tc must be -1, 0 or 1");
+    if (opt->vgroup < 0 || opt->vgroup > 8) bad("vgroup must be in [0, 8]");
   }
 }
 
@@ -312,6 +313,59 @@ void build_lists(etdm_handle *h, const GridGeom &g, int n_tiles, int **d_ptr, in
 }
 
 }  // namespace
+
+// V groups of a mixed-precision handle: greedy runs of at most vg_max
+// consecutive 4x4x8 tiles whose function lists have a union of at most 128
+// functions, their tables and X^T slices (built on the device).  A rebuild
+// frees the previous group arrays.
+void etdm::build_vgroups(etdm_handle *h, int vg_max, cudaStream_t s) {
+  const int T = h->n_tiles_tc;
+  const std::vector<int> &tmu = h->h_tmu, &mu_off = h->h_mu_off;
+  for (void *p : {(void *)h->d_vg_t0, (void *)h->d_vg_nu, (void *)h->d_vg_eoff,
+                  (void *)h->d_vg_xoff, (void *)h->d_vg_mu, (void *)h->d_xv, (void *)h->d_vent})
+    dfree(h, p);
+  std::vector<int> vg_t0, vg_nu, vg_eoff(1, 0), vg_xoff(1, 0), vg_mu;
+  std::vector<int> un, tmp;
+  long xkb = 0;
+  for (int t = 0; t < T;) {
+    un.assign(tmu.begin() + mu_off[t], tmu.begin() + mu_off[t + 1]);
+    int nt = 1;
+    while (nt < std::min(vg_max, tc_group_max()) && t + nt < T) {
+      tmp.clear();
+      std::set_union(un.begin(), un.end(), tmu.begin() + mu_off[t + nt],
+                     tmu.begin() + mu_off[t + nt + 1], std::back_inserter(tmp));
+      if ((int)tmp.size() > tc_max_list()) break;
+      un.swap(tmp);
+      ++nt;
+    }
+    const int np = tc_v_entries((int)un.size());
+    vg_t0.push_back(t);
+    vg_nu.push_back((int)un.size());
+    vg_mu.insert(vg_mu.end(), un.begin(), un.end());
+    vg_mu.resize(vg_mu.size() + (np - un.size()), 0);
+    vg_eoff.push_back((int)vg_mu.size());
+    xkb += (long)np * nt * tc_v_slices();  // 256-byte units: 8 K steps x 32 B per slice
+    if (xkb > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
+    vg_xoff.push_back((int)xkb);
+    t += nt;
+  }
+  vg_t0.push_back(T);
+  h->vg_max = vg_max;
+  h->n_vg = (int)vg_nu.size();
+  h->xv_entries = vg_eoff.back();
+  h->h_vg_t0 = vg_t0;
+  h->h_vg_eoff = vg_eoff;
+  h->h_vg_nu = vg_nu;
+  h->h_vg_xoff = vg_xoff;
+  h->d_vg_t0 = dupload(h, vg_t0.data(), vg_t0.size());
+  h->d_vg_nu = dupload(h, vg_nu.data(), std::max<size_t>(vg_nu.size(), 1));
+  h->d_vg_eoff = dupload(h, vg_eoff.data(), vg_eoff.size());
+  h->d_vg_xoff = dupload(h, vg_xoff.data(), vg_xoff.size());
+  h->d_vg_mu = dupload(h, vg_mu.data(), std::max<size_t>(vg_mu.size(), 1));
+  h->d_xv = dalloc<uint8_t>(h, (size_t)vg_xoff.back() * 256);
+  h->d_vent = dalloc<float4>(h, std::max<size_t>(vg_mu.size(), 1));
+  CUDA_TRY(launch_xv_build(h, s));
+}
 
 // L-BFGS memory, line-search buffers and reduction scratch for h->nvar
 // variables (both parametrizations).
@@ -467,61 +521,18 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     }
     mu_off[T] = (int)tmu.size();
     xr_off[T] = (int)xr;
-    std::vector<int> vg_t0, vg_nu, vg_eoff(1, 0), vg_xoff(1, 0), vg_mu;
-    {
-      std::vector<int> un, tmp;
-      long xkb = 0;
-      for (int t = 0; t < T;) {
-        un.assign(tmu.begin() + mu_off[t], tmu.begin() + mu_off[t + 1]);
-        int nt = 1;
-        while (nt < tc_group_max() && t + nt < T) {
-          tmp.clear();
-          std::set_union(un.begin(), un.end(), tmu.begin() + mu_off[t + nt],
-                         tmu.begin() + mu_off[t + nt + 1], std::back_inserter(tmp));
-          if ((int)tmp.size() > tc_max_list()) break;
-          un.swap(tmp);
-          ++nt;
-        }
-        const int np = tc_v_entries((int)un.size());
-        vg_t0.push_back(t);
-        vg_nu.push_back((int)un.size());
-        vg_mu.insert(vg_mu.end(), un.begin(), un.end());
-        vg_mu.resize(vg_mu.size() + (np - un.size()), 0);
-        vg_eoff.push_back((int)vg_mu.size());
-        xkb += (long)np * nt * tc_v_slices();  // 256-byte units: 8 K steps x 32 B per slice
-        if (xkb > INT32_MAX) throw Fail{ETDM_ERR_INVALID_ARG, "grid too large for the mixed path"};
-        vg_xoff.push_back((int)xkb);
-        t += nt;
-      }
-      vg_t0.push_back(T);
-    }
-    h->n_vg = (int)vg_nu.size();
     h->xr_steps = xr;
-    h->xv_entries = vg_eoff.back();
-    auto upload = [&](const std::vector<int> &v) {
-      int *d = dalloc<int>(h, std::max<size_t>(v.size(), 1));
-      if (!v.empty()) CUDA_TRY(cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
-      return d;
-    };
     h->h_xr_off = xr_off;
-    h->h_vg_t0 = vg_t0;
-    h->h_vg_eoff = vg_eoff;
     h->h_mu_off = mu_off;
-    h->h_vg_nu = vg_nu;
-    h->h_vg_xoff = vg_xoff;
-    h->d_xr_off = upload(xr_off);
-    h->d_mu_off = upload(mu_off);
-    h->d_tmu = upload(tmu);
-    h->d_vg_t0 = upload(vg_t0);
-    h->d_vg_nu = upload(vg_nu);
-    h->d_vg_eoff = upload(vg_eoff);
-    h->d_vg_xoff = upload(vg_xoff);
-    h->d_vg_mu = upload(vg_mu);
+    h->h_tmu = tmu;
+    h->d_xr_off = dupload(h, xr_off.data(), xr_off.size());
+    h->d_mu_off = dupload(h, mu_off.data(), mu_off.size());
+    h->d_tmu = dupload(h, tmu.data(), std::max<size_t>(tmu.size(), 1));
     h->d_xr = dalloc<uint8_t>(h, (size_t)xr * 16384);              // 4 slices x 4 KB per K step
-    h->d_xv = dalloc<uint8_t>(h, (size_t)vg_xoff.back() * 256);
-    h->d_vent = dalloc<float4>(h, std::max<size_t>(vg_mu.size(), 1));
     h->d_vt = dalloc<float2>(h, (size_t)T * 128);
-    CUDA_TRY(launch_operand_build(h, s));
+    CUDA_TRY(launch_xr_build(h, s));
+    h->vg_max = (o.vgroup > 0) ? o.vgroup : 2;
+    etdm::build_vgroups(h, h->vg_max, s);
     h->d_Osl = dalloc<uint2>(h, osl_elems(M, h->N));  // [chunk][M][osl_width(N)]
     const long ch = tc_max_list();  // orbitals per chunk of the density pass
     const long nsc = (h->N + ch - 1) / ch * ch;  // whole chunks, zero beyond N
@@ -712,6 +723,7 @@ void etdm_default_options(etdm_options *opt) {
   opt->param = ETDM_PARAM_OCCVIRT;
   opt->expm = ETDM_EXPM_EIG;
   opt->ref_update = 0;
+  opt->vgroup = 0;
 }
 
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {
@@ -1058,6 +1070,7 @@ int etdm_layout(const etdm_handle *h, int64_t *dims) {
 }
 
 int64_t etdm_array_bytes(const etdm_handle *h, int32_t which) {
+  if (h && which == ETDM_ARR_TUNE) return 64;
   if (!h || !h->members.empty()) return -1;  // a batch: ask its systems (etdm_system_handle)
   const int64_t M = h->M, N = h->N;
   if (h->kpath) {  // complex [n_k][M][M] matrices, [n_k][M] vectors
@@ -1105,6 +1118,14 @@ int etdm_get_array(etdm_handle *h, int32_t which, void *dst, int64_t n_bytes) {
     CUDA_TRY(cudaSetDevice(h->device));
     CUDA_TRY(cudaDeviceSynchronize());
     const void *src = nullptr;
+    if (which == ETDM_ARR_TUNE) {
+      double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      t[0] = h->members.empty() ? h->vg_max
+                                : (h->tune_choice ? h->tune_choice : h->members[0]->vg_max);
+      for (size_t i = 0; i < h->tune_ms.size() && i < 6; ++i) t[1 + i] = h->tune_ms[i];
+      memcpy(dst, t, sizeof(t));
+      return ETDM_OK;
+    }
     if (h->kpath) {
       switch (which) {
         case ETDM_ARR_S: src = h->d_kS; break;

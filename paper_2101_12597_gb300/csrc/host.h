@@ -39,6 +39,17 @@ T *dalloc(etdm_handle *h, size_t count) {
   return (T *)p;
 }
 
+// release one allocation of h early (nullptr: nothing)
+inline void dfree(etdm_handle *h, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == p) {
+      cudaFree(p);
+      h->allocs.erase(h->allocs.begin() + i);
+      return;
+    }
+}
+
 // a device copy of n host elements, owned by h
 template <typename T>
 T *dupload(etdm_handle *h, const T *src, size_t n) {
@@ -79,6 +90,9 @@ struct StageTimer {
     h->prof_events.push_back({stage, {e0, e1}});
   }
 };
+
+// V groups of at most vg_max tiles, their tables and X^T slices (capi.cu)
+void build_vgroups(etdm_handle *h, int vg_max, cudaStream_t s);
 
 // L-BFGS memory, line-search buffers and reduction scratch for h->nvar
 // variables (capi.cu).

@@ -349,6 +349,8 @@ struct etdm_handle {
   // V groups: runs of consecutive 4x4x8 tiles whose function lists have a union
   // of at most 128 functions; the V pass accumulates a group in one pass
   int n_vg = 0;
+  int vg_max = 2;                        // tiles per V group at most (this handle's choice)
+  std::vector<int> h_tmu;                // host copy of d_tmu (V groups are rebuilt from it)
   int *d_vg_t0 = nullptr;                // [n_vg + 1] first tile of each group
   int *d_vg_nu = nullptr;                // [n_vg] functions in the group's union
   int *d_vg_eoff = nullptr;              // [n_vg + 1] padded union entries before a group
@@ -434,7 +436,8 @@ struct etdm_handle {
   long long graph_kernels_eval = 0, graph_kernels_round = 0;
   unsigned char *h_ctl = nullptr;     // pinned mirror of d_ctlbuf
   double *h_res = nullptr;            // pinned: [3 n_sys] results, then the status words
-  int tune_choice = 0;                // work partition the autotuner picked
+  int tune_choice = 0;                // tiles per V group the autotuner picked (0: not tuned)
+  std::vector<double> tune_ms;        // (tiles per group, ms per batched evaluation) tried
   // optional per-stage CUDA-event timing (etdm_set_profiling)
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
@@ -496,7 +499,9 @@ DfLaunch df_launch_plan(const std::vector<DfArgs> &args);
 cudaError_t launch_df_potential(const DfLaunch &L, const DfArgs *av, const int *active,
                                 cudaStream_t s);
 int df_pot_blocks(etdm_handle *h);
-cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);
+cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s);  // both below
+cudaError_t launch_xr_build(etdm_handle *h, cudaStream_t s);  // density X slices
+cudaError_t launch_xv_build(etdm_handle *h, cudaStream_t s);  // V X^T slices of the groups
 int tc_rho_steps(int nu);
 int tc_v_entries(int nu);
 int tc_group_max();

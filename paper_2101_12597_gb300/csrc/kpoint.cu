@@ -189,11 +189,22 @@ __global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb,
     for (int i = 1 + tid; i < m; i += nt) u[i] = cscale(u[i], inv);
     __syncthreads();
     for (int i = tid; i < n; i += nt) hrow[i] = i >= o ? u[i - o] : make_double2(0.0, 0.0);
-    // p = A_t u: a warp per row
+    // p = A_t u: a warp per row, four independent partial sums per lane so
+    // that four loads of the row are in flight at once
     for (int i = warp; i < m; i += nw) {
       const double2 *row = A + (long)(o + i) * n + o;
-      double2 s = make_double2(0.0, 0.0);
-      for (int l = lane; l < m; l += 32) cfma(s, row[l], u[l]);
+      double2 s4[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                       make_double2(0.0, 0.0)};
+      int l = lane;
+      for (; l + 96 < m; l += 128) {
+        const double2 a0 = row[l], a1 = row[l + 32], a2 = row[l + 64], a3 = row[l + 96];
+        cfma(s4[0], a0, u[l]);
+        cfma(s4[1], a1, u[l + 32]);
+        cfma(s4[2], a2, u[l + 64]);
+        cfma(s4[3], a3, u[l + 96]);
+      }
+      for (; l < m; l += 32) cfma(s4[0], row[l], u[l]);
+      double2 s = cadd(cadd(s4[0], s4[1]), cadd(s4[2], s4[3]));
       for (int q = 16; q > 0; q >>= 1) {
         s.x += __shfl_xor_sync(0xffffffffu, s.x, q);
         s.y += __shfl_xor_sync(0xffffffffu, s.y, q);
@@ -206,13 +217,28 @@ __global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb,
     kr = block_sum(kr);
     for (int i = tid; i < m; i += nt) p[i] = csub(p[i], cscale(u[i], kr));
     __syncthreads();
-    // A_t -= 2 (u w^dagger + w u^dagger)
-    for (long q = tid; q < (long)m * m; q += nt) {
-      const int i = (int)(q / m), l = (int)(q % m);
-      double2 t = cmul(u[i], cconj(p[l]));
-      cfma(t, p[i], cconj(u[l]));
-      double2 *a = A + (long)(o + i) * n + o + l;
-      *a = csub(*a, cscale(t, 2.0));
+    // A_t -= 2 (u w^dagger + w u^dagger): a warp per row, lanes along it
+    for (int i = warp; i < m; i += nw) {
+      double2 *row = A + (long)(o + i) * n + o;
+      const double2 ui = cscale(u[i], 2.0), wi = cscale(p[i], 2.0);
+      int l = lane;
+      for (; l + 96 < m; l += 128) {
+        double2 a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = row[l + 32 * k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = l + 32 * k;
+          double2 t = cmul(ui, cconj(p[c]));
+          cfma(t, wi, cconj(u[c]));
+          row[c] = csub(a[k], t);
+        }
+      }
+      for (; l < m; l += 32) {
+        double2 t = cmul(ui, cconj(p[l]));
+        cfma(t, wi, cconj(u[l]));
+        row[l] = csub(row[l], t);
+      }
     }
     __syncthreads();
   }
@@ -223,27 +249,51 @@ __global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb,
   }
 }
 
-// Implicit QL with Wilkinson shifts on the real tridiagonal (d, |e|); thread 0
-// computes each sweep's rotations, every thread applies them to its rows of Z
-// (stored by columns, Zt[c][r]).  Then the eigenvalues are ranked ascending.
-// More than 60 sweeps for one eigenvalue sets ETDM_ERR_NOT_CONVERGED.
-__global__ void __launch_bounds__(512) ztql_kernel(const double *db, const double2 *eb, double *wb,
-                                                    double2 *phib, double *Ztb, int *permb,
-                                                    int *flags, int n) {
+// Implicit QL with Wilkinson shifts on the real tridiagonal (d, |e|).  The
+// rows of Z are split over kQlRows-row blocks: every block of a matrix runs the
+// same scalar sweeps (bit-identical: the same code on the same data) and
+// applies them to its own rows, held in shared memory by columns (Zs[c][r]).
+// Warp 0's lane 0 computes sweep t into one half of a double buffer while
+// warp 1 applies sweep t - 1 from the other; a block barrier separates the
+// sweeps.  More than 60 sweeps for one eigenvalue sets ETDM_ERR_NOT_CONVERGED.
+// Block 0 of each matrix ranks the eigenvalues (ties by index) and writes the
+// phases Phi with T = Phi T_r Phi^dagger.
+constexpr int kQlRows = 32;
+
+struct QlSweep {
+  int hi, st, valid;
+};
+
+// sqrt(x^2 + y^2) for the magnitudes of a normalized eigenproblem (no overflow
+// below 1e150)
+__device__ __forceinline__ double ql_norm(double x, double y) { return sqrt(fma(x, x, y * y)); }
+
+__global__ void __launch_bounds__(64) ztql_kernel(const double *db, const double2 *eb, double *wb,
+                                                   double2 *phib, double *Ztb, int *permb,
+                                                   int *flags, int n, int rows) {
   extern __shared__ double qsm[];
-  double *d = qsm, *e = qsm + n, *cs = qsm + 2 * n, *sn = qsm + 3 * n;
-  __shared__ int hi_s, stop_s, done_s;
-  const int b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  double *Zt = Ztb + (long)b * n * n;
-  for (long q = tid; q < (long)n * n; q += nt) Zt[q] = (q / n == q % n) ? 1.0 : 0.0;
-  for (int i = tid; i < n; i += nt) {
+  double *d = qsm, *e = qsm + n;
+  double *cs = qsm + 2 * n, *sn = qsm + 4 * n;  // [2][n] each
+  double *Zs = qsm + 6 * n;                      // [n][rows]
+  __shared__ QlSweep sw[2];
+  __shared__ int finished;
+  const int b = blockIdx.y, r0 = blockIdx.x * rows, tid = threadIdx.x;
+  const int nr = min(rows, n - r0);
+  for (int q = tid; q < n * rows; q += blockDim.x) {
+    const int c = q / rows, r = q % rows;
+    Zs[q] = (r0 + r == c) ? 1.0 : 0.0;
+  }
+  for (int i = tid; i < n; i += blockDim.x) {
     d[i] = db[(long)b * n + i];
     const double2 ei = eb[(long)b * n + i];
-    e[i] = hypot(ei.x, ei.y);
+    e[i] = ql_norm(ei.x, ei.y);
+  }
+  if (tid == 0) {
+    sw[0].valid = sw[1].valid = 0;
+    finished = 0;
   }
   __syncthreads();
-  double anorm = 0.0;
-  if (tid == 0) {  // phases: T[j+1][j] = phi_(j+1) conj(phi_j) |e_j|
+  if (blockIdx.x == 0 && tid == 0) {  // phases: T[j+1][j] = phi_(j+1) conj(phi_j) |e_j|
     double2 ph = make_double2(1.0, 0.0);
     phib[(long)b * n] = ph;
     for (int j = 0; j + 1 < n; ++j) {
@@ -252,86 +302,105 @@ __global__ void __launch_bounds__(512) ztql_kernel(const double *db, const doubl
       if (a > 0.0) ph = cmul(ph, make_double2(ej.x / a, ej.y / a));
       phib[(long)b * n + j + 1] = ph;
     }
-    for (int j = 0; j < n; ++j) anorm = fmax(anorm, fabs(d[j]) + e[j] + (j ? e[j - 1] : 0.0));
   }
+  // scalar state of lane 0 of warp 0
   const double eps = 2.220446049250313e-16;
-  int dn = 0;  // the block's copy of done_s (read between two barriers)
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    for (;;) {
-      if (tid == 0) {
+  double anorm = 0.0;
+  int l = 0, iter = 0;
+  if (tid == 0)
+    for (int j = 0; j < n; ++j) anorm = fmax(anorm, fabs(d[j]) + e[j] + (j ? e[j - 1] : 0.0));
+  for (int t = 0;; ++t) {
+    const int cur = t & 1, prev = cur ^ 1;
+    if (tid == 0) {  // the next sweep (or the end) into buffer cur
+      QlSweep out{0, 0, 0};
+      bool done = false;
+      while (!done) {
+        if (l >= n) {
+          done = true;
+          break;
+        }
         int m = l;
         for (; m < n - 1; ++m) {
           const double dd = fabs(d[m]) + fabs(d[m + 1]);
           if (fabs(e[m]) <= eps * dd || fabs(e[m]) <= eps * eps * anorm) break;
         }
-        done_s = (m == l);
-        if (!done_s) {
-          if (++iter > 60) {
-            atomicExch(flags + FLAG_ERR, ETDM_ERR_NOT_CONVERGED);
-            done_s = 2;
-          } else {
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-            double s = 1.0, c = 1.0, pp = 0.0;
-            int i = m - 1;
-            for (; i >= l; --i) {
-              const double f = s * e[i], bb = c * e[i];
-              r = hypot(f, g);
-              e[i + 1] = r;
-              if (r == 0.0) {  // underflow: deflate here
-                d[i + 1] -= pp;
-                e[m] = 0.0;
-                break;
-              }
-              s = f / r;
-              c = g / r;
-              g = d[i + 1] - pp;
-              r = (d[i] - g) * s + 2.0 * c * bb;
-              pp = s * r;
-              d[i + 1] = g + pp;
-              g = c * r - bb;
-              cs[i] = c;
-              sn[i] = s;
-            }
-            stop_s = i + 1;  // rotations i = m-1 .. stop_s were made
-            if (i < l) {
-              d[l] -= pp;
-              e[l] = g;
-              e[m] = 0.0;
-            }
-            hi_s = m;
+        if (m == l) {  // eigenvalue l converged
+          ++l;
+          iter = 0;
+          continue;
+        }
+        if (++iter > 60) {
+          atomicExch(flags + FLAG_ERR, ETDM_ERR_NOT_CONVERGED);
+          l = n;
+          continue;
+        }
+        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        double r = ql_norm(g, 1.0);
+        g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+        double s = 1.0, c = 1.0, pp = 0.0;
+        double *csb = cs + cur * n, *snb = sn + cur * n;
+        int i = m - 1;
+        for (; i >= l; --i) {
+          const double f = s * e[i], bb = c * e[i];
+          r = ql_norm(f, g);
+          e[i + 1] = r;
+          if (r == 0.0) {  // underflow: deflate here
+            d[i + 1] -= pp;
+            e[m] = 0.0;
+            break;
           }
+          const double inv = 1.0 / r;
+          s = f * inv;
+          c = g * inv;
+          g = d[i + 1] - pp;
+          r = (d[i] - g) * s + 2.0 * c * bb;
+          pp = s * r;
+          d[i + 1] = g + pp;
+          g = c * r - bb;
+          csb[i] = c;
+          snb[i] = s;
         }
-      }
-      __syncthreads();
-      dn = done_s;
-      const int hi = hi_s, st = stop_s;
-      __syncthreads();  // every thread has read the sweep's words before thread 0 writes again
-      if (dn) break;
-      for (int r = tid; r < n; r += nt) {  // rotate columns (i, i+1) of row r, i = hi-1 .. st
-        double carry = Zt[(long)hi * n + r];
-        for (int i = hi - 1; i >= st; --i) {
-          const double zi = Zt[(long)i * n + r];
-          Zt[(long)(i + 1) * n + r] = sn[i] * zi + cs[i] * carry;
-          carry = cs[i] * zi - sn[i] * carry;
+        if (i < l) {
+          d[l] -= pp;
+          e[l] = g;
+          e[m] = 0.0;
         }
-        Zt[(long)st * n + r] = carry;
+        out = QlSweep{m, i + 1, 1};
+        break;
       }
-      __syncthreads();
+      sw[cur] = out;
+      if (done) finished = 1;
+    } else if (tid >= 32 && tid - 32 < nr && sw[prev].valid) {  // warp 1: sweep t - 1 on its row
+      const int rr = tid - 32;
+      const int hi = sw[prev].hi, st = sw[prev].st;
+      const double *csb = cs + prev * n, *snb = sn + prev * n;
+      double carry = Zs[hi * rows + rr];
+      for (int i = hi - 1; i >= st; --i) {
+        const double zi = Zs[i * rows + rr];
+        Zs[(i + 1) * rows + rr] = snb[i] * zi + csb[i] * carry;
+        carry = csb[i] * zi - snb[i] * carry;
+      }
+      Zs[st * rows + rr] = carry;
     }
-    if (dn == 2) break;
+    __syncthreads();
+    // no sweep t: sweep t - 1 was applied in this step, so every rotation is in
+    // (finished is written once, before the barrier, and read after it)
+    if (finished) break;
   }
   __syncthreads();
-  // rank the eigenvalues (ties by index)
-  for (int i = tid; i < n; i += nt) {
-    int rk = 0;
-    const double di = d[i];
-    for (int j = 0; j < n; ++j) rk += (d[j] < di) || (d[j] == di && j < i);
-    wb[(long)b * n + rk] = di;
-    permb[(long)b * n + rk] = i;
+  double *Zt = Ztb + (long)b * n * n;
+  for (int q = tid; q < n * rows; q += blockDim.x) {
+    const int c = q / rows, r = q % rows;
+    if (r < nr) Zt[(long)c * n + r0 + r] = Zs[q];
   }
+  if (blockIdx.x == 0)
+    for (int i = tid; i < n; i += blockDim.x) {
+      int rk = 0;
+      const double di = d[i];
+      for (int j = 0; j < n; ++j) rk += (d[j] < di) || (d[j] == di && j < i);
+      wb[(long)b * n + rk] = di;
+      permb[(long)b * n + rk] = i;
+    }
 }
 
 // V[:, c] = H_0 ... H_(n-3) Phi Z[:, perm[c]] for a slab of kBackW columns.
@@ -402,10 +471,13 @@ cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, voi
   if (err != cudaSuccess) return err;
   zhetrd_kernel<<<batch, 1024, smt, s>>>(A, hv, d, e, n);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  const int smq = 4 * n * (int)sizeof(double);
+  // rows of Z per block: up to kQlRows, as many as 200 KB of shared memory holds
+  const int rows = std::max(1, std::min(kQlRows, (200 * 1024 / 8 - 6 * n) / n));
+  const int smq = (6 * n + n * rows) * (int)sizeof(double);
   err = cudaFuncSetAttribute(ztql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
   if (err != cudaSuccess) return err;
-  ztql_kernel<<<batch, 512, smq, s>>>(d, e, w, phi, Z, perm, flags, n);
+  ztql_kernel<<<dim3((n + rows - 1) / rows, batch), 64, smq, s>>>(d, e, w, phi, Z, perm, flags, n,
+                                                                  rows);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   const int smb = n * kBackW * (int)sizeof(double2);
   err = cudaFuncSetAttribute(zback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);

@@ -692,7 +692,10 @@ constexpr int kVStages = (200 * 1024) / kVStage;  // operand ring in 200 KB of s
 constexpr int kVEpiW = 16, kVBldW = 8;  // warps: 0-15 read-out, 16-23 build W
 constexpr int kVEpi = kVEpiW * 32, kVBld = kVBldW * 32;
 constexpr int kVThreads = kVEpi + kVBld + 64;
-constexpr int kVGmax = 2;                         // tiles per V group at most
+// tiles per V group at most (the group size is chosen per handle, <= this):
+// an order-0 accumulator sums kVGmax * 128 products below 2^14 each, so 8
+// keeps every partial sum within 2^24 (exact in FP32)
+constexpr int kVGmax = 8;
 constexpr int kVTileBuf = kVGmax * kTP * 8 + kNmax * 16;  // v pairs + union entries
 
 struct VBars {
@@ -1099,19 +1102,28 @@ cudaError_t launch_count_unique(etdm_handle *h, int *d_nu, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s) {
+cudaError_t launch_xr_build(etdm_handle *h, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(xr_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kStageBytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(xv_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kStageBytes);
-  if (e != cudaSuccess) return e;
   const int blocks = std::min(h->n_tiles_tc, 4 * h->num_sms);
   xr_build_kernel<<<blocks, 256, kStageBytes, s>>>(tc_args(h));
-  e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xv_build(etdm_handle *h, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(xv_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStageBytes);
   if (e != cudaSuccess) return e;
+  const int blocks = std::min(h->n_tiles_tc, 4 * h->num_sms);
   xv_build_kernel<<<blocks, 256, kStageBytes, s>>>(tc_args(h));
   return cudaGetLastError();
+}
+
+cudaError_t launch_operand_build(etdm_handle *h, cudaStream_t s) {
+  cudaError_t e = launch_xr_build(h, s);
+  if (e != cudaSuccess) return e;
+  return launch_xv_build(h, s);
 }
 
 int tc_rho_steps(int nu) { return rsteps(nu); }

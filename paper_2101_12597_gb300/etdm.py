@@ -34,7 +34,9 @@ ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           # full-A path: complex [n_k][M][M] matrices and [n_k][M] vectors
           "S_k": (0, np.complex128), "T_k": (1, np.complex128), "C0_k": (2, np.complex128),
           "H_k": (7, np.complex128), "D_k": (8, np.complex128), "occ": (22, np.float64),
-          "eps_ref": (23, np.float64), "omega": (24, np.float64)}
+          "eps_ref": (23, np.float64), "omega": (24, np.float64),
+          # tiles per V group in use, then (tiles, ms per evaluation) pairs timed at set-up
+          "tune": (25, np.float64)}
 DIM_NAMES = ["M", "N", "V", "G", "n_tiles", "entries", "max_list", "tx", "ty",
              "tz", "sum_npt2", "precision"]
 
@@ -78,7 +80,8 @@ class EtdmOptions(ctypes.Structure):
                 ("dense_tc", ctypes.c_int32),
                 ("param", ctypes.c_int32),
                 ("expm", ctypes.c_int32),
-                ("ref_update", ctypes.c_int32)]
+                ("ref_update", ctypes.c_int32),
+                ("vgroup", ctypes.c_int32)]
 
 
 _lib = None
@@ -230,7 +233,7 @@ def _system_struct(sysd, s=None):
 
 
 def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc=0,
-             param="occvirt", expm="eig", ref_update=0):
+             param="occvirt", expm="eig", ref_update=0, vgroup=0):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision]
@@ -243,6 +246,7 @@ def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_
     o.param = PARAM[param]
     o.expm = EXPM[expm]
     o.ref_update = ref_update
+    o.vgroup = vgroup
     return o
 
 
@@ -463,10 +467,12 @@ class ETDM:
 
 class ETDMBatch:
     """Many systems in one handle (etdm_init_batch): packed variable vectors,
-    one energy per system, one graph per evaluation on the mixed path."""
+    one energy per system, one graph per evaluation on the mixed path.
+    vgroup = 0 lets the set-up time V groups of 2, 4 and 8 tiles and keep the
+    fastest (tune() reports it); 1..8 fixes the group size."""
 
     def __init__(self, systems, precision="mixed", lbfgs_m=3, gamma=0.25, beta0=1.0,
-                 device=0, dense_blocks=0):
+                 device=0, dense_blocks=0, vgroup=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDMBatch needs a CUDA GPU; there is no CPU fallback")
@@ -476,7 +482,8 @@ class ETDMBatch:
             raise ValueError("need at least one system")
         arr = (EtdmSystem * n)()
         self._keep = [_system_struct(d, arr[i])[1] for i, d in enumerate(systems)]
-        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks)
+        o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks,
+                     vgroup=vgroup)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_batch(arr, n, ctypes.byref(o), ctypes.byref(h))
@@ -498,6 +505,13 @@ class ETDMBatch:
     def _raise(self, rc):
         if rc != ETDM_OK:
             raise EtdmError(rc, self.lib.etdm_last_error(self.h).decode())
+
+    def tune(self):
+        """(tiles per V group in use, {tiles: ms per batched evaluation} timed at set-up)."""
+        t = np.zeros(8)
+        self._raise(self.lib.etdm_get_array(self.h, ARRAYS["tune"][0],
+                                            t.ctypes.data_as(ctypes.c_void_p), 64))
+        return int(t[0]), {int(t[1 + 2 * i]): float(t[2 + 2 * i]) for i in range(3) if t[1 + 2 * i]}
 
     def pack(self, arrays):
         """One packed float64 vector from the per-system (N_i, V_i) arrays."""

@@ -256,3 +256,32 @@ def test_fp64_batch_runs_each_system_on_the_plain_path(mols, sample, oracle_eg):
         gref = oracle_eg[i][1]
         assert np.abs(g[k] - gref).max() < 1e-9 * np.abs(gref).max()
     b.close()
+
+
+def test_vgroup_autotuner_and_fixed_sizes(batch, mols, oracle_eg):
+    """The set-up timed V groups of 2, 4 and 8 tiles and kept the fastest; a
+    batch with each size fixed gives every molecule's energy within the bar,
+    and the sizes agree with one another to the slicing's rounding."""
+    import torch
+    from paper_2101_12597_gb300.etdm import ETDMBatch
+    used, timed = batch.tune()
+    print("V-group autotuner:", used, {k: round(v, 3) for k, v in timed.items()})
+    assert sorted(timed) == [2, 4, 8] and used in timed
+    assert timed[used] == min(timed.values())
+    sub = list(range(0, len(mols), 10))
+    Es = {}
+    for vg in (2, 8):
+        b = ETDMBatch([mols[i] for i in sub], precision="mixed", vgroup=vg)
+        try:
+            assert b.tune()[0] == vg
+            a = torch.tensor(b.pack([mols[i]["a0"] for i in sub]), device=b.dev)
+            E, _ = b.energy_grad(a)
+            torch.cuda.synchronize()
+            b.check()
+            Es[vg] = E.cpu().numpy()
+        finally:
+            b.close()
+        dE = np.abs(Es[vg] - np.array([oracle_eg[i][0] for i in sub]))
+        print(f"vgroup {vg}: max |dE| = {dE.max():.3e} Ha over {len(sub)} molecules")
+        assert dE.max() < E_TOL
+    assert np.abs(Es[2] - Es[8]).max() < 2e-7

@@ -41,7 +41,8 @@ def test_default_options(lib):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     assert (o.precision, o.lbfgs_m, o.gamma, o.beta0, o.device, o.dense_blocks,
-            o.dense_tc, o.param, o.expm, o.ref_update) == (0, 3, 0.25, 1.0, 0, 0, 0, 0, 0, 0)
+            o.dense_tc, o.param, o.expm, o.ref_update, o.vgroup) == (0, 3, 0.25, 1.0, 0, 0, 0, 0, 0,
+                                                                      0, 0)
 
 
 def _system(lib, d, **over):
