@@ -37,6 +37,7 @@ METRIC = "ETDM energy+gradient evals/sec vs plain FP64 GPU path at |dE|<1e-6 Ha"
 WORKLOADS = {
     "water576": "water576: 1728 atoms, M=4608, N=2304, 192^3 grid, 25 A box, r_c=3.5 A",
     "water32": "water32: 96 atoms, M=256, N=128, 96^3 grid, 9.9 A box, r_c=4 A",
+    "water216": "water216: 648 atoms, M=1728, N=864, 128^3 grid, 18.03 A box, r_c=3.5 A",
     "small": "small molecule: 8 atoms, M=16, N=4, 32^3 grid, 6.4 A box",
     "molecules148": "molecules148: 148 molecules of 2-20 atoms (M 4-60), each on its own "
                     "48^3 grid over a 9.6 A box, r_c=4 A, evaluated as one batch",
@@ -47,13 +48,13 @@ WORKLOADS = {
 # workloads whose resident operands (basis slices, grids) exceed the 129 MB L2:
 # the timed steps run back to back; the small molecule fits in L2 and flushes it
 # before every step instead
-LARGE = {"water576", "water32"}
+LARGE = {"water576", "water216", "water32"}
 
 
 def workload_system(name):
     import etdm_synth as synth
     return {"water32": synth.config_water32, "small": synth.config_small_molecule,
-            "water576": synth.config_water576,
+            "water576": synth.config_water576, "water216": synth.config_water216,
             "molecules148": synth.config_molecules148,
             "crystal64": synth.config_crystal64}[name]()
 

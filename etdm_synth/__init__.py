@@ -162,6 +162,14 @@ def config_water576():
                      rcut_ang=3.5, a_sigma=0.01, seed=2)
 
 
+def config_water216():
+    """216 water-like units (648 atoms), M=1728, N=864, 128^3 grid over an
+    18.03 A box (the water576 density), r_c = 3.5 A, A_ov ~ N(0, 0.01) (seed
+    2): a mid-size box for profiler captures (a few GB on the device)."""
+    return water_box(lattice=(6, 6, 6), box_ang=18.03, grid=(128, 128, 128),
+                     rcut_ang=3.5, a_sigma=0.01, seed=2)
+
+
 def config_water75():
     """75 water-like units (225 atoms), M=600, N=300, 64^3 grid over a 13.13 A
     box (the water32 density), r_c = 3.5 A, A_ov ~ N(0, 0.02) (seed 5): the

@@ -17,6 +17,8 @@ def _min_image(d, box):
 @pytest.mark.parametrize("make,units,M,N,grid,box_ang,rc_ang,a_sigma", [
     (synth.config_water32, 32, 256, 128, 96, 9.9, 4.0, 0.02),
     (synth.config_water576, 576, 4608, 2304, 192, 25.0, 3.5, 0.01),
+    (synth.config_water216, 216, 1728, 864, 128, 18.03, 3.5, 0.01),
+    (synth.config_water75, 75, 600, 300, 64, 13.13, 3.5, 0.02),
 ])
 def test_water_boxes(make, units, M, N, grid, box_ang, rc_ang, a_sigma):
     d = make()
@@ -141,3 +143,18 @@ def test_batch_molecule_through_the_oracle():
     D = o.density_matrix(o.orbitals(m["a0"]))
     assert abs(float(np.sum(D * o.reference()["S"])) - m["n_electrons"]) < 1e-12
     assert abs(o.dV * o.density(D).sum() - m["n_electrons"]) < 1e-8 * m["n_electrons"]
+
+
+def test_gpu_sized_crystals():
+    """The two crystals of the GPU k-point tests: the two-atom cell with a
+    hard radius below twice its shortest edge, and the 8-atom cell with a
+    ragged grid and the Fermi level inside a band."""
+    t = synth.tiny_crystal(rcut_ang=3.0)
+    assert len(t["bf_exp"]) == 4 and np.allclose(t["bf_rcut"], 3.0 * A)
+    assert np.all(t["bf_rcut"] < 2.0 * t["box"].min())
+    s = synth.small_crystal()
+    assert len(s["bf_exp"]) == 24 and s["n_electrons"] == 12
+    assert tuple(s["grid"]) == (26, 24, 22)
+    assert np.all(s["bf_rcut"] < 2.0 * s["box"].min())
+    assert len(s["kw"]) == 8 and abs(s["kw"].sum() - 1.0) < 1e-15
+    assert s["a0"].shape == (8 * 24 * 24,)
