@@ -852,15 +852,34 @@ def run_kpoints(args):
            "h2d_bytes_per_step": 8 * solver.nvar, "d2h_bytes_per_step": 8 * solver.nvar + 8,
            "evals": n_e2e}
     per_eval = {k: v / max(evals, 1) for k, v in stage_ms.items()}
-    # dominant stage: FP64 ALU bound (complex products, the eigensolver)
+    # FP64 ALU bound: the complex products of the dense stages (9 per evaluation
+    # on the eigendecomposition route: U, O, D, then H O, O^dag(HO), L W,
+    # W^dag(LW), W X, X W^dag; 4 on the scaling-and-squaring route: O, D, H O,
+    # O^dag(HO)), and the exp stage (eigensolver, or the products of the Taylor
+    # polynomial and the squarings)
     M, nk = solver.M, solver.nvar // (solver.M * solver.M)
     zflop = 8.0 * M ** 3 * nk  # one batched complex product
-    roof = {"bound": "alu", "kernel": "zgemm_kernel (dense forward + reverse: 9 batched "
-            "complex products per evaluation)",
-            "achieved": 9 * zflop / ((per_eval["dense_fwd"] + per_eval["dense_rev"]) * 1e-3) / 1e12,
-            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
-            "peak_source": "nominal FP64 rate of a GB300 (no measured FP64 figure)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    nprod = 9 if args.expm == "eig" else 4
+    dense_ms = per_eval["dense_fwd"] + per_eval["dense_rev"]
+    roof_dense = {"bound": "alu", "kernel": f"zgemm_kernel ({nprod} batched complex products "
+                  "per evaluation in the dense stages)",
+                  "achieved": nprod * zflop / (dense_ms * 1e-3) / 1e12,
+                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": None,
+                  "peak_source": "nominal FP64 rate of a GB300 (no measured FP64 figure)"}
+    roof_dense["frac"] = roof_dense["achieved"] / roof_dense["peak"]
+    if args.expm == "eig":
+        # the eigensolver: Householder reduction (16/3 M^3 real flops per complex
+        # matrix), QL with rotations applied to Z (about 3 M^3 for ~1.5 sweeps per
+        # eigenvalue over M rows), back-transformation (8 M^3)
+        eflop = (16.0 / 3.0 + 3.0 + 8.0) * M ** 3 * nk
+        roof = {"bound": "alu", "kernel": "zhetrd_kernel + ztql_kernel + zback_kernel (the "
+                "eigendecomposition of iA(k), Eq. 35)",
+                "achieved": eflop / (per_eval["eig"] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "nominal FP64 rate of a GB300 (no measured FP64 figure)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:  # every step is a batched complex product (the exp stage's count varies with |A|)
+        roof = dict(roof_dense)
     if rank != 0:
         return
     line = {
@@ -879,7 +898,8 @@ def run_kpoints(args):
                    "evals_timed": int(all_evals), "E_first": float(E_h[0]),
                    "E_last": float(E_h[-1]), "stage_ms_per_eval": per_eval,
                    "M": M, "n_k": nk},
-        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "roofline": roof, "roofline_dense": roof_dense, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
         from oracle.etdm_kpoints import BlochOracle
