@@ -469,68 +469,66 @@ def run_ours(args):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     # float-pair multiply-add: 12 FP32 instructions, each one lane-cycle
     pair_peak = 152 * 128 * sm_mhz * 1e6 * 2.0 / 12.0 / 1e12
-    grid_roof = None
-    for dom in sorted(per_eval, key=lambda k: -per_eval[k]):
-        if dom in ("dense_fwd", "dense_rev"):
-            flops = 2.0 * (fwd if dom == "dense_fwd" else rev)
-            achieved = flops / (per_eval[dom] * 1e-3) / 1e12
-            kern = "dense_forward_kernel" if dom == "dense_fwd" else "dense_reverse_kernel"
-            # the float-pair products go to the tensor cores from 2^26 multiply-adds
-            # on (every product of the chains at this size when the smallest does)
-            on_tc = mixed and (args.dense_tc == 1 or
-                               (args.dense_tc == 0 and N * N * min(N, V) >= 1 << 26))
-            if on_tc:
-                kern = kern.replace("_kernel", "_tc_kernel")
-                pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
-                # executed: 15 BF16 slice products per multiply-add, the outputs
-                # padded to 128 x 64 tiles and K to 16
-                pad = (lambda x, q: -(-x // q) * q)
-                ex_fwd, ex_rev = dense_macs(pad(M, 128), pad(N, 64), pad(V, 64), J)
-                executed = 15 * 2.0 * (ex_fwd if dom == "dense_fwd" else ex_rev)
-                ex_t = executed / (per_eval[dom] * 1e-3) / 1e12
-                roof = {"bound": "tensor", "achieved": achieved, "peak": pk / 15.0,
-                        "unit": "TFLOP/s", "frac": achieved / (pk / 15.0),
-                        "traffic": captured_traffic(kern, args.workload),
-                        "kernel": kern + " (float-pair products as exact BF16 slice "
-                                         "products on tcgen05)",
-                        "peak_source": f"derived: {src} dense bf16"
-                                       + (" (sustained)" if "bf16_tflops_sustained" in peaks else "")
-                                       + " / 15 BF16 slice products per float-pair multiply-add",
-                        "algorithmic_flops_per_launch": flops, "doublings": J,
-                        "executed_bf16_tflops": ex_t, "executed_frac": ex_t / pk}
-            elif mixed:
-                roof = {"bound": "alu", "achieved": achieved, "peak": pair_peak,
-                        "unit": "TFLOP/s", "frac": achieved / pair_peak,
-                        "traffic": captured_traffic(kern + "<float2>", args.workload),
-                        "kernel": kern + "<float2> (float-pair products on the FP32 pipes)",
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x "
-                                       f"{sm_mhz:.0f} MHz / 12 FP32 instructions per "
-                                       "float-pair multiply-add, 2 flops each",
-                        "algorithmic_flops_per_launch": flops, "doublings": J}
-            else:
-                roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                        "traffic": None, "kernel": kern + "<double> (FP64 DFMA)",
-                        "peak_source": "nominal FP64 rate of a GB300",
-                        "algorithmic_flops_per_launch": flops, "doublings": J}
-            break
-        if dom in ("rho", "vmat"):
-            roof = None
-            break
-    # the dominant grid pass (one multiply-add per (point, mu, nu) within r_c)
-    gdom = max(("rho", "vmat"), key=lambda k: per_eval[k])
+    pk_s = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
+    pk_src = f"{src} dense bf16" + (" (sustained)" if "bf16_tflops_sustained" in peaks else "")
+
+    def dense_roof(dom):
+        if not per_eval.get(dom, 0.0) > 0.0:
+            return None
+        flops = 2.0 * (fwd if dom == "dense_fwd" else rev)
+        achieved = flops / (per_eval[dom] * 1e-3) / 1e12
+        kern = "dense_forward_kernel" if dom == "dense_fwd" else "dense_reverse_kernel"
+        # the float-pair products go to the tensor cores from 2^26 multiply-adds
+        # on (every product of the chains at this size when the smallest does)
+        on_tc = mixed and (args.dense_tc == 1 or
+                           (args.dense_tc == 0 and N * N * min(N, V) >= 1 << 26))
+        if on_tc:
+            kern = kern.replace("_kernel", "_tc_kernel")
+            # executed: 15 BF16 slice products per multiply-add, the outputs
+            # padded to 128 x 64 tiles and K to 16
+            pad = (lambda x, q: -(-x // q) * q)
+            ex_fwd, ex_rev = dense_macs(pad(M, 128), pad(N, 64), pad(V, 64), J)
+            executed = 15 * 2.0 * (ex_fwd if dom == "dense_fwd" else ex_rev)
+            ex_t = executed / (per_eval[dom] * 1e-3) / 1e12
+            return {"bound": "tensor", "achieved": achieved, "peak": pk_s / 15.0,
+                    "unit": "TFLOP/s", "frac": achieved / (pk_s / 15.0),
+                    "traffic": captured_traffic(kern, args.workload),
+                    "kernel": kern + " (float-pair products as exact BF16 slice "
+                                     "products on tcgen05)",
+                    "peak_source": "derived: " + pk_src
+                                   + " / 15 BF16 slice products per float-pair multiply-add",
+                    "algorithmic_flops_per_launch": flops, "doublings": J,
+                    "frac_of_bf16_peak": achieved / pk_s,
+                    "executed_bf16_tflops": ex_t, "executed_frac": ex_t / pk_s}
+        if mixed:
+            return {"bound": "alu", "achieved": achieved, "peak": pair_peak,
+                    "unit": "TFLOP/s", "frac": achieved / pair_peak,
+                    "traffic": captured_traffic(kern + "<float2>", args.workload),
+                    "kernel": kern + "<float2> (float-pair products on the FP32 pipes)",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x "
+                                   f"{sm_mhz:.0f} MHz / 12 FP32 instructions per "
+                                   "float-pair multiply-add, 2 flops each",
+                    "algorithmic_flops_per_launch": flops, "doublings": J}
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None, "kernel": kern + "<double> (FP64 DFMA)",
+                "peak_source": "nominal FP64 rate of a GB300",
+                "algorithmic_flops_per_launch": flops, "doublings": J}
+
+    # a grid pass: one multiply-add per (point, mu, nu) within r_c
     gflops = 2.0 * dims["sum_npt2"]
-    gach = gflops / (per_eval[gdom] * 1e-3) / 1e12
-    if not mixed:
-        grid_roof = {"bound": "alu", "achieved": gach, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": gach / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": f"{gdom}_fp64 (FP64 DFMA)",
-                     "peak_source": "nominal FP64 rate of a GB300"}
-    else:
-        # the stage is timed inside a long step: the sustained BF16 figure
-        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", BF16_FALLBACK_TFLOPS))
+
+    def grid_roof_of(g):
+        if not per_eval.get(g, 0.0) > 0.0:
+            return None
+        gach = gflops / (per_eval[g] * 1e-3) / 1e12
+        if not mixed:
+            return {"bound": "alu", "achieved": gach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": gach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": f"{g}_fp64 (FP64 DFMA)",
+                    "peak_source": "nominal FP64 rate of a GB300"}
         nu = solver.get_array("tile_nu_tc").astype(np.int64)  # functions per 128-point tile
-        if gdom == "vmat":  # 8 slice products per 16-point K step of a V group (runs of
+        if g == "vmat":  # 8 slice products per 16-point K step of a V group (runs of
             # consecutive tiles), M = 128 rows, N = the group's union list padded to 16
             t0v = solver.get_array("vgroup_t0").astype(np.int64)
             gnu = solver.get_array("vgroup_nu").astype(np.int64)
@@ -540,15 +538,21 @@ def run_ours(args):
             nmpad = sum(max(32, ((min(128, N - m0) + 31) // 32) * 32) for m0 in range(0, N, 128))
             ksteps = np.maximum(1, (nu + 15) // 16)
             executed = float((9 * 2.0 * 128 * nmpad * 16 * ksteps).sum())
-        grid_roof = {"bound": "tensor", "achieved": gach, "peak": pk, "unit": "TFLOP/s",
-                     "frac": gach / pk,
-                     "traffic": captured_traffic(f"{gdom}_tc_kernel", args.workload),
-                     "kernel": f"{gdom}_tc_kernel",
-                     "peak_source": f"{src} dense bf16" + (" (sustained)" if "bf16_tflops_sustained" in peaks else ""),
-                     "executed_tflops": executed / (per_eval[gdom] * 1e-3) / 1e12,
-                     "executed_frac": executed / (per_eval[gdom] * 1e-3) / 1e12 / pk}
-    if roof is None:
-        roof = grid_roof
+        return {"bound": "tensor", "achieved": gach, "peak": pk_s, "unit": "TFLOP/s",
+                "frac": gach / pk_s,
+                "traffic": captured_traffic(f"{g}_tc_kernel", args.workload),
+                "kernel": f"{g}_tc_kernel", "peak_source": pk_src,
+                "algorithmic_flops_per_launch": gflops,
+                "executed_tflops": executed / (per_eval[g] * 1e-3) / 1e12,
+                "executed_frac": executed / (per_eval[g] * 1e-3) / 1e12 / pk_s}
+
+    passes = {g: grid_roof_of(g) for g in ("rho", "vmat")}
+    passes.update({d: dense_roof(d) for d in ("dense_fwd", "dense_rev")})
+    # the dominant kernel is the stage with the largest time
+    dom = max((k for k in passes if passes[k] is not None), key=lambda k: per_eval[k])
+    roof = passes[dom]
+    gdom = max((k for k in ("rho", "vmat") if passes[k] is not None), key=lambda k: per_eval[k])
+    grid_roof = passes[gdom]
 
     if rank != 0:
         return
@@ -570,6 +574,7 @@ def run_ours(args):
                    "E_run_Ha": E_run},
         "roofline": roof,
         "roofline_grid": grid_roof,
+        "roofline_passes": passes,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
