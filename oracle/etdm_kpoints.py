@@ -79,8 +79,9 @@ class BlochOracle(Oracle):
     """One periodic system with k-point sampling and a full skew-Hermitian A(k)
     per k-point."""
 
-    def __init__(self, sysd, **kw):
+    def __init__(self, sysd, sic=False, **kw):
         super().__init__(sysd, **kw)
+        self.sic = bool(sic)
         self.kfrac = np.atleast_2d(np.asarray(sysd["kpts"], dtype=np.float64))
         self.kw = np.asarray(sysd["kw"], dtype=np.float64)
         self.kT = float(sysd["kT"])
@@ -212,8 +213,13 @@ class BlochOracle(Oracle):
             e, Y = np.linalg.eigh(Sih @ hk @ Sih)
             S.append(Sk); T.append(Tk); H0.append(hk)
             C0.append(Sih @ Y); eps.append(e)
-        mu = fermi_level(eps, self.kw, self.n_e, self.kT)
-        f = [2.0 * self.kw[k] * fermi_dirac((eps[k] - mu) / self.kT) for k in range(self.nk)]
+        if self.kT == 0.0:  # integer occupation (one k-point): the n_e / 2 lowest doubly
+            assert self.nk == 1
+            mu = 0.0
+            f = [np.where(np.arange(self.M) < self.n_e // 2, 2.0 * self.kw[0], 0.0)]
+        else:
+            mu = fermi_level(eps, self.kw, self.n_e, self.kT)
+            f = [2.0 * self.kw[k] * fermi_dirac((eps[k] - mu) / self.kT) for k in range(self.nk)]
         self._kref = dict(S=S, T=T, hcore=H0, C0=C0, eps_core=eps, mu=mu, f=f, vext=vext)
         return self._kref
 
@@ -282,7 +288,47 @@ class BlochOracle(Oracle):
         return [(O * ref["f"][k][None, :]) @ O.conj().T for k, (_, O) in enumerate(orbs)]
 
     def energy(self, a):
-        return self.energy_terms_k(self.density_matrices(self.orbitals_k(a)))[0]
+        orbs = self.orbitals_k(a)
+        E = self.energy_terms_k(self.density_matrices(orbs))[0]
+        if self.sic:
+            E += self.sic_terms(orbs[0][1], self.reference_k()["f"][0])[0]
+        return E
+
+    # ---- Perdew-Zunger self-interaction correction (Eq. 16-18 as read) -------------
+    def lda_x_polarized(self, n):
+        """Exchange of a fully spin-polarized density n (one spin channel):
+        e_x = -(3/4)(6/pi)^(1/3) n^(4/3), v_x = -(6/pi)^(1/3) n^(1/3) (the
+        unpolarized formula at 2n, halved: E_x^unpol[2n] = 2 E_x^pol[n])."""
+        if not self.exchange:
+            return np.zeros_like(n), np.zeros_like(n)
+        r = np.maximum(n, 0.0)
+        cx = (6.0 / math.pi) ** (1.0 / 3.0)
+        r13 = np.cbrt(r)
+        return -0.75 * cx * r * r13, -cx * r13
+
+    def sic_terms(self, O, f):
+        """PZ-SIC at one k-point (the Gamma point) for orbitals O (columns) with
+        occupations f (spin included): E_SIC = -sum_k f_k (E_H[n_k] + E_x^pol[n_k])
+        with the unit orbital densities n_k = |phi_k|^2, one self-interaction per
+        electron; the orbital potentials V^k = v_H[n_k] + v_x^pol[n_k] and the
+        matrix S with S_mk = <phi_m|V^k|phi_k>."""
+        X = self.Xk(0) if self._cache_x else None
+        E = 0.0
+        S = np.zeros((self.M, self.M), dtype=np.complex128)
+        for k in range(self.M):
+            if f[k] == 0.0:
+                continue
+            if X is not None:
+                phi = X @ O[:, k]
+            else:
+                phi = np.concatenate([Xp @ O[:, k] for _, Xp in self._planes_k(0)])
+            n = (phi.conj() * phi).real.reshape(tuple(self.n))
+            vH = self.hartree_potential(n)
+            ex, vx = self.lda_x_polarized(n)
+            E -= f[k] * (0.5 * self.dV * _fsum(n * vH) + self.dV * _fsum(ex))
+            Vk = self.potential_matrix_k(vH + vx, 0)
+            S[:, k] = O.conj().T @ (Vk @ O[:, k])
+        return E, S
 
     def energy_grad(self, a, want=False):
         """E and the real-variable gradient (nk * M^2) at the variables a."""
@@ -290,6 +336,11 @@ class BlochOracle(Oracle):
         orbs = self.orbitals_k(a)
         Ds = self.density_matrices(orbs)
         E, terms, rho, v = self.energy_terms_k(Ds)
+        if self.sic:
+            assert self.nk == 1 and not np.any(self.kfrac), "PZ-SIC at the Gamma point only"
+            E_sic, S = self.sic_terms(orbs[0][1], ref["f"][0])
+            terms = dict(terms, sic=E_sic)
+            E = E + E_sic
         g = np.empty(self.nk * self.nvar)
         extra = []
         for k, (A, O) in enumerate(orbs):
@@ -297,6 +348,11 @@ class BlochOracle(Oracle):
             Hmo = O.conj().T @ H @ O
             f = ref["f"][k]
             L = f[:, None] * Hmo - Hmo * f[None, :]
+            if self.sic:
+                # the orbital-dependent Hamiltonians H - V^k (E_SIC enters with a
+                # minus sign): L_mk += f_k <m|V^k|k> - f_m <m|V^m|k>, the second
+                # term the Hermitian conjugate of the first with m, k swapped
+                L = L + S * f[None, :] - (S * f[None, :]).conj().T
             dEda = self.grad_eq39(A, L)
             g[k * self.nvar:(k + 1) * self.nvar] = self.vars_of_grad(dEda)
             extra.append(dict(H=H, Hmo=Hmo, L=L, dEda=dEda, O=O, D=Ds[k]))

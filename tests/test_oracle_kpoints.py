@@ -408,3 +408,61 @@ def test_ss_minimization_with_reference_updates(tiny):
         if ru == 5:
             assert nu == 3
         assert abs(bo.energy_grad_approx(a)[0] - E[-1]) < 1e-12
+
+
+def _gamma_full(d):
+    g = dict(d)
+    g.update(kpts=np.zeros((1, 3)), kw=np.ones(1), kT=0.0)
+    return g
+
+
+def test_pzsic_gradient_central_differences():
+    """PZ-SIC (Eq. 16-18 as read): the Eq. 39 gradient with the SIC L matches
+    central differences of E in real and imaginary variables."""
+    d = _gamma_full(synth.config_small_molecule())
+    bo = BlochOracle(d, sic=True)
+    rng = np.random.default_rng(3)
+    a = rng.normal(0.0, 0.05, bo.nvar)
+    _, g = bo.energy_grad(a)
+    h = 1e-5
+    for i in rng.choice(bo.nvar, 16, replace=False):
+        ap, am = a.copy(), a.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (bo.energy(ap) - bo.energy(am)) / (2 * h)
+        assert abs(g[i] - fd) < 2e-9, (i, g[i], fd)
+
+
+def test_pzsic_two_electrons_in_one_orbital():
+    """One doubly occupied orbital: the self-interaction correction removes the
+    exchange exactly (E_x[2n] = 2 E_x^pol[n]) and leaves the Hartree energy of
+    the two electrons in each other's field, 2 E_H[n] = E_H[2n] / 2."""
+    d = _gamma_full(synth.tiny())
+    bo = BlochOracle(d, sic=True)
+    assert bo.n_e == 2
+    a = 0.1 * np.random.default_rng(5).normal(size=bo.nvar)
+    E, _, ex = bo.energy_grad(a, want=True)
+    t = ex["terms"]
+    assert abs(E - (t["kinetic"] + t["external"] + 0.5 * t["hartree"])) < 1e-12 * abs(E) + 1e-14
+    assert abs(t["exchange"] + t["sic"] + 0.5 * t["hartree"]) < 1e-12 * abs(t["hartree"])
+
+
+def test_pzsic_is_not_unitary_invariant():
+    """Rotations among the occupied orbitals leave the Kohn-Sham energy alone
+    but change the SIC energy; at A = 0 the occupied-occupied gradient is zero
+    for Kohn-Sham (Eq. 42) and not for PZ-SIC."""
+    d = _gamma_full(synth.config_small_molecule())
+    ks, pz = BlochOracle(d), BlochOracle(d, sic=True)
+    N, M = ks.n_e // 2, ks.M
+    A = np.zeros((M, M))
+    A[0, 1], A[1, 0] = 0.3, -0.3   # a real rotation of occupied orbitals 0 and 1
+    a = np.zeros(ks.nvar)
+    a[:M * (M - 1) // 2] = A[ks._iu]
+    z = np.zeros(ks.nvar)
+    assert abs(ks.energy(a) - ks.energy(z)) < 1e-12
+    assert abs(pz.energy(a) - pz.energy(z)) > 1e-6
+    iu = list(zip(*ks._iu))
+    occ = [p for p, (i, j) in enumerate(iu) if j < N]
+    g_ks, g_pz = ks.energy_grad(z)[1], pz.energy_grad(z)[1]
+    assert np.abs(g_ks[occ]).max() < 1e-12
+    assert np.abs(g_pz[occ]).max() > 1e-6
