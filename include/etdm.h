@@ -78,6 +78,18 @@ enum {
                         chosen by etdm_options.ref_update */
 };
 
+enum {
+  ETDM_FUNC_KS = 0,    /* the Kohn-Sham functional of Eq. 1 (unitary invariant) */
+  ETDM_FUNC_PZSIC = 1  /* Kohn-Sham plus the Perdew-Zunger self-interaction
+                          correction (Sec. 2, Eq. 16-18): E - sum_k f_k (E_H[n_k] +
+                          E_x[n_k, 0]) with the unit orbital densities n_k =
+                          |phi_k|^2 and spin-polarized Slater exchange; the
+                          gradient takes L_mk = [F, H]_mk + f_k <m|V^k|k> -
+                          f_m <m|V^m|k>, V^k = v_H[n_k] + v_x[n_k, 0].  Full-A
+                          path at the Gamma point with integer occupation
+                          (n_k <= 1 at k = 0, kT = 0), FP64 */
+};
+
 /* One periodic system (Eq. 3-5).  All host pointers, read during
  * etdm_init_basis only.  n_k = 0 is the Gamma point alone; n_k >= 1 selects
  * the full-A path over the given k-points (Bloch functions of Eq. 5 without
@@ -134,6 +146,7 @@ typedef struct {
                            (default) picks it: 2 for one system, and for a batch
                            the fastest of 2, 4 and 8 in timed evaluations at
                            set-up (the choice: ETDM_ARR_TUNE) */
+  int32_t functional;   /* ETDM_FUNC_KS (default) or ETDM_FUNC_PZSIC */
 } etdm_options;
 
 /* Fill *opt with the defaults above (FP64, m = 3, gamma 0.25, beta0 1,

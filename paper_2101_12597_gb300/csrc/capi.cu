@@ -199,6 +199,15 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
     if (opt->dense_blocks < 0) bad("dense_blocks must be >= 0");
     if (opt->dense_tc < -1 || opt->dense_tc > 1) bad("dense_tc must be -1, 0 or 1");
     if (opt->vgroup < 0 || opt->vgroup > 8) bad("vgroup must be in [0, 8]");
+    if (opt->functional != ETDM_FUNC_KS && opt->functional != ETDM_FUNC_PZSIC)
+      bad("unknown functional");
+    if (opt->functional == ETDM_FUNC_PZSIC) {
+      if (!full) bad("PZ-SIC needs the full-A path (ETDM_PARAM_FULL)");
+      if (sys->n_k > 1 || sys->kT != 0.0) bad("PZ-SIC runs at one k-point with kT = 0");
+      if (sys->n_k == 1)
+        for (int a = 0; a < 3; ++a)
+          if (sys->k_frac[a] != 0.0) bad("PZ-SIC runs at the Gamma point");
+    }
   }
 }
 
@@ -421,6 +430,7 @@ void init_impl(etdm_handle *h, const etdm_system *sys, const etdm_options *opt) 
     h->n_elec = sys->n_electrons;
     h->kexpm = o.expm;
     h->ref_every = o.ref_update;
+    h->sic = o.functional == ETDM_FUNC_PZSIC;
   }
   int ndev = 0;
   CUDA_TRY(cudaGetDeviceCount(&ndev));
@@ -724,6 +734,7 @@ void etdm_default_options(etdm_options *opt) {
   opt->expm = ETDM_EXPM_EIG;
   opt->ref_update = 0;
   opt->vgroup = 0;
+  opt->functional = ETDM_FUNC_KS;
 }
 
 int etdm_init_basis(const etdm_system *sys, const etdm_options *opt, etdm_handle **out) {

@@ -312,6 +312,10 @@ struct etdm_handle {
   double2 *d_kB = nullptr, *d_kB2 = nullptr, *d_kB3 = nullptr;  // scaling and squaring
   unsigned long long *d_knorm = nullptr;  // 1-norm of A (double bits)
   double *d_kfro = nullptr;     // Frobenius partials
+  // PZ-SIC (Gamma point, integer occupations)
+  bool sic = false;
+  double2 *d_sicD = nullptr, *d_sicV = nullptr, *d_sicS = nullptr, *d_sicX = nullptr;
+  double *d_sicn = nullptr, *d_sicv = nullptr, *d_sicpart = nullptr;
   int n[3] = {0, 0, 0};
   long G = 0;
   double L[3], h[3], dV = 0, omega = 0, sigma = 0;

@@ -71,6 +71,13 @@ void init_kpoints(etdm_handle *h, const etdm_system *sys) {
   alloc_opt_buffers(h);
   h->d_kpden = dalloc<double>(h, h->nvar);
   h->d_kpw = dalloc<double>(h, h->nvar);
+  if (h->sic) {
+    for (double2 **p : {&h->d_sicD, &h->d_sicV, &h->d_sicS}) *p = dalloc<double2>(h, MM);
+    h->d_sicX = dalloc<double2>(h, M);
+    h->d_sicn = dalloc<double>(h, h->G);
+    h->d_sicv = dalloc<double>(h, h->G);
+    h->d_sicpart = dalloc<double>(h, (size_t)std::max(h->N, 1) * k_sic_parts());
+  }
   if (h->kexpm == ETDM_EXPM_SS) {
     for (double2 **p : {&h->d_kB, &h->d_kB2, &h->d_kB3}) *p = dalloc<double2>(h, KM);
     h->d_knorm = dalloc<unsigned long long>(h, 1);
@@ -153,6 +160,42 @@ void expm_ss_k(etdm_handle *h, const double *a, double2 *U, cudaStream_t s) {
 
 }  // namespace
 
+// PZ-SIC (Gamma point, integer occupations): for each occupied orbital k the
+// unit density n_k = |phi_k|^2 (the density pass with D = O_k O_k^dagger), its
+// Hartree potential (the spectral Poisson solve) and spin-polarized exchange,
+// the energy partials of -f_k (E_H[n_k] + E_x^pol[n_k]), the orbital potential
+// matrix V^k (the V pass) and the column S[:, k] = O^dagger V^k O_k.
+void sic_orbitals_k(etdm_handle *h, cudaStream_t s) {
+  const int M = h->M;
+  const KGeom &G = h->kg;
+  const double fk = 2.0 * h->h_kw[0];
+  for (int k = 0; k < h->N; ++k) {
+    CUDA_TRY(k_rank1(h->d_kO, k, M, h->d_sicD, s));
+    CUDA_TRY(k_dr(G, h->d_sicD, h->d_kDR, s));
+    CUDA_TRY(launch_rho_k(h, h->d_kDR, h->d_sicn, s));
+    CUDA_TRY(launch_pack_real(h, h->d_sicn, h->d_fft, s));
+    CUDA_TRY(fft3d(h, h->d_fft, -1, s));
+    CUDA_TRY(launch_poisson_scale(h, h->d_fft, s));
+    CUDA_TRY(fft3d(h, h->d_fft, +1, s));
+    CUDA_TRY(k_sic_potential(h->d_sicn, h->d_fft, h->d_sicv, h->G, h->dV, fk,
+                             h->d_sicpart + (size_t)k * k_sic_parts(), s));
+    CUDA_TRY(cudaMemsetAsync(h->d_kVR, 0, (size_t)G.nR * M * M * 8, s));
+    CUDA_TRY(launch_vmat_k(h, h->d_sicv, h->d_kVR, s));
+    CUDA_TRY(k_hamiltonian(G, nullptr, h->d_kVR, h->d_sicV, s));
+    ZgemmArgs x{};  // X = V^k O_k
+    x.A = h->d_sicV; x.B = h->d_kO + k; x.C = h->d_sicX;
+    x.m = M; x.n = 1; x.k = M; x.lda = M; x.ldb = M; x.ldc = 1;
+    x.opa = 0; x.opb = 0; x.alpha = make_double2(1.0, 0.0); x.beta = make_double2(0.0, 0.0);
+    CUDA_TRY(launch_zgemm(x, 1, s));
+    ZgemmArgs y{};  // S[:, k] = O^dagger X
+    y.A = h->d_kO; y.B = h->d_sicX; y.C = h->d_sicS + k;
+    y.m = M; y.n = 1; y.k = M; y.lda = M; y.ldb = 1; y.ldc = M;
+    y.opa = 1; y.opb = 0; y.alpha = make_double2(1.0, 0.0); y.beta = make_double2(0.0, 0.0);
+    CUDA_TRY(launch_zgemm(y, 1, s));
+  }
+  h->launches += 16L * h->N;
+}
+
 void refresh_reference_k(etdm_handle *h, cudaStream_t s) {
   const int M = h->M, nk = h->nk;
   CUDA_TRY(cudaMemsetAsync(h->d_a, 0, h->nvar * 8, s));
@@ -232,10 +275,12 @@ void evaluate_k(etdm_handle *h, const double *a, double *E, double *g, cudaStrea
   CUDA_TRY(fft3d(h, h->d_fft, +1, s));
   CUDA_TRY(launch_potential(h, s));
   h->n_gridpart = kPotBlocks;
+  if (h->sic) sic_orbitals_k(h, s);
   tp.done();
   StageTimer tk(h, s, ETDM_STAGE_DENSE_REV);
   CUDA_TRY(k_energy(h->d_kD, h->d_kT, KM, h->d_kpart, h->d_gridpart, h->n_gridpart, h->d_eterms,
-                    E, h->d_flags, s));
+                    E, h->d_flags, s, h->sic ? h->d_sicpart : nullptr,
+                    h->sic ? h->N * k_sic_parts() : 0));
   h->launches += 25;
   if (!g) {
     tk.done();
@@ -252,6 +297,7 @@ void evaluate_k(etdm_handle *h, const double *a, double *E, double *g, cudaStrea
   CUDA_TRY(zgemm_sq(h->d_kH, 0, h->d_kO, 0, h->d_kX1, M, nk, s));     // H O
   CUDA_TRY(zgemm_sq(h->d_kO, 1, h->d_kX1, 0, h->d_kX2, M, nk, s));    // O^dagger H O
   CUDA_TRY(k_commutator(h->d_kX2, h->d_kf, nk, M, s));                // L
+  if (h->sic) CUDA_TRY(k_sic_L(h->d_kX2, h->d_sicS, h->d_kf, M, s));   // orbital potentials
   if (ss) {  // Eq. 42: G ~ L^T
     CUDA_TRY(k_grad_vars(h->d_kX2, g, nk, M, s));
     tg.done();

@@ -673,15 +673,18 @@ __global__ void __launch_bounds__(256) k_kinetic_kernel(const double2 *D, const 
 // E = kinetic + external + Hartree + exchange (Eq. 1) from the partials.
 __global__ void __launch_bounds__(1024) k_energy_kernel(const double *kpart, int nkp,
                                                         const double *gridpart, int ngp,
+                                                        const double *sicpart, int nsp,
                                                         double *eterms, double *E, int *flags) {
-  double kin = 0.0, t3[3] = {0.0, 0.0, 0.0};
+  double kin = 0.0, t3[3] = {0.0, 0.0, 0.0}, sic = 0.0;
   for (int b = threadIdx.x; b < nkp; b += blockDim.x) kin += kpart[b];
+  for (int b = threadIdx.x; b < nsp; b += blockDim.x) sic += sicpart[b];
   for (int b = threadIdx.x; b < ngp; b += blockDim.x)
     for (int q = 0; q < 3; ++q) t3[q] += gridpart[3 * b + q];
   kin = block_sum(kin);
+  sic = block_sum(sic);
   for (int q = 0; q < 3; ++q) t3[q] = block_sum(t3[q]);
   if (threadIdx.x == 0) {
-    const double e = kin + t3[0] + t3[1] + t3[2];
+    const double e = kin + t3[0] + t3[1] + t3[2] + sic;
     eterms[0] = kin; eterms[1] = t3[0]; eterms[2] = t3[1]; eterms[3] = t3[2];
     if (E) *E = e;
     if (!(e == e) || isinf(e)) atomicExch(flags + FLAG_ERR, ETDM_ERR_NUMERIC);
@@ -832,6 +835,64 @@ __global__ void k_overlap_kinetic_kernel(const double *center, const double *alp
   }
 }
 
+static int k_blocks(long n);
+
+// ---- Perdew-Zunger self-interaction correction (Gamma point) ------------------------
+// D = O_k O_k^dagger for orbital column k (the unit orbital density's matrix)
+__global__ void k_rank1_kernel(const double2 *O, int k, int M, double2 *D) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < MM; q += (long)gridDim.x * blockDim.x) {
+    const int mu = (int)(q / M), nu = (int)(q % M);
+    D[q] = cmul(O[(long)mu * M + k], cconj(O[(long)nu * M + k]));
+  }
+}
+
+// v_k = v_H[n_k] + v_x^pol[n_k] with v_x^pol = -(6/pi)^(1/3) n^(1/3) (a fully
+// polarized density), and the block partials of -f_k (E_H + E_x^pol):
+// part[b] = -f_k dV (sum n v_H / 2 + sum e_x^pol), e_x^pol = 3/4 n v_x^pol
+__global__ void __launch_bounds__(256) k_sic_potential_kernel(const double *n, const double2 *vh,
+                                                              double *v, long G, double dV,
+                                                              double fk, double *part) {
+  const double cx = cbrt(6.0 / M_PI);
+  double s = 0.0;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < G; e += (long)gridDim.x * blockDim.x) {
+    const double r = n[e];
+    const double rp = r > 0.0 ? r : 0.0;
+    const double vx = -cx * cbrt(rp);
+    const double h = vh[e].x;
+    v[e] = h + vx;
+    s += 0.5 * r * h + 0.75 * rp * vx;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = -fk * dV * s;
+}
+
+// L += S diag(f) - (S diag(f))^dagger, S_mk = <phi_m|V^k|phi_k>
+__global__ void k_sic_L_kernel(double2 *L, const double2 *S, const double *f, int M) {
+  const long MM = (long)M * M;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < MM; q += (long)gridDim.x * blockDim.x) {
+    const int m = (int)(q / M), k = (int)(q % M);
+    const double2 a = cscale(S[q], f[k]);
+    const double2 b = cscale(cconj(S[(long)k * M + m]), f[m]);
+    L[q] = cadd(L[q], csub(a, b));
+  }
+}
+
+cudaError_t k_rank1(const double2 *O, int k, int M, double2 *D, cudaStream_t s) {
+  k_rank1_kernel<<<k_blocks((long)M * M), 256, 0, s>>>(O, k, M, D);
+  return cudaGetLastError();
+}
+int k_sic_parts() { return 256; }
+cudaError_t k_sic_potential(const double *n, const double2 *vh, double *v, long G, double dV,
+                            double fk, double *part, cudaStream_t s) {
+  k_sic_potential_kernel<<<k_sic_parts(), 256, 0, s>>>(n, vh, v, G, dV, fk, part);
+  return cudaGetLastError();
+}
+cudaError_t k_sic_L(double2 *L, const double2 *S, const double *f, int M, cudaStream_t s) {
+  k_sic_L_kernel<<<k_blocks((long)M * M), 256, 0, s>>>(L, S, f, M);
+  return cudaGetLastError();
+}
+
 // ---- launchers ------------------------------------------------------------------------
 static int k_blocks(long n) {
   long b = (n + 255) / 256;
@@ -955,9 +1016,10 @@ cudaError_t k_grad_vars(const double2 *GT, double *g, int nk, int M, cudaStream_
 int k_kinetic_parts() { return 512; }
 cudaError_t k_energy(const double2 *D, const double2 *T, long n, double *part,
                      const double *gridpart, int ngp, double *eterms, double *E, int *flags,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double *sicpart, int nsp) {
   k_kinetic_kernel<<<k_kinetic_parts(), 256, 0, s>>>(D, T, n, part);
-  k_energy_kernel<<<1, 1024, 0, s>>>(part, k_kinetic_parts(), gridpart, ngp, eterms, E, flags);
+  k_energy_kernel<<<1, 1024, 0, s>>>(part, k_kinetic_parts(), gridpart, ngp, sicpart, nsp, eterms,
+                                     E, flags);
   return cudaGetLastError();
 }
 cudaError_t k_occupation(const double *eps, const double *kw, int nk, int M, double ne, double kT,

@@ -56,7 +56,14 @@ cudaError_t k_grad_vars(const double2 *GT, double *g, int nk, int M, cudaStream_
 int k_kinetic_parts();
 cudaError_t k_energy(const double2 *D, const double2 *T, long n, double *part,
                      const double *gridpart, int ngp, double *eterms, double *E, int *flags,
-                     cudaStream_t s);
+                     cudaStream_t s, const double *sicpart = nullptr, int nsp = 0);
+// PZ-SIC (Gamma point): orbital density matrix, orbital potential and energy
+// partials, the L correction
+cudaError_t k_rank1(const double2 *O, int k, int M, double2 *D, cudaStream_t s);
+int k_sic_parts();
+cudaError_t k_sic_potential(const double *n, const double2 *vh, double *v, long G, double dV,
+                            double fk, double *part, cudaStream_t s);
+cudaError_t k_sic_L(double2 *L, const double2 *S, const double *f, int M, cudaStream_t s);
 cudaError_t k_occupation(const double *eps, const double *kw, int nk, int M, double ne, double kT,
                          double *f, double *mu, cudaStream_t s);
 cudaError_t k_diag(const double2 *C, const double2 *X, double *out, int nk, int M, cudaStream_t s);
@@ -72,6 +79,8 @@ void evaluate_k(etdm_handle *h, const double *a, double *E, double *g, cudaStrea
 // Eq. 33 orbital energies and preconditioner parts at the current reference
 // (one evaluation at A = 0, E into h->d_E and the gradient into h->d_g)
 void refresh_reference_k(etdm_handle *h, cudaStream_t s);
+// PZ-SIC terms of the current orbitals (Gamma point): energy partials and S
+void sic_orbitals_k(etdm_handle *h, cudaStream_t s);
 // reference update of Sec. 3.5: C0 <- C0 exp(A(a)), a <- 0, then the refresh
 void reference_update_k(etdm_handle *h, double *a, cudaStream_t s);
 // |L| and |[A, L]| (Frobenius, all k-points) with L rebuilt from an

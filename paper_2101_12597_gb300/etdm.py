@@ -21,6 +21,7 @@ STATUS = {0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NOT_CONVERGED"
 PRECISION = {"fp64": 0, "mixed": 1}
 PARAM = {"occvirt": 0, "full": 1}
 EXPM = {"eig": 0, "ss": 1}
+FUNCTIONAL = {"ks": 0, "pzsic": 1}
 ARRAYS = {"S": (0, np.float64), "T": (1, np.float64), "C0": (2, np.float64),
           "order": (3, np.int32), "vext": (4, np.float64), "rho": (5, np.float64),
           "vtot": (6, np.float64), "H": (7, np.float64), "D": (8, np.float64),
@@ -81,7 +82,8 @@ class EtdmOptions(ctypes.Structure):
                 ("param", ctypes.c_int32),
                 ("expm", ctypes.c_int32),
                 ("ref_update", ctypes.c_int32),
-                ("vgroup", ctypes.c_int32)]
+                ("vgroup", ctypes.c_int32),
+                ("functional", ctypes.c_int32)]
 
 
 _lib = None
@@ -233,7 +235,7 @@ def _system_struct(sysd, s=None):
 
 
 def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc=0,
-             param="occvirt", expm="eig", ref_update=0, vgroup=0):
+             param="occvirt", expm="eig", ref_update=0, vgroup=0, functional="ks"):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision]
@@ -247,6 +249,7 @@ def _options(lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_
     o.expm = EXPM[expm]
     o.ref_update = ref_update
     o.vgroup = vgroup
+    o.functional = FUNCTIONAL[functional]
     return o
 
 
@@ -257,10 +260,12 @@ class ETDM:
     then Im a_ij for i <= j, per k-point).  On that path expm="ss" evaluates
     exp(A) by scaling and squaring with the approximate gradient G ~ L^T, and
     ref_update (n > 0: every n steps, -1: the |L| < 3 |[A, L]| test) makes
-    minimize() move the reference, C0 <- C0 exp(A), A <- 0."""
+    minimize() move the reference, C0 <- C0 exp(A), A <- 0; functional="pzsic"
+    adds the Perdew-Zunger self-interaction correction (Gamma point, kT = 0)."""
 
     def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
-                 device=0, dense_blocks=0, dense_tc=0, param=None, expm="eig", ref_update=0):
+                 device=0, dense_blocks=0, dense_tc=0, param=None, expm="eig", ref_update=0,
+                 functional="ks"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
@@ -271,7 +276,7 @@ class ETDM:
             param = "full" if sysd.get("kpts") is not None else "occvirt"
         self.full = param == "full"
         o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc,
-                     param, expm, ref_update)
+                     param, expm, ref_update, functional=functional)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))

@@ -41,8 +41,8 @@ def test_default_options(lib):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     assert (o.precision, o.lbfgs_m, o.gamma, o.beta0, o.device, o.dense_blocks,
-            o.dense_tc, o.param, o.expm, o.ref_update, o.vgroup) == (0, 3, 0.25, 1.0, 0, 0, 0, 0, 0,
-                                                                      0, 0)
+            o.dense_tc, o.param, o.expm, o.ref_update, o.vgroup,
+            o.functional) == (0, 3, 0.25, 1.0, 0, 0, 0, 0, 0, 0, 0, 0)
 
 
 def _system(lib, d, **over):
@@ -153,6 +153,31 @@ def test_ss_options_checked(lib, expm, ref, full, frag):
     o = EtdmOptions()
     lib.etdm_default_options(ctypes.byref(o))
     o.expm, o.ref_update = expm, ref
+    h = ctypes.c_void_p()
+    rc = lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
+    assert rc == -1
+    assert frag in lib.etdm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kT,kfrac,param,frag", [
+    (0.0, None, 0, "full-A path"),
+    (0.01, (0.0, 0.0, 0.0), 1, "kT = 0"),
+    (0.0, (0.25, 0.0, 0.0), 1, "Gamma point"),
+])
+def test_pzsic_options_checked(lib, kT, kfrac, param, frag):
+    from paper_2101_12597_gb300.etdm import EtdmOptions
+    d = synth.config_small_molecule()
+    s, keep = _system(lib, d)
+    if kfrac is not None:
+        kf = np.array(kfrac, dtype=np.float64)
+        w = np.ones(1)
+        keep.update(kf=kf, w=w)
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        s.n_k, s.k_frac, s.k_w = 1, dp(kf), dp(w)
+    s.kT = kT
+    o = EtdmOptions()
+    lib.etdm_default_options(ctypes.byref(o))
+    o.functional, o.param = 1, param
     h = ctypes.c_void_p()
     rc = lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))
     assert rc == -1
