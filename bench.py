@@ -845,8 +845,10 @@ def run_kpoints(args):
     t_max = reduce_max(total_ms, world, dev)
     all_evals = reduce_sum(evals, world, dev)
     value = all_evals / (t_max / 1e3)
-    # end to end through the host-buffer entry point
-    a_host = np.ascontiguousarray(d["a0"])
+    # end to end through the host-buffer entry point (at the workload's seeded
+    # variables when they are full-A variables, else at A = 0)
+    a_host = np.ascontiguousarray(d["a0"]) if np.size(d["a0"]) == solver.nvar \
+        else np.zeros(solver.var_shape)
     solver.energy_grad_host(a_host)
     torch.cuda.synchronize()
     n_e2e = min(args.steps, 5)

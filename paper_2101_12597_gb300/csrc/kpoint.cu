@@ -126,11 +126,11 @@ cudaError_t zgemm_sq(const double2 *A, int opa, const double2 *B, int opb, doubl
 
 // ---- Hermitian eigensolver (FP64) ------------------------------------------------
 // A = V diag(w) V^dagger for a batch of n x n Hermitian matrices, in three
-// kernels: Householder reduction to a tridiagonal T = Q^dagger A Q (one block
-// per matrix, the matrix held in L2), implicit QL iterations with Wilkinson
-// shifts on the real tridiagonal Phi^dagger T Phi (Phi a diagonal of phases;
-// one block per matrix, rotations applied by all threads to the rows of Z),
-// and the back-transformation V = Q Phi Z (blocks over slabs of columns).
+// kernels: Householder reduction to a tridiagonal T = Q^dagger A Q (a group
+// of blocks per matrix, the matrix held in L2), implicit QL iterations with
+// Wilkinson shifts on the real tridiagonal Phi^dagger T Phi (Phi a diagonal of
+// phases; the sweeps replicated in blocks of rows of Z), and the
+// back-transformation V = Q Phi Z (blocks over slabs of columns).
 // Eigenvalues ascending.
 
 // Reflector j maps x = A[j+1 .., j] to alpha e_1: H_j = I - 2 u u^dagger with
@@ -138,60 +138,113 @@ cudaError_t zgemm_sq(const double2 *A, int opa, const double2 *B, int opb, doubl
 // in hv[j][j+1 ..] (zero when the column is already reduced).  The trailing
 // block becomes H A H = A - 2 u w^dagger - 2 w u^dagger, w = p - (u^dagger p) u,
 // p = A u.  d[j] = Re A[j][j], e[j] = T[j+1][j].
-__global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb, double *db,
-                                                       double2 *eb, int n) {
-  extern __shared__ double2 zsm[];
-  double2 *u = zsm;       // [n]
-  double2 *p = zsm + n;   // [n]
-  __shared__ double2 alpha_s;
-  __shared__ int skip_s;
-  const int b = blockIdx.x;
-  double2 *A = Ab + (long)b * n * n;
-  double2 *hv = hvb + (long)b * n * n;
-  double *d = db + (long)b * n;
-  double2 *e = eb + (long)b * n;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int j = 0; j + 1 < n; ++j) {
-    const int m = n - j - 1, o = j + 1;
-    for (int i = tid; i < m; i += nt) u[i] = A[(long)(o + i) * n + j];
-    __syncthreads();
-    double tail = 0.0;
-    for (int i = 1 + tid; i < m; i += nt) tail += u[i].x * u[i].x + u[i].y * u[i].y;
-    tail = block_sum(tail);
-    if (tid == 0) {
-      const double2 x0 = u[0];
-      const double ax0 = hypot(x0.x, x0.y);
-      if (tail == 0.0) {  // already reduced: no reflection
-        skip_s = 1;
-        alpha_s = x0;
-      } else {
-        const double xn = sqrt(ax0 * ax0 + tail);
-        const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-        alpha_s = make_double2(-ph.x * xn, -ph.y * xn);
-        const double v0 = ax0 + xn;                   // v_0 = ph (|x_0| + |x|)
-        const double inv = 1.0 / sqrt(v0 * v0 + tail);  // 1 / |v|
-        u[0] = make_double2(ph.x * v0 * inv, ph.y * v0 * inv);
-        p[0] = make_double2(inv, 0.0);                // scale of the other entries
-        skip_s = 0;
+// The reduction runs on a group of G blocks per matrix (a cooperative launch,
+// gridDim = (G, batch)): row i of the trailing matrix belongs to block
+// i mod G.  Step j: the owner of row j forms the reflector from that row (the
+// column below the diagonal, conjugated) and publishes u; after a group
+// barrier every block forms p_i = (A_t u)_i for its rows and a partial of
+// K = u^dagger p; after a second barrier every block forms w = p - K u and
+// applies the rank-2 update to its rows.  The group barrier is two words per
+// matrix, its waits bounded (ETDM_ERR_TIMEOUT, then every block returns).
+struct HtrdWork {
+  double2 *u;      // [batch][n] reflector of the current step
+  double2 *p;      // [batch][n] A_t u
+  double *kpart;   // [batch][G] partials of u^dagger p
+  int *skip;       // [batch] the current step needs no reflection
+  unsigned *bar;   // [batch][2] group barrier: count, generation
+};
+
+__device__ __forceinline__ bool group_barrier(unsigned *bar, unsigned nb, int *flags) {
+  __syncthreads();
+  if (nb == 1) return true;
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = ld_acquire_gpu(bar + 1);
+    const unsigned arrived = atom_add_acq_rel_gpu(bar, 1u);
+    if (arrived == nb - 1) {
+      st_relaxed_gpu(bar, 0u);
+      st_release_gpu(bar + 1, g + 1);
+    } else {
+      long it = 0;
+      while (ld_acquire_gpu(bar + 1) == g) {
+        if (++it > kSpinLimit) {
+          atomicExch(flags + FLAG_ERR, ETDM_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
     }
-    __syncthreads();
-    if (tid == 0) e[j] = alpha_s;
-    double2 *hrow = hv + (long)j * n;
-    if (skip_s) {
-      for (int i = tid; i < n; i += nt) hrow[i] = make_double2(0.0, 0.0);
+    if (*(volatile int *)(flags + FLAG_ERR) == ETDM_ERR_TIMEOUT) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(512) zhetrd_group_kernel(double2 *Ab, double2 *hvb, double *db,
+                                                            double2 *eb, int n, HtrdWork W,
+                                                            int *flags) {
+  extern __shared__ double2 hsm[];
+  double2 *u = hsm;       // [n]
+  double2 *w = hsm + n;   // [n]
+  __shared__ double2 alpha_s;
+  __shared__ double inv_s, kr_s;
+  __shared__ int skip_s;
+  const int b = blockIdx.y, G = gridDim.x, r = blockIdx.x;
+  double2 *A = Ab + (long)b * n * n;
+  double2 *hv = hvb + (long)b * n * n;
+  double2 *ug = W.u + (long)b * n, *pg = W.p + (long)b * n;
+  double *kp = W.kpart + (long)b * G;
+  unsigned *bar = W.bar + 2 * b;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = n - j - 1, o = j + 1;
+    __syncthreads();  // this block's updates of its rows (row j among them) are done
+    if (j % G == r) {  // the owner of row j: the reflector from conj(A[j][o..])
+      const double2 *row = A + (long)j * n + o;
+      double tail = 0.0;
+      for (int l = 1 + tid; l < m; l += nt) tail += row[l].x * row[l].x + row[l].y * row[l].y;
+      tail = block_sum(tail);
+      if (tid == 0) {
+        const double2 x0 = cconj(row[0]);
+        const double ax0 = hypot(x0.x, x0.y);
+        if (tail == 0.0) {
+          skip_s = 1;
+          alpha_s = x0;
+        } else {
+          const double xn = sqrt(ax0 * ax0 + tail);
+          const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+          alpha_s = make_double2(-ph.x * xn, -ph.y * xn);
+          const double v0 = ax0 + xn;
+          const double inv = 1.0 / sqrt(v0 * v0 + tail);
+          inv_s = inv;
+          ug[0] = make_double2(ph.x * v0 * inv, ph.y * v0 * inv);
+          skip_s = 0;
+        }
+        W.skip[b] = skip_s;
+        eb[(long)b * n + j] = alpha_s;
+      }
       __syncthreads();
+      double2 *hrow = hv + (long)j * n;
+      if (skip_s) {
+        for (int i = tid; i < n; i += nt) hrow[i] = make_double2(0.0, 0.0);
+      } else {
+        for (int l = 1 + tid; l < m; l += nt) ug[l] = cscale(cconj(row[l]), inv_s);
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) hrow[i] = i >= o ? ug[i - o] : make_double2(0.0, 0.0);
+      }
+    }
+    if (!group_barrier(bar, G, flags)) return;
+    if (*(volatile int *)(W.skip + b)) {
+      if (!group_barrier(bar, G, flags)) return;  // (keeps the barrier count of the group)
       continue;
     }
-    const double inv = p[0].x;
+    for (int l = tid; l < m; l += nt) u[l] = ug[l];
     __syncthreads();
-    for (int i = 1 + tid; i < m; i += nt) u[i] = cscale(u[i], inv);
-    __syncthreads();
-    for (int i = tid; i < n; i += nt) hrow[i] = i >= o ? u[i - o] : make_double2(0.0, 0.0);
-    // p = A_t u: a warp per row, four independent partial sums per lane so
-    // that four loads of the row are in flight at once
-    for (int i = warp; i < m; i += nw) {
+    // p_i = (A_t u)_i for the rows of this block: a warp per row
+    double kpart = 0.0;
+    for (int q = warp; (long)q * G + ((r - o % G + G) % G) < m; q += nw) {
+      const int i = q * G + ((r - o % G + G) % G);  // trailing row index with (o + i) % G == r
       const double2 *row = A + (long)(o + i) * n + o;
       double2 s4[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
                        make_double2(0.0, 0.0)};
@@ -204,23 +257,33 @@ __global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb,
         cfma(s4[3], a3, u[l + 96]);
       }
       for (; l < m; l += 32) cfma(s4[0], row[l], u[l]);
-      double2 s = cadd(cadd(s4[0], s4[1]), cadd(s4[2], s4[3]));
-      for (int q = 16; q > 0; q >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, q);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, q);
+      double2 sv = cadd(cadd(s4[0], s4[1]), cadd(s4[2], s4[3]));
+      for (int sh = 16; sh > 0; sh >>= 1) {
+        sv.x += __shfl_xor_sync(0xffffffffu, sv.x, sh);
+        sv.y += __shfl_xor_sync(0xffffffffu, sv.y, sh);
       }
-      if (lane == 0) p[i] = s;
+      if (lane == 0) {
+        pg[i] = sv;
+        kpart += u[i].x * sv.x + u[i].y * sv.y;  // Re(conj(u_i) p_i)
+      }
+    }
+    kpart = block_sum(kpart);
+    if (tid == 0) kp[r] = kpart;
+    if (!group_barrier(bar, G, flags)) return;
+    if (tid == 0) {
+      double k = 0.0;
+      for (int q = 0; q < G; ++q) k += kp[q];
+      kr_s = k;
     }
     __syncthreads();
-    double kr = 0.0;  // K = u^dagger p (real for Hermitian A)
-    for (int i = tid; i < m; i += nt) kr += u[i].x * p[i].x + u[i].y * p[i].y;
-    kr = block_sum(kr);
-    for (int i = tid; i < m; i += nt) p[i] = csub(p[i], cscale(u[i], kr));
+    const double kr = kr_s;
+    for (int l = tid; l < m; l += nt) w[l] = csub(pg[l], cscale(u[l], kr));
     __syncthreads();
-    // A_t -= 2 (u w^dagger + w u^dagger): a warp per row, lanes along it
-    for (int i = warp; i < m; i += nw) {
+    // A_t -= 2 (u w^dagger + w u^dagger) on this block's rows
+    for (int q = warp; (long)q * G + ((r - o % G + G) % G) < m; q += nw) {
+      const int i = q * G + ((r - o % G + G) % G);
       double2 *row = A + (long)(o + i) * n + o;
-      const double2 ui = cscale(u[i], 2.0), wi = cscale(p[i], 2.0);
+      const double2 ui = cscale(u[i], 2.0), wi = cscale(w[i], 2.0);
       int l = lane;
       for (; l + 96 < m; l += 128) {
         double2 a[4];
@@ -229,24 +292,23 @@ __global__ void __launch_bounds__(1024) zhetrd_kernel(double2 *Ab, double2 *hvb,
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int c = l + 32 * k;
-          double2 t = cmul(ui, cconj(p[c]));
+          double2 t = cmul(ui, cconj(w[c]));
           cfma(t, wi, cconj(u[c]));
           row[c] = csub(a[k], t);
         }
       }
       for (; l < m; l += 32) {
-        double2 t = cmul(ui, cconj(p[l]));
+        double2 t = cmul(ui, cconj(w[l]));
         cfma(t, wi, cconj(u[l]));
         row[l] = csub(row[l], t);
       }
     }
-    __syncthreads();
   }
-  for (int i = tid; i < n; i += nt) d[i] = A[(long)i * n + i].x;
-  if (tid == 0) {
-    e[n - 1] = make_double2(0.0, 0.0);
-    if (n >= 1) for (int i = 0; i < n; ++i) hv[(long)(n - 1) * n + i] = make_double2(0.0, 0.0);
-  }
+  if (!group_barrier(bar, G, flags)) return;
+  for (int i = r * nt + tid; i < n; i += G * nt) db[(long)b * n + i] = A[(long)i * n + i].x;
+  if (r == 0 && tid == 0) eb[(long)b * n + n - 1] = make_double2(0.0, 0.0);
+  if (r == 0)
+    for (int i = tid; i < n; i += nt) hv[(long)(n - 1) * n + i] = make_double2(0.0, 0.0);
 }
 
 // Implicit QL with Wilkinson shifts on the real tridiagonal (d, |e|).  The
@@ -267,6 +329,18 @@ struct QlSweep {
 // sqrt(x^2 + y^2) for the magnitudes of a normalized eigenproblem (no overflow
 // below 1e150)
 __device__ __forceinline__ double ql_norm(double x, double y) { return sqrt(fma(x, x, y * y)); }
+
+// 1 / sqrt(x) for x in [1e-30, 1e30]: a single-precision seed (relative error
+// below 2^-21) refined by two Newton-Raphson steps y <- y (3 - x y^2) / 2, each
+// of which squares the relative error (2^-42, then below the FP64 rounding):
+// the QL sweep's only square root and division, in fewer dependent FP64
+// operations than a correctly rounded sqrt and divide
+__device__ __forceinline__ double ql_rsqrt(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y;
+}
 
 __global__ void __launch_bounds__(64) ztql_kernel(const double *db, const double2 *eb, double *wb,
                                                    double2 *phib, double *Ztb, int *permb,
@@ -342,14 +416,21 @@ __global__ void __launch_bounds__(64) ztql_kernel(const double *db, const double
         int i = m - 1;
         for (; i >= l; --i) {
           const double f = s * e[i], bb = c * e[i];
-          r = ql_norm(f, g);
+          const double x = fma(f, f, g * g);
+          double inv;
+          if (x >= 1e-30 && x <= 1e30) {
+            inv = ql_rsqrt(x);
+            r = x * inv;
+          } else {
+            r = sqrt(x);
+            inv = 1.0 / r;
+          }
           e[i + 1] = r;
           if (r == 0.0) {  // underflow: deflate here
             d[i + 1] -= pp;
             e[m] = 0.0;
             break;
           }
-          const double inv = 1.0 / r;
           s = f * inv;
           c = g * inv;
           g = d[i + 1] - pp;
@@ -447,9 +528,12 @@ __global__ void __launch_bounds__(256) zback_kernel(const double2 *hvb, const do
   }
 }
 
+constexpr int kHtrdGroup = 16;  // blocks per matrix of the group reduction, at most
+
 size_t heev_work_bytes(int n, int batch) {
   const size_t nn = (size_t)n * n * batch;
-  return nn * 16 /* hv */ + nn * 8 /* Z */ + (size_t)n * batch * (8 + 16 + 16 + 4) + 256 * 6;
+  return nn * 16 /* hv */ + nn * 8 /* Z */ + (size_t)n * batch * (8 + 16 + 16 + 4) +
+         (size_t)batch * (2 * n * 16 + kHtrdGroup * 8 + 4 + 8) + 256 * 12;
 }
 
 // A (destroyed) -> w ascending, V (columns); work from heev_work_bytes.
@@ -464,13 +548,35 @@ cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, voi
   double *d = (double *)p; p += al((size_t)n * batch * 8);
   double2 *e = (double2 *)p; p += al((size_t)n * batch * 16);
   double2 *phi = (double2 *)p; p += al((size_t)n * batch * 16);
-  int *perm = (int *)p;
+  int *perm = (int *)p; p += al((size_t)n * batch * 4);
+  HtrdWork hw;
+  hw.u = (double2 *)p; p += al((size_t)batch * n * 16);
+  hw.p = (double2 *)p; p += al((size_t)batch * n * 16);
+  hw.kpart = (double *)p; p += al((size_t)batch * kHtrdGroup * 8);
+  hw.skip = (int *)p; p += al((size_t)batch * 4);
+  hw.bar = (unsigned *)p;
   cudaError_t err;
   const int smt = 2 * n * (int)sizeof(double2);
-  err = cudaFuncSetAttribute(zhetrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smt);
+  err = cudaFuncSetAttribute(zhetrd_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smt);
   if (err != cudaSuccess) return err;
-  zhetrd_kernel<<<batch, 1024, smt, s>>>(A, hv, d, e, n);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  // blocks per matrix: up to kHtrdGroup, about 32 rows each, all co-resident
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zhetrd_group_kernel, 512, smt)) !=
+      cudaSuccess)
+    return err;
+  int G = std::min(kHtrdGroup, std::max(1, (n + 31) / 32));
+  while (G > 1 && (long)G * batch > (long)sms * per_sm) --G;
+  if ((long)G * batch > (long)sms * per_sm) return cudaErrorInvalidConfiguration;
+  if ((err = cudaMemsetAsync(hw.bar, 0, (size_t)batch * 2 * sizeof(unsigned), s)) != cudaSuccess)
+    return err;
+  {
+    void *args[] = {&A, &hv, &d, &e, &n, &hw, &flags};
+    err = cudaLaunchCooperativeKernel((void *)zhetrd_group_kernel, dim3(G, batch), dim3(512), args,
+                                      smt, s);
+    if (err != cudaSuccess) return err;
+  }
   // rows of Z per block: up to kQlRows, as many as 200 KB of shared memory holds
   const int rows = std::max(1, std::min(kQlRows, (200 * 1024 / 8 - 6 * n) / n));
   const int smq = (6 * n + n * rows) * (int)sizeof(double);

@@ -253,3 +253,18 @@ def test_float_pair_dot_sub():
         A, B, Cc, D = [x[0] + x[1] for x in (a, b, c, d)]
         h, l = dot_sub(a, b, c, d)
         assert abs(h + l - (A * B - Cc * D)) <= F(2) ** -43 * (abs(A * B) + abs(Cc * D))
+
+
+def test_ql_reciprocal_square_root():
+    """The QL sweeps' 1/sqrt (kpoint.cu, ql_rsqrt): a single-precision seed
+    with any relative error up to 2^-21, refined by two Newton-Raphson steps
+    y <- y (3 - x y^2) / 2 in FP64, is within 2 ulp of 1/sqrt(x) over the
+    range it is used on, [1e-30, 1e30]."""
+    rng = np.random.default_rng(0)
+    x = np.exp(rng.uniform(np.log(1e-30), np.log(1e30), 200000))
+    y = (1.0 / np.sqrt(x.astype(np.float32))).astype(np.float64)
+    y = y * (1.0 + rng.uniform(-2.0 ** -21, 2.0 ** -21, x.size))
+    for _ in range(2):
+        y = y * (1.5 - (0.5 * x) * (y * y))
+    rel = np.abs(y - 1.0 / np.sqrt(x)) * np.sqrt(x)
+    assert rel.max() < 2.0 * 2.0 ** -52
