@@ -307,6 +307,7 @@ struct etdm_handle {
   void *d_kwork = nullptr;      // eigensolver workspace
   bool kref_set = false;        // reference given by etdm_set_reference
   int kexpm = 0;                // ETDM_EXPM_EIG (Eq. 35, Eq. 39) or ETDM_EXPM_SS (Eq. 38, Eq. 42)
+  int tri_method = 1;           // tridiagonal eigenpairs of iA(k): 1 bisection + inverse iteration, 0 QL
   int ref_every = 0;            // reference updates in etdm_minimize (ETDM_EXPM_SS)
   long long ref_updates = 0;    // reference updates made so far
   double2 *d_kB = nullptr, *d_kB2 = nullptr, *d_kB3 = nullptr;  // scaling and squaring

@@ -249,7 +249,8 @@ void evaluate_k(etdm_handle *h, const double *a, double *E, double *g, cudaStrea
   } else {  // U = exp(A) through the eigendecomposition of iA (Eq. 35)
     StageTimer te(h, s, ETDM_STAGE_EIG);
     CUDA_TRY(k_build_iA(a, nk, M, h->d_kX1, s));
-    CUDA_TRY(launch_heev(h->d_kX1, h->d_komega, h->d_kW, M, nk, h->d_kwork, h->d_flags, s));
+    CUDA_TRY(launch_heev(h->d_kX1, h->d_komega, h->d_kW, M, nk, h->d_kwork, h->d_flags, s,
+                         h->tri_method));
     te.done();
   }
   StageTimer tf(h, s, ETDM_STAGE_DENSE_FWD);

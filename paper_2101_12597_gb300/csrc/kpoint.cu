@@ -484,6 +484,238 @@ __global__ void __launch_bounds__(64) ztql_kernel(const double *db, const double
     }
 }
 
+// ---- tridiagonal eigenpairs by bisection and inverse iteration --------------------
+// The parallel alternative to the QL sweeps for the real tridiagonal (d, |e|):
+// the matrix splits where an off-diagonal is negligible; slot i (row i) is the
+// (i - p)-th eigenpair of the block [p, q) containing row i.  Each thread finds
+// its eigenvalue by bisection on the block's Sturm count (in parallel over the
+// eigenvalues), then inverse iteration (tridiagonal LU with partial pivoting,
+// three solves from a pseudo-random start) gives its vector, supported on the
+// block.  Eigenvalues of a block closer than 1e-3 |T| form a cluster (a
+// rank-deficient A gives one large cluster at zero): a block per cluster then
+// orthonormalizes the cluster's vectors in order by classical Gram-Schmidt
+// applied twice, which leaves an orthonormal basis of the cluster's invariant
+// subspace.  Then the eigenvalues are ranked.
+__device__ __forceinline__ bool tri_split(const double *d, const double *ae, int j) {
+  // off-diagonal j (between rows j and j + 1) is negligible
+  return ae[j] <= 2.2204460492503131e-16 * (fabs(d[j]) + fabs(d[j + 1])) || ae[j] <= 1e-300;
+}
+
+// the block [p, q) containing row i
+__device__ void tri_block(const double *d, const double *ae, int n, int i, int *p, int *q) {
+  int a = i, b = i + 1;
+  while (a > 0 && !tri_split(d, ae, a - 1)) --a;
+  while (b < n && !tri_split(d, ae, b - 1)) ++b;
+  *p = a;
+  *q = b;
+}
+
+// eigenvalues of block [p, q) below x (Sturm count; a pivot of magnitude below
+// pivmin is replaced by -pivmin)
+__device__ int tri_count(const double *d, const double *ae, int p, int q, double x, double pivmin) {
+  int c = 0;
+  double v = d[p] - x;
+  if (fabs(v) < pivmin) v = -pivmin;
+  c += v < 0.0;
+  for (int j = p + 1; j < q; ++j) {
+    v = (d[j] - x) - ae[j - 1] * ae[j - 1] / v;
+    if (fabs(v) < pivmin) v = -pivmin;
+    c += v < 0.0;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(128) tri_bisect_kernel(const double *db, const double2 *eb,
+                                                          double *lam, double *aeb, int n) {
+  const int b = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double *d = db + (long)b * n;
+  double *ae = aeb + (long)b * n;
+  // |e| once per matrix (block 0 of the matrix writes, the others compute their own copy)
+  __shared__ double sae[kEigMax], sd[kEigMax];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double2 ej = eb[(long)b * n + j];
+    sae[j] = j < n - 1 ? hypot(ej.x, ej.y) : 0.0;
+    sd[j] = d[j];
+    if (blockIdx.x == 0) ae[j] = sae[j];
+  }
+  __syncthreads();
+  if (i >= n) return;
+  int p, q;
+  tri_block(sd, sae, n, i, &p, &q);
+  const int li = i - p;
+  double lo = 1e300, hi = -1e300, emax = 0.0;  // Gershgorin bounds of the block
+  for (int j = p; j < q; ++j) {
+    const double r = (j > p ? sae[j - 1] : 0.0) + (j + 1 < q ? sae[j] : 0.0);
+    lo = fmin(lo, sd[j] - r);
+    hi = fmax(hi, sd[j] + r);
+    if (j + 1 < q) emax = fmax(emax, sae[j]);
+  }
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax * emax);
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  lo -= 2.2e-16 * tnorm + pivmin;
+  hi += 2.2e-16 * tnorm + pivmin;
+  for (int it = 0; it < 200; ++it) {  // invariant: count(lo) <= li < count(hi)
+    const double mid = 0.5 * (lo + hi);
+    if (!(hi - lo > 2.2e-16 * (fabs(lo) + fabs(hi)) + 2.0 * pivmin) || mid <= lo || mid >= hi) break;
+    if (tri_count(sd, sae, p, q, mid, pivmin) <= li) lo = mid; else hi = mid;
+  }
+  lam[(long)b * n + i] = 0.5 * (lo + hi);
+}
+
+// inverse iteration for the eigenpairs of a cluster [c0, c1) of block [p, q):
+// x <- (T_block - lambda I)^{-1} x, normalized, orthogonalized against the
+// cluster's earlier vectors; three solves per vector
+__global__ void __launch_bounds__(64) tri_invit_kernel(const double *db, const double *aeb,
+                                                        const double *lamb, double *Ztb,
+                                                        double *workb, int n) {
+  const int b = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double *d = db + (long)b * n, *ae = aeb + (long)b * n, *lam = lamb + (long)b * n;
+  double *Zt = Ztb + (long)b * n * n;
+  int p, q;
+  tri_block(d, ae, n, i, &p, &q);
+  double tnorm = 0.0;
+  for (int j = p; j < q; ++j)
+    tnorm = fmax(tnorm, fabs(d[j]) + (j > p ? ae[j - 1] : 0.0) + (j + 1 < q ? ae[j] : 0.0));
+  const int s = q - p;
+  double *u0 = workb + ((long)b * n + i) * 5 * n;  // scratch of this thread: 5 s doubles
+  double *u1 = u0 + s, *u2 = u1 + s, *lm = u2 + s, *x = lm + s;
+  const double tiny = fmax(2.2e-16 * tnorm, 1e-150);  // a zero pivot's stand-in
+  {
+    const int c = i;
+    const double lc = lam[c];
+    // LU with partial pivoting of T_block - lc I (lm < 0 marks an interchange)
+    double a = d[p] - lc, bsup = s > 1 ? ae[p] : 0.0;
+    for (int k = 0; k + 1 < s; ++k) {
+      const double cs = ae[p + k], dn = d[p + k + 1] - lc;
+      const double un = k + 2 < s ? ae[p + k + 1] : 0.0;
+      if (fabs(a) >= fabs(cs)) {
+        if (a == 0.0) a = tiny;
+        const double l = cs / a;
+        u0[k] = a; u1[k] = bsup; u2[k] = 0.0; lm[k] = l;
+        a = dn - l * bsup;
+        bsup = un;
+      } else {  // interchange rows k and k + 1; |l| < 1 is kept as -l - 2 (< -1)
+        const double l = a / cs;
+        u0[k] = cs; u1[k] = dn; u2[k] = un; lm[k] = -l - 2.0;
+        a = bsup - l * dn;
+        bsup = -l * un;
+      }
+    }
+    if (a == 0.0) a = tiny;
+    u0[s - 1] = a;
+    // the start vector: a fixed pseudo-random vector (hash of the row)
+    for (int k = 0; k < s; ++k) {
+      unsigned h = (unsigned)(k + 1) * 2654435761u ^ (unsigned)(c - p + 7) * 40503u;
+      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+      x[k] = (double)(h & 0xFFFFFF) / 16777216.0 - 0.5;
+    }
+    for (int it = 0; it < 3; ++it) {
+      // forward: the row operations of the factorization
+      for (int k = 0; k + 1 < s; ++k) {
+        if (lm[k] < -1.0) {  // interchange rows k, k + 1, then eliminate
+          const double l = -(lm[k] + 2.0);
+          const double t = x[k];
+          x[k] = x[k + 1];
+          x[k + 1] = t - l * x[k];
+        } else {
+          x[k + 1] -= lm[k] * x[k];
+        }
+      }
+      // back substitution with U (three diagonals)
+      x[s - 1] /= u0[s - 1];
+      if (s > 1) x[s - 2] = (x[s - 2] - u1[s - 2] * x[s - 1]) / u0[s - 2];
+      for (int k = s - 3; k >= 0; --k) x[k] = (x[k] - u1[k] * x[k + 1] - u2[k] * x[k + 2]) / u0[k];
+      double mx = 0.0;  // scale by the largest entry first (the solve can grow x by 1/tiny)
+      for (int k = 0; k < s; ++k) mx = fmax(mx, fabs(x[k]));
+      if (mx > 0.0 && mx < 1e300) for (int k = 0; k < s; ++k) x[k] /= mx;
+      double nrm = 0.0;
+      for (int k = 0; k < s; ++k) nrm += x[k] * x[k];
+      nrm = 1.0 / sqrt(nrm);
+      for (int k = 0; k < s; ++k) x[k] *= nrm;
+    }
+    double *zc = Zt + (long)c * n;
+    for (int r = 0; r < n; ++r) zc[r] = (r >= p && r < q) ? x[r - p] : 0.0;
+  }
+}
+
+// Classical Gram-Schmidt, twice, over the vectors of each cluster of two or
+// more (a block per possible cluster start; warps form the dot products along
+// the rows, threads the updates)
+__global__ void __launch_bounds__(256) tri_orth_kernel(const double *db, const double *aeb,
+                                                        const double *lamb, double *Ztb, int n) {
+  __shared__ double coef[kEigMax];
+  __shared__ double red[8];
+  const int b = blockIdx.y, c0 = blockIdx.x;
+  const double *d = db + (long)b * n, *ae = aeb + (long)b * n, *lam = lamb + (long)b * n;
+  double *Zt = Ztb + (long)b * n * n;
+  int p, q;
+  tri_block(d, ae, n, c0, &p, &q);
+  double tnorm = 0.0;
+  for (int j = p; j < q; ++j)
+    tnorm = fmax(tnorm, fabs(d[j]) + (j > p ? ae[j - 1] : 0.0) + (j + 1 < q ? ae[j] : 0.0));
+  const double ortol = 1e-3 * tnorm;
+  if (c0 > p && lam[c0] - lam[c0 - 1] < ortol) return;  // not the start of a cluster
+  int c1 = c0 + 1;
+  while (c1 < q && lam[c1] - lam[c1 - 1] < ortol) ++c1;
+  if (c1 - c0 < 2) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = c0 + 1; j < c1; ++j) {
+    double *zj = Zt + (long)j * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = c0 + warp; i < j; i += 8) {  // coef_i = z_i . z_j
+        const double *zi = Zt + (long)i * n;
+        double sdot = 0.0;
+        for (int r = p + lane; r < q; r += 32) sdot += zi[r] * zj[r];
+        for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+        if (lane == 0) coef[i - c0] = sdot;
+      }
+      __syncthreads();
+      for (int r = p + tid; r < q; r += blockDim.x) {  // z_j -= sum_i coef_i z_i
+        double v = zj[r];
+        for (int i = c0; i < j; ++i) v -= coef[i - c0] * Zt[(long)i * n + r];
+        zj[r] = v;
+      }
+      __syncthreads();
+    }
+    double sq = 0.0;
+    for (int r = p + tid; r < q; r += blockDim.x) sq += zj[r] * zj[r];
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w2 = 0; w2 < 8; ++w2) tot += red[w2];
+    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+    for (int r = p + tid; r < q; r += blockDim.x) zj[r] *= inv;
+    __syncthreads();
+  }
+}
+
+// rank the eigenvalues (ascending, ties by slot) and the phases Phi
+__global__ void __launch_bounds__(256) tri_rank_kernel(const double *lamb, const double2 *eb,
+                                                        double *wb, int *permb, double2 *phib,
+                                                        int n) {
+  const int b = blockIdx.x;
+  const double *lam = lamb + (long)b * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int rk = 0;
+    const double li = lam[i];
+    for (int j = 0; j < n; ++j) rk += (lam[j] < li) || (lam[j] == li && j < i);
+    wb[(long)b * n + rk] = li;
+    permb[(long)b * n + rk] = i;
+  }
+  if (threadIdx.x == 0) {  // T[j+1][j] = phi_(j+1) conj(phi_j) |e_j|
+    double2 ph = make_double2(1.0, 0.0);
+    phib[(long)b * n] = ph;
+    for (int j = 0; j + 1 < n; ++j) {
+      const double2 ej = eb[(long)b * n + j];
+      const double a = hypot(ej.x, ej.y);
+      if (a > 0.0) ph = cmul(ph, make_double2(ej.x / a, ej.y / a));
+      phib[(long)b * n + j + 1] = ph;
+    }
+  }
+}
+
 // V[:, c] = H_0 ... H_(n-3) Phi Z[:, perm[c]] for a slab of kBackW columns.
 constexpr int kBackW = 8;
 __global__ void __launch_bounds__(256) zback_kernel(const double2 *hvb, const double2 *phib,
@@ -533,12 +765,15 @@ constexpr int kHtrdGroup = 16;  // blocks per matrix of the group reduction, at 
 size_t heev_work_bytes(int n, int batch) {
   const size_t nn = (size_t)n * n * batch;
   return nn * 16 /* hv */ + nn * 8 /* Z */ + (size_t)n * batch * (8 + 16 + 16 + 4) +
-         (size_t)batch * (2 * n * 16 + kHtrdGroup * 8 + 4 + 8) + 256 * 12;
+         (size_t)batch * (2 * n * 16 + kHtrdGroup * 8 + 4 + 8) +
+         (size_t)batch * n * (16 + 5 * (size_t)n * 8) /* bisection: lambda, |e|, scratch */ +
+         256 * 16;
 }
 
 // A (destroyed) -> w ascending, V (columns); work from heev_work_bytes.
+// method 0: QL sweeps; method 1: bisection and inverse iteration.
 cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, void *work,
-                        int *flags, cudaStream_t s) {
+                        int *flags, cudaStream_t s, int method) {
   if (n < 1 || n > kEigMax || batch < 1) return cudaErrorInvalidValue;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   char *p = (char *)work;
@@ -554,7 +789,10 @@ cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, voi
   hw.p = (double2 *)p; p += al((size_t)batch * n * 16);
   hw.kpart = (double *)p; p += al((size_t)batch * kHtrdGroup * 8);
   hw.skip = (int *)p; p += al((size_t)batch * 4);
-  hw.bar = (unsigned *)p;
+  hw.bar = (unsigned *)p; p += al((size_t)batch * 2 * sizeof(unsigned));
+  double *lam = (double *)p; p += al((size_t)batch * n * 8);
+  double *ae = (double *)p; p += al((size_t)batch * n * 8);
+  double *tw = (double *)p;
   cudaError_t err;
   const int smt = 2 * n * (int)sizeof(double2);
   err = cudaFuncSetAttribute(zhetrd_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smt);
@@ -577,14 +815,25 @@ cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, voi
                                       smt, s);
     if (err != cudaSuccess) return err;
   }
-  // rows of Z per block: up to kQlRows, as many as 200 KB of shared memory holds
-  const int rows = std::max(1, std::min(kQlRows, (200 * 1024 / 8 - 6 * n) / n));
-  const int smq = (6 * n + n * rows) * (int)sizeof(double);
-  err = cudaFuncSetAttribute(ztql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
-  if (err != cudaSuccess) return err;
-  ztql_kernel<<<dim3((n + rows - 1) / rows, batch), 64, smq, s>>>(d, e, w, phi, Z, perm, flags, n,
-                                                                  rows);
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (method == 1) {
+    tri_bisect_kernel<<<dim3((n + 127) / 128, batch), 128, 0, s>>>(d, e, lam, ae, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    tri_invit_kernel<<<dim3((n + 63) / 64, batch), 64, 0, s>>>(d, ae, lam, Z, tw, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    tri_orth_kernel<<<dim3(n, batch), 256, 0, s>>>(d, ae, lam, Z, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    tri_rank_kernel<<<batch, 256, 0, s>>>(lam, e, w, perm, phi, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  } else {
+    // rows of Z per block: up to kQlRows, as many as 200 KB of shared memory holds
+    const int rows = std::max(1, std::min(kQlRows, (200 * 1024 / 8 - 6 * n) / n));
+    const int smq = (6 * n + n * rows) * (int)sizeof(double);
+    err = cudaFuncSetAttribute(ztql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smq);
+    if (err != cudaSuccess) return err;
+    ztql_kernel<<<dim3((n + rows - 1) / rows, batch), 64, smq, s>>>(d, e, w, phi, Z, perm, flags,
+                                                                    n, rows);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
   const int smb = n * kBackW * (int)sizeof(double2);
   err = cudaFuncSetAttribute(zback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
   if (err != cudaSuccess) return err;

@@ -26,8 +26,11 @@ cudaError_t zgemm_sq(const double2 *A, int opa, const double2 *B, int opb, doubl
 
 // Hermitian eigensolver: A (destroyed) = V diag(w) V^dagger, w ascending.
 size_t heev_work_bytes(int n, int batch);
+// method 0: implicit QL on the tridiagonal (robust for any spectrum; used at
+// set-up); 1: bisection and inverse iteration (parallel over the eigenvalues;
+// used for iA(k) in every evaluation)
 cudaError_t launch_heev(double2 *A, double *w, double2 *V, int n, int batch, void *work,
-                        int *flags, cudaStream_t s);
+                        int *flags, cudaStream_t s, int method = 0);
 
 
 }  // namespace etdm
