@@ -6,9 +6,14 @@
 //
 // cos sqrt(P) and sin sqrt(P)/sqrt(P) (P = A_ov A_ov^T) are entire functions
 // of P.  They are evaluated without an eigendecomposition: Taylor series of
-// Q = P / 4^j with |Q|_F <= 1, then j doubling steps
+// Q = P / 4^j with spectral radius rho(Q) <= 1, then j doubling steps
 //   cos 2x = 1 + 4k + 2k^2 (k = cos x - 1),  sin 2x / 2x = (sin x / x) cos x,
-// which keep the small quantity k = cos x - 1 without cancellation.  The two
+// which keep the small quantity k = cos x - 1 without cancellation.  P is
+// symmetric, so the truncation error of a series in Q (and of its derivative)
+// is bounded through rho(Q), and rho(P) <= |P^m|_F^(1/m) for every m: j is
+// taken from the smallest of |P|_F, |P^2|_F^(1/2) and |P^4|_F^(1/4), the powers
+// the series needs anyway (for a P with many comparable eigenvalues the
+// Frobenius norm alone overstates rho by up to sqrt(N)).  The two
 // degree-10 series are evaluated by Paterson-Stockmeyer blocking: Q^2, Q^3,
 // Q^4, blocks B_i = sum_r c_{4i+r} Q^r (r < 4), and Horner in Q^4,
 //   p(Q) = B_0 + Q^4 (B_1 + Q^4 B_2),
@@ -753,7 +758,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
   const long NN = (long)N * N;
   const long gtid = (long)cp.rank * blockDim.x + threadIdx.x;
   const long gstride = (long)cp.size * blockDim.x;
-  __shared__ int sh_j;
+  __shared__ int sh_j, sh_jf;
   __shared__ double sh_sc;
   // A_ov as R: the float-pair engine converts the FP64 input once, in the first phase
   const void *const Ar = X::kPair ? (const void *)a.Af : (const void *)a.A;
@@ -769,12 +774,60 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     if (threadIdx.x == 0) a.red[cp.rank] = sq;
   }
   BARRIER_OR_RETURN();
-  {  // j from |P|_F (every block sums the partials in the same order)
+  {  // the range check |P|_F <= 4^kJmax (every block sums the partials in the same order)
     const double t = block_sum_of(a.red, cp.size);
     double nrm = sqrt(t);
     int j = 0;
     while (nrm > 1.0 && j <= kJmax) { nrm *= 0.25; ++j; }
     if (!(t == t) || isinf(t)) j = kJmax + 1;
+    if (threadIdx.x == 0) sh_jf = j;
+  }
+  __syncthreads();
+  const int JF = sh_jf;  // the doublings |P|_F alone would take
+  if (JF > kJmax) {
+    if (gtid == 0) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
+    return;
+  }
+  double *const Qs = a.Qk;
+  auto slot = [&](int k) { return Qs + (long)k * NN; };
+  // P^2, P^3 and P^4 unscaled (|P|_F <= 4^8 keeps |P^4| below 2^64), with the
+  // squares of P^2 and P^4 summed for the bounds on rho(P)
+  {
+    Phase ph = mkphase(N, N, N, slot(kQ2), N);
+    ph.np = 1; ph.p[0] = mk(a.P, N, 0, a.P, N, 0, 1.0);
+    double sq = 0.0;
+    run_phases<R, TCK>(cp, &ph, 1, &sq);
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) a.red[cp.size + cp.rank] = sq;
+  }
+  BARRIER_OR_RETURN();
+  {
+    Phase ph[2];
+    ph[0] = mkphase(N, N, N, slot(kQ3), N);
+    ph[0].np = 1; ph[0].p[0] = mk(a.P, N, 0, slot(kQ2), N, 0, 1.0);
+    ph[1] = mkphase(N, N, N, slot(kQ4), N);
+    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
+    run_phases<R, TCK>(cp, ph, 2);
+  }
+  BARRIER_OR_RETURN();
+  {
+    double sq = 0.0;
+    for (long e = gtid; e < NN; e += gstride) {
+      const double x = X::dbl(X::ld(slot(kQ4), e));
+      sq += x * x;
+    }
+    sq = block_sum(sq);
+    if (threadIdx.x == 0) a.red[2 * cp.size + cp.rank] = sq;
+  }
+  BARRIER_OR_RETURN();
+  {  // j from the smallest bound on rho(P)
+    const double t1 = block_sum_of(a.red, cp.size);
+    const double t2 = block_sum_of(a.red + cp.size, cp.size);
+    const double t4 = block_sum_of(a.red + 2 * cp.size, cp.size);
+    double rho = fmin(sqrt(t1), fmin(sqrt(sqrt(t2)), sqrt(sqrt(sqrt(t4)))));
+    if (!(rho == rho)) rho = sqrt(t1);
+    int j = 0;
+    while (rho > 1.0 && j < JF) { rho *= 0.25; ++j; }
     if (threadIdx.x == 0) {
       sh_j = j;
       sh_sc = ldexp(1.0, -2 * j);
@@ -783,38 +836,23 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
   __syncthreads();
   const int J = sh_j;
   const double sc = sh_sc;
-  if (J > kJmax) {
-    if (gtid == 0) atomicExch(a.flags + FLAG_ERR, ETDM_ERR_NUMERIC);
-    return;
-  }
   if (gtid == 0) { a.flags[FLAG_J] = J; a.scal[0] = sc; }
-  double *const Qs = a.Qk;
-  auto slot = [&](int k) { return Qs + (long)k * NN; };
-  // Q = sc P is kept for the reverse pass; the products below use P with the
-  // scale in their coefficients
-  for (long e = gtid; e < NN; e += gstride) X::st(slot(kQ1), e, X::scale2(X::ld(a.P, e), sc));
-  {  // Q^2 = sc^2 P P
-    Phase ph = mkphase(N, N, N, slot(kQ2), N);
-    ph.np = 1; ph.p[0] = mk(a.P, N, 0, a.P, N, 0, sc * sc);
-    run_phases<R, TCK>(cp, &ph, 1);
-  }
-  BARRIER_OR_RETURN();
-  {  // Q^3 = sc P Q^2, Q^4 = Q^2 Q^2
-    Phase ph[2];
-    ph[0] = mkphase(N, N, N, slot(kQ3), N);
-    ph[0].np = 1; ph[0].p[0] = mk(a.P, N, 0, slot(kQ2), N, 0, sc);
-    ph[1] = mkphase(N, N, N, slot(kQ4), N);
-    ph[1].np = 1; ph[1].p[0] = mk(slot(kQ2), N, 0, slot(kQ2), N, 0, 1.0);
-    run_phases<R, TCK>(cp, ph, 2);
-  }
-  BARRIER_OR_RETURN();
-  // Paterson-Stockmeyer blocks B_i = sum_r c_{4i+r} Q^r (r < 4) enter the
-  // products below as epilogue terms; B_2 is also stored for the reverse pass
+  // Q^r = sc^r P^r in place (powers of two: exact), Q = sc P kept for the
+  // reverse pass; the products below use P with the scale in their
+  // coefficients.  Paterson-Stockmeyer blocks B_i = sum_r c_{4i+r} Q^r (r < 4)
+  // enter the products below as epilogue terms; B_2 is also stored for the
+  // reverse pass
   auto cf = [&](const double *c, int k) { return k <= kTaylor ? c[k] : 0.0; };
+  const double sc2 = sc * sc, sc3 = sc2 * sc, sc4 = sc2 * sc2;
   for (long e = gtid; e < NN; e += gstride) {
     const int i = (int)(e / N), c = (int)(e % N);
-    const R q[4] = {X::from(i == c ? 1.0 : 0.0), X::ld(slot(kQ1), e), X::ld(slot(kQ2), e),
-                    X::ld(slot(kQ3), e)};
+    const R q1 = X::scale2(X::ld(a.P, e), sc), q2 = X::scale2(X::ld(slot(kQ2), e), sc2),
+            q3 = X::scale2(X::ld(slot(kQ3), e), sc3), q4 = X::scale2(X::ld(slot(kQ4), e), sc4);
+    X::st(slot(kQ1), e, q1);
+    X::st(slot(kQ2), e, q2);
+    X::st(slot(kQ3), e, q3);
+    X::st(slot(kQ4), e, q4);
+    const R q[4] = {X::from(i == c ? 1.0 : 0.0), q1, q2, q3};
     R bc = X::zero(), bs = X::zero();
     for (int r = 0; r < 4; ++r) {
       bc = X::fma(cf(a.ck, 8 + r), q[r], bc);
@@ -823,6 +861,7 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     X::st(slot(kBc2), e, bc);
     X::st(slot(kBs2), e, bs);
   }
+  BARRIER_OR_RETURN();
   {  // T = B_1 + Q^4 B_2 = B_1 + c_8 Q^4 + c_9 sc Q^4 P + c_10 Q^4 Q^2 (+ c_11 Q^4 Q^3)
     Phase ph[2];
     const double *co[2] = {a.ck, a.sk};

@@ -133,6 +133,47 @@ def test_large_rotation_exercises_doubling(small):
     U = s.get_array("Uocc").reshape(o.M, o.N)
     Uref = o.expm_eig(o.full_A(a)).real[:, : o.N]
     np.testing.assert_allclose(U, Uref, atol=1e-12)
+    # one dominant eigenvalue (21.2): the series needs 4^J >= 21.2
+    assert int(s.get_array("doublings")[0]) == 3
+
+
+def _doublings_for(x):
+    j = 0
+    while x > 1.0:
+        x *= 0.25
+        j += 1
+    return j
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spread_spectrum_doublings_follow_the_spectral_radius(water32, precision):
+    """A rotation whose P = A A^T has 128 comparable eigenvalues (largest
+    3.07, |P|_F = 12.8): the series of exp(A) converges for spectral radius
+    rho(P / 4^J) <= 1, so one doubling suffices where |P|_F alone would take
+    two; the energy, the gradient and U_occ still equal the oracle's Eq. 35 /
+    Eq. 39 route."""
+    torch = _torch()
+    d, o, s64 = water32
+    s = s64 if precision == "fp64" else _solver(d, "mixed")
+    a = synth.direction(d["a0"].shape, seed=33, scale=0.08)
+    P = a @ a.T
+    lmax = float(np.linalg.eigvalsh(P)[-1])
+    E_ref, g_ref = o.energy_grad(a)
+    E, g = s.energy_grad(torch.tensor(a, device="cuda"))
+    torch.cuda.synchronize()
+    s.check()
+    J = int(s.get_array("doublings")[0])
+    assert 4.0 ** J >= lmax
+    assert J < _doublings_for(float(np.linalg.norm(P)))
+    assert J == 1
+    tol_e, tol_g, tol_u = (1e-9, 1e-8, 1e-12) if precision == "fp64" else (E_TOL, G_TOL, 1e-11)
+    assert abs(float(E.item()) - E_ref) < tol_e
+    assert _grad_err(g.cpu().numpy(), g_ref) <= tol_g
+    U = s.get_array("Uocc").reshape(o.M, o.N)
+    Uref = o.expm_eig(o.full_A(a)).real[:, : o.N]
+    np.testing.assert_allclose(U, Uref, atol=tol_u)
+    if s is not s64:
+        s.close()
 
 
 def test_rotation_beyond_range_reports_numeric(small):
