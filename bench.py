@@ -343,14 +343,14 @@ def captured_traffic(kernel, workload):
 def dense_macs(M, N, V, J):
     """Multiply-adds of the dense chains of one evaluation (Eq. 7, 37 and the
     reverse pass), product by product as the kernels run them: forward P, Q^2,
-    Q^3, Q^4, the two Paterson-Stockmeyer steps of cos and sin (two products
-    each, c_11 = 0 for degree 10), k and s, J doublings of two products, U_vo,
-    O = C0 U, then T O (mixed) or D = 2 O O^T; reverse 4 H O (4 V O), C0^T Gbar,
-    the two products at U_vo, J reverse doublings of four products, 14 N^3 of
-    the series' reverse and the two products of g."""
+    Q^3, Q^4, the two Paterson-Stockmeyer steps of cos and sin (one product
+    each), k and s, J doublings of two products, U_vo, O = C0 U, then T O
+    (mixed) or D = 2 O O^T; reverse 4 H O (4 V O), C0^T Gbar, the two products
+    at U_vo, J reverse doublings of three products (symmetric cotangents),
+    12 N^3 of the series' reverse and the one product of g."""
     n3 = float(N) ** 3
-    fwd = 2.0 * N * N * V + (9 + 2 * J) * n3 + 2.0 * M * M * N
-    rev = 2.0 * M * M * N + 4.0 * N * N * V + (14 + 4 * J) * n3
+    fwd = 2.0 * N * N * V + (7 + 2 * J) * n3 + 2.0 * M * M * N
+    rev = 2.0 * M * M * N + 3.0 * N * N * V + (12 + 3 * J) * n3
     return fwd, rev
 
 

@@ -744,6 +744,44 @@ __device__ __forceinline__ void addc(Phase &ph, const void *c, int ld, double be
   ph.C[ph.nc] = c; ph.ldc[ph.nc] = ld; ph.beta[ph.nc] = beta; ++ph.nc;
 }
 
+// In place, for each of the n N x N row-major matrices X: X <- s (X + X^T).
+// A block takes a pair of 32 x 32 tiles (I, J), I <= J, reads both and writes
+// both, so no element is read after another block has rewritten it.  The
+// reverse pass uses it to keep the cotangents of the symmetric intermediates
+// symmetric (the chain's intermediates are symmetric functions of P, and P =
+// A A^T moves only in symmetric directions, so only the symmetric part of a
+// cotangent reaches the gradient); a pair X K + K X then is Y + Y^T with the
+// one product Y = X K.
+template <class R>
+__device__ void sym_pass(const Coop &cp, double *const *mats, int n, int N, double s) {
+  using X = Num<R>;
+  __shared__ R ta[32][33], tb[32][33];
+  const int nt = (N + 31) / 32;
+  const long pairs = (long)nt * (nt + 1) / 2;
+  for (long w = cp.rank; w < pairs * n; w += cp.size) {
+    R *const Xm = reinterpret_cast<R *>(mats[w / pairs]);
+    long p = w % pairs;
+    int I = 0;
+    while (p >= nt - I) { p -= nt - I; ++I; }
+    const int J = I + (int)p;
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31;
+      const int i1 = I * 32 + r, j1 = J * 32 + c, i2 = J * 32 + r, j2 = I * 32 + c;
+      ta[r][c] = (i1 < N && j1 < N) ? X::ld(Xm, (long)i1 * N + j1) : X::zero();
+      tb[r][c] = (i2 < N && j2 < N) ? X::ld(Xm, (long)i2 * N + j2) : X::zero();
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31;
+      const int i1 = I * 32 + r, j1 = J * 32 + c, i2 = J * 32 + r, j2 = I * 32 + c;
+      if (i1 < N && j1 < N) X::st(Xm, (long)i1 * N + j1, X::scale2(X::add(ta[r][c], tb[c][r]), s));
+      if (I != J && i2 < N && j2 < N)
+        X::st(Xm, (long)i2 * N + j2, X::scale2(X::add(tb[r][c], ta[c][r]), s));
+    }
+    __syncthreads();
+  }
+}
+
 #define BARRIER_OR_RETURN()   \
   do {                        \
     if (!cp.sync()) return;   \
@@ -862,21 +900,18 @@ __device__ void dense_forward(const DenseArgs &a, const Coop &cp) {
     X::st(slot(kBs2), e, bs);
   }
   BARRIER_OR_RETURN();
-  {  // T = B_1 + Q^4 B_2 = B_1 + c_8 Q^4 + c_9 sc Q^4 P + c_10 Q^4 Q^2 (+ c_11 Q^4 Q^3)
+  {  // T = B_1 + Q^4 B_2 (B_2 stored by the pass above)
     Phase ph[2];
     const double *co[2] = {a.ck, a.sk};
     double *const out[2] = {slot(kTc), slot(kTs)};
+    const int b2[2] = {kBc2, kBs2};
     for (int w = 0; w < 2; ++w) {
       const double *c = co[w];
       ph[w] = mkphase(N, N, N, out[w], N);
-      ph[w].np = 0;
-      ph[w].p[ph[w].np++] = mk(slot(kQ4), N, 0, a.P, N, 0, cf(c, 9) * sc);
-      ph[w].p[ph[w].np++] = mk(slot(kQ4), N, 0, slot(kQ2), N, 0, cf(c, 10));
-      ph[w].p[ph[w].np++] = mk(slot(kQ4), N, 0, slot(kQ3), N, 0, cf(c, 11));
+      ph[w].np = 1; ph[w].p[0] = mk(slot(kQ4), N, 0, slot(b2[w]), N, 0, 1.0);
       addc(ph[w], a.P, N, cf(c, 5) * sc);
       addc(ph[w], slot(kQ2), N, cf(c, 6));
       addc(ph[w], slot(kQ3), N, cf(c, 7));
-      addc(ph[w], slot(kQ4), N, cf(c, 8));
       ph[w].diag = cf(c, 4);
     }
     run_phases<R, TCK>(cp, ph, 2);
@@ -1054,23 +1089,38 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
-  const double *kb = a.Ubar;  // Kbar_J = cotangent of cos sqrt(P) = Ubar_o
+  // symmetric cotangents of k_J (Ubar_o, the first N rows of Ubar, which the
+  // residual below still reads) and of s_J
+  {
+    for (long e = gtid; e < NN; e += gstride) X::st(a.Kbar[1], e, X::ld(a.Ubar, e));
+    BARRIER_OR_RETURN();
+    double *const m2[2] = {a.Kbar[1], a.Sbar[0]};
+    sym_pass<R>(cp, m2, 2, N, 0.5);
+  }
+  BARRIER_OR_RETURN();
+  const double *kb = a.Kbar[1];
   const double *sb = a.Sbar[0];
   int pp = 0;
   for (int t = J - 1; t >= 0; --t) {
+    // k' = 4k + 2k^2, s' = s + s k with kbar', sbar' symmetric:
+    //   kbar = 4 kbar' + 2 (kbar' k + k kbar') + sym(s sbar') = Z + Z^T,
+    //          Z = 2 kbar' + 2 kbar' k + s sbar' / 2,
+    //   sbar = sbar' + sym(sbar' k) = W + W^T,  W = sbar' / 2 + sbar' k / 2
     const double *Kc = a.Kt + (long)t * NN, *Sc = a.St + (long)t * NN;
     double *kbo = a.Kbar[pp], *sbo = a.Sbar[1 - pp];
     Phase ph[2];
     ph[0] = mkphase(N, N, N, sbo, N);
-    ph[0].np = 1; ph[0].p[0] = mk(sb, N, 0, Kc, N, 0, 1.0);
-    addc(ph[0], sb, N, 1.0);
+    ph[0].np = 1; ph[0].p[0] = mk(sb, N, 0, Kc, N, 0, 0.5);
+    addc(ph[0], sb, N, 0.5);
     ph[1] = mkphase(N, N, N, kbo, N);
-    ph[1].np = 3;
+    ph[1].np = 2;
     ph[1].p[0] = mk(kb, N, 0, Kc, N, 0, 2.0);
-    ph[1].p[1] = mk(Kc, N, 0, kb, N, 0, 2.0);
-    ph[1].p[2] = mk(Sc, N, 0, sb, N, 0, 1.0);
-    addc(ph[1], kb, N, 4.0);
+    ph[1].p[1] = mk(Sc, N, 0, sb, N, 0, 0.5);
+    addc(ph[1], kb, N, 2.0);
     run_phases<R, TCK>(cp, ph, 2);
+    BARRIER_OR_RETURN();
+    double *const m2[2] = {kbo, sbo};
+    sym_pass<R>(cp, m2, 2, N, 1.0);
     BARRIER_OR_RETURN();
     kb = kbo; sb = sbo; pp = 1 - pp;
   }
@@ -1121,34 +1171,47 @@ __device__ void dense_reverse(const DenseArgs &a, int want_grad, const Coop &cp)
     X::st(wr(kQ3b), e, qb[3]);
   }
   BARRIER_OR_RETURN();
-  {  // back through Q^4 = Q^2 Q^2 and Q^3 = Q Q^2
+  {  // the cotangents of Q^4, Q^3 and the blocks' parts of Qbar, Q2bar made symmetric
+    double *const m4[4] = {wr(kQ4b), wr(kQ3b), wr(kQ1bB), wr(kQ2bB)};
+    sym_pass<R>(cp, m4, 4, N, 0.5);
+  }
+  BARRIER_OR_RETURN();
+  {  // back through Q^4 = Q^2 Q^2 and Q^3 = Q Q^2:
+     //   Q2bar = Q2bar_B + (Q4bar Q^2 + Q^2 Q4bar) + sym(Q Q3bar) = Z + Z^T,
+     //           Z = Q2bar_B / 2 + Q4bar Q^2 + Q Q3bar / 2,
+     //   Qbar_t = Q1bar_B + sym(Q3bar Q^2) = Zt + Zt^T,  Zt = Q1bar_B / 2 + Q3bar Q^2 / 2
     Phase ph[2];
-    ph[0] = mkphase(N, N, N, wr(kQ2b), N);  // Q2bar = Q2bar_B + Q4bar Q^2 + Q^2 Q4bar + Q Q3bar
-    ph[0].np = 3;
+    ph[0] = mkphase(N, N, N, wr(kQ2b), N);
+    ph[0].np = 2;
     ph[0].p[0] = mk(wr(kQ4b), N, 0, slot(kQ2), N, 0, 1.0);
-    ph[0].p[1] = mk(slot(kQ2), N, 0, wr(kQ4b), N, 0, 1.0);
-    ph[0].p[2] = mk(slot(kQ1), N, 0, wr(kQ3b), N, 0, 1.0);
-    addc(ph[0], wr(kQ2bB), N, 1.0);
-    ph[1] = mkphase(N, N, N, wr(kQ1bt), N);  // Qbar_t = Q1bar_B + Q3bar Q^2
-    ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 1.0);
-    addc(ph[1], wr(kQ1bB), N, 1.0);
+    ph[0].p[1] = mk(slot(kQ1), N, 0, wr(kQ3b), N, 0, 0.5);
+    addc(ph[0], wr(kQ2bB), N, 0.5);
+    ph[1] = mkphase(N, N, N, wr(kQ1bt), N);
+    ph[1].np = 1; ph[1].p[0] = mk(wr(kQ3b), N, 0, slot(kQ2), N, 0, 0.5);
+    addc(ph[1], wr(kQ1bB), N, 0.5);
     run_phases<R, TCK>(cp, ph, 2);
   }
   BARRIER_OR_RETURN();
-  {  // back through Q^2 = Q Q: Qbar = Qbar_t + Q2bar Q + Q Q2bar
+  {
+    double *const m2[2] = {wr(kQ2b), wr(kQ1bt)};
+    sym_pass<R>(cp, m2, 2, N, 1.0);
+  }
+  BARRIER_OR_RETURN();
+  {  // back through Q^2 = Q Q: Qbar = Qbar_t + Q2bar Q + Q Q2bar = Z + Z^T, Z = Qbar_t / 2 + Q2bar Q
     Phase ph = mkphase(N, N, N, wr(kQ1b), N);
-    ph.np = 2;
-    ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
-    ph.p[1] = mk(slot(kQ1), N, 0, wr(kQ2b), N, 0, 1.0);
-    addc(ph, wr(kQ1bt), N, 1.0);
+    ph.np = 1; ph.p[0] = mk(wr(kQ2b), N, 0, slot(kQ1), N, 0, 1.0);
+    addc(ph, wr(kQ1bt), N, 0.5);
     run_phases<R, TCK>(cp, &ph, 1);
   }
   BARRIER_OR_RETURN();
-  {  // Q = sc P: g = Abar + (Pbar + Pbar^T) A = Abar + sc Qbar A + sc Qbar^T A, written as FP64
+  {
+    double *const m1[1] = {wr(kQ1b)};
+    sym_pass<R>(cp, m1, 1, N, 1.0);
+  }
+  BARRIER_OR_RETURN();
+  {  // Q = sc P: g = Abar + (Pbar + Pbar^T) A = Abar + 2 sc Qbar A (Qbar symmetric), written as FP64
     Phase ph = mkphase(N, V, N, a.g, V);
-    ph.np = 2;
-    ph.p[0] = mk(wr(kQ1b), N, 0, Ar, V, 0, sc);
-    ph.p[1] = mk(wr(kQ1b), N, 1, Ar, V, 0, sc);
+    ph.np = 1; ph.p[0] = mk(wr(kQ1b), N, 0, Ar, V, 0, 2.0 * sc);
     addc(ph, a.Abar, V, 1.0);
     ph.out64 = 1;
     run_phases<R, TCK>(cp, &ph, 1);
