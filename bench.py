@@ -319,17 +319,21 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def captured_traffic(kernel, workload):
+def captured_traffic(kernel, workload, doublings=None):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    summaries (lines `traffic <kernel> <bytes> <source>:<sha256[:16]> <workload>`),
-    or None when the kernel's source changed since that capture."""
+    summaries (lines `traffic <kernel> <bytes> <source>:<sha256[:16]> <workload>`,
+    optionally followed by `doublings=<j>` for the dense chains, whose product
+    count depends on it), or None when the kernel's source changed since that
+    capture or the capture ran another number of doublings."""
     import glob
     import hashlib
     for summ in sorted(glob.glob(os.path.join(ROOT, "profiles", "traffic_*.md"))):
         try:
             for ln in open(summ):
                 f = ln.split()
-                if len(f) != 5 or f[0] != "traffic" or f[1] != kernel or f[4] != workload:
+                if len(f) not in (5, 6) or f[0] != "traffic" or f[1] != kernel or f[4] != workload:
+                    continue
+                if len(f) == 6 and f[5] != f"doublings={doublings}":
                     continue
                 src, h = f[3].split(":")
                 path = os.path.join(ROOT, "paper_2101_12597_gb300", "csrc", src)
@@ -492,7 +496,7 @@ def run_ours(args):
             ex_t = executed / (per_eval[dom] * 1e-3) / 1e12
             return {"bound": "tensor", "achieved": achieved, "peak": pk_s / 15.0,
                     "unit": "TFLOP/s", "frac": achieved / (pk_s / 15.0),
-                    "traffic": captured_traffic(kern, args.workload),
+                    "traffic": captured_traffic(kern, args.workload, J),
                     "kernel": kern + " (float-pair products as exact BF16 slice "
                                      "products on tcgen05)",
                     "peak_source": "derived: " + pk_src
@@ -503,7 +507,7 @@ def run_ours(args):
         if mixed:
             return {"bound": "alu", "achieved": achieved, "peak": pair_peak,
                     "unit": "TFLOP/s", "frac": achieved / pair_peak,
-                    "traffic": captured_traffic(kern + "<float2>", args.workload),
+                    "traffic": captured_traffic(kern + "<float2>", args.workload, J),
                     "kernel": kern + "<float2> (float-pair products on the FP32 pipes)",
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x "
                                    f"{sm_mhz:.0f} MHz / 12 FP32 instructions per "
