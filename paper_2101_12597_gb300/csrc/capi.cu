@@ -402,6 +402,7 @@ void etdm::alloc_opt_buffers(etdm_handle *h) {
   h->d_gt = dalloc<double>(h, nvar);
   h->d_p = dalloc<double>(h, nvar);
   h->d_dot = dalloc<double>(h, 4);
+  h->d_dotpart = dalloc<double>(h, kDotBlocks);
   CUDA_TRY(cudaMallocHost(&h->h_pinned, 16 * sizeof(double)));  // [0, 8) values, [8, 16) status words
 }
 
@@ -957,8 +958,8 @@ static int minimize_impl(etdm_handle *h, double *a_dev, int32_t n_steps, double 
     auto phi = [&](double alpha) -> Pt {
       CUDA_TRY(launch_axpy(a_dev, alpha, h->d_p, h->d_at, nvar, s));
       evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
-      CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, nullptr, s));
-      h->launches += 2;
+      CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, h->d_dotpart, s));
+      h->launches += 3;
       CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 4 * 8, cudaMemcpyDeviceToHost, s));
       check_flags(h, s);
       last_resid = hp[3];
@@ -992,14 +993,14 @@ static int minimize_impl(etdm_handle *h, double *a_dev, int32_t n_steps, double 
       }
       ++since_update;
       lbfgs(h, a_dev, h->d_g, h->d_p, s);
-      CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
-      h->launches += 1;
+      CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, h->d_dotpart, s));
+      h->launches += 2;
       // the first trial (alpha = 1) is queued before the direction is checked:
       // one synchronization for both; discarded if p is not a descent direction
       CUDA_TRY(launch_axpy(a_dev, 1.0, h->d_p, h->d_at, nvar, s));
       evaluate(h, h->d_at, h->d_dot, h->d_gt, s);
-      CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, nullptr, s));
-      h->launches += 2;
+      CUDA_TRY(launch_dot(h->d_gt, h->d_p, nvar, h->d_dot + 1, h->d_dotpart, s));
+      h->launches += 3;
       CUDA_TRY(cudaMemcpyAsync(hp, h->d_dot, 4 * 8, cudaMemcpyDeviceToHost, s));
       check_flags(h, s);
       last_resid = hp[3];
@@ -1011,8 +1012,8 @@ static int minimize_impl(etdm_handle *h, double *a_dev, int32_t n_steps, double 
         double st[3] = {0.0, 0.0, 0.0};
         CUDA_TRY(cudaMemcpy(h->d_lbstate, st, sizeof(st), cudaMemcpyHostToDevice));
         lbfgs(h, a_dev, h->d_g, h->d_p, s);
-        CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, nullptr, s));
-        h->launches += 1;
+        CUDA_TRY(launch_dot(h->d_g, h->d_p, nvar, h->d_dot + 2, h->d_dotpart, s));
+        h->launches += 2;
         CUDA_TRY(cudaMemcpyAsync(hp + 2, h->d_dot + 2, 8, cudaMemcpyDeviceToHost, s));
         check_flags(h, s);
         d0 = hp[2];

@@ -1599,11 +1599,19 @@ __global__ void precond_kernel(LbfgsArgs a, const double *g, double *pg) {
     pg[e] = precond_of(a, e, beta) * g[e];
 }
 
-// Deterministic single-block dot product (line-search scalars).
-__global__ void __launch_bounds__(1024) dot_kernel(const double *x, const double *y, long n,
-                                                   double *out) {
+// Dot product of the line-search scalars in two deterministic stages: each
+// block sums a fixed grid-stride share, then one block adds the partials in
+// index order.
+__global__ void __launch_bounds__(256) dot_part_kernel(const double *x, const double *y, long n,
+                                                       double *part) {
   double s = 0.0;
-  for (long e = threadIdx.x; e < n; e += blockDim.x) s += x[e] * y[e];
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    s += x[e] * y[e];
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void __launch_bounds__(kDotBlocks) dot_final_kernel(const double *part, int nb, double *out) {
+  double s = (int)threadIdx.x < nb ? part[threadIdx.x] : 0.0;
   s = block_sum(s);
   if (threadIdx.x == 0) *out = s;
 }
@@ -1805,9 +1813,11 @@ cudaError_t launch_precond(etdm_handle *h, const double *g, double *pg, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_dot(const double *x, const double *y, long n, double *out, double *,
+cudaError_t launch_dot(const double *x, const double *y, long n, double *out, double *part,
                        cudaStream_t s) {
-  dot_kernel<<<1, 1024, 0, s>>>(x, y, n, out);
+  const int nb = (int)std::max(1L, std::min<long>(kDotBlocks, (n + 255) / 256));
+  dot_part_kernel<<<nb, 256, 0, s>>>(x, y, n, part);
+  dot_final_kernel<<<1, kDotBlocks, 0, s>>>(part, nb, out);
   return cudaGetLastError();
 }
 

@@ -416,6 +416,7 @@ struct etdm_handle {
   // host-API staging and line search buffers
   double *d_a = nullptr, *d_g = nullptr, *d_at = nullptr, *d_gt = nullptr,
          *d_p = nullptr, *d_dot = nullptr;
+  double *d_dotpart = nullptr;  // [kDotBlocks] partial sums of the line-search dots
   double *h_pinned = nullptr;
   std::vector<void *> allocs;
   // a batch of systems (etdm_init_batch): the members own every per-system
@@ -482,7 +483,10 @@ cudaError_t launch_dense_reverse(etdm_handle *h, const double *a, double *g, dou
 cudaError_t launch_lbfgs(etdm_handle *h, const double *a, const double *g, double *p,
                          cudaStream_t s);
 cudaError_t launch_precond(etdm_handle *h, const double *g, double *pg, cudaStream_t s);
-cudaError_t launch_dot(const double *x, const double *y, long n, double *out, double *red,
+// out = x . y over n elements: kDotBlocks block partials into part, then one
+// block sums them in index order (the same result on every call)
+constexpr int kDotBlocks = 512;
+cudaError_t launch_dot(const double *x, const double *y, long n, double *out, double *part,
                        cudaStream_t s);
 cudaError_t launch_axpy(const double *x, double alpha, const double *p, double *out, long n,
                         cudaStream_t s);
