@@ -142,3 +142,28 @@ def test_oracle_plane_sample_is_the_oracles_grid_work():
     Vm = sum(o.potential_plane(o.basis_plane(i), v[i * per:(i + 1) * per])
              for i in range(int(o.n[0]))) * o.dV
     np.testing.assert_allclose(Vm, o.potential_matrix(v), rtol=1e-12, atol=1e-14)
+
+
+def test_captured_traffic_matches_source_hash_and_doublings(tmp_path, monkeypatch):
+    """The traffic of a kernel comes from a committed summary line only while
+    the kernel's source is unchanged, and for the dense chains only at the
+    doubling count it was captured with."""
+    import hashlib
+    src = tmp_path / "paper_2101_12597_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k.cu").write_text("// kernel source\n")
+    h = hashlib.sha256((src / "k.cu").read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic_w.md").write_text(
+        "text before\n"
+        f"traffic a_kernel 1000 k.cu:{h} w1\n"
+        f"traffic b_kernel 2000 k.cu:{h} w1 doublings=3\n"
+        f"traffic c_kernel 3000 k.cu:{'0' * 16} w1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.captured_traffic("a_kernel", "w1") == 1000
+    assert bench.captured_traffic("a_kernel", "w1", 5) == 1000  # no count on the line
+    assert bench.captured_traffic("a_kernel", "w2") is None
+    assert bench.captured_traffic("b_kernel", "w1", 3) == 2000
+    assert bench.captured_traffic("b_kernel", "w1", 4) is None
+    assert bench.captured_traffic("c_kernel", "w1") is None  # source changed since
