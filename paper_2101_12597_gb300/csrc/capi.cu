@@ -96,10 +96,11 @@ void evaluate(etdm_handle *h, const double *a, double *E, double *g, cudaStream_
     }
     t.done();
   }
-  // kernels: dense forward and reverse; mixed: O slices, density, 5 potential
-  // passes, V and its fixed-point conversion; FP64: density, pack, 2 x 3 FFT
-  // passes, scale, potential (+ V with the gradient)
-  h->launches += mixed ? 11 : 12;
+  // kernels: dense forward and reverse; mixed: O slices (column maxima, then
+  // the slices), density, 5 potential passes, V and its fixed-point
+  // conversion; FP64: density, pack, 2 x 3 FFT passes, scale, potential (+ V
+  // with the gradient)
+  h->launches += 12;
   if (mixed) {  // also needed for the energy: first-order correction of D's quantization
     StageTimer t(h, s, ETDM_STAGE_VMAT);
     CUDA_TRY(launch_mixed_vmat(h->plan, s));

@@ -225,6 +225,7 @@ struct OsArgs {
   uint2 *Osl;       // [chunk][M][ocw]
   float *oscale;    // [whole chunks of 128] 2^g_m
   double *dO;       // [M][N] O - Oq
+  unsigned long long *omax;  // [N] max |O| of each column as the bits of a double
 };
 
 // V of one system from its fixed-point sums (mixed path).
@@ -244,6 +245,9 @@ struct MixedPlan {
   DfLaunch dfl{};
   const OsArgs *os = nullptr;   // [n_sys] (device)
   int os_maxN = 0;
+  long os_maxMN = 0;
+  unsigned long long *omax = nullptr;  // every system's column maxima, one array
+  size_t omax_bytes = 0;               // zeroed before each evaluation's O slicing
   const VfArgs *vf = nullptr;   // [n_sys] (device)
   int vf_blocks = 1;
   unsigned long long *vfix = nullptr;  // every system's fixed-point V sums, one array

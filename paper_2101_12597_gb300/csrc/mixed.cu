@@ -1013,26 +1013,42 @@ __global__ void tables_f32_kernel(const double *sq, const double *ex, const doub
 // chain): g_m = ilogb(max_mu |O_mu,m|) + 2, K0 + K1 + K2 = O 2^(8 - g) to 24 bits
 // (K_k on the 2^-8k grid); dO = O - Oq (FP64) for the first-order energy
 // correction sum (4 H O) o dO.
+// O slicing, the first of two coalesced passes over the row-major O: the
+// largest |O| of each column (orbital), as the bits of a non-negative double
+// (which order as integers); a warp takes 32 consecutive columns over a run
+// of 64 rows.  omax is zero on entry.
+__global__ void __launch_bounds__(256) omax_kernel(const OsArgs *av, const int *active) {
+  if (!active[blockIdx.y]) return;
+  const OsArgs &a = av[blockIdx.y];
+  const int M = a.M, N = a.N;
+  const int ncg = (N + 31) / 32, nrc = (M + 63) / 64;
+  const long items = (long)ncg * nrc;
+  const int lane = threadIdx.x & 31;
+  const long wstride = ((long)gridDim.x * blockDim.x) >> 5;
+  for (long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < items; w += wstride) {
+    const int m = (int)(w % ncg) * 32 + lane, r0 = (int)(w / ncg) * 64;
+    if (m >= N) continue;
+    const int r1 = min(r0 + 64, M);
+    double mx = 0.0;
+    for (int r = r0; r < r1; ++r) mx = fmax(mx, fabs(pair::to_double(a.O[(long)r * N + m])));
+    atomicMax(a.omax + m, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// The second pass: element (r, m) cut into three slices with the column's
+// power of two 2^g (g from the column maximum), the remainder O - Oq, and
+// the column scale (written by the thread of row 0).
 __global__ void __launch_bounds__(256) oslice_kernel(const OsArgs *av, const int *active) {
   if (!active[blockIdx.y]) return;
   const OsArgs &a = av[blockIdx.y];
-  const int m = blockIdx.x;  // orbital (blockIdx.y: the system)
-  if (m >= a.N) return;
   const int M = a.M, N = a.N;
-  double mx = 0.0;
-  for (int r = threadIdx.x; r < M; r += blockDim.x) mx = fmax(mx, fabs(pair::to_double(a.O[(long)r * N + m])));
-  __shared__ double red[256];
-  red[threadIdx.x] = mx;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  mx = red[0];
-  const int g = mx > 0.0 ? ilogb(mx) + 2 : 0;
-  if (threadIdx.x == 0) a.oscale[m] = ldexpf(1.f, g);
-  for (int r = threadIdx.x; r < M; r += blockDim.x) {
-    const double o = pair::to_double(a.O[(long)r * N + m]);
+  const long MN = (long)M * N;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / N), m = (int)(e % N);
+    const double mx = __longlong_as_double((long long)a.omax[m]);
+    const int g = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (r == 0) a.oscale[m] = ldexpf(1.f, g);
+    const double o = pair::to_double(a.O[e]);
     const double t0 = ldexp(o, 8 - g);
     const double r0 = rint(t0);
     const double t1 = (t0 - r0) * 256.0;
@@ -1040,7 +1056,7 @@ __global__ void __launch_bounds__(256) oslice_kernel(const OsArgs *av, const int
     const double t2 = (t1 - r1) * 256.0;
     const double r2 = rint(t2);
     const double q = ldexp(r0 + (r1 + r2 * (1.0 / 256.0)) * (1.0 / 256.0), g - 8);
-    a.dO[(long)r * N + m] = o - q;
+    a.dO[e] = o - q;
     a.Osl[((long)(m / a.ocw) * M + r) * a.ocw + m % a.ocw] = make_uint2(
         (uint32_t)bf16_bits((float)r0) | ((uint32_t)bf16_bits((float)(r1 * (1.0 / 256.0))) << 16),
         (uint32_t)bf16_bits((float)(r2 * (1.0 / 65536.0))));
@@ -1146,8 +1162,16 @@ VfArgs vf_args(etdm_handle *h) {
 }
 
 cudaError_t launch_mixed_rho(const MixedPlan &P, cudaStream_t s) {
-  oslice_kernel<<<dim3(std::max(P.os_maxN, 1), P.n_sys), 256, 0, s>>>(P.os, P.active);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(P.omax, 0, P.omax_bytes, s);
+  if (e != cudaSuccess) return e;
+  {
+    const long warps = (long)((P.os_maxN + 31) / 32) * ((P.os_maxMN / std::max(P.os_maxN, 1) + 63) / 64);
+    const int bx = (int)std::max<long>(1, std::min<long>((warps + 7) / 8, 4096));
+    omax_kernel<<<dim3(bx, P.n_sys), 256, 0, s>>>(P.os, P.active);
+    const int bs = (int)std::max<long>(1, std::min<long>((P.os_maxMN + 255) / 256, 4096));
+    oslice_kernel<<<dim3(bs, P.n_sys), 256, 0, s>>>(P.os, P.active);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t sm = (size_t)kRhoStages * kRhoStage;
   e = cudaFuncSetAttribute(rho_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

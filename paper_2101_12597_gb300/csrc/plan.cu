@@ -37,13 +37,19 @@ void build_mixed_plan(etdm_handle *owner, const std::vector<etdm_handle *> &subs
   std::vector<DfArgs> df(ns);
   std::vector<OsArgs> os(ns);
   std::vector<VfArgs> vf(ns);
-  long maxMM = 1;
-  for (int i = 0; i < ns; ++i) {
+  long maxMM = 1, sumN = 0;
+  for (auto *h : subs) sumN += h->N;
+  P->omax = dalloc<unsigned long long>(owner, std::max<long>(sumN, 1));
+  P->omax_bytes = (size_t)std::max<long>(sumN, 1) * sizeof(unsigned long long);
+  for (int i = 0, off = 0; i < ns; ++i) {
     tc[i] = tc_args(subs[i]);
     df[i] = df_args(subs[i]);
     os[i] = os_args(subs[i]);
+    os[i].omax = P->omax + off;
+    off += subs[i]->N;
     vf[i] = vf_args(subs[i]);
     P->os_maxN = std::max(P->os_maxN, subs[i]->N);
+    P->os_maxMN = std::max(P->os_maxMN, (long)subs[i]->M * subs[i]->N);
     maxMM = std::max(maxMM, (long)subs[i]->M * subs[i]->M);
   }
   const TcArgs *d_tc = dupload(owner, tc.data(), ns);

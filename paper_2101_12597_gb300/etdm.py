@@ -261,11 +261,13 @@ class ETDM:
     exp(A) by scaling and squaring with the approximate gradient G ~ L^T, and
     ref_update (n > 0: every n steps, -1: the |L| < 3 |[A, L]| test) makes
     minimize() move the reference, C0 <- C0 exp(A), A <- 0; functional="pzsic"
-    adds the Perdew-Zunger self-interaction correction (Gamma point, kT = 0)."""
+    adds the Perdew-Zunger self-interaction correction (Gamma point, kT = 0).
+    vgroup (mixed path) sets the tiles per V group of the grid -> basis pass
+    (0: the default of 2)."""
 
     def __init__(self, sysd, precision="fp64", lbfgs_m=3, gamma=0.25, beta0=1.0,
                  device=0, dense_blocks=0, dense_tc=0, param=None, expm="eig", ref_update=0,
-                 functional="ks"):
+                 functional="ks", vgroup=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ETDM needs a CUDA GPU; there is no CPU fallback")
@@ -276,7 +278,7 @@ class ETDM:
             param = "full" if sysd.get("kpts") is not None else "occvirt"
         self.full = param == "full"
         o = _options(self.lib, precision, lbfgs_m, gamma, beta0, device, dense_blocks, dense_tc,
-                     param, expm, ref_update, functional=functional)
+                     param, expm, ref_update, vgroup=vgroup, functional=functional)
         torch.cuda.init()
         h = ctypes.c_void_p()
         rc = self.lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h))

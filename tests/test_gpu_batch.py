@@ -145,8 +145,9 @@ def test_batch_minimization_trajectories(batch, mols, sample):
     (each with its own line search, the rounds synchronized across the batch).
 
     1. Batching changes nothing but rounding: every sampled molecule's
-       trajectory follows the one its own single-system handle takes on the same
-       mixed path over the first five steps (trial counts equal, step lengths
+       trajectory follows the one its own single-system handle (with the
+       batch's V-group size) takes on the same mixed path over the first five
+       steps (trial counts equal, step lengths
        within 1e-5 relative, energies within 1e-7 relative).  The batched dense
        kernels run on a different number of blocks than the single-system
        ones, which changes the tile shapes of some products and so the
@@ -179,8 +180,11 @@ def test_batch_minimization_trajectories(batch, mols, sample):
     assert np.all(np.diff(E, axis=1) <= 1e-6 * np.abs(E[:, :1]))  # no step raises E
     final = batch.split(a.cpu().numpy())
     worst_single = 0.0
+    # the single-system handles take the V-group size the batch's set-up chose:
+    # the groups set the V pass's slice exponents, hence its rounding
+    vg = batch.tune()[0]
     for i in sample:
-        s = ETDM(mols[i], precision="mixed")
+        s = ETDM(mols[i], precision="mixed", vgroup=vg)
         ai = torch.tensor(mols[i]["a0"], device="cuda")
         Es, als, trs = s.minimize(ai, STEPS)
         s.close()

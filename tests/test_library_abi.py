@@ -187,3 +187,13 @@ def test_pzsic_options_checked(lib, kT, kfrac, param, frag):
 def test_set_reference_rejects_null_handle(lib):
     rc = lib.etdm_set_reference(None, 0, None, None)
     assert rc == -6
+
+
+def test_single_system_binding_passes_vgroup(lib):
+    """The single-system handle's V-group size reaches the options struct (the
+    batch's tuned size can be reproduced on one system)."""
+    import inspect
+    from paper_2101_12597_gb300.etdm import ETDM, _options
+    assert "vgroup" in inspect.signature(ETDM.__init__).parameters
+    for vg in (0, 2, 4, 8):
+        assert _options(lib, "mixed", 3, 0.25, 1.0, 0, 0, vgroup=vg).vgroup == vg
