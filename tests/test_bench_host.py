@@ -167,3 +167,14 @@ def test_captured_traffic_matches_source_hash_and_doublings(tmp_path, monkeypatc
     assert bench.captured_traffic("b_kernel", "w1", 3) == 2000
     assert bench.captured_traffic("b_kernel", "w1", 4) is None
     assert bench.captured_traffic("c_kernel", "w1") is None  # source changed since
+
+
+def test_l2_rule_per_workload_and_precision():
+    """Steps run back to back only where a step's inputs exceed L2: the mixed
+    path's resident slices from water32 up, the FP64 path's dense matrices from
+    water216 up; every other run flushes L2 before each timed step."""
+    assert bench.runs_back_to_back("water576", "mixed")
+    assert bench.runs_back_to_back("water32", "mixed")
+    assert not bench.runs_back_to_back("water32", "fp64")
+    assert bench.runs_back_to_back("water216", "fp64")
+    assert not bench.runs_back_to_back("small", "mixed")
