@@ -1283,6 +1283,7 @@ int etdm_init_batch(const etdm_system *sys, int32_t n_sys, const etdm_options *o
                     etdm_handle **out) {
   if (!out) return set_err(nullptr, ETDM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  if (!sys || n_sys < 1) return set_err(nullptr, ETDM_ERR_INVALID_ARG, "need n_sys >= 1 systems");
   etdm_handle *h = new etdm_handle();
   try {
     if (opt) validate(sys, opt);

@@ -197,3 +197,17 @@ def test_single_system_binding_passes_vgroup(lib):
     assert "vgroup" in inspect.signature(ETDM.__init__).parameters
     for vg in (0, 2, 4, 8):
         assert _options(lib, "mixed", 3, 0.25, 1.0, 0, 0, vgroup=vg).vgroup == vg
+
+
+def test_init_batch_needs_systems(lib):
+    """An empty batch is rejected before any system is read or device work done."""
+    from paper_2101_12597_gb300.etdm import EtdmOptions
+    d = synth.config_small_molecule()
+    s, keep = _system(lib, d)
+    o = EtdmOptions()
+    lib.etdm_default_options(ctypes.byref(o))
+    for sys_ptr, n in ((ctypes.byref(s), 0), (None, 3), (ctypes.byref(s), -2)):
+        h = ctypes.c_void_p()
+        assert lib.etdm_init_batch(sys_ptr, n, ctypes.byref(o), ctypes.byref(h)) == -1
+        assert "n_sys" in lib.etdm_last_error(None).decode()
+        assert not h.value
