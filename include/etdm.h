@@ -365,7 +365,9 @@ const char *etdm_last_error(const etdm_handle *h);
  *   h0_dev [n]      diagonal initial inverse Hessian (any positive diagonal)
  *   p_dev  [n]      output direction (may not alias the inputs)
  * Limits: 0 <= m <= 16 and 0 <= n <= 2^40; larger m returns
- * ETDM_ERR_INVALID_ARG with a message for etdm_last_error(NULL).  The first
+ * ETDM_ERR_INVALID_ARG with a message for etdm_last_error(NULL).  n = 0
+ * returns ETDM_OK at once without touching the device (the status word then
+ * keeps the previous call's value).  The first
  * call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  Every call clears the array's barrier and
