@@ -7,11 +7,14 @@
  * occupied-virtual parametrization A = [[0, A_ov], [-A_ov^T, 0]] (Eq. 36);
  * the library evaluates E(A_ov) (Eq. 1) and dE/dA_ov (Eq. 14, 20), applies
  * the diagonal preconditioner (Eq. 33-34) and the L-BFGS two-loop update
- * (Sec. 3.1), and runs the line search of Eq. 25-29 on the host.
+ * (Sec. 3.1), and runs the line search of Eq. 25-29 on the host.  With
+ * k-points (or ETDM_PARAM_FULL) the variables are instead the full
+ * skew-Hermitian A(k) of every k-point (Eq. 8, 22-24) over Bloch functions
+ * (Eq. 5), with exp(A(k)) by Eq. 35 or Eq. 38 and the gradient of Eq. 39-42.
  *
  * The model Hamiltonian is: normalized s-type Gaussians truncated at a hard
  * radius, Gaussian ion charges, a spectral (FFT) Poisson solve and Slater
- * exchange, all on a periodic real-space grid at the Gamma point.
+ * exchange, all on a periodic real-space grid.
  *
  * Conventions (every entry point):
  *  - Return value: ETDM_OK (0) or a negative ETDM_ERR_* status; nothing
@@ -23,7 +26,9 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
  *    stream).  One handle must not be used from two streams at once.
  *  - Matrices are row-major FP64.  A_ov, g and p are N x V row-major
- *    (N occupied, V = M - N virtual orbitals), so g[i*V + j] = dE/dA_ov[i][j].
+ *    (N occupied, V = M - N virtual orbitals), so g[i*V + j] = dE/dA_ov[i][j];
+ *    on the full-A path they hold n_k M^2 reals per the layout under
+ *    ETDM_PARAM_FULL.
  *  - Units: bohr, hartree.
  */
 #ifndef ETDM_H
@@ -205,7 +210,9 @@ etdm_handle *etdm_system_handle(etdm_handle *h, int32_t sys);
 int etdm_set_active(etdm_handle *h, const int32_t *active_host);
 
 /* One energy + gradient evaluation (Eq. 1, 7, 12, 11, 14 / 39-41):
- * a_dev [N*V] (A_ov) -> E_dev [1] and g_dev [N*V] = dE/dA_ov (Eq. 20).
+ * a_dev [N*V] (A_ov) -> E_dev [1] and g_dev [N*V] = dE/dA_ov (Eq. 20);
+ * on the full-A path a_dev and g_dev hold n_k M^2 reals (ETDM_PARAM_FULL),
+ * and with ETDM_EXPM_SS g_dev is the approximate gradient of Eq. 42.
  * On a batch: a_dev, g_dev packed per etdm_system_layout, E_dev [n_sys].
  * g_dev may be NULL (energy only).  Asynchronous on `stream`; numerical
  * failures (NaN/Inf, |P| beyond the exp range) are reported by the next
@@ -304,7 +311,9 @@ enum {
   ETDM_ARR_VGROUP_NU = 19,    /* mixed precision: functions in each V group's union
                                  list (i32, one per group) */
   ETDM_ARR_DOUBLINGS = 20,    /* [1] i32 doubling steps j of the last evaluation's
-                                 exp (|A_ov A_ov^T|_F / 4^j <= 1) */
+                                 exp: the least j with b / 4^j <= 1, where
+                                 b = min(|P|_F, |P^2|_F^(1/2), |P^4|_F^(1/4))
+                                 bounds the spectral radius of P = A_ov A_ov^T */
   ETDM_ARR_STATUS = 21,       /* [4] i32 device status words: error code, doublings,
                                  then where a bounded wait of the tensor-core
                                  products gave up and at which count (0: none) */
