@@ -110,7 +110,8 @@ typedef struct {
   double box[3];          /* orthorhombic cell edges, bohr */
   int32_t grid[3];        /* grid points per axis; prime factors <= 13 */
   double ion_sigma;       /* Gaussian ion-charge width, bohr */
-  int32_t n_electrons;    /* even, 2 <= n_electrons <= 2M; N = n_electrons/2 */
+  int32_t n_electrons;    /* even, 2 <= n_electrons <= 2M; N = n_electrons/2;
+                             the occupied-virtual path needs N < M */
   int32_t n_k;            /* k-points (0: Gamma point, occupied-virtual A) */
   const double *k_frac;   /* [n_k*3] k-points in fractional reciprocal coordinates */
   const double *k_w;      /* [n_k] positive weights summing to 1 */

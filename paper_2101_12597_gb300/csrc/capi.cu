@@ -184,6 +184,9 @@ void validate(const etdm_system *sys, const etdm_options *opt) {
   } else if (opt && opt->param != ETDM_PARAM_OCCVIRT) {
     bad("unknown param");
   }
+  if (!full && sys->n_electrons / 2 >= sys->n_basis)
+    bad("the occupied-virtual path needs a virtual orbital (n_electrons < 2 n_basis): "
+        "with none, A_ov is empty and E does not depend on it");
   if (opt) {
     if (opt->expm != ETDM_EXPM_EIG && opt->expm != ETDM_EXPM_SS) bad("unknown expm");
     if (opt->expm == ETDM_EXPM_SS && !full) bad("expm = ETDM_EXPM_SS needs the full-A path");

@@ -69,6 +69,7 @@ def _system(lib, d, **over):
     (dict(grid=(34, 32, 32)), "prime factors"),
     (dict(n_electrons=7), "even"),
     (dict(n_electrons=40), "n_electrons"),
+    (dict(n_electrons=32), "virtual orbital"),
     (dict(bf_rcut=np.full(16, 100.0)), "bf_rcut"),
     (dict(bf_exp=-np.ones(16)), "bf_exp"),
 ])
