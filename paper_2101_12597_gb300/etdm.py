@@ -193,10 +193,16 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _stream_ptr(stream):
+def _stream_ptr(stream, dev):
+    """The cudaStream_t of `stream` for a call on the device dev (default: dev's
+    current stream).  A stream of another device is refused: the library runs
+    the call on dev and would queue it on a stream it cannot use there."""
     import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    if stream.device != dev:
+        raise ValueError(f"stream is on {stream.device}, not {dev}")
+    return ctypes.c_void_p(stream.cuda_stream)
 
 
 def _system_struct(sysd, s=None):
@@ -334,7 +340,7 @@ class ETDM:
         rc = self.lib.etdm_energy_grad(self.h, ctypes.c_void_p(a.data_ptr()),
                                        ctypes.c_void_p(E.data_ptr()),
                                        ctypes.c_void_p(g.data_ptr()) if want_grad else None,
-                                       _stream_ptr(stream))
+                                       _stream_ptr(stream, self.dev))
         self._raise(rc)
         return E, (g if want_grad else None)
 
@@ -358,7 +364,7 @@ class ETDM:
         self._check_tensor(out, self.var_shape, "out")
         self._raise(self.lib.etdm_precondition(self.h, ctypes.c_void_p(g.data_ptr()),
                                                ctypes.c_void_p(out.data_ptr()),
-                                               _stream_ptr(stream)))
+                                               _stream_ptr(stream, self.dev)))
         return out
 
     def lbfgs_step(self, a, g, out=None, stream=None):
@@ -373,7 +379,7 @@ class ETDM:
         self._raise(self.lib.etdm_lbfgs_step(self.h, ctypes.c_void_p(a.data_ptr()),
                                              ctypes.c_void_p(g.data_ptr()),
                                              ctypes.c_void_p(out.data_ptr()),
-                                             _stream_ptr(stream)))
+                                             _stream_ptr(stream, self.dev)))
         return out
 
     def lbfgs_reset(self):
@@ -411,7 +417,7 @@ class ETDM:
         self._raise(self.lib.etdm_minimize(self.h, ctypes.c_void_p(a.data_ptr()), n_steps,
                                            _dptr(E), _dptr(al),
                                            tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                           _stream_ptr(stream)))
+                                           _stream_ptr(stream, self.dev)))
         return E, al, tr
 
     def minimize_converge(self, a, max_steps=333, tol=1e-10 / 27.211386245988 ** 2,
@@ -427,13 +433,13 @@ class ETDM:
         self._raise(self.lib.etdm_minimize_converge(
             self.h, ctypes.c_void_p(a.data_ptr()), max_steps, tol, _dptr(E), _dptr(al),
             tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(res), ctypes.byref(done),
-            _stream_ptr(stream)))
+            _stream_ptr(stream, self.dev)))
         k = int(done.value)
         return k, E[:k + 1], al[:k + 1], tr[:k + 1], res[:k + 1]
 
     def check(self, stream=None):
         """Wait for `stream` and raise EtdmError on a deferred device-side error."""
-        self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream)))
+        self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream, self.dev)))
 
     def get_array(self, name):
         """A copy of an internal array (names in ARRAYS: S, T, C0, rho, H, ...)."""
@@ -539,7 +545,7 @@ class ETDMBatch:
         _require(g, self.dev, "g", numel=self.nvar)
         self._raise(self.lib.etdm_energy_grad(self.h, ctypes.c_void_p(a.data_ptr()),
                                               ctypes.c_void_p(E.data_ptr()),
-                                              ctypes.c_void_p(g.data_ptr()), _stream_ptr(stream)))
+                                              ctypes.c_void_p(g.data_ptr()), _stream_ptr(stream, self.dev)))
         return E, g
 
     def energy_grad_host(self, a):
@@ -567,14 +573,14 @@ class ETDMBatch:
         self._raise(self.lib.etdm_minimize(self.h, ctypes.c_void_p(a.data_ptr()), n_steps,
                                            _dptr(E), _dptr(al),
                                            tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                           _stream_ptr(stream)))
+                                           _stream_ptr(stream, self.dev)))
         return E, al, tr
 
     def lbfgs_reset(self):
         self._raise(self.lib.etdm_lbfgs_reset(self.h))
 
     def check(self, stream=None):
-        self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream)))
+        self._raise(self.lib.etdm_check(self.h, _stream_ptr(stream, self.dev)))
 
     def launches(self):
         """Kernel launches (graph kernel nodes included) since the last call."""
@@ -613,6 +619,8 @@ def pair_gemm(A, B, ta=False, tb=False, stream=None):
         raise ValueError(f"inner dimensions differ: {k} and {k2}")
     _require(A, A.device, "A", shape=tuple(A.shape))
     _require(B, A.device, "B", shape=tuple(B.shape))
+    if stream is not None and stream.device != A.device:
+        raise ValueError(f"stream is on {stream.device}, not {A.device}")
     C = torch.empty((m, n), dtype=torch.float64, device=A.device)
     with torch.cuda.device(A.device):
         st = stream if stream is not None else torch.cuda.current_stream(A.device)

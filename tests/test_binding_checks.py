@@ -122,6 +122,7 @@ def _stub_solver(N=3, V=5):
 def test_marshalling_with_a_stub_library():
     class Stream:  # a caller-owned stream: only its handle is passed on
         cuda_stream = 0
+        device = CPU
 
     st = Stream()
     s = _stub_solver()
@@ -153,3 +154,19 @@ def test_marshalling_with_a_stub_library():
         s.energy_grad_host(np.zeros((5, 3)))
     E, gh = s.energy_grad_host(np.zeros((3, 5)))
     assert gh.shape == (3, 5) and s.lib.calls[-1][0] == "etdm_energy_grad_host"
+
+
+def test_handle_calls_refuse_a_stream_of_another_device():
+    """A caller's stream must belong to the handle's device: the check runs
+    before the library is called."""
+    class Stream:
+        cuda_stream = 0
+        device = torch.device("meta")
+
+    s = _stub_solver()
+    a = _t(3, 5)
+    with pytest.raises(ValueError, match="stream is on meta"):
+        s.energy_grad(a, stream=Stream())
+    with pytest.raises(ValueError, match="stream is on meta"):
+        s.lbfgs_step(a, _t(3, 5), stream=Stream())
+    assert s.lib.calls == []
