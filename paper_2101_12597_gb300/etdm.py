@@ -445,6 +445,9 @@ class ETDM:
         """A copy of an internal array (names in ARRAYS: S, T, C0, rho, H, ...)."""
         which, dt = ARRAYS[name]
         nb = self.lib.etdm_array_bytes(self.h, which)
+        if nb < 0:
+            raise ValueError(f"array {name!r} does not exist on this handle's path "
+                             "(full A, occupied-virtual or a batch)")
         out = np.zeros(nb // np.dtype(dt).itemsize, dtype=dt)
         self._raise(self.lib.etdm_get_array(self.h, which, out.ctypes.data_as(ctypes.c_void_p),
                                             nb))

@@ -170,3 +170,14 @@ def test_handle_calls_refuse_a_stream_of_another_device():
     with pytest.raises(ValueError, match="stream is on meta"):
         s.lbfgs_step(a, _t(3, 5), stream=Stream())
     assert s.lib.calls == []
+
+
+def test_get_array_of_another_path_is_a_clear_error():
+    """etdm_array_bytes returns -1 for an array the handle's path does not
+    have (e.g. Uocc on the full-A path); the binding says so instead of
+    allocating a negative size."""
+    s = _stub_solver()
+    s.lib.etdm_array_bytes = lambda h, which: -1
+    with pytest.raises(ValueError, match="'Uocc' does not exist"):
+        s.get_array("Uocc")
+    assert s.lib.calls == []
