@@ -268,3 +268,92 @@ def test_ql_reciprocal_square_root():
         y = y * (1.5 - (0.5 * x) * (y * y))
     rel = np.abs(y - 1.0 / np.sqrt(x)) * np.sqrt(x)
     assert rel.max() < 2.0 * 2.0 ** -52
+
+
+# ---- five slices: the tensor-core products of the dense chains --------------------------
+
+C5 = [F(3, 2) * F(2) ** (23 - 8 * k) for k in range(5)]  # 1.5 * 2^(23 - 8k)
+
+
+def slices5(x, sc):
+    """The cut of the dense chains' products: the high part alone gives the
+    slices of orders 0 and 1 (exact remainders), the low part joins the
+    remainder once (the one rounding), then orders 2, 3 and 4."""
+    r = [fadd(fma(x[0], sc, C5[0]), -C5[0])]
+    u = fma(x[0], sc, -r[0])
+    r.append(fadd(fadd(u, C5[1]), -C5[1]))
+    u = fma(x[1], sc, fadd(u, -r[1]))
+    for k in (2, 3, 4):
+        r.append(fadd(fadd(u, C5[k]), -C5[k]))
+        u = fadd(u, -r[k])
+    return r
+
+
+def _row_scale(row):
+    """2^(8 - e) with e = floor(log2 max|hi|) + 2: every |x sc| below 128."""
+    b = max(abs(x[0]) for x in row)
+    return F(2) ** (8 - (math.floor(math.log2(b)) + 2))
+
+
+def _five_slice_dot(a, b):
+    """sum_k a_k b_k as the tensor-core product forms it over one chunk of K:
+    slices of both operands, orders 0, 1, 2 in one FP32 sum each, orders 3 and
+    4 together in a fourth, orders >= 5 dropped.  Returns the four sums, their
+    exact values, the scales and the slices."""
+    sa, sb = _row_scale(a), _row_scale(b)
+    A = [slices5(x, sa) for x in a]
+    B = [slices5(y, sb) for y in b]
+    acc, exact = [F(0)] * 4, [F(0)] * 4
+    for ra, rb in zip(A, B):
+        for i in range(5):
+            for j in range(5 - i):
+                p = ra[i] * rb[j]
+                assert fmul(ra[i], rb[j]) == p        # BF16 x BF16 is exact in FP32
+                q = min(i + j, 3)
+                acc[q] = fadd(acc[q], p)
+                exact[q] += p
+    return acc, exact, sa, sb, A, B
+
+
+def test_five_slices_bf16_and_reconstruct():
+    """Each slice is exact in BF16, a multiple of 2^-8k with a numerator of at
+    most 129, and the five carry x sc to 2^-32 (x sc below 128)."""
+    rng = np.random.default_rng(21)
+    row = [split(float(v)) for v in rng.uniform(-1, 1, 400) * 2.0 ** rng.integers(-9, 3, 400)]
+    sc = _row_scale(row)
+    for x in row:
+        assert abs((x[0] + x[1]) * sc) < 128
+        r = slices5(x, sc)
+        for k, rk in enumerate(r):
+            assert sig_bits(rk) <= 8
+            num = rk * F(2) ** (8 * k)
+            assert num.denominator == 1 and abs(num) <= 129
+        assert abs((x[0] + x[1]) * sc - sum(r)) <= F(2) ** -32
+
+
+def test_five_slice_orders_exact_over_a_chunk_and_the_product_bound():
+    """Over a chunk of 21 K steps (336 elements) the sums of orders 0, 1 and 2
+    never round: at most three products per element of at most 129^2 units
+    each, 3 x 336 x 129^2 < 2^24.  The chunk's dot product, in the units of the
+    scaled operands (|a sc|, |b sc| < 128), is within K 2^-23 + K^2 2^-32 of
+    the exact one: per element the dropped orders >= 5 (at most
+    129^2 (4 2^-40 + 3 2^-48 + ...) < 2^-23.9) and the slices' cut (2^-32 of
+    each operand, times the other one), and the FP32 sum of orders 3 and 4,
+    each addition within 2^-24 of a partial sum of at most K 2^-7.9.  For
+    operands whose entries are comparable to their maxima the error is about
+    2^-39 of sum |a b| or less (checked at 2^-38)."""
+    assert 3 * 336 * 129 ** 2 < 2 ** 24
+    rng = np.random.default_rng(22)
+    K = 336
+    for spread in (9, 0):  # entries over 2^9 below the maximum, or comparable to it
+        a = [split(float(v)) for v in rng.uniform(-1, 1, K) * 2.0 ** rng.integers(-spread, 1, K)]
+        b = [split(float(v)) for v in rng.uniform(-1, 1, K) * 2.0 ** rng.integers(-spread, 1, K)]
+        acc, exact, sa, sb, _, _ = _five_slice_dot(a, b)
+        for q in range(3):
+            assert acc[q] == exact[q]
+        got = acc[0] + acc[1] + acc[2] + acc[3]
+        true = sum((x[0] + x[1]) * sa * (y[0] + y[1]) * sb for x, y in zip(a, b))
+        assert abs(got - true) <= K * F(2) ** -23 + K * K * F(2) ** -32
+        if spread == 0:
+            mag = sum(abs((x[0] + x[1]) * sa * (y[0] + y[1]) * sb) for x, y in zip(a, b))
+            assert abs(got - true) <= F(2) ** -38 * mag
