@@ -403,8 +403,9 @@ int etdm_lbfgs_direction_noalloc_status(void *stream);
  * tensor-core path of the mixed-precision dense chains (Eq. 7, 37 and their
  * reverse pass): rows of op(A) and columns of op(B) cut into five exact BF16
  * slices each after a power-of-two scaling, the slice products of orders <= 4
- * accumulated exactly in tensor memory (orders 0-3 over 240-element K chunks,
- * order 4 in FP32), the chunks summed in float pairs.  Relative error about
+ * accumulated in tensor memory (orders 0, 1 and 2 exactly, one sum each over
+ * 336-element K chunks; orders 3 and 4 together in one FP32 sum), the chunks
+ * summed in float pairs.  Relative error about
  * 2^-39 of |A||B| per entry.  Allocates its workspace, synchronizes `stream`;
  * a bounded wait that gave up returns ETDM_ERR_TIMEOUT.  1 <= m, n, k <= 65536. */
 int etdm_pair_gemm(const double *A_dev, const double *B_dev, double *C_dev, int32_t m,
