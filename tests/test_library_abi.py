@@ -212,3 +212,46 @@ def test_init_batch_needs_systems(lib):
         assert lib.etdm_init_batch(sys_ptr, n, ctypes.byref(o), ctypes.byref(h)) == -1
         assert "n_sys" in lib.etdm_last_error(None).decode()
         assert not h.value
+
+
+@pytest.mark.parametrize("field,value,frag", [
+    ("precision", 2, "unknown precision"),
+    ("lbfgs_m", 0, "lbfgs_m"),
+    ("lbfgs_m", 17, "lbfgs_m"),
+    ("gamma", 1.5, "gamma"),
+    ("beta0", 0.0, "beta0"),
+    ("dense_blocks", -1, "dense_blocks"),
+    ("dense_tc", 2, "dense_tc"),
+    ("vgroup", 9, "vgroup"),
+    ("functional", 2, "unknown functional"),
+])
+def test_general_options_checked(lib, field, value, frag):
+    """Every option outside its documented range is refused at set-up, before
+    any device work, with a message naming it."""
+    from paper_2101_12597_gb300.etdm import EtdmOptions
+    s, keep = _system(lib, synth.config_small_molecule())
+    o = EtdmOptions()
+    lib.etdm_default_options(ctypes.byref(o))
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    assert lib.etdm_init_basis(ctypes.byref(s), ctypes.byref(o), ctypes.byref(h)) == -1
+    assert frag in lib.etdm_last_error(None).decode()
+    assert not h.value
+
+
+def test_geometry_checked(lib):
+    """Positions outside the cell, a function on a missing atom, a non-positive
+    ion width or cell edge are refused at set-up with a message."""
+    for mutate, frag in [
+        (lambda s, k: k["pos"].__setitem__((0, 0), -0.1), "positions"),
+        (lambda s, k: k["bf_atom"].__setitem__(0, 99), "bf_atom"),
+        (lambda s, k: setattr(s, "ion_sigma", 0.0), "ion_sigma"),
+        (lambda s, k: s.box.__setitem__(1, -1.0), "box"),
+        (lambda s, k: setattr(s, "n_atoms", 0), "n_atoms"),
+    ]:
+        s, keep = _system(lib, synth.config_small_molecule())  # fresh arrays each time
+        mutate(s, keep)
+        h = ctypes.c_void_p()
+        assert lib.etdm_init_basis(ctypes.byref(s), None, ctypes.byref(h)) == -1
+        assert frag in lib.etdm_last_error(None).decode(), frag
+        assert not h.value
