@@ -1,0 +1,28 @@
+"""The C ABI from C: include/etdm.h compiles as strict C99 and a C program
+links against libetdm.so and gets the documented answers from the calls that
+return before any device work (no GPU needed)."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_c99_client_compiles_links_and_runs(tmp_path):
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2101_12597_gb300 import build
+    build.build()
+    libdir = os.path.join(ROOT, "paper_2101_12597_gb300")
+    exe = str(tmp_path / "abi_client")
+    subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror",
+                    "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_client.c"),
+                    "-L", libdir, "-letdm", f"-Wl,-rpath,{libdir}", "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) >= 15 and all(ln.startswith("ok ") for ln in lines), r.stdout
