@@ -358,8 +358,10 @@ enum {
 int etdm_set_profiling(etdm_handle *h, int on);
 int etdm_stage_times(etdm_handle *h, double *ms, int64_t *counts);
 
-/* Message of the last failed call on h (or, when h is NULL, of the last failed
- * init or handle-free call).  Valid until the next call on the same handle. */
+/* Message of the last failed call on h (or, when h is NULL, of the calling
+ * thread's last failed call without a handle: init, the allocation-free
+ * direction, the tensor-core product).  Valid until the next call on the same
+ * handle (or, for NULL, the next failing such call on the same thread). */
 const char *etdm_last_error(const etdm_handle *h);
 
 /* Allocation-free L-BFGS direction.  The paper has no counterpart: this entry

@@ -19,7 +19,9 @@ using namespace etdm;
 
 namespace {
 
-std::string g_init_err;
+// message of the last failure without a handle, per host thread (handles
+// initialized from several threads at once do not race on it)
+thread_local std::string g_init_err;
 
 void release(etdm_handle *h) {
   if (!h) return;

@@ -2,12 +2,20 @@
  * it) and every entry point must link.  Only calls that fail or answer before
  * any device work are made, so no GPU is needed; the program prints one line
  * per check and returns the number of failed checks. */
+#include <pthread.h>
 #include <stdio.h>
 #include <string.h>
 
 #include "etdm.h"
 
 static int fails = 0;
+
+/* a failing call without a handle on another thread */
+static void *other_thread(void *arg) {
+  etdm_handle *h = NULL;
+  (void)arg;
+  return etdm_init_basis(NULL, NULL, &h) == ETDM_ERR_INVALID_ARG ? (void *)1 : NULL;
+}
 
 static void check(int ok, const char *what) {
   printf("%s %s\n", ok ? "ok" : "FAIL", what);
@@ -45,6 +53,15 @@ int main(void) {
   check(etdm_lbfgs_direction_noalloc(g, NULL, NULL, 17, 4, g, g, NULL) == ETDM_ERR_INVALID_ARG,
         "allocation-free direction: more pairs than its scratch holds");
   check(strstr(etdm_last_error(NULL), "scratch limit") != NULL, "... with the limit named");
+  {
+    pthread_t t;
+    void *ok = NULL;
+    check(pthread_create(&t, NULL, other_thread, NULL) == 0 && pthread_join(t, &ok) == 0 &&
+              ok != NULL,
+          "a failing init on another thread");
+    check(strstr(etdm_last_error(NULL), "scratch limit") != NULL,
+          "... leaves this thread's message as it was");
+  }
   check(etdm_lbfgs_direction_noalloc(g, NULL, NULL, 0, 0, g, g, NULL) == ETDM_OK,
         "allocation-free direction: n = 0 returns at once");
   check(etdm_pair_gemm(NULL, NULL, NULL, 0, 0, 0, 0, 0, NULL) == ETDM_ERR_INVALID_ARG,

@@ -21,7 +21,8 @@ def test_c99_client_compiles_links_and_runs(tmp_path):
     subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror",
                     "-I", os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "abi_client.c"),
-                    "-L", libdir, "-letdm", f"-Wl,-rpath,{libdir}", "-o", exe], check=True)
+                    "-L", libdir, "-letdm", f"-Wl,-rpath,{libdir}", "-pthread", "-o", exe],
+                   check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout + r.stderr
     lines = r.stdout.strip().splitlines()
